@@ -1,0 +1,261 @@
+"""FP64 CPU oracle for the multiwalk / indirect-index Barnes-Hut path of
+"Accelerated FDPS" (arXiv 1907.02290).
+
+TEST INFRASTRUCTURE. Only the test suite, ``__graft_entry__.smoke()`` and
+``bench.py`` (its cpu_baseline leg and its ``--impl reference`` arm) may import
+this package. It shares no code with the CUDA path and never imports it.
+
+The arithmetic lives in ``afdps_oracle.c`` (plain C, FP64, built with
+``-ffp-contract=off``); this module only compiles it and marshals numpy arrays.
+Each wrapper names the paper passage its C function follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "afdps_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "libafdps_oracle.so")
+_lib = None
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I64 = ctypes.POINTER(ctypes.c_int64)
+_I32 = ctypes.POINTER(ctypes.c_int32)
+_U64 = ctypes.POINTER(ctypes.c_uint64)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP when available). Returns the path."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+            "-fPIC", "-shared", _SRC, "-o", _LIB_PATH + ".tmp", "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
+                       capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(_LIB_PATH + ".tmp", _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        L = _lib
+        L.afo_direct_sum.argtypes = [ctypes.c_int64, _D, _D, _D, _D, ctypes.c_double,
+                                     ctypes.c_int64, _I64, _D, _D, _D, _D]
+        L.afo_root_cell.argtypes = [ctypes.c_int64, _D, _D, _D, _D]
+        L.afo_root_cell.restype = ctypes.c_int
+        L.afo_morton_keys.argtypes = [ctypes.c_int64, _D, _D, _D, _D, _U64]
+        L.afo_radix_sort.argtypes = [ctypes.c_int64, _U64, _U64, _I64]
+        L.afo_build.argtypes = [ctypes.c_int64, _D, _D, _D, _D, ctypes.c_int, ctypes.c_int,
+                                ctypes.c_double, ctypes.c_double, ctypes.c_int]
+        L.afo_build.restype = ctypes.c_void_p
+        L.afo_update.argtypes = [ctypes.c_void_p, _D, _D, _D, _D]
+        L.afo_update.restype = ctypes.c_int
+        L.afo_force.argtypes = [ctypes.c_void_p, _D, _D, _D, _D]
+        L.afo_free.argtypes = [ctypes.c_void_p]
+        L.afo_sizes.argtypes = [ctypes.c_void_p, _I64]
+        L.afo_get_root.argtypes = [ctypes.c_void_p, _D]
+        L.afo_get_order.argtypes = [ctypes.c_void_p, _U64, _I64]
+        L.afo_get_cells.argtypes = [ctypes.c_void_p, _I32, _I64, _I64, _I64, _I64, _I32, _I64]
+        L.afo_get_moments.argtypes = [ctypes.c_void_p, _D, _D, _D]
+        L.afo_get_groups.argtypes = [ctypes.c_void_p, _I64, _I64, _I64, _D, _I32]
+        L.afo_get_lists.argtypes = [ctypes.c_void_p, _I64, _I32, _I64, _I32]
+        L.afo_leapfrog.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64,
+                                   _D, _D, _D, _D, _D, _D, _D, _D, _D, _D, _D,
+                                   ctypes.c_double, ctypes.c_int, ctypes.c_int, _I64]
+        L.afo_leapfrog.restype = ctypes.c_int
+        L.afo_num_threads.restype = ctypes.c_int
+    return _lib
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def num_threads() -> int:
+    return int(lib().afo_num_threads())
+
+
+def direct_sum(x, y, z, m, eps, targets=None):
+    """Softened O(N^2) direct sum (the exact target; reading R1).
+    Returns (ax, ay, az, pot) for ``targets`` (default: all particles)."""
+    x, y, z, m = map(_f64, (x, y, z, m))
+    n = x.shape[0]
+    tgt = np.arange(n, dtype=np.int64) if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
+    out = [np.zeros(tgt.shape[0]) for _ in range(4)]
+    lib().afo_direct_sum(n, _p(x, _D), _p(y, _D), _p(z, _D), _p(m, _D), float(eps),
+                         tgt.shape[0], _p(tgt, _I64), *(_p(o, _D) for o in out))
+    return tuple(out)
+
+
+def root_cell(x, y, z):
+    """Root cell (Section 4.3; reading R2): (cx, cy, cz, L)."""
+    x, y, z = map(_f64, (x, y, z))
+    root = np.zeros(4)
+    rc = lib().afo_root_cell(x.shape[0], _p(x, _D), _p(y, _D), _p(z, _D), _p(root, _D))
+    if rc != 0:
+        raise ValueError("non-finite coordinate")
+    return root
+
+
+def morton_keys(x, y, z, root):
+    """Morton keys (Section 4.3 step 1; reading R3)."""
+    x, y, z = map(_f64, (x, y, z))
+    root = _f64(root)
+    keys = np.zeros(x.shape[0], dtype=np.uint64)
+    lib().afo_morton_keys(x.shape[0], _p(x, _D), _p(y, _D), _p(z, _D), _p(root, _D),
+                          _p(keys, _U64))
+    return keys
+
+
+def radix_sort(keys):
+    """LSD radix sort of key-index pairs (Section 4.3 step 2, Section 6.2).
+    Returns (sorted keys, permutation)."""
+    keys = np.ascontiguousarray(keys, dtype=np.uint64)
+    ks = np.zeros_like(keys)
+    perm = np.zeros(keys.shape[0], dtype=np.int64)
+    lib().afo_radix_sort(keys.shape[0], _p(keys, _U64), _p(ks, _U64), _p(perm, _I64))
+    return ks, perm
+
+
+@dataclass
+class Cells:
+    level: np.ndarray
+    first: np.ndarray
+    count: np.ndarray
+    parent: np.ndarray
+    skip: np.ndarray
+    n_child: np.ndarray
+    child: np.ndarray  # (n_cells, 8), -1 where the octant is empty
+
+
+class Tree:
+    """One construction step of the tree method (Section 4.2, 4.3) kept for
+    reuse steps. Wraps the C ``afo_tree``; arrays are copied out on request."""
+
+    def __init__(self, x, y, z, m, *, n_leaf=16, n_grp=64, theta=0.5, eps=1.0 / 256,
+                 quad=False):
+        self._args = dict(n_leaf=n_leaf, n_grp=n_grp, theta=theta, eps=eps, quad=quad)
+        x, y, z, m = map(_f64, (x, y, z, m))
+        self.n = x.shape[0]
+        h = lib().afo_build(self.n, _p(x, _D), _p(y, _D), _p(z, _D), _p(m, _D),
+                            int(n_leaf), int(n_grp), float(theta), float(eps), int(quad))
+        if not h:
+            raise ValueError("non-finite particle data")
+        self._h = ctypes.c_void_p(h)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().afo_free(h)
+            self._h = None
+
+    def sizes(self):
+        s = np.zeros(5, dtype=np.int64)
+        lib().afo_sizes(self._h, _p(s, _I64))
+        return {"n": int(s[0]), "n_cells": int(s[1]), "n_groups": int(s[2]),
+                "n_epj": int(s[3]), "n_spj": int(s[4])}
+
+    def root(self):
+        r = np.zeros(4)
+        lib().afo_get_root(self._h, _p(r, _D))
+        return r
+
+    def order(self):
+        keys = np.zeros(self.n, dtype=np.uint64)
+        perm = np.zeros(self.n, dtype=np.int64)
+        lib().afo_get_order(self._h, _p(keys, _U64), _p(perm, _I64))
+        return keys, perm
+
+    def cells(self) -> Cells:
+        nc = self.sizes()["n_cells"]
+        lv = np.zeros(nc, np.int32)
+        f, c, p, s = (np.zeros(nc, np.int64) for _ in range(4))
+        nch = np.zeros(nc, np.int32)
+        ch = np.zeros(nc * 8, np.int64)
+        lib().afo_get_cells(self._h, _p(lv, _I32), _p(f, _I64), _p(c, _I64), _p(p, _I64),
+                            _p(s, _I64), _p(nch, _I32), _p(ch, _I64))
+        return Cells(lv, f, c, p, s, nch, ch.reshape(nc, 8))
+
+    def moments(self):
+        """(M, COM (n_cells,3), Q (n_cells,6) as xx yy zz xy xz yz)."""
+        nc = self.sizes()["n_cells"]
+        M = np.zeros(nc)
+        com = np.zeros(nc * 3)
+        q = np.zeros(nc * 6)
+        lib().afo_get_moments(self._h, _p(M, _D), _p(com, _D), _p(q, _D))
+        return M, com.reshape(nc, 3), q.reshape(nc, 6)
+
+    def groups(self):
+        ng = self.sizes()["n_groups"]
+        f, c, cell = (np.zeros(ng, np.int64) for _ in range(3))
+        box = np.zeros(ng * 6)
+        self_in = np.zeros(ng, np.int32)
+        lib().afo_get_groups(self._h, _p(f, _I64), _p(c, _I64), _p(cell, _I64), _p(box, _D),
+                             _p(self_in, _I32))
+        return {"first": f, "count": c, "cell": cell, "box": box.reshape(ng, 6),
+                "self_in": self_in}
+
+    def lists(self):
+        """CSR lists: (epj_off, epj, spj_off, spj)."""
+        s = self.sizes()
+        ng = s["n_groups"]
+        eo = np.zeros(ng + 1, np.int64)
+        so = np.zeros(ng + 1, np.int64)
+        e = np.zeros(s["n_epj"], np.int32)
+        sp = np.zeros(s["n_spj"], np.int32)
+        lib().afo_get_lists(self._h, _p(eo, _I64), _p(e, _I32), _p(so, _I64), _p(sp, _I32))
+        return eo, e, so, sp
+
+    def update(self, x, y, z, m):
+        """Reusing step (Section 4.2): new particle data, same topology/lists."""
+        x, y, z, m = map(_f64, (x, y, z, m))
+        if lib().afo_update(self._h, _p(x, _D), _p(y, _D), _p(z, _D), _p(m, _D)) != 0:
+            raise ValueError("non-finite particle data")
+
+    def force(self):
+        """FP64 force on the saved lists, caller order: (ax, ay, az, pot)."""
+        out = [np.zeros(self.n) for _ in range(4)]
+        lib().afo_force(self._h, *(_p(o, _D) for o in out))
+        return tuple(out)
+
+    def interactions(self):
+        """Sum over groups of n_i * (n_epj + n_spj) (self pair included)."""
+        g = self.groups()
+        eo, _, so, _ = self.lists()
+        return int(np.sum(g["count"] * ((eo[1:] - eo[:-1]) + (so[1:] - so[:-1]))))
+
+
+def leapfrog(x, y, z, vx, vy, vz, m, *, dt, n_steps, n_reuse, n_leaf=16, n_grp=64,
+             theta=0.5, eps=1.0 / 256, quad=False):
+    """Kick-drift-kick leapfrog with list reuse (reading R11). Evaluation 0
+    (the initial force) is a construction step; evaluation k is one when
+    k % n_reuse == 0. Returns new (x, y, z, vx, vy, vz, ax, ay, az, pot)."""
+    arrs = [np.array(a, dtype=np.float64, copy=True) for a in (x, y, z, vx, vy, vz)]
+    m = _f64(m)
+    t = Tree(*arrs[:3], m, n_leaf=n_leaf, n_grp=n_grp, theta=theta, eps=eps, quad=quad)
+    acc = [np.ascontiguousarray(a) for a in t.force()]
+    h = ctypes.c_void_p(t._h.value)
+    t._h = None  # ownership moves to the C loop
+    counter = np.array([1], dtype=np.int64)
+    rc = lib().afo_leapfrog(ctypes.byref(h), arrs[0].shape[0], *(_p(a, _D) for a in arrs),
+                            _p(m, _D), *(_p(a, _D) for a in acc), float(dt), int(n_steps),
+                            int(n_reuse), _p(counter, _I64))
+    lib().afo_free(h)
+    if rc != 0:
+        raise ValueError("non-finite particle data")
+    return (*arrs, *acc)

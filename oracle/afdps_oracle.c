@@ -1,0 +1,800 @@
+/*
+ * afdps_oracle.c -- plain, slow, FP64 CPU oracle for the multiwalk,
+ * indirect-index Barnes-Hut gravity path of "Accelerated FDPS -- Algorithms
+ * to Use Accelerators with FDPS" (Iwasawa, Namekata, Nitadori, Nomura, Wang,
+ * Tsubouchi, Makino; arXiv 1907.02290).
+ *
+ * TEST INFRASTRUCTURE. This file is the checker, not the product. Only the
+ * test suite, __graft_entry__.smoke() and bench.py's cpu_baseline / reference
+ * leg load it. It shares no code, header, table or helper with the CUDA path
+ * in paper_1907_02290_gb300/csrc, and neither side includes the other.
+ *
+ * Every function follows the step of the paper named in its comment, in the
+ * paper's order. Where the paper is silent the reading taken is stated at the
+ * function and collected in the "Readings" list below.
+ *
+ * Readings of the paper (silent or ambiguous points), fixed here:
+ *  R1 force law: Plummer-softened Newtonian gravity with G = 1,
+ *     a_i = sum_j m_j (x_j - x_i) / (|x_j - x_i|^2 + eps^2)^(3/2),
+ *     phi_i = -sum_j m_j / (|x_j - x_i|^2 + eps^2)^(1/2), j != i.
+ *     (Section 6.2 counts n_op = 23 flops per interaction; consistent.)
+ *     A pair with |x_j - x_i|^2 + eps^2 == 0 contributes nothing.
+ *  R2 root cell (Section 4.3 "coordinates of the root cell are determined
+ *     using the positions of all particles"): centre = (min+max)/2 per axis,
+ *     side L = smallest power of two >= 1.000001 * (largest extent); L = 1
+ *     when the extent is 0.
+ *  R3 Morton key (Section 4.3 step 1; 64-bit key, Section 6.2): 21 bits per
+ *     axis, q_d = floor((x_d - (c_d - L/2)) * (2^21 / L)) clamped to
+ *     [0, 2^21 - 1]; bit 3k+2 = x bit k, 3k+1 = y bit k, 3k = z bit k.
+ *  R4 sort (Section 4.3 step 2, Section 6.2): LSD radix sort, eight passes of
+ *     eight-bit digits, stable; equal keys keep caller order.
+ *  R5 tree (Section 4.3 step 4): a cell splits while count > n_leaf and its
+ *     level < 21; children are the non-empty octants in Morton order, found
+ *     per level by binary search on the sorted keys. Cells are built level by
+ *     level; the exported numbering is depth-first pre-order (children in
+ *     Morton order), which equals ascending (first particle, level).
+ *  R6 moments (Section 4.3, bottom-up): monopole M = sum m and centre of mass
+ *     COM = S / M with S = sum m x ("center-of-mass approximation",
+ *     Section 6.2). Leaves sum their particles in Morton order; internal
+ *     cells sum their children in Morton order. A massless cell takes its
+ *     geometric centre as COM. Quadrupole (traceless, about the COM):
+ *     Q_ab = sum m (3 d_a d_b - |d|^2 delta_ab); parents add the children's
+ *     Q shifted by the parallel-axis term.
+ *  R7 groups (Section 3, n_grp): i-groups are the maximal cells holding at
+ *     most n_grp particles, in depth-first order; a leaf holding more than
+ *     n_grp particles (only possible at level 21, or when n_grp < n_leaf) is
+ *     cut into consecutive chunks of n_grp.
+ *  R8 opening criterion (Section 2 "standard Barnes-Hut scheme", opening
+ *     angle theta): a cell of side s is accepted as a superparticle for
+ *     group g iff s^2 < theta^2 d^2, with d the distance from the cell's COM
+ *     to the group's bounding box (0 inside). Evaluated in IEEE FP32 on
+ *     FP32-rounded inputs, no fused multiply-add, in the order written in
+ *     mac_accept(), so that any two implementations decide identically.
+ *  R9 list order: the walk is depth-first from the root, children in Morton
+ *     order; an accepted cell appends its cell id to the SPJ list, an opened
+ *     leaf appends all its particles (Morton positions) to the EPJ list.
+ *  R10 quadrupole softening: phi_q = -(1/2) r.Q.r / rs^5 with
+ *     rs^2 = |r|^2 + eps^2, and a_q = Q r / rs^5 - (5/2)(r.Q.r) r / rs^7,
+ *     r = x_i - COM.
+ *  R11 integrator: kick-drift-kick leapfrog; force evaluation k of a run is
+ *     a construction step when k % n_reuse == 0, else it reuses the lists.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define AFO_LEVELS 21 /* deepest level; 21 key bits per axis */
+
+/* ------------------------------------------------------------------------ */
+/* Exact target: softened direct summation (R1).                           */
+/* ------------------------------------------------------------------------ */
+
+/* For every target t in tgt[0..n_tgt), sum over all j != tgt[t]. */
+void afo_direct_sum(int64_t n, const double *x, const double *y, const double *z,
+                    const double *m, double eps, int64_t n_tgt, const int64_t *tgt,
+                    double *ax, double *ay, double *az, double *pot) {
+  const double eps2 = eps * eps;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t t = 0; t < n_tgt; t++) {
+    const int64_t i = tgt[t];
+    double sx = 0.0, sy = 0.0, sz = 0.0, sp = 0.0;
+    for (int64_t j = 0; j < n; j++) {
+      if (j == i) continue;
+      const double dx = x[j] - x[i], dy = y[j] - y[i], dz = z[j] - z[i];
+      const double r2 = dx * dx + dy * dy + dz * dz + eps2;
+      if (r2 == 0.0) continue;
+      const double rinv = 1.0 / sqrt(r2);
+      const double mr = m[j] * rinv;
+      const double mr3 = mr * rinv * rinv;
+      sx += mr3 * dx;
+      sy += mr3 * dy;
+      sz += mr3 * dz;
+      sp -= mr;
+    }
+    ax[t] = sx;
+    ay[t] = sy;
+    az[t] = sz;
+    pot[t] = sp;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Root cell (Section 4.3; reading R2).                                     */
+/* ------------------------------------------------------------------------ */
+
+/* root[0..2] = centre, root[3] = side L (a power of two). Returns 0, or -1
+ * when a coordinate is not finite. */
+int afo_root_cell(int64_t n, const double *x, const double *y, const double *z,
+                  double root[4]) {
+  double lo[3] = {0.0, 0.0, 0.0}, hi[3] = {0.0, 0.0, 0.0};
+  const double *p[3] = {x, y, z};
+  for (int64_t i = 0; i < n; i++)
+    for (int d = 0; d < 3; d++)
+      if (!isfinite(p[d][i])) return -1;
+  if (n > 0) {
+    for (int d = 0; d < 3; d++) lo[d] = hi[d] = p[d][0];
+    for (int64_t i = 1; i < n; i++)
+      for (int d = 0; d < 3; d++) {
+        if (p[d][i] < lo[d]) lo[d] = p[d][i];
+        if (p[d][i] > hi[d]) hi[d] = p[d][i];
+      }
+  }
+  double ext = 0.0;
+  for (int d = 0; d < 3; d++) {
+    root[d] = (lo[d] + hi[d]) * 0.5;
+    const double e = hi[d] - lo[d];
+    if (e > ext) ext = e;
+  }
+  const double target = ext * 1.000001;
+  double L = 1.0;
+  if (target > 0.0) {
+    while (L < target) L *= 2.0;
+    while (L * 0.5 >= target) L *= 0.5;
+  }
+  root[3] = L;
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Morton keys (Section 4.3 step 1; reading R3).                            */
+/* ------------------------------------------------------------------------ */
+
+static uint32_t grid_coord(double v, double corner, double scale) {
+  const double t = floor((v - corner) * scale);
+  if (!(t > 0.0)) return 0u;
+  if (t > 2097151.0) return 2097151u;
+  return (uint32_t)t;
+}
+
+/* Interleave one bit at a time: x bit k -> key bit 3k+2, y -> 3k+1, z -> 3k. */
+static uint64_t interleave3(uint32_t qx, uint32_t qy, uint32_t qz) {
+  uint64_t key = 0;
+  for (int k = 0; k < AFO_LEVELS; k++) {
+    key |= (uint64_t)((qx >> k) & 1u) << (3 * k + 2);
+    key |= (uint64_t)((qy >> k) & 1u) << (3 * k + 1);
+    key |= (uint64_t)((qz >> k) & 1u) << (3 * k);
+  }
+  return key;
+}
+
+void afo_morton_keys(int64_t n, const double *x, const double *y, const double *z,
+                     const double root[4], uint64_t *keys) {
+  const double half = root[3] * 0.5;
+  const double cx = root[0] - half, cy = root[1] - half, cz = root[2] - half;
+  const double scale = 2097152.0 / root[3]; /* 2^21 / L, a power of two */
+  for (int64_t i = 0; i < n; i++)
+    keys[i] = interleave3(grid_coord(x[i], cx, scale), grid_coord(y[i], cy, scale),
+                          grid_coord(z[i], cz, scale));
+}
+
+/* ------------------------------------------------------------------------ */
+/* Radix sort of key-index pairs (Section 4.3 step 2, Section 6.2: 8-bit    */
+/* chunks, eight passes; each pass is a stable counting sort).              */
+/* ------------------------------------------------------------------------ */
+
+void afo_radix_sort(int64_t n, const uint64_t *keys_in, uint64_t *keys_out, int64_t *perm) {
+  uint64_t *ka = malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
+  uint64_t *kb = malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
+  int64_t *ia = malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  int64_t *ib = malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  for (int64_t i = 0; i < n; i++) {
+    ka[i] = keys_in[i];
+    ia[i] = i;
+  }
+  for (int pass = 0; pass < 8; pass++) {
+    const int shift = 8 * pass;
+    int64_t count[257];
+    memset(count, 0, sizeof(count));
+    for (int64_t i = 0; i < n; i++) count[((ka[i] >> shift) & 255u) + 1]++;
+    for (int b = 0; b < 256; b++) count[b + 1] += count[b];
+    for (int64_t i = 0; i < n; i++) {
+      const int b = (int)((ka[i] >> shift) & 255u);
+      const int64_t dst = count[b]++;
+      kb[dst] = ka[i];
+      ib[dst] = ia[i];
+    }
+    uint64_t *tk = ka; ka = kb; kb = tk;
+    int64_t *ti = ia; ia = ib; ib = ti;
+  }
+  for (int64_t i = 0; i < n; i++) {
+    keys_out[i] = ka[i];
+    perm[i] = ia[i];
+  }
+  free(ka); free(kb); free(ia); free(ib);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Tree state.                                                              */
+/* ------------------------------------------------------------------------ */
+
+typedef struct afo_tree {
+  int64_t n;
+  int n_leaf, n_grp, quad;
+  double theta, eps;
+  double root[4];
+  uint64_t *keys;   /* sorted keys */
+  int64_t *perm;    /* perm[k] = caller index of the k-th particle in Morton order */
+  double *xs, *ys, *zs, *ms; /* Morton-ordered EPI/EPJ copies (Section 4.3 step 3) */
+  /* cells, exported in depth-first pre-order */
+  int64_t n_cells;
+  int32_t *level;
+  int64_t *first, *count, *parent, *skip;
+  int32_t *n_child;
+  int64_t *child; /* 8 slots per cell, by octant digit, -1 when empty */
+  double *mass, *smom, *com, *qmom; /* M; S = sum m x (3); COM (3); Q (6) */
+  /* groups */
+  int64_t n_groups;
+  int64_t *g_first, *g_count, *g_cell;
+  double *g_box; /* min x,y,z then max x,y,z */
+  int32_t *g_self;
+  /* lists (CSR, one EPJ and one SPJ list per group) */
+  int64_t *epj_off, *spj_off;
+  int32_t *epj, *spj;
+} afo_tree;
+
+static void *xcalloc(size_t count, size_t size) {
+  return calloc(count > 0 ? count : 1, size);
+}
+
+void afo_free(afo_tree *t) {
+  if (!t) return;
+  free(t->keys); free(t->perm); free(t->xs); free(t->ys); free(t->zs); free(t->ms);
+  free(t->level); free(t->first); free(t->count); free(t->parent); free(t->skip);
+  free(t->n_child); free(t->child); free(t->mass); free(t->smom); free(t->com); free(t->qmom);
+  free(t->g_first); free(t->g_count); free(t->g_cell); free(t->g_box); free(t->g_self);
+  free(t->epj_off); free(t->spj_off); free(t->epj); free(t->spj);
+  free(t);
+}
+
+/* First index in [lo, hi) with keys[idx] >= v (binary search, Section 4.3). */
+static int64_t lower_bound_key(const uint64_t *keys, int64_t lo, int64_t hi, uint64_t v) {
+  while (lo < hi) {
+    const int64_t mid = lo + (hi - lo) / 2;
+    if (keys[mid] < v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+/* Reorder (Section 4.3 step 3): copy FP data into Morton order. */
+static void reorder(afo_tree *t, const double *x, const double *y, const double *z,
+                    const double *m) {
+  for (int64_t k = 0; k < t->n; k++) {
+    const int64_t i = t->perm[k];
+    t->xs[k] = x[i];
+    t->ys[k] = y[i];
+    t->zs[k] = z[i];
+    t->ms[k] = m[i];
+  }
+}
+
+/* Link (Section 4.3 step 4, reading R5): build cells level by level, top
+ * down; the children of a splitting cell are found by binary search for the
+ * boundaries of its eight octants. Then renumber depth-first pre-order. */
+static void link_cells(afo_tree *t) {
+  const int64_t n = t->n;
+  int64_t cap = 64, nc = 0;
+  int32_t *lv = malloc(sizeof(int32_t) * cap);
+  int64_t *fi = malloc(sizeof(int64_t) * cap), *ct = malloc(sizeof(int64_t) * cap);
+  int64_t *pa = malloc(sizeof(int64_t) * cap), *ch = malloc(sizeof(int64_t) * cap * 8);
+  if (n > 0) {
+    lv[0] = 0; fi[0] = 0; ct[0] = n; pa[0] = -1;
+    for (int o = 0; o < 8; o++) ch[o] = -1;
+    nc = 1;
+  }
+  int64_t lvl_begin = 0, lvl_end = nc;
+  for (int l = 0; l < AFO_LEVELS && lvl_begin < lvl_end; l++) {
+    for (int64_t c = lvl_begin; c < lvl_end; c++) {
+      if (ct[c] <= t->n_leaf) continue;
+      const uint64_t prefix = t->keys[fi[c]] >> (3 * (AFO_LEVELS - l));
+      const int shift = 3 * (AFO_LEVELS - l - 1);
+      const int64_t end = fi[c] + ct[c];
+      for (int o = 0; o < 8; o++) {
+        const uint64_t k0 = ((prefix << 3) | (uint64_t)o) << shift;
+        const uint64_t k1 = ((prefix << 3) + (uint64_t)o + 1) << shift;
+        const int64_t b0 = lower_bound_key(t->keys, fi[c], end, k0);
+        const int64_t b1 = lower_bound_key(t->keys, b0, end, k1);
+        if (b1 <= b0) continue;
+        if (nc == cap) {
+          cap *= 2;
+          lv = realloc(lv, sizeof(int32_t) * cap);
+          fi = realloc(fi, sizeof(int64_t) * cap);
+          ct = realloc(ct, sizeof(int64_t) * cap);
+          pa = realloc(pa, sizeof(int64_t) * cap);
+          ch = realloc(ch, sizeof(int64_t) * cap * 8);
+        }
+        lv[nc] = l + 1; fi[nc] = b0; ct[nc] = b1 - b0; pa[nc] = c;
+        for (int q = 0; q < 8; q++) ch[nc * 8 + q] = -1;
+        ch[c * 8 + o] = nc;
+        nc++;
+      }
+    }
+    lvl_begin = lvl_end;
+    lvl_end = nc;
+  }
+  /* Depth-first pre-order numbering (children in Morton order). */
+  int64_t *rank = malloc(sizeof(int64_t) * (size_t)(nc > 0 ? nc : 1));
+  int64_t *size = malloc(sizeof(int64_t) * (size_t)(nc > 0 ? nc : 1));
+  for (int64_t c = nc - 1; c >= 0; c--) { /* deeper levels come later */
+    size[c] = 1;
+    for (int o = 0; o < 8; o++)
+      if (ch[c * 8 + o] >= 0) size[c] += size[ch[c * 8 + o]];
+  }
+  int64_t *stack = malloc(sizeof(int64_t) * (size_t)(nc > 0 ? nc : 1));
+  int64_t sp = 0, next = 0;
+  if (nc > 0) stack[sp++] = 0;
+  while (sp > 0) {
+    const int64_t c = stack[--sp];
+    rank[c] = next++;
+    for (int o = 7; o >= 0; o--)
+      if (ch[c * 8 + o] >= 0) stack[sp++] = ch[c * 8 + o];
+  }
+  t->n_cells = nc;
+  t->level = xcalloc(nc, sizeof(int32_t));
+  t->first = xcalloc(nc, sizeof(int64_t));
+  t->count = xcalloc(nc, sizeof(int64_t));
+  t->parent = xcalloc(nc, sizeof(int64_t));
+  t->skip = xcalloc(nc, sizeof(int64_t));
+  t->n_child = xcalloc(nc, sizeof(int32_t));
+  t->child = xcalloc(nc * 8, sizeof(int64_t));
+  for (int64_t c = 0; c < nc; c++) {
+    const int64_t r = rank[c];
+    t->level[r] = lv[c];
+    t->first[r] = fi[c];
+    t->count[r] = ct[c];
+    t->parent[r] = pa[c] >= 0 ? rank[pa[c]] : -1;
+    t->skip[r] = r + size[c];
+    int nch = 0;
+    for (int o = 0; o < 8; o++) {
+      const int64_t cc = ch[c * 8 + o];
+      t->child[r * 8 + o] = cc >= 0 ? rank[cc] : -1;
+      if (cc >= 0) nch++;
+    }
+    t->n_child[r] = nch;
+  }
+  free(lv); free(fi); free(ct); free(pa); free(ch); free(rank); free(size); free(stack);
+}
+
+/* Geometric centre of a cell: the root corner plus (q + 1/2) cell sides. */
+static void cell_centre(const afo_tree *t, int64_t c, double out[3]) {
+  const int l = t->level[c];
+  const uint64_t prefix = l > 0 ? t->keys[t->first[c]] >> (3 * (AFO_LEVELS - l)) : 0;
+  uint32_t q[3] = {0, 0, 0};
+  for (int k = 0; k < l; k++) {
+    q[0] |= (uint32_t)((prefix >> (3 * k + 2)) & 1u) << k;
+    q[1] |= (uint32_t)((prefix >> (3 * k + 1)) & 1u) << k;
+    q[2] |= (uint32_t)((prefix >> (3 * k)) & 1u) << k;
+  }
+  const double s = ldexp(t->root[3], -l);
+  for (int d = 0; d < 3; d++)
+    out[d] = (t->root[d] - t->root[3] * 0.5) + ((double)q[d] + 0.5) * s;
+}
+
+static int is_leaf(const afo_tree *t, int64_t c) { return t->n_child[c] == 0; }
+
+/* Multipole moments, bottom-up (Section 4.3; reading R6). Pre-order ids are
+ * visited from last to first, so every child is done before its parent. */
+static void moments(afo_tree *t) {
+  const int64_t nc = t->n_cells;
+  for (int64_t c = nc - 1; c >= 0; c--) {
+    double M = 0.0, S[3] = {0.0, 0.0, 0.0};
+    if (is_leaf(t, c)) {
+      for (int64_t k = t->first[c]; k < t->first[c] + t->count[c]; k++) {
+        M += t->ms[k];
+        S[0] += t->ms[k] * t->xs[k];
+        S[1] += t->ms[k] * t->ys[k];
+        S[2] += t->ms[k] * t->zs[k];
+      }
+    } else {
+      for (int o = 0; o < 8; o++) {
+        const int64_t cc = t->child[c * 8 + o];
+        if (cc < 0) continue;
+        M += t->mass[cc];
+        for (int d = 0; d < 3; d++) S[d] += t->smom[cc * 3 + d];
+      }
+    }
+    t->mass[c] = M;
+    for (int d = 0; d < 3; d++) t->smom[c * 3 + d] = S[d];
+    if (M != 0.0) {
+      for (int d = 0; d < 3; d++) t->com[c * 3 + d] = S[d] / M;
+    } else {
+      cell_centre(t, c, &t->com[c * 3]);
+    }
+  }
+  if (!t->quad) return;
+  for (int64_t c = nc - 1; c >= 0; c--) {
+    double Q[6] = {0, 0, 0, 0, 0, 0}; /* xx yy zz xy xz yz */
+    const double *g = &t->com[c * 3];
+    if (is_leaf(t, c)) {
+      for (int64_t k = t->first[c]; k < t->first[c] + t->count[c]; k++) {
+        const double d[3] = {t->xs[k] - g[0], t->ys[k] - g[1], t->zs[k] - g[2]};
+        const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        const double mk = t->ms[k];
+        Q[0] += mk * (3.0 * d[0] * d[0] - r2);
+        Q[1] += mk * (3.0 * d[1] * d[1] - r2);
+        Q[2] += mk * (3.0 * d[2] * d[2] - r2);
+        Q[3] += mk * (3.0 * d[0] * d[1]);
+        Q[4] += mk * (3.0 * d[0] * d[2]);
+        Q[5] += mk * (3.0 * d[1] * d[2]);
+      }
+    } else {
+      for (int o = 0; o < 8; o++) {
+        const int64_t cc = t->child[c * 8 + o];
+        if (cc < 0) continue;
+        const double *gc = &t->com[cc * 3];
+        const double D[3] = {gc[0] - g[0], gc[1] - g[1], gc[2] - g[2]};
+        const double r2 = D[0] * D[0] + D[1] * D[1] + D[2] * D[2];
+        const double mc = t->mass[cc];
+        const double *qc = &t->qmom[cc * 6];
+        Q[0] += qc[0] + mc * (3.0 * D[0] * D[0] - r2);
+        Q[1] += qc[1] + mc * (3.0 * D[1] * D[1] - r2);
+        Q[2] += qc[2] + mc * (3.0 * D[2] * D[2] - r2);
+        Q[3] += qc[3] + mc * (3.0 * D[0] * D[1]);
+        Q[4] += qc[4] + mc * (3.0 * D[0] * D[2]);
+        Q[5] += qc[5] + mc * (3.0 * D[1] * D[2]);
+      }
+    }
+    for (int q = 0; q < 6; q++) t->qmom[c * 6 + q] = Q[q];
+  }
+}
+
+/* i-groups (Section 3, n_grp; reading R7), depth-first. */
+static void make_groups(afo_tree *t) {
+  int64_t cap = 64, ng = 0;
+  int64_t *gf = malloc(sizeof(int64_t) * cap), *gc = malloc(sizeof(int64_t) * cap);
+  int64_t *gcell = malloc(sizeof(int64_t) * cap);
+  int64_t *stack = malloc(sizeof(int64_t) * (size_t)(t->n_cells > 0 ? t->n_cells : 1));
+  int64_t sp = 0;
+  if (t->n_cells > 0) stack[sp++] = 0;
+  while (sp > 0) {
+    const int64_t c = stack[--sp];
+    if (t->count[c] <= t->n_grp || is_leaf(t, c)) {
+      for (int64_t s = 0; s < t->count[c]; s += t->n_grp) {
+        if (ng == cap) {
+          cap *= 2;
+          gf = realloc(gf, sizeof(int64_t) * cap);
+          gc = realloc(gc, sizeof(int64_t) * cap);
+          gcell = realloc(gcell, sizeof(int64_t) * cap);
+        }
+        gf[ng] = t->first[c] + s;
+        gc[ng] = (t->count[c] - s) < t->n_grp ? (t->count[c] - s) : t->n_grp;
+        gcell[ng] = c;
+        ng++;
+      }
+      continue;
+    }
+    for (int o = 7; o >= 0; o--)
+      if (t->child[c * 8 + o] >= 0) stack[sp++] = t->child[c * 8 + o];
+  }
+  free(stack);
+  t->n_groups = ng;
+  t->g_first = gf;
+  t->g_count = gc;
+  t->g_cell = gcell;
+  t->g_box = xcalloc(ng * 6, sizeof(double));
+  t->g_self = xcalloc(ng, sizeof(int32_t));
+}
+
+/* Tight FP64 bounding box of every group's particles. */
+static void group_boxes(afo_tree *t) {
+  for (int64_t g = 0; g < t->n_groups; g++) {
+    double *b = &t->g_box[g * 6];
+    const int64_t f = t->g_first[g];
+    b[0] = b[3] = t->xs[f];
+    b[1] = b[4] = t->ys[f];
+    b[2] = b[5] = t->zs[f];
+    for (int64_t k = f + 1; k < f + t->g_count[g]; k++) {
+      if (t->xs[k] < b[0]) b[0] = t->xs[k];
+      if (t->ys[k] < b[1]) b[1] = t->ys[k];
+      if (t->zs[k] < b[2]) b[2] = t->zs[k];
+      if (t->xs[k] > b[3]) b[3] = t->xs[k];
+      if (t->ys[k] > b[4]) b[4] = t->ys[k];
+      if (t->zs[k] > b[5]) b[5] = t->zs[k];
+    }
+  }
+}
+
+/* Opening criterion (reading R8), FP32, no contraction (built with
+ * -ffp-contract=off). Returns 1 when the cell is accepted as an SPJ. */
+static int mac_accept(const float bmin[3], const float bmax[3], const float com[3],
+                      float s2, float theta2) {
+  float d[3];
+  for (int k = 0; k < 3; k++) {
+    d[k] = 0.0f;
+    if (com[k] < bmin[k]) d[k] = bmin[k] - com[k];
+    else if (com[k] > bmax[k]) d[k] = com[k] - bmax[k];
+  }
+  float d2 = d[0] * d[0];
+  d2 = d2 + d[1] * d[1];
+  d2 = d2 + d[2] * d[2];
+  const float rhs = theta2 * d2;
+  return s2 < rhs;
+}
+
+/* Barnes' vectorised walk for one group (Section 2, Section 4.1; R8, R9).
+ * With epj/spj NULL it only counts. */
+static void walk_group(const afo_tree *t, int64_t g, int32_t *epj, int32_t *spj,
+                       int64_t *n_epj, int64_t *n_spj, int32_t *self_in) {
+  float bmin[3], bmax[3];
+  for (int k = 0; k < 3; k++) {
+    bmin[k] = (float)t->g_box[g * 6 + k];
+    bmax[k] = (float)t->g_box[g * 6 + 3 + k];
+  }
+  const float theta2 = (float)t->theta * (float)t->theta;
+  const float L = (float)t->root[3];
+  int64_t ne = 0, ns = 0;
+  int32_t self = 0;
+  int64_t stack[8 * (AFO_LEVELS + 2)];
+  int sp = 0;
+  if (t->n_cells > 0) stack[sp++] = 0;
+  while (sp > 0) {
+    const int64_t c = stack[--sp];
+    const float s = ldexpf(L, -t->level[c]);
+    const float s2 = s * s;
+    float com[3];
+    for (int k = 0; k < 3; k++) com[k] = (float)t->com[c * 3 + k];
+    if (mac_accept(bmin, bmax, com, s2, theta2)) {
+      if (spj) spj[ns] = (int32_t)c;
+      ns++;
+    } else if (is_leaf(t, c)) {
+      const int64_t f = t->first[c];
+      for (int64_t k = f; k < f + t->count[c]; k++) {
+        if (epj) epj[ne] = (int32_t)k;
+        ne++;
+      }
+      if (t->g_first[g] >= f && t->g_first[g] < f + t->count[c]) self = 1;
+    } else {
+      for (int o = 7; o >= 0; o--)
+        if (t->child[c * 8 + o] >= 0) stack[sp++] = t->child[c * 8 + o];
+    }
+  }
+  *n_epj = ne;
+  *n_spj = ns;
+  *self_in = self;
+}
+
+static void make_lists(afo_tree *t) {
+  const int64_t ng = t->n_groups;
+  int64_t *ce = xcalloc(ng, sizeof(int64_t)), *cs = xcalloc(ng, sizeof(int64_t));
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t g = 0; g < ng; g++)
+    walk_group(t, g, NULL, NULL, &ce[g], &cs[g], &t->g_self[g]);
+  t->epj_off = xcalloc(ng + 1, sizeof(int64_t));
+  t->spj_off = xcalloc(ng + 1, sizeof(int64_t));
+  for (int64_t g = 0; g < ng; g++) {
+    t->epj_off[g + 1] = t->epj_off[g] + ce[g];
+    t->spj_off[g + 1] = t->spj_off[g] + cs[g];
+  }
+  t->epj = xcalloc(t->epj_off[ng], sizeof(int32_t));
+  t->spj = xcalloc(t->spj_off[ng], sizeof(int32_t));
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t g = 0; g < ng; g++) {
+    int64_t a, b;
+    int32_t s;
+    walk_group(t, g, t->epj + t->epj_off[g], t->spj + t->spj_off[g], &a, &b, &s);
+  }
+  free(ce);
+  free(cs);
+}
+
+/* Construction step (Section 4.3, Section 4.2 "tree construction step"):
+ * root, keys, sort, reorder, link, moments, groups and interaction lists.
+ * Returns NULL on bad input (non-finite coordinates or masses). */
+afo_tree *afo_build(int64_t n, const double *x, const double *y, const double *z,
+                    const double *m, int n_leaf, int n_grp, double theta, double eps,
+                    int quad) {
+  for (int64_t i = 0; i < n; i++)
+    if (!isfinite(m[i])) return NULL;
+  afo_tree *t = calloc(1, sizeof(afo_tree));
+  t->n = n;
+  t->n_leaf = n_leaf;
+  t->n_grp = n_grp;
+  t->theta = theta;
+  t->eps = eps;
+  t->quad = quad;
+  if (afo_root_cell(n, x, y, z, t->root) != 0) {
+    free(t);
+    return NULL;
+  }
+  uint64_t *raw = xcalloc(n, sizeof(uint64_t));
+  afo_morton_keys(n, x, y, z, t->root, raw);
+  t->keys = xcalloc(n, sizeof(uint64_t));
+  t->perm = xcalloc(n, sizeof(int64_t));
+  afo_radix_sort(n, raw, t->keys, t->perm);
+  free(raw);
+  t->xs = xcalloc(n, sizeof(double));
+  t->ys = xcalloc(n, sizeof(double));
+  t->zs = xcalloc(n, sizeof(double));
+  t->ms = xcalloc(n, sizeof(double));
+  reorder(t, x, y, z, m);
+  link_cells(t);
+  t->mass = xcalloc(t->n_cells, sizeof(double));
+  t->smom = xcalloc(t->n_cells * 3, sizeof(double));
+  t->com = xcalloc(t->n_cells * 3, sizeof(double));
+  t->qmom = xcalloc(t->n_cells * 6, sizeof(double));
+  moments(t);
+  make_groups(t);
+  group_boxes(t);
+  make_lists(t);
+  return t;
+}
+
+/* Reusing step (Section 4.2): topology and lists are kept; the particle
+ * data are reordered with the saved permutation and the moments and group
+ * boxes are recomputed from the new positions. */
+int afo_update(afo_tree *t, const double *x, const double *y, const double *z,
+               const double *m) {
+  for (int64_t i = 0; i < t->n; i++)
+    if (!isfinite(x[i]) || !isfinite(y[i]) || !isfinite(z[i]) || !isfinite(m[i])) return -1;
+  reorder(t, x, y, z, m);
+  moments(t);
+  group_boxes(t);
+  return 0;
+}
+
+/* Force on the saved lists (Section 5: interaction of the EPJs and SPJs of a
+ * group's list with its EPIs), FP64, results in caller order. */
+void afo_force(const afo_tree *t, double *ax, double *ay, double *az, double *pot) {
+  const double eps2 = t->eps * t->eps;
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t g = 0; g < t->n_groups; g++) {
+    for (int64_t i = t->g_first[g]; i < t->g_first[g] + t->g_count[g]; i++) {
+      const double xi = t->xs[i], yi = t->ys[i], zi = t->zs[i];
+      double sx = 0.0, sy = 0.0, sz = 0.0, sp = 0.0;
+      for (int64_t e = t->epj_off[g]; e < t->epj_off[g + 1]; e++) {
+        const int64_t j = t->epj[e];
+        if (j == i) continue;
+        const double dx = t->xs[j] - xi, dy = t->ys[j] - yi, dz = t->zs[j] - zi;
+        const double r2 = dx * dx + dy * dy + dz * dz + eps2;
+        if (r2 == 0.0) continue;
+        const double rinv = 1.0 / sqrt(r2);
+        const double mr = t->ms[j] * rinv;
+        const double mr3 = mr * rinv * rinv;
+        sx += mr3 * dx;
+        sy += mr3 * dy;
+        sz += mr3 * dz;
+        sp -= mr;
+      }
+      for (int64_t e = t->spj_off[g]; e < t->spj_off[g + 1]; e++) {
+        const int64_t c = t->spj[e];
+        const double *cm = &t->com[c * 3];
+        const double dx = cm[0] - xi, dy = cm[1] - yi, dz = cm[2] - zi;
+        const double r2 = dx * dx + dy * dy + dz * dz + eps2;
+        if (r2 == 0.0) continue;
+        const double rinv = 1.0 / sqrt(r2);
+        const double mr = t->mass[c] * rinv;
+        const double mr3 = mr * rinv * rinv;
+        sx += mr3 * dx;
+        sy += mr3 * dy;
+        sz += mr3 * dz;
+        sp -= mr;
+        if (t->quad) {
+          /* R10 with r = x_i - COM = -(dx, dy, dz). */
+          const double *Q = &t->qmom[c * 6];
+          const double r[3] = {-dx, -dy, -dz};
+          const double Qr[3] = {Q[0] * r[0] + Q[3] * r[1] + Q[4] * r[2],
+                                Q[3] * r[0] + Q[1] * r[1] + Q[5] * r[2],
+                                Q[4] * r[0] + Q[5] * r[1] + Q[2] * r[2]};
+          const double rQr = r[0] * Qr[0] + r[1] * Qr[1] + r[2] * Qr[2];
+          const double rinv2 = rinv * rinv;
+          const double rinv5 = rinv2 * rinv2 * rinv;
+          const double rinv7 = rinv5 * rinv2;
+          sx += Qr[0] * rinv5 - 2.5 * rQr * r[0] * rinv7;
+          sy += Qr[1] * rinv5 - 2.5 * rQr * r[1] * rinv7;
+          sz += Qr[2] * rinv5 - 2.5 * rQr * r[2] * rinv7;
+          sp -= 0.5 * rQr * rinv5;
+        }
+      }
+      const int64_t o = t->perm[i];
+      ax[o] = sx;
+      ay[o] = sy;
+      az[o] = sz;
+      pot[o] = sp;
+    }
+  }
+}
+
+/* Kick-drift-kick leapfrog with list reuse (reading R11). acc holds the
+ * accelerations at the start (caller order, ax/ay/az) and is updated. The
+ * tree *t is rebuilt on construction steps; *t may be replaced. */
+int afo_leapfrog(afo_tree **tp, int64_t n, double *x, double *y, double *z, double *vx,
+                 double *vy, double *vz, const double *m, double *ax, double *ay, double *az,
+                 double *pot, double dt, int n_steps, int n_reuse, int64_t *eval_counter) {
+  for (int s = 0; s < n_steps; s++) {
+    for (int64_t i = 0; i < n; i++) {
+      vx[i] += ax[i] * (0.5 * dt);
+      vy[i] += ay[i] * (0.5 * dt);
+      vz[i] += az[i] * (0.5 * dt);
+      x[i] += vx[i] * dt;
+      y[i] += vy[i] * dt;
+      z[i] += vz[i] * dt;
+    }
+    afo_tree *t = *tp;
+    if (*eval_counter % n_reuse == 0) {
+      afo_tree *nt = afo_build(n, x, y, z, m, t->n_leaf, t->n_grp, t->theta, t->eps, t->quad);
+      if (!nt) return -1;
+      afo_free(t);
+      *tp = t = nt;
+    } else if (afo_update(t, x, y, z, m) != 0) {
+      return -1;
+    }
+    (*eval_counter)++;
+    afo_force(t, ax, ay, az, pot);
+    for (int64_t i = 0; i < n; i++) {
+      vx[i] += ax[i] * (0.5 * dt);
+      vy[i] += ay[i] * (0.5 * dt);
+      vz[i] += az[i] * (0.5 * dt);
+    }
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Accessors for the ctypes wrapper.                                        */
+/* ------------------------------------------------------------------------ */
+
+void afo_sizes(const afo_tree *t, int64_t out[5]) {
+  out[0] = t->n;
+  out[1] = t->n_cells;
+  out[2] = t->n_groups;
+  out[3] = t->n_groups > 0 ? t->epj_off[t->n_groups] : 0;
+  out[4] = t->n_groups > 0 ? t->spj_off[t->n_groups] : 0;
+}
+
+void afo_get_root(const afo_tree *t, double root[4]) { memcpy(root, t->root, sizeof(t->root)); }
+
+void afo_get_order(const afo_tree *t, uint64_t *keys, int64_t *perm) {
+  memcpy(keys, t->keys, sizeof(uint64_t) * (size_t)t->n);
+  memcpy(perm, t->perm, sizeof(int64_t) * (size_t)t->n);
+}
+
+void afo_get_cells(const afo_tree *t, int32_t *level, int64_t *first, int64_t *count,
+                   int64_t *parent, int64_t *skip, int32_t *n_child, int64_t *child) {
+  const size_t nc = (size_t)t->n_cells;
+  memcpy(level, t->level, sizeof(int32_t) * nc);
+  memcpy(first, t->first, sizeof(int64_t) * nc);
+  memcpy(count, t->count, sizeof(int64_t) * nc);
+  memcpy(parent, t->parent, sizeof(int64_t) * nc);
+  memcpy(skip, t->skip, sizeof(int64_t) * nc);
+  memcpy(n_child, t->n_child, sizeof(int32_t) * nc);
+  memcpy(child, t->child, sizeof(int64_t) * nc * 8);
+}
+
+void afo_get_moments(const afo_tree *t, double *mass, double *com, double *quad) {
+  const size_t nc = (size_t)t->n_cells;
+  memcpy(mass, t->mass, sizeof(double) * nc);
+  memcpy(com, t->com, sizeof(double) * nc * 3);
+  memcpy(quad, t->qmom, sizeof(double) * nc * 6);
+}
+
+void afo_get_groups(const afo_tree *t, int64_t *first, int64_t *count, int64_t *cell,
+                    double *box, int32_t *self_in) {
+  const size_t ng = (size_t)t->n_groups;
+  memcpy(first, t->g_first, sizeof(int64_t) * ng);
+  memcpy(count, t->g_count, sizeof(int64_t) * ng);
+  memcpy(cell, t->g_cell, sizeof(int64_t) * ng);
+  memcpy(box, t->g_box, sizeof(double) * ng * 6);
+  memcpy(self_in, t->g_self, sizeof(int32_t) * ng);
+}
+
+void afo_get_lists(const afo_tree *t, int64_t *epj_off, int32_t *epj, int64_t *spj_off,
+                   int32_t *spj) {
+  const size_t ng = (size_t)t->n_groups;
+  memcpy(epj_off, t->epj_off, sizeof(int64_t) * (ng + 1));
+  memcpy(spj_off, t->spj_off, sizeof(int64_t) * (ng + 1));
+  if (ng > 0) {
+    memcpy(epj, t->epj, sizeof(int32_t) * (size_t)t->epj_off[ng]);
+    memcpy(spj, t->spj, sizeof(int32_t) * (size_t)t->spj_off[ng]);
+  }
+}
+
+int afo_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
