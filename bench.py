@@ -1,0 +1,397 @@
+#!/usr/bin/env python3
+"""Benchmark of the tree-gravity hot path on one GB300 (or N replicas).
+
+Workload (default ``plummer_1m``): Plummer sphere, N = 2^20 equal masses,
+eps = 1/1024, theta = 0.5, n_leaf = 16, n_grp = 256, monopole superparticles,
+FP32 force kernel on FP64 particle data, indirect index lists reused over 4
+kick-drift-kick steps (dt = 1/256). One bench step = one KDK timestep: kick +
+drift, then force evaluation k (a construction step -- tree build + lists --
+when k % 4 == 0, a reusing step otherwise), then kick.
+
+Metric: force interactions per second (interactions = sum over i-groups of
+n_i * (n_epj + n_spj)) over the timed steps, plus ms per step.
+
+  value     device time (CUDA events on the library's stream), inputs
+            resident in HBM, L2 flushed (256 MB write) between timed steps.
+  e2e       the same steps through the host-array entry point
+            (afd_calc_force_all_host): pinned host x, y, z, m copied in and
+            the n x 4 float result copied out every step.
+  roofline  the force kernel, ALU-bound: 23 flops per interaction (the
+            paper's n_op) / its event-timed duration, against the FP32 peak
+            152 SMs x 128 lanes x 2 flops x the median SM clock sampled
+            during the timed region.
+  cpu_baseline  the FP64 CPU oracle on the host cores, bounded sample.
+
+``--impl reference`` times the oracle itself on the same workload (each step
+a bounded sample, extrapolated to the full step) and prints its own line.
+Multi-GPU (torchrun): every rank runs an independent replica of the
+workload (the path has no exchange step at one tree per GPU); value is the
+sum of all ranks' interactions over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FLOPS_PER_INTERACTION = 23  # n_op, Section 6.2 / Appendix A
+SMS, FP32_LANES = 152, 128
+L2_FLUSH_BYTES = 256 << 20
+# dram__bytes_read.sum + dram__bytes_write.sum of one force-kernel launch on
+# this workload, from the capture summarised in profiles/ (None until taken
+# on the current kernel).
+FORCE_TRAFFIC_BYTES = None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=16)
+    ap.add_argument("--warmup", type=int, default=4)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", default="plummer_1m")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name):
+    import ics
+
+    wl = dict(ics.WORKLOADS[name])
+    wl.setdefault("n_reuse", 4)
+    wl.setdefault("dt", 1.0 / 256)
+    wl["name"] = name
+    return wl
+
+
+def describe(wl):
+    return (f"{wl['name']}: {wl['model']} N={wl['n']} eps={wl['eps']:.6g} theta={wl['theta']} "
+            f"n_leaf=16 n_grp={wl['n_grp']} {'quadrupole' if wl['quad'] else 'monopole'} "
+            f"lists reused over {wl['n_reuse']} KDK steps dt={wl['dt']:.6g}")
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        mhz, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+def cpu_baseline(wl, max_groups_frac=0.25):
+    """The FP64 oracle on the host cores: one construction step, one reusing
+    step, and the force of a fraction of the groups; extrapolated to the
+    interactions/s of the full reuse window."""
+    import numpy as np
+
+    import ics
+    import oracle
+
+    p = ics.make(wl["model"], wl["n"], wl["seed"])
+    kw = dict(n_grp=wl["n_grp"], theta=wl["theta"], eps=wl["eps"], quad=wl["quad"])
+    t0 = time.perf_counter()
+    t = oracle.Tree(p.x, p.y, p.z, p.m, **kw)
+    t_build = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    t.update(p.x, p.y, p.z, p.m)
+    t_update = time.perf_counter() - t0
+    g = t.groups()
+    eo, _, so, _ = t.lists()
+    per_group = g["count"] * ((eo[1:] - eo[:-1]) + (so[1:] - so[:-1]))
+    stride = max(1, int(round(1.0 / max_groups_frac)))
+    sel = np.arange(0, len(per_group), stride)
+    t0 = time.perf_counter()
+    t.force_groups(sel)
+    t_force = time.perf_counter() - t0
+    i_total = float(per_group.sum())
+    i_sel = float(per_group[sel].sum())
+    r = wl["n_reuse"]
+    window = t_build + (r - 1) * t_update + r * t_force * (i_total / i_sel)
+    value = r * i_total / window
+    sample = (f"{wl['name']}: one construction step ({t_build:.2f} s) and one reusing step "
+              f"({t_update:.2f} s) on all N, force on every {stride}th group ({t_force:.2f} s, "
+              f"{i_sel:.3g} of {i_total:.3g} interactions), extrapolated to a {r}-step window")
+    return {"value": value, "unit": "interactions/s", "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": sample,
+            "ms_per_step": 1e3 * window / r}
+
+
+def run_reference(args, wl):
+    """--impl reference: the oracle as it stands, K timed bounded steps."""
+    import numpy as np
+
+    import ics
+    import oracle
+
+    p = ics.make(wl["model"], wl["n"], wl["seed"])
+    kw = dict(n_grp=wl["n_grp"], theta=wl["theta"], eps=wl["eps"], quad=wl["quad"])
+    stride = 16
+    t = None
+    tot_i, tot_s = 0.0, 0.0
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        if t is None or k % wl["n_reuse"] == 0:
+            t = oracle.Tree(p.x, p.y, p.z, p.m, **kw)
+        else:
+            t.update(p.x, p.y, p.z, p.m)
+        t_tree = time.perf_counter() - t0
+        g = t.groups()
+        eo, _, so, _ = t.lists()
+        per_group = g["count"] * ((eo[1:] - eo[:-1]) + (so[1:] - so[:-1]))
+        sel = np.arange(k % stride, len(per_group), stride)
+        t0 = time.perf_counter()
+        t.force_groups(sel)
+        t_force = time.perf_counter() - t0
+        i_total, i_sel = float(per_group.sum()), float(per_group[sel].sum())
+        step_s = t_tree + t_force * i_total / max(i_sel, 1.0)
+        if k >= args.warmup:
+            tot_i += i_total
+            tot_s += step_s
+    value = tot_i / tot_s
+    ms = 1e3 * tot_s / args.steps
+    sample = (f"each step: full tree build or reuse update on all N, force on every {stride}th "
+              f"group, extrapolated to all groups")
+    line = {
+        "impl": "reference", "metric": "force interactions/s", "value": value,
+        "unit": "interactions/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": describe(wl)},
+        "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    wl = workload(args.workload)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, wl)
+        return
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import ics
+    import paper_1907_02290_gb300 as afd
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    p = ics.make(wl["model"], wl["n"], wl["seed"])
+    n = p.n
+    T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    x, y, z, vx, vy, vz, m = (T(a) for a in (p.x, p.y, p.z, p.vx, p.vy, p.vz, p.m))
+    acc = torch.zeros(n, 4, dtype=torch.float32, device=dev)
+    cfg = afd.Config(eps=wl["eps"], theta=wl["theta"], n_leaf=16, n_grp=wl["n_grp"],
+                     multipole=int(wl["quad"]))
+    g = afd.Gravity(cfg, local, stream)
+    ctx = g.ctx
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    dt, R = wl["dt"], wl["n_reuse"]
+
+    afd.afd_calc_force_all(ctx, x, y, z, m, acc, afd.AFD_MAKE_LIST_FOR_REUSE)  # evaluation 0
+    state = {"k": 1}
+
+    def step():
+        k = state["k"]
+        afd.afd_kick_drift(ctx, x, y, z, vx, vy, vz, acc, 0.5 * dt, dt)
+        mode = afd.AFD_MAKE_LIST_FOR_REUSE if k % R == 0 else afd.AFD_REUSE_LIST
+        afd.afd_calc_force_all(ctx, x, y, z, m, acc, mode)
+        afd.afd_kick(ctx, vx, vy, vz, acc, 0.5 * dt)
+        state["k"] = k + 1
+        return mode
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    launches0 = g.stats()["launches"]
+    step_ms, force_ms, inter, modes = [], [], [], []
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mode = step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        force_ms.append(afd.afd_last_force_ms(ctx))
+        inter.append(g.stats()["interactions"])
+        modes.append(mode)
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter() - t_wall
+    launches = g.stats()["launches"] - launches0
+    clocks = sampler.stop()
+    total_ms = float(sum(step_ms))
+    total_i = float(sum(inter))
+    if dist:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ti = torch.tensor([total_i], device=dev, dtype=torch.float64)
+        dist.all_reduce(ti, op=dist.ReduceOp.SUM)
+        total_ms, total_i_all = float(tt.item()), float(ti.item())
+    else:
+        total_i_all = total_i
+    value = total_i_all / (total_ms * 1e-3)
+
+    # ---- roofline of the force kernel ----
+    f_ms = float(np.mean(force_ms))
+    i_launch = float(np.mean(inter))
+    achieved = FLOPS_PER_INTERACTION * i_launch / (f_ms * 1e-3) / 1e12
+    mhz = clocks.get("sm_mhz") or 2070.0
+    peak = SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": FORCE_TRAFFIC_BYTES,
+                "kernel": "k_force", "flops_per_interaction": FLOPS_PER_INTERACTION,
+                "interactions_per_launch": i_launch, "launch_ms": f_ms,
+                "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 x {mhz:.0f} MHz "
+                              "(median SM clock sampled during the timed region)"}
+    cons = [s for s, md in zip(step_ms, modes) if md == afd.AFD_MAKE_LIST_FOR_REUSE]
+    reus = [s for s, md in zip(step_ms, modes) if md == afd.AFD_REUSE_LIST]
+
+    # ---- end to end through the host-array entry point ----
+    e2e = None
+    if not args.no_e2e:
+        hx, hy, hz, hm = (torch.tensor(a, dtype=torch.float64).pin_memory()
+                          for a in (p.x, p.y, p.z, p.m))
+        hacc = torch.zeros(n, 4, dtype=torch.float32).pin_memory()
+        g2 = afd.Gravity(cfg, local, stream)
+        afd.afd_calc_force_all_host(g2.ctx, hx, hy, hz, hm, hacc, afd.AFD_MAKE_LIST_FOR_REUSE)
+        for k in range(1, args.warmup + 1):
+            afd.afd_calc_force_all_host(g2.ctx, hx, hy, hz, hm, hacc,
+                                        afd.AFD_MAKE_LIST_FOR_REUSE if k % R == 0
+                                        else afd.AFD_REUSE_LIST)
+        if dist:
+            dist.barrier()
+        e_i, t0 = 0.0, time.perf_counter()
+        for k in range(args.warmup + 1, args.warmup + 1 + args.steps):
+            afd.afd_calc_force_all_host(g2.ctx, hx, hy, hz, hm, hacc,
+                                        afd.AFD_MAKE_LIST_FOR_REUSE if k % R == 0
+                                        else afd.AFD_REUSE_LIST)
+            e_i += g2.stats()["interactions"]
+        e_s = time.perf_counter() - t0
+        if dist:
+            tt = torch.tensor([e_s], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e_s = float(tt.item())
+            ti = torch.tensor([e_i], device=dev, dtype=torch.float64)
+            dist.all_reduce(ti, op=dist.ReduceOp.SUM)
+            e_i = float(ti.item())
+        e2e = {"value": e_i / e_s, "unit": "interactions/s", "h2d_bytes_per_step": 4 * 8 * n,
+               "d2h_bytes_per_step": 16 * n, "ms_per_step": 1e3 * e_s / args.steps,
+               "call": "afd_calc_force_all_host (force evaluation per step; integration not "
+                       "included)"}
+        g2.close()
+
+    if rank != 0:
+        g.close()
+        if dist:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": "force interactions/s", "value": value, "unit": "interactions/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32",
+        "dtype_detail": "force kernel FP32 (hi/lo group-relative coordinates); tree, "
+                        "moments and integration FP64",
+        "data": "synthetic (seeded Plummer sphere)",
+        "config": {"workload": describe(wl), "n": n, "l2": "flushed (256 MB write) between "
+                   "timed steps, outside the timed events", "parallelism":
+                   "replicas" if world > 1 else "single GPU"},
+        "ms_per_construction_step": float(np.mean(cons)) if cons else None,
+        "ms_per_reuse_step": float(np.mean(reus)) if reus else None,
+        "interactions_per_step": total_i / args.steps,
+        "roofline": roofline,
+        "clocks": clocks,
+        "gpu_launches": launches,
+        "wall_s_timed_region": t_wall,
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    print(json.dumps(line))
+    g.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,223 @@
+/*
+ * afdps.h -- C ABI of the GB300 (sm_103a) multiwalk, indirect-index
+ * Barnes-Hut gravity library (method of "Accelerated FDPS", Iwasawa et al.,
+ * arXiv 1907.02290).
+ *
+ * The library computes softened gravitational accelerations and potentials
+ * with the tree method: Morton-key octree (Section 4.3), i-groups of at most
+ * n_grp particles sharing one interaction list (Barnes' vectorisation,
+ * Section 2), many groups per kernel launch (multiwalk, Section 3), lists of
+ * particle and superparticle INDICES into device-resident arrays (indirect
+ * addressing, Section 4.1), and lists kept and reused across steps while the
+ * moments are recomputed (list reuse, Section 4.2). The three list modes
+ * mirror the paper's MAKE_LIST / MAKE_LIST_FOR_REUSE / REUSE_LIST (Section 5).
+ *
+ * Conventions shared by every entry point:
+ *  - Particle arrays are device pointers to FP64 structure-of-arrays data in
+ *    the caller's particle order (x, y, z, m: one double per particle). The
+ *    caller owns them; they must stay valid until the work queued by the call
+ *    has run on the context's stream. Nothing is copied to the host unless the
+ *    entry point says so.
+ *  - Outputs (acc4) are device pointers, caller particle order: four floats
+ *    per particle (ax, ay, az, phi), 16-byte aligned. G = 1.
+ *  - Work is queued on the CUDA stream given at creation (or set later); the
+ *    calls that build a tree or lists synchronise that stream once to size
+ *    their buffers, the reuse step and the force calculation do not.
+ *  - The context owns the tree, groups, lists and scratch memory (device
+ *    allocations made with cudaMalloc, grown on demand, freed by
+ *    afd_destroy).
+ *  - Every int-returning call returns AFD_OK (0) or a negative afd_status;
+ *    nothing throws across the ABI. Errors found by device code in calls that
+ *    do not synchronise (non-finite input in a reuse step, a walk that ran
+ *    out of stack) are kept in a device status word and returned by the next
+ *    synchronising call or by afd_sync().
+ *  - One context is not thread-safe; different contexts are independent.
+ */
+#ifndef AFDPS_H
+#define AFDPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct afd_ctx afd_ctx;
+
+/* List modes of the top-level call (Section 5: the FDPS enum). */
+typedef enum {
+  AFD_MAKE_LIST = 0,           /* build tree + lists, do not keep them for reuse */
+  AFD_MAKE_LIST_FOR_REUSE = 1, /* build tree + lists and keep them */
+  AFD_REUSE_LIST = 2           /* keep topology and lists; recompute moments */
+} afd_list_mode;
+
+typedef enum {
+  AFD_OK = 0,
+  AFD_ERR_ARG = -1,           /* bad argument (null pointer, bad config, n < 0) */
+  AFD_ERR_CUDA = -2,          /* a CUDA runtime call failed */
+  AFD_ERR_NONFINITE = -3,     /* a coordinate or mass is NaN or infinite */
+  AFD_ERR_NO_SAVED_LIST = -4, /* REUSE_LIST without lists made for reuse */
+  AFD_ERR_SHAPE = -5,         /* particle count differs from the saved tree */
+  AFD_ERR_LIST_OVERFLOW = -6, /* a list or cell count exceeds 32-bit indexing */
+  AFD_ERR_TIMEOUT = -7,       /* a bounded device wait gave up */
+  AFD_ERR_NO_TREE = -8,       /* lists or force requested before a tree */
+  AFD_ERR_OOM = -9,           /* device allocation failed */
+  AFD_ERR_WALK_STACK = -10    /* a tree walk overflowed its per-warp stack */
+} afd_status;
+
+/* Method parameters. Paper values: n_leaf = 16, theta in [0.25, 1]
+ * (Section 6.1); eps and the multipole order are not given by the paper. */
+typedef struct {
+  double eps;            /* Plummer softening length, >= 0 */
+  double theta;          /* opening angle, >= 0 (0 opens every cell) */
+  int32_t n_leaf;        /* a cell splits while it holds more particles, >= 1 */
+  int32_t n_grp;         /* maximum particles per i-group, 1 .. 1024 */
+  int32_t multipole;     /* 0: monopole superparticles, 1: + quadrupole */
+  int32_t far_precision; /* 0: FP32 superparticle terms, 1: BF16, 2: FP16 */
+  int32_t mac;           /* 0: theta criterion (only value accepted) */
+  int32_t reserved;      /* must be 0 */
+} afd_config;
+
+/* Create a context on CUDA device `device`, queuing work on `stream` (a
+ * cudaStream_t; NULL = the legacy default stream). *out receives the
+ * context. Returns AFD_ERR_ARG for a bad config. */
+int afd_create(afd_ctx **out, const afd_config *cfg, int device, void *stream);
+
+/* Free every device buffer of the context (synchronises its stream). */
+void afd_destroy(afd_ctx *ctx);
+
+/* Replace the stream later work is queued on. */
+int afd_set_stream(afd_ctx *ctx, void *stream);
+
+/* Tree construction (Section 4.3): root cell from all positions, 63-bit
+ * Morton keys (21 bits per axis), stable LSD radix sort of (key, index),
+ * reorder of the particle data into Morton order, level-wise octree link,
+ * bottom-up monopole (and quadrupole) moments, and i-groups. x, y, z, m are
+ * n device doubles each (caller order). n = 0 is allowed (empty tree).
+ * Synchronises once. Invalidates saved lists. AFD_ERR_NONFINITE if a
+ * coordinate or mass is not finite. */
+int afd_tree_build(afd_ctx *ctx, const double *x, const double *y, const double *z,
+                   const double *m, int64_t n);
+
+/* Interaction lists for every i-group (Sections 2, 3, 4.1): a depth-first
+ * walk under the opening-angle criterion producing, per group, a list of
+ * particle indices (EPJ) and a list of cell indices (SPJ) into the device
+ * arrays. mode is AFD_MAKE_LIST or AFD_MAKE_LIST_FOR_REUSE; the latter keeps
+ * the lists for later AFD_REUSE_LIST steps. Needs a tree. Synchronises once. */
+int afd_make_interaction_lists(afd_ctx *ctx, int mode);
+
+/* Reusing step (Section 4.2): keep the topology, groups and lists; reorder
+ * the new particle data with the saved permutation and recompute the cell
+ * moments bottom-up. x, y, z, m: device doubles, same n as the saved tree.
+ * Does not synchronise. AFD_ERR_NO_SAVED_LIST without lists kept for reuse. */
+int afd_reuse_lists(afd_ctx *ctx, const double *x, const double *y, const double *z,
+                    const double *m);
+
+/* Force kernel (Section 5, the indirect-index dispatch): for every group and
+ * every EPJ / SPJ index of its list, sum the softened attraction on each of
+ * the group's particles. acc4: device, n x (ax, ay, az, phi) floats, caller
+ * order, overwritten. Does not synchronise. */
+int afd_calc_force(afd_ctx *ctx, float *acc4);
+
+/* The top-level call of Section 5 (calcForceAllAndWriteBackMultiWalkIndex):
+ * MAKE_LIST / MAKE_LIST_FOR_REUSE build the tree and lists, REUSE_LIST runs
+ * the reusing step; then the force kernel writes acc4. */
+int afd_calc_force_all(afd_ctx *ctx, const double *x, const double *y, const double *z,
+                       const double *m, int64_t n, float *acc4, int mode);
+
+/* The same top-level call on HOST arrays (caller order): copies x, y, z, m
+ * to the device, runs afd_calc_force_all, copies the n x 4 floats back to
+ * acc4_host and synchronises. Pinned host memory gives the fastest copies. */
+int afd_calc_force_all_host(afd_ctx *ctx, const double *x, const double *y, const double *z,
+                            const double *m, int64_t n, float *acc4_host, int mode);
+
+/* Kick-drift (first half of a KDK leapfrog step, caller order, device
+ * arrays): v += a * dt_kick, then x += v * dt_drift. acc4 as written by
+ * afd_calc_force. */
+int afd_kick_drift(afd_ctx *ctx, double *x, double *y, double *z, double *vx, double *vy,
+                   double *vz, const float *acc4, int64_t n, double dt_kick, double dt_drift);
+
+/* Kick: v += a * dt_kick. */
+int afd_kick(afd_ctx *ctx, double *vx, double *vy, double *vz, const float *acc4, int64_t n,
+             double dt_kick);
+
+/* n_steps kick-drift-kick steps of size dt on device arrays. acc4 holds the
+ * accelerations at the start and receives those at the end. Force
+ * evaluation k of the context (counted since the last AFD_MAKE_LIST_FOR_REUSE
+ * issued by this call) rebuilds the tree and lists when k % n_reuse == 0 and
+ * reuses them otherwise; the first evaluation of a call always rebuilds. */
+int afd_leapfrog(afd_ctx *ctx, double *x, double *y, double *z, double *vx, double *vy,
+                 double *vz, const double *m, int64_t n, float *acc4, double dt, int n_steps,
+                 int n_reuse);
+
+/* FP64 energies: out[0] = sum m v^2 / 2, out[1] = sum m phi / 2 (phi from
+ * acc4). Host array of two doubles; synchronises. */
+int afd_energy(afd_ctx *ctx, const double *vx, const double *vy, const double *vz,
+               const double *m, const float *acc4, int64_t n, double *out);
+
+/* Wait for the context's stream and return the device status word. */
+int afd_sync(afd_ctx *ctx);
+
+/* Sizes of the current tree and lists: out[0] n, [1] cells, [2] groups,
+ * [3] EPJ entries, [4] SPJ entries, [5] interactions of one force
+ * evaluation (sum over groups of n_i * (n_epj + n_spj)), [6] lists saved
+ * for reuse (0/1), [7] deepest level, [8] kernels launched by this context
+ * so far, [9] force-kernel work units (32-particle group chunks). Host
+ * array of 10 int64. */
+int afd_stats(afd_ctx *ctx, int64_t *out);
+
+/* Copy an internal array to host memory for inspection and parity tests.
+ * With host_buf NULL only *bytes is set to the size needed. Synchronises.
+ * Items and element types:
+ *   ROOT        4 x f64 (centre x, y, z, side L)
+ *   KEYS        n x u64 sorted Morton keys
+ *   PERM        n x u32 caller index of each Morton position
+ *   CELL_LEVEL  cells x u32      CELL_FIRST  cells x u32
+ *   CELL_COUNT  cells x u32      CELL_SKIP   cells x u32 (pre-order end of subtree)
+ *   CELL_PARENT cells x u32 (0xffffffff for the root)
+ *   CELL_CHILD  cells x 8 x u32 (by octant, 0xffffffff when empty)
+ *   CELL_MASS   cells x f64      CELL_COM    cells x 3 x f64
+ *   CELL_QUAD   cells x 6 x f64 (xx yy zz xy xz yz; zeros when monopole)
+ *   GROUP_FIRST groups x u32     GROUP_COUNT groups x u32
+ *   GROUP_BOX   groups x 6 x f64 (min x y z, max x y z)
+ *   GROUP_SELF  groups x u32 (1 when the group's own particles are EPJs)
+ *   EPJ_OFF / SPJ_OFF (groups + 1) x u64, EPJ_IDX / SPJ_IDX entries x u32
+ * Cells are numbered in depth-first pre-order, children in Morton order. */
+typedef enum {
+  AFD_EXPORT_ROOT = 0,
+  AFD_EXPORT_KEYS = 1,
+  AFD_EXPORT_PERM = 2,
+  AFD_EXPORT_CELL_LEVEL = 3,
+  AFD_EXPORT_CELL_FIRST = 4,
+  AFD_EXPORT_CELL_COUNT = 5,
+  AFD_EXPORT_CELL_SKIP = 6,
+  AFD_EXPORT_CELL_PARENT = 7,
+  AFD_EXPORT_CELL_CHILD = 8,
+  AFD_EXPORT_CELL_MASS = 9,
+  AFD_EXPORT_CELL_COM = 10,
+  AFD_EXPORT_CELL_QUAD = 11,
+  AFD_EXPORT_GROUP_FIRST = 12,
+  AFD_EXPORT_GROUP_COUNT = 13,
+  AFD_EXPORT_GROUP_BOX = 14,
+  AFD_EXPORT_GROUP_SELF = 15,
+  AFD_EXPORT_EPJ_OFF = 16,
+  AFD_EXPORT_EPJ_IDX = 17,
+  AFD_EXPORT_SPJ_OFF = 18,
+  AFD_EXPORT_SPJ_IDX = 19
+} afd_export_item;
+
+int afd_export(afd_ctx *ctx, int what, void *host_buf, size_t *bytes);
+
+/* Milliseconds of the most recent force kernel launch as measured by CUDA
+ * events recorded around it on the context's stream (synchronises). */
+int afd_last_force_ms(afd_ctx *ctx, float *ms);
+
+/* Human-readable text for a status code (static storage). */
+const char *afd_error_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AFDPS_H */

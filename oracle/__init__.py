@@ -62,6 +62,7 @@ def lib():
         L.afo_update.argtypes = [ctypes.c_void_p, _D, _D, _D, _D]
         L.afo_update.restype = ctypes.c_int
         L.afo_force.argtypes = [ctypes.c_void_p, _D, _D, _D, _D]
+        L.afo_force_groups.argtypes = [ctypes.c_void_p, ctypes.c_int64, _I64, _D, _D, _D, _D]
         L.afo_free.argtypes = [ctypes.c_void_p]
         L.afo_sizes.argtypes = [ctypes.c_void_p, _I64]
         L.afo_get_root.argtypes = [ctypes.c_void_p, _D]
@@ -231,6 +232,14 @@ class Tree:
         """FP64 force on the saved lists, caller order: (ax, ay, az, pot)."""
         out = [np.zeros(self.n) for _ in range(4)]
         lib().afo_force(self._h, *(_p(o, _D) for o in out))
+        return tuple(out)
+
+    def force_groups(self, groups):
+        """FP64 force for the particles of the listed groups only (caller
+        order); other entries are NaN."""
+        sel = np.ascontiguousarray(groups, dtype=np.int64)
+        out = [np.full(self.n, np.nan) for _ in range(4)]
+        lib().afo_force_groups(self._h, sel.shape[0], _p(sel, _I64), *(_p(o, _D) for o in out))
         return tuple(out)
 
     def interactions(self):

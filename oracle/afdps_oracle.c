@@ -636,11 +636,16 @@ int afo_update(afo_tree *t, const double *x, const double *y, const double *z,
 }
 
 /* Force on the saved lists (Section 5: interaction of the EPJs and SPJs of a
- * group's list with its EPIs), FP64, results in caller order. */
-void afo_force(const afo_tree *t, double *ax, double *ay, double *az, double *pot) {
+ * group's list with its EPIs), FP64, results in caller order. Only the
+ * groups sel[0..n_sel) are evaluated (all groups when sel is NULL); the
+ * outputs of other particles are left untouched. */
+void afo_force_groups(const afo_tree *t, int64_t n_sel, const int64_t *sel, double *ax,
+                      double *ay, double *az, double *pot) {
   const double eps2 = t->eps * t->eps;
+  const int64_t ng = sel ? n_sel : t->n_groups;
 #pragma omp parallel for schedule(dynamic, 4)
-  for (int64_t g = 0; g < t->n_groups; g++) {
+  for (int64_t gs = 0; gs < ng; gs++) {
+    const int64_t g = sel ? sel[gs] : gs;
     for (int64_t i = t->g_first[g]; i < t->g_first[g] + t->g_count[g]; i++) {
       const double xi = t->xs[i], yi = t->ys[i], zi = t->zs[i];
       double sx = 0.0, sy = 0.0, sz = 0.0, sp = 0.0;
@@ -695,6 +700,10 @@ void afo_force(const afo_tree *t, double *ax, double *ay, double *az, double *po
       pot[o] = sp;
     }
   }
+}
+
+void afo_force(const afo_tree *t, double *ax, double *ay, double *az, double *pot) {
+  afo_force_groups(t, 0, NULL, ax, ay, az, pot);
 }
 
 /* Kick-drift-kick leapfrog with list reuse (reading R11). acc holds the

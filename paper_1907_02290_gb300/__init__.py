@@ -1,0 +1,300 @@
+"""GB300 (sm_103a) multiwalk, indirect-index Barnes-Hut gravity.
+
+Thin ctypes binding over ``libafdps.so`` (C ABI in ``include/afdps.h``). The
+functions keep the C names and only marshal arguments: torch tensors become
+device pointers, a torch CUDA stream becomes a ``cudaStream_t``. Every step of
+the computation runs in the library's CUDA kernels; there is no fallback. If
+the library has not been built, importing the binding raises.
+
+Build it with ``python -m paper_1907_02290_gb300.build`` (or
+``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+AFD_MAKE_LIST = 0
+AFD_MAKE_LIST_FOR_REUSE = 1
+AFD_REUSE_LIST = 2
+
+EXPORT = {
+    "root": (0, np.float64), "keys": (1, np.uint64), "perm": (2, np.uint32),
+    "cell_level": (3, np.uint32), "cell_first": (4, np.uint32), "cell_count": (5, np.uint32),
+    "cell_skip": (6, np.uint32), "cell_parent": (7, np.uint32), "cell_child": (8, np.uint32),
+    "cell_mass": (9, np.float64), "cell_com": (10, np.float64), "cell_quad": (11, np.float64),
+    "group_first": (12, np.uint32), "group_count": (13, np.uint32),
+    "group_box": (14, np.float64), "group_self": (15, np.uint32),
+    "epj_off": (16, np.uint64), "epj_idx": (17, np.uint32),
+    "spj_off": (18, np.uint64), "spj_idx": (19, np.uint32),
+}
+
+
+class AfdError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {afd_error_string(status)} (status {status})")
+
+
+class afd_config(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("theta", ctypes.c_double),
+                ("n_leaf", ctypes.c_int32), ("n_grp", ctypes.c_int32),
+                ("multipole", ctypes.c_int32), ("far_precision", ctypes.c_int32),
+                ("mac", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+_VP = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libafdps.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                           "(there is no CPU fallback)")
+    L = ctypes.CDLL(path)
+    sig = {
+        "afd_create": ([ctypes.POINTER(_VP), ctypes.POINTER(afd_config), ctypes.c_int, _VP], ctypes.c_int),
+        "afd_destroy": ([_VP], None),
+        "afd_set_stream": ([_VP, _VP], ctypes.c_int),
+        "afd_tree_build": ([_VP, _VP, _VP, _VP, _VP, _I64], ctypes.c_int),
+        "afd_make_interaction_lists": ([_VP, ctypes.c_int], ctypes.c_int),
+        "afd_reuse_lists": ([_VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+        "afd_calc_force": ([_VP, _VP], ctypes.c_int),
+        "afd_calc_force_all": ([_VP, _VP, _VP, _VP, _VP, _I64, _VP, ctypes.c_int], ctypes.c_int),
+        "afd_calc_force_all_host": ([_VP, _VP, _VP, _VP, _VP, _I64, _VP, ctypes.c_int], ctypes.c_int),
+        "afd_kick_drift": ([_VP] + [_VP] * 7 + [_I64, _D, _D], ctypes.c_int),
+        "afd_kick": ([_VP] + [_VP] * 4 + [_I64, _D], ctypes.c_int),
+        "afd_leapfrog": ([_VP] + [_VP] * 7 + [_I64, _VP, _D, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "afd_energy": ([_VP] + [_VP] * 5 + [_I64, _VP], ctypes.c_int),
+        "afd_sync": ([_VP], ctypes.c_int),
+        "afd_stats": ([_VP, _VP], ctypes.c_int),
+        "afd_export": ([_VP, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+        "afd_last_force_ms": ([_VP, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+        "afd_error_string": ([ctypes.c_int], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise AfdError(status, where)
+
+
+def _dptr(t, dtype=None, n=None, what="tensor"):
+    """Device pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{what} must be {dtype}, got {t.dtype}")
+    if n is not None and t.numel() < n:
+        raise ValueError(f"{what} holds {t.numel()} elements, needs {n}")
+    return _VP(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return _VP(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------- C names
+
+
+def afd_error_string(status: int) -> str:
+    return lib().afd_error_string(int(status)).decode()
+
+
+def afd_create(cfg: afd_config, device: int = 0, stream=None):
+    h = _VP()
+    _check(lib().afd_create(ctypes.byref(h), ctypes.byref(cfg), int(device), _stream_ptr(stream)),
+           "afd_create")
+    return h
+
+
+def afd_destroy(ctx):
+    lib().afd_destroy(ctx)
+
+
+def afd_set_stream(ctx, stream):
+    _check(lib().afd_set_stream(ctx, _stream_ptr(stream)), "afd_set_stream")
+
+
+def afd_tree_build(ctx, x, y, z, m):
+    import torch
+    n = x.numel()
+    p = [_dptr(a, torch.float64, n, nm) for a, nm in zip((x, y, z, m), "xyzm")]
+    _check(lib().afd_tree_build(ctx, *p, n), "afd_tree_build")
+
+
+def afd_make_interaction_lists(ctx, mode=AFD_MAKE_LIST_FOR_REUSE):
+    _check(lib().afd_make_interaction_lists(ctx, int(mode)), "afd_make_interaction_lists")
+
+
+def afd_reuse_lists(ctx, x, y, z, m):
+    import torch
+    n = x.numel()
+    p = [_dptr(a, torch.float64, n, nm) for a, nm in zip((x, y, z, m), "xyzm")]
+    _check(lib().afd_reuse_lists(ctx, *p), "afd_reuse_lists")
+
+
+def afd_calc_force(ctx, acc4):
+    import torch
+    _check(lib().afd_calc_force(ctx, _dptr(acc4, torch.float32, None, "acc4")), "afd_calc_force")
+
+
+def afd_calc_force_all(ctx, x, y, z, m, acc4, mode):
+    import torch
+    n = x.numel()
+    p = [_dptr(a, torch.float64, n, nm) for a, nm in zip((x, y, z, m), "xyzm")]
+    _check(lib().afd_calc_force_all(ctx, *p, n, _dptr(acc4, torch.float32, 4 * n, "acc4"),
+                                    int(mode)), "afd_calc_force_all")
+
+
+def afd_calc_force_all_host(ctx, x, y, z, m, acc4, mode):
+    """Host-array variant: x, y, z, m float64 and acc4 float32 (n, 4) CPU
+    tensors or numpy arrays (pinned memory gives the fastest copies)."""
+    def hp(a, dtype):
+        if hasattr(a, "data_ptr"):
+            if a.is_cuda or not a.is_contiguous():
+                raise ValueError("host arrays must be contiguous CPU tensors")
+            return _VP(a.data_ptr())
+        if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be contiguous with the right dtype")
+        return _VP(a.ctypes.data)
+    n = len(x)
+    p = [hp(a, np.float64) for a in (x, y, z, m)]
+    _check(lib().afd_calc_force_all_host(ctx, *p, n, hp(acc4, np.float32), int(mode)),
+           "afd_calc_force_all_host")
+
+
+def afd_kick_drift(ctx, x, y, z, vx, vy, vz, acc4, dt_kick, dt_drift):
+    import torch
+    n = x.numel()
+    p = [_dptr(a, torch.float64, n) for a in (x, y, z, vx, vy, vz)]
+    _check(lib().afd_kick_drift(ctx, *p, _dptr(acc4, torch.float32, 4 * n), n, float(dt_kick),
+                                float(dt_drift)), "afd_kick_drift")
+
+
+def afd_kick(ctx, vx, vy, vz, acc4, dt_kick):
+    import torch
+    n = vx.numel()
+    p = [_dptr(a, torch.float64, n) for a in (vx, vy, vz)]
+    _check(lib().afd_kick(ctx, *p, _dptr(acc4, torch.float32, 4 * n), n, float(dt_kick)),
+           "afd_kick")
+
+
+def afd_leapfrog(ctx, x, y, z, vx, vy, vz, m, acc4, dt, n_steps, n_reuse):
+    import torch
+    n = x.numel()
+    p = [_dptr(a, torch.float64, n) for a in (x, y, z, vx, vy, vz, m)]
+    _check(lib().afd_leapfrog(ctx, *p, n, _dptr(acc4, torch.float32, 4 * n), float(dt),
+                              int(n_steps), int(n_reuse)), "afd_leapfrog")
+
+
+def afd_energy(ctx, vx, vy, vz, m, acc4):
+    import torch
+    n = vx.numel()
+    out = (ctypes.c_double * 2)()
+    p = [_dptr(a, torch.float64, n) for a in (vx, vy, vz, m)]
+    _check(lib().afd_energy(ctx, *p, _dptr(acc4, torch.float32, 4 * n), n,
+                            ctypes.cast(out, _VP)), "afd_energy")
+    return float(out[0]), float(out[1])
+
+
+def afd_sync(ctx):
+    _check(lib().afd_sync(ctx), "afd_sync")
+
+
+def afd_stats(ctx) -> dict:
+    out = (ctypes.c_int64 * 10)()
+    _check(lib().afd_stats(ctx, ctypes.cast(out, _VP)), "afd_stats")
+    keys = ("n", "n_cells", "n_groups", "n_epj", "n_spj", "interactions", "saved", "max_level",
+            "launches", "n_units")
+    return dict(zip(keys, (int(v) for v in out)))
+
+
+def afd_export(ctx, what: str) -> np.ndarray:
+    item, dtype = EXPORT[what]
+    nbytes = ctypes.c_size_t(0)
+    _check(lib().afd_export(ctx, item, None, ctypes.byref(nbytes)), "afd_export")
+    arr = np.zeros(nbytes.value // np.dtype(dtype).itemsize, dtype=dtype)
+    if nbytes.value:
+        _check(lib().afd_export(ctx, item, _VP(arr.ctypes.data), ctypes.byref(nbytes)),
+               "afd_export")
+    return arr
+
+
+def afd_last_force_ms(ctx) -> float:
+    v = ctypes.c_float(0.0)
+    _check(lib().afd_last_force_ms(ctx, ctypes.byref(v)), "afd_last_force_ms")
+    return float(v.value)
+
+
+# ---------------------------------------------------------------- convenience
+
+
+@dataclass
+class Config:
+    eps: float = 1.0 / 256
+    theta: float = 0.5
+    n_leaf: int = 16
+    n_grp: int = 64
+    multipole: int = 0
+    far_precision: int = 0
+
+    def c(self) -> afd_config:
+        return afd_config(float(self.eps), float(self.theta), int(self.n_leaf), int(self.n_grp),
+                          int(self.multipole), int(self.far_precision), 0, 0)
+
+
+class Gravity:
+    """Owns one library context; methods forward to the C entry points."""
+
+    def __init__(self, cfg: Config, device: int = 0, stream=None):
+        self.cfg = cfg
+        self.ctx = afd_create(cfg.c(), device, stream)
+
+    def close(self):
+        if self.ctx is not None and self.ctx.value:
+            afd_destroy(self.ctx)
+        self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def force_all(self, x, y, z, m, acc4, mode=AFD_MAKE_LIST_FOR_REUSE):
+        afd_calc_force_all(self.ctx, x, y, z, m, acc4, mode)
+
+    def stats(self):
+        return afd_stats(self.ctx)
+
+    def export(self, what):
+        return afd_export(self.ctx, what)

@@ -1,0 +1,461 @@
+// C ABI entry points (include/afdps.h), the kick/drift kernels of the
+// leapfrog and the FP64 energy reduction.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "afd_internal.cuh"
+
+using namespace afd;
+
+namespace {
+
+// Makes the context's device current for the duration of a call and
+// restores the caller's device afterwards.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+#define TRY(x)                    \
+  do {                            \
+    int _s = (x);                 \
+    if (_s != AFD_OK) return _s;  \
+  } while (0)
+
+inline int cuda_ok(cudaError_t e) {
+  if (e == cudaSuccess) return AFD_OK;
+  cudaGetLastError();
+  return AFD_ERR_CUDA;
+}
+
+constexpr int kThreads = 256;
+
+__global__ void k_kick_drift(double *__restrict__ x, double *__restrict__ y,
+                             double *__restrict__ z, double *__restrict__ vx,
+                             double *__restrict__ vy, double *__restrict__ vz,
+                             const float4 *__restrict__ acc, int64_t n, double dtk, double dtd) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 a = acc[i];
+  const double ux = vx[i] + (double)a.x * dtk;
+  const double uy = vy[i] + (double)a.y * dtk;
+  const double uz = vz[i] + (double)a.z * dtk;
+  vx[i] = ux;
+  vy[i] = uy;
+  vz[i] = uz;
+  x[i] += ux * dtd;
+  y[i] += uy * dtd;
+  z[i] += uz * dtd;
+}
+
+__global__ void k_kick(double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz,
+                       const float4 *__restrict__ acc, int64_t n, double dtk) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 a = acc[i];
+  vx[i] += (double)a.x * dtk;
+  vy[i] += (double)a.y * dtk;
+  vz[i] += (double)a.z * dtk;
+}
+
+// FP64 energies with a fixed reduction order: block b sums a fixed slice,
+// the last block sums the block partials in block order.
+constexpr int kEnergyBlocks = 304;
+
+__global__ void k_energy(const double *__restrict__ vx, const double *__restrict__ vy,
+                         const double *__restrict__ vz, const double *__restrict__ m,
+                         const float4 *__restrict__ acc, int64_t n, double *__restrict__ part,
+                         unsigned *__restrict__ counter, double *__restrict__ out) {
+  double k = 0.0, w = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v2 = vx[i] * vx[i] + vy[i] * vy[i] + vz[i] * vz[i];
+    k += 0.5 * m[i] * v2;
+    w += 0.5 * m[i] * (double)acc[i].w;
+  }
+  __shared__ double sk[kThreads], sw[kThreads];
+  __shared__ bool last;
+  sk[threadIdx.x] = k;
+  sw[threadIdx.x] = w;
+  __syncthreads();
+  for (int s = kThreads / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      sk[threadIdx.x] += sk[threadIdx.x + s];
+      sw[threadIdx.x] += sw[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = sk[0];
+    part[2 * blockIdx.x + 1] = sw[0];
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  double K = 0.0, W = 0.0;
+  for (unsigned b = 0; b < gridDim.x; b++) {
+    K += __ldcg(&part[2 * b]);
+    W += __ldcg(&part[2 * b + 1]);
+  }
+  out[0] = K;
+  out[1] = W;
+  *counter = 0u;
+}
+
+int read_status(afd_ctx *c) {
+  int *pin = static_cast<int *>(c->pinned);
+  if (cudaMemcpyAsync(pin, c->status.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return AFD_ERR_CUDA;
+  }
+  const int bits = *pin;
+  if (bits) cudaMemsetAsync(c->status.p, 0, sizeof(int), c->stream);
+  return status_to_error(bits);
+}
+
+int tree_build(afd_ctx *c, const double *x, const double *y, const double *z, const double *m,
+               int64_t n) {
+  if (n < 0 || n >= ((int64_t)1 << 31)) return AFD_ERR_ARG;
+  if (n > 0 && (!x || !y || !z || !m)) return AFD_ERR_ARG;
+  c->have_tree = c->have_lists = c->saved = false;
+  TRY(launch_root(c, x, y, z, m, n));
+  TRY(launch_keys(c, x, y, z, n));
+  TRY(launch_sort(c, n));
+  TRY(launch_reorder(c, x, y, z, m, n));
+  TRY(launch_link(c, n));
+  TRY(read_status(c));
+  TRY(launch_moments(c));
+  TRY(launch_groups(c));
+  TRY(launch_group_boxes(c));
+  c->n = n;
+  c->have_tree = true;
+  return AFD_OK;
+}
+
+int make_lists(afd_ctx *c, int mode) {
+  if (mode != AFD_MAKE_LIST && mode != AFD_MAKE_LIST_FOR_REUSE) return AFD_ERR_ARG;
+  if (!c->have_tree) return AFD_ERR_NO_TREE;
+  c->have_lists = c->saved = false;
+  TRY(launch_walk(c));
+  c->have_lists = true;
+  c->saved = mode == AFD_MAKE_LIST_FOR_REUSE;
+  return AFD_OK;
+}
+
+int reuse(afd_ctx *c, const double *x, const double *y, const double *z, const double *m) {
+  if (!c->saved || !c->have_lists) return AFD_ERR_NO_SAVED_LIST;
+  if (c->n > 0 && (!x || !y || !z || !m)) return AFD_ERR_ARG;
+  TRY(launch_reorder(c, x, y, z, m, c->n));
+  TRY(launch_moments(c));
+  TRY(launch_group_boxes(c));
+  return AFD_OK;
+}
+
+int calc_force(afd_ctx *c, float *acc4) {
+  if (!c->have_lists) return c->have_tree ? AFD_ERR_NO_SAVED_LIST : AFD_ERR_NO_TREE;
+  if (c->n > 0 && !acc4) return AFD_ERR_ARG;
+  return launch_force(c, acc4);
+}
+
+int calc_force_all(afd_ctx *c, const double *x, const double *y, const double *z,
+                   const double *m, int64_t n, float *acc4, int mode) {
+  if (mode == AFD_REUSE_LIST) {
+    if (!c->saved) return AFD_ERR_NO_SAVED_LIST;
+    if (n != c->n) return AFD_ERR_SHAPE;
+    TRY(reuse(c, x, y, z, m));
+  } else {
+    TRY(tree_build(c, x, y, z, m, n));
+    TRY(make_lists(c, mode));
+  }
+  return calc_force(c, acc4);
+}
+
+inline unsigned nblocks(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+}  // namespace
+
+extern "C" {
+
+int afd_create(afd_ctx **out, const afd_config *cfg, int device, void *stream) {
+  if (!out || !cfg) return AFD_ERR_ARG;
+  *out = nullptr;
+  if (!std::isfinite(cfg->eps) || cfg->eps < 0.0 || !std::isfinite(cfg->theta) ||
+      cfg->theta < 0.0 || cfg->n_leaf < 1 || cfg->n_grp < 1 || cfg->n_grp > 1024 ||
+      (cfg->multipole != 0 && cfg->multipole != 1) || cfg->far_precision < 0 ||
+      cfg->far_precision > 2 || cfg->mac != 0 || cfg->reserved != 0)
+    return AFD_ERR_ARG;
+  DeviceGuard g(device);
+  if (!g.ok) return AFD_ERR_CUDA;
+  afd_ctx *c = new (std::nothrow) afd_ctx();
+  if (!c) return AFD_ERR_OOM;
+  c->cfg = *cfg;
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(stream);
+  if (cudaMallocHost(&c->pinned, 256) != cudaSuccess || cudaEventCreate(&c->ev0) != cudaSuccess ||
+      cudaEventCreate(&c->ev1) != cudaSuccess || reserve(c->status, 16) != AFD_OK ||
+      reserve(c->red_count, 16) != AFD_OK || reserve(c->u64acc, 64) != AFD_OK ||
+      cudaMemset(c->status.p, 0, 16) != cudaSuccess ||
+      cudaMemset(c->red_count.p, 0, 16) != cudaSuccess) {
+    cudaGetLastError();
+    afd_destroy(c);
+    return AFD_ERR_CUDA;
+  }
+  *out = c;
+  return AFD_OK;
+}
+
+void afd_destroy(afd_ctx *c) {
+  if (!c) return;
+  DeviceGuard g(c->device);
+  cudaStreamSynchronize(c->stream);
+  DevBuf *bufs[] = {&c->root, &c->status, &c->red_part, &c->red_count, &c->u64acc, &c->keys,
+                    &c->keys2, &c->perm, &c->perm2, &c->sort_cnt, &c->sort_off, &c->xs, &c->ys,
+                    &c->zs, &c->ms, &c->jhi, &c->jlo, &c->lk_d, &c->lk_c, &c->lk_e, &c->lk_cnt,
+                    &c->lk_off, &c->c_level, &c->c_first, &c->c_count, &c->c_skip, &c->c_parent,
+                    &c->c_child, &c->c_arrive, &c->c_mass, &c->c_smom, &c->c_com, &c->c_quad,
+                    &c->s_hi, &c->s_lo, &c->s_q0, &c->s_q1, &c->node_f, &c->node_i, &c->g_cnt,
+                    &c->g_off, &c->g_first, &c->g_count, &c->g_box, &c->g_boxf, &c->g_chi,
+                    &c->g_clo, &c->g_self, &c->u_cnt, &c->u_off, &c->u_group, &c->l_cnt_e,
+                    &c->l_cnt_s, &c->epj_off, &c->spj_off, &c->epj, &c->spj, &c->scan_tmp,
+                    &c->hx, &c->hy, &c->hz, &c->hm, &c->hacc};
+  for (DevBuf *b : bufs) release(*b);
+  if (c->pinned) cudaFreeHost(c->pinned);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  delete c;
+}
+
+int afd_set_stream(afd_ctx *c, void *stream) {
+  if (!c) return AFD_ERR_ARG;
+  c->stream = static_cast<cudaStream_t>(stream);
+  return AFD_OK;
+}
+
+int afd_tree_build(afd_ctx *c, const double *x, const double *y, const double *z,
+                   const double *m, int64_t n) {
+  if (!c) return AFD_ERR_ARG;
+  DeviceGuard g(c->device);
+  return tree_build(c, x, y, z, m, n);
+}
+
+int afd_make_interaction_lists(afd_ctx *c, int mode) {
+  if (!c) return AFD_ERR_ARG;
+  DeviceGuard g(c->device);
+  return make_lists(c, mode);
+}
+
+int afd_reuse_lists(afd_ctx *c, const double *x, const double *y, const double *z,
+                    const double *m) {
+  if (!c) return AFD_ERR_ARG;
+  DeviceGuard g(c->device);
+  return reuse(c, x, y, z, m);
+}
+
+int afd_calc_force(afd_ctx *c, float *acc4) {
+  if (!c) return AFD_ERR_ARG;
+  DeviceGuard g(c->device);
+  return calc_force(c, acc4);
+}
+
+int afd_calc_force_all(afd_ctx *c, const double *x, const double *y, const double *z,
+                       const double *m, int64_t n, float *acc4, int mode) {
+  if (!c) return AFD_ERR_ARG;
+  if (mode < AFD_MAKE_LIST || mode > AFD_REUSE_LIST) return AFD_ERR_ARG;
+  DeviceGuard g(c->device);
+  return calc_force_all(c, x, y, z, m, n, acc4, mode);
+}
+
+int afd_calc_force_all_host(afd_ctx *c, const double *x, const double *y, const double *z,
+                            const double *m, int64_t n, float *acc4_host, int mode) {
+  if (!c || n < 0) return AFD_ERR_ARG;
+  if (n > 0 && (!x || !y || !z || !m || !acc4_host)) return AFD_ERR_ARG;
+  if (mode < AFD_MAKE_LIST || mode > AFD_REUSE_LIST) return AFD_ERR_ARG;
+  DeviceGuard g(c->device);
+  const size_t bd = sizeof(double) * (size_t)n;
+  TRY(reserve(c->hx, bd));
+  TRY(reserve(c->hy, bd));
+  TRY(reserve(c->hz, bd));
+  TRY(reserve(c->hm, bd));
+  TRY(reserve(c->hacc, sizeof(float4) * (size_t)n));
+  if (n > 0) {
+    TRY(cuda_ok(cudaMemcpyAsync(c->hx.p, x, bd, cudaMemcpyHostToDevice, c->stream)));
+    TRY(cuda_ok(cudaMemcpyAsync(c->hy.p, y, bd, cudaMemcpyHostToDevice, c->stream)));
+    TRY(cuda_ok(cudaMemcpyAsync(c->hz.p, z, bd, cudaMemcpyHostToDevice, c->stream)));
+    TRY(cuda_ok(cudaMemcpyAsync(c->hm.p, m, bd, cudaMemcpyHostToDevice, c->stream)));
+  }
+  TRY(calc_force_all(c, ptr<double>(c->hx), ptr<double>(c->hy), ptr<double>(c->hz),
+                     ptr<double>(c->hm), n, ptr<float>(c->hacc), mode));
+  if (n > 0)
+    TRY(cuda_ok(cudaMemcpyAsync(acc4_host, c->hacc.p, sizeof(float4) * (size_t)n,
+                                cudaMemcpyDeviceToHost, c->stream)));
+  TRY(cuda_ok(cudaStreamSynchronize(c->stream)));
+  return read_status(c);
+}
+
+int afd_kick_drift(afd_ctx *c, double *x, double *y, double *z, double *vx, double *vy,
+                   double *vz, const float *acc4, int64_t n, double dt_kick, double dt_drift) {
+  if (!c || n < 0) return AFD_ERR_ARG;
+  if (n == 0) return AFD_OK;
+  if (!x || !y || !z || !vx || !vy || !vz || !acc4) return AFD_ERR_ARG;
+  DeviceGuard g(c->device);
+  k_kick_drift<<<nblocks(n), kThreads, 0, c->stream>>>(
+      x, y, z, vx, vy, vz, reinterpret_cast<const float4 *>(acc4), n, dt_kick, dt_drift);
+  c->launches++;
+  return cuda_ok(cudaGetLastError());
+}
+
+int afd_kick(afd_ctx *c, double *vx, double *vy, double *vz, const float *acc4, int64_t n,
+             double dt_kick) {
+  if (!c || n < 0) return AFD_ERR_ARG;
+  if (n == 0) return AFD_OK;
+  if (!vx || !vy || !vz || !acc4) return AFD_ERR_ARG;
+  DeviceGuard g(c->device);
+  k_kick<<<nblocks(n), kThreads, 0, c->stream>>>(vx, vy, vz,
+                                                 reinterpret_cast<const float4 *>(acc4), n,
+                                                 dt_kick);
+  c->launches++;
+  return cuda_ok(cudaGetLastError());
+}
+
+int afd_leapfrog(afd_ctx *c, double *x, double *y, double *z, double *vx, double *vy,
+                 double *vz, const double *m, int64_t n, float *acc4, double dt, int n_steps,
+                 int n_reuse) {
+  if (!c || n < 0 || n_steps < 0 || n_reuse < 1) return AFD_ERR_ARG;
+  DeviceGuard g(c->device);
+  for (int s = 0; s < n_steps; s++) {
+    TRY(afd_kick_drift(c, x, y, z, vx, vy, vz, acc4, n, 0.5 * dt, dt));
+    const int64_t k = (int64_t)s + 1;
+    const bool rebuild = (k % n_reuse == 0) || !c->saved || c->n != n;
+    TRY(calc_force_all(c, x, y, z, m, n, acc4,
+                       rebuild ? AFD_MAKE_LIST_FOR_REUSE : AFD_REUSE_LIST));
+    TRY(afd_kick(c, vx, vy, vz, acc4, n, 0.5 * dt));
+  }
+  return AFD_OK;
+}
+
+int afd_energy(afd_ctx *c, const double *vx, const double *vy, const double *vz,
+               const double *m, const float *acc4, int64_t n, double *out) {
+  if (!c || !out || n < 0) return AFD_ERR_ARG;
+  out[0] = out[1] = 0.0;
+  if (n == 0) return AFD_OK;
+  if (!vx || !vy || !vz || !m || !acc4) return AFD_ERR_ARG;
+  DeviceGuard g(c->device);
+  TRY(reserve(c->red_part, sizeof(double) * 2 * kEnergyBlocks + 64));
+  double *part = ptr<double>(c->red_part);
+  double *res = part + 2 * kEnergyBlocks;
+  int64_t nb = (n + kThreads - 1) / kThreads;
+  if (nb > kEnergyBlocks) nb = kEnergyBlocks;
+  k_energy<<<(unsigned)nb, kThreads, 0, c->stream>>>(vx, vy, vz, m,
+                                                     reinterpret_cast<const float4 *>(acc4), n,
+                                                     part, ptr<unsigned>(c->red_count), res);
+  c->launches++;
+  TRY(cuda_ok(cudaGetLastError()));
+  double *pin = static_cast<double *>(c->pinned);
+  TRY(cuda_ok(cudaMemcpyAsync(pin, res, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream)));
+  TRY(cuda_ok(cudaStreamSynchronize(c->stream)));
+  out[0] = pin[0];
+  out[1] = pin[1];
+  return AFD_OK;
+}
+
+int afd_sync(afd_ctx *c) {
+  if (!c) return AFD_ERR_ARG;
+  DeviceGuard g(c->device);
+  return read_status(c);
+}
+
+int afd_stats(afd_ctx *c, int64_t *out) {
+  if (!c || !out) return AFD_ERR_ARG;
+  out[0] = c->have_tree ? c->n : 0;
+  out[1] = c->have_tree ? c->n_cells : 0;
+  out[2] = c->have_tree ? c->n_groups : 0;
+  out[3] = c->have_lists ? (int64_t)c->n_epj : 0;
+  out[4] = c->have_lists ? (int64_t)c->n_spj : 0;
+  out[5] = c->have_lists ? (int64_t)c->interactions : 0;
+  out[6] = c->saved ? 1 : 0;
+  out[7] = c->have_tree ? c->max_level : 0;
+  out[8] = c->launches;
+  out[9] = c->n_units;
+  return AFD_OK;
+}
+
+int afd_export(afd_ctx *c, int what, void *host_buf, size_t *bytes) {
+  if (!c || !bytes) return AFD_ERR_ARG;
+  const void *src = nullptr;
+  size_t sz = 0;
+  const size_t n = (size_t)c->n, nc = (size_t)c->n_cells, ng = (size_t)c->n_groups;
+  const bool tree = c->have_tree, lists = c->have_lists;
+  switch (what) {
+    case AFD_EXPORT_ROOT: src = c->root.p; sz = tree ? 4 * sizeof(double) : 0; break;
+    case AFD_EXPORT_KEYS: src = c->keys.p; sz = tree ? n * 8 : 0; break;
+    case AFD_EXPORT_PERM: src = c->perm.p; sz = tree ? n * 4 : 0; break;
+    case AFD_EXPORT_CELL_LEVEL: src = c->c_level.p; sz = tree ? nc * 4 : 0; break;
+    case AFD_EXPORT_CELL_FIRST: src = c->c_first.p; sz = tree ? nc * 4 : 0; break;
+    case AFD_EXPORT_CELL_COUNT: src = c->c_count.p; sz = tree ? nc * 4 : 0; break;
+    case AFD_EXPORT_CELL_SKIP: src = c->c_skip.p; sz = tree ? nc * 4 : 0; break;
+    case AFD_EXPORT_CELL_PARENT: src = c->c_parent.p; sz = tree ? nc * 4 : 0; break;
+    case AFD_EXPORT_CELL_CHILD: src = c->c_child.p; sz = tree ? nc * 32 : 0; break;
+    case AFD_EXPORT_CELL_MASS: src = c->c_mass.p; sz = tree ? nc * 8 : 0; break;
+    case AFD_EXPORT_CELL_COM: src = c->c_com.p; sz = tree ? nc * 24 : 0; break;
+    case AFD_EXPORT_CELL_QUAD: src = c->c_quad.p; sz = tree ? nc * 48 : 0; break;
+    case AFD_EXPORT_GROUP_FIRST: src = c->g_first.p; sz = tree ? ng * 4 : 0; break;
+    case AFD_EXPORT_GROUP_COUNT: src = c->g_count.p; sz = tree ? ng * 4 : 0; break;
+    case AFD_EXPORT_GROUP_BOX: src = c->g_box.p; sz = tree ? ng * 48 : 0; break;
+    case AFD_EXPORT_GROUP_SELF: src = c->g_self.p; sz = lists ? ng * 4 : 0; break;
+    case AFD_EXPORT_EPJ_OFF: src = c->epj_off.p; sz = lists ? (ng + 1) * 8 : 0; break;
+    case AFD_EXPORT_EPJ_IDX: src = c->epj.p; sz = lists ? (size_t)c->n_epj * 4 : 0; break;
+    case AFD_EXPORT_SPJ_OFF: src = c->spj_off.p; sz = lists ? (ng + 1) * 8 : 0; break;
+    case AFD_EXPORT_SPJ_IDX: src = c->spj.p; sz = lists ? (size_t)c->n_spj * 4 : 0; break;
+    default: return AFD_ERR_ARG;
+  }
+  if (!host_buf) {
+    *bytes = sz;
+    return AFD_OK;
+  }
+  if (*bytes < sz) return AFD_ERR_ARG;
+  *bytes = sz;
+  if (sz == 0) return AFD_OK;
+  DeviceGuard g(c->device);
+  TRY(cuda_ok(cudaStreamSynchronize(c->stream)));
+  return cuda_ok(cudaMemcpy(host_buf, src, sz, cudaMemcpyDeviceToHost));
+}
+
+int afd_last_force_ms(afd_ctx *c, float *ms) {
+  if (!c || !ms) return AFD_ERR_ARG;
+  *ms = 0.0f;
+  if (!c->force_timed) return AFD_OK;
+  DeviceGuard g(c->device);
+  TRY(cuda_ok(cudaEventSynchronize(c->ev1)));
+  return cuda_ok(cudaEventElapsedTime(ms, c->ev0, c->ev1));
+}
+
+const char *afd_error_string(int status) {
+  switch (status) {
+    case AFD_OK: return "ok";
+    case AFD_ERR_ARG: return "invalid argument";
+    case AFD_ERR_CUDA: return "CUDA runtime error";
+    case AFD_ERR_NONFINITE: return "non-finite particle coordinate or mass";
+    case AFD_ERR_NO_SAVED_LIST: return "no interaction lists saved for reuse";
+    case AFD_ERR_SHAPE: return "particle count differs from the saved tree";
+    case AFD_ERR_LIST_OVERFLOW: return "list or cell count exceeds 32-bit indexing";
+    case AFD_ERR_TIMEOUT: return "bounded device wait or walk iteration limit reached";
+    case AFD_ERR_NO_TREE: return "no tree built";
+    case AFD_ERR_OOM: return "device allocation failed";
+    case AFD_ERR_WALK_STACK: return "tree walk overflowed its stack";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,128 @@
+// Internal declarations of the sm_103a tree-gravity library: the context,
+// device buffers and the host-side launchers of every kernel. Not part of
+// the C ABI (include/afdps.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "afdps.h"
+
+namespace afd {
+
+constexpr int kLevels = 21;          // 21 key bits per axis, deepest level
+constexpr uint32_t kNone = 0xffffffffu;
+
+// A device allocation that only grows.
+struct DevBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+};
+
+int reserve(DevBuf &b, size_t bytes);  // AFD_OK or AFD_ERR_OOM
+void release(DevBuf &b);
+template <class T>
+inline T *ptr(const DevBuf &b) {
+  return static_cast<T *>(b.p);
+}
+
+// Device status word bits (OR-ed by kernels, decoded on the host).
+enum : int {
+  kStNonFinite = 1,
+  kStWalkStack = 2,
+  kStWalkIter = 4,
+  kStOverflow = 8,
+};
+int status_to_error(int bits);
+
+}  // namespace afd
+
+struct afd_ctx {
+  afd_config cfg{};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+
+  // sizes of the current tree / lists
+  int64_t n = 0;
+  int64_t n_cells = 0;
+  int64_t n_groups = 0;
+  int64_t n_units = 0;
+  uint64_t n_epj = 0, n_spj = 0, interactions = 0;
+  int max_level = 0;
+  bool have_tree = false, have_lists = false, saved = false;
+
+  // root cell and status
+  afd::DevBuf root;       // f64[4] centre xyz, L
+  afd::DevBuf status;     // i32[1]
+  afd::DevBuf red_part;   // root-reduction partials
+  afd::DevBuf red_count;  // u32 last-block counter (kept at 0 between launches)
+  afd::DevBuf u64acc;     // u64[4] small accumulators
+
+  // keys, sort and reorder
+  afd::DevBuf keys, keys2, perm, perm2, sort_cnt, sort_off;
+  afd::DevBuf xs, ys, zs, ms;  // FP64 Morton order
+  afd::DevBuf jhi, jlo;        // float4 (hi xyz, m) and (lo xyz, 0) per particle
+
+  // link
+  afd::DevBuf lk_d, lk_c, lk_e;  // u8 per particle
+  afd::DevBuf lk_cnt, lk_off;    // u32 per particle (+1)
+
+  // cells (depth-first pre-order)
+  afd::DevBuf c_level, c_first, c_count, c_skip, c_parent, c_child, c_arrive;
+  afd::DevBuf c_mass, c_smom, c_com, c_quad;  // f64
+  afd::DevBuf s_hi, s_lo, s_q0, s_q1;         // float4 superparticle data
+  afd::DevBuf node_f, node_i;                 // walk node data (float4, uint2)
+
+  // groups and force work units
+  afd::DevBuf g_cnt, g_off;
+  afd::DevBuf g_first, g_count, g_box, g_boxf, g_chi, g_clo, g_self;
+  afd::DevBuf u_cnt, u_off, u_group;
+
+  // lists (CSR)
+  afd::DevBuf l_cnt_e, l_cnt_s, epj_off, spj_off, epj, spj;
+
+  // scan scratch
+  afd::DevBuf scan_tmp;
+
+  // host-array entry point staging
+  afd::DevBuf hx, hy, hz, hm, hacc;
+
+  // pinned host scratch for small reads
+  void *pinned = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool force_timed = false;
+
+  int64_t eval_counter = 0;
+  int64_t launches = 0;  // kernels queued by this context so far
+};
+
+namespace afd {
+
+// ---- scans (afd_util.cu) ----
+// Exclusive scan of n values into out[0..n]; out[n] is the total.
+int scan_u32(afd_ctx *c, const uint32_t *in, uint32_t *out, int64_t n);
+int scan_u32_to_u64(afd_ctx *c, const uint32_t *in, uint64_t *out, int64_t n);
+
+// ---- tree (afd_tree.cu) ----
+int launch_root(afd_ctx *c, const double *x, const double *y, const double *z, const double *m,
+                int64_t n);
+int launch_keys(afd_ctx *c, const double *x, const double *y, const double *z, int64_t n);
+int launch_sort(afd_ctx *c, int64_t n);  // sorts keys/perm in place (result in keys, perm)
+int launch_reorder(afd_ctx *c, const double *x, const double *y, const double *z,
+                   const double *m, int64_t n);
+int launch_link(afd_ctx *c, int64_t n);        // sets c->n_cells, c->max_level (syncs)
+int launch_moments(afd_ctx *c);                // bottom-up moments + superparticle data
+int launch_groups(afd_ctx *c);                 // sets c->n_groups, c->n_units (syncs)
+int launch_group_boxes(afd_ctx *c);
+
+// ---- walk (afd_walk.cu) ----
+int launch_walk(afd_ctx *c);  // lists; sets n_epj, n_spj, interactions (syncs)
+
+// ---- force (afd_force.cu) ----
+int launch_force(afd_ctx *c, float *acc4);
+
+// ---- integration (afd_api.cu) ----
+
+}  // namespace afd

@@ -1,0 +1,826 @@
+// Tree construction on sm_103a (Section 4.3 of the paper): root cell, Morton
+// keys, stable LSD radix sort, reorder into Morton order, octree link and
+// bottom-up moments, i-groups.
+//
+// FP64 arithmetic that decides an integer or feeds the opening criterion
+// (key scaling, moment sums, centres) is written with explicit _rn
+// intrinsics so that no multiply-add is contracted: the results are the
+// IEEE results of the operation sequence stated in each kernel.
+#include <cfloat>
+
+#include "afd_internal.cuh"
+
+namespace afd {
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned blocks_for(int64_t n, int threads = kThreads) {
+  return (unsigned)((n + threads - 1) / threads);
+}
+
+// ---------------------------------------------------------------------------
+// Root cell: bounding box of all particles, centre (min+max)/2, side L = the
+// smallest power of two >= 1.000001 * largest extent (1 for a zero extent).
+// One pass; the last block to finish reduces the per-block partials.
+// ---------------------------------------------------------------------------
+constexpr int kRootBlocks = 608;
+
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__global__ void __launch_bounds__(kThreads) k_root(const double *__restrict__ x,
+                                                   const double *__restrict__ y,
+                                                   const double *__restrict__ z,
+                                                   const double *__restrict__ m, int64_t n,
+                                                   double *__restrict__ part,
+                                                   unsigned *__restrict__ counter,
+                                                   double *__restrict__ root, int *status) {
+  double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+  int bad = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v[3] = {x[i], y[i], z[i]};
+    const double mv = m[i];
+    bad |= !isfinite(mv);
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      bad |= !isfinite(v[d]);
+      lo[d] = fmin(lo[d], v[d]);
+      hi[d] = fmax(hi[d], v[d]);
+    }
+  }
+  __shared__ double sh[kThreads / 32][6];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    lo[d] = warp_min(lo[d]);
+    hi[d] = warp_max(hi[d]);
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, kStNonFinite);
+  if (lane == 0)
+    for (int d = 0; d < 3; d++) {
+      sh[warp][d] = lo[d];
+      sh[warp][3 + d] = hi[d];
+    }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b[6];
+    for (int d = 0; d < 6; d++) b[d] = sh[0][d];
+    for (int w = 1; w < kThreads / 32; w++)
+      for (int d = 0; d < 3; d++) {
+        b[d] = fmin(b[d], sh[w][d]);
+        b[3 + d] = fmax(b[3 + d], sh[w][3 + d]);
+      }
+    for (int d = 0; d < 6; d++) part[blockIdx.x * 6 + d] = b[d];
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  double b[6];
+  for (int d = 0; d < 6; d++) b[d] = __ldcg(&part[d]);
+  for (unsigned k = 1; k < gridDim.x; k++)
+    for (int d = 0; d < 3; d++) {
+      b[d] = fmin(b[d], __ldcg(&part[k * 6 + d]));
+      b[3 + d] = fmax(b[3 + d], __ldcg(&part[k * 6 + 3 + d]));
+    }
+  double ext = 0.0;
+  for (int d = 0; d < 3; d++) {
+    root[d] = __dmul_rn(__dadd_rn(b[d], b[3 + d]), 0.5);
+    const double e = __dsub_rn(b[3 + d], b[d]);
+    if (e > ext) ext = e;
+  }
+  const double target = __dmul_rn(ext, 1.000001);
+  double L = 1.0;
+  if (target > 0.0) {
+    while (L < target) L = __dmul_rn(L, 2.0);
+    while (__dmul_rn(L, 0.5) >= target) L = __dmul_rn(L, 0.5);
+  }
+  root[3] = L;
+  *counter = 0u;  // ready for the next launch
+}
+
+// ---------------------------------------------------------------------------
+// Morton keys: q_d = clamp(floor((x_d - (c_d - L/2)) * 2^21 / L)), bits
+// interleaved x-y-z from the most significant end (63 bits used).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t spread3(uint32_t v) {
+  uint64_t x = v & 0x1fffffu;
+  x = (x | (x << 32)) & 0x1f00000000ffffull;
+  x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+  x = (x | (x << 8)) & 0x100f00f00f00f00full;
+  x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+  x = (x | (x << 2)) & 0x1249249249249249ull;
+  return x;
+}
+
+__device__ __forceinline__ uint32_t grid_coord(double v, double corner, double scale) {
+  const double t = floor(__dmul_rn(__dsub_rn(v, corner), scale));
+  if (!(t > 0.0)) return 0u;
+  if (t > 2097151.0) return 2097151u;
+  return (uint32_t)t;
+}
+
+__global__ void __launch_bounds__(kThreads) k_keys(const double *__restrict__ x,
+                                                   const double *__restrict__ y,
+                                                   const double *__restrict__ z, int64_t n,
+                                                   const double *__restrict__ root,
+                                                   uint64_t *__restrict__ keys,
+                                                   uint32_t *__restrict__ perm) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double L = root[3];
+  const double half = __dmul_rn(L, 0.5);
+  const double scale = __ddiv_rn(2097152.0, L);
+  const uint32_t qx = grid_coord(x[i], __dsub_rn(root[0], half), scale);
+  const uint32_t qy = grid_coord(y[i], __dsub_rn(root[1], half), scale);
+  const uint32_t qz = grid_coord(z[i], __dsub_rn(root[2], half), scale);
+  keys[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+  perm[i] = (uint32_t)i;
+}
+
+// ---------------------------------------------------------------------------
+// Stable LSD radix sort of (key, index), 8-bit digits, 8 passes. Each pass:
+// per-tile digit histogram, exclusive scan in digit-major order, then a
+// stable scatter in which every tile ranks its keys in input order
+// (warp match for lanes, shared counters for warps and rounds).
+// ---------------------------------------------------------------------------
+constexpr int kSortThreads = 256;
+constexpr int kSortRounds = 16;
+constexpr int kSortTile = kSortThreads * kSortRounds;
+constexpr int kSortWarps = kSortThreads / 32;
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint64_t *__restrict__ keys,
+                                                            int64_t n, int shift,
+                                                            uint32_t *__restrict__ cnt,
+                                                            int num_tiles) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  for (int k = threadIdx.x; k < kSortTile; k += kSortThreads) {
+    const int64_t i = base + k;
+    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  cnt[(int64_t)threadIdx.x * num_tiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
+    const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
+    uint32_t *__restrict__ vout, int64_t n, int shift, const uint32_t *__restrict__ off,
+    int num_tiles) {
+  __shared__ uint32_t gbase[256];
+  __shared__ uint32_t run[256];
+  __shared__ uint32_t wcnt[kSortWarps][256];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  gbase[tid] = off[(int64_t)tid * num_tiles + blockIdx.x];
+  run[tid] = 0;
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  for (int r = 0; r < kSortRounds; r++) {
+    const int64_t i = base + (int64_t)r * kSortThreads + tid;
+    const bool valid = i < n;
+    const uint64_t key = valid ? kin[i] : 0ull;
+    const uint32_t val = valid ? vin[i] : 0u;
+    const uint32_t digit = valid ? (uint32_t)((key >> shift) & 255u) : 256u;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; w++) wcnt[w][tid] = 0;
+    __syncthreads();
+    const unsigned peers = __match_any_sync(0xffffffffu, digit);
+    const uint32_t lrank = __popc(peers & lt);
+    if (valid && lane == __ffs(peers) - 1) wcnt[warp][digit] = __popc(peers);
+    __syncthreads();
+    {
+      uint32_t b = run[tid];
+#pragma unroll
+      for (int w = 0; w < kSortWarps; w++) {
+        const uint32_t c = wcnt[w][tid];
+        wcnt[w][tid] = b;
+        b += c;
+      }
+      run[tid] = b;
+    }
+    __syncthreads();
+    if (valid) {
+      const uint32_t pos = gbase[digit] + wcnt[warp][digit] + lrank;
+      kout[pos] = key;
+      vout[pos] = val;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Reorder (Section 4.3 step 3): gather the caller-order FP64 data into Morton
+// order, and split positions into FP32 hi/lo pairs (hi = RN(x), lo =
+// RN(x - hi)) for the force kernel's group-relative coordinates.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void split2(double v, float &h, float &l) {
+  h = __double2float_rn(v);
+  l = __double2float_rn(__dsub_rn(v, (double)h));
+}
+
+__global__ void __launch_bounds__(kThreads) k_reorder(
+    const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
+    const double *__restrict__ m, int64_t n, const uint32_t *__restrict__ perm,
+    double *__restrict__ xs, double *__restrict__ ys, double *__restrict__ zs,
+    double *__restrict__ ms, float4 *__restrict__ jhi, float4 *__restrict__ jlo, int *status) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const uint32_t i = perm[k];
+  const double vx = x[i], vy = y[i], vz = z[i], vm = m[i];
+  if (!isfinite(vx) || !isfinite(vy) || !isfinite(vz) || !isfinite(vm))
+    atomicOr(status, kStNonFinite);
+  xs[k] = vx;
+  ys[k] = vy;
+  zs[k] = vz;
+  ms[k] = vm;
+  float hx, hy, hz, lx, ly, lz;
+  split2(vx, hx, lx);
+  split2(vy, hy, ly);
+  split2(vz, hz, lz);
+  jhi[k] = make_float4(hx, hy, hz, __double2float_rn(vm));
+  jlo[k] = make_float4(lx, ly, lz, 0.0f);
+}
+
+// ---------------------------------------------------------------------------
+// Link (Section 4.3 step 4). The level-l cell holding particle i exists iff
+// every ancestor holds more than n_leaf particles (and l <= 21); it is
+// started by i iff i is the first particle of its level-l key prefix. With
+//   d_i = equal leading digits of keys i-1 and i (-1 for i = 0),
+//   c_j = equal leading digits of keys j and j + n_leaf,
+//   E_i = min(21, 1 + max_{j in [i-n_leaf, i]} c_j)  (0 when n <= n_leaf),
+// particle i starts exactly the cells of levels d_i+1 .. E_i, and E_i is the
+// level of its leaf. Emitting cells per particle in (i, level) order gives
+// depth-first pre-order directly; cell boundaries come from a binary search
+// on the sorted keys, as in the paper.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int common_digits(uint64_t a, uint64_t b) {
+  const uint64_t x = a ^ b;
+  if (x == 0) return kLevels;
+  return (__clzll((long long)x) - 1) / 3;
+}
+
+__global__ void __launch_bounds__(kThreads) k_link_dc(const uint64_t *__restrict__ K, int64_t n,
+                                                      int n_leaf, uint8_t *__restrict__ dI,
+                                                      uint8_t *__restrict__ cJ) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t ki = K[i];
+  dI[i] = i == 0 ? (uint8_t)255 : (uint8_t)common_digits(K[i - 1], ki);
+  if (i + n_leaf < n) cJ[i] = (uint8_t)common_digits(ki, K[i + n_leaf]);
+}
+
+__global__ void __launch_bounds__(kThreads) k_link_count(const uint8_t *__restrict__ dI,
+                                                         const uint8_t *__restrict__ cJ,
+                                                         int64_t n, int n_leaf,
+                                                         uint8_t *__restrict__ eI,
+                                                         uint32_t *__restrict__ cnt,
+                                                         unsigned *__restrict__ max_level) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int E = 0;
+  if (i < n) {
+    const int64_t lo = i - n_leaf > 0 ? i - n_leaf : 0;
+    const int64_t hi = i < n - n_leaf - 1 ? i : n - n_leaf - 1;
+    int mx = -1;
+    for (int64_t j = lo; j <= hi; j++) mx = max(mx, (int)cJ[j]);
+    E = mx < 0 ? 0 : min(kLevels, mx + 1);
+    const int d = i == 0 ? -1 : (int)dI[i];
+    eI[i] = (uint8_t)E;
+    cnt[i] = (uint32_t)max(0, E - d);
+  }
+  // deepest leaf level: one atomic per warp
+  const unsigned wm = __reduce_max_sync(0xffffffffu, (unsigned)E);
+  if ((threadIdx.x & 31) == 0 && wm > 0) atomicMax(max_level, wm);
+}
+
+__device__ __forceinline__ int64_t lower_bound_key(const uint64_t *K, int64_t lo, int64_t hi,
+                                                   uint64_t v) {
+  while (lo < hi) {
+    const int64_t mid = lo + ((hi - lo) >> 1);
+    if (K[mid] < v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kThreads) k_link_emit(
+    const uint64_t *__restrict__ K, const uint8_t *__restrict__ dI, const uint8_t *__restrict__ eI,
+    const uint32_t *__restrict__ off, int64_t n, uint32_t *__restrict__ level,
+    uint32_t *__restrict__ first, uint32_t *__restrict__ count, uint32_t *__restrict__ skip,
+    uint32_t *__restrict__ parent, uint32_t *__restrict__ child) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int d = i == 0 ? -1 : (int)dI[i];
+  const int E = eI[i];
+  const uint64_t ki = K[i];
+  for (int l = d + 1; l <= E; l++) {
+    const uint32_t id = off[i] + (uint32_t)(l - d - 1);
+    int64_t end = n;
+    if (l > 0) {
+      const int shift = 3 * (kLevels - l);
+      const uint64_t P = ki >> shift;
+      end = lower_bound_key(K, i + 1, n, (P + 1) << shift);
+    }
+    level[id] = (uint32_t)l;
+    first[id] = (uint32_t)i;
+    count[id] = (uint32_t)(end - i);
+    skip[id] = off[end];
+    uint32_t par = kNone;
+    if (l > 0) {
+      if (l - 1 >= d + 1) {
+        par = id - 1;
+      } else {
+        const int pshift = 3 * (kLevels - l + 1);
+        const uint64_t PP = ki >> pshift;
+        const int64_t s = lower_bound_key(K, 0, i, PP << pshift);
+        const int ds = s == 0 ? -1 : (int)dI[s];
+        par = off[s] + (uint32_t)((l - 1) - ds - 1);
+      }
+      child[(size_t)par * 8 + ((ki >> (3 * (kLevels - l))) & 7u)] = id;
+    }
+    parent[id] = par;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Moments (Section 4.3, bottom-up). One thread per leaf sums its particles
+// in Morton order, then climbs: the last child to finish (arrival counter)
+// sums the parent's children in octant order. M, S = sum m x, COM = S / M
+// (the geometric centre for a massless cell); optional traceless quadrupole
+// about the COM with the parallel-axis shift. Finishing a cell also writes
+// the superparticle data (COM hi/lo, mass, quadrupole as floats) and the
+// walk node (FP32 COM, squared side, first, count, leaf bit).
+// ---------------------------------------------------------------------------
+struct MomArgs {
+  int64_t n_cells;
+  const uint32_t *level, *first, *count, *parent, *child;
+  const double *xs, *ys, *zs, *ms;
+  const uint64_t *keys;
+  const double *root;
+  double *mass, *smom, *com, *quad;
+  unsigned *arrive;
+  float4 *s_hi, *s_lo, *s_q0, *s_q1, *node_f;
+  uint2 *node_i;
+  int quad_on;
+};
+
+__device__ __forceinline__ int n_children(const uint32_t *child, uint32_t c) {
+  int k = 0;
+#pragma unroll
+  for (int o = 0; o < 8; o++) k += __ldg(&child[(size_t)c * 8 + o]) != kNone;
+  return k;
+}
+
+__device__ void finish_cell(const MomArgs &a, uint32_t c, double M, const double S[3], bool leaf) {
+  double g[3];
+  if (M != 0.0) {
+    for (int d = 0; d < 3; d++) g[d] = __ddiv_rn(S[d], M);
+  } else {
+    const int l = (int)a.level[c];
+    const uint64_t prefix = l > 0 ? a.keys[a.first[c]] >> (3 * (kLevels - l)) : 0ull;
+    uint32_t q[3] = {0u, 0u, 0u};
+    for (int k = 0; k < l; k++) {
+      q[0] |= (uint32_t)((prefix >> (3 * k + 2)) & 1u) << k;
+      q[1] |= (uint32_t)((prefix >> (3 * k + 1)) & 1u) << k;
+      q[2] |= (uint32_t)((prefix >> (3 * k)) & 1u) << k;
+    }
+    const double L = a.root[3];
+    const double s = ldexp(L, -l);
+    for (int d = 0; d < 3; d++)
+      g[d] = __dadd_rn(__dsub_rn(a.root[d], __dmul_rn(L, 0.5)), __dmul_rn((double)q[d] + 0.5, s));
+  }
+  a.mass[c] = M;
+  for (int d = 0; d < 3; d++) {
+    a.smom[(size_t)c * 3 + d] = S[d];
+    a.com[(size_t)c * 3 + d] = g[d];
+  }
+  float h[3], lo[3];
+  for (int d = 0; d < 3; d++) split2(g[d], h[d], lo[d]);
+  a.s_hi[c] = make_float4(h[0], h[1], h[2], __double2float_rn(M));
+  a.s_lo[c] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+  const float sd = ldexpf(__double2float_rn(a.root[3]), -(int)a.level[c]);
+  a.node_f[c] = make_float4(h[0], h[1], h[2], __fmul_rn(sd, sd));
+  a.node_i[c] = make_uint2(a.first[c], a.count[c] | (leaf ? 0x80000000u : 0u));
+}
+
+__device__ void leaf_quad(const MomArgs &a, uint32_t c) {
+  const double *g = &a.com[(size_t)c * 3];
+  double Q[6] = {0, 0, 0, 0, 0, 0};
+  const uint32_t f = a.first[c], e = f + a.count[c];
+  for (uint32_t k = f; k < e; k++) {
+    const double d0 = __dsub_rn(a.xs[k], g[0]), d1 = __dsub_rn(a.ys[k], g[1]),
+                 d2 = __dsub_rn(a.zs[k], g[2]);
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
+    const double mk = a.ms[k];
+    Q[0] = __dadd_rn(Q[0], __dmul_rn(mk, __dsub_rn(__dmul_rn(__dmul_rn(3.0, d0), d0), r2)));
+    Q[1] = __dadd_rn(Q[1], __dmul_rn(mk, __dsub_rn(__dmul_rn(__dmul_rn(3.0, d1), d1), r2)));
+    Q[2] = __dadd_rn(Q[2], __dmul_rn(mk, __dsub_rn(__dmul_rn(__dmul_rn(3.0, d2), d2), r2)));
+    Q[3] = __dadd_rn(Q[3], __dmul_rn(mk, __dmul_rn(__dmul_rn(3.0, d0), d1)));
+    Q[4] = __dadd_rn(Q[4], __dmul_rn(mk, __dmul_rn(__dmul_rn(3.0, d0), d2)));
+    Q[5] = __dadd_rn(Q[5], __dmul_rn(mk, __dmul_rn(__dmul_rn(3.0, d1), d2)));
+  }
+  for (int q = 0; q < 6; q++) a.quad[(size_t)c * 6 + q] = Q[q];
+  a.s_q0[c] = make_float4(__double2float_rn(Q[0]), __double2float_rn(Q[1]),
+                          __double2float_rn(Q[2]), __double2float_rn(Q[3]));
+  a.s_q1[c] = make_float4(__double2float_rn(Q[4]), __double2float_rn(Q[5]), 0.0f, 0.0f);
+}
+
+__device__ void internal_quad(const MomArgs &a, uint32_t c) {
+  const double *g = &a.com[(size_t)c * 3];
+  double Q[6] = {0, 0, 0, 0, 0, 0};
+  for (int o = 0; o < 8; o++) {
+    const uint32_t cc = __ldg(&a.child[(size_t)c * 8 + o]);
+    if (cc == kNone) continue;
+    const double D0 = __dsub_rn(__ldcg(&a.com[(size_t)cc * 3 + 0]), g[0]);
+    const double D1 = __dsub_rn(__ldcg(&a.com[(size_t)cc * 3 + 1]), g[1]);
+    const double D2 = __dsub_rn(__ldcg(&a.com[(size_t)cc * 3 + 2]), g[2]);
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(D0, D0), __dmul_rn(D1, D1)), __dmul_rn(D2, D2));
+    const double mc = __ldcg(&a.mass[cc]);
+    double qc[6];
+    for (int q = 0; q < 6; q++) qc[q] = __ldcg(&a.quad[(size_t)cc * 6 + q]);
+    Q[0] = __dadd_rn(Q[0], __dadd_rn(qc[0], __dmul_rn(mc, __dsub_rn(__dmul_rn(__dmul_rn(3.0, D0), D0), r2))));
+    Q[1] = __dadd_rn(Q[1], __dadd_rn(qc[1], __dmul_rn(mc, __dsub_rn(__dmul_rn(__dmul_rn(3.0, D1), D1), r2))));
+    Q[2] = __dadd_rn(Q[2], __dadd_rn(qc[2], __dmul_rn(mc, __dsub_rn(__dmul_rn(__dmul_rn(3.0, D2), D2), r2))));
+    Q[3] = __dadd_rn(Q[3], __dadd_rn(qc[3], __dmul_rn(mc, __dmul_rn(__dmul_rn(3.0, D0), D1))));
+    Q[4] = __dadd_rn(Q[4], __dadd_rn(qc[4], __dmul_rn(mc, __dmul_rn(__dmul_rn(3.0, D0), D2))));
+    Q[5] = __dadd_rn(Q[5], __dadd_rn(qc[5], __dmul_rn(mc, __dmul_rn(__dmul_rn(3.0, D1), D2))));
+  }
+  for (int q = 0; q < 6; q++) a.quad[(size_t)c * 6 + q] = Q[q];
+  a.s_q0[c] = make_float4(__double2float_rn(Q[0]), __double2float_rn(Q[1]),
+                          __double2float_rn(Q[2]), __double2float_rn(Q[3]));
+  a.s_q1[c] = make_float4(__double2float_rn(Q[4]), __double2float_rn(Q[5]), 0.0f, 0.0f);
+}
+
+__global__ void __launch_bounds__(kThreads) k_moments(MomArgs a) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.n_cells) return;
+  uint32_t c = (uint32_t)t;
+  if (n_children(a.child, c) != 0) return;
+  {
+    double M = 0.0, S[3] = {0.0, 0.0, 0.0};
+    const uint32_t f = a.first[c], e = f + a.count[c];
+    for (uint32_t k = f; k < e; k++) {
+      const double mk = a.ms[k];
+      M = __dadd_rn(M, mk);
+      S[0] = __dadd_rn(S[0], __dmul_rn(mk, a.xs[k]));
+      S[1] = __dadd_rn(S[1], __dmul_rn(mk, a.ys[k]));
+      S[2] = __dadd_rn(S[2], __dmul_rn(mk, a.zs[k]));
+    }
+    finish_cell(a, c, M, S, true);
+    if (a.quad_on) leaf_quad(a, c);
+  }
+  for (;;) {
+    const uint32_t p = a.parent[c];
+    if (p == kNone) break;
+    __threadfence();
+    const unsigned old = atomicAdd(&a.arrive[p], 1u);
+    if ((int)old != n_children(a.child, p) - 1) break;
+    __threadfence();
+    double M = 0.0, S[3] = {0.0, 0.0, 0.0};
+    for (int o = 0; o < 8; o++) {
+      const uint32_t cc = __ldg(&a.child[(size_t)p * 8 + o]);
+      if (cc == kNone) continue;
+      M = __dadd_rn(M, __ldcg(&a.mass[cc]));
+      for (int d = 0; d < 3; d++) S[d] = __dadd_rn(S[d], __ldcg(&a.smom[(size_t)cc * 3 + d]));
+    }
+    finish_cell(a, p, M, S, false);
+    if (a.quad_on) internal_quad(a, p);
+    c = p;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// i-groups: the maximal cells holding at most n_grp particles, in
+// pre-order; a larger leaf is cut into chunks of n_grp.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_group_count(int64_t n_cells,
+                                                          const uint32_t *__restrict__ count,
+                                                          const uint32_t *__restrict__ parent,
+                                                          const uint32_t *__restrict__ child,
+                                                          uint32_t n_grp,
+                                                          uint32_t *__restrict__ gcnt) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_cells) return;
+  const uint32_t cnt = count[c];
+  uint32_t g = 0;
+  if (cnt <= n_grp) {
+    const uint32_t p = parent[c];
+    g = (p == kNone || count[p] > n_grp) ? 1u : 0u;
+  } else if (n_children(child, (uint32_t)c) == 0) {
+    g = (cnt + n_grp - 1) / n_grp;
+  }
+  gcnt[c] = g;
+}
+
+__global__ void __launch_bounds__(kThreads) k_group_fill(
+    int64_t n_cells, const uint32_t *__restrict__ first, const uint32_t *__restrict__ count,
+    const uint32_t *__restrict__ gcnt, const uint32_t *__restrict__ goff, uint32_t n_grp,
+    uint32_t *__restrict__ g_first, uint32_t *__restrict__ g_count,
+    uint32_t *__restrict__ u_cnt) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_cells) return;
+  const uint32_t k_n = gcnt[c];
+  for (uint32_t k = 0; k < k_n; k++) {
+    const uint32_t g = goff[c] + k;
+    const uint32_t f = first[c] + k * n_grp;
+    const uint32_t rem = count[c] - k * n_grp;
+    const uint32_t cn = rem < n_grp ? rem : n_grp;
+    g_first[g] = f;
+    g_count[g] = cn;
+    u_cnt[g] = (cn + 31u) / 32u;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_unit_fill(int64_t n_groups,
+                                                        const uint32_t *__restrict__ u_off,
+                                                        uint32_t *__restrict__ u_group) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n_groups) return;
+  for (uint32_t u = u_off[g]; u < u_off[g + 1]; u++) u_group[u] = (uint32_t)g;
+}
+
+// Tight FP64 box per group (one warp per group; min/max are exact), its
+// FP32 copy for the opening criterion, and the box centre as hi/lo floats
+// (the reference point of the force kernel's relative coordinates).
+__global__ void __launch_bounds__(kThreads) k_group_box(
+    int64_t n_groups, const uint32_t *__restrict__ g_first, const uint32_t *__restrict__ g_count,
+    const double *__restrict__ xs, const double *__restrict__ ys, const double *__restrict__ zs,
+    double *__restrict__ box, float *__restrict__ boxf, float4 *__restrict__ chi,
+    float4 *__restrict__ clo) {
+  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (g >= n_groups) return;
+  const uint32_t f = g_first[g], e = f + g_count[g];
+  double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+  for (uint32_t k = f + lane; k < e; k += 32) {
+    const double v[3] = {xs[k], ys[k], zs[k]};
+    for (int d = 0; d < 3; d++) {
+      lo[d] = fmin(lo[d], v[d]);
+      hi[d] = fmax(hi[d], v[d]);
+    }
+  }
+  for (int d = 0; d < 3; d++) {
+    lo[d] = warp_min(lo[d]);
+    hi[d] = warp_max(hi[d]);
+  }
+  if (lane != 0) return;
+  float ch[3], cl[3];
+  for (int d = 0; d < 3; d++) {
+    box[g * 6 + d] = lo[d];
+    box[g * 6 + 3 + d] = hi[d];
+    boxf[g * 6 + d] = __double2float_rn(lo[d]);
+    boxf[g * 6 + 3 + d] = __double2float_rn(hi[d]);
+    split2(__dmul_rn(__dadd_rn(lo[d], hi[d]), 0.5), ch[d], cl[d]);
+  }
+  chi[g] = make_float4(ch[0], ch[1], ch[2], 0.0f);
+  clo[g] = make_float4(cl[0], cl[1], cl[2], 0.0f);
+}
+
+inline int ck() { return cudaGetLastError() == cudaSuccess ? AFD_OK : AFD_ERR_CUDA; }
+
+}  // namespace
+
+#define AFD_TRY(x)            \
+  do {                        \
+    int _s = (x);             \
+    if (_s != AFD_OK) return _s; \
+  } while (0)
+
+int launch_root(afd_ctx *c, const double *x, const double *y, const double *z, const double *m,
+                int64_t n) {
+  AFD_TRY(reserve(c->root, sizeof(double) * 4));
+  AFD_TRY(reserve(c->red_part, sizeof(double) * 6 * kRootBlocks));
+  if (n == 0) {
+    const double r[4] = {0.0, 0.0, 0.0, 1.0};
+    return cudaMemcpyAsync(c->root.p, r, sizeof(r), cudaMemcpyHostToDevice, c->stream) == cudaSuccess
+               ? AFD_OK
+               : AFD_ERR_CUDA;
+  }
+  int64_t nb = (n + kThreads * 4 - 1) / (kThreads * 4);
+  if (nb > kRootBlocks) nb = kRootBlocks;
+  k_root<<<(unsigned)nb, kThreads, 0, c->stream>>>(x, y, z, m, n, ptr<double>(c->red_part),
+                                                  ptr<unsigned>(c->red_count),
+                                                  ptr<double>(c->root), ptr<int>(c->status));
+  c->launches++;
+  return ck();
+}
+
+int launch_keys(afd_ctx *c, const double *x, const double *y, const double *z, int64_t n) {
+  AFD_TRY(reserve(c->keys, sizeof(uint64_t) * n));
+  AFD_TRY(reserve(c->perm, sizeof(uint32_t) * n));
+  if (n == 0) return AFD_OK;
+  k_keys<<<blocks_for(n), kThreads, 0, c->stream>>>(x, y, z, n, ptr<double>(c->root),
+                                                    ptr<uint64_t>(c->keys), ptr<uint32_t>(c->perm));
+  c->launches++;
+  return ck();
+}
+
+int launch_sort(afd_ctx *c, int64_t n) {
+  if (n <= 1) return AFD_OK;
+  const int num_tiles = (int)((n + kSortTile - 1) / kSortTile);
+  const int64_t nc = (int64_t)256 * num_tiles;
+  AFD_TRY(reserve(c->keys2, sizeof(uint64_t) * n));
+  AFD_TRY(reserve(c->perm2, sizeof(uint32_t) * n));
+  AFD_TRY(reserve(c->sort_cnt, sizeof(uint32_t) * nc));
+  AFD_TRY(reserve(c->sort_off, sizeof(uint32_t) * (nc + 1)));
+  uint64_t *ka = ptr<uint64_t>(c->keys), *kb = ptr<uint64_t>(c->keys2);
+  uint32_t *va = ptr<uint32_t>(c->perm), *vb = ptr<uint32_t>(c->perm2);
+  for (int pass = 0; pass < 8; pass++) {
+    const int shift = 8 * pass;
+    k_sort_hist<<<num_tiles, kSortThreads, 0, c->stream>>>(ka, n, shift,
+                                                            ptr<uint32_t>(c->sort_cnt), num_tiles);
+    c->launches++;
+    AFD_TRY(ck());
+    AFD_TRY(scan_u32(c, ptr<uint32_t>(c->sort_cnt), ptr<uint32_t>(c->sort_off), nc));
+    k_sort_scatter<<<num_tiles, kSortThreads, 0, c->stream>>>(
+        ka, va, kb, vb, n, shift, ptr<uint32_t>(c->sort_off), num_tiles);
+    c->launches++;
+    AFD_TRY(ck());
+    uint64_t *tk = ka; ka = kb; kb = tk;
+    uint32_t *tv = va; va = vb; vb = tv;
+  }
+  // eight passes: the result is back in keys / perm
+  return AFD_OK;
+}
+
+int launch_reorder(afd_ctx *c, const double *x, const double *y, const double *z,
+                   const double *m, int64_t n) {
+  for (afd::DevBuf *b : {&c->xs, &c->ys, &c->zs, &c->ms}) AFD_TRY(reserve(*b, sizeof(double) * n));
+  AFD_TRY(reserve(c->jhi, sizeof(float4) * n));
+  AFD_TRY(reserve(c->jlo, sizeof(float4) * n));
+  if (n == 0) return AFD_OK;
+  k_reorder<<<blocks_for(n), kThreads, 0, c->stream>>>(
+      x, y, z, m, n, ptr<uint32_t>(c->perm), ptr<double>(c->xs), ptr<double>(c->ys),
+      ptr<double>(c->zs), ptr<double>(c->ms), ptr<float4>(c->jhi), ptr<float4>(c->jlo),
+      ptr<int>(c->status));
+  c->launches++;
+  return ck();
+}
+
+int launch_link(afd_ctx *c, int64_t n) {
+  AFD_TRY(reserve(c->lk_d, n));
+  AFD_TRY(reserve(c->lk_c, n));
+  AFD_TRY(reserve(c->lk_e, n));
+  AFD_TRY(reserve(c->lk_cnt, sizeof(uint32_t) * n));
+  AFD_TRY(reserve(c->lk_off, sizeof(uint32_t) * (n + 1)));
+  AFD_TRY(reserve(c->u64acc, sizeof(uint64_t) * 4));
+  if (n == 0) {
+    c->n_cells = 0;
+    c->max_level = 0;
+    return AFD_OK;
+  }
+  const int n_leaf = c->cfg.n_leaf;
+  unsigned *maxl = ptr<unsigned>(c->u64acc);
+  if (cudaMemsetAsync(maxl, 0, sizeof(unsigned), c->stream) != cudaSuccess) return AFD_ERR_CUDA;
+  k_link_dc<<<blocks_for(n), kThreads, 0, c->stream>>>(ptr<uint64_t>(c->keys), n, n_leaf,
+                                                       ptr<uint8_t>(c->lk_d), ptr<uint8_t>(c->lk_c));
+  c->launches++;
+  k_link_count<<<blocks_for(n), kThreads, 0, c->stream>>>(
+      ptr<uint8_t>(c->lk_d), ptr<uint8_t>(c->lk_c), n, n_leaf, ptr<uint8_t>(c->lk_e),
+      ptr<uint32_t>(c->lk_cnt), maxl);
+  c->launches++;
+  AFD_TRY(ck());
+  AFD_TRY(scan_u32(c, ptr<uint32_t>(c->lk_cnt), ptr<uint32_t>(c->lk_off), n));
+  uint32_t *pin = static_cast<uint32_t *>(c->pinned);
+  cudaMemcpyAsync(pin, ptr<uint32_t>(c->lk_off) + n, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                  c->stream);
+  cudaMemcpyAsync(pin + 1, maxl, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return AFD_ERR_CUDA;
+  const int64_t nc = pin[0];
+  c->n_cells = nc;
+  c->max_level = (int)pin[1];
+  const size_t u = sizeof(uint32_t) * (size_t)nc;
+  for (afd::DevBuf *b : {&c->c_level, &c->c_first, &c->c_count, &c->c_skip, &c->c_parent,
+                         &c->c_arrive})
+    AFD_TRY(reserve(*b, u));
+  AFD_TRY(reserve(c->c_child, u * 8));
+  if (cudaMemsetAsync(c->c_child.p, 0xff, u * 8, c->stream) != cudaSuccess) return AFD_ERR_CUDA;
+  k_link_emit<<<blocks_for(n), kThreads, 0, c->stream>>>(
+      ptr<uint64_t>(c->keys), ptr<uint8_t>(c->lk_d), ptr<uint8_t>(c->lk_e),
+      ptr<uint32_t>(c->lk_off), n, ptr<uint32_t>(c->c_level), ptr<uint32_t>(c->c_first),
+      ptr<uint32_t>(c->c_count), ptr<uint32_t>(c->c_skip), ptr<uint32_t>(c->c_parent),
+      ptr<uint32_t>(c->c_child));
+  c->launches++;
+  return ck();
+}
+
+int launch_moments(afd_ctx *c) {
+  const int64_t nc = c->n_cells;
+  AFD_TRY(reserve(c->c_mass, sizeof(double) * nc));
+  AFD_TRY(reserve(c->c_smom, sizeof(double) * 3 * nc));
+  AFD_TRY(reserve(c->c_com, sizeof(double) * 3 * nc));
+  AFD_TRY(reserve(c->c_quad, sizeof(double) * 6 * nc));
+  for (afd::DevBuf *b : {&c->s_hi, &c->s_lo, &c->s_q0, &c->s_q1, &c->node_f})
+    AFD_TRY(reserve(*b, sizeof(float4) * nc));
+  AFD_TRY(reserve(c->node_i, sizeof(uint2) * nc));
+  if (nc == 0) return AFD_OK;
+  if (cudaMemsetAsync(c->c_arrive.p, 0, sizeof(unsigned) * nc, c->stream) != cudaSuccess)
+    return AFD_ERR_CUDA;
+  if (!c->cfg.multipole) {
+    if (cudaMemsetAsync(c->c_quad.p, 0, sizeof(double) * 6 * nc, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->s_q0.p, 0, sizeof(float4) * nc, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->s_q1.p, 0, sizeof(float4) * nc, c->stream) != cudaSuccess)
+      return AFD_ERR_CUDA;
+  }
+  MomArgs a;
+  a.n_cells = nc;
+  a.level = ptr<uint32_t>(c->c_level);
+  a.first = ptr<uint32_t>(c->c_first);
+  a.count = ptr<uint32_t>(c->c_count);
+  a.parent = ptr<uint32_t>(c->c_parent);
+  a.child = ptr<uint32_t>(c->c_child);
+  a.xs = ptr<double>(c->xs);
+  a.ys = ptr<double>(c->ys);
+  a.zs = ptr<double>(c->zs);
+  a.ms = ptr<double>(c->ms);
+  a.keys = ptr<uint64_t>(c->keys);
+  a.root = ptr<double>(c->root);
+  a.mass = ptr<double>(c->c_mass);
+  a.smom = ptr<double>(c->c_smom);
+  a.com = ptr<double>(c->c_com);
+  a.quad = ptr<double>(c->c_quad);
+  a.arrive = ptr<unsigned>(c->c_arrive);
+  a.s_hi = ptr<float4>(c->s_hi);
+  a.s_lo = ptr<float4>(c->s_lo);
+  a.s_q0 = ptr<float4>(c->s_q0);
+  a.s_q1 = ptr<float4>(c->s_q1);
+  a.node_f = ptr<float4>(c->node_f);
+  a.node_i = ptr<uint2>(c->node_i);
+  a.quad_on = c->cfg.multipole;
+  k_moments<<<blocks_for(nc), kThreads, 0, c->stream>>>(a);
+  c->launches++;
+  return ck();
+}
+
+int launch_groups(afd_ctx *c) {
+  const int64_t nc = c->n_cells;
+  AFD_TRY(reserve(c->g_cnt, sizeof(uint32_t) * nc));
+  AFD_TRY(reserve(c->g_off, sizeof(uint32_t) * (nc + 1)));
+  if (nc == 0) {
+    c->n_groups = 0;
+    c->n_units = 0;
+    return AFD_OK;
+  }
+  const uint32_t n_grp = (uint32_t)c->cfg.n_grp;
+  k_group_count<<<blocks_for(nc), kThreads, 0, c->stream>>>(
+      nc, ptr<uint32_t>(c->c_count), ptr<uint32_t>(c->c_parent), ptr<uint32_t>(c->c_child), n_grp,
+      ptr<uint32_t>(c->g_cnt));
+  c->launches++;
+  AFD_TRY(ck());
+  AFD_TRY(scan_u32(c, ptr<uint32_t>(c->g_cnt), ptr<uint32_t>(c->g_off), nc));
+  uint32_t *pin = static_cast<uint32_t *>(c->pinned);
+  cudaMemcpyAsync(pin, ptr<uint32_t>(c->g_off) + nc, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                  c->stream);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return AFD_ERR_CUDA;
+  const int64_t ng = pin[0];
+  c->n_groups = ng;
+  for (afd::DevBuf *b : {&c->g_first, &c->g_count, &c->g_self, &c->u_cnt})
+    AFD_TRY(reserve(*b, sizeof(uint32_t) * ng));
+  AFD_TRY(reserve(c->u_off, sizeof(uint32_t) * (ng + 1)));
+  AFD_TRY(reserve(c->g_box, sizeof(double) * 6 * ng));
+  AFD_TRY(reserve(c->g_boxf, sizeof(float) * 6 * ng));
+  AFD_TRY(reserve(c->g_chi, sizeof(float4) * ng));
+  AFD_TRY(reserve(c->g_clo, sizeof(float4) * ng));
+  k_group_fill<<<blocks_for(nc), kThreads, 0, c->stream>>>(
+      nc, ptr<uint32_t>(c->c_first), ptr<uint32_t>(c->c_count), ptr<uint32_t>(c->g_cnt),
+      ptr<uint32_t>(c->g_off), n_grp, ptr<uint32_t>(c->g_first), ptr<uint32_t>(c->g_count),
+      ptr<uint32_t>(c->u_cnt));
+  c->launches++;
+  AFD_TRY(ck());
+  AFD_TRY(scan_u32(c, ptr<uint32_t>(c->u_cnt), ptr<uint32_t>(c->u_off), ng));
+  cudaMemcpyAsync(pin, ptr<uint32_t>(c->u_off) + ng, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                  c->stream);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return AFD_ERR_CUDA;
+  c->n_units = pin[0];
+  AFD_TRY(reserve(c->u_group, sizeof(uint32_t) * c->n_units));
+  k_unit_fill<<<blocks_for(ng), kThreads, 0, c->stream>>>(ng, ptr<uint32_t>(c->u_off),
+                                                          ptr<uint32_t>(c->u_group));
+  c->launches++;
+  return ck();
+}
+
+int launch_group_boxes(afd_ctx *c) {
+  const int64_t ng = c->n_groups;
+  if (ng == 0) return AFD_OK;
+  k_group_box<<<blocks_for(ng * 32), kThreads, 0, c->stream>>>(
+      ng, ptr<uint32_t>(c->g_first), ptr<uint32_t>(c->g_count), ptr<double>(c->xs),
+      ptr<double>(c->ys), ptr<double>(c->zs), ptr<double>(c->g_box), ptr<float>(c->g_boxf),
+      ptr<float4>(c->g_chi), ptr<float4>(c->g_clo));
+  c->launches++;
+  return ck();
+}
+
+}  // namespace afd

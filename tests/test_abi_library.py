@@ -1,0 +1,79 @@
+"""The C-ABI library without a GPU: it builds, loads, exports every entry
+point include/afdps.h declares, and validates arguments on the host. No
+compute call is made here."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "afdps.h")
+PKG = os.path.join(ROOT, "paper_1907_02290_gb300")
+
+
+def declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char \*)\s*(afd_\w+)\s*\(", text, re.M)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1907_02290_gb300 import build
+
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared()
+    for required in ("afd_create", "afd_destroy", "afd_tree_build", "afd_make_interaction_lists",
+                     "afd_reuse_lists", "afd_calc_force", "afd_calc_force_all",
+                     "afd_error_string", "afd_export"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT (afd_\w+)$", out, re.M))
+    missing = [n for n in declared() if n not in exported]
+    assert not missing, missing
+    lib = ctypes.CDLL(libpath)
+    for n in declared():
+        assert getattr(lib, n)
+
+
+def test_host_side_validation_without_gpu(libpath):
+    import paper_1907_02290_gb300 as afd
+
+    L = afd.lib()
+    assert afd.afd_error_string(0) == "ok"
+    assert "saved" in afd.afd_error_string(-4)
+    h = ctypes.c_void_p()
+    for bad in (afd.Config(n_grp=0), afd.Config(n_grp=2048), afd.Config(eps=-1.0),
+                afd.Config(theta=float("nan")), afd.Config(n_leaf=0), afd.Config(multipole=2)):
+        assert L.afd_create(ctypes.byref(h), ctypes.byref(bad.c()), 0, None) == -1
+    assert L.afd_create(None, None, 0, None) == -1
+    assert L.afd_calc_force(None, None) == -1
+    assert L.afd_stats(None, None) == -1
+
+
+def test_product_path_never_touches_the_oracle():
+    """The package and its sources neither import nor link the oracle."""
+    for dirpath, _, files in os.walk(PKG):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "afdps_oracle" not in text and "afo_" not in text, f
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    import paper_1907_02290_gb300 as afd
+
+    monkeypatch.setattr(afd, "_lib", None)
+    monkeypatch.setattr(afd._build, "LIB", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        afd.lib()

@@ -1,0 +1,297 @@
+"""GPU parity: the sm_103a library (through its C ABI) against the FP64 CPU
+oracle on the same seeded inputs.
+
+Bit-exact: root cell, Morton keys, permutation, tree topology, monopole
+moments, groups, group boxes and the theta-criterion lists (both sides take
+every decision in the same IEEE precision with the same operation order).
+Floating point: the FP32 force kernel against the FP64 oracle force on the
+same lists, rms relative acceleration error <= 1e-6 (the bound the method's
+accuracy target states), potential likewise.
+"""
+import numpy as np
+import pytest
+
+import ics
+
+pytestmark = pytest.mark.gpu
+
+NONE = 0xFFFFFFFF
+FORCE_RMS_TOL = 1e-6
+POT_RMS_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def env(orc):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1907_02290_gb300 as afd
+
+    return torch, afd, orc
+
+
+def run_gpu(env, p, *, n_leaf=16, n_grp=64, theta=0.5, eps=1.0 / 256, quad=False,
+            mode=None):
+    torch, afd, _ = env
+    cfg = afd.Config(eps=eps, theta=theta, n_leaf=n_leaf, n_grp=n_grp, multipole=int(quad))
+    g = afd.Gravity(cfg, 0, torch.cuda.current_stream())
+    dev = torch.device("cuda:0")
+    x, y, z, m = (torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+                  for a in (p.x, p.y, p.z, p.m))
+    acc = torch.full((p.n, 4), float("nan"), dtype=torch.float32, device=dev)
+    g.force_all(x, y, z, m, acc, afd.AFD_MAKE_LIST_FOR_REUSE if mode is None else mode)
+    torch.cuda.synchronize()
+    return g, acc.cpu().numpy().astype(np.float64), (x, y, z, m, acc)
+
+
+def rms_rel_acc(a, ref):
+    ax, ay, az = ref[:3]
+    num = (a[:, 0] - ax) ** 2 + (a[:, 1] - ay) ** 2 + (a[:, 2] - az) ** 2
+    return float(np.sqrt(np.mean(num / (ax ** 2 + ay ** 2 + az ** 2))))
+
+
+def rms_rel_pot(a, ref):
+    return float(np.sqrt(np.mean((a[:, 3] - ref[3]) ** 2 / ref[3] ** 2)))
+
+
+def u32(a):
+    return np.where(a < 0, NONE, a).astype(np.uint32)
+
+
+def check_structure(g, t, quad=False):
+    """Everything the method decides, bit for bit."""
+    assert np.array_equal(g.export("root"), t.root())
+    keys, perm = t.order()
+    assert np.array_equal(g.export("keys"), keys)
+    assert np.array_equal(g.export("perm"), perm.astype(np.uint32))
+    c = t.cells()
+    assert np.array_equal(g.export("cell_level"), c.level.astype(np.uint32))
+    assert np.array_equal(g.export("cell_first"), c.first.astype(np.uint32))
+    assert np.array_equal(g.export("cell_count"), c.count.astype(np.uint32))
+    assert np.array_equal(g.export("cell_skip"), c.skip.astype(np.uint32))
+    assert np.array_equal(g.export("cell_parent"), u32(c.parent))
+    assert np.array_equal(g.export("cell_child").reshape(-1, 8), u32(c.child))
+    M, com, Q = t.moments()
+    assert np.array_equal(g.export("cell_mass"), M)
+    assert np.array_equal(g.export("cell_com").reshape(-1, 3), com)
+    if quad:
+        gq = g.export("cell_quad").reshape(-1, 6)
+        scale = np.abs(Q).max(axis=1, keepdims=True) + 1e-300
+        assert np.max(np.abs(gq - Q) / scale) < 1e-12
+    gr = t.groups()
+    assert np.array_equal(g.export("group_first"), gr["first"].astype(np.uint32))
+    assert np.array_equal(g.export("group_count"), gr["count"].astype(np.uint32))
+    assert np.array_equal(g.export("group_box").reshape(-1, 6), gr["box"])
+    assert np.array_equal(g.export("group_self"), gr["self_in"].astype(np.uint32))
+    eo, e, so, s = t.lists()
+    assert np.array_equal(g.export("epj_off"), eo.astype(np.uint64))
+    assert np.array_equal(g.export("spj_off"), so.astype(np.uint64))
+    assert np.array_equal(g.export("epj_idx"), e.astype(np.uint32))
+    assert np.array_equal(g.export("spj_idx"), s.astype(np.uint32))
+    st = g.stats()
+    assert st["n_cells"] == len(c.level) and st["n_groups"] == len(gr["first"])
+    assert st["interactions"] == t.interactions()
+
+
+CASES = {
+    # name: (particles, kwargs)
+    "plummer_16k_ragged": (lambda: ics.plummer(16384 + 123, 1),
+                           dict(n_grp=64, theta=0.5, eps=1.0 / 256)),
+    "uniform_20k_grp256": (lambda: ics.uniform_sphere(20000, 5),
+                           dict(n_grp=256, theta=0.7, eps=1.0 / 512)),
+    "plummer_5k_leaf4_theta03": (lambda: ics.plummer(5000, 9),
+                                 dict(n_leaf=4, n_grp=16, theta=0.3, eps=1.0 / 128)),
+    "galaxy_40k_quad": (lambda: ics.galaxy(40000, 3),
+                        dict(n_grp=512, theta=0.4, eps=1.0 / 2048, quad=True)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_structure_and_force_parity(env, name):
+    _, _, orc = env
+    make, kw = CASES[name]
+    p = make()
+    g, a, _ = run_gpu(env, p, **kw)
+    t = orc.Tree(p.x, p.y, p.z, p.m, **kw)
+    check_structure(g, t, quad=kw.get("quad", False))
+    ref = t.force()
+    assert np.all(np.isfinite(a))
+    assert rms_rel_acc(a, ref) <= FORCE_RMS_TOL
+    assert rms_rel_pot(a, ref) <= POT_RMS_TOL
+    g.close()
+
+
+def test_clustered_and_coincident(env):
+    """Clumps, exact duplicates and a max-depth leaf cut into chunks."""
+    _, _, orc = env
+    a = ics.plummer(3000, 4)
+    b = ics.plummer(2000, 5)
+    n_dup = 700
+    x = np.concatenate([a.x, 0.01 * b.x + 3.0, np.full(n_dup, -2.0)])
+    y = np.concatenate([a.y, 0.01 * b.y, np.full(n_dup, 1.0)])
+    z = np.concatenate([a.z, 0.01 * b.z, np.full(n_dup, 0.5)])
+    m = np.full(x.shape[0], 1.0 / x.shape[0])
+    p = ics.Particles(x, y, z, x * 0, x * 0, x * 0, m)
+    kw = dict(n_grp=64, theta=0.6, eps=1.0 / 512)
+    g, acc, _ = run_gpu(env, p, **kw)
+    t = orc.Tree(x, y, z, m, **kw)
+    check_structure(g, t)
+    assert g.stats()["max_level"] == 21
+    ref = t.force()
+    assert rms_rel_acc(acc[:5000], [r[:5000] for r in ref]) <= FORCE_RMS_TOL
+    # duplicates: zero acceleration from each other, potential of the clump exact-ish
+    g.close()
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 16, 17, 33])
+def test_tiny_sizes(env, n):
+    _, _, orc = env
+    p = ics.plummer(max(n, 1), 12)
+    if n == 0:
+        p = ics.Particles(*(np.zeros(0) for _ in range(7)))
+    kw = dict(n_grp=8, theta=0.5, eps=0.05)
+    g, acc, _ = run_gpu(env, p, **kw)
+    t = orc.Tree(p.x, p.y, p.z, p.m, **kw)
+    if n == 0:
+        assert g.stats()["n_cells"] == 0
+        g.close()
+        return
+    check_structure(g, t)
+    ref = t.force()
+    if n == 1:
+        assert np.all(acc == 0)
+    else:
+        assert rms_rel_acc(acc, ref) <= FORCE_RMS_TOL
+    g.close()
+
+
+def test_zero_softening(env):
+    """eps = 0 takes the guarded kernel: coincident pairs contribute nothing."""
+    _, _, orc = env
+    p = ics.plummer(6000, 21)
+    x = p.x.copy()
+    x[:10] = x[10]  # ten coincident with particle 10
+    y, z = p.y.copy(), p.z.copy()
+    y[:10] = y[10]
+    z[:10] = z[10]
+    q = ics.Particles(x, y, z, p.vx, p.vy, p.vz, p.m)
+    kw = dict(n_grp=64, theta=0.5, eps=0.0)
+    g, acc, _ = run_gpu(env, q, **kw)
+    t = orc.Tree(x, y, z, p.m, **kw)
+    check_structure(g, t)
+    ref = t.force()
+    assert np.all(np.isfinite(acc))
+    assert rms_rel_acc(acc[20:], [r[20:] for r in ref]) <= 2e-6
+    g.close()
+
+
+def test_reuse_step_parity(env):
+    """MAKE_LIST_FOR_REUSE, drift, REUSE_LIST: same lists, new moments/forces."""
+    torch, afd, orc = env
+    p = ics.plummer(12000, 31)
+    kw = dict(n_grp=64, theta=0.5, eps=1.0 / 256)
+    g, _, (x, y, z, m, acc) = run_gpu(env, p, **kw)
+    t = orc.Tree(p.x, p.y, p.z, p.m, **kw)
+    lists0 = [g.export(k) for k in ("epj_off", "epj_idx", "spj_off", "spj_idx")]
+    dt = 0.01
+    x2, y2, z2 = p.x + dt * p.vx, p.y + dt * p.vy, p.z + dt * p.vz
+    x.copy_(torch.tensor(x2, device=x.device))
+    y.copy_(torch.tensor(y2, device=x.device))
+    z.copy_(torch.tensor(z2, device=x.device))
+    afd.afd_calc_force_all(g.ctx, x, y, z, m, acc, afd.AFD_REUSE_LIST)
+    torch.cuda.synchronize()
+    t.update(x2, y2, z2, p.m)
+    for a, b in zip(lists0, [g.export(k) for k in ("epj_off", "epj_idx", "spj_off", "spj_idx")]):
+        assert np.array_equal(a, b)
+    M, com, _ = t.moments()
+    assert np.array_equal(g.export("cell_mass"), M)
+    assert np.array_equal(g.export("cell_com").reshape(-1, 3), com)
+    ref = t.force()
+    a = acc.cpu().numpy().astype(np.float64)
+    assert rms_rel_acc(a, ref) <= FORCE_RMS_TOL
+    g.close()
+
+
+def test_host_entry_point_matches_device(env):
+    torch, afd, _ = env
+    p = ics.plummer(9000, 41)
+    kw = dict(n_grp=64, theta=0.5, eps=1.0 / 256)
+    g, a_dev, _ = run_gpu(env, p, **kw)
+    out = np.zeros((p.n, 4), dtype=np.float32)
+    afd.afd_calc_force_all_host(g.ctx, p.x, p.y, p.z, p.m, out, afd.AFD_MAKE_LIST_FOR_REUSE)
+    assert np.array_equal(out.astype(np.float64), a_dev)
+    g.close()
+
+
+def test_leapfrog_against_oracle(env):
+    torch, afd, orc = env
+    p = ics.plummer(4096, 51)
+    kw = dict(n_grp=64, theta=0.4, eps=1.0 / 64)
+    dt, steps, reuse = 1.0 / 256, 8, 4
+    g, _, (x, y, z, m, acc) = run_gpu(env, p, **kw)
+    dev = x.device
+    vx, vy, vz = (torch.tensor(v, device=dev) for v in p.vel())
+    afd.afd_leapfrog(g.ctx, x, y, z, vx, vy, vz, m, acc, dt, steps, reuse)
+    ref = orc.leapfrog(p.x, p.y, p.z, p.vx, p.vy, p.vz, p.m, dt=dt, n_steps=steps,
+                       n_reuse=reuse, **kw)
+    for got, want in zip((x, y, z, vx, vy, vz), ref[:6]):
+        assert np.max(np.abs(got.cpu().numpy() - want)) < 1e-7
+    K, W = afd.afd_energy(g.ctx, vx, vy, vz, m, acc)
+    assert K == pytest.approx(0.5 * np.sum(p.m * (ref[3] ** 2 + ref[4] ** 2 + ref[5] ** 2)), rel=1e-6)
+    assert W == pytest.approx(0.5 * np.sum(p.m * ref[9]), rel=1e-5)
+    g.close()
+
+
+def test_errors_are_reported(env):
+    torch, afd, _ = env
+    dev = torch.device("cuda:0")
+    cfg = afd.Config(eps=0.01, theta=0.5, n_grp=32)
+    g = afd.Gravity(cfg, 0, torch.cuda.current_stream())
+    acc = torch.zeros(100, 4, dtype=torch.float32, device=dev)
+    x = torch.rand(100, dtype=torch.float64, device=dev)
+    m = torch.full((100,), 0.01, dtype=torch.float64, device=dev)
+    with pytest.raises(afd.AfdError) as e:
+        afd.afd_calc_force_all(g.ctx, x, x, x, m, acc, afd.AFD_REUSE_LIST)
+    assert e.value.status == -4  # no saved lists
+    with pytest.raises(afd.AfdError) as e:
+        afd.afd_calc_force(g.ctx, acc)
+    assert e.value.status == -8  # no tree
+    bad = x.clone()
+    bad[17] = float("nan")
+    with pytest.raises(afd.AfdError) as e:
+        afd.afd_calc_force_all(g.ctx, bad, x, x, m, acc, afd.AFD_MAKE_LIST)
+    assert e.value.status == -3
+    afd.afd_calc_force_all(g.ctx, x, x, x, m, acc, afd.AFD_MAKE_LIST)  # context still usable
+    with pytest.raises(afd.AfdError) as e:
+        afd.afd_calc_force_all(g.ctx, x, x, x, m, acc, afd.AFD_REUSE_LIST)
+    assert e.value.status == -4  # MAKE_LIST does not keep lists
+    afd.afd_calc_force_all(g.ctx, x, x, x, m, acc, afd.AFD_MAKE_LIST_FOR_REUSE)
+    with pytest.raises(afd.AfdError) as e:
+        afd.afd_calc_force_all(g.ctx, x[:50], x[:50], x[:50], m[:50], acc, afd.AFD_REUSE_LIST)
+    assert e.value.status == -5
+    with pytest.raises(afd.AfdError):
+        afd.Gravity(afd.Config(n_grp=0), 0)
+    g.close()
+
+
+def test_full_size_plummer_1m(env):
+    """The 2^20-particle Plummer workload in the bench's launch configuration:
+    keys, topology, groups and lists bit-exact; forces of sampled groups."""
+    _, _, orc = env
+    wl = ics.WORKLOADS["plummer_1m"]
+    p = ics.plummer(wl["n"], wl["seed"])
+    kw = dict(n_grp=wl["n_grp"], theta=wl["theta"], eps=wl["eps"])
+    g, a, _ = run_gpu(env, p, **kw)
+    t = orc.Tree(p.x, p.y, p.z, p.m, **kw)
+    check_structure(g, t)
+    ng = t.sizes()["n_groups"]
+    sel = np.arange(0, ng, 61)
+    ref = t.force_groups(sel)
+    mask = np.isfinite(ref[0])
+    assert mask.sum() > 5000
+    assert rms_rel_acc(a[mask], [r[mask] for r in ref]) <= FORCE_RMS_TOL
+    assert rms_rel_pot(a[mask], [r[mask] for r in ref]) <= POT_RMS_TOL
+    g.close()
