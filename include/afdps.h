@@ -63,7 +63,8 @@ typedef enum {
   AFD_ERR_TIMEOUT = -7,       /* a bounded device wait gave up */
   AFD_ERR_NO_TREE = -8,       /* lists or force requested before a tree */
   AFD_ERR_OOM = -9,           /* device allocation failed */
-  AFD_ERR_WALK_STACK = -10    /* a tree walk overflowed its per-warp stack */
+  AFD_ERR_WALK_STACK = -10,   /* a tree walk overflowed its per-warp stack */
+  AFD_ERR_TOO_LARGE = -11     /* problem size above the limit of afd_root_cell_static */
 } afd_status;
 
 /* Method parameters. Paper values: n_leaf = 16, theta in [0.25, 1]
@@ -212,6 +213,39 @@ int afd_export(afd_ctx *ctx, int what, void *host_buf, size_t *bytes);
 /* Milliseconds of the most recent force kernel launch as measured by CUDA
  * events recorded around it on the context's stream (synchronises). */
 int afd_last_force_ms(afd_ctx *ctx, float *ms);
+
+/* Root cell of a particle set without any device allocation.
+ *
+ * The paper has no counterpart: this entry point is for callers that cannot
+ * allocate device memory -- code whose GPU memory is entirely owned by
+ * another allocator (for example a framework's memory pool), or loops that
+ * must not call cudaMalloc / cudaFree after start-up because those calls can
+ * synchronise the device. It needs no context (afd_create allocates).
+ *
+ * Computes the same root cell as afd_tree_build -- centre (min + max) / 2 per
+ * axis, side = the smallest power of two >= 1.000001 x the largest extent
+ * (1 for a zero extent; root (0, 0, 0, 1) for n = 0) -- from x, y, z (n
+ * device doubles each, caller order), and checks m (n device doubles) for
+ * finiteness. root_out: device, 4 doubles (centre x, y, z, side).
+ * nonfinite_out: device int, set to 1 when a coordinate or mass is NaN or
+ * infinite (NaN coordinates are then left out of the box), else 0. Queued on
+ * `stream` (a cudaStream_t; NULL = the legacy default stream); the call does
+ * not synchronise.
+ *
+ * Scratch: a file-scope static device array of 29,440 bytes, which every GPU
+ * that loads the library keeps until the process exits. All calls on a
+ * device share it and it keeps the last call's contents; each call clears
+ * the part that must start at zero. Calls whose work overlaps on the GPU
+ * (different streams or host threads) race on it: serialise them. The first
+ * call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; the lookup is not
+ * stream-ordered, so make that first call before any stream capture.
+ *
+ * n must lie in 0 .. 2^31 - 1 (the library's particle index range); a larger
+ * n returns AFD_ERR_TOO_LARGE before the device is touched. The call makes no
+ * cudaMalloc, cudaFree or other allocating call. */
+int afd_root_cell_static(const double *x, const double *y, const double *z, const double *m,
+                         int64_t n, double *root_out, int *nonfinite_out, void *stream);
 
 /* Human-readable text for a status code (static storage). */
 const char *afd_error_string(int status);

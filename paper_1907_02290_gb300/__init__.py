@@ -87,6 +87,7 @@ def lib():
         "afd_export": ([_VP, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
         "afd_last_force_ms": ([_VP, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
         "afd_error_string": ([ctypes.c_int], ctypes.c_char_p),
+        "afd_root_cell_static": ([_VP, _VP, _VP, _VP, _I64, _VP, _VP, _VP], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -253,6 +254,18 @@ def afd_last_force_ms(ctx) -> float:
     v = ctypes.c_float(0.0)
     _check(lib().afd_last_force_ms(ctx, ctypes.byref(v)), "afd_last_force_ms")
     return float(v.value)
+
+
+def afd_root_cell_static(x, y, z, m, root_out, nonfinite_out, stream=None):
+    """Root cell without any device allocation (for callers that cannot
+    allocate): root_out float64 (4,) and nonfinite_out int32 (1,) CUDA
+    tensors receive the result; queued on ``stream``."""
+    import torch
+    n = x.numel()
+    p = [_dptr(a, torch.float64, n, nm) for a, nm in zip((x, y, z, m), "xyzm")]
+    _check(lib().afd_root_cell_static(*p, n, _dptr(root_out, torch.float64, 4, "root_out"),
+                                      _dptr(nonfinite_out, torch.int32, 1, "nonfinite_out"),
+                                      _stream_ptr(stream)), "afd_root_cell_static")
 
 
 # ---------------------------------------------------------------- convenience

@@ -454,6 +454,7 @@ const char *afd_error_string(int status) {
     case AFD_ERR_NO_TREE: return "no tree built";
     case AFD_ERR_OOM: return "device allocation failed";
     case AFD_ERR_WALK_STACK: return "tree walk overflowed its stack";
+    case AFD_ERR_TOO_LARGE: return "problem size above the static scratch limit (n <= 2^31 - 1)";
     default: return "unknown status";
   }
 }
