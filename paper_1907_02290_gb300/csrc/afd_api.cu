@@ -159,7 +159,6 @@ int reuse(afd_ctx *c, const double *x, const double *y, const double *z, const d
   if (c->n > 0 && (!x || !y || !z || !m)) return AFD_ERR_ARG;
   TRY(launch_reorder(c, x, y, z, m, c->n));
   TRY(launch_moments(c));
-  TRY(launch_group_boxes(c));
   return AFD_OK;
 }
 
@@ -226,8 +225,8 @@ void afd_destroy(afd_ctx *c) {
                     &c->lk_off, &c->c_level, &c->c_first, &c->c_count, &c->c_skip, &c->c_parent,
                     &c->c_child, &c->c_arrive, &c->c_mass, &c->c_smom, &c->c_com, &c->c_quad,
                     &c->s_hi, &c->s_lo, &c->s_q0, &c->s_q1, &c->node_f, &c->node_i, &c->g_cnt,
-                    &c->g_off, &c->g_first, &c->g_count, &c->g_box, &c->g_boxf, &c->g_chi,
-                    &c->g_clo, &c->g_self, &c->u_cnt, &c->u_off, &c->u_group, &c->l_cnt_e,
+                    &c->g_off, &c->g_first, &c->g_count, &c->g_cell, &c->g_box, &c->g_boxf,
+                    &c->g_self, &c->u_cnt, &c->u_off, &c->u_info, &c->l_cnt_e,
                     &c->l_cnt_s, &c->epj_off, &c->spj_off, &c->epj, &c->spj, &c->scan_tmp,
                     &c->hx, &c->hy, &c->hz, &c->hm, &c->hacc};
   for (DevBuf *b : bufs) release(*b);

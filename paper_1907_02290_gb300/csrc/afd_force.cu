@@ -3,17 +3,23 @@
 // warp per unit. The warp walks the group's EPJ list, then its SPJ list, 32
 // entries at a time: each lane gathers one j by index (float4 hi + float4 lo
 // of a particle or of a cell's centre of mass), forms its coordinates
-// relative to the group centre, stages them in shared memory, and then every
-// lane runs the 32 interactions against its own i-particle.
+// relative to the group origin, stages them in shared memory, and then every
+// lane runs the 32 interactions against its own i-particle. The gathers of
+// the next chunk are issued before the current chunk is computed.
 //
-// Precision. Positions are FP64 in memory. Group-relative coordinates are
-// formed from hi/lo FP32 pairs, (x_hi - c_hi) + (x_lo - c_lo): when x and c
-// are close the hi difference is exact (Sterbenz) and the result equals the
-// FP64 difference rounded to FP32 up to the tiny lo terms; when they are far
-// apart the relative rounding error is that of one FP32 operation. The
-// pairwise term is FP32 with a hardware reciprocal square root. Each chunk's
-// 32 terms are summed in FP32 and the chunk sums are accumulated with Kahan
-// compensation.
+// Packed arithmetic: each lane evaluates two j's (an even and an odd slot
+// of the chunk) against its i in one pass of f32x2 instructions -- 13
+// packed FP32 operations and two MUFU.RSQ per two interactions -- which
+// halves the issue slots of the scalar loop.
+//
+// Precision. Positions are FP64 in memory. Coordinates relative to the
+// group origin (the centre of mass of the group's cell) are formed from
+// hi/lo FP32 pairs, (x_hi - c_hi) + (x_lo - c_lo): when x and c are close
+// the hi difference is exact (Sterbenz) and the result equals the FP64
+// difference rounded to FP32 up to the tiny lo terms; when they are far
+// apart the relative rounding error is that of one FP32 operation. Each
+// chunk's terms are summed in FP32 (one sum per even/odd stream) and the
+// chunk sums are accumulated with Kahan compensation.
 //
 // Per interaction: 3 FADD (dx), 3 FFMA (r^2), 1 MUFU.RSQ, 3 FMUL, 3 FFMA (a),
 // 1 FADD (phi) -- 23 flops by the paper's convention (Section 6.2, n_op).
@@ -22,14 +28,29 @@
 namespace afd {
 namespace {
 
-constexpr int kForceWarps = 4;
+#ifndef AFD_FORCE_MIN_BLOCKS
+#define AFD_FORCE_MIN_BLOCKS 8  // resident blocks per SM the register budget targets
+#endif
+#ifndef AFD_FORCE_WARPS
+#define AFD_FORCE_WARPS 4
+#endif
+#ifndef AFD_FORCE_ILP2
+#define AFD_FORCE_ILP2 1  // two independent accumulator chains per lane
+#endif
+#ifndef AFD_FORCE_FLUSH_PAIRS
+#define AFD_FORCE_FLUSH_PAIRS 16  // pair-iterations per lane between Kahan flushes
+#endif
+#ifndef AFD_FORCE_PERSISTENT
+#define AFD_FORCE_PERSISTENT 0  // warps take units from an atomic queue
+#endif
+constexpr int kForceWarps = AFD_FORCE_WARPS;
 constexpr int kForceThreads = 32 * kForceWarps;
 
 struct ForceArgs {
   int64_t n_units;
-  const uint32_t *u_group, *u_off;
-  const uint32_t *g_first, *g_count, *g_self;
-  const float4 *g_chi, *g_clo;
+  unsigned long long *queue;  // work counter of the persistent variant (zeroed per launch)
+  const uint2 *u_info;
+  const uint32_t *g_first, *g_count, *g_self, *g_cell;
   const float4 *jhi, *jlo;  // particles, Morton order
   const float4 *shi, *slo;  // cells
   const float4 *sq0, *sq1;  // cell quadrupoles
@@ -44,33 +65,6 @@ __device__ __forceinline__ float rsqrt_fast(float x) {
   float r;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
-}
-
-__device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
-  const float y = v - c;
-  const float t = s + y;
-  c = (t - s) - y;
-  s = t;
-}
-
-struct Acc {
-  float x = 0.f, y = 0.f, z = 0.f, p = 0.f;     // running sums
-  float cx = 0.f, cy = 0.f, cz = 0.f, cp = 0.f; // Kahan compensation
-};
-
-template <bool GUARD>
-__device__ __forceinline__ void interact(float4 j, float xi, float yi, float zi, float eps2,
-                                         float &px, float &py, float &pz, float &pp) {
-  const float dx = j.x - xi, dy = j.y - yi, dz = j.z - zi;
-  const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-  float rinv = rsqrt_fast(r2);
-  if (GUARD) rinv = r2 > 0.0f ? rinv : 0.0f;
-  const float mr = j.w * rinv;
-  const float mr3 = mr * rinv * rinv;
-  px = fmaf(mr3, dx, px);
-  py = fmaf(mr3, dy, py);
-  pz = fmaf(mr3, dz, pz);
-  pp += mr;
 }
 
 // Quadrupole term of one cell (Q about its COM, r = x_i - COM = -d):
@@ -106,101 +100,344 @@ __device__ __forceinline__ void interact_quad(float4 j, float4 q0, float4 q1, fl
   pp = fmaf(0.5f * dqd, rinv5, pp);
 }
 
-template <bool GUARD, bool QUAD>
-__global__ void __launch_bounds__(kForceThreads) k_force(ForceArgs a) {
-  __shared__ float4 jbuf[kForceWarps][32];
-  __shared__ float4 qbuf0[QUAD ? kForceWarps : 1][32];
-  __shared__ float4 qbuf1[QUAD ? kForceWarps : 1][32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t u = (int64_t)blockIdx.x * kForceWarps + w;
-  if (u >= a.n_units) return;
-  const uint32_t g = a.u_group[u];
-  const uint32_t chunk = (uint32_t)u - a.u_off[g];
-  const uint32_t gf = a.g_first[g], gc = a.g_count[g];
-  const uint32_t il = chunk * 32u + lane;
-  const bool active = il < gc;
-  const uint32_t i = gf + il;
-  const float4 ch = a.g_chi[g], cl = a.g_clo[g];
-  float xi = 0.f, yi = 0.f, zi = 0.f, mi = 0.f;
-  if (active) {
-    const float4 h = a.jhi[i], l = a.jlo[i];
-    xi = (h.x - ch.x) + (l.x - cl.x);
-    yi = (h.y - ch.y) + (l.y - cl.y);
-    zi = (h.z - ch.z) + (l.z - cl.z);
-    mi = h.w;
+// ---- packed FP32 pairs (two lanes of work in one 64-bit register) ----
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 pk(float a, float b) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void upk(f2 v, float &a, float &b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+  f2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+  f2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+  f2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+  f2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+// One lane, one i-particle, two j's (an even and an odd slot of the chunk)
+// per packed instruction: 13 f32x2 operations and 2 MUFU.RSQ for two
+// interactions.
+template <bool GUARD>
+__device__ __forceinline__ void interact2(float4 a, float4 b, f2 XI, f2 YI, f2 ZI, f2 E2, f2 &AX,
+                                          f2 &AY, f2 &AZ, f2 &PP) {
+  const f2 DX = sub2(pk(a.x, a.y), XI);
+  const f2 DY = sub2(pk(a.z, a.w), YI);
+  const f2 DZ = sub2(pk(b.x, b.y), ZI);
+  const f2 R2 = fma2(DX, DX, fma2(DY, DY, fma2(DZ, DZ, E2)));
+  float r0, r1;
+  upk(R2, r0, r1);
+  float q0 = rsqrt_fast(r0), q1 = rsqrt_fast(r1);
+  if (GUARD) {
+    q0 = r0 > 0.0f ? q0 : 0.0f;
+    q1 = r1 > 0.0f ? q1 : 0.0f;
   }
-  Acc acc;
-  const float eps2 = a.eps2;
-  // ---- EPJ list: particles ----
-  {
-    const uint64_t o0 = a.off_e[g], o1 = a.off_e[g + 1];
-    for (uint64_t base = o0; base < o1; base += 32) {
-      const uint64_t k = base + lane;
-      float4 r = make_float4(1e18f, 1e18f, 1e18f, 0.0f);
-      if (k < o1) {
-        const uint32_t j = a.epj[k];
-        const float4 h = a.jhi[j], l = a.jlo[j];
-        r = make_float4((h.x - ch.x) + (l.x - cl.x), (h.y - ch.y) + (l.y - cl.y),
-                        (h.z - ch.z) + (l.z - cl.z), h.w);
-      }
-      __syncwarp();
-      jbuf[w][lane] = r;
-      __syncwarp();
-      float px = 0.f, py = 0.f, pz = 0.f, pp = 0.f;
-#pragma unroll 8
-      for (int t = 0; t < 32; t++) interact<GUARD>(jbuf[w][t], xi, yi, zi, eps2, px, py, pz, pp);
-      kahan_add(acc.x, acc.cx, px);
-      kahan_add(acc.y, acc.cy, py);
-      kahan_add(acc.z, acc.cz, pz);
-      kahan_add(acc.p, acc.cp, pp);
+  const f2 RI = pk(q0, q1);
+  const f2 MR = mul2(pk(b.z, b.w), RI);
+  const f2 MR3 = mul2(mul2(MR, RI), RI);
+  AX = fma2(MR3, DX, AX);
+  AY = fma2(MR3, DY, AY);
+  AZ = fma2(MR3, DZ, AZ);
+  PP = add2(PP, MR);
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N));
+}
+
+// Shared-memory staging of one warp: raw j data of two chunks in flight
+// (double buffer filled by cp.async) and the packed pair layout of the chunk
+// being computed:
+//   P0[p] = (x_2p, x_2p+1, y_2p, y_2p+1), P1[p] = (z_2p, z_2p+1, m_2p, m_2p+1).
+template <bool QUAD>
+struct WarpStage {
+  float4 rh[2][32], rl[2][32];
+  float4 rq0[QUAD ? 2 : 1][QUAD ? 32 : 1], rq1[QUAD ? 2 : 1][QUAD ? 32 : 1];
+  float4 P0[16], P1[16];
+  float4 jb[QUAD ? 32 : 1], q0[QUAD ? 32 : 1], q1[QUAD ? 32 : 1];
+  float4 ch, cl;  // origin of the relative coordinates (hi, lo)
+};
+
+// Per-lane state: IPT i-particles (coordinates duplicated in both halves of
+// a packed pair) and eps^2.
+template <int IPT>
+struct Lane {
+  int lane, stream;
+  f2 XI[IPT], YI[IPT], ZI[IPT];
+  f2 E2;
+};
+
+// Kahan-compensated running sums of one i-particle (both packed streams folded).
+struct Sums {
+  float sx, sy, sz, sp;
+  float cx, cy, cz, cp;
+};
+
+__device__ __forceinline__ void kahan_fold(float &s, float &c, f2 v) {
+  float v0, v1;
+  upk(v, v0, v1);
+  const float y = (v0 + v1) - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+// Issue the asynchronous gather of list entries [base, base + 32) into
+// buffer b (lanes past the end copy nothing).
+template <bool QUAD>
+__device__ __forceinline__ void gather(WarpStage<QUAD> &st, int b, int lane, uint64_t k,
+                                       uint64_t o1, uint32_t j, const float4 *hi,
+                                       const float4 *lo, const float4 *sq0, const float4 *sq1,
+                                       bool quad_list) {
+  if (k < o1) {
+    cp_async16(&st.rh[b][lane], hi + j);
+    cp_async16(&st.rl[b][lane], lo + j);
+    if (QUAD && quad_list) {
+      cp_async16(&st.rq0[b][lane], sq0 + j);
+      cp_async16(&st.rq1[b][lane], sq1 + j);
     }
   }
-  // ---- SPJ list: cells (monopole, optionally quadrupole) ----
-  {
-    const uint64_t o0 = a.off_s[g], o1 = a.off_s[g + 1];
-    for (uint64_t base = o0; base < o1; base += 32) {
-      const uint64_t k = base + lane;
-      float4 r = make_float4(1e18f, 1e18f, 1e18f, 0.0f);
-      float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0;
-      if (k < o1) {
-        const uint32_t j = a.spj[k];
-        const float4 h = a.shi[j], l = a.slo[j];
-        r = make_float4((h.x - ch.x) + (l.x - cl.x), (h.y - ch.y) + (l.y - cl.y),
-                        (h.z - ch.z) + (l.z - cl.z), h.w);
-        if (QUAD) {
-          q0 = a.sq0[j];
-          q1 = a.sq1[j];
-        }
-      }
-      __syncwarp();
-      jbuf[w][lane] = r;
-      if (QUAD) {
-        qbuf0[w][lane] = q0;
-        qbuf1[w][lane] = q1;
-      }
-      __syncwarp();
-      float px = 0.f, py = 0.f, pz = 0.f, pp = 0.f;
-      if (QUAD) {
+  cp_async_commit();
+}
+
+// One list (EPJ or SPJ) of one group for one warp with S j-streams.
+template <bool GUARD, bool QUAD, int S, int IPT>
+__device__ __forceinline__ void run_list(WarpStage<QUAD> &st, const Lane<IPT> &ln, Sums *sm,
+                                         const uint32_t *idx, uint64_t o0, uint64_t o1,
+                                         const float4 *hi, const float4 *lo, const float4 *sq0,
+                                         const float4 *sq1, bool quad_list, float eps2) {
+  if (o0 >= o1) return;
+  const int lane = ln.lane;
+  const f2 Z0 = pk(0.0f, 0.0f);
+  // prologue: chunk 0 in flight, index of chunk 1 in a register
+  uint32_t j0 = o0 + lane < o1 ? idx[o0 + lane] : 0u;
+  gather<QUAD>(st, 0, lane, o0 + lane, o1, j0, hi, lo, sq0, sq1, quad_list);
+  uint32_t jn = o0 + 32 + lane < o1 ? idx[o0 + 32 + lane] : 0u;
+  f2 AX[IPT], AY[IPT], AZ[IPT], PP[IPT];
+#pragma unroll
+  for (int q = 0; q < IPT; q++) AX[q] = AY[q] = AZ[q] = PP[q] = Z0;
+  int pending = 0;  // pair-iterations accumulated since the last Kahan flush
+  int b = 0;
+  for (uint64_t base = o0; base < o1; base += 32) {
+    // next chunk in flight, index of the one after in a register
+    const uint64_t nb = base + 32;
+    gather<QUAD>(st, b ^ 1, lane, nb + lane, o1, jn, hi, lo, sq0, sq1, quad_list);
+    jn = nb + 32 + lane < o1 ? idx[nb + 32 + lane] : 0u;
+    cp_async_wait<1>();  // this lane's copies of the current chunk have landed
+    // relative coordinates of this lane's j (far, massless padding past the end)
+    float rx = 1e18f, ry = 1e18f, rz = 1e18f, rm = 0.0f;
+    if (base + lane < o1) {
+      const float4 h = st.rh[b][lane], l = st.rl[b][lane];
+      const float4 ch = st.ch, cl = st.cl;
+      rx = (h.x - ch.x) + (l.x - cl.x);
+      ry = (h.y - ch.y) + (l.y - cl.y);
+      rz = (h.z - ch.z) + (l.z - cl.z);
+      rm = h.w;
+    }
+    __syncwarp();
+    if (QUAD && quad_list) {
+      st.jb[lane] = make_float4(rx, ry, rz, rm);
+      const bool v = base + lane < o1;
+      st.q0[lane] = v ? st.rq0[b][lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+      st.q1[lane] = v ? st.rq1[b][lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+      float *p0 = reinterpret_cast<float *>(&st.P0[lane >> 1]);
+      float *p1 = reinterpret_cast<float *>(&st.P1[lane >> 1]);
+      const int e = lane & 1;
+      p0[e] = rx;
+      p0[2 + e] = ry;
+      p1[e] = rz;
+      p1[2 + e] = rm;
+    }
+    __syncwarp();
+    if (QUAD && quad_list) {
+#pragma unroll
+      for (int q = 0; q < IPT; q++) {
+        float px = 0.f, py = 0.f, pz = 0.f, pp = 0.f, xi, yi, zi, dummy;
+        upk(ln.XI[q], xi, dummy);
+        upk(ln.YI[q], yi, dummy);
+        upk(ln.ZI[q], zi, dummy);
 #pragma unroll 4
-        for (int t = 0; t < 32; t++)
-          interact_quad<GUARD>(jbuf[w][t], qbuf0[w][t], qbuf1[w][t], xi, yi, zi, eps2, px, py, pz, pp);
-      } else {
-#pragma unroll 8
-        for (int t = 0; t < 32; t++) interact<GUARD>(jbuf[w][t], xi, yi, zi, eps2, px, py, pz, pp);
+        for (int t = ln.stream; t < 32; t += S)
+          interact_quad<GUARD>(st.jb[t], st.q0[t], st.q1[t], xi, yi, zi, eps2, px, py, pz, pp);
+        AX[q] = add2(AX[q], pk(px, 0.f));
+        AY[q] = add2(AY[q], pk(py, 0.f));
+        AZ[q] = add2(AZ[q], pk(pz, 0.f));
+        PP[q] = add2(PP[q], pk(pp, 0.f));
       }
-      kahan_add(acc.x, acc.cx, px);
-      kahan_add(acc.y, acc.cy, py);
-      kahan_add(acc.z, acc.cz, pz);
-      kahan_add(acc.p, acc.cp, pp);
+    } else if (AFD_FORCE_ILP2 && S == 1) {
+      f2 BX = Z0, BY = Z0, BZ = Z0, BP = Z0;
+#pragma unroll
+      for (int t = 0; t < 16; t += 2) {
+        interact2<GUARD>(st.P0[t], st.P1[t], ln.XI[0], ln.YI[0], ln.ZI[0], ln.E2, AX[0], AY[0],
+                         AZ[0], PP[0]);
+        interact2<GUARD>(st.P0[t + 1], st.P1[t + 1], ln.XI[0], ln.YI[0], ln.ZI[0], ln.E2, BX, BY,
+                         BZ, BP);
+      }
+      AX[0] = add2(AX[0], BX);
+      AY[0] = add2(AY[0], BY);
+      AZ[0] = add2(AZ[0], BZ);
+      PP[0] = add2(PP[0], BP);
+    } else {
+#pragma unroll
+      for (int t = ln.stream; t < 16; t += S)
+        interact2<GUARD>(st.P0[t], st.P1[t], ln.XI[0], ln.YI[0], ln.ZI[0], ln.E2, AX[0], AY[0],
+                         AZ[0], PP[0]);
+    }
+    pending += 16 / S;
+    if (pending >= AFD_FORCE_FLUSH_PAIRS || nb >= o1) {
+#pragma unroll
+      for (int q = 0; q < IPT; q++) {
+        kahan_fold(sm[q].sx, sm[q].cx, AX[q]);
+        kahan_fold(sm[q].sy, sm[q].cy, AY[q]);
+        kahan_fold(sm[q].sz, sm[q].cz, AZ[q]);
+        kahan_fold(sm[q].sp, sm[q].cp, PP[q]);
+        AX[q] = AY[q] = AZ[q] = PP[q] = Z0;
+      }
+      pending = 0;
+    }
+    b ^= 1;
+  }
+  cp_async_wait<0>();
+  __syncwarp();
+}
+
+template <bool GUARD, bool QUAD, int S, int IPT>
+__device__ __forceinline__ void run_unit(WarpStage<QUAD> &st, const ForceArgs &a, uint32_t g,
+                                         const Lane<IPT> &ln, Sums *sm) {
+  run_list<GUARD, QUAD, S, IPT>(st, ln, sm, a.epj, a.off_e[g], a.off_e[g + 1], a.jhi, a.jlo,
+                                nullptr, nullptr, false, a.eps2);
+  run_list<GUARD, QUAD, S, IPT>(st, ln, sm, a.spj, a.off_s[g], a.off_s[g + 1], a.shi, a.slo,
+                                a.sq0, a.sq1, QUAD, a.eps2);
+}
+
+// One work unit with IPT particles per lane and S j-streams: set up the
+// lanes' i-particles, run both lists, combine the streams and write.
+template <bool GUARD, bool QUAD, int S, int IPT>
+__device__ __forceinline__ void unit_body(const ForceArgs &a, WarpStage<QUAD> &st, int lane,
+                                          uint32_t g, uint32_t ioff) {
+  constexpr int W = 32 / S;
+  Lane<IPT> ln;
+  ln.lane = lane;
+  ln.stream = lane / W;
+  const uint32_t gf = a.g_first[g], gc = a.g_count[g];
+  // origin of the relative coordinates: the group cell's centre of mass
+  const uint32_t gcell = a.g_cell[g];
+  const float4 ch = a.shi[gcell], cl = a.slo[gcell];
+  if (lane == 0) {
+    st.ch = ch;
+    st.cl = cl;
+  }
+  uint32_t il[IPT];
+  bool active[IPT];
+  float mi[IPT];
+#pragma unroll
+  for (int q = 0; q < IPT; q++) {
+    il[q] = ioff + (uint32_t)(q * 32 + (lane & (W - 1)));
+    active[q] = il[q] < gc;
+    float xi = 0.f, yi = 0.f, zi = 0.f;
+    mi[q] = 0.f;
+    if (active[q]) {
+      const float4 h = a.jhi[gf + il[q]], l = a.jlo[gf + il[q]];
+      xi = (h.x - ch.x) + (l.x - cl.x);
+      yi = (h.y - ch.y) + (l.y - cl.y);
+      zi = (h.z - ch.z) + (l.z - cl.z);
+      mi[q] = h.w;
+    }
+    ln.XI[q] = pk(xi, xi);
+    ln.YI[q] = pk(yi, yi);
+    ln.ZI[q] = pk(zi, zi);
+  }
+  ln.E2 = pk(a.eps2, a.eps2);
+  Sums sm[IPT];
+#pragma unroll
+  for (int q = 0; q < IPT; q++)
+    sm[q].sx = sm[q].sy = sm[q].sz = sm[q].sp = sm[q].cx = sm[q].cy = sm[q].cz = sm[q].cp = 0.0f;
+  __syncwarp();
+  run_unit<GUARD, QUAD, S, IPT>(st, a, g, ln, sm);
+  const bool self = !GUARD && a.g_self[g];
+#pragma unroll
+  for (int q = 0; q < IPT; q++) {
+    float ax = sm[q].sx - sm[q].cx, ay = sm[q].sy - sm[q].cy, az = sm[q].sz - sm[q].cz;
+    float pot = sm[q].sp - sm[q].cp;
+    // combine the j-streams of each particle
+#pragma unroll
+    for (int o = W; o < 32; o <<= 1) {
+      ax += __shfl_xor_sync(0xffffffffu, ax, o);
+      ay += __shfl_xor_sync(0xffffffffu, ay, o);
+      az += __shfl_xor_sync(0xffffffffu, az, o);
+      pot += __shfl_xor_sync(0xffffffffu, pot, o);
+    }
+    if (active[q] && ln.stream == 0) {
+      // Remove the self pair (dx = 0 exactly, so it added m_i / eps to phi only).
+      if (self) {
+        const float r2 = fmaf(0.0f, 0.0f, fmaf(0.0f, 0.0f, fmaf(0.0f, 0.0f, a.eps2)));
+        pot -= mi[q] * rsqrt_fast(r2);
+      }
+      a.out[a.perm[gf + il[q]]] = make_float4(ax, ay, az, -pot);
     }
   }
-  if (!active) return;
-  // Remove the self pair (dx = 0 exactly, so it added m_i / eps to phi only).
-  if (!GUARD && a.g_self[g]) {
-    const float r2 = fmaf(0.0f, 0.0f, fmaf(0.0f, 0.0f, fmaf(0.0f, 0.0f, eps2)));
-    kahan_add(acc.p, acc.cp, -(mi * rsqrt_fast(r2)));
+}
+
+// Work unit u: group g = info.x, first particle offset = info.y & 0xffff,
+// j-stream split sidx = info.y >> 16 (S = 1 << sidx streams of W = 32 >> sidx
+// particles; lane = stream * W + particle).
+// Work unit u: group g = info.x; info.y holds the first particle offset
+// (bits 0-15) and log2 of the j-stream split S (bits 16-17).
+template <bool GUARD, bool QUAD>
+__device__ __forceinline__ void force_unit(const ForceArgs &a, WarpStage<QUAD> &st, int lane,
+                                           int64_t u) {
+  const uint2 info = a.u_info[u];
+  const uint32_t g = info.x, ioff = info.y & 0xffffu;
+  const int sidx = (int)((info.y >> 16) & 3u);
+  if (sidx == 0) unit_body<GUARD, QUAD, 1, 1>(a, st, lane, g, ioff);
+  else if (sidx == 1) unit_body<GUARD, QUAD, 2, 1>(a, st, lane, g, ioff);
+  else unit_body<GUARD, QUAD, 4, 1>(a, st, lane, g, ioff);
+}
+
+template <bool GUARD, bool QUAD>
+__global__ void __launch_bounds__(kForceThreads, QUAD ? 4 : AFD_FORCE_MIN_BLOCKS * 4 / AFD_FORCE_WARPS)
+    k_force(ForceArgs a) {
+  __shared__ WarpStage<QUAD> stage[kForceWarps];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (AFD_FORCE_PERSISTENT) {
+    for (;;) {
+      unsigned long long u = 0;
+      if (lane == 0) u = atomicAdd(a.queue, 1ull);
+      u = __shfl_sync(0xffffffffu, u, 0);
+      if ((int64_t)u >= a.n_units) return;
+      force_unit<GUARD, QUAD>(a, stage[w], lane, (int64_t)u);
+      __syncwarp();
+    }
+  } else {
+    const int64_t u = (int64_t)blockIdx.x * kForceWarps + w;
+    if (u >= a.n_units) return;
+    force_unit<GUARD, QUAD>(a, stage[w], lane, u);
   }
-  a.out[a.perm[i]] = make_float4(acc.x, acc.y, acc.z, -acc.p);
 }
 
 }  // namespace
@@ -209,13 +446,11 @@ int launch_force(afd_ctx *c, float *acc4) {
   if (c->n == 0 || c->n_units == 0) return AFD_OK;
   ForceArgs a;
   a.n_units = c->n_units;
-  a.u_group = ptr<uint32_t>(c->u_group);
-  a.u_off = ptr<uint32_t>(c->u_off);
+  a.u_info = ptr<uint2>(c->u_info);
   a.g_first = ptr<uint32_t>(c->g_first);
   a.g_count = ptr<uint32_t>(c->g_count);
   a.g_self = ptr<uint32_t>(c->g_self);
-  a.g_chi = ptr<float4>(c->g_chi);
-  a.g_clo = ptr<float4>(c->g_clo);
+  a.g_cell = ptr<uint32_t>(c->g_cell);
   a.jhi = ptr<float4>(c->jhi);
   a.jlo = ptr<float4>(c->jlo);
   a.shi = ptr<float4>(c->s_hi);
@@ -230,7 +465,17 @@ int launch_force(afd_ctx *c, float *acc4) {
   const float e = (float)c->cfg.eps;
   a.eps2 = e * e;
   a.out = reinterpret_cast<float4 *>(acc4);
-  const unsigned nb = (unsigned)((c->n_units + kForceWarps - 1) / kForceWarps);
+  a.queue = ptr<unsigned long long>(c->u64acc) + 2;
+  unsigned nb = (unsigned)((c->n_units + kForceWarps - 1) / kForceWarps);
+  if (AFD_FORCE_PERSISTENT) {
+    if (cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), c->stream) != cudaSuccess)
+      return AFD_ERR_CUDA;
+    int per_sm = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force<false, false>, kForceThreads, 0);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    const unsigned cap = (unsigned)(per_sm > 0 ? per_sm : 1) * (unsigned)(sms > 0 ? sms : 1);
+    if (nb > cap) nb = cap;
+  }
   const bool guard = !(a.eps2 > 0.0f);
   cudaEventRecord(c->ev0, c->stream);
   if (c->cfg.multipole) {

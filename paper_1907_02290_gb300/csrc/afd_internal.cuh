@@ -77,8 +77,8 @@ struct afd_ctx {
 
   // groups and force work units
   afd::DevBuf g_cnt, g_off;
-  afd::DevBuf g_first, g_count, g_box, g_boxf, g_chi, g_clo, g_self;
-  afd::DevBuf u_cnt, u_off, u_group;
+  afd::DevBuf g_first, g_count, g_cell, g_box, g_boxf, g_self;
+  afd::DevBuf u_cnt, u_off, u_info;
 
   // lists (CSR)
   afd::DevBuf l_cnt_e, l_cnt_s, epj_off, spj_off, epj, spj;

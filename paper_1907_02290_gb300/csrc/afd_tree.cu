@@ -14,6 +14,9 @@ namespace afd {
 namespace {
 
 constexpr int kThreads = 256;
+#ifndef AFD_MAX_SIDX
+#define AFD_MAX_SIDX 2u  // largest log2 of the j-stream split of a remainder unit
+#endif
 
 inline unsigned blocks_for(int64_t n, int threads = kThreads) {
   return (unsigned)((n + threads - 1) / threads);
@@ -86,14 +89,36 @@ __global__ void __launch_bounds__(kThreads) k_root(const double *__restrict__ x,
     last = atomicAdd(counter, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (!last || threadIdx.x != 0) return;
+  if (!last) return;
   __threadfence();
-  double b[6];
-  for (int d = 0; d < 6; d++) b[d] = __ldcg(&part[d]);
-  for (unsigned k = 1; k < gridDim.x; k++)
+  // the last block reduces all partials, every thread a strided share
+  for (int d = 0; d < 3; d++) {
+    lo[d] = DBL_MAX;
+    hi[d] = -DBL_MAX;
+  }
+  for (unsigned k = threadIdx.x; k < gridDim.x; k += blockDim.x)
     for (int d = 0; d < 3; d++) {
-      b[d] = fmin(b[d], __ldcg(&part[k * 6 + d]));
-      b[3 + d] = fmax(b[3 + d], __ldcg(&part[k * 6 + 3 + d]));
+      lo[d] = fmin(lo[d], __ldcg(&part[k * 6 + d]));
+      hi[d] = fmax(hi[d], __ldcg(&part[k * 6 + 3 + d]));
+    }
+  for (int d = 0; d < 3; d++) {
+    lo[d] = warp_min(lo[d]);
+    hi[d] = warp_max(hi[d]);
+  }
+  __syncthreads();
+  if (lane == 0)
+    for (int d = 0; d < 3; d++) {
+      sh[warp][d] = lo[d];
+      sh[warp][3 + d] = hi[d];
+    }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double b[6];
+  for (int d = 0; d < 6; d++) b[d] = sh[0][d];
+  for (int w = 1; w < kThreads / 32; w++)
+    for (int d = 0; d < 3; d++) {
+      b[d] = fmin(b[d], sh[w][d]);
+      b[3 + d] = fmax(b[3 + d], sh[w][3 + d]);
     }
   double ext = 0.0;
   for (int d = 0; d < 3; d++) {
@@ -502,6 +527,9 @@ __global__ void __launch_bounds__(kThreads) k_moments(MomArgs a) {
   }
 }
 
+// Force-kernel work units of a group of cn particles (see k_unit_fill).
+__device__ __forceinline__ uint32_t unit_count(uint32_t cn) { return (cn + 31u) / 32u; }
+
 // ---------------------------------------------------------------------------
 // i-groups: the maximal cells holding at most n_grp particles, in
 // pre-order; a larger leaf is cut into chunks of n_grp.
@@ -529,7 +557,7 @@ __global__ void __launch_bounds__(kThreads) k_group_fill(
     int64_t n_cells, const uint32_t *__restrict__ first, const uint32_t *__restrict__ count,
     const uint32_t *__restrict__ gcnt, const uint32_t *__restrict__ goff, uint32_t n_grp,
     uint32_t *__restrict__ g_first, uint32_t *__restrict__ g_count,
-    uint32_t *__restrict__ u_cnt) {
+    uint32_t *__restrict__ g_cell, uint32_t *__restrict__ u_cnt) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n_cells) return;
   const uint32_t k_n = gcnt[c];
@@ -540,26 +568,36 @@ __global__ void __launch_bounds__(kThreads) k_group_fill(
     const uint32_t cn = rem < n_grp ? rem : n_grp;
     g_first[g] = f;
     g_count[g] = cn;
-    u_cnt[g] = (cn + 31u) / 32u;
+    g_cell[g] = (uint32_t)c;
+    u_cnt[g] = unit_count(cn);
   }
 }
 
+// Force-kernel work units of a group: one per 32 particles; the last one,
+// holding r < 32 particles, splits its warp into S = 4 (r <= 8) or S = 2
+// (r <= 16) j-streams. info = (group, first offset | log2(S) << 16).
 __global__ void __launch_bounds__(kThreads) k_unit_fill(int64_t n_groups,
+                                                        const uint32_t *__restrict__ g_count,
                                                         const uint32_t *__restrict__ u_off,
-                                                        uint32_t *__restrict__ u_group) {
+                                                        uint2 *__restrict__ u_info) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n_groups) return;
-  for (uint32_t u = u_off[g]; u < u_off[g + 1]; u++) u_group[u] = (uint32_t)g;
+  const uint32_t cn = g_count[g];
+  uint32_t k = 0;
+  for (uint32_t u = u_off[g]; u < u_off[g + 1]; u++, k++) {
+    const uint32_t r = cn - 32u * k;
+    uint32_t sidx = r >= 32u ? 0u : (r <= 8u ? 2u : (r <= 16u ? 1u : 0u));
+    if (sidx > AFD_MAX_SIDX) sidx = AFD_MAX_SIDX;
+    u_info[u] = make_uint2((uint32_t)g, (32u * k) | (sidx << 16));
+  }
 }
 
-// Tight FP64 box per group (one warp per group; min/max are exact), its
-// FP32 copy for the opening criterion, and the box centre as hi/lo floats
-// (the reference point of the force kernel's relative coordinates).
+// Tight FP64 box per group (one warp per group; min/max are exact) and its
+// FP32 copy for the opening criterion.
 __global__ void __launch_bounds__(kThreads) k_group_box(
     int64_t n_groups, const uint32_t *__restrict__ g_first, const uint32_t *__restrict__ g_count,
     const double *__restrict__ xs, const double *__restrict__ ys, const double *__restrict__ zs,
-    double *__restrict__ box, float *__restrict__ boxf, float4 *__restrict__ chi,
-    float4 *__restrict__ clo) {
+    double *__restrict__ box, float *__restrict__ boxf) {
   const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (g >= n_groups) return;
@@ -577,16 +615,12 @@ __global__ void __launch_bounds__(kThreads) k_group_box(
     hi[d] = warp_max(hi[d]);
   }
   if (lane != 0) return;
-  float ch[3], cl[3];
   for (int d = 0; d < 3; d++) {
     box[g * 6 + d] = lo[d];
     box[g * 6 + 3 + d] = hi[d];
     boxf[g * 6 + d] = __double2float_rn(lo[d]);
     boxf[g * 6 + 3 + d] = __double2float_rn(hi[d]);
-    split2(__dmul_rn(__dadd_rn(lo[d], hi[d]), 0.5), ch[d], cl[d]);
   }
-  chi[g] = make_float4(ch[0], ch[1], ch[2], 0.0f);
-  clo[g] = make_float4(cl[0], cl[1], cl[2], 0.0f);
 }
 
 inline int ck() { return cudaGetLastError() == cudaSuccess ? AFD_OK : AFD_ERR_CUDA; }
@@ -787,17 +821,15 @@ int launch_groups(afd_ctx *c) {
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return AFD_ERR_CUDA;
   const int64_t ng = pin[0];
   c->n_groups = ng;
-  for (afd::DevBuf *b : {&c->g_first, &c->g_count, &c->g_self, &c->u_cnt})
+  for (afd::DevBuf *b : {&c->g_first, &c->g_count, &c->g_cell, &c->g_self, &c->u_cnt})
     AFD_TRY(reserve(*b, sizeof(uint32_t) * ng));
   AFD_TRY(reserve(c->u_off, sizeof(uint32_t) * (ng + 1)));
   AFD_TRY(reserve(c->g_box, sizeof(double) * 6 * ng));
   AFD_TRY(reserve(c->g_boxf, sizeof(float) * 6 * ng));
-  AFD_TRY(reserve(c->g_chi, sizeof(float4) * ng));
-  AFD_TRY(reserve(c->g_clo, sizeof(float4) * ng));
   k_group_fill<<<blocks_for(nc), kThreads, 0, c->stream>>>(
       nc, ptr<uint32_t>(c->c_first), ptr<uint32_t>(c->c_count), ptr<uint32_t>(c->g_cnt),
       ptr<uint32_t>(c->g_off), n_grp, ptr<uint32_t>(c->g_first), ptr<uint32_t>(c->g_count),
-      ptr<uint32_t>(c->u_cnt));
+      ptr<uint32_t>(c->g_cell), ptr<uint32_t>(c->u_cnt));
   c->launches++;
   AFD_TRY(ck());
   AFD_TRY(scan_u32(c, ptr<uint32_t>(c->u_cnt), ptr<uint32_t>(c->u_off), ng));
@@ -805,9 +837,10 @@ int launch_groups(afd_ctx *c) {
                   c->stream);
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return AFD_ERR_CUDA;
   c->n_units = pin[0];
-  AFD_TRY(reserve(c->u_group, sizeof(uint32_t) * c->n_units));
-  k_unit_fill<<<blocks_for(ng), kThreads, 0, c->stream>>>(ng, ptr<uint32_t>(c->u_off),
-                                                          ptr<uint32_t>(c->u_group));
+  AFD_TRY(reserve(c->u_info, sizeof(uint2) * c->n_units));
+  k_unit_fill<<<blocks_for(ng), kThreads, 0, c->stream>>>(ng, ptr<uint32_t>(c->g_count),
+                                                          ptr<uint32_t>(c->u_off),
+                                                          ptr<uint2>(c->u_info));
   c->launches++;
   return ck();
 }
@@ -817,8 +850,7 @@ int launch_group_boxes(afd_ctx *c) {
   if (ng == 0) return AFD_OK;
   k_group_box<<<blocks_for(ng * 32), kThreads, 0, c->stream>>>(
       ng, ptr<uint32_t>(c->g_first), ptr<uint32_t>(c->g_count), ptr<double>(c->xs),
-      ptr<double>(c->ys), ptr<double>(c->zs), ptr<double>(c->g_box), ptr<float>(c->g_boxf),
-      ptr<float4>(c->g_chi), ptr<float4>(c->g_clo));
+      ptr<double>(c->ys), ptr<double>(c->zs), ptr<double>(c->g_box), ptr<float>(c->g_boxf));
   c->launches++;
   return ck();
 }
