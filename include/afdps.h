@@ -95,7 +95,8 @@ int afd_set_stream(afd_ctx *ctx, void *stream);
  * Morton keys (21 bits per axis), stable LSD radix sort of (key, index),
  * reorder of the particle data into Morton order, level-wise octree link,
  * bottom-up monopole (and quadrupole) moments, and i-groups. x, y, z, m are
- * n device doubles each (caller order). n = 0 is allowed (empty tree).
+ * n device doubles each (caller order), 0 <= n < 2^30 (n = 0 gives an empty
+ * tree).
  * Synchronises once. Invalidates saved lists. AFD_ERR_NONFINITE if a
  * coordinate or mass is not finite. */
 int afd_tree_build(afd_ctx *ctx, const double *x, const double *y, const double *z,

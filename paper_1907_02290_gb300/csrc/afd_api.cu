@@ -127,7 +127,7 @@ int read_status(afd_ctx *c) {
 
 int tree_build(afd_ctx *c, const double *x, const double *y, const double *z, const double *m,
                int64_t n) {
-  if (n < 0 || n >= ((int64_t)1 << 31)) return AFD_ERR_ARG;
+  if (n < 0 || n >= ((int64_t)1 << 30)) return AFD_ERR_ARG;
   if (n > 0 && (!x || !y || !z || !m)) return AFD_ERR_ARG;
   c->have_tree = c->have_lists = c->saved = false;
   TRY(launch_root(c, x, y, z, m, n));
@@ -136,7 +136,7 @@ int tree_build(afd_ctx *c, const double *x, const double *y, const double *z, co
   TRY(launch_reorder(c, x, y, z, m, n));
   TRY(launch_link(c, n));
   TRY(read_status(c));
-  TRY(launch_moments(c));
+  TRY(launch_moments(c, true));
   TRY(launch_groups(c));
   TRY(launch_group_boxes(c));
   c->n = n;
@@ -158,7 +158,7 @@ int reuse(afd_ctx *c, const double *x, const double *y, const double *z, const d
   if (!c->saved || !c->have_lists) return AFD_ERR_NO_SAVED_LIST;
   if (c->n > 0 && (!x || !y || !z || !m)) return AFD_ERR_ARG;
   TRY(launch_reorder(c, x, y, z, m, c->n));
-  TRY(launch_moments(c));
+  TRY(launch_moments(c, false));
   return AFD_OK;
 }
 
@@ -224,7 +224,7 @@ void afd_destroy(afd_ctx *c) {
                     &c->zs, &c->ms, &c->jhi, &c->jlo, &c->lk_d, &c->lk_c, &c->lk_e, &c->lk_cnt,
                     &c->lk_off, &c->c_level, &c->c_first, &c->c_count, &c->c_skip, &c->c_parent,
                     &c->c_child, &c->c_arrive, &c->c_mass, &c->c_smom, &c->c_com, &c->c_quad,
-                    &c->s_hi, &c->s_lo, &c->s_q0, &c->s_q1, &c->node_f, &c->node_i, &c->g_cnt,
+                    &c->s_hi, &c->s_lo, &c->s_q0, &c->s_q1, &c->node_f, &c->node_i, &c->c_block, &c->g_cnt,
                     &c->g_off, &c->g_first, &c->g_count, &c->g_cell, &c->g_box, &c->g_boxf,
                     &c->g_self, &c->u_cnt, &c->u_off, &c->u_info, &c->l_cnt_e,
                     &c->l_cnt_s, &c->epj_off, &c->spj_off, &c->epj, &c->spj, &c->scan_tmp,

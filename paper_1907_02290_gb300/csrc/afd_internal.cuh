@@ -74,6 +74,7 @@ struct afd_ctx {
   afd::DevBuf c_mass, c_smom, c_com, c_quad;  // f64
   afd::DevBuf s_hi, s_lo, s_q0, s_q1;         // float4 superparticle data
   afd::DevBuf node_f, node_i;                 // walk node data (float4, uint2)
+  afd::DevBuf c_block;                        // per cell 8 child walk records (2 x uint4 each)
 
   // groups and force work units
   afd::DevBuf g_cnt, g_off;
@@ -113,7 +114,7 @@ int launch_sort(afd_ctx *c, int64_t n);  // sorts keys/perm in place (result in 
 int launch_reorder(afd_ctx *c, const double *x, const double *y, const double *z,
                    const double *m, int64_t n);
 int launch_link(afd_ctx *c, int64_t n);        // sets c->n_cells, c->max_level (syncs)
-int launch_moments(afd_ctx *c);                // bottom-up moments + superparticle data
+int launch_moments(afd_ctx *c, bool child_blocks);  // bottom-up moments + superparticle data
 int launch_groups(afd_ctx *c);                 // sets c->n_groups, c->n_units (syncs)
 int launch_group_boxes(afd_ctx *c);
 

@@ -399,6 +399,7 @@ struct MomArgs {
   unsigned *arrive;
   float4 *s_hi, *s_lo, *s_q0, *s_q1, *node_f;
   uint2 *node_i;
+  uint4 *block;  // child walk records, 8 per cell (null: not written)
   int quad_on;
 };
 
@@ -523,6 +524,23 @@ __global__ void __launch_bounds__(kThreads) k_moments(MomArgs a) {
     }
     finish_cell(a, p, M, S, false);
     if (a.quad_on) internal_quad(a, p);
+    if (a.block) {
+      // the walk's view of p's children: (COM_f32, s^2) and (first,
+      // count | leaf, id, 0) per octant slot, id = kNone when empty
+      for (int o = 0; o < 8; o++) {
+        const uint32_t cc = __ldg(&a.child[(size_t)p * 8 + o]);
+        uint4 nf = make_uint4(0u, 0u, 0u, 0u), meta = make_uint4(0u, 0u, kNone, 0u);
+        if (cc != kNone) {
+          const float4 f = __ldcg(&a.node_f[cc]);
+          const uint2 ni = __ldcg(&a.node_i[cc]);
+          nf = make_uint4(__float_as_uint(f.x), __float_as_uint(f.y), __float_as_uint(f.z),
+                          __float_as_uint(f.w));
+          meta = make_uint4(ni.x, ni.y, cc, 0u);
+        }
+        a.block[((size_t)p * 8 + o) * 2] = nf;
+        a.block[((size_t)p * 8 + o) * 2 + 1] = meta;
+      }
+    }
     c = p;
   }
 }
@@ -751,8 +769,9 @@ int launch_link(afd_ctx *c, int64_t n) {
   return ck();
 }
 
-int launch_moments(afd_ctx *c) {
+int launch_moments(afd_ctx *c, bool child_blocks) {
   const int64_t nc = c->n_cells;
+  if (child_blocks) AFD_TRY(reserve(c->c_block, sizeof(uint4) * 16 * (size_t)nc));
   AFD_TRY(reserve(c->c_mass, sizeof(double) * nc));
   AFD_TRY(reserve(c->c_smom, sizeof(double) * 3 * nc));
   AFD_TRY(reserve(c->c_com, sizeof(double) * 3 * nc));
@@ -793,6 +812,7 @@ int launch_moments(afd_ctx *c) {
   a.s_q1 = ptr<float4>(c->s_q1);
   a.node_f = ptr<float4>(c->node_f);
   a.node_i = ptr<uint2>(c->node_i);
+  a.block = child_blocks ? ptr<uint4>(c->c_block) : nullptr;
   a.quad_on = c->cfg.multipole;
   k_moments<<<blocks_for(nc), kThreads, 0, c->stream>>>(a);
   c->launches++;

@@ -4,11 +4,15 @@
 //   an accepted cell appends its id to the group's SPJ list,
 //   an opened leaf appends its particles' Morton positions to the EPJ list,
 //   an opened internal cell is replaced by its children.
-// The warp keeps a stack of cells whose decision is already known. Each
-// step either emits the run of accepted / leaf entries at the top of the
-// stack in order, or expands the open cell at the top, deciding its (up to
-// eight) children in parallel. Emission therefore follows depth-first
-// order exactly. Two passes: counts, then (after a scan) the fill.
+// The warp keeps a stack of cells whose decision is already known (top =
+// next in depth-first order). Each step emits the run of accepted / leaf
+// entries at the top, in order, and replaces up to four of the open entries
+// among the next 32 by their children -- replacing an entry in place by its
+// children keeps the depth-first order, whichever entries are expanded
+// first. The children of an expanded cell come from one 256-byte block of
+// walk records (written by the moments kernel), eight lanes per cell, so an
+// expansion costs one coalesced load. Two passes: counts, then (after a
+// scan) the fill.
 //
 // The opening criterion is evaluated in FP32 without contraction: with d the
 // distance from the cell's centre of mass to the group's bounding box (0
@@ -21,7 +25,8 @@ namespace {
 
 constexpr int kWalkWarps = 4;
 constexpr int kWalkThreads = 32 * kWalkWarps;
-constexpr int kStack = 8 * (kLevels + 2);
+constexpr int kStack = 512;  // entries per warp; >= 8 * 23 + 4 * 32 needed
+constexpr int kExpand = 4;   // cells expanded per step at most
 constexpr uint32_t kOpen = 0u, kAccept = 1u, kLeaf = 2u;
 
 struct WalkArgs {
@@ -30,7 +35,7 @@ struct WalkArgs {
   const uint32_t *g_first;
   const float4 *node_f;
   const uint2 *node_i;
-  const uint32_t *child;
+  const uint4 *block;
   float theta2;
   uint32_t *cnt_e, *cnt_s, *gself;
   const uint64_t *off_e, *off_s;
@@ -46,25 +51,33 @@ __device__ __forceinline__ float sep_axis(float c, float lo, float hi) {
   return d;
 }
 
-__device__ __forceinline__ uint32_t decide(const float *bmin, const float *bmax, float4 nf,
-                                           uint2 ni, float theta2) {
-  const float dx = sep_axis(nf.x, bmin[0], bmax[0]);
-  const float dy = sep_axis(nf.y, bmin[1], bmax[1]);
-  const float dz = sep_axis(nf.z, bmin[2], bmax[2]);
+__device__ __forceinline__ uint32_t decide(const float *bmin, const float *bmax, float cx,
+                                           float cy, float cz, float s2, bool leaf,
+                                           float theta2) {
+  const float dx = sep_axis(cx, bmin[0], bmax[0]);
+  const float dy = sep_axis(cy, bmin[1], bmax[1]);
+  const float dz = sep_axis(cz, bmin[2], bmax[2]);
   float d2 = __fmul_rn(dx, dx);
   d2 = __fadd_rn(d2, __fmul_rn(dy, dy));
   d2 = __fadd_rn(d2, __fmul_rn(dz, dz));
   const float rhs = __fmul_rn(theta2, d2);
-  if (nf.w < rhs) return kAccept;
-  return (ni.y >> 31) ? kLeaf : kOpen;
+  if (s2 < rhs) return kAccept;
+  return leaf ? kLeaf : kOpen;
+}
+
+// Stack entry: x = cell id (open / accepted) or first particle (leaf);
+// y = decision << 30 | particle count (leaf).
+__device__ __forceinline__ uint2 make_entry(uint32_t dec, uint32_t id, uint32_t first,
+                                            uint32_t count) {
+  return dec == kLeaf ? make_uint2(first, (dec << 30) | count) : make_uint2(id, dec << 30);
 }
 
 template <bool FILL>
 __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
-  __shared__ uint32_t stk_all[kWalkWarps][kStack];
+  __shared__ uint2 stk_all[kWalkWarps][kStack];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
-  uint32_t *stk = stk_all[wib];
+  uint2 *stk = stk_all[wib];
   for (int64_t g = (int64_t)blockIdx.x * kWalkWarps + wib; g < a.n_groups;
        g += (int64_t)gridDim.x * kWalkWarps) {
     float bmin[3], bmax[3];
@@ -77,7 +90,12 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
     const uint64_t be = FILL ? a.off_e[g] : 0, bs = FILL ? a.off_s[g] : 0;
     uint64_t ne = 0, ns = 0;
     bool self = false;
-    if (lane == 0) stk[0] = 0u | (decide(bmin, bmax, a.node_f[0], a.node_i[0], a.theta2) << 30);
+    if (lane == 0) {
+      const float4 nf = a.node_f[0];
+      const uint2 ni = a.node_i[0];
+      const uint32_t d = decide(bmin, bmax, nf.x, nf.y, nf.z, nf.w, (ni.y >> 31) != 0, a.theta2);
+      stk[0] = make_entry(d, 0u, ni.x, ni.y & 0x7fffffffu);
+    }
     int sp = 1;
     uint32_t iters = 0;
     __syncwarp();
@@ -87,23 +105,18 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
         break;
       }
       const int nv = sp < 32 ? sp : 32;
-      const uint32_t e = lane < nv ? stk[sp - 1 - lane] : 0u;
-      const uint32_t dec = e >> 30, cid = e & 0x3fffffffu;
+      const uint2 e = lane < nv ? stk[sp - 1 - lane] : make_uint2(0u, 0u);
+      const uint32_t dec = e.y >> 30;
       const unsigned om = __ballot_sync(0xffffffffu, lane < nv && dec == kOpen);
       const int f = om ? __ffs(om) - 1 : nv;
-      const bool emit = lane < f;
-      const bool acc = emit && dec == kAccept;
-      const bool lf = emit && dec == kLeaf;
+      // ---- emit the decided run at the top, in order ----
+      const bool acc = lane < f && dec == kAccept;
+      const bool lf = lane < f && dec == kLeaf;
       const unsigned am = __ballot_sync(0xffffffffu, acc);
-      if (FILL && acc) a.spj[bs + ns + __popc(am & lt)] = cid;
+      if (FILL && acc) a.spj[bs + ns + __popc(am & lt)] = e.x;
       ns += __popc(am);
-      uint32_t lfirst = 0, lcnt = 0;
-      if (lf) {
-        const uint2 ni = a.node_i[cid];
-        lfirst = ni.x;
-        lcnt = ni.y & 0x7fffffffu;
-        if (gfirst >= lfirst && gfirst - lfirst < lcnt) self = true;
-      }
+      const uint32_t lfirst = lf ? e.x : 0u, lcnt = lf ? (e.y & 0x3fffffffu) : 0u;
+      if (lf && gfirst >= lfirst && gfirst - lfirst < lcnt) self = true;
       uint32_t inc = lcnt;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -124,24 +137,78 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
         }
       }
       ne += tot;
-      sp -= f;
-      if (f < nv) {
-        const uint32_t c = __shfl_sync(0xffffffffu, cid, f);
-        sp -= 1;
-        const uint32_t ch = lane < 8 ? a.child[(size_t)c * 8 + lane] : kNone;
-        const bool valid = ch != kNone;
-        uint32_t d = 0;
-        if (valid) d = decide(bmin, bmax, a.node_f[ch], a.node_i[ch], a.theta2);
-        const unsigned vm = __ballot_sync(0xffffffffu, valid);
-        const int nvc = __popc(vm);
-        if (sp + nvc > kStack) {
-          if (lane == 0) atomicOr(a.status, kStWalkStack);
-          break;
-        }
+      if (!om) {  // nothing open among the top entries: all emitted
+        sp -= nv;
         __syncwarp();
-        if (valid) stk[sp + nvc - 1 - __popc(vm & lt)] = ch | (d << 30);
-        sp += nvc;
+        continue;
       }
+      // ---- expand the first E open entries among the top nv ----
+      int E = __popc(om) < kExpand ? __popc(om) : kExpand;
+      // position (lane index) of the q-th open entry
+      unsigned rest = om;
+      int pos_q[kExpand];
+#pragma unroll
+      for (int q = 0; q < kExpand; q++) {
+        pos_q[q] = rest ? __ffs(rest) - 1 : -1;
+        if (rest) rest &= rest - 1;
+      }
+      int last = pos_q[E - 1];
+      // keep the stack bounded: fall back to one expansion near the limit
+      if ((sp - (last + 1)) + 8 * E + (last + 1 - f - E) > kStack) {
+        E = 1;
+        last = pos_q[0];
+      }
+      const int q_me = lane >> 3, c_me = lane & 7;
+      int p_me = -1;
+#pragma unroll
+      for (int q = 0; q < kExpand; q++)
+        if (q == q_me) p_me = pos_q[q];
+      const uint32_t cid_me = __shfl_sync(0xffffffffu, e.x, p_me < 0 ? 0 : p_me);
+      bool valid = false;
+      uint2 child_entry = make_uint2(0u, 0u);
+      if (q_me < E) {
+        const uint4 *blk = a.block + ((size_t)cid_me * 8 + c_me) * 2;
+        const uint4 nf = blk[0], meta = blk[1];
+        valid = meta.z != kNone;
+        if (valid) {
+          const uint32_t d = decide(bmin, bmax, __uint_as_float(nf.x), __uint_as_float(nf.y),
+                                    __uint_as_float(nf.z), __uint_as_float(nf.w),
+                                    (meta.y >> 31) != 0, a.theta2);
+          child_entry = make_entry(d, meta.z, meta.x, meta.y & 0x7fffffffu);
+        }
+      }
+      const unsigned vm = __ballot_sync(0xffffffffu, valid);
+      // output count of each rewritten position [f, last]: children or itself
+      int expanded_q = -1;
+#pragma unroll
+      for (int q = 0; q < kExpand; q++)
+        if (q < E && pos_q[q] == lane) expanded_q = q;
+      uint32_t cnt = 0;
+      if (lane >= f && lane <= last)
+        cnt = expanded_q >= 0 ? __popc((vm >> (8 * expanded_q)) & 0xffu) : 1u;
+      uint32_t oinc = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, oinc, o);
+        if (lane >= o) oinc += t;
+      }
+      const uint32_t K = __shfl_sync(0xffffffffu, oinc, 31);
+      const uint32_t off_me = oinc - cnt;
+      const int spn = sp - (last + 1);
+      if (spn + (int)K > kStack) {
+        if (lane == 0) atomicOr(a.status, kStWalkStack);
+        break;
+      }
+      // output offset of this lane's parent position (child lanes)
+      const uint32_t off_par = __shfl_sync(0xffffffffu, off_me, p_me < 0 ? 0 : p_me);
+      __syncwarp();
+      if (lane >= f && lane <= last && expanded_q < 0) stk[spn + K - 1 - off_me] = e;
+      if (valid) {
+        const unsigned mine = (vm >> (8 * q_me)) & 0xffu;
+        const uint32_t o = off_par + __popc(mine & ((1u << c_me) - 1u));
+        stk[spn + K - 1 - o] = child_entry;
+      }
+      sp = spn + (int)K;
       __syncwarp();
     }
     self = __any_sync(0xffffffffu, self);
@@ -182,14 +249,13 @@ int launch_walk(afd_ctx *c) {
     cudaMemsetAsync(c->spj_off.p, 0, sizeof(uint64_t), c->stream);
     return cudaGetLastError() == cudaSuccess ? AFD_OK : AFD_ERR_CUDA;
   }
-  if (c->n_cells >= (int64_t)1 << 30) return AFD_ERR_LIST_OVERFLOW;
   WalkArgs a;
   a.n_groups = ng;
   a.boxf = ptr<float>(c->g_boxf);
   a.g_first = ptr<uint32_t>(c->g_first);
   a.node_f = ptr<float4>(c->node_f);
   a.node_i = ptr<uint2>(c->node_i);
-  a.child = ptr<uint32_t>(c->c_child);
+  a.block = ptr<uint4>(c->c_block);
   const float th = (float)c->cfg.theta;
   a.theta2 = th * th;
   a.cnt_e = ptr<uint32_t>(c->l_cnt_e);
