@@ -40,6 +40,9 @@ namespace {
 #ifndef AFD_FORCE_FLUSH_PAIRS
 #define AFD_FORCE_FLUSH_PAIRS 16  // pair-iterations per lane between Kahan flushes
 #endif
+#ifndef AFD_FORCE_CHUNK
+#define AFD_FORCE_CHUNK 32  // list entries staged per warp per step (32 or 64)
+#endif
 #ifndef AFD_FORCE_PERSISTENT
 #define AFD_FORCE_PERSISTENT 0  // warps take units from an atomic queue
 #endif
@@ -173,12 +176,16 @@ __device__ __forceinline__ void cp_async_wait() {
 // (double buffer filled by cp.async) and the packed pair layout of the chunk
 // being computed:
 //   P0[p] = (x_2p, x_2p+1, y_2p, y_2p+1), P1[p] = (z_2p, z_2p+1, m_2p, m_2p+1).
+constexpr int kChunk = AFD_FORCE_CHUNK;  // list entries per staged chunk
+constexpr int kPer = kChunk / 32;        // entries staged by each lane
+constexpr int kPairs = kChunk / 2;       // packed pairs per chunk
+
 template <bool QUAD>
 struct WarpStage {
-  float4 rh[2][32], rl[2][32];
-  float4 rq0[QUAD ? 2 : 1][QUAD ? 32 : 1], rq1[QUAD ? 2 : 1][QUAD ? 32 : 1];
-  float4 P0[16], P1[16];
-  float4 jb[QUAD ? 32 : 1], q0[QUAD ? 32 : 1], q1[QUAD ? 32 : 1];
+  float4 rh[2][kChunk], rl[2][kChunk];
+  float4 rq0[QUAD ? 2 : 1][QUAD ? kChunk : 1], rq1[QUAD ? 2 : 1][QUAD ? kChunk : 1];
+  float4 P0[kPairs], P1[kPairs];
+  float4 jb[QUAD ? kChunk : 1], q0[QUAD ? kChunk : 1], q1[QUAD ? kChunk : 1];
   float4 ch, cl;  // origin of the relative coordinates (hi, lo)
 };
 
@@ -206,22 +213,36 @@ __device__ __forceinline__ void kahan_fold(float &s, float &c, f2 v) {
   s = t;
 }
 
-// Issue the asynchronous gather of list entries [base, base + 32) into
-// buffer b (lanes past the end copy nothing).
+// Issue the asynchronous gather of list entries [base, base + kChunk) into
+// buffer b: lane l copies entries base + l + 32 r (lanes past the end copy
+// nothing). j[r] are the entries' indices.
 template <bool QUAD>
-__device__ __forceinline__ void gather(WarpStage<QUAD> &st, int b, int lane, uint64_t k,
-                                       uint64_t o1, uint32_t j, const float4 *hi,
+__device__ __forceinline__ void gather(WarpStage<QUAD> &st, int b, int lane, uint64_t base,
+                                       uint64_t o1, const uint32_t *j, const float4 *hi,
                                        const float4 *lo, const float4 *sq0, const float4 *sq1,
                                        bool quad_list) {
-  if (k < o1) {
-    cp_async16(&st.rh[b][lane], hi + j);
-    cp_async16(&st.rl[b][lane], lo + j);
-    if (QUAD && quad_list) {
-      cp_async16(&st.rq0[b][lane], sq0 + j);
-      cp_async16(&st.rq1[b][lane], sq1 + j);
+#pragma unroll
+  for (int r = 0; r < kPer; r++) {
+    const int slot = lane + 32 * r;
+    if (base + slot < o1) {
+      cp_async16(&st.rh[b][slot], hi + j[r]);
+      cp_async16(&st.rl[b][slot], lo + j[r]);
+      if (QUAD && quad_list) {
+        cp_async16(&st.rq0[b][slot], sq0 + j[r]);
+        cp_async16(&st.rq1[b][slot], sq1 + j[r]);
+      }
     }
   }
   cp_async_commit();
+}
+
+__device__ __forceinline__ void load_idx(uint32_t *j, const uint32_t *idx, uint64_t base,
+                                         uint64_t o1, int lane) {
+#pragma unroll
+  for (int r = 0; r < kPer; r++) {
+    const uint64_t k = base + lane + 32 * r;
+    j[r] = k < o1 ? idx[k] : 0u;
+  }
 }
 
 // One list (EPJ or SPJ) of one group for one warp with S j-streams.
@@ -233,45 +254,56 @@ __device__ __forceinline__ void run_list(WarpStage<QUAD> &st, const Lane<IPT> &l
   if (o0 >= o1) return;
   const int lane = ln.lane;
   const f2 Z0 = pk(0.0f, 0.0f);
-  // prologue: chunk 0 in flight, index of chunk 1 in a register
-  uint32_t j0 = o0 + lane < o1 ? idx[o0 + lane] : 0u;
-  gather<QUAD>(st, 0, lane, o0 + lane, o1, j0, hi, lo, sq0, sq1, quad_list);
-  uint32_t jn = o0 + 32 + lane < o1 ? idx[o0 + 32 + lane] : 0u;
+  // prologue: chunk 0 in flight, indices of chunk 1 in registers
+  uint32_t j0[kPer], jn[kPer];
+  load_idx(j0, idx, o0, o1, lane);
+  gather<QUAD>(st, 0, lane, o0, o1, j0, hi, lo, sq0, sq1, quad_list);
+  load_idx(jn, idx, o0 + kChunk, o1, lane);
   f2 AX[IPT], AY[IPT], AZ[IPT], PP[IPT];
 #pragma unroll
   for (int q = 0; q < IPT; q++) AX[q] = AY[q] = AZ[q] = PP[q] = Z0;
   int pending = 0;  // pair-iterations accumulated since the last Kahan flush
   int b = 0;
-  for (uint64_t base = o0; base < o1; base += 32) {
-    // next chunk in flight, index of the one after in a register
-    const uint64_t nb = base + 32;
-    gather<QUAD>(st, b ^ 1, lane, nb + lane, o1, jn, hi, lo, sq0, sq1, quad_list);
-    jn = nb + 32 + lane < o1 ? idx[nb + 32 + lane] : 0u;
+  for (uint64_t base = o0; base < o1; base += kChunk) {
+    // next chunk in flight, indices of the one after in registers
+    const uint64_t nb = base + kChunk;
+    gather<QUAD>(st, b ^ 1, lane, nb, o1, jn, hi, lo, sq0, sq1, quad_list);
+    load_idx(jn, idx, nb + kChunk, o1, lane);
     cp_async_wait<1>();  // this lane's copies of the current chunk have landed
-    // relative coordinates of this lane's j (far, massless padding past the end)
-    float rx = 1e18f, ry = 1e18f, rz = 1e18f, rm = 0.0f;
-    if (base + lane < o1) {
-      const float4 h = st.rh[b][lane], l = st.rl[b][lane];
-      const float4 ch = st.ch, cl = st.cl;
-      rx = (h.x - ch.x) + (l.x - cl.x);
-      ry = (h.y - ch.y) + (l.y - cl.y);
-      rz = (h.z - ch.z) + (l.z - cl.z);
-      rm = h.w;
+    float rx[kPer], ry[kPer], rz[kPer], rm[kPer];
+    const float4 ch = st.ch, cl = st.cl;
+#pragma unroll
+    for (int r = 0; r < kPer; r++) {
+      // relative coordinates of this lane's j (far, massless padding past the end)
+      const int slot = lane + 32 * r;
+      rx[r] = ry[r] = rz[r] = 1e18f;
+      rm[r] = 0.0f;
+      if (base + slot < o1) {
+        const float4 h = st.rh[b][slot], l = st.rl[b][slot];
+        rx[r] = (h.x - ch.x) + (l.x - cl.x);
+        ry[r] = (h.y - ch.y) + (l.y - cl.y);
+        rz[r] = (h.z - ch.z) + (l.z - cl.z);
+        rm[r] = h.w;
+      }
     }
     __syncwarp();
-    if (QUAD && quad_list) {
-      st.jb[lane] = make_float4(rx, ry, rz, rm);
-      const bool v = base + lane < o1;
-      st.q0[lane] = v ? st.rq0[b][lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-      st.q1[lane] = v ? st.rq1[b][lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-    } else {
-      float *p0 = reinterpret_cast<float *>(&st.P0[lane >> 1]);
-      float *p1 = reinterpret_cast<float *>(&st.P1[lane >> 1]);
-      const int e = lane & 1;
-      p0[e] = rx;
-      p0[2 + e] = ry;
-      p1[e] = rz;
-      p1[2 + e] = rm;
+#pragma unroll
+    for (int r = 0; r < kPer; r++) {
+      const int slot = lane + 32 * r;
+      if (QUAD && quad_list) {
+        st.jb[slot] = make_float4(rx[r], ry[r], rz[r], rm[r]);
+        const bool v = base + slot < o1;
+        st.q0[slot] = v ? st.rq0[b][slot] : make_float4(0.f, 0.f, 0.f, 0.f);
+        st.q1[slot] = v ? st.rq1[b][slot] : make_float4(0.f, 0.f, 0.f, 0.f);
+      } else {
+        float *p0 = reinterpret_cast<float *>(&st.P0[slot >> 1]);
+        float *p1 = reinterpret_cast<float *>(&st.P1[slot >> 1]);
+        const int e = slot & 1;
+        p0[e] = rx[r];
+        p0[2 + e] = ry[r];
+        p1[e] = rz[r];
+        p1[2 + e] = rm[r];
+      }
     }
     __syncwarp();
     if (QUAD && quad_list) {
@@ -282,7 +314,7 @@ __device__ __forceinline__ void run_list(WarpStage<QUAD> &st, const Lane<IPT> &l
         upk(ln.YI[q], yi, dummy);
         upk(ln.ZI[q], zi, dummy);
 #pragma unroll 4
-        for (int t = ln.stream; t < 32; t += S)
+        for (int t = ln.stream; t < kChunk; t += S)
           interact_quad<GUARD>(st.jb[t], st.q0[t], st.q1[t], xi, yi, zi, eps2, px, py, pz, pp);
         AX[q] = add2(AX[q], pk(px, 0.f));
         AY[q] = add2(AY[q], pk(py, 0.f));
@@ -292,7 +324,7 @@ __device__ __forceinline__ void run_list(WarpStage<QUAD> &st, const Lane<IPT> &l
     } else if (AFD_FORCE_ILP2 && S == 1) {
       f2 BX = Z0, BY = Z0, BZ = Z0, BP = Z0;
 #pragma unroll
-      for (int t = 0; t < 16; t += 2) {
+      for (int t = 0; t < kPairs; t += 2) {
         interact2<GUARD>(st.P0[t], st.P1[t], ln.XI[0], ln.YI[0], ln.ZI[0], ln.E2, AX[0], AY[0],
                          AZ[0], PP[0]);
         interact2<GUARD>(st.P0[t + 1], st.P1[t + 1], ln.XI[0], ln.YI[0], ln.ZI[0], ln.E2, BX, BY,
@@ -304,11 +336,11 @@ __device__ __forceinline__ void run_list(WarpStage<QUAD> &st, const Lane<IPT> &l
       PP[0] = add2(PP[0], BP);
     } else {
 #pragma unroll
-      for (int t = ln.stream; t < 16; t += S)
+      for (int t = ln.stream; t < kPairs; t += S)
         interact2<GUARD>(st.P0[t], st.P1[t], ln.XI[0], ln.YI[0], ln.ZI[0], ln.E2, AX[0], AY[0],
                          AZ[0], PP[0]);
     }
-    pending += 16 / S;
+    pending += kPairs / S;
     if (pending >= AFD_FORCE_FLUSH_PAIRS || nb >= o1) {
 #pragma unroll
       for (int q = 0; q < IPT; q++) {
