@@ -19,7 +19,8 @@ n_i * (n_epj + n_spj)) over the timed steps, plus ms per step.
   roofline  the force kernel, ALU-bound: 23 flops per interaction (the
             paper's n_op) / its event-timed duration, against the FP32 peak
             152 SMs x 128 lanes x 2 flops x the median SM clock sampled
-            during the timed region.
+            during the timed region; the FMA rate measured by afd_fp32_peak
+            is reported beside it.
   cpu_baseline  the FP64 CPU oracle on the host cores, bounded sample.
 
 ``--impl reference`` times the oracle itself on the same workload (each step
@@ -54,7 +55,7 @@ FORCE_TRAFFIC_BYTES = None
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=16)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", default="plummer_1m")
@@ -179,7 +180,7 @@ def run_reference(args, wl):
 
     p = ics.make(wl["model"], wl["n"], wl["seed"])
     kw = dict(n_grp=wl["n_grp"], theta=wl["theta"], eps=wl["eps"], quad=wl["quad"])
-    stride = 16
+    stride = 32
     t = None
     tot_i, tot_s = 0.0, 0.0
     for k in range(args.warmup + args.steps):
@@ -316,8 +317,11 @@ def main():
     achieved = FLOPS_PER_INTERACTION * i_launch / (f_ms * 1e-3) / 1e12
     mhz = clocks.get("sm_mhz") or 2070.0
     peak = SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    measured = afd.afd_fp32_peak(local, stream)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": FORCE_TRAFFIC_BYTES,
+                "measured_fp32_fma_tflops": measured,
+                "frac_of_measured_fma": achieved / measured,
                 "kernel": "k_force", "flops_per_interaction": FLOPS_PER_INTERACTION,
                 "interactions_per_launch": i_launch, "launch_ms": f_ms,
                 "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 x {mhz:.0f} MHz "

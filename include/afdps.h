@@ -248,6 +248,13 @@ int afd_last_force_ms(afd_ctx *ctx, float *ms);
 int afd_root_cell_static(const double *x, const double *y, const double *z, const double *m,
                          int64_t n, double *root_out, int *nonfinite_out, void *stream);
 
+/* Measured FP32 rate of device `device` in TFLOP/s: the F_GPU of the force
+ * kernel model (Appendix A, Eq. model_kernel), from a kernel of independent
+ * packed FP32 FMA chains timed with CUDA events on `stream` (best of three
+ * launches; synchronises; allocates 4 bytes of scratch). Reported next to the
+ * nominal peak (SMs x 128 lanes x 2 flops x clock) in benchmarks. */
+int afd_fp32_peak(int device, void *stream, double *tflops_out);
+
 /* Human-readable text for a status code (static storage). */
 const char *afd_error_string(int status);
 

@@ -88,6 +88,7 @@ def lib():
         "afd_last_force_ms": ([_VP, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
         "afd_error_string": ([ctypes.c_int], ctypes.c_char_p),
         "afd_root_cell_static": ([_VP, _VP, _VP, _VP, _I64, _VP, _VP, _VP], ctypes.c_int),
+        "afd_fp32_peak": ([ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -266,6 +267,13 @@ def afd_root_cell_static(x, y, z, m, root_out, nonfinite_out, stream=None):
     _check(lib().afd_root_cell_static(*p, n, _dptr(root_out, torch.float64, 4, "root_out"),
                                       _dptr(nonfinite_out, torch.int32, 1, "nonfinite_out"),
                                       _stream_ptr(stream)), "afd_root_cell_static")
+
+
+def afd_fp32_peak(device: int = 0, stream=None) -> float:
+    """Measured FP32 FMA rate of the device in TFLOP/s."""
+    v = ctypes.c_double(0.0)
+    _check(lib().afd_fp32_peak(int(device), _stream_ptr(stream), ctypes.byref(v)), "afd_fp32_peak")
+    return float(v.value)
 
 
 # ---------------------------------------------------------------- convenience
