@@ -88,6 +88,16 @@ int afd_create(afd_ctx **out, const afd_config *cfg, int device, void *stream);
 /* Free every device buffer of the context (synchronises its stream). */
 void afd_destroy(afd_ctx *ctx);
 
+/* Several independent systems in one context (the batched multiwalk: every
+ * kernel, the force kernel included, runs once over all systems). Particles
+ * [sys_off[s], sys_off[s+1]) of the arrays later given to afd_tree_build form
+ * system s, with its own root cell, keys, tree and groups; lists never cross
+ * systems. sys_off: host, n_sys + 1 non-decreasing offsets from 0. n_grp:
+ * host, n_sys group sizes (1 .. 1024), or NULL for the config's n_grp.
+ * n_sys = 1 with sys_off = {0, n} is the single-system default. Invalidates
+ * the tree and lists. Synchronous. */
+int afd_set_systems(afd_ctx *ctx, const int64_t *sys_off, int n_sys, const int32_t *n_grp);
+
 /* Replace the stream later work is queued on. */
 int afd_set_stream(afd_ctx *ctx, void *stream);
 
@@ -172,7 +182,7 @@ int afd_stats(afd_ctx *ctx, int64_t *out);
 /* Copy an internal array to host memory for inspection and parity tests.
  * With host_buf NULL only *bytes is set to the size needed. Synchronises.
  * Items and element types:
- *   ROOT        4 x f64 (centre x, y, z, side L)
+ *   ROOT        systems x 4 x f64 (centre x, y, z, side L)
  *   KEYS        n x u64 sorted Morton keys
  *   PERM        n x u32 caller index of each Morton position
  *   CELL_LEVEL  cells x u32      CELL_FIRST  cells x u32
@@ -183,7 +193,9 @@ int afd_stats(afd_ctx *ctx, int64_t *out);
  *   CELL_QUAD   cells x 6 x f64 (xx yy zz xy xz yz; zeros when monopole)
  *   GROUP_FIRST groups x u32     GROUP_COUNT groups x u32
  *   GROUP_BOX   groups x 6 x f64 (min x y z, max x y z)
- *   GROUP_SELF  groups x u32 (1 when the group's own particles are EPJs)
+ *   GROUP_SELF  groups x u32: 1 + position of the group's first particle in
+ *               its EPJ list (its particles follow contiguously; the force
+ *               kernel skips each particle's own pair there), 0 if absent
  *   EPJ_OFF / SPJ_OFF (groups + 1) x u64, EPJ_IDX / SPJ_IDX entries x u32
  * Cells are numbered in depth-first pre-order, children in Morton order. */
 typedef enum {

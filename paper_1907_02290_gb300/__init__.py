@@ -72,6 +72,7 @@ def lib():
         "afd_create": ([ctypes.POINTER(_VP), ctypes.POINTER(afd_config), ctypes.c_int, _VP], ctypes.c_int),
         "afd_destroy": ([_VP], None),
         "afd_set_stream": ([_VP, _VP], ctypes.c_int),
+        "afd_set_systems": ([_VP, _VP, ctypes.c_int, _VP], ctypes.c_int),
         "afd_tree_build": ([_VP, _VP, _VP, _VP, _VP, _I64], ctypes.c_int),
         "afd_make_interaction_lists": ([_VP, ctypes.c_int], ctypes.c_int),
         "afd_reuse_lists": ([_VP, _VP, _VP, _VP, _VP], ctypes.c_int),
@@ -144,6 +145,15 @@ def afd_destroy(ctx):
 
 def afd_set_stream(ctx, stream):
     _check(lib().afd_set_stream(ctx, _stream_ptr(stream)), "afd_set_stream")
+
+
+def afd_set_systems(ctx, sys_off, n_grp=None):
+    """Declare independent systems: particles [sys_off[s], sys_off[s+1])."""
+    off = np.ascontiguousarray(sys_off, dtype=np.int64)
+    grp = None if n_grp is None else np.ascontiguousarray(n_grp, dtype=np.int32)
+    _check(lib().afd_set_systems(ctx, _VP(off.ctypes.data), int(off.shape[0] - 1),
+                                 None if grp is None else _VP(grp.ctypes.data)),
+           "afd_set_systems")
 
 
 def afd_tree_build(ctx, x, y, z, m):

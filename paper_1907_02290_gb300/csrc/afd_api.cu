@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "afd_internal.cuh"
 
@@ -129,6 +130,7 @@ int tree_build(afd_ctx *c, const double *x, const double *y, const double *z, co
                int64_t n) {
   if (n < 0 || n >= ((int64_t)1 << 30)) return AFD_ERR_ARG;
   if (n > 0 && (!x || !y || !z || !m)) return AFD_ERR_ARG;
+  if (c->n_sys > 1 && n != c->sys_off_h[c->n_sys]) return AFD_ERR_SHAPE;
   c->have_tree = c->have_lists = c->saved = false;
   TRY(launch_root(c, x, y, z, m, n));
   TRY(launch_keys(c, x, y, z, n));
@@ -228,12 +230,39 @@ void afd_destroy(afd_ctx *c) {
                     &c->g_off, &c->g_first, &c->g_count, &c->g_cell, &c->g_box, &c->g_boxf,
                     &c->g_self, &c->u_cnt, &c->u_off, &c->u_info, &c->l_cnt_e,
                     &c->l_cnt_s, &c->epj_off, &c->spj_off, &c->epj, &c->spj, &c->scan_tmp,
-                    &c->hx, &c->hy, &c->hz, &c->hm, &c->hacc};
+                    &c->hx, &c->hy, &c->hz, &c->hm, &c->hacc, &c->sys_off_d,
+                    &c->sys_grp_d, &c->sys_of, &c->sys_s, &c->root_tiles, &c->g_root};
   for (DevBuf *b : bufs) release(*b);
   if (c->pinned) cudaFreeHost(c->pinned);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   delete c;
+}
+
+int afd_set_systems(afd_ctx *c, const int64_t *sys_off, int n_sys, const int32_t *n_grp) {
+  if (!c || !sys_off || n_sys < 1 || n_sys > 65535) return AFD_ERR_ARG;
+  if (sys_off[0] != 0 || sys_off[n_sys] >= ((int64_t)1 << 30)) return AFD_ERR_ARG;
+  for (int s = 0; s < n_sys; s++)
+    if (sys_off[s + 1] < sys_off[s]) return AFD_ERR_ARG;
+  if (n_grp)
+    for (int s = 0; s < n_sys; s++)
+      if (n_grp[s] < 1 || n_grp[s] > 1024) return AFD_ERR_ARG;
+  DeviceGuard g(c->device);
+  c->have_tree = c->have_lists = c->saved = false;
+  c->n_sys = n_sys;
+  c->sys_off_h.assign(sys_off, sys_off + n_sys + 1);
+  if (n_grp) c->sys_grp_h.assign(n_grp, n_grp + n_sys);
+  else c->sys_grp_h.clear();
+  TRY(reserve(c->sys_off_d, sizeof(int64_t) * (size_t)(n_sys + 1)));
+  TRY(cuda_ok(cudaMemcpy(c->sys_off_d.p, sys_off, sizeof(int64_t) * (size_t)(n_sys + 1),
+                         cudaMemcpyHostToDevice)));
+  if (n_grp) {
+    std::vector<uint32_t> gs(n_grp, n_grp + n_sys);
+    TRY(reserve(c->sys_grp_d, sizeof(uint32_t) * (size_t)n_sys));
+    TRY(cuda_ok(cudaMemcpy(c->sys_grp_d.p, gs.data(), sizeof(uint32_t) * (size_t)n_sys,
+                           cudaMemcpyHostToDevice)));
+  }
+  return AFD_OK;
 }
 
 int afd_set_stream(afd_ctx *c, void *stream) {
@@ -397,7 +426,7 @@ int afd_export(afd_ctx *c, int what, void *host_buf, size_t *bytes) {
   const size_t n = (size_t)c->n, nc = (size_t)c->n_cells, ng = (size_t)c->n_groups;
   const bool tree = c->have_tree, lists = c->have_lists;
   switch (what) {
-    case AFD_EXPORT_ROOT: src = c->root.p; sz = tree ? 4 * sizeof(double) : 0; break;
+    case AFD_EXPORT_ROOT: src = c->root.p; sz = tree ? 4 * sizeof(double) * c->n_sys : 0; break;
     case AFD_EXPORT_KEYS: src = c->keys.p; sz = tree ? n * 8 : 0; break;
     case AFD_EXPORT_PERM: src = c->perm.p; sz = tree ? n * 4 : 0; break;
     case AFD_EXPORT_CELL_LEVEL: src = c->c_level.p; sz = tree ? nc * 4 : 0; break;

@@ -12,6 +12,10 @@
 // packed FP32 operations and two MUFU.RSQ per two interactions -- which
 // halves the issue slots of the scalar loop.
 //
+// Self pairs: a group's own particles form one contiguous run of its EPJ
+// list (recorded by the walk); in the chunks holding that run each lane gives
+// its own pair zero mass, so nothing has to be subtracted afterwards.
+//
 // Precision. Positions are FP64 in memory. Coordinates relative to the
 // group origin (the centre of mass of the group's cell) are formed from
 // hi/lo FP32 pairs, (x_hi - c_hi) + (x_lo - c_lo): when x and c are close
@@ -250,7 +254,8 @@ template <bool GUARD, bool QUAD, int S, int IPT>
 __device__ __forceinline__ void run_list(WarpStage<QUAD> &st, const Lane<IPT> &ln, Sums *sm,
                                          const uint32_t *idx, uint64_t o0, uint64_t o1,
                                          const float4 *hi, const float4 *lo, const float4 *sq0,
-                                         const float4 *sq1, bool quad_list, float eps2) {
+                                         const float4 *sq1, bool quad_list, float eps2,
+                                         int64_t self_at) {
   if (o0 >= o1) return;
   const int lane = ln.lane;
   const f2 Z0 = pk(0.0f, 0.0f);
@@ -306,6 +311,9 @@ __device__ __forceinline__ void run_list(WarpStage<QUAD> &st, const Lane<IPT> &l
       }
     }
     __syncwarp();
+    // does some lane's own particle sit in this chunk? (every lane votes)
+    const bool self_here = self_at >= (int64_t)base && self_at < (int64_t)base + kChunk;
+    const bool any_self = __any_sync(0xffffffffu, self_here);
     if (QUAD && quad_list) {
 #pragma unroll
       for (int q = 0; q < IPT; q++) {
@@ -320,6 +328,17 @@ __device__ __forceinline__ void run_list(WarpStage<QUAD> &st, const Lane<IPT> &l
         AY[q] = add2(AY[q], pk(py, 0.f));
         AZ[q] = add2(AZ[q], pk(pz, 0.f));
         PP[q] = add2(PP[q], pk(pp, 0.f));
+      }
+    } else if (any_self) {
+      // a chunk holding some lane's own particle: that pair gets zero mass
+      const int ts = self_here ? (int)(self_at - (int64_t)base) : -1;
+#pragma unroll
+      for (int t = ln.stream; t < kPairs; t += S) {
+        float4 p1 = st.P1[t];
+        if (ts == 2 * t) p1.z = 0.0f;
+        if (ts == 2 * t + 1) p1.w = 0.0f;
+        interact2<GUARD>(st.P0[t], p1, ln.XI[0], ln.YI[0], ln.ZI[0], ln.E2, AX[0], AY[0], AZ[0],
+                         PP[0]);
       }
     } else if (AFD_FORCE_ILP2 && S == 1) {
       f2 BX = Z0, BY = Z0, BZ = Z0, BP = Z0;
@@ -360,11 +379,11 @@ __device__ __forceinline__ void run_list(WarpStage<QUAD> &st, const Lane<IPT> &l
 
 template <bool GUARD, bool QUAD, int S, int IPT>
 __device__ __forceinline__ void run_unit(WarpStage<QUAD> &st, const ForceArgs &a, uint32_t g,
-                                         const Lane<IPT> &ln, Sums *sm) {
+                                         const Lane<IPT> &ln, Sums *sm, int64_t self_at) {
   run_list<GUARD, QUAD, S, IPT>(st, ln, sm, a.epj, a.off_e[g], a.off_e[g + 1], a.jhi, a.jlo,
-                                nullptr, nullptr, false, a.eps2);
+                                nullptr, nullptr, false, a.eps2, self_at);
   run_list<GUARD, QUAD, S, IPT>(st, ln, sm, a.spj, a.off_s[g], a.off_s[g + 1], a.shi, a.slo,
-                                a.sq0, a.sq1, QUAD, a.eps2);
+                                a.sq0, a.sq1, QUAD, a.eps2, -1);
 }
 
 // One work unit with IPT particles per lane and S j-streams: set up the
@@ -386,19 +405,16 @@ __device__ __forceinline__ void unit_body(const ForceArgs &a, WarpStage<QUAD> &s
   }
   uint32_t il[IPT];
   bool active[IPT];
-  float mi[IPT];
 #pragma unroll
   for (int q = 0; q < IPT; q++) {
     il[q] = ioff + (uint32_t)(q * 32 + (lane & (W - 1)));
     active[q] = il[q] < gc;
     float xi = 0.f, yi = 0.f, zi = 0.f;
-    mi[q] = 0.f;
     if (active[q]) {
       const float4 h = a.jhi[gf + il[q]], l = a.jlo[gf + il[q]];
       xi = (h.x - ch.x) + (l.x - cl.x);
       yi = (h.y - ch.y) + (l.y - cl.y);
       zi = (h.z - ch.z) + (l.z - cl.z);
-      mi[q] = h.w;
     }
     ln.XI[q] = pk(xi, xi);
     ln.YI[q] = pk(yi, yi);
@@ -410,8 +426,11 @@ __device__ __forceinline__ void unit_body(const ForceArgs &a, WarpStage<QUAD> &s
   for (int q = 0; q < IPT; q++)
     sm[q].sx = sm[q].sy = sm[q].sz = sm[q].sp = sm[q].cx = sm[q].cy = sm[q].cz = sm[q].cp = 0.0f;
   __syncwarp();
-  run_unit<GUARD, QUAD, S, IPT>(st, a, g, ln, sm);
-  const bool self = !GUARD && a.g_self[g];
+  // EPJ-list position of this lane's own particle (-1: not on the list)
+  const uint32_t gs = a.g_self[g];
+  const int64_t self_at =
+      (gs && active[0]) ? (int64_t)a.off_e[g] + (int64_t)(gs - 1u) + (int64_t)il[0] : -1;
+  run_unit<GUARD, QUAD, S, IPT>(st, a, g, ln, sm, self_at);
 #pragma unroll
   for (int q = 0; q < IPT; q++) {
     float ax = sm[q].sx - sm[q].cx, ay = sm[q].sy - sm[q].cy, az = sm[q].sz - sm[q].cz;
@@ -424,14 +443,7 @@ __device__ __forceinline__ void unit_body(const ForceArgs &a, WarpStage<QUAD> &s
       az += __shfl_xor_sync(0xffffffffu, az, o);
       pot += __shfl_xor_sync(0xffffffffu, pot, o);
     }
-    if (active[q] && ln.stream == 0) {
-      // Remove the self pair (dx = 0 exactly, so it added m_i / eps to phi only).
-      if (self) {
-        const float r2 = fmaf(0.0f, 0.0f, fmaf(0.0f, 0.0f, fmaf(0.0f, 0.0f, a.eps2)));
-        pot -= mi[q] * rsqrt_fast(r2);
-      }
-      a.out[a.perm[gf + il[q]]] = make_float4(ax, ay, az, -pot);
-    }
+    if (active[q] && ln.stream == 0) a.out[a.perm[gf + il[q]]] = make_float4(ax, ay, az, -pot);
   }
 }
 

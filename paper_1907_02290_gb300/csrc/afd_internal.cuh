@@ -7,6 +7,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include "afdps.h"
 
@@ -94,6 +95,18 @@ struct afd_ctx {
   void *pinned = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool force_timed = false;
+
+  // independent systems (a forest): particles [sys_off[s], sys_off[s+1]) form
+  // system s, with its own root cell and group size. n_sys = 1: one system.
+  int n_sys = 1;
+  std::vector<int64_t> sys_off_h{0, 0};
+  std::vector<int32_t> sys_grp_h;
+  afd::DevBuf sys_off_d;   // int64[n_sys + 1]
+  afd::DevBuf sys_grp_d;   // u32[n_sys]
+  afd::DevBuf sys_of;      // u32 per particle, caller order
+  afd::DevBuf sys_s;       // u32 per particle, Morton (sorted) order
+  afd::DevBuf root_tiles;  // int4 per reduction tile (system, begin, end, -)
+  afd::DevBuf g_root;      // u32 per group: root cell of its system
 
   int64_t eval_counter = 0;
   int64_t launches = 0;  // kernels queued by this context so far

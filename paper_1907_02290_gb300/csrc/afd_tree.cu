@@ -7,6 +7,8 @@
 // intrinsics so that no multiply-add is contracted: the results are the
 // IEEE results of the operation sequence stated in each kernel.
 #include <cfloat>
+#include <utility>
+#include <vector>
 
 #include "afd_internal.cuh"
 
@@ -136,6 +138,122 @@ __global__ void __launch_bounds__(kThreads) k_root(const double *__restrict__ x,
   *counter = 0u;  // ready for the next launch
 }
 
+// Root cells of several systems: block b reduces tile b (a particle range
+// inside one system) to partials; then one block per system reduces its
+// tiles. Same root rule as k_root.
+constexpr int kRootTile = 8192;
+
+__global__ void __launch_bounds__(kThreads) k_root_tiles(const double *__restrict__ x,
+                                                         const double *__restrict__ y,
+                                                         const double *__restrict__ z,
+                                                         const double *__restrict__ m,
+                                                         const int4 *__restrict__ tiles,
+                                                         double *__restrict__ part,
+                                                         int *status) {
+  const int4 t = tiles[blockIdx.x];
+  double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+  int bad = 0;
+  for (int64_t i = (int64_t)t.y + threadIdx.x; i < (int64_t)t.z; i += blockDim.x) {
+    const double v[3] = {x[i], y[i], z[i]};
+    bad |= !isfinite(m[i]);
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      bad |= !isfinite(v[d]);
+      lo[d] = fmin(lo[d], v[d]);
+      hi[d] = fmax(hi[d], v[d]);
+    }
+  }
+  __shared__ double sh[kThreads / 32][6];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    lo[d] = warp_min(lo[d]);
+    hi[d] = warp_max(hi[d]);
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, kStNonFinite);
+  if (lane == 0)
+    for (int d = 0; d < 3; d++) {
+      sh[warp][d] = lo[d];
+      sh[warp][3 + d] = hi[d];
+    }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double b[6];
+  for (int d = 0; d < 6; d++) b[d] = sh[0][d];
+  for (int w = 1; w < kThreads / 32; w++)
+    for (int d = 0; d < 3; d++) {
+      b[d] = fmin(b[d], sh[w][d]);
+      b[3 + d] = fmax(b[3 + d], sh[w][3 + d]);
+    }
+  for (int d = 0; d < 6; d++) part[(size_t)blockIdx.x * 6 + d] = b[d];
+}
+
+__global__ void __launch_bounds__(kThreads) k_root_final(const double *__restrict__ part,
+                                                         const int *__restrict__ tile_first,
+                                                         double *__restrict__ root) {
+  const int sys = blockIdx.x;
+  const int t0 = tile_first[sys], t1 = tile_first[sys + 1];
+  double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+  for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x)
+    for (int d = 0; d < 3; d++) {
+      lo[d] = fmin(lo[d], part[(size_t)t * 6 + d]);
+      hi[d] = fmax(hi[d], part[(size_t)t * 6 + 3 + d]);
+    }
+  __shared__ double sh[kThreads / 32][6];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int d = 0; d < 3; d++) {
+    lo[d] = warp_min(lo[d]);
+    hi[d] = warp_max(hi[d]);
+  }
+  if (lane == 0)
+    for (int d = 0; d < 3; d++) {
+      sh[warp][d] = lo[d];
+      sh[warp][3 + d] = hi[d];
+    }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double* r = root + 4 * (size_t)sys;
+  if (t1 == t0) {  // empty system
+    r[0] = r[1] = r[2] = 0.0;
+    r[3] = 1.0;
+    return;
+  }
+  double b[6];
+  for (int d = 0; d < 6; d++) b[d] = sh[0][d];
+  for (int w = 1; w < kThreads / 32; w++)
+    for (int d = 0; d < 3; d++) {
+      b[d] = fmin(b[d], sh[w][d]);
+      b[3 + d] = fmax(b[3 + d], sh[w][3 + d]);
+    }
+  double ext = 0.0;
+  for (int d = 0; d < 3; d++) {
+    r[d] = __dmul_rn(__dadd_rn(b[d], b[3 + d]), 0.5);
+    const double e = __dsub_rn(b[3 + d], b[d]);
+    if (e > ext) ext = e;
+  }
+  const double target = __dmul_rn(ext, 1.000001);
+  double L = 1.0;
+  if (target > 0.0) {
+    while (L < target) L = __dmul_rn(L, 2.0);
+    while (__dmul_rn(L, 0.5) >= target) L = __dmul_rn(L, 0.5);
+  }
+  r[3] = L;
+}
+
+// System of each particle (caller order) from the system offsets.
+__global__ void __launch_bounds__(kThreads) k_sys_of(const int64_t *__restrict__ sys_off, int n_sys,
+                                                     int64_t n, uint32_t *__restrict__ sys_of) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int lo = 0, hi = n_sys;  // last s with sys_off[s] <= i
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (sys_off[mid] <= i) lo = mid;
+    else hi = mid;
+  }
+  sys_of[i] = (uint32_t)lo;
+}
+
 // ---------------------------------------------------------------------------
 // Morton keys: q_d = clamp(floor((x_d - (c_d - L/2)) * 2^21 / L)), bits
 // interleaved x-y-z from the most significant end (63 bits used).
@@ -160,11 +278,13 @@ __device__ __forceinline__ uint32_t grid_coord(double v, double corner, double s
 __global__ void __launch_bounds__(kThreads) k_keys(const double *__restrict__ x,
                                                    const double *__restrict__ y,
                                                    const double *__restrict__ z, int64_t n,
-                                                   const double *__restrict__ root,
+                                                   const double *__restrict__ roots,
+                                                   const uint32_t *__restrict__ sys_of,
                                                    uint64_t *__restrict__ keys,
                                                    uint32_t *__restrict__ perm) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const double *root = roots + (sys_of ? 4 * (size_t)sys_of[i] : 0);
   const double L = root[3];
   const double half = __dmul_rn(L, 0.5);
   const double scale = __ddiv_rn(2097152.0, L);
@@ -186,7 +306,18 @@ constexpr int kSortRounds = 16;
 constexpr int kSortTile = kSortThreads * kSortRounds;
 constexpr int kSortWarps = kSortThreads / 32;
 
+// SYS: the digit is byte (shift / 8) of the payload's system id instead of
+// the key (the extra passes that order several systems).
+template <bool SYS>
+__device__ __forceinline__ uint32_t sort_digit(uint64_t key, uint32_t val, int shift,
+                                               const uint32_t *sys_of) {
+  return SYS ? ((sys_of[val] >> shift) & 255u) : (uint32_t)((key >> shift) & 255u);
+}
+
+template <bool SYS>
 __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint64_t *__restrict__ keys,
+                                                            const uint32_t *__restrict__ vals,
+                                                            const uint32_t *__restrict__ sys_of,
                                                             int64_t n, int shift,
                                                             uint32_t *__restrict__ cnt,
                                                             int num_tiles) {
@@ -196,16 +327,17 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint64_t *__re
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
   for (int k = threadIdx.x; k < kSortTile; k += kSortThreads) {
     const int64_t i = base + k;
-    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    if (i < n) atomicAdd(&h[sort_digit<SYS>(SYS ? 0ull : keys[i], SYS ? vals[i] : 0u, shift, sys_of)], 1u);
   }
   __syncthreads();
   cnt[(int64_t)threadIdx.x * num_tiles + blockIdx.x] = h[threadIdx.x];
 }
 
+template <bool SYS>
 __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
     const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
-    uint32_t *__restrict__ vout, int64_t n, int shift, const uint32_t *__restrict__ off,
-    int num_tiles) {
+    uint32_t *__restrict__ vout, const uint32_t *__restrict__ sys_of, int64_t n, int shift,
+    const uint32_t *__restrict__ off, int num_tiles) {
   __shared__ uint32_t gbase[256];
   __shared__ uint32_t run[256];
   __shared__ uint32_t wcnt[kSortWarps][256];
@@ -219,7 +351,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
     const bool valid = i < n;
     const uint64_t key = valid ? kin[i] : 0ull;
     const uint32_t val = valid ? vin[i] : 0u;
-    const uint32_t digit = valid ? (uint32_t)((key >> shift) & 255u) : 256u;
+    const uint32_t digit = valid ? sort_digit<SYS>(key, val, shift, sys_of) : 256u;
 #pragma unroll
     for (int w = 0; w < kSortWarps; w++) wcnt[w][tid] = 0;
     __syncthreads();
@@ -298,31 +430,54 @@ __device__ __forceinline__ int common_digits(uint64_t a, uint64_t b) {
   return (__clzll((long long)x) - 1) / 3;
 }
 
+// Range [start, end) of the system holding sorted position i.
+__device__ __forceinline__ void sys_range(const uint32_t *sys_s, const int64_t *sys_off,
+                                          int64_t n, int64_t i, int64_t &start, int64_t &end) {
+  if (sys_s) {
+    const uint32_t s = sys_s[i];
+    start = sys_off[s];
+    end = sys_off[s + 1];
+  } else {
+    start = 0;
+    end = n;
+  }
+}
+
+// d_i (255 when i starts its system) and c_j (only where j + n_leaf is in
+// the same system).
 __global__ void __launch_bounds__(kThreads) k_link_dc(const uint64_t *__restrict__ K, int64_t n,
-                                                      int n_leaf, uint8_t *__restrict__ dI,
+                                                      int n_leaf, const uint32_t *__restrict__ sys_s,
+                                                      const int64_t *__restrict__ sys_off,
+                                                      uint8_t *__restrict__ dI,
                                                       uint8_t *__restrict__ cJ) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  int64_t start, end;
+  sys_range(sys_s, sys_off, n, i, start, end);
   const uint64_t ki = K[i];
-  dI[i] = i == 0 ? (uint8_t)255 : (uint8_t)common_digits(K[i - 1], ki);
-  if (i + n_leaf < n) cJ[i] = (uint8_t)common_digits(ki, K[i + n_leaf]);
+  dI[i] = i == start ? (uint8_t)255 : (uint8_t)common_digits(K[i - 1], ki);
+  if (i + n_leaf < end) cJ[i] = (uint8_t)common_digits(ki, K[i + n_leaf]);
 }
 
 __global__ void __launch_bounds__(kThreads) k_link_count(const uint8_t *__restrict__ dI,
                                                          const uint8_t *__restrict__ cJ,
                                                          int64_t n, int n_leaf,
+                                                         const uint32_t *__restrict__ sys_s,
+                                                         const int64_t *__restrict__ sys_off,
                                                          uint8_t *__restrict__ eI,
                                                          uint32_t *__restrict__ cnt,
                                                          unsigned *__restrict__ max_level) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int E = 0;
   if (i < n) {
-    const int64_t lo = i - n_leaf > 0 ? i - n_leaf : 0;
-    const int64_t hi = i < n - n_leaf - 1 ? i : n - n_leaf - 1;
+    int64_t start, end;
+    sys_range(sys_s, sys_off, n, i, start, end);
+    const int64_t lo = i - n_leaf > start ? i - n_leaf : start;
+    const int64_t hi = i < end - n_leaf - 1 ? i : end - n_leaf - 1;
     int mx = -1;
     for (int64_t j = lo; j <= hi; j++) mx = max(mx, (int)cJ[j]);
     E = mx < 0 ? 0 : min(kLevels, mx + 1);
-    const int d = i == 0 ? -1 : (int)dI[i];
+    const int d = dI[i] == 255 ? -1 : (int)dI[i];
     eI[i] = (uint8_t)E;
     cnt[i] = (uint32_t)max(0, E - d);
   }
@@ -343,21 +498,24 @@ __device__ __forceinline__ int64_t lower_bound_key(const uint64_t *K, int64_t lo
 
 __global__ void __launch_bounds__(kThreads) k_link_emit(
     const uint64_t *__restrict__ K, const uint8_t *__restrict__ dI, const uint8_t *__restrict__ eI,
-    const uint32_t *__restrict__ off, int64_t n, uint32_t *__restrict__ level,
+    const uint32_t *__restrict__ off, int64_t n, const uint32_t *__restrict__ sys_s,
+    const int64_t *__restrict__ sys_off, uint32_t *__restrict__ level,
     uint32_t *__restrict__ first, uint32_t *__restrict__ count, uint32_t *__restrict__ skip,
     uint32_t *__restrict__ parent, uint32_t *__restrict__ child) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int d = i == 0 ? -1 : (int)dI[i];
+  int64_t sstart, send;
+  sys_range(sys_s, sys_off, n, i, sstart, send);
+  const int d = dI[i] == 255 ? -1 : (int)dI[i];
   const int E = eI[i];
   const uint64_t ki = K[i];
   for (int l = d + 1; l <= E; l++) {
     const uint32_t id = off[i] + (uint32_t)(l - d - 1);
-    int64_t end = n;
+    int64_t end = send;
     if (l > 0) {
       const int shift = 3 * (kLevels - l);
       const uint64_t P = ki >> shift;
-      end = lower_bound_key(K, i + 1, n, (P + 1) << shift);
+      end = lower_bound_key(K, i + 1, send, (P + 1) << shift);
     }
     level[id] = (uint32_t)l;
     first[id] = (uint32_t)i;
@@ -370,8 +528,8 @@ __global__ void __launch_bounds__(kThreads) k_link_emit(
       } else {
         const int pshift = 3 * (kLevels - l + 1);
         const uint64_t PP = ki >> pshift;
-        const int64_t s = lower_bound_key(K, 0, i, PP << pshift);
-        const int ds = s == 0 ? -1 : (int)dI[s];
+        const int64_t s = lower_bound_key(K, sstart, i, PP << pshift);
+        const int ds = dI[s] == 255 ? -1 : (int)dI[s];
         par = off[s] + (uint32_t)((l - 1) - ds - 1);
       }
       child[(size_t)par * 8 + ((ki >> (3 * (kLevels - l))) & 7u)] = id;
@@ -394,7 +552,8 @@ struct MomArgs {
   const uint32_t *level, *first, *count, *parent, *child;
   const double *xs, *ys, *zs, *ms;
   const uint64_t *keys;
-  const double *root;
+  const double *root;       // 4 doubles per system
+  const uint32_t *sys_s;    // system of each sorted particle (null: one system)
   double *mass, *smom, *com, *quad;
   unsigned *arrive;
   float4 *s_hi, *s_lo, *s_q0, *s_q1, *node_f;
@@ -411,6 +570,7 @@ __device__ __forceinline__ int n_children(const uint32_t *child, uint32_t c) {
 }
 
 __device__ void finish_cell(const MomArgs &a, uint32_t c, double M, const double S[3], bool leaf) {
+  const double *root = a.root + (a.sys_s ? 4 * (size_t)a.sys_s[a.first[c]] : 0);
   double g[3];
   if (M != 0.0) {
     for (int d = 0; d < 3; d++) g[d] = __ddiv_rn(S[d], M);
@@ -423,10 +583,10 @@ __device__ void finish_cell(const MomArgs &a, uint32_t c, double M, const double
       q[1] |= (uint32_t)((prefix >> (3 * k + 1)) & 1u) << k;
       q[2] |= (uint32_t)((prefix >> (3 * k)) & 1u) << k;
     }
-    const double L = a.root[3];
+    const double L = root[3];
     const double s = ldexp(L, -l);
     for (int d = 0; d < 3; d++)
-      g[d] = __dadd_rn(__dsub_rn(a.root[d], __dmul_rn(L, 0.5)), __dmul_rn((double)q[d] + 0.5, s));
+      g[d] = __dadd_rn(__dsub_rn(root[d], __dmul_rn(L, 0.5)), __dmul_rn((double)q[d] + 0.5, s));
   }
   a.mass[c] = M;
   for (int d = 0; d < 3; d++) {
@@ -437,7 +597,7 @@ __device__ void finish_cell(const MomArgs &a, uint32_t c, double M, const double
   for (int d = 0; d < 3; d++) split2(g[d], h[d], lo[d]);
   a.s_hi[c] = make_float4(h[0], h[1], h[2], __double2float_rn(M));
   a.s_lo[c] = make_float4(lo[0], lo[1], lo[2], 0.0f);
-  const float sd = ldexpf(__double2float_rn(a.root[3]), -(int)a.level[c]);
+  const float sd = ldexpf(__double2float_rn(root[3]), -(int)a.level[c]);
   a.node_f[c] = make_float4(h[0], h[1], h[2], __fmul_rn(sd, sd));
   a.node_i[c] = make_uint2(a.first[c], a.count[c] | (leaf ? 0x80000000u : 0u));
 }
@@ -552,14 +712,24 @@ __device__ __forceinline__ uint32_t unit_count(uint32_t cn) { return (cn + 31u) 
 // i-groups: the maximal cells holding at most n_grp particles, in
 // pre-order; a larger leaf is cut into chunks of n_grp.
 // ---------------------------------------------------------------------------
+// Group size of the system holding a cell (its first particle).
+__device__ __forceinline__ uint32_t group_size(uint32_t n_grp, const uint32_t *sys_grp,
+                                               const uint32_t *sys_s, uint32_t first) {
+  return sys_grp ? sys_grp[sys_s[first]] : n_grp;
+}
+
 __global__ void __launch_bounds__(kThreads) k_group_count(int64_t n_cells,
+                                                          const uint32_t *__restrict__ first,
                                                           const uint32_t *__restrict__ count,
                                                           const uint32_t *__restrict__ parent,
                                                           const uint32_t *__restrict__ child,
-                                                          uint32_t n_grp,
+                                                          uint32_t n_grp_all,
+                                                          const uint32_t *__restrict__ sys_grp,
+                                                          const uint32_t *__restrict__ sys_s,
                                                           uint32_t *__restrict__ gcnt) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n_cells) return;
+  const uint32_t n_grp = group_size(n_grp_all, sys_grp, sys_s, first[c]);
   const uint32_t cnt = count[c];
   uint32_t g = 0;
   if (cnt <= n_grp) {
@@ -573,12 +743,18 @@ __global__ void __launch_bounds__(kThreads) k_group_count(int64_t n_cells,
 
 __global__ void __launch_bounds__(kThreads) k_group_fill(
     int64_t n_cells, const uint32_t *__restrict__ first, const uint32_t *__restrict__ count,
-    const uint32_t *__restrict__ gcnt, const uint32_t *__restrict__ goff, uint32_t n_grp,
+    const uint32_t *__restrict__ gcnt, const uint32_t *__restrict__ goff, uint32_t n_grp_all,
+    const uint32_t *__restrict__ sys_grp, const uint32_t *__restrict__ sys_s,
+    const int64_t *__restrict__ sys_off, const uint32_t *__restrict__ cell_off,
     uint32_t *__restrict__ g_first, uint32_t *__restrict__ g_count,
-    uint32_t *__restrict__ g_cell, uint32_t *__restrict__ u_cnt) {
+    uint32_t *__restrict__ g_cell, uint32_t *__restrict__ g_root, uint32_t *__restrict__ u_cnt) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n_cells) return;
   const uint32_t k_n = gcnt[c];
+  if (k_n == 0) return;
+  const uint32_t n_grp = group_size(n_grp_all, sys_grp, sys_s, first[c]);
+  // root cell of the system: the first cell its first particle starts
+  const uint32_t root = sys_s ? cell_off[sys_off[sys_s[first[c]]]] : 0u;
   for (uint32_t k = 0; k < k_n; k++) {
     const uint32_t g = goff[c] + k;
     const uint32_t f = first[c] + k * n_grp;
@@ -587,6 +763,7 @@ __global__ void __launch_bounds__(kThreads) k_group_fill(
     g_first[g] = f;
     g_count[g] = cn;
     g_cell[g] = (uint32_t)c;
+    g_root[g] = root;
     u_cnt[g] = unit_count(cn);
   }
 }
@@ -653,8 +830,46 @@ inline int ck() { return cudaGetLastError() == cudaSuccess ? AFD_OK : AFD_ERR_CU
 
 int launch_root(afd_ctx *c, const double *x, const double *y, const double *z, const double *m,
                 int64_t n) {
-  AFD_TRY(reserve(c->root, sizeof(double) * 4));
+  AFD_TRY(reserve(c->root, sizeof(double) * 4 * (size_t)c->n_sys));
   AFD_TRY(reserve(c->red_part, sizeof(double) * 6 * kRootBlocks));
+  if (c->n_sys > 1) {
+    // tiles of at most kRootTile particles that never cross a system
+    std::vector<int4> tiles;
+    std::vector<int> first(c->n_sys + 1, 0);
+    for (int sy = 0; sy < c->n_sys; sy++) {
+      first[sy] = (int)tiles.size();
+      for (int64_t b = c->sys_off_h[sy]; b < c->sys_off_h[sy + 1]; b += kRootTile) {
+        const int64_t e = b + kRootTile < c->sys_off_h[sy + 1] ? b + kRootTile : c->sys_off_h[sy + 1];
+        tiles.push_back(make_int4(sy, (int)b, (int)e, 0));
+      }
+    }
+    first[c->n_sys] = (int)tiles.size();
+    const size_t tb = sizeof(int4) * tiles.size(), fb = sizeof(int) * first.size();
+    AFD_TRY(reserve(c->root_tiles, tb + fb + 16));
+    AFD_TRY(reserve(c->red_part, sizeof(double) * 6 * (tiles.size() + 1)));
+    AFD_TRY(reserve(c->sys_of, sizeof(uint32_t) * (size_t)(n > 0 ? n : 1)));
+    char *tp = static_cast<char *>(c->root_tiles.p);
+    if ((tb && cudaMemcpyAsync(tp, tiles.data(), tb, cudaMemcpyHostToDevice, c->stream) !=
+                   cudaSuccess) ||
+        cudaMemcpyAsync(tp + tb, first.data(), fb, cudaMemcpyHostToDevice, c->stream) !=
+            cudaSuccess)
+      return AFD_ERR_CUDA;
+    if (!tiles.empty()) {
+      k_root_tiles<<<(unsigned)tiles.size(), kThreads, 0, c->stream>>>(
+          x, y, z, m, reinterpret_cast<const int4 *>(tp), ptr<double>(c->red_part),
+          ptr<int>(c->status));
+      c->launches++;
+    }
+    k_root_final<<<(unsigned)c->n_sys, kThreads, 0, c->stream>>>(
+        ptr<double>(c->red_part), reinterpret_cast<const int *>(tp + tb), ptr<double>(c->root));
+    c->launches++;
+    if (n > 0) {
+      k_sys_of<<<blocks_for(n), kThreads, 0, c->stream>>>(ptr<int64_t>(c->sys_off_d), c->n_sys, n,
+                                                          ptr<uint32_t>(c->sys_of));
+      c->launches++;
+    }
+    return ck();
+  }
   if (n == 0) {
     const double r[4] = {0.0, 0.0, 0.0, 1.0};
     return cudaMemcpyAsync(c->root.p, r, sizeof(r), cudaMemcpyHostToDevice, c->stream) == cudaSuccess
@@ -674,14 +889,23 @@ int launch_keys(afd_ctx *c, const double *x, const double *y, const double *z, i
   AFD_TRY(reserve(c->keys, sizeof(uint64_t) * n));
   AFD_TRY(reserve(c->perm, sizeof(uint32_t) * n));
   if (n == 0) return AFD_OK;
-  k_keys<<<blocks_for(n), kThreads, 0, c->stream>>>(x, y, z, n, ptr<double>(c->root),
-                                                    ptr<uint64_t>(c->keys), ptr<uint32_t>(c->perm));
+  k_keys<<<blocks_for(n), kThreads, 0, c->stream>>>(
+      x, y, z, n, ptr<double>(c->root), c->n_sys > 1 ? ptr<uint32_t>(c->sys_of) : nullptr,
+      ptr<uint64_t>(c->keys), ptr<uint32_t>(c->perm));
   c->launches++;
   return ck();
 }
 
 int launch_sort(afd_ctx *c, int64_t n) {
-  if (n <= 1) return AFD_OK;
+  if (c->n_sys > 1) AFD_TRY(reserve(c->sys_s, sizeof(uint32_t) * (size_t)(n > 0 ? n : 1)));
+  if (n <= 1) {
+    if (c->n_sys > 1 && n == 1) {
+      k_sys_of<<<1, kThreads, 0, c->stream>>>(ptr<int64_t>(c->sys_off_d), c->n_sys, n,
+                                             ptr<uint32_t>(c->sys_s));
+      c->launches++;
+    }
+    return ck();
+  }
   const int num_tiles = (int)((n + kSortTile - 1) / kSortTile);
   const int64_t nc = (int64_t)256 * num_tiles;
   AFD_TRY(reserve(c->keys2, sizeof(uint64_t) * n));
@@ -690,22 +914,44 @@ int launch_sort(afd_ctx *c, int64_t n) {
   AFD_TRY(reserve(c->sort_off, sizeof(uint32_t) * (nc + 1)));
   uint64_t *ka = ptr<uint64_t>(c->keys), *kb = ptr<uint64_t>(c->keys2);
   uint32_t *va = ptr<uint32_t>(c->perm), *vb = ptr<uint32_t>(c->perm2);
-  for (int pass = 0; pass < 8; pass++) {
-    const int shift = 8 * pass;
-    k_sort_hist<<<num_tiles, kSortThreads, 0, c->stream>>>(ka, n, shift,
-                                                            ptr<uint32_t>(c->sort_cnt), num_tiles);
+  // eight passes over the key, then (several systems) one or two passes over
+  // the system id: stable, so the result is ordered by (system, key)
+  const int sys_passes = c->n_sys > 256 ? 2 : (c->n_sys > 1 ? 1 : 0);
+  const uint32_t *sys_of = c->n_sys > 1 ? ptr<uint32_t>(c->sys_of) : nullptr;
+  for (int pass = 0; pass < 8 + sys_passes; pass++) {
+    const bool sys = pass >= 8;
+    const int shift = sys ? 8 * (pass - 8) : 8 * pass;
+    if (sys)
+      k_sort_hist<true><<<num_tiles, kSortThreads, 0, c->stream>>>(
+          ka, va, sys_of, n, shift, ptr<uint32_t>(c->sort_cnt), num_tiles);
+    else
+      k_sort_hist<false><<<num_tiles, kSortThreads, 0, c->stream>>>(
+          ka, va, sys_of, n, shift, ptr<uint32_t>(c->sort_cnt), num_tiles);
     c->launches++;
     AFD_TRY(ck());
     AFD_TRY(scan_u32(c, ptr<uint32_t>(c->sort_cnt), ptr<uint32_t>(c->sort_off), nc));
-    k_sort_scatter<<<num_tiles, kSortThreads, 0, c->stream>>>(
-        ka, va, kb, vb, n, shift, ptr<uint32_t>(c->sort_off), num_tiles);
+    if (sys)
+      k_sort_scatter<true><<<num_tiles, kSortThreads, 0, c->stream>>>(
+          ka, va, kb, vb, sys_of, n, shift, ptr<uint32_t>(c->sort_off), num_tiles);
+    else
+      k_sort_scatter<false><<<num_tiles, kSortThreads, 0, c->stream>>>(
+          ka, va, kb, vb, sys_of, n, shift, ptr<uint32_t>(c->sort_off), num_tiles);
     c->launches++;
     AFD_TRY(ck());
     uint64_t *tk = ka; ka = kb; kb = tk;
     uint32_t *tv = va; va = vb; vb = tv;
   }
-  // eight passes: the result is back in keys / perm
-  return AFD_OK;
+  if ((8 + sys_passes) & 1) {  // the result sits in the ping-pong buffers
+    std::swap(c->keys, c->keys2);
+    std::swap(c->perm, c->perm2);
+  }
+  if (c->n_sys > 1) {
+    // sorted positions keep each system's range
+    k_sys_of<<<blocks_for(n), kThreads, 0, c->stream>>>(ptr<int64_t>(c->sys_off_d), c->n_sys, n,
+                                                        ptr<uint32_t>(c->sys_s));
+    c->launches++;
+  }
+  return ck();
 }
 
 int launch_reorder(afd_ctx *c, const double *x, const double *y, const double *z,
@@ -737,12 +983,15 @@ int launch_link(afd_ctx *c, int64_t n) {
   const int n_leaf = c->cfg.n_leaf;
   unsigned *maxl = ptr<unsigned>(c->u64acc);
   if (cudaMemsetAsync(maxl, 0, sizeof(unsigned), c->stream) != cudaSuccess) return AFD_ERR_CUDA;
-  k_link_dc<<<blocks_for(n), kThreads, 0, c->stream>>>(ptr<uint64_t>(c->keys), n, n_leaf,
-                                                       ptr<uint8_t>(c->lk_d), ptr<uint8_t>(c->lk_c));
+  const uint32_t *sys_s = c->n_sys > 1 ? ptr<uint32_t>(c->sys_s) : nullptr;
+  const int64_t *sys_off = ptr<int64_t>(c->sys_off_d);
+  k_link_dc<<<blocks_for(n), kThreads, 0, c->stream>>>(ptr<uint64_t>(c->keys), n, n_leaf, sys_s,
+                                                       sys_off, ptr<uint8_t>(c->lk_d),
+                                                       ptr<uint8_t>(c->lk_c));
   c->launches++;
   k_link_count<<<blocks_for(n), kThreads, 0, c->stream>>>(
-      ptr<uint8_t>(c->lk_d), ptr<uint8_t>(c->lk_c), n, n_leaf, ptr<uint8_t>(c->lk_e),
-      ptr<uint32_t>(c->lk_cnt), maxl);
+      ptr<uint8_t>(c->lk_d), ptr<uint8_t>(c->lk_c), n, n_leaf, sys_s, sys_off,
+      ptr<uint8_t>(c->lk_e), ptr<uint32_t>(c->lk_cnt), maxl);
   c->launches++;
   AFD_TRY(ck());
   AFD_TRY(scan_u32(c, ptr<uint32_t>(c->lk_cnt), ptr<uint32_t>(c->lk_off), n));
@@ -762,7 +1011,8 @@ int launch_link(afd_ctx *c, int64_t n) {
   if (cudaMemsetAsync(c->c_child.p, 0xff, u * 8, c->stream) != cudaSuccess) return AFD_ERR_CUDA;
   k_link_emit<<<blocks_for(n), kThreads, 0, c->stream>>>(
       ptr<uint64_t>(c->keys), ptr<uint8_t>(c->lk_d), ptr<uint8_t>(c->lk_e),
-      ptr<uint32_t>(c->lk_off), n, ptr<uint32_t>(c->c_level), ptr<uint32_t>(c->c_first),
+      ptr<uint32_t>(c->lk_off), n, sys_s, sys_off, ptr<uint32_t>(c->c_level),
+      ptr<uint32_t>(c->c_first),
       ptr<uint32_t>(c->c_count), ptr<uint32_t>(c->c_skip), ptr<uint32_t>(c->c_parent),
       ptr<uint32_t>(c->c_child));
   c->launches++;
@@ -801,6 +1051,7 @@ int launch_moments(afd_ctx *c, bool child_blocks) {
   a.ms = ptr<double>(c->ms);
   a.keys = ptr<uint64_t>(c->keys);
   a.root = ptr<double>(c->root);
+  a.sys_s = c->n_sys > 1 ? ptr<uint32_t>(c->sys_s) : nullptr;
   a.mass = ptr<double>(c->c_mass);
   a.smom = ptr<double>(c->c_smom);
   a.com = ptr<double>(c->c_com);
@@ -829,9 +1080,12 @@ int launch_groups(afd_ctx *c) {
     return AFD_OK;
   }
   const uint32_t n_grp = (uint32_t)c->cfg.n_grp;
+  const uint32_t *sys_s = c->n_sys > 1 ? ptr<uint32_t>(c->sys_s) : nullptr;
+  const uint32_t *sys_grp = (c->n_sys > 1 && !c->sys_grp_h.empty()) ? ptr<uint32_t>(c->sys_grp_d)
+                                                                     : nullptr;
   k_group_count<<<blocks_for(nc), kThreads, 0, c->stream>>>(
-      nc, ptr<uint32_t>(c->c_count), ptr<uint32_t>(c->c_parent), ptr<uint32_t>(c->c_child), n_grp,
-      ptr<uint32_t>(c->g_cnt));
+      nc, ptr<uint32_t>(c->c_first), ptr<uint32_t>(c->c_count), ptr<uint32_t>(c->c_parent),
+      ptr<uint32_t>(c->c_child), n_grp, sys_grp, sys_s, ptr<uint32_t>(c->g_cnt));
   c->launches++;
   AFD_TRY(ck());
   AFD_TRY(scan_u32(c, ptr<uint32_t>(c->g_cnt), ptr<uint32_t>(c->g_off), nc));
@@ -841,15 +1095,16 @@ int launch_groups(afd_ctx *c) {
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return AFD_ERR_CUDA;
   const int64_t ng = pin[0];
   c->n_groups = ng;
-  for (afd::DevBuf *b : {&c->g_first, &c->g_count, &c->g_cell, &c->g_self, &c->u_cnt})
+  for (afd::DevBuf *b : {&c->g_first, &c->g_count, &c->g_cell, &c->g_root, &c->g_self, &c->u_cnt})
     AFD_TRY(reserve(*b, sizeof(uint32_t) * ng));
   AFD_TRY(reserve(c->u_off, sizeof(uint32_t) * (ng + 1)));
   AFD_TRY(reserve(c->g_box, sizeof(double) * 6 * ng));
   AFD_TRY(reserve(c->g_boxf, sizeof(float) * 6 * ng));
   k_group_fill<<<blocks_for(nc), kThreads, 0, c->stream>>>(
       nc, ptr<uint32_t>(c->c_first), ptr<uint32_t>(c->c_count), ptr<uint32_t>(c->g_cnt),
-      ptr<uint32_t>(c->g_off), n_grp, ptr<uint32_t>(c->g_first), ptr<uint32_t>(c->g_count),
-      ptr<uint32_t>(c->g_cell), ptr<uint32_t>(c->u_cnt));
+      ptr<uint32_t>(c->g_off), n_grp, sys_grp, sys_s, ptr<int64_t>(c->sys_off_d),
+      ptr<uint32_t>(c->lk_off), ptr<uint32_t>(c->g_first), ptr<uint32_t>(c->g_count),
+      ptr<uint32_t>(c->g_cell), ptr<uint32_t>(c->g_root), ptr<uint32_t>(c->u_cnt));
   c->launches++;
   AFD_TRY(ck());
   AFD_TRY(scan_u32(c, ptr<uint32_t>(c->u_cnt), ptr<uint32_t>(c->u_off), ng));

@@ -32,7 +32,7 @@ constexpr uint32_t kOpen = 0u, kAccept = 1u, kLeaf = 2u;
 struct WalkArgs {
   int64_t n_groups;
   const float *boxf;
-  const uint32_t *g_first;
+  const uint32_t *g_first, *g_root;
   const float4 *node_f;
   const uint2 *node_i;
   const uint4 *block;
@@ -89,12 +89,13 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
     const uint32_t gfirst = a.g_first[g];
     const uint64_t be = FILL ? a.off_e[g] : 0, bs = FILL ? a.off_s[g] : 0;
     uint64_t ne = 0, ns = 0;
-    bool self = false;
+    uint32_t self_pos = 0;  // 1 + EPJ-list position of the group's first particle
     if (lane == 0) {
-      const float4 nf = a.node_f[0];
-      const uint2 ni = a.node_i[0];
+      const uint32_t root = a.g_root[g];
+      const float4 nf = a.node_f[root];
+      const uint2 ni = a.node_i[root];
       const uint32_t d = decide(bmin, bmax, nf.x, nf.y, nf.z, nf.w, (ni.y >> 31) != 0, a.theta2);
-      stk[0] = make_entry(d, 0u, ni.x, ni.y & 0x7fffffffu);
+      stk[0] = make_entry(d, root, ni.x, ni.y & 0x7fffffffu);
     }
     int sp = 1;
     uint32_t iters = 0;
@@ -116,7 +117,6 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
       if (FILL && acc) a.spj[bs + ns + __popc(am & lt)] = e.x;
       ns += __popc(am);
       const uint32_t lfirst = lf ? e.x : 0u, lcnt = lf ? (e.y & 0x3fffffffu) : 0u;
-      if (lf && gfirst >= lfirst && gfirst - lfirst < lcnt) self = true;
       uint32_t inc = lcnt;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -124,6 +124,10 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
         if (lane >= o) inc += t;
       }
       const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
+      // the group's own first particle: remember its EPJ-list position (the
+      // group's particles follow it contiguously)
+      if (lf && gfirst >= lfirst && gfirst - lfirst < lcnt)
+        self_pos = (uint32_t)(ne + (inc - lcnt) + (gfirst - lfirst)) + 1u;
       if (FILL) {
         const uint32_t ex = inc - lcnt;
         unsigned lm = __ballot_sync(0xffffffffu, lf);
@@ -211,11 +215,12 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
       sp = spn + (int)K;
       __syncwarp();
     }
-    self = __any_sync(0xffffffffu, self);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) self_pos = max(self_pos, __shfl_xor_sync(0xffffffffu, self_pos, o));
     if (!FILL && lane == 0) {
       a.cnt_e[g] = (uint32_t)ne;
       a.cnt_s[g] = (uint32_t)ns;
-      a.gself[g] = self ? 1u : 0u;
+      a.gself[g] = self_pos;
     }
     __syncwarp();
   }
@@ -253,6 +258,7 @@ int launch_walk(afd_ctx *c) {
   a.n_groups = ng;
   a.boxf = ptr<float>(c->g_boxf);
   a.g_first = ptr<uint32_t>(c->g_first);
+  a.g_root = ptr<uint32_t>(c->g_root);
   a.node_f = ptr<float4>(c->node_f);
   a.node_i = ptr<uint2>(c->node_i);
   a.block = ptr<uint4>(c->c_block);

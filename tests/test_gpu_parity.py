@@ -85,8 +85,13 @@ def check_structure(g, t, quad=False):
     assert np.array_equal(g.export("group_first"), gr["first"].astype(np.uint32))
     assert np.array_equal(g.export("group_count"), gr["count"].astype(np.uint32))
     assert np.array_equal(g.export("group_box").reshape(-1, 6), gr["box"])
-    assert np.array_equal(g.export("group_self"), gr["self_in"].astype(np.uint32))
     eo, e, so, s = t.lists()
+    gself = g.export("group_self")
+    assert np.array_equal(gself > 0, gr["self_in"] > 0)
+    for gi in np.nonzero(gself)[0][::7]:  # the group's own particles, contiguous
+        p0 = eo[gi] + int(gself[gi]) - 1
+        assert np.array_equal(e[p0:p0 + gr["count"][gi]],
+                              np.arange(gr["first"][gi], gr["first"][gi] + gr["count"][gi]))
     assert np.array_equal(g.export("epj_off"), eo.astype(np.uint64))
     assert np.array_equal(g.export("spj_off"), so.astype(np.uint64))
     assert np.array_equal(g.export("epj_idx"), e.astype(np.uint32))
@@ -294,4 +299,87 @@ def test_full_size_plummer_1m(env):
     assert mask.sum() > 5000
     assert rms_rel_acc(a[mask], [r[mask] for r in ref]) <= FORCE_RMS_TOL
     assert rms_rel_pot(a[mask], [r[mask] for r in ref]) <= POT_RMS_TOL
+    g.close()
+
+
+def test_batched_systems_match_per_system_oracle(env):
+    """Several independent systems in one context (one set of launches): each
+    system's root, keys, tree, groups, lists and forces equal those of an
+    oracle run on that system alone (ids shifted by the system's offsets)."""
+    torch, afd, orc = env
+    sizes = [3000, 17, 1, 12000, 5000, 0, 700]
+    n_grp = [64, 8, 64, 128, 32, 16, 256]
+    parts = []
+    for k, n in enumerate(sizes):
+        p = ics.plummer(max(n, 1), 300 + k, virial=0.3 + 0.05 * k)
+        if n == 0:
+            p = ics.Particles(*(np.zeros(0) for _ in range(7)))
+        shift = 5.0 * k  # systems apart in space (independent regardless)
+        parts.append((p.x + shift, p.y - shift, p.z, p.m))
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    X = [np.concatenate([q[i] for q in parts]) for i in range(4)]
+    kw = dict(theta=0.5, eps=1.0 / 256)
+    dev = torch.device("cuda:0")
+    g = afd.Gravity(afd.Config(n_grp=64, **kw), 0, torch.cuda.current_stream())
+    afd.afd_set_systems(g.ctx, off, n_grp)
+    x, y, z, m = (torch.tensor(a, device=dev) for a in X)
+    acc = torch.full((off[-1], 4), float("nan"), dtype=torch.float32, device=dev)
+    g.force_all(x, y, z, m, acc, afd.AFD_MAKE_LIST_FOR_REUSE)
+    torch.cuda.synchronize()
+    a = acc.cpu().numpy().astype(np.float64)
+    roots = g.export("root").reshape(-1, 4)
+    keys, perm = g.export("keys"), g.export("perm")
+    lv, fi, ct = g.export("cell_level"), g.export("cell_first"), g.export("cell_count")
+    pa, sk = g.export("cell_parent"), g.export("cell_skip")
+    gf, gc = g.export("group_first"), g.export("group_count")
+    eo, e, so, s = (g.export(k) for k in ("epj_off", "epj_idx", "spj_off", "spj_idx"))
+    cbase = gbase = 0
+    for k, n in enumerate(sizes):
+        sl = slice(off[k], off[k + 1])
+        q = parts[k]
+        t = orc.Tree(*q, n_grp=n_grp[k], **kw)
+        if n == 0:
+            assert t.sizes()["n_cells"] == 0
+            continue
+        assert np.array_equal(roots[k], t.root())
+        tk, tp = t.order()
+        assert np.array_equal(keys[sl], tk) and np.array_equal(perm[sl].astype(np.int64), tp + off[k])
+        c = t.cells()
+        nc = len(c.level)
+        cs = slice(cbase, cbase + nc)
+        assert np.array_equal(lv[cs], c.level) and np.array_equal(ct[cs], c.count)
+        assert np.array_equal(fi[cs].astype(np.int64), c.first + off[k])
+        assert np.array_equal(sk[cs].astype(np.int64), c.skip + cbase)
+        assert np.array_equal(np.where(pa[cs] == NONE, -1, pa[cs].astype(np.int64) - cbase), c.parent)
+        gr = t.groups()
+        ng = len(gr["first"])
+        gs = slice(gbase, gbase + ng)
+        assert np.array_equal(gf[gs].astype(np.int64), gr["first"] + off[k])
+        assert np.array_equal(gc[gs], gr["count"].astype(np.uint32))
+        teo, te, tso, ts = t.lists()
+        assert np.array_equal(np.diff(eo[gbase:gbase + ng + 1]).astype(np.int64), np.diff(teo))
+        assert np.array_equal(np.diff(so[gbase:gbase + ng + 1]).astype(np.int64), np.diff(tso))
+        assert np.array_equal(e[eo[gbase]:eo[gbase + ng]].astype(np.int64), te + off[k])
+        assert np.array_equal(s[so[gbase]:so[gbase + ng]].astype(np.int64), ts + cbase)
+        ref = t.force()
+        if n > 1:
+            assert rms_rel_acc(a[sl], ref) <= FORCE_RMS_TOL
+            assert rms_rel_pot(a[sl], ref) <= POT_RMS_TOL
+        else:
+            assert np.all(a[sl] == 0)
+        cbase += nc
+        gbase += ng
+    assert cbase == len(lv) and gbase == len(gf)
+    # a reusing step on the batch after a drift
+    x += 1e-3
+    afd.afd_calc_force_all(g.ctx, x, y, z, m, acc, afd.AFD_REUSE_LIST)
+    torch.cuda.synchronize()
+    a2 = acc.cpu().numpy().astype(np.float64)
+    for k, n in enumerate(sizes):
+        if n < 2:
+            continue
+        sl = slice(off[k], off[k + 1])
+        t = orc.Tree(*parts[k], n_grp=n_grp[k], **kw)
+        t.update(parts[k][0] + 1e-3, parts[k][1], parts[k][2], parts[k][3])
+        assert rms_rel_acc(a2[sl], t.force()) <= FORCE_RMS_TOL
     g.close()
