@@ -68,6 +68,10 @@ def workload(name):
     import ics
 
     wl = dict(ics.WORKLOADS[name])
+    if wl["model"] == "batch":
+        _, off, _ = ics.make_batch(wl["n_systems"], wl["seed"])
+        wl["n"] = int(off[-1])
+        wl["sys_off"] = off
     wl.setdefault("n_reuse", 4)
     wl.setdefault("dt", 1.0 / 256)
     wl["name"] = name
@@ -75,6 +79,12 @@ def workload(name):
 
 
 def describe(wl):
+    if wl["model"] == "batch":
+        return (f"{wl['name']}: {wl['n_systems']} Plummer systems (N log-uniform in [2^12, 2^20], "
+                f"virial ratio uniform in [0.3, 0.7]) N_total={wl['n']} eps={wl['eps']:.6g} "
+                f"theta={wl['theta']} n_leaf=16 n_grp autotuned per system, monopole, one launch "
+                f"per kernel over all systems, reusing steps replayed from a CUDA graph, lists "
+                f"reused over {wl['n_reuse']} KDK steps dt={wl['dt']:.6g}")
     return (f"{wl['name']}: {wl['model']} N={wl['n']} eps={wl['eps']:.6g} theta={wl['theta']} "
             f"n_leaf=16 n_grp={wl['n_grp']} {'quadrupole' if wl['quad'] else 'monopole'} "
             f"lists reused over {wl['n_reuse']} KDK steps dt={wl['dt']:.6g}")
@@ -133,6 +143,14 @@ class ClockSampler:
                 "samples": len(mhz)}
 
 
+def particles(wl):
+    import ics
+
+    if wl["model"] == "batch":
+        return ics.make_batch(wl["n_systems"], wl["seed"])[0]
+    return ics.make(wl["model"], wl["n"], wl["seed"])
+
+
 def cpu_baseline(wl, max_groups_frac=0.25):
     """The FP64 oracle on the host cores: one construction step, one reusing
     step, and the force of a fraction of the groups; extrapolated to the
@@ -142,7 +160,14 @@ def cpu_baseline(wl, max_groups_frac=0.25):
     import ics
     import oracle
 
-    p = ics.make(wl["model"], wl["n"], wl["seed"])
+    p = particles(wl)
+    label = wl["name"]
+    if wl["model"] == "batch":  # the largest system stands for the batch
+        off = wl["sys_off"]
+        k = int(np.argmax(np.diff(off)))
+        p = ics.Particles(*(getattr(p, a)[off[k]:off[k + 1]]
+                            for a in ("x", "y", "z", "vx", "vy", "vz", "m")))
+        label = f"{wl['name']} (largest system, N={p.n})"
     kw = dict(n_grp=wl["n_grp"], theta=wl["theta"], eps=wl["eps"], quad=wl["quad"])
     t0 = time.perf_counter()
     t = oracle.Tree(p.x, p.y, p.z, p.m, **kw)
@@ -163,7 +188,7 @@ def cpu_baseline(wl, max_groups_frac=0.25):
     r = wl["n_reuse"]
     window = t_build + (r - 1) * t_update + r * t_force * (i_total / i_sel)
     value = r * i_total / window
-    sample = (f"{wl['name']}: one construction step ({t_build:.2f} s) and one reusing step "
+    sample = (f"{label}: one construction step ({t_build:.2f} s) and one reusing step "
               f"({t_update:.2f} s) on all N, force on every {stride}th group ({t_force:.2f} s, "
               f"{i_sel:.3g} of {i_total:.3g} interactions), extrapolated to a {r}-step window")
     return {"value": value, "unit": "interactions/s", "cores": oracle.num_threads(),
@@ -175,10 +200,14 @@ def run_reference(args, wl):
     """--impl reference: the oracle as it stands, K timed bounded steps."""
     import numpy as np
 
-    import ics
     import oracle
 
-    p = ics.make(wl["model"], wl["n"], wl["seed"])
+    p = particles(wl)
+    if wl["model"] == "batch":  # the largest system stands for the batch
+        off = wl["sys_off"]
+        k = int(np.argmax(np.diff(off)))
+        p = type(p)(*(getattr(p, a)[off[k]:off[k + 1]]
+                      for a in ("x", "y", "z", "vx", "vy", "vz", "m")))
     kw = dict(n_grp=wl["n_grp"], theta=wl["theta"], eps=wl["eps"], quad=wl["quad"])
     stride = 32
     t = None
@@ -247,8 +276,9 @@ def main():
 
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
-    p = ics.make(wl["model"], wl["n"], wl["seed"])
+    stream = torch.cuda.Stream(dev)  # a capturable (non-default) stream
+    torch.cuda.set_stream(stream)
+    p = particles(wl)
     n = p.n
     T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
     x, y, z, vx, vy, vz, m = (T(a) for a in (p.x, p.y, p.z, p.vx, p.vy, p.vz, p.m))
@@ -259,16 +289,29 @@ def main():
     ctx = g.ctx
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     dt, R = wl["dt"], wl["n_reuse"]
+    batch = wl["model"] == "batch"
+    tuned = None
+    if batch:
+        afd.afd_set_systems(ctx, wl["sys_off"])
+        tuned = afd.afd_autotune_n_grp(ctx, x, y, z, m, acc, [32, 64, 128, 256, 512], R,
+                                       n_sys=wl["n_systems"])
 
     afd.afd_calc_force_all(ctx, x, y, z, m, acc, afd.AFD_MAKE_LIST_FOR_REUSE)  # evaluation 0
+    if batch:
+        afd.afd_graph_capture_step(ctx, x, y, z, vx, vy, vz, m, acc, dt)
     state = {"k": 1}
 
     def step():
         k = state["k"]
-        afd.afd_kick_drift(ctx, x, y, z, vx, vy, vz, acc, 0.5 * dt, dt)
         mode = afd.AFD_MAKE_LIST_FOR_REUSE if k % R == 0 else afd.AFD_REUSE_LIST
-        afd.afd_calc_force_all(ctx, x, y, z, m, acc, mode)
-        afd.afd_kick(ctx, vx, vy, vz, acc, 0.5 * dt)
+        if batch and mode == afd.AFD_REUSE_LIST:
+            afd.afd_graph_launch(ctx)  # kick-drift, reusing step, force, kick
+        else:
+            afd.afd_kick_drift(ctx, x, y, z, vx, vy, vz, acc, 0.5 * dt, dt)
+            afd.afd_calc_force_all(ctx, x, y, z, m, acc, mode)
+            afd.afd_kick(ctx, vx, vy, vz, acc, 0.5 * dt)
+            if batch:  # buffers may have moved: capture the new reusing step
+                afd.afd_graph_capture_step(ctx, x, y, z, vx, vy, vz, m, acc, dt)
         state["k"] = k + 1
         return mode
 
@@ -292,7 +335,8 @@ def main():
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        force_ms.append(afd.afd_last_force_ms(ctx))
+        if not (batch and mode == afd.AFD_REUSE_LIST):  # graph replays carry no events
+            force_ms.append(afd.afd_last_force_ms(ctx))
         inter.append(g.stats()["interactions"])
         modes.append(mode)
     torch.cuda.synchronize(dev)
@@ -312,7 +356,7 @@ def main():
     value = total_i_all / (total_ms * 1e-3)
 
     # ---- roofline of the force kernel ----
-    f_ms = float(np.mean(force_ms))
+    f_ms = float(np.mean(force_ms)) if force_ms else float("nan")
     i_launch = float(np.mean(inter))
     achieved = FLOPS_PER_INTERACTION * i_launch / (f_ms * 1e-3) / 1e12
     mhz = clocks.get("sm_mhz") or 2070.0
@@ -336,6 +380,8 @@ def main():
                           for a in (p.x, p.y, p.z, p.m))
         hacc = torch.zeros(n, 4, dtype=torch.float32).pin_memory()
         g2 = afd.Gravity(cfg, local, stream)
+        if batch:
+            afd.afd_set_systems(g2.ctx, wl["sys_off"], tuned)
         afd.afd_calc_force_all_host(g2.ctx, hx, hy, hz, hm, hacc, afd.AFD_MAKE_LIST_FOR_REUSE)
         for k in range(1, args.warmup + 1):
             afd.afd_calc_force_all_host(g2.ctx, hx, hy, hz, hm, hacc,
@@ -385,6 +431,7 @@ def main():
         "roofline": roofline,
         "clocks": clocks,
         "gpu_launches": launches,
+        "n_grp_autotuned": None if tuned is None else [int(v) for v in tuned],
         "wall_s_timed_region": t_wall,
     }
     if e2e:

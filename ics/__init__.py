@@ -172,7 +172,19 @@ WORKLOADS = {
                              n_grp=256, quad=True),
     "uniform_4m": dict(model="uniform_sphere", n=1 << 22, seed=5, eps=1.0 / 1024, theta=0.5,
                        n_grp=256, quad=False),
+    # 32 Plummer systems, N log-uniform in [2^12, 2^20], virial ratio in [0.3, 0.7]
+    "batch32": dict(model="batch", n=None, seed=100, eps=1.0 / 512, theta=0.5, n_grp=64,
+                    quad=False, n_systems=32),
 }
+
+
+def make_batch(n_systems: int = 32, seed_base: int = 100):
+    """Concatenated particles of ``batch`` and the system offsets."""
+    systems, sizes, qs = batch(n_systems, seed_base)
+    cat = Particles(*(np.concatenate([getattr(p, a) for p in systems])
+                      for a in ("x", "y", "z", "vx", "vy", "vz", "m")))
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    return cat, off, qs
 
 
 def make(model: str, n: int, seed: int) -> Particles:

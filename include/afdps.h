@@ -168,6 +168,39 @@ int afd_leapfrog(afd_ctx *ctx, double *x, double *y, double *z, double *vx, doub
 int afd_energy(afd_ctx *ctx, const double *vx, const double *vy, const double *vz,
                const double *m, const float *acc4, int64_t n, double *out);
 
+/* Per-system work of the current lists: inter[s] = interactions of system s
+ * (sum over its groups of n_i (n_epj + n_spj)), entries[s] = its list
+ * entries. Host arrays of n_sys int64. Synchronises. */
+int afd_system_stats(afd_ctx *ctx, int64_t *inter, int64_t *entries);
+
+/* Capture one reusing timestep into a CUDA graph owned by the context:
+ * kick-drift (v += a dt/2, x += v dt), the reusing step of Section 4.2
+ * (reorder with the saved permutation, moments), the force kernel on the
+ * saved lists, kick. The arrays (device, caller order) must keep their
+ * addresses for every replay; the context's stream must not be the legacy
+ * default stream; lists must have been made for reuse. Nothing runs at
+ * capture time. Replay with afd_graph_launch; a new construction step
+ * (afd_tree_build with more cells or groups) requires a new capture. */
+int afd_graph_capture_step(afd_ctx *ctx, double *x, double *y, double *z, double *vx,
+                           double *vy, double *vz, const double *m, float *acc4, double dt);
+
+/* Replay the captured timestep on the context's stream (one launch). */
+int afd_graph_launch(afd_ctx *ctx);
+
+/* Autotune the group size n_grp -- the adjustable parameter of Barnes'
+ * vectorisation and of the multiwalk (Sections 3 and 6.1) -- for the
+ * particles x, y, z, m (device, n, the systems set by afd_set_systems). For
+ * each candidate cand[0..n_cand) (1 .. 1024) the tree, the lists and the
+ * force are computed twice and timed with CUDA events on the second pass;
+ * each system gets the candidate minimising t_construction * (its share of
+ * list entries) / n_reuse + t_force * (its share of interactions). The
+ * choice is written to best (host, n_sys ints) and installed as the group
+ * sizes (via afd_set_systems, or the config's n_grp for one system). acc4
+ * (device, n x 4 floats) is scratch. Synchronises; leaves no tree. */
+int afd_autotune_n_grp(afd_ctx *ctx, const double *x, const double *y, const double *z,
+                       const double *m, int64_t n, const int32_t *cand, int n_cand, int n_reuse,
+                       float *acc4, int32_t *best);
+
 /* Wait for the context's stream and return the device status word. */
 int afd_sync(afd_ctx *ctx);
 

@@ -90,6 +90,11 @@ def lib():
         "afd_error_string": ([ctypes.c_int], ctypes.c_char_p),
         "afd_root_cell_static": ([_VP, _VP, _VP, _VP, _I64, _VP, _VP, _VP], ctypes.c_int),
         "afd_fp32_peak": ([ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "afd_system_stats": ([_VP, _VP, _VP], ctypes.c_int),
+        "afd_graph_capture_step": ([_VP] + [_VP] * 8 + [_D], ctypes.c_int),
+        "afd_graph_launch": ([_VP], ctypes.c_int),
+        "afd_autotune_n_grp": ([_VP, _VP, _VP, _VP, _VP, _I64, _VP, ctypes.c_int, ctypes.c_int, _VP,
+                                _VP], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -277,6 +282,40 @@ def afd_root_cell_static(x, y, z, m, root_out, nonfinite_out, stream=None):
     _check(lib().afd_root_cell_static(*p, n, _dptr(root_out, torch.float64, 4, "root_out"),
                                       _dptr(nonfinite_out, torch.int32, 1, "nonfinite_out"),
                                       _stream_ptr(stream)), "afd_root_cell_static")
+
+
+def afd_system_stats(ctx, n_sys):
+    """Per-system (interactions, list entries) of the current lists."""
+    inter = np.zeros(n_sys, np.int64)
+    entries = np.zeros(n_sys, np.int64)
+    _check(lib().afd_system_stats(ctx, _VP(inter.ctypes.data), _VP(entries.ctypes.data)),
+           "afd_system_stats")
+    return inter, entries
+
+
+def afd_graph_capture_step(ctx, x, y, z, vx, vy, vz, m, acc4, dt):
+    import torch
+    n = x.numel()
+    p = [_dptr(a, torch.float64, n) for a in (x, y, z, vx, vy, vz, m)]
+    _check(lib().afd_graph_capture_step(ctx, *p, _dptr(acc4, torch.float32, 4 * n), float(dt)),
+           "afd_graph_capture_step")
+
+
+def afd_graph_launch(ctx):
+    _check(lib().afd_graph_launch(ctx), "afd_graph_launch")
+
+
+def afd_autotune_n_grp(ctx, x, y, z, m, acc4, candidates, n_reuse, n_sys=1):
+    """Autotune n_grp per system; returns the chosen sizes (installed)."""
+    import torch
+    n = x.numel()
+    p = [_dptr(a, torch.float64, n, nm) for a, nm in zip((x, y, z, m), "xyzm")]
+    cand = np.ascontiguousarray(candidates, dtype=np.int32)
+    best = np.zeros(n_sys, np.int32)
+    _check(lib().afd_autotune_n_grp(ctx, *p, n, _VP(cand.ctypes.data), int(cand.shape[0]),
+                                    int(n_reuse), _dptr(acc4, torch.float32, 4 * n, "acc4"),
+                                    _VP(best.ctypes.data)), "afd_autotune_n_grp")
+    return best
 
 
 def afd_fp32_peak(device: int = 0, stream=None) -> float:

@@ -185,6 +185,31 @@ int calc_force_all(afd_ctx *c, const double *x, const double *y, const double *z
 
 inline unsigned nblocks(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
+int kick_drift_launch(afd_ctx *c, double *x, double *y, double *z, double *vx, double *vy,
+                      double *vz, const float *acc4, int64_t n, double dtk, double dtd) {
+  if (n == 0) return AFD_OK;
+  k_kick_drift<<<nblocks(n), kThreads, 0, c->stream>>>(
+      x, y, z, vx, vy, vz, reinterpret_cast<const float4 *>(acc4), n, dtk, dtd);
+  c->launches++;
+  return cuda_ok(cudaGetLastError());
+}
+
+int kick_launch(afd_ctx *c, double *vx, double *vy, double *vz, const float *acc4, int64_t n,
+                double dtk) {
+  if (n == 0) return AFD_OK;
+  k_kick<<<nblocks(n), kThreads, 0, c->stream>>>(vx, vy, vz,
+                                                 reinterpret_cast<const float4 *>(acc4), n, dtk);
+  c->launches++;
+  return cuda_ok(cudaGetLastError());
+}
+
+void graph_release(afd_ctx *c) {
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->graph_exec = nullptr;
+  c->graph = nullptr;
+}
+
 }  // namespace
 
 extern "C" {
@@ -221,6 +246,7 @@ void afd_destroy(afd_ctx *c) {
   if (!c) return;
   DeviceGuard g(c->device);
   cudaStreamSynchronize(c->stream);
+  graph_release(c);
   DevBuf *bufs[] = {&c->root, &c->status, &c->red_part, &c->red_count, &c->u64acc, &c->keys,
                     &c->keys2, &c->perm, &c->perm2, &c->sort_cnt, &c->sort_off, &c->xs, &c->ys,
                     &c->zs, &c->ms, &c->jhi, &c->jlo, &c->lk_d, &c->lk_c, &c->lk_e, &c->lk_cnt,
@@ -338,10 +364,7 @@ int afd_kick_drift(afd_ctx *c, double *x, double *y, double *z, double *vx, doub
   if (n == 0) return AFD_OK;
   if (!x || !y || !z || !vx || !vy || !vz || !acc4) return AFD_ERR_ARG;
   DeviceGuard g(c->device);
-  k_kick_drift<<<nblocks(n), kThreads, 0, c->stream>>>(
-      x, y, z, vx, vy, vz, reinterpret_cast<const float4 *>(acc4), n, dt_kick, dt_drift);
-  c->launches++;
-  return cuda_ok(cudaGetLastError());
+  return kick_drift_launch(c, x, y, z, vx, vy, vz, acc4, n, dt_kick, dt_drift);
 }
 
 int afd_kick(afd_ctx *c, double *vx, double *vy, double *vz, const float *acc4, int64_t n,
@@ -350,11 +373,7 @@ int afd_kick(afd_ctx *c, double *vx, double *vy, double *vz, const float *acc4, 
   if (n == 0) return AFD_OK;
   if (!vx || !vy || !vz || !acc4) return AFD_ERR_ARG;
   DeviceGuard g(c->device);
-  k_kick<<<nblocks(n), kThreads, 0, c->stream>>>(vx, vy, vz,
-                                                 reinterpret_cast<const float4 *>(acc4), n,
-                                                 dt_kick);
-  c->launches++;
-  return cuda_ok(cudaGetLastError());
+  return kick_launch(c, vx, vy, vz, acc4, n, dt_kick);
 }
 
 int afd_leapfrog(afd_ctx *c, double *x, double *y, double *z, double *vx, double *vy,
@@ -395,6 +414,129 @@ int afd_energy(afd_ctx *c, const double *vx, const double *vy, const double *vz,
   TRY(cuda_ok(cudaStreamSynchronize(c->stream)));
   out[0] = pin[0];
   out[1] = pin[1];
+  return AFD_OK;
+}
+
+int afd_system_stats(afd_ctx *c, int64_t *inter, int64_t *entries) {
+  if (!c || !inter || !entries) return AFD_ERR_ARG;
+  if (!c->have_lists) return c->have_tree ? AFD_ERR_NO_SAVED_LIST : AFD_ERR_NO_TREE;
+  DeviceGuard g(c->device);
+  DevBuf tmp;
+  const size_t b = sizeof(unsigned long long) * (size_t)c->n_sys;
+  int st = reserve(tmp, 2 * b);
+  if (st == AFD_OK) {
+    unsigned long long *d = ptr<unsigned long long>(tmp);
+    st = launch_sys_stats(c, d, d + c->n_sys);
+    if (st == AFD_OK) st = cuda_ok(cudaStreamSynchronize(c->stream));
+    if (st == AFD_OK) st = cuda_ok(cudaMemcpy(inter, d, b, cudaMemcpyDeviceToHost));
+    if (st == AFD_OK) st = cuda_ok(cudaMemcpy(entries, d + c->n_sys, b, cudaMemcpyDeviceToHost));
+  }
+  release(tmp);
+  return st;
+}
+
+int afd_graph_capture_step(afd_ctx *c, double *x, double *y, double *z, double *vx, double *vy,
+                           double *vz, const double *m, float *acc4, double dt) {
+  if (!c) return AFD_ERR_ARG;
+  if (!c->saved || !c->have_lists) return AFD_ERR_NO_SAVED_LIST;
+  if (c->stream == nullptr) return AFD_ERR_ARG;  // the legacy stream cannot be captured
+  DeviceGuard g(c->device);
+  graph_release(c);
+  const int64_t n = c->n;
+  TRY(cuda_ok(cudaStreamSynchronize(c->stream)));
+  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return AFD_ERR_CUDA;
+  }
+  const int64_t l0 = c->launches;
+  int st = kick_drift_launch(c, x, y, z, vx, vy, vz, acc4, n, 0.5 * dt, dt);
+  if (st == AFD_OK) st = reuse(c, x, y, z, m);
+  if (st == AFD_OK) st = calc_force(c, acc4);
+  if (st == AFD_OK) st = kick_launch(c, vx, vy, vz, acc4, n, 0.5 * dt);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(c->stream, &graph);
+  if (st != AFD_OK || ec != cudaSuccess) {
+    cudaGetLastError();
+    if (graph) cudaGraphDestroy(graph);
+    return st != AFD_OK ? st : AFD_ERR_CUDA;
+  }
+  c->graph = graph;
+  if (cudaGraphInstantiate(&c->graph_exec, graph, 0) != cudaSuccess) {
+    cudaGetLastError();
+    graph_release(c);
+    return AFD_ERR_CUDA;
+  }
+  c->graph_launches = c->launches - l0;
+  c->launches = l0;
+  return AFD_OK;
+}
+
+int afd_graph_launch(afd_ctx *c) {
+  if (!c) return AFD_ERR_ARG;
+  if (!c->graph_exec) return AFD_ERR_NO_SAVED_LIST;
+  DeviceGuard g(c->device);
+  TRY(cuda_ok(cudaGraphLaunch(c->graph_exec, c->stream)));
+  c->launches += c->graph_launches;
+  return AFD_OK;
+}
+
+int afd_autotune_n_grp(afd_ctx *c, const double *x, const double *y, const double *z,
+                       const double *m, int64_t n, const int32_t *cand, int n_cand, int n_reuse,
+                       float *acc4, int32_t *best) {
+  if (!c || !cand || n_cand < 1 || n_reuse < 1 || !best || (n > 0 && !acc4)) return AFD_ERR_ARG;
+  for (int k = 0; k < n_cand; k++)
+    if (cand[k] < 1 || cand[k] > 1024) return AFD_ERR_ARG;
+  DeviceGuard g(c->device);
+  const int ns = c->n_sys;
+  const std::vector<int64_t> off = c->sys_off_h;
+  std::vector<double> cost((size_t)ns * n_cand, 0.0);
+  std::vector<int64_t> inter(ns), entries(ns);
+  cudaEvent_t e[4];
+  for (auto &ev : e)
+    if (cudaEventCreate(&ev) != cudaSuccess) return AFD_ERR_CUDA;
+  int st = AFD_OK;
+  for (int k = 0; k < n_cand && st == AFD_OK; k++) {
+    std::vector<int32_t> grp(ns, cand[k]);
+    if (ns > 1) st = afd_set_systems(c, off.data(), ns, grp.data());
+    else c->cfg.n_grp = cand[k];
+    for (int rep = 0; rep < 2 && st == AFD_OK; rep++) {  // the first pass warms up
+      cudaEventRecord(e[0], c->stream);
+      st = tree_build(c, x, y, z, m, n);
+      if (st == AFD_OK) st = make_lists(c, AFD_MAKE_LIST_FOR_REUSE);
+      cudaEventRecord(e[1], c->stream);
+      if (st == AFD_OK) st = calc_force(c, acc4);
+      cudaEventRecord(e[2], c->stream);
+    }
+    if (st != AFD_OK) break;
+    float t_build = 0.f, t_force = 0.f;
+    cudaEventSynchronize(e[2]);
+    cudaEventElapsedTime(&t_build, e[0], e[1]);
+    cudaEventElapsedTime(&t_force, e[1], e[2]);
+    st = afd_system_stats(c, inter.data(), entries.data());
+    if (st != AFD_OK) break;
+    double it = 0, en = 0;
+    for (int s2 = 0; s2 < ns; s2++) {
+      it += (double)inter[s2];
+      en += (double)entries[s2];
+    }
+    for (int s2 = 0; s2 < ns; s2++) {
+      // measured times shared out by each system's list entries / interactions
+      const double cb = en > 0 ? t_build * (double)entries[s2] / en : 0.0;
+      const double cf = it > 0 ? t_force * (double)inter[s2] / it : 0.0;
+      cost[(size_t)s2 * n_cand + k] = cb / n_reuse + cf;
+    }
+  }
+  for (auto &ev : e) cudaEventDestroy(ev);
+  if (st != AFD_OK) return st;
+  for (int s2 = 0; s2 < ns; s2++) {
+    int kb = 0;
+    for (int k = 1; k < n_cand; k++)
+      if (cost[(size_t)s2 * n_cand + k] < cost[(size_t)s2 * n_cand + kb]) kb = k;
+    best[s2] = cand[kb];
+  }
+  if (ns > 1) return afd_set_systems(c, off.data(), ns, best);
+  c->cfg.n_grp = best[0];
+  c->have_tree = c->have_lists = c->saved = false;
   return AFD_OK;
 }
 

@@ -521,7 +521,11 @@ int launch_force(afd_ctx *c, float *acc4) {
     if (nb > cap) nb = cap;
   }
   const bool guard = !(a.eps2 > 0.0f);
-  cudaEventRecord(c->ev0, c->stream);
+  // timing events only outside stream capture
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(c->stream, &cap);
+  const bool timed = cap == cudaStreamCaptureStatusNone;
+  if (timed) cudaEventRecord(c->ev0, c->stream);
   if (c->cfg.multipole) {
     if (guard) k_force<true, true><<<nb, kForceThreads, 0, c->stream>>>(a);
     else k_force<false, true><<<nb, kForceThreads, 0, c->stream>>>(a);
@@ -531,8 +535,10 @@ int launch_force(afd_ctx *c, float *acc4) {
     k_force<false, false><<<nb, kForceThreads, 0, c->stream>>>(a);
   }
   c->launches++;
-  cudaEventRecord(c->ev1, c->stream);
-  c->force_timed = true;
+  if (timed) {
+    cudaEventRecord(c->ev1, c->stream);
+    c->force_timed = true;
+  }
   return cudaGetLastError() == cudaSuccess ? AFD_OK : AFD_ERR_CUDA;
 }
 

@@ -110,6 +110,11 @@ struct afd_ctx {
 
   int64_t eval_counter = 0;
   int64_t launches = 0;  // kernels queued by this context so far
+
+  // captured reusing timestep (afd_graph_capture_step / afd_graph_launch)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  int64_t graph_launches = 0;  // kernels inside the captured graph
 };
 
 namespace afd {
@@ -136,6 +141,11 @@ int launch_walk(afd_ctx *c);  // lists; sets n_epj, n_spj, interactions (syncs)
 
 // ---- force (afd_force.cu) ----
 int launch_force(afd_ctx *c, float *acc4);
+
+// ---- per-system statistics (afd_walk.cu) ----
+// inter[s] = sum over system s's groups of n_i (n_epj + n_spj); entries[s] =
+// its list entries. Device arrays of n_sys u64, overwritten.
+int launch_sys_stats(afd_ctx *c, unsigned long long *inter, unsigned long long *entries);
 
 // ---- integration (afd_api.cu) ----
 

@@ -239,7 +239,33 @@ __global__ void k_interactions(int64_t n_groups, const uint32_t *__restrict__ g_
   if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
 }
 
+__global__ void k_sys_stats(int64_t n_groups, const uint32_t *__restrict__ g_first,
+                            const uint32_t *__restrict__ g_count, const uint32_t *__restrict__ ce,
+                            const uint32_t *__restrict__ cs, const uint32_t *__restrict__ sys_s,
+                            unsigned long long *inter, unsigned long long *entries) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n_groups) return;
+  const uint32_t sy = sys_s ? sys_s[g_first[g]] : 0u;
+  const unsigned long long e = (unsigned long long)ce[g] + cs[g];
+  atomicAdd(&inter[sy], e * g_count[g]);
+  atomicAdd(&entries[sy], e);
+}
+
 }  // namespace
+
+int launch_sys_stats(afd_ctx *c, unsigned long long *inter, unsigned long long *entries) {
+  const size_t b = sizeof(unsigned long long) * (size_t)c->n_sys;
+  if (cudaMemsetAsync(inter, 0, b, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(entries, 0, b, c->stream) != cudaSuccess)
+    return AFD_ERR_CUDA;
+  if (c->n_groups == 0) return AFD_OK;
+  k_sys_stats<<<(unsigned)((c->n_groups + 255) / 256), 256, 0, c->stream>>>(
+      c->n_groups, ptr<uint32_t>(c->g_first), ptr<uint32_t>(c->g_count),
+      ptr<uint32_t>(c->l_cnt_e), ptr<uint32_t>(c->l_cnt_s),
+      c->n_sys > 1 ? ptr<uint32_t>(c->sys_s) : nullptr, inter, entries);
+  c->launches++;
+  return cudaGetLastError() == cudaSuccess ? AFD_OK : AFD_ERR_CUDA;
+}
 
 int launch_walk(afd_ctx *c) {
   const int64_t ng = c->n_groups;

@@ -383,3 +383,62 @@ def test_batched_systems_match_per_system_oracle(env):
         t.update(parts[k][0] + 1e-3, parts[k][1], parts[k][2], parts[k][3])
         assert rms_rel_acc(a2[sl], t.force()) <= FORCE_RMS_TOL
     g.close()
+
+
+def test_graph_replay_equals_direct_steps(env):
+    """A captured reusing timestep replays exactly what the direct calls do."""
+    torch, afd, _ = env
+    p = ics.plummer(20000, 77)
+    kw = dict(n_grp=64, theta=0.5, eps=1.0 / 256)
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.Stream()
+    dt = 1.0 / 256
+    results = []
+    for use_graph in (False, True):
+        with torch.cuda.stream(stream):
+            g = afd.Gravity(afd.Config(**kw), 0, stream)
+            x, y, z, vx, vy, vz, m = (torch.tensor(a, device=dev) for a in
+                                      (p.x, p.y, p.z, p.vx, p.vy, p.vz, p.m))
+            acc = torch.zeros(p.n, 4, dtype=torch.float32, device=dev)
+            afd.afd_calc_force_all(g.ctx, x, y, z, m, acc, afd.AFD_MAKE_LIST_FOR_REUSE)
+            if use_graph:
+                afd.afd_graph_capture_step(g.ctx, x, y, z, vx, vy, vz, m, acc, dt)
+                for _ in range(3):
+                    afd.afd_graph_launch(g.ctx)
+            else:
+                for _ in range(3):
+                    afd.afd_kick_drift(g.ctx, x, y, z, vx, vy, vz, acc, 0.5 * dt, dt)
+                    afd.afd_calc_force_all(g.ctx, x, y, z, m, acc, afd.AFD_REUSE_LIST)
+                    afd.afd_kick(g.ctx, vx, vy, vz, acc, 0.5 * dt)
+            stream.synchronize()
+            results.append([t.cpu().numpy() for t in (x, y, z, vx, vy, vz, acc)])
+            g.close()
+    for a, b in zip(*results):
+        assert np.array_equal(a, b)
+
+
+def test_autotuner_installs_candidates_and_stays_exact(env):
+    torch, afd, orc = env
+    sizes = [4000, 9000, 600, 2500]
+    parts = [ics.plummer(n, 500 + k) for k, n in enumerate(sizes)]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    X = [np.concatenate([getattr(q, a) for q in parts]) for a in "xyzm"]
+    kw = dict(theta=0.5, eps=1.0 / 256)
+    dev = torch.device("cuda:0")
+    g = afd.Gravity(afd.Config(n_grp=64, **kw), 0, torch.cuda.current_stream())
+    afd.afd_set_systems(g.ctx, off)
+    x, y, z, m = (torch.tensor(a, device=dev) for a in X)
+    acc = torch.zeros(off[-1], 4, dtype=torch.float32, device=dev)
+    cand = [16, 64, 256]
+    best = afd.afd_autotune_n_grp(g.ctx, x, y, z, m, acc, cand, 4, n_sys=len(sizes))
+    assert all(b in cand for b in best)
+    g.force_all(x, y, z, m, acc, afd.AFD_MAKE_LIST_FOR_REUSE)
+    torch.cuda.synchronize()
+    a = acc.cpu().numpy().astype(np.float64)
+    inter, entries = afd.afd_system_stats(g.ctx, len(sizes))
+    for k, q in enumerate(parts):
+        t = orc.Tree(q.x, q.y, q.z, q.m, n_grp=int(best[k]), **kw)
+        assert inter[k] == t.interactions()
+        sl = slice(off[k], off[k + 1])
+        assert rms_rel_acc(a[sl], t.force()) <= FORCE_RMS_TOL
+    g.close()
