@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", default="plummer_1m")
+    ap.add_argument("--far", type=int, choices=(0, 1, 2), default=None,
+                    help="far-field precision of quadrupole superparticles: 0 fp32, 1 bf16, 2 fp16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -85,8 +87,9 @@ def describe(wl):
                 f"theta={wl['theta']} n_leaf=16 n_grp autotuned per system, monopole, one launch "
                 f"per kernel over all systems, reusing steps replayed from a CUDA graph, lists "
                 f"reused over {wl['n_reuse']} KDK steps dt={wl['dt']:.6g}")
+    far = {0: "", 1: " (bf16 far field)", 2: " (fp16 far field)"}[wl.get("far", 0)]
     return (f"{wl['name']}: {wl['model']} N={wl['n']} eps={wl['eps']:.6g} theta={wl['theta']} "
-            f"n_leaf=16 n_grp={wl['n_grp']} {'quadrupole' if wl['quad'] else 'monopole'} "
+            f"n_leaf=16 n_grp={wl['n_grp']} {'quadrupole' + far if wl['quad'] else 'monopole'} "
             f"lists reused over {wl['n_reuse']} KDK steps dt={wl['dt']:.6g}")
 
 
@@ -252,6 +255,8 @@ def run_reference(args, wl):
 def main():
     args = parse()
     wl = workload(args.workload)
+    if args.far is not None:
+        wl["far"] = args.far
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -284,7 +289,7 @@ def main():
     x, y, z, vx, vy, vz, m = (T(a) for a in (p.x, p.y, p.z, p.vx, p.vy, p.vz, p.m))
     acc = torch.zeros(n, 4, dtype=torch.float32, device=dev)
     cfg = afd.Config(eps=wl["eps"], theta=wl["theta"], n_leaf=16, n_grp=wl["n_grp"],
-                     multipole=int(wl["quad"]))
+                     multipole=int(wl["quad"]), far_precision=int(wl.get("far", 0)))
     g = afd.Gravity(cfg, local, stream)
     ctx = g.ctx
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)

@@ -61,6 +61,7 @@ struct ForceArgs {
   const float4 *jhi, *jlo;  // particles, Morton order
   const float4 *shi, *slo;  // cells
   const float4 *sq0, *sq1;  // cell quadrupoles
+  const float4 *nodef;      // cell walk data (s^2 in .w)
   const uint64_t *off_e, *off_s;
   const uint32_t *epj, *spj;
   const uint32_t *perm;
@@ -72,39 +73,6 @@ __device__ __forceinline__ float rsqrt_fast(float x) {
   float r;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
-}
-
-// Quadrupole term of one cell (Q about its COM, r = x_i - COM = -d):
-//   phi -= (1/2) r.Q.r / rs^5,  a += Q r / rs^5 - (5/2) (r.Q.r) r / rs^7.
-template <bool GUARD>
-__device__ __forceinline__ void interact_quad(float4 j, float4 q0, float4 q1, float xi, float yi,
-                                              float zi, float eps2, float &px, float &py,
-                                              float &pz, float &pp) {
-  const float dx = j.x - xi, dy = j.y - yi, dz = j.z - zi;
-  const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-  float rinv = rsqrt_fast(r2);
-  if (GUARD) rinv = r2 > 0.0f ? rinv : 0.0f;
-  const float rinv2 = rinv * rinv;
-  const float mr = j.w * rinv;
-  const float mr3 = mr * rinv2;
-  // monopole
-  px = fmaf(mr3, dx, px);
-  py = fmaf(mr3, dy, py);
-  pz = fmaf(mr3, dz, pz);
-  pp += mr;
-  // quadrupole with r = -d: Q r = -(Q d), r.Q.r = d.Q.d
-  const float qdx = fmaf(q0.x, dx, fmaf(q0.w, dy, q1.x * dz));
-  const float qdy = fmaf(q0.w, dx, fmaf(q0.y, dy, q1.y * dz));
-  const float qdz = fmaf(q1.x, dx, fmaf(q1.y, dy, q0.z * dz));
-  const float dqd = fmaf(dx, qdx, fmaf(dy, qdy, dz * qdz));
-  const float rinv5 = rinv2 * rinv2 * rinv;
-  const float rinv7 = rinv5 * rinv2;
-  // a = -(Q d)/rs^5 + (5/2)(d.Q.d) d / rs^7
-  const float t = 2.5f * dqd * rinv7;
-  px = fmaf(t, dx, fmaf(-rinv5, qdx, px));
-  py = fmaf(t, dy, fmaf(-rinv5, qdy, py));
-  pz = fmaf(t, dz, fmaf(-rinv5, qdz, pz));
-  pp = fmaf(0.5f * dqd, rinv5, pp);
 }
 
 // ---- packed FP32 pairs (two lanes of work in one 64-bit register) ----
@@ -176,6 +144,133 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N));
 }
 
+// Monopole + quadrupole of two cells (even, odd) against one i, packed.
+// With d = COM - x_i (so r = x_i - COM = -d): Q r = -(Q d), r.Q.r = d.Q.d,
+//   a += M d / rs^3 - (Q d) / rs^5 + (5/2)(d.Q.d) d / rs^7,
+//   phi_sum += M / rs + (1/2)(d.Q.d) / rs^5   (phi = -phi_sum).
+template <bool GUARD>
+__device__ __forceinline__ void interact_quad2(float4 a, float4 b, float4 qa, float4 qb,
+                                               float4 qc, f2 XI, f2 YI, f2 ZI, f2 E2, f2 &AX,
+                                               f2 &AY, f2 &AZ, f2 &PP) {
+  const f2 DX = sub2(pk(a.x, a.y), XI);
+  const f2 DY = sub2(pk(a.z, a.w), YI);
+  const f2 DZ = sub2(pk(b.x, b.y), ZI);
+  const f2 R2 = fma2(DX, DX, fma2(DY, DY, fma2(DZ, DZ, E2)));
+  float r0, r1;
+  upk(R2, r0, r1);
+  float q0 = rsqrt_fast(r0), q1 = rsqrt_fast(r1);
+  if (GUARD) {
+    q0 = r0 > 0.0f ? q0 : 0.0f;
+    q1 = r1 > 0.0f ? q1 : 0.0f;
+  }
+  const f2 RI = pk(q0, q1);
+  const f2 RI2 = mul2(RI, RI);
+  const f2 MR = mul2(pk(b.z, b.w), RI);
+  const f2 MR3 = mul2(MR, RI2);
+  const f2 QXX = pk(qa.x, qa.y), QYY = pk(qa.z, qa.w), QZZ = pk(qb.x, qb.y);
+  const f2 QXY = pk(qb.z, qb.w), QXZ = pk(qc.x, qc.y), QYZ = pk(qc.z, qc.w);
+  const f2 QDX = fma2(QXX, DX, fma2(QXY, DY, mul2(QXZ, DZ)));
+  const f2 QDY = fma2(QXY, DX, fma2(QYY, DY, mul2(QYZ, DZ)));
+  const f2 QDZ = fma2(QXZ, DX, fma2(QYZ, DY, mul2(QZZ, DZ)));
+  const f2 DQD = fma2(DX, QDX, fma2(DY, QDY, mul2(DZ, QDZ)));
+  const f2 RI5 = mul2(mul2(RI2, RI2), RI);
+  const f2 RI7 = mul2(RI5, RI2);
+  const f2 K = fma2(mul2(pk(2.5f, 2.5f), DQD), RI7, MR3);  // M/rs^3 + 2.5 dQd/rs^7
+  const f2 NRI5 = sub2(pk(0.0f, 0.0f), RI5);
+  AX = fma2(K, DX, fma2(NRI5, QDX, AX));
+  AY = fma2(K, DY, fma2(NRI5, QDY, AY));
+  AZ = fma2(K, DZ, fma2(NRI5, QDZ, AZ));
+  PP = fma2(mul2(pk(0.5f, 0.5f), DQD), RI5, add2(PP, MR));
+}
+
+// ---- packed half precision (FP16 or BF16) for the far-field quadrupole shape
+template <int FAR>  // 1: bf16x2, 2: f16x2
+__device__ __forceinline__ uint32_t h2_from_f2(f2 v) {
+  float a, b;
+  upk(v, a, b);
+  uint32_t r;
+  if (FAR == 1) asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+  else asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+  return r;
+}
+template <int FAR>
+__device__ __forceinline__ f2 f2_from_h2(uint32_t v) {
+  float a, b;
+  if (FAR == 1) {
+    a = __uint_as_float(v << 16);
+    b = __uint_as_float(v & 0xffff0000u);
+  } else {
+    asm("{.reg .f16 lo, hi; mov.b32 {lo, hi}, %2; cvt.f32.f16 %0, lo; cvt.f32.f16 %1, hi;}"
+        : "=f"(a), "=f"(b) : "r"(v));
+  }
+  return pk(a, b);
+}
+template <int FAR>
+__device__ __forceinline__ uint32_t hfma2(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  if (FAR == 1) asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  else asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+template <int FAR>
+__device__ __forceinline__ uint32_t hmul2(uint32_t a, uint32_t b) {
+  uint32_t d;
+  if (FAR == 1) asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  else asm("mul.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+template <int FAR>
+__device__ __forceinline__ uint32_t hconst2(float v) {
+  return h2_from_f2<FAR>(pk(v, v));
+}
+
+// Monopole + quadrupole of two cells against one i with the quadrupole shape
+// in half precision. Qn = Q / (M s^2) (dimensionless, |Qn| <= 3; the 2^-2l
+// cell-size factor is a power of two) and u = d / rs (|u| <= 1) stay within
+// FP16 / BF16 range whatever the distance; the dimensional factor
+// M s^2 / rs^4 and the accumulation stay FP32:
+//   a += M d / rs^3 + (M s^2 / rs^4) (2.5 (u.Qn.u) u - Qn u)
+//   phi_sum += M / rs + 0.5 (u.Qn.u) M s^2 / rs^3.
+template <bool GUARD, int FAR>
+__device__ __forceinline__ void interact_quad2_half(float4 a, float4 b, uint4 qa, uint2 qb,
+                                                    f2 S2, f2 XI, f2 YI, f2 ZI, f2 E2, f2 &AX,
+                                                    f2 &AY, f2 &AZ, f2 &PP) {
+  const f2 DX = sub2(pk(a.x, a.y), XI);
+  const f2 DY = sub2(pk(a.z, a.w), YI);
+  const f2 DZ = sub2(pk(b.x, b.y), ZI);
+  const f2 R2 = fma2(DX, DX, fma2(DY, DY, fma2(DZ, DZ, E2)));
+  float r0, r1;
+  upk(R2, r0, r1);
+  float q0 = rsqrt_fast(r0), q1 = rsqrt_fast(r1);
+  if (GUARD) {
+    q0 = r0 > 0.0f ? q0 : 0.0f;
+    q1 = r1 > 0.0f ? q1 : 0.0f;
+  }
+  const f2 RI = pk(q0, q1);
+  const f2 RI2 = mul2(RI, RI);
+  const f2 MR = mul2(pk(b.z, b.w), RI);
+  const f2 MR3 = mul2(MR, RI2);
+  // unit vector and the quadrupole shape in half precision
+  const uint32_t UX = h2_from_f2<FAR>(mul2(DX, RI));
+  const uint32_t UY = h2_from_f2<FAR>(mul2(DY, RI));
+  const uint32_t UZ = h2_from_f2<FAR>(mul2(DZ, RI));
+  // qa = (xx, yy, zz, xy), qb = (xz, yz), each an (even, odd) pair
+  const uint32_t QUX = hfma2<FAR>(qa.x, UX, hfma2<FAR>(qa.w, UY, hmul2<FAR>(qb.x, UZ)));
+  const uint32_t QUY = hfma2<FAR>(qa.w, UX, hfma2<FAR>(qa.y, UY, hmul2<FAR>(qb.y, UZ)));
+  const uint32_t QUZ = hfma2<FAR>(qb.x, UX, hfma2<FAR>(qb.y, UY, hmul2<FAR>(qa.z, UZ)));
+  const uint32_t UQU = hfma2<FAR>(UX, QUX, hfma2<FAR>(UY, QUY, hmul2<FAR>(UZ, QUZ)));
+  const uint32_t C = hmul2<FAR>(hconst2<FAR>(2.5f), UQU);
+  const uint32_t NEG = hconst2<FAR>(-1.0f);
+  const f2 BX = f2_from_h2<FAR>(hfma2<FAR>(C, UX, hmul2<FAR>(NEG, QUX)));
+  const f2 BY = f2_from_h2<FAR>(hfma2<FAR>(C, UY, hmul2<FAR>(NEG, QUY)));
+  const f2 BZ = f2_from_h2<FAR>(hfma2<FAR>(C, UZ, hmul2<FAR>(NEG, QUZ)));
+  const f2 SC = mul2(mul2(MR3, S2), RI);  // M s^2 / rs^4
+  AX = fma2(SC, BX, fma2(MR3, DX, AX));
+  AY = fma2(SC, BY, fma2(MR3, DY, AY));
+  AZ = fma2(SC, BZ, fma2(MR3, DZ, AZ));
+  PP = fma2(mul2(mul2(pk(0.5f, 0.5f), f2_from_h2<FAR>(UQU)), MR), mul2(S2, RI2), add2(PP, MR));
+}
+
 // Shared-memory staging of one warp: raw j data of two chunks in flight
 // (double buffer filled by cp.async) and the packed pair layout of the chunk
 // being computed:
@@ -188,8 +283,15 @@ template <bool QUAD>
 struct WarpStage {
   float4 rh[2][kChunk], rl[2][kChunk];
   float4 rq0[QUAD ? 2 : 1][QUAD ? kChunk : 1], rq1[QUAD ? 2 : 1][QUAD ? kChunk : 1];
+  float4 rnf[QUAD ? 2 : 1][QUAD ? kChunk : 1];  // cell walk data (s^2 in .w)
   float4 P0[kPairs], P1[kPairs];
-  float4 jb[QUAD ? kChunk : 1], q0[QUAD ? kChunk : 1], q1[QUAD ? kChunk : 1];
+  // quadrupole pairs: QA = (xx, yy), QB = (zz, xy), QC = (xz, yz), each (even, odd)
+  float4 QA[QUAD ? kPairs : 1], QB[QUAD ? kPairs : 1], QC[QUAD ? kPairs : 1];
+  // half-precision far field: normalised quadrupole pairs (xx, yy, zz, xy), (xz, yz) as
+  // (even, odd) half2 words, and the cell side squared of both cells
+  uint4 HA[QUAD ? kPairs : 1];
+  uint2 HB[QUAD ? kPairs : 1];
+  float2 S2[QUAD ? kPairs : 1];
   float4 ch, cl;  // origin of the relative coordinates (hi, lo)
 };
 
@@ -224,7 +326,7 @@ template <bool QUAD>
 __device__ __forceinline__ void gather(WarpStage<QUAD> &st, int b, int lane, uint64_t base,
                                        uint64_t o1, const uint32_t *j, const float4 *hi,
                                        const float4 *lo, const float4 *sq0, const float4 *sq1,
-                                       bool quad_list) {
+                                       const float4 *nodef, bool quad_list) {
 #pragma unroll
   for (int r = 0; r < kPer; r++) {
     const int slot = lane + 32 * r;
@@ -234,6 +336,7 @@ __device__ __forceinline__ void gather(WarpStage<QUAD> &st, int b, int lane, uin
       if (QUAD && quad_list) {
         cp_async16(&st.rq0[b][slot], sq0 + j[r]);
         cp_async16(&st.rq1[b][slot], sq1 + j[r]);
+        if (nodef) cp_async16(&st.rnf[b][slot], nodef + j[r]);
       }
     }
   }
@@ -250,19 +353,19 @@ __device__ __forceinline__ void load_idx(uint32_t *j, const uint32_t *idx, uint6
 }
 
 // One list (EPJ or SPJ) of one group for one warp with S j-streams.
-template <bool GUARD, bool QUAD, int S, int IPT>
+template <bool GUARD, bool QUAD, int FAR, int S, int IPT>
 __device__ __forceinline__ void run_list(WarpStage<QUAD> &st, const Lane<IPT> &ln, Sums *sm,
                                          const uint32_t *idx, uint64_t o0, uint64_t o1,
                                          const float4 *hi, const float4 *lo, const float4 *sq0,
-                                         const float4 *sq1, bool quad_list, float eps2,
-                                         int64_t self_at) {
+                                         const float4 *sq1, const float4 *nodef, bool quad_list,
+                                         float eps2, int64_t self_at) {
   if (o0 >= o1) return;
   const int lane = ln.lane;
   const f2 Z0 = pk(0.0f, 0.0f);
   // prologue: chunk 0 in flight, indices of chunk 1 in registers
   uint32_t j0[kPer], jn[kPer];
   load_idx(j0, idx, o0, o1, lane);
-  gather<QUAD>(st, 0, lane, o0, o1, j0, hi, lo, sq0, sq1, quad_list);
+  gather<QUAD>(st, 0, lane, o0, o1, j0, hi, lo, sq0, sq1, FAR ? nodef : nullptr, quad_list);
   load_idx(jn, idx, o0 + kChunk, o1, lane);
   f2 AX[IPT], AY[IPT], AZ[IPT], PP[IPT];
 #pragma unroll
@@ -272,7 +375,7 @@ __device__ __forceinline__ void run_list(WarpStage<QUAD> &st, const Lane<IPT> &l
   for (uint64_t base = o0; base < o1; base += kChunk) {
     // next chunk in flight, indices of the one after in registers
     const uint64_t nb = base + kChunk;
-    gather<QUAD>(st, b ^ 1, lane, nb, o1, jn, hi, lo, sq0, sq1, quad_list);
+    gather<QUAD>(st, b ^ 1, lane, nb, o1, jn, hi, lo, sq0, sq1, FAR ? nodef : nullptr, quad_list);
     load_idx(jn, idx, nb + kChunk, o1, lane);
     cp_async_wait<1>();  // this lane's copies of the current chunk have landed
     float rx[kPer], ry[kPer], rz[kPer], rm[kPer];
@@ -295,40 +398,66 @@ __device__ __forceinline__ void run_list(WarpStage<QUAD> &st, const Lane<IPT> &l
 #pragma unroll
     for (int r = 0; r < kPer; r++) {
       const int slot = lane + 32 * r;
+      float *p0 = reinterpret_cast<float *>(&st.P0[slot >> 1]);
+      float *p1 = reinterpret_cast<float *>(&st.P1[slot >> 1]);
+      const int e = slot & 1;
+      p0[e] = rx[r];
+      p0[2 + e] = ry[r];
+      p1[e] = rz[r];
+      p1[2 + e] = rm[r];
       if (QUAD && quad_list) {
-        st.jb[slot] = make_float4(rx[r], ry[r], rz[r], rm[r]);
         const bool v = base + slot < o1;
-        st.q0[slot] = v ? st.rq0[b][slot] : make_float4(0.f, 0.f, 0.f, 0.f);
-        st.q1[slot] = v ? st.rq1[b][slot] : make_float4(0.f, 0.f, 0.f, 0.f);
-      } else {
-        float *p0 = reinterpret_cast<float *>(&st.P0[slot >> 1]);
-        float *p1 = reinterpret_cast<float *>(&st.P1[slot >> 1]);
-        const int e = slot & 1;
-        p0[e] = rx[r];
-        p0[2 + e] = ry[r];
-        p1[e] = rz[r];
-        p1[2 + e] = rm[r];
+        const float4 q0 = v ? st.rq0[b][slot] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 q1 = v ? st.rq1[b][slot] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float *qa = reinterpret_cast<float *>(&st.QA[slot >> 1]);
+        float *qb = reinterpret_cast<float *>(&st.QB[slot >> 1]);
+        float *qc = reinterpret_cast<float *>(&st.QC[slot >> 1]);
+        qa[e] = q0.x;      // xx
+        qa[2 + e] = q0.y;  // yy
+        qb[e] = q0.z;      // zz
+        qb[2 + e] = q0.w;  // xy
+        qc[e] = q1.x;      // xz
+        qc[2 + e] = q1.y;  // yz
+        if (FAR) {
+          // normalised shape Qn = Q / (M s^2) as this lane's half of each pair
+          const float s2c = v ? st.rnf[b][slot].w : 1.0f;
+          const float den = rm[r] * s2c;
+          const float inv = den > 0.0f ? 1.0f / den : 0.0f;
+          const float qn[6] = {q0.x * inv, q0.y * inv, q0.z * inv, q0.w * inv, q1.x * inv,
+                               q1.y * inv};
+          unsigned short hq[6];
+#pragma unroll
+          for (int k = 0; k < 6; k++) {
+            if (FAR == 1) asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(hq[k]) : "f"(qn[k]));
+            else asm("cvt.rn.f16.f32 %0, %1;" : "=h"(hq[k]) : "f"(qn[k]));
+          }
+          unsigned short *ha = reinterpret_cast<unsigned short *>(&st.HA[slot >> 1]);
+          unsigned short *hb = reinterpret_cast<unsigned short *>(&st.HB[slot >> 1]);
+          ha[0 + e] = hq[0];  // xx
+          ha[2 + e] = hq[1];  // yy
+          ha[4 + e] = hq[2];  // zz
+          ha[6 + e] = hq[3];  // xy
+          hb[0 + e] = hq[4];  // xz
+          hb[2 + e] = hq[5];  // yz
+          reinterpret_cast<float *>(&st.S2[slot >> 1])[e] = s2c;
+        }
       }
     }
     __syncwarp();
     // does some lane's own particle sit in this chunk? (every lane votes)
     const bool self_here = self_at >= (int64_t)base && self_at < (int64_t)base + kChunk;
     const bool any_self = __any_sync(0xffffffffu, self_here);
-    if (QUAD && quad_list) {
-#pragma unroll
-      for (int q = 0; q < IPT; q++) {
-        float px = 0.f, py = 0.f, pz = 0.f, pp = 0.f, xi, yi, zi, dummy;
-        upk(ln.XI[q], xi, dummy);
-        upk(ln.YI[q], yi, dummy);
-        upk(ln.ZI[q], zi, dummy);
+    if (QUAD && quad_list && FAR) {
 #pragma unroll 4
-        for (int t = ln.stream; t < kChunk; t += S)
-          interact_quad<GUARD>(st.jb[t], st.q0[t], st.q1[t], xi, yi, zi, eps2, px, py, pz, pp);
-        AX[q] = add2(AX[q], pk(px, 0.f));
-        AY[q] = add2(AY[q], pk(py, 0.f));
-        AZ[q] = add2(AZ[q], pk(pz, 0.f));
-        PP[q] = add2(PP[q], pk(pp, 0.f));
-      }
+      for (int t = ln.stream; t < kPairs; t += S)
+        interact_quad2_half<GUARD, FAR ? FAR : 1>(st.P0[t], st.P1[t], st.HA[t], st.HB[t],
+                                                  pk(st.S2[t].x, st.S2[t].y), ln.XI[0], ln.YI[0],
+                                                  ln.ZI[0], ln.E2, AX[0], AY[0], AZ[0], PP[0]);
+    } else if (QUAD && quad_list) {
+#pragma unroll 4
+      for (int t = ln.stream; t < kPairs; t += S)
+        interact_quad2<GUARD>(st.P0[t], st.P1[t], st.QA[t], st.QB[t], st.QC[t], ln.XI[0],
+                              ln.YI[0], ln.ZI[0], ln.E2, AX[0], AY[0], AZ[0], PP[0]);
     } else if (any_self) {
       // a chunk holding some lane's own particle: that pair gets zero mass
       const int ts = self_here ? (int)(self_at - (int64_t)base) : -1;
@@ -377,18 +506,18 @@ __device__ __forceinline__ void run_list(WarpStage<QUAD> &st, const Lane<IPT> &l
   __syncwarp();
 }
 
-template <bool GUARD, bool QUAD, int S, int IPT>
+template <bool GUARD, bool QUAD, int FAR, int S, int IPT>
 __device__ __forceinline__ void run_unit(WarpStage<QUAD> &st, const ForceArgs &a, uint32_t g,
                                          const Lane<IPT> &ln, Sums *sm, int64_t self_at) {
-  run_list<GUARD, QUAD, S, IPT>(st, ln, sm, a.epj, a.off_e[g], a.off_e[g + 1], a.jhi, a.jlo,
-                                nullptr, nullptr, false, a.eps2, self_at);
-  run_list<GUARD, QUAD, S, IPT>(st, ln, sm, a.spj, a.off_s[g], a.off_s[g + 1], a.shi, a.slo,
-                                a.sq0, a.sq1, QUAD, a.eps2, -1);
+  run_list<GUARD, QUAD, FAR, S, IPT>(st, ln, sm, a.epj, a.off_e[g], a.off_e[g + 1], a.jhi, a.jlo,
+                                     nullptr, nullptr, nullptr, false, a.eps2, self_at);
+  run_list<GUARD, QUAD, FAR, S, IPT>(st, ln, sm, a.spj, a.off_s[g], a.off_s[g + 1], a.shi, a.slo,
+                                     a.sq0, a.sq1, a.nodef, QUAD, a.eps2, -1);
 }
 
 // One work unit with IPT particles per lane and S j-streams: set up the
 // lanes' i-particles, run both lists, combine the streams and write.
-template <bool GUARD, bool QUAD, int S, int IPT>
+template <bool GUARD, bool QUAD, int FAR, int S, int IPT>
 __device__ __forceinline__ void unit_body(const ForceArgs &a, WarpStage<QUAD> &st, int lane,
                                           uint32_t g, uint32_t ioff) {
   constexpr int W = 32 / S;
@@ -430,7 +559,7 @@ __device__ __forceinline__ void unit_body(const ForceArgs &a, WarpStage<QUAD> &s
   const uint32_t gs = a.g_self[g];
   const int64_t self_at =
       (gs && active[0]) ? (int64_t)a.off_e[g] + (int64_t)(gs - 1u) + (int64_t)il[0] : -1;
-  run_unit<GUARD, QUAD, S, IPT>(st, a, g, ln, sm, self_at);
+  run_unit<GUARD, QUAD, FAR, S, IPT>(st, a, g, ln, sm, self_at);
 #pragma unroll
   for (int q = 0; q < IPT; q++) {
     float ax = sm[q].sx - sm[q].cx, ay = sm[q].sy - sm[q].cy, az = sm[q].sz - sm[q].cz;
@@ -452,18 +581,18 @@ __device__ __forceinline__ void unit_body(const ForceArgs &a, WarpStage<QUAD> &s
 // particles; lane = stream * W + particle).
 // Work unit u: group g = info.x; info.y holds the first particle offset
 // (bits 0-15) and log2 of the j-stream split S (bits 16-17).
-template <bool GUARD, bool QUAD>
+template <bool GUARD, bool QUAD, int FAR>
 __device__ __forceinline__ void force_unit(const ForceArgs &a, WarpStage<QUAD> &st, int lane,
                                            int64_t u) {
   const uint2 info = a.u_info[u];
   const uint32_t g = info.x, ioff = info.y & 0xffffu;
   const int sidx = (int)((info.y >> 16) & 3u);
-  if (sidx == 0) unit_body<GUARD, QUAD, 1, 1>(a, st, lane, g, ioff);
-  else if (sidx == 1) unit_body<GUARD, QUAD, 2, 1>(a, st, lane, g, ioff);
-  else unit_body<GUARD, QUAD, 4, 1>(a, st, lane, g, ioff);
+  if (sidx == 0) unit_body<GUARD, QUAD, FAR, 1, 1>(a, st, lane, g, ioff);
+  else if (sidx == 1) unit_body<GUARD, QUAD, FAR, 2, 1>(a, st, lane, g, ioff);
+  else unit_body<GUARD, QUAD, FAR, 4, 1>(a, st, lane, g, ioff);
 }
 
-template <bool GUARD, bool QUAD>
+template <bool GUARD, bool QUAD, int FAR>
 __global__ void __launch_bounds__(kForceThreads, QUAD ? 4 : AFD_FORCE_MIN_BLOCKS * 4 / AFD_FORCE_WARPS)
     k_force(ForceArgs a) {
   __shared__ WarpStage<QUAD> stage[kForceWarps];
@@ -474,13 +603,13 @@ __global__ void __launch_bounds__(kForceThreads, QUAD ? 4 : AFD_FORCE_MIN_BLOCKS
       if (lane == 0) u = atomicAdd(a.queue, 1ull);
       u = __shfl_sync(0xffffffffu, u, 0);
       if ((int64_t)u >= a.n_units) return;
-      force_unit<GUARD, QUAD>(a, stage[w], lane, (int64_t)u);
+      force_unit<GUARD, QUAD, FAR>(a, stage[w], lane, (int64_t)u);
       __syncwarp();
     }
   } else {
     const int64_t u = (int64_t)blockIdx.x * kForceWarps + w;
     if (u >= a.n_units) return;
-    force_unit<GUARD, QUAD>(a, stage[w], lane, u);
+    force_unit<GUARD, QUAD, FAR>(a, stage[w], lane, u);
   }
 }
 
@@ -501,6 +630,7 @@ int launch_force(afd_ctx *c, float *acc4) {
   a.slo = ptr<float4>(c->s_lo);
   a.sq0 = ptr<float4>(c->s_q0);
   a.sq1 = ptr<float4>(c->s_q1);
+  a.nodef = ptr<float4>(c->node_f);
   a.off_e = ptr<uint64_t>(c->epj_off);
   a.off_s = ptr<uint64_t>(c->spj_off);
   a.epj = ptr<uint32_t>(c->epj);
@@ -515,7 +645,7 @@ int launch_force(afd_ctx *c, float *acc4) {
     if (cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), c->stream) != cudaSuccess)
       return AFD_ERR_CUDA;
     int per_sm = 0, sms = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force<false, false>, kForceThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force<false, false, 0>, kForceThreads, 0);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
     const unsigned cap = (unsigned)(per_sm > 0 ? per_sm : 1) * (unsigned)(sms > 0 ? sms : 1);
     if (nb > cap) nb = cap;
@@ -526,14 +656,22 @@ int launch_force(afd_ctx *c, float *acc4) {
   cudaStreamIsCapturing(c->stream, &cap);
   const bool timed = cap == cudaStreamCaptureStatusNone;
   if (timed) cudaEventRecord(c->ev0, c->stream);
-  if (c->cfg.multipole) {
-    if (guard) k_force<true, true><<<nb, kForceThreads, 0, c->stream>>>(a);
-    else k_force<false, true><<<nb, kForceThreads, 0, c->stream>>>(a);
-  } else if (guard) {
-    k_force<true, false><<<nb, kForceThreads, 0, c->stream>>>(a);
+  const int far = c->cfg.multipole ? c->cfg.far_precision : 0;
+#define AFD_LAUNCH_FORCE(G, Q, F) k_force<G, Q, F><<<nb, kForceThreads, 0, c->stream>>>(a)
+  if (!c->cfg.multipole) {
+    if (guard) AFD_LAUNCH_FORCE(true, false, 0);
+    else AFD_LAUNCH_FORCE(false, false, 0);
+  } else if (far == 1) {
+    if (guard) AFD_LAUNCH_FORCE(true, true, 1);
+    else AFD_LAUNCH_FORCE(false, true, 1);
+  } else if (far == 2) {
+    if (guard) AFD_LAUNCH_FORCE(true, true, 2);
+    else AFD_LAUNCH_FORCE(false, true, 2);
   } else {
-    k_force<false, false><<<nb, kForceThreads, 0, c->stream>>>(a);
+    if (guard) AFD_LAUNCH_FORCE(true, true, 0);
+    else AFD_LAUNCH_FORCE(false, true, 0);
   }
+#undef AFD_LAUNCH_FORCE
   c->launches++;
   if (timed) {
     cudaEventRecord(c->ev1, c->stream);

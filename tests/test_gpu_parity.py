@@ -442,3 +442,59 @@ def test_autotuner_installs_candidates_and_stays_exact(env):
         sl = slice(off[k], off[k + 1])
         assert rms_rel_acc(a[sl], t.force()) <= FORCE_RMS_TOL
     g.close()
+
+
+@pytest.mark.parametrize("far,tol", [(1, 2e-3), (2, 2e-4)])
+def test_half_precision_far_field(env, far, tol):
+    """BF16 (far=1) / FP16 (far=2) quadrupole shape with FP32 geometry and
+    accumulation: same lists, small error against the FP64 oracle."""
+    torch, afd, orc = env
+    p = ics.plummer(60000, 91)
+    kw = dict(n_grp=256, theta=0.6, eps=1.0 / 1024)
+    dev = torch.device("cuda:0")
+    cfg = afd.Config(multipole=1, far_precision=far, **kw)
+    g = afd.Gravity(cfg, 0, torch.cuda.current_stream())
+    x, y, z, m = (torch.tensor(a, device=dev) for a in (p.x, p.y, p.z, p.m))
+    acc = torch.zeros(p.n, 4, dtype=torch.float32, device=dev)
+    g.force_all(x, y, z, m, acc, afd.AFD_MAKE_LIST_FOR_REUSE)
+    torch.cuda.synchronize()
+    t = orc.Tree(p.x, p.y, p.z, p.m, quad=True, **kw)
+    check_structure(g, t, quad=True)
+    ref = t.force()
+    a = acc.cpu().numpy().astype(np.float64)
+    assert rms_rel_acc(a, ref) <= tol
+    assert rms_rel_pot(a, ref) <= tol
+    g.close()
+
+
+def test_mixed_precision_workload_against_direct_sum(env, capsys):
+    """The N = 2^22 Plummer workload with quadrupole superparticles at
+    theta = 0.6: FP32, BF16 and FP16 far field, rms and max relative force
+    error against the FP64 direct sum on 4096 seeded sample particles."""
+    torch, afd, orc = env
+    wl = ics.WORKLOADS["plummer_4m_mixed"]
+    p = ics.plummer(wl["n"], wl["seed"])
+    samples = np.random.Generator(np.random.Philox(4096)).choice(p.n, 4096, replace=False)
+    ref = orc.direct_sum(p.x, p.y, p.z, p.m, wl["eps"], samples)
+    dev = torch.device("cuda:0")
+    x, y, z, m = (torch.tensor(a, device=dev) for a in (p.x, p.y, p.z, p.m))
+    acc = torch.zeros(p.n, 4, dtype=torch.float32, device=dev)
+    errs = {}
+    for far in (0, 1, 2):
+        cfg = afd.Config(eps=wl["eps"], theta=wl["theta"], n_grp=wl["n_grp"], multipole=1,
+                         far_precision=far)
+        g = afd.Gravity(cfg, 0, torch.cuda.current_stream())
+        g.force_all(x, y, z, m, acc, afd.AFD_MAKE_LIST_FOR_REUSE)
+        torch.cuda.synchronize()
+        a = acc.cpu().numpy().astype(np.float64)[samples]
+        num = np.sqrt((a[:, 0] - ref[0]) ** 2 + (a[:, 1] - ref[1]) ** 2 + (a[:, 2] - ref[2]) ** 2)
+        rel = num / np.sqrt(ref[0] ** 2 + ref[1] ** 2 + ref[2] ** 2)
+        errs[far] = (float(np.sqrt(np.mean(rel ** 2))), float(rel.max()))
+        g.close()
+    with capsys.disabled():
+        for far, name in ((0, "fp32"), (1, "bf16"), (2, "fp16")):
+            print(f"\nmixed-precision far field {name}: rms rel err {errs[far][0]:.4e} "
+                  f"max {errs[far][1]:.4e}")
+    # the far-field precision barely moves the tree's own error
+    assert errs[0][0] < 5e-3
+    assert errs[2][0] < 1.05 * errs[0][0] and errs[1][0] < 1.3 * errs[0][0]
