@@ -27,6 +27,14 @@ _D = ctypes.POINTER(ctypes.c_double)
 _I64 = ctypes.POINTER(ctypes.c_int64)
 _I32 = ctypes.POINTER(ctypes.c_int32)
 _U64 = ctypes.POINTER(ctypes.c_uint64)
+_F32 = ctypes.POINTER(ctypes.c_float)
+
+# Learned opening criterion (readings R12-R15 of afdps_oracle.c): features,
+# hidden units and the length of the flat parameter vector
+# mu[8] isd[8] W1[32][8] b1[32] W2[32][32] b2[32] w3[32] b3[1].
+MAC_NF = 8
+MAC_NH = 32
+MAC_NP = 2 * MAC_NF + MAC_NH * MAC_NF + MAC_NH + MAC_NH * MAC_NH + MAC_NH + MAC_NH + 1
 
 
 def build(force: bool = False) -> str:
@@ -76,6 +84,21 @@ def lib():
                                    ctypes.c_double, ctypes.c_int, ctypes.c_int, _I64]
         L.afo_leapfrog.restype = ctypes.c_int
         L.afo_num_threads.restype = ctypes.c_int
+        L.afo_build_mac.argtypes = L.afo_build.argtypes + [_F32, ctypes.c_double,
+                                                          ctypes.c_double, ctypes.c_double, _F32]
+        L.afo_build_mac.restype = ctypes.c_void_p
+        L.afo_lg2_batch.argtypes = [ctypes.c_int64, _F32, _F32]
+        L.afo_mac_features.argtypes = [_F32, _F32, _F32, ctypes.c_float, ctypes.c_float, _F32,
+                                       ctypes.c_int64, ctypes.c_float, ctypes.c_float, _F32]
+        L.afo_mlp_forward_batch.argtypes = [_F32, ctypes.c_int64, _F32, _F32]
+        L.afo_mac_label.argtypes = [ctypes.c_int64, _D, _D, _D, _D, ctypes.c_int64, _D, _D, _D,
+                                    _D, ctypes.c_double, _D, _D, ctypes.c_double, ctypes.c_int]
+        L.afo_mac_label.restype = ctypes.c_double
+        L.afo_pair_features_batch.argtypes = [ctypes.c_void_p, ctypes.c_int64, _I64, _F32]
+        L.afo_pair_label_batch.argtypes = [ctypes.c_void_p, ctypes.c_int64, _I64, _D]
+        L.afo_band_pairs.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_int64, _I64]
+        L.afo_band_pairs.restype = ctypes.c_int64
     return _lib
 
 
@@ -149,12 +172,27 @@ class Tree:
     reuse steps. Wraps the C ``afo_tree``; arrays are copied out on request."""
 
     def __init__(self, x, y, z, m, *, n_leaf=16, n_grp=64, theta=0.5, eps=1.0 / 256,
-                 quad=False):
+                 quad=False, mac=None, amag=None):
+        """``mac``: dict(params, theta_lo, theta_hi, tau) of the learned
+        criterion (R14; params are FP16-rounded, see ``fp16_round``);
+        ``amag``: reference |a| per particle (caller order, FP32). The
+        learned criterion is used when both are given; with ``amag`` alone
+        the tree only carries the reference magnitudes (for features and
+        labels)."""
         self._args = dict(n_leaf=n_leaf, n_grp=n_grp, theta=theta, eps=eps, quad=quad)
         x, y, z, m = map(_f64, (x, y, z, m))
         self.n = x.shape[0]
-        h = lib().afo_build(self.n, _p(x, _D), _p(y, _D), _p(z, _D), _p(m, _D),
-                            int(n_leaf), int(n_grp), float(theta), float(eps), int(quad))
+        w = lo = hi = tau = None
+        if mac is not None:
+            w = np.ascontiguousarray(mac["params"], dtype=np.float32)
+            assert w.shape == (MAC_NP,)
+            lo, hi, tau = float(mac["theta_lo"]), float(mac["theta_hi"]), float(mac["tau"])
+        a = None if amag is None else np.ascontiguousarray(amag, dtype=np.float32)
+        self._amag = a
+        h = lib().afo_build_mac(self.n, _p(x, _D), _p(y, _D), _p(z, _D), _p(m, _D),
+                                int(n_leaf), int(n_grp), float(theta), float(eps), int(quad),
+                                None if w is None else _p(w, _F32), lo or 0.0, hi or 0.0,
+                                tau or 0.0, None if a is None else _p(a, _F32))
         if not h:
             raise ValueError("non-finite particle data")
         self._h = ctypes.c_void_p(h)
@@ -242,6 +280,27 @@ class Tree:
         lib().afo_force_groups(self._h, sel.shape[0], _p(sel, _I64), *(_p(o, _D) for o in out))
         return tuple(out)
 
+    def band_pairs(self, theta_lo, theta_hi):
+        """(group, cell) pairs left to the network by R14 (int64, (n, 2))."""
+        n = int(lib().afo_band_pairs(self._h, float(theta_lo), float(theta_hi), 0, None))
+        out = np.zeros((max(n, 1), 2), dtype=np.int64)
+        lib().afo_band_pairs(self._h, float(theta_lo), float(theta_hi), n, _p(out, _I64))
+        return out[:n]
+
+    def pair_features(self, pairs):
+        """FP32 features of R12 for (group, cell) pairs; needs ``amag``."""
+        pr = np.ascontiguousarray(pairs, dtype=np.int64).reshape(-1, 2)
+        f = np.zeros((pr.shape[0], MAC_NF), dtype=np.float32)
+        lib().afo_pair_features_batch(self._h, pr.shape[0], _p(pr, _I64), _p(f, _F32))
+        return f
+
+    def pair_labels(self, pairs):
+        """FP64 training targets of R15 for (group, cell) pairs."""
+        pr = np.ascontiguousarray(pairs, dtype=np.int64).reshape(-1, 2)
+        out = np.zeros(pr.shape[0])
+        lib().afo_pair_label_batch(self._h, pr.shape[0], _p(pr, _I64), _p(out, _D))
+        return out
+
     def interactions(self):
         """Sum over groups of n_i * (n_epj + n_spj) (self pair included)."""
         g = self.groups()
@@ -268,3 +327,103 @@ def leapfrog(x, y, z, vx, vy, vz, m, *, dt, n_steps, n_reuse, n_leaf=16, n_grp=6
     if rc != 0:
         raise ValueError("non-finite particle data")
     return (*arrs, *acc)
+
+
+# ---------------------------------------------------------------------------
+# Learned opening criterion (not in the paper; readings R12-R15).
+# ---------------------------------------------------------------------------
+
+def lg2(x):
+    """The deterministic FP32 log2 of R12."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    out = np.zeros_like(x)
+    lib().afo_lg2_batch(x.size, _p(x, _F32), _p(out, _F32))
+    return out
+
+
+def mac_features(bmin, bmax, com, s2, M, Q, count, eps2, amin):
+    """R12 features from raw FP32 inputs (one pair)."""
+    b0, b1, c = (np.ascontiguousarray(v, dtype=np.float32) for v in (bmin, bmax, com))
+    q = np.ascontiguousarray(Q, dtype=np.float32)
+    f = np.zeros(MAC_NF, dtype=np.float32)
+    lib().afo_mac_features(_p(b0, _F32), _p(b1, _F32), _p(c, _F32), float(np.float32(s2)),
+                           float(np.float32(M)), _p(q, _F32), int(count),
+                           float(np.float32(eps2)), float(np.float32(amin)), _p(f, _F32))
+    return f
+
+
+def mac_label(xi, ai, xj, mj, M, com, Q, eps, quad):
+    """R15 target for group particles xi (n_i, 3) with reference magnitudes
+    ai and a cell of particles xj (n_j, 3), mj with monopole M at com and
+    quadrupole Q."""
+    xi, xj = np.asarray(xi, np.float64).reshape(-1, 3), np.asarray(xj, np.float64).reshape(-1, 3)
+    cols_i = [np.ascontiguousarray(xi[:, k]) for k in range(3)]
+    cols_j = [np.ascontiguousarray(xj[:, k]) for k in range(3)]
+    ai, mj, com, Q = map(_f64, (ai, mj, com, Q))
+    return float(lib().afo_mac_label(xi.shape[0], *(_p(c, _D) for c in cols_i), _p(ai, _D),
+                                     xj.shape[0], *(_p(c, _D) for c in cols_j), _p(mj, _D),
+                                     float(M), _p(com, _D), _p(Q, _D), float(eps), int(quad)))
+
+
+def fp16_round(params):
+    """Parameters as the criterion stores them (R13): FP16 values in FP32."""
+    return np.asarray(params, dtype=np.float32).astype(np.float16).astype(np.float32)
+
+
+def mlp_forward(params, feats):
+    """R13 network in FP32 (fused multiply-adds, fixed order) per feature row."""
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    f = np.ascontiguousarray(feats, dtype=np.float32).reshape(-1, MAC_NF)
+    out = np.zeros(f.shape[0], dtype=np.float32)
+    lib().afo_mlp_forward_batch(_p(p, _F32), f.shape[0], _p(f, _F32), _p(out, _F32))
+    return out
+
+
+def mlp_unpack(params):
+    """Split the flat vector into (mu, isd, W1, b1, W2, b2, w3, b3)."""
+    p = np.asarray(params)
+    sizes = [MAC_NF, MAC_NF, MAC_NH * MAC_NF, MAC_NH, MAC_NH * MAC_NH, MAC_NH, MAC_NH, 1]
+    parts, o = [], 0
+    for s in sizes:
+        parts.append(p[o:o + s])
+        o += s
+    mu, isd, W1, b1, W2, b2, w3, b3 = parts
+    return mu, isd, W1.reshape(MAC_NH, MAC_NF), b1, W2.reshape(MAC_NH, MAC_NH), b2, w3, b3
+
+
+def mlp_loss(params, feats, labels):
+    """Mean squared error of the R13 network in FP64 (no FP16 rounding)."""
+    mu, isd, W1, b1, W2, b2, w3, b3 = mlp_unpack(np.asarray(params, np.float64))
+    X = (np.asarray(feats, np.float64) - mu) * isd
+    H1 = np.maximum(X @ W1.T + b1, 0.0)
+    H2 = np.maximum(H1 @ W2.T + b2, 0.0)
+    y = H2 @ w3 + b3[0]
+    return float(np.mean((y - np.asarray(labels, np.float64)) ** 2))
+
+
+def mlp_loss_grad(params, feats, labels):
+    """FP64 backward pass of ``mlp_loss`` (chain rule through both ReLU
+    layers; the derivative of ReLU at 0 is taken as 0). Returns (loss, grad)
+    with grad laid out like params (zero for mu and isd, which are not
+    trained)."""
+    mu, isd, W1, b1, W2, b2, w3, b3 = mlp_unpack(np.asarray(params, np.float64))
+    X = (np.asarray(feats, np.float64) - mu) * isd
+    Z1 = X @ W1.T + b1
+    H1 = np.maximum(Z1, 0.0)
+    Z2 = H1 @ W2.T + b2
+    H2 = np.maximum(Z2, 0.0)
+    y = H2 @ w3 + b3[0]
+    r = y - np.asarray(labels, np.float64)
+    B = X.shape[0]
+    dy = 2.0 * r / B
+    g_w3 = H2.T @ dy
+    g_b3 = np.array([dy.sum()])
+    dZ2 = np.outer(dy, w3) * (Z2 > 0.0)
+    g_W2 = dZ2.T @ H1
+    g_b2 = dZ2.sum(axis=0)
+    dZ1 = (dZ2 @ W2) * (Z1 > 0.0)
+    g_W1 = dZ1.T @ X
+    g_b1 = dZ1.sum(axis=0)
+    grad = np.concatenate([np.zeros(2 * MAC_NF), g_W1.ravel(), g_b1, g_W2.ravel(), g_b2,
+                           g_w3, g_b3])
+    return float(np.mean(r * r)), grad

@@ -58,7 +58,38 @@
  *     r = x_i - COM.
  *  R11 integrator: kick-drift-kick leapfrog; force evaluation k of a run is
  *     a construction step when k % n_reuse == 0, else it reuses the lists.
+ *
+ * The learned opening criterion is not in the paper (the paper uses the
+ * opening angle only, Section 2); its definition is fixed here:
+ *  R12 features of a (group g, cell c) pair, eight FP32 numbers computed
+ *     without contraction in the order written in afo_mac_features(): with
+ *     d^2 the squared COM-to-box distance of R8, s the cell side, M and Q
+ *     the cell's monopole and quadrupole rounded to FP32, n_c its particle
+ *     count, A_g the smallest reference acceleration magnitude among the
+ *     group's particles, u the vector from the COM to the box centre and e
+ *     the half diagonal of the box:
+ *       f0 = log2(s/d)        f1 = log2(M / (d^2 A_g))
+ *       f2 = log2(|Q|_F / (M s^2))   f3 = log2(e/d)      f4 = log2(n_c)
+ *       f5 = log2(eps/d)      f6 = u.Q.u / (|u|^2 |Q|_F)  f7 = log2(|u|/d)
+ *     each clamped to [-32, 32]. log2 is lg2(): the exponent of the FP32
+ *     argument plus t*p(t) on its mantissa 1+t, p a fixed quartic (Horner
+ *     with fused multiply-adds); 0 or subnormal arguments give -127.
+ *  R13 network: 8-32-32-1 perceptron with ReLU on both hidden layers; input
+ *     k is normalised as (f_k - mu_k) * isd_k; every parameter (mu and isd
+ *     included) is an FP16 value; each unit is its bias followed by fused
+ *     multiply-adds over its inputs in index order, in FP32.
+ *  R14 learned decision for cell c and group g: open if c contains the
+ *     group's first particle; accept if s^2 < theta_lo^2 d^2; open if not
+ *     s^2 < theta_hi^2 d^2; otherwise accept iff the network's output is
+ *     below tau. Without weights or reference accelerations the walk uses
+ *     R8 (the theta criterion is the fallback).
+ *  R15 training target of a pair: log2 of max over the group's particles i
+ *     of |a_i^cell - a_i^exact| / A_i, where a_i^cell is the cell's
+ *     superparticle term (R1, plus R10 with quadrupoles), a_i^exact the
+ *     direct sum over the cell's particles and A_i particle i's reference
+ *     acceleration magnitude; clamped to [-40, 8].
  */
+#include <float.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -68,6 +99,14 @@
 #endif
 
 #define AFO_LEVELS 21 /* deepest level; 21 key bits per axis */
+
+/* Learned opening criterion (R12-R13): 8 features, two hidden layers of 32.
+ * Parameter vector: mu[8] isd[8] W1[32][8] b1[32] W2[32][32] b2[32] w3[32]
+ * b3[1]. */
+#define AFO_MAC_NF 8
+#define AFO_MAC_NH 32
+#define AFO_MAC_NP (2 * AFO_MAC_NF + AFO_MAC_NH * AFO_MAC_NF + AFO_MAC_NH + \
+                    AFO_MAC_NH * AFO_MAC_NH + AFO_MAC_NH + AFO_MAC_NH + 1)
 
 /* ------------------------------------------------------------------------ */
 /* Exact target: softened direct summation (R1).                           */
@@ -234,6 +273,13 @@ typedef struct afo_tree {
   /* lists (CSR, one EPJ and one SPJ list per group) */
   int64_t *epj_off, *spj_off;
   int32_t *epj, *spj;
+  /* learned opening criterion (R12-R15): on when weights and reference
+   * accelerations were given */
+  int mac_on, need_q;
+  float mac_w[AFO_MAC_NP];
+  float mac_lo2, mac_hi2, mac_tau;
+  float *amag_s; /* reference |a| per particle, Morton order */
+  float *g_amin; /* smallest of them per group */
 } afo_tree;
 
 static void *xcalloc(size_t count, size_t size) {
@@ -247,6 +293,7 @@ void afo_free(afo_tree *t) {
   free(t->n_child); free(t->child); free(t->mass); free(t->smom); free(t->com); free(t->qmom);
   free(t->g_first); free(t->g_count); free(t->g_cell); free(t->g_box); free(t->g_self);
   free(t->epj_off); free(t->spj_off); free(t->epj); free(t->spj);
+  free(t->amag_s); free(t->g_amin);
   free(t);
 }
 
@@ -404,7 +451,7 @@ static void moments(afo_tree *t) {
       cell_centre(t, c, &t->com[c * 3]);
     }
   }
-  if (!t->quad) return;
+  if (!t->quad && !t->need_q) return; /* R12 reads Q even without R10 */
   for (int64_t c = nc - 1; c >= 0; c--) {
     double Q[6] = {0, 0, 0, 0, 0, 0}; /* xx yy zz xy xz yz */
     const double *g = &t->com[c * 3];
@@ -514,7 +561,295 @@ static int mac_accept(const float bmin[3], const float bmax[3], const float com[
   return s2 < rhs;
 }
 
-/* Barnes' vectorised walk for one group (Section 2, Section 4.1; R8, R9).
+/* ------------------------------------------------------------------------ */
+/* Learned opening criterion (not in the paper; readings R12-R15).          */
+/* ------------------------------------------------------------------------ */
+
+/* lg2 of R12: exponent plus t * p(t) on the mantissa 1 + t, t in [0, 1).
+ * p is a least-squares quartic fit of log2(1 + t) / t (max error 1.8e-5). */
+float afo_lg2(float x) {
+  if (!(x >= FLT_MIN)) return -127.0f;
+  if (x > FLT_MAX) return 128.0f;
+  uint32_t b;
+  memcpy(&b, &x, sizeof(b));
+  const int e = (int)((b >> 23) & 0xffu) - 127;
+  const uint32_t mb = (b & 0x7fffffu) | 0x3f800000u;
+  float mant;
+  memcpy(&mant, &mb, sizeof(mant));
+  const float t = mant - 1.0f;
+  float p = 0.04526829347014427f;
+  p = fmaf(p, t, -0.19351652264595032f);
+  p = fmaf(p, t, 0.41524556279182434f);
+  p = fmaf(p, t, -0.708865225315094f);
+  p = fmaf(p, t, 1.4418798685073853f);
+  const float pt = p * t;
+  return (float)e + pt;
+}
+
+void afo_lg2_batch(int64_t n, const float *x, float *out) {
+  for (int64_t i = 0; i < n; i++) out[i] = afo_lg2(x[i]);
+}
+
+static float clamp32(float v) { return v < -32.0f ? -32.0f : (v > 32.0f ? 32.0f : v); }
+
+/* Features of R12 from FP32 inputs: the group box, the cell's COM, squared
+ * side s2, mass M, quadrupole Q (xx yy zz xy xz yz), particle count, eps^2
+ * and the group's smallest reference |a|. */
+void afo_mac_features(const float bmin[3], const float bmax[3], const float com[3], float s2,
+                      float M, const float Q[6], int64_t count, float eps2, float amin,
+                      float f[AFO_MAC_NF]) {
+  float d[3], u[3], w[3];
+  for (int k = 0; k < 3; k++) {
+    d[k] = 0.0f;
+    if (com[k] < bmin[k]) d[k] = bmin[k] - com[k];
+    else if (com[k] > bmax[k]) d[k] = com[k] - bmax[k];
+    const float mid = (bmin[k] + bmax[k]) * 0.5f;
+    u[k] = mid - com[k];
+    w[k] = bmax[k] - bmin[k];
+  }
+  float d2 = d[0] * d[0];
+  d2 = d2 + d[1] * d[1];
+  d2 = d2 + d[2] * d[2];
+  float u2 = u[0] * u[0];
+  u2 = u2 + u[1] * u[1];
+  u2 = u2 + u[2] * u[2];
+  float e2 = w[0] * w[0];
+  e2 = e2 + w[1] * w[1];
+  e2 = e2 + w[2] * w[2];
+  e2 = e2 * 0.25f;
+  float off = Q[3] * Q[3];
+  off = off + Q[4] * Q[4];
+  off = off + Q[5] * Q[5];
+  float q2 = Q[0] * Q[0];
+  q2 = q2 + Q[1] * Q[1];
+  q2 = q2 + Q[2] * Q[2];
+  q2 = q2 + (off + off);
+  float Qu[3];
+  Qu[0] = Q[0] * u[0] + Q[3] * u[1];
+  Qu[0] = Qu[0] + Q[4] * u[2];
+  Qu[1] = Q[3] * u[0] + Q[1] * u[1];
+  Qu[1] = Qu[1] + Q[5] * u[2];
+  Qu[2] = Q[4] * u[0] + Q[5] * u[1];
+  Qu[2] = Qu[2] + Q[2] * u[2];
+  float uQu = u[0] * Qu[0] + u[1] * Qu[1];
+  uQu = uQu + u[2] * Qu[2];
+  const float ld = afo_lg2(d2), ls = afo_lg2(s2), lm = afo_lg2(M);
+  f[0] = 0.5f * (ls - ld);
+  f[1] = (lm - ld) - afo_lg2(amin);
+  f[2] = (0.5f * afo_lg2(q2) - lm) - ls;
+  f[3] = 0.5f * (afo_lg2(e2) - ld);
+  f[4] = afo_lg2((float)count);
+  f[5] = 0.5f * (afo_lg2(eps2) - ld);
+  f[6] = 0.0f;
+  if (u2 > 0.0f && q2 > 0.0f) {
+    const float den = u2 * sqrtf(q2);
+    if (den > 0.0f) f[6] = uQu / den;
+  }
+  f[7] = 0.5f * (afo_lg2(u2) - ld);
+  for (int k = 0; k < AFO_MAC_NF; k++) f[k] = clamp32(f[k]);
+}
+
+/* Network of R13 on one feature vector; p holds FP16-representable values. */
+float afo_mlp_forward(const float *p, const float f[AFO_MAC_NF]) {
+  const float *mu = p, *isd = p + AFO_MAC_NF;
+  const float *W1 = p + 2 * AFO_MAC_NF, *b1 = W1 + AFO_MAC_NH * AFO_MAC_NF;
+  const float *W2 = b1 + AFO_MAC_NH, *b2 = W2 + AFO_MAC_NH * AFO_MAC_NH;
+  const float *w3 = b2 + AFO_MAC_NH, *b3 = w3 + AFO_MAC_NH;
+  float x[AFO_MAC_NF], h1[AFO_MAC_NH], h2[AFO_MAC_NH];
+  for (int k = 0; k < AFO_MAC_NF; k++) x[k] = (f[k] - mu[k]) * isd[k];
+  for (int j = 0; j < AFO_MAC_NH; j++) {
+    float acc = b1[j];
+    for (int k = 0; k < AFO_MAC_NF; k++) acc = fmaf(W1[j * AFO_MAC_NF + k], x[k], acc);
+    h1[j] = acc > 0.0f ? acc : 0.0f;
+  }
+  for (int j = 0; j < AFO_MAC_NH; j++) {
+    float acc = b2[j];
+    for (int k = 0; k < AFO_MAC_NH; k++) acc = fmaf(W2[j * AFO_MAC_NH + k], h1[k], acc);
+    h2[j] = acc > 0.0f ? acc : 0.0f;
+  }
+  float y = b3[0];
+  for (int k = 0; k < AFO_MAC_NH; k++) y = fmaf(w3[k], h2[k], y);
+  return y;
+}
+
+void afo_mlp_forward_batch(const float *p, int64_t n, const float *feat, float *out) {
+  for (int64_t i = 0; i < n; i++) out[i] = afo_mlp_forward(p, feat + i * AFO_MAC_NF);
+}
+
+/* Training target of R15 for n_i group particles (xi, yi, zi, reference
+ * magnitudes ai) and a cell of n_j particles with monopole M at com and
+ * quadrupole Q (used when quad != 0). FP64 throughout. */
+double afo_mac_label(int64_t n_i, const double *xi, const double *yi, const double *zi,
+                     const double *ai, int64_t n_j, const double *xj, const double *yj,
+                     const double *zj, const double *mj, double M, const double com[3],
+                     const double Q[6], double eps, int quad) {
+  const double eps2 = eps * eps;
+  double worst = 0.0;
+  for (int64_t i = 0; i < n_i; i++) {
+    double ex[3] = {0.0, 0.0, 0.0};
+    for (int64_t j = 0; j < n_j; j++) {
+      const double dx = xj[j] - xi[i], dy = yj[j] - yi[i], dz = zj[j] - zi[i];
+      const double r2 = dx * dx + dy * dy + dz * dz + eps2;
+      if (r2 == 0.0) continue;
+      const double rinv = 1.0 / sqrt(r2);
+      const double mr3 = mj[j] * rinv * rinv * rinv;
+      ex[0] += mr3 * dx;
+      ex[1] += mr3 * dy;
+      ex[2] += mr3 * dz;
+    }
+    double ap[3] = {0.0, 0.0, 0.0};
+    const double dx = com[0] - xi[i], dy = com[1] - yi[i], dz = com[2] - zi[i];
+    const double r2 = dx * dx + dy * dy + dz * dz + eps2;
+    if (r2 > 0.0) {
+      const double rinv = 1.0 / sqrt(r2);
+      const double mr3 = M * rinv * rinv * rinv;
+      ap[0] = mr3 * dx;
+      ap[1] = mr3 * dy;
+      ap[2] = mr3 * dz;
+      if (quad) { /* R10, r = x_i - COM */
+        const double r[3] = {-dx, -dy, -dz};
+        const double Qr[3] = {Q[0] * r[0] + Q[3] * r[1] + Q[4] * r[2],
+                              Q[3] * r[0] + Q[1] * r[1] + Q[5] * r[2],
+                              Q[4] * r[0] + Q[5] * r[1] + Q[2] * r[2]};
+        const double rQr = r[0] * Qr[0] + r[1] * Qr[1] + r[2] * Qr[2];
+        const double rinv2 = rinv * rinv, rinv5 = rinv2 * rinv2 * rinv, rinv7 = rinv5 * rinv2;
+        for (int k = 0; k < 3; k++) ap[k] += Qr[k] * rinv5 - 2.5 * rQr * r[k] * rinv7;
+      }
+    }
+    const double e0 = ap[0] - ex[0], e1 = ap[1] - ex[1], e2 = ap[2] - ex[2];
+    const double err = sqrt(e0 * e0 + e1 * e1 + e2 * e2) / ai[i];
+    if (err > worst || isnan(err)) worst = err;
+  }
+  double lab = worst > 0.0 ? log2(worst) : -40.0;
+  if (!(lab <= 8.0)) lab = 8.0; /* also NaN (zero reference magnitude) */
+  if (lab < -40.0) lab = -40.0;
+  return lab;
+}
+
+/* FP32 inputs of R12 for cell c as the walk sees them. */
+static void cell_inputs(const afo_tree *t, int64_t c, float com[3], float *s2, float *M,
+                        float Q[6]) {
+  const float s = ldexpf((float)t->root[3], -t->level[c]);
+  *s2 = s * s;
+  for (int k = 0; k < 3; k++) com[k] = (float)t->com[c * 3 + k];
+  *M = (float)t->mass[c];
+  for (int q = 0; q < 6; q++) Q[q] = (float)t->qmom[c * 6 + q];
+}
+
+static void group_boxf(const afo_tree *t, int64_t g, float bmin[3], float bmax[3]) {
+  for (int k = 0; k < 3; k++) {
+    bmin[k] = (float)t->g_box[g * 6 + k];
+    bmax[k] = (float)t->g_box[g * 6 + 3 + k];
+  }
+}
+
+static int contains_group(const afo_tree *t, int64_t g, int64_t c) {
+  return t->g_first[g] >= t->first[c] && t->g_first[g] < t->first[c] + t->count[c];
+}
+
+/* Squared COM-to-box distance of R8 (same operations as mac_accept). */
+static float box_d2(const float bmin[3], const float bmax[3], const float com[3]) {
+  float d[3];
+  for (int k = 0; k < 3; k++) {
+    d[k] = 0.0f;
+    if (com[k] < bmin[k]) d[k] = bmin[k] - com[k];
+    else if (com[k] > bmax[k]) d[k] = com[k] - bmax[k];
+  }
+  float d2 = d[0] * d[0];
+  d2 = d2 + d[1] * d[1];
+  d2 = d2 + d[2] * d[2];
+  return d2;
+}
+
+/* Features of the pair (g, c) in a tree built with reference accelerations. */
+void afo_pair_features(const afo_tree *t, int64_t g, int64_t c, float f[AFO_MAC_NF]) {
+  float bmin[3], bmax[3], com[3], s2, M, Q[6];
+  group_boxf(t, g, bmin, bmax);
+  cell_inputs(t, c, com, &s2, &M, Q);
+  const float e = (float)t->eps;
+  afo_mac_features(bmin, bmax, com, s2, M, Q, t->count[c], e * e,
+                   t->g_amin ? t->g_amin[g] : 0.0f, f);
+}
+
+/* Learned decision of R14; 1 = accept cell c as a superparticle of g. */
+static int learned_accept(const afo_tree *t, int64_t g, int64_t c, const float bmin[3],
+                          const float bmax[3], const float com[3], float s2) {
+  if (contains_group(t, g, c)) return 0;
+  const float d2 = box_d2(bmin, bmax, com);
+  const float lo = t->mac_lo2 * d2;
+  if (s2 < lo) return 1;
+  const float hi = t->mac_hi2 * d2;
+  if (!(s2 < hi)) return 0;
+  float f[AFO_MAC_NF];
+  afo_pair_features(t, g, c, f);
+  return afo_mlp_forward(t->mac_w, f) < t->mac_tau;
+}
+
+/* Training target of R15 for the pair (g, c). */
+double afo_pair_label(const afo_tree *t, int64_t g, int64_t c) {
+  const int64_t f = t->g_first[g], fc = t->first[c];
+  double ai[1024];
+  const int64_t ni = t->g_count[g] < 1024 ? t->g_count[g] : 1024;
+  for (int64_t i = 0; i < ni; i++) ai[i] = t->amag_s ? (double)t->amag_s[f + i] : 0.0;
+  return afo_mac_label(ni, t->xs + f, t->ys + f, t->zs + f, ai, t->count[c], t->xs + fc,
+                       t->ys + fc, t->zs + fc, t->ms + fc, t->mass[c], &t->com[c * 3],
+                       &t->qmom[c * 6], t->eps, t->quad);
+}
+
+void afo_pair_features_batch(const afo_tree *t, int64_t n, const int64_t *pairs, float *f) {
+  for (int64_t i = 0; i < n; i++)
+    afo_pair_features(t, pairs[2 * i], pairs[2 * i + 1], f + i * AFO_MAC_NF);
+}
+
+void afo_pair_label_batch(const afo_tree *t, int64_t n, const int64_t *pairs, double *out) {
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int64_t i = 0; i < n; i++) out[i] = afo_pair_label(t, pairs[2 * i], pairs[2 * i + 1]);
+}
+
+/* Every (group, cell) pair whose decision R14 leaves to the network, over
+ * the walk that opens every other cell not accepted below theta_lo: band
+ * cells are recorded and opened. Writes up to cap pairs (group, cell) in
+ * group order, depth-first, children in Morton order; returns the count. */
+int64_t afo_band_pairs(const afo_tree *t, double theta_lo, double theta_hi, int64_t cap,
+                       int64_t *pairs) {
+  const float lo2 = (float)theta_lo * (float)theta_lo;
+  const float hi2 = (float)theta_hi * (float)theta_hi;
+  int64_t np = 0;
+  int64_t *stack = malloc(sizeof(int64_t) * (size_t)(8 * t->n_cells + 8));
+  for (int64_t g = 0; g < t->n_groups; g++) {
+    float bmin[3], bmax[3];
+    group_boxf(t, g, bmin, bmax);
+    int64_t sp = 0;
+    if (t->n_cells > 0) stack[sp++] = 0;
+    while (sp > 0) {
+      const int64_t c = stack[--sp];
+      float com[3], s2, M, Q[6];
+      cell_inputs(t, c, com, &s2, &M, Q);
+      int open = 1;
+      if (!contains_group(t, g, c)) {
+        const float d2 = box_d2(bmin, bmax, com);
+        const float lo = lo2 * d2, hi = hi2 * d2;
+        if (s2 < lo) {
+          open = 0;
+        } else if (s2 < hi) {
+          if (np < cap) {
+            pairs[2 * np] = g;
+            pairs[2 * np + 1] = c;
+          }
+          np++;
+        }
+      }
+      if (open && !is_leaf(t, c))
+        for (int o = 7; o >= 0; o--)
+          if (t->child[c * 8 + o] >= 0) stack[sp++] = t->child[c * 8 + o];
+    }
+  }
+  free(stack);
+  return np;
+}
+
+/* Barnes' vectorised walk for one group (Section 2, Section 4.1; R8 or
+ * R14, R9).
  * With epj/spj NULL it only counts. */
 static void walk_group(const afo_tree *t, int64_t g, int32_t *epj, int32_t *spj,
                        int64_t *n_epj, int64_t *n_spj, int32_t *self_in) {
@@ -536,7 +871,9 @@ static void walk_group(const afo_tree *t, int64_t g, int32_t *epj, int32_t *spj,
     const float s2 = s * s;
     float com[3];
     for (int k = 0; k < 3; k++) com[k] = (float)t->com[c * 3 + k];
-    if (mac_accept(bmin, bmax, com, s2, theta2)) {
+    const int accept = t->mac_on ? learned_accept(t, g, c, bmin, bmax, com, s2)
+                                 : mac_accept(bmin, bmax, com, s2, theta2);
+    if (accept) {
       if (spj) spj[ns] = (int32_t)c;
       ns++;
     } else if (is_leaf(t, c)) {
@@ -582,10 +919,14 @@ static void make_lists(afo_tree *t) {
 
 /* Construction step (Section 4.3, Section 4.2 "tree construction step"):
  * root, keys, sort, reorder, link, moments, groups and interaction lists.
- * Returns NULL on bad input (non-finite coordinates or masses). */
-afo_tree *afo_build(int64_t n, const double *x, const double *y, const double *z,
-                    const double *m, int n_leaf, int n_grp, double theta, double eps,
-                    int quad) {
+ * With mac_w (AFO_MAC_NP FP16-valued parameters) and amag (reference |a|
+ * per particle, caller order) both given, the lists follow the learned
+ * decision of R14 with theta_lo, theta_hi and tau; otherwise R8. Returns
+ * NULL on bad input (non-finite coordinates or masses). */
+afo_tree *afo_build_mac(int64_t n, const double *x, const double *y, const double *z,
+                        const double *m, int n_leaf, int n_grp, double theta, double eps,
+                        int quad, const float *mac_w, double theta_lo, double theta_hi,
+                        double tau, const float *amag) {
   for (int64_t i = 0; i < n; i++)
     if (!isfinite(m[i])) return NULL;
   afo_tree *t = calloc(1, sizeof(afo_tree));
@@ -595,6 +936,14 @@ afo_tree *afo_build(int64_t n, const double *x, const double *y, const double *z
   t->theta = theta;
   t->eps = eps;
   t->quad = quad;
+  t->need_q = amag != NULL;
+  if (mac_w && amag) {
+    t->mac_on = 1;
+    memcpy(t->mac_w, mac_w, sizeof(t->mac_w));
+    t->mac_lo2 = (float)theta_lo * (float)theta_lo;
+    t->mac_hi2 = (float)theta_hi * (float)theta_hi;
+    t->mac_tau = (float)tau;
+  }
   if (afo_root_cell(n, x, y, z, t->root) != 0) {
     free(t);
     return NULL;
@@ -618,8 +967,26 @@ afo_tree *afo_build(int64_t n, const double *x, const double *y, const double *z
   moments(t);
   make_groups(t);
   group_boxes(t);
+  if (amag) {
+    t->amag_s = xcalloc(n, sizeof(float));
+    for (int64_t k = 0; k < n; k++) t->amag_s[k] = amag[t->perm[k]];
+    t->g_amin = xcalloc(t->n_groups, sizeof(float));
+    for (int64_t g = 0; g < t->n_groups; g++) {
+      float a = t->amag_s[t->g_first[g]];
+      for (int64_t k = t->g_first[g] + 1; k < t->g_first[g] + t->g_count[g]; k++)
+        if (t->amag_s[k] < a) a = t->amag_s[k];
+      t->g_amin[g] = a;
+    }
+  }
   make_lists(t);
   return t;
+}
+
+afo_tree *afo_build(int64_t n, const double *x, const double *y, const double *z,
+                    const double *m, int n_leaf, int n_grp, double theta, double eps,
+                    int quad) {
+  return afo_build_mac(n, x, y, z, m, n_leaf, n_grp, theta, eps, quad, NULL, 0.0, 0.0, 0.0,
+                       NULL);
 }
 
 /* Reusing step (Section 4.2): topology and lists are kept; the particle
