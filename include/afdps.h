@@ -64,7 +64,8 @@ typedef enum {
   AFD_ERR_NO_TREE = -8,       /* lists or force requested before a tree */
   AFD_ERR_OOM = -9,           /* device allocation failed */
   AFD_ERR_WALK_STACK = -10,   /* a tree walk overflowed its per-warp stack */
-  AFD_ERR_TOO_LARGE = -11     /* problem size above the limit of afd_root_cell_static */
+  AFD_ERR_TOO_LARGE = -11,    /* problem size above the limit of afd_root_cell_static */
+  AFD_ERR_NO_REFERENCE = -12  /* learned-criterion sampling without reference accelerations */
 } afd_status;
 
 /* Method parameters. Paper values: n_leaf = 16, theta in [0.25, 1]
@@ -76,7 +77,8 @@ typedef struct {
   int32_t n_grp;         /* maximum particles per i-group, 1 .. 1024 */
   int32_t multipole;     /* 0: monopole superparticles, 1: + quadrupole */
   int32_t far_precision; /* 0: FP32 superparticle terms, 1: BF16, 2: FP16 */
-  int32_t mac;           /* 0: theta criterion (only value accepted) */
+  int32_t mac;           /* 0: theta criterion; 1: learned criterion allowed (see
+                            afd_mac_set; quadrupole moments are then always kept) */
   int32_t reserved;      /* must be 0 */
 } afd_config;
 
@@ -299,6 +301,105 @@ int afd_root_cell_static(const double *x, const double *y, const double *z, cons
  * launches; synchronises; allocates 4 bytes of scratch). Reported next to the
  * nominal peak (SMs x 128 lanes x 2 flops x clock) in benchmarks. */
 int afd_fp32_peak(int device, void *stream, double *tflops_out);
+
+/* ---------------------------------------------------------------------------
+ * Learned opening criterion.
+ *
+ * Not in the paper, which accepts a cell by its opening angle alone (the
+ * "standard Barnes-Hut scheme", Section 2; theta, Section 6.1). A small
+ * network scores a (group, cell) pair from size, distance and multipole
+ * moments and predicts the log2 of the largest relative force error, over
+ * the group's particles, that replacing the cell's particles by its
+ * superparticle would cause. The walk (afd_make_interaction_lists) then
+ * decides a cell c for group g as follows, in FP32:
+ *   - open c if it holds g's first particle;
+ *   - accept c if s^2 < theta_lo^2 d^2 (s cell side, d COM-to-box distance);
+ *   - open c unless s^2 < theta_hi^2 d^2;
+ *   - otherwise accept c iff the network's output < tau.
+ * Features (8, FP32): log2(s/d), log2(M / (d^2 A_g)), log2(|Q|_F / (M s^2)),
+ * log2(e/d), log2(n_c), log2(eps/d), u.Q.u / (|u|^2 |Q|_F), log2(|u|/d),
+ * each clamped to [-32, 32] -- M, Q, n_c the cell's mass, traceless
+ * quadrupole and particle count, A_g the smallest reference |a| among the
+ * group's particles, e half the group box diagonal, u = box centre - COM.
+ * log2 is a fixed polynomial (exponent + t p(t) on the mantissa 1 + t).
+ * Network: 8-32-32-1, ReLU, inputs (f - mu) * isd, FP16 parameters, FP32
+ * fused multiply-adds in input order. Without weights (afd_mac_set) or
+ * reference magnitudes for the current particles, the walk uses theta.
+ *
+ * Parameter vector (AFD_MAC_PARAMS floats): mu[8] isd[8] W1[32][8] b1[32]
+ * W2[32][32] b2[32] w3[32] b3[1], row-major (W[j][k]: unit j, input k).
+ * ------------------------------------------------------------------------- */
+#define AFD_MAC_FEATURES 8
+#define AFD_MAC_HIDDEN 32
+#define AFD_MAC_PARAMS 1393
+
+/* Install the network (params: host, AFD_MAC_PARAMS floats, rounded to FP16
+ * on the device) and the band [theta_lo, theta_hi] and threshold tau; params
+ * NULL removes it (theta criterion). The context must have been created
+ * with cfg.mac = 1. Synchronises. */
+int afd_mac_set(afd_ctx *ctx, const float *params, double theta_lo, double theta_hi, double tau);
+
+/* Reference acceleration magnitudes for feature 2 and the targets: amag,
+ * device, n floats, caller order (copied). With cfg.mac = 1 every force
+ * evaluation also stores |a| of its result here, so later construction
+ * steps use the latest accelerations. Does not synchronise. */
+int afd_mac_set_reference(afd_ctx *ctx, const float *amag, int64_t n);
+
+/* Training samples from the current tree (needs cfg.mac = 1, a tree and
+ * reference magnitudes for its particles, else AFD_ERR_NO_TREE /
+ * AFD_ERR_NO_REFERENCE). The pairs are those the criterion would leave to the
+ * network: a walk per group that accepts below theta_lo and opens every
+ * other cell records each visited cell in [theta_lo, theta_hi). A pair is
+ * kept when keep >= 1, or when a fixed hash of (seed, group, cell) falls
+ * below keep * 2^32. For the first min(total, cap) kept pairs, in group
+ * order: feat (device, cap x 8 floats) gets the features and label (device,
+ * cap floats) the target -- log2 of max over the group's particles of
+ * |a_cell - a_exact| / |a_ref| (superparticle term, with the quadrupole when
+ * cfg.multipole = 1, against the direct sum over the cell's particles),
+ * clamped to [-40, 8]. pair (device, cap x 2 u32 (group, cell), or NULL)
+ * receives the pairs. *n_out (host) = total kept pairs, which may exceed
+ * cap. Synchronises. */
+int afd_mac_samples(afd_ctx *ctx, double theta_lo, double theta_hi, double keep, uint64_t seed,
+                    int64_t cap, float *feat, float *label, uint32_t *pair, int64_t *n_out);
+
+/* out (host, 4 int64): [0] the last walk used the learned criterion (0/1),
+ * [1] network evaluations in it, [2] cells the network accepted, [3]
+ * reference magnitudes present for the current particles (0/1).
+ * Synchronises when [0] is 1. */
+int afd_mac_info(afd_ctx *ctx, int64_t *out);
+
+/* The network's output for n feature rows (feat: device, n x 8 floats; out:
+ * device, n floats), with params (host) rounded to FP16 exactly as the walk
+ * uses them. Queued on `stream` (a cudaStream_t, NULL = legacy default);
+ * synchronises it. */
+int afd_mlp_forward(const float *params, const float *feat, int64_t n, float *out, void *stream);
+
+/* Mean squared error of the network (FP32 parameters, not rounded) on n
+ * device samples, and its gradient with respect to every parameter (host,
+ * AFD_MAC_PARAMS floats; zero for mu and isd, which are not trained). The
+ * forward and backward passes are this library's kernels; the block partial
+ * sums are reduced in a fixed order. 1 <= n <= 2^24. Synchronises. */
+int afd_mlp_loss_grad(const float *params, const float *feat, const float *label, int64_t n,
+                      float *grad, float *loss, void *stream);
+
+/* Train the network on n device samples (feat n x 8, label n): mu and isd
+ * from the feature statistics (FP16 values), b3 from the mean target,
+ * He-normal weights from `seed`; then `epochs` passes of Adam (lr with a
+ * cosine decay to 5%, betas 0.9 / 0.999) over minibatches of `batch`
+ * (1 .. 65536) in a fresh seeded order per epoch, minimising the mean
+ * squared error. params (host, AFD_MAC_PARAMS floats) receives the FP32
+ * result; loss_hist (host, epochs floats, may be NULL) each epoch's mean
+ * minibatch loss. Deterministic for a given seed. Synchronises. */
+int afd_mlp_train(const float *feat, const float *label, int64_t n, int epochs, int batch,
+                  double lr, uint64_t seed, float *params, float *loss_hist, void *stream);
+
+/* FP64 direct summation (G = 1, Plummer softening eps, j != i, pairs at zero
+ * softened distance skipped) for n_t targets: out (device, n_t x 4 doubles)
+ * = (ax, ay, az, phi) of particle targets[t] (device u32 indices < n; a
+ * target >= n gives NaN) from the n particles x, y, z, m (device). Queued on
+ * `stream`; does not synchronise. */
+int afd_direct_sum(const double *x, const double *y, const double *z, const double *m, int64_t n,
+                   const uint32_t *targets, int64_t n_t, double eps, double *out, void *stream);
 
 /* Human-readable text for a status code (static storage). */
 const char *afd_error_string(int status);

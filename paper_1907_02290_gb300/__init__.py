@@ -95,6 +95,16 @@ def lib():
         "afd_graph_launch": ([_VP], ctypes.c_int),
         "afd_autotune_n_grp": ([_VP, _VP, _VP, _VP, _VP, _I64, _VP, ctypes.c_int, ctypes.c_int, _VP,
                                 _VP], ctypes.c_int),
+        "afd_mac_set": ([_VP, _VP, _D, _D, _D], ctypes.c_int),
+        "afd_mac_set_reference": ([_VP, _VP, _I64], ctypes.c_int),
+        "afd_mac_samples": ([_VP, _D, _D, _D, ctypes.c_uint64, _I64, _VP, _VP, _VP, _VP],
+                            ctypes.c_int),
+        "afd_mac_info": ([_VP, _VP], ctypes.c_int),
+        "afd_mlp_forward": ([_VP, _VP, _I64, _VP, _VP], ctypes.c_int),
+        "afd_mlp_loss_grad": ([_VP, _VP, _VP, _I64, _VP, _VP, _VP], ctypes.c_int),
+        "afd_mlp_train": ([_VP, _VP, _I64, ctypes.c_int, ctypes.c_int, _D, ctypes.c_uint64, _VP,
+                           _VP, _VP], ctypes.c_int),
+        "afd_direct_sum": ([_VP, _VP, _VP, _VP, _I64, _VP, _I64, _D, _VP, _VP], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -325,6 +335,105 @@ def afd_fp32_peak(device: int = 0, stream=None) -> float:
     return float(v.value)
 
 
+# ---------------------------------------------------------------- learned criterion
+
+AFD_MAC_FEATURES = 8
+AFD_MAC_HIDDEN = 32
+AFD_MAC_PARAMS = 1393
+
+
+def _host_f32(a, n, what):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if a.size != n:
+        raise ValueError(f"{what} must hold {n} floats, got {a.size}")
+    return a
+
+
+def afd_mac_set(ctx, params, theta_lo, theta_hi, tau):
+    """Install the network (host floats; None removes it)."""
+    if params is None:
+        _check(lib().afd_mac_set(ctx, None, 0.0, 0.0, 0.0), "afd_mac_set")
+        return
+    p = _host_f32(params, AFD_MAC_PARAMS, "params")
+    _check(lib().afd_mac_set(ctx, _VP(p.ctypes.data), float(theta_lo), float(theta_hi),
+                             float(tau)), "afd_mac_set")
+
+
+def afd_mac_set_reference(ctx, amag):
+    import torch
+    _check(lib().afd_mac_set_reference(ctx, _dptr(amag, torch.float32, what="amag"),
+                                       amag.numel()), "afd_mac_set_reference")
+
+
+def afd_mac_samples(ctx, theta_lo, theta_hi, keep, seed, feat, label, pair=None):
+    """Fill feat (cap x 8), label (cap) and optionally pair (cap x 2 int32
+    tensor viewed as u32); returns the total number of kept pairs."""
+    import torch
+    cap = label.numel()
+    n = ctypes.c_int64(0)
+    _check(lib().afd_mac_samples(ctx, float(theta_lo), float(theta_hi), float(keep), int(seed),
+                                 cap, _dptr(feat, torch.float32, 8 * cap, "feat"),
+                                 _dptr(label, torch.float32, cap, "label"),
+                                 _dptr(pair, torch.int32, 2 * cap, "pair"), ctypes.byref(n)),
+           "afd_mac_samples")
+    return int(n.value)
+
+
+def afd_mac_info(ctx) -> dict:
+    out = np.zeros(4, dtype=np.int64)
+    _check(lib().afd_mac_info(ctx, _VP(out.ctypes.data)), "afd_mac_info")
+    return {"learned": int(out[0]), "evaluations": int(out[1]), "accepted": int(out[2]),
+            "reference": int(out[3])}
+
+
+def afd_mlp_forward(params, feat, out, stream=None):
+    import torch
+    p = _host_f32(params, AFD_MAC_PARAMS, "params")
+    n = out.numel()
+    _check(lib().afd_mlp_forward(_VP(p.ctypes.data), _dptr(feat, torch.float32, 8 * n, "feat"), n,
+                                 _dptr(out, torch.float32, n, "out"), _stream_ptr(stream)),
+           "afd_mlp_forward")
+
+
+def afd_mlp_loss_grad(params, feat, label, stream=None):
+    """(loss, grad as numpy float32 array of AFD_MAC_PARAMS)."""
+    import torch
+    p = _host_f32(params, AFD_MAC_PARAMS, "params")
+    n = label.numel()
+    grad = np.zeros(AFD_MAC_PARAMS, dtype=np.float32)
+    loss = ctypes.c_float(0.0)
+    _check(lib().afd_mlp_loss_grad(_VP(p.ctypes.data), _dptr(feat, torch.float32, 8 * n, "feat"),
+                                   _dptr(label, torch.float32, n, "label"), n,
+                                   _VP(grad.ctypes.data), ctypes.byref(loss), _stream_ptr(stream)),
+           "afd_mlp_loss_grad")
+    return float(loss.value), grad
+
+
+def afd_mlp_train(feat, label, epochs, batch, lr, seed, stream=None):
+    """(params as numpy float32, per-epoch loss as numpy float32)."""
+    import torch
+    n = label.numel()
+    params = np.zeros(AFD_MAC_PARAMS, dtype=np.float32)
+    hist = np.zeros(int(epochs), dtype=np.float32)
+    _check(lib().afd_mlp_train(_dptr(feat, torch.float32, 8 * n, "feat"),
+                               _dptr(label, torch.float32, n, "label"), n, int(epochs), int(batch),
+                               float(lr), int(seed), _VP(params.ctypes.data),
+                               _VP(hist.ctypes.data), _stream_ptr(stream)), "afd_mlp_train")
+    return params, hist
+
+
+def afd_direct_sum(x, y, z, m, targets, eps, out, stream=None):
+    """out: (n_t, 4) float64 CUDA tensor; targets: int32 CUDA tensor (u32)."""
+    import torch
+    n = x.numel()
+    nt = targets.numel()
+    _check(lib().afd_direct_sum(_dptr(x, torch.float64, n, "x"), _dptr(y, torch.float64, n, "y"),
+                                _dptr(z, torch.float64, n, "z"), _dptr(m, torch.float64, n, "m"),
+                                n, _dptr(targets, torch.int32, nt, "targets"), nt, float(eps),
+                                _dptr(out, torch.float64, 4 * nt, "out"), _stream_ptr(stream)),
+           "afd_direct_sum")
+
+
 # ---------------------------------------------------------------- convenience
 
 
@@ -336,10 +445,11 @@ class Config:
     n_grp: int = 64
     multipole: int = 0
     far_precision: int = 0
+    mac: int = 0
 
     def c(self) -> afd_config:
         return afd_config(float(self.eps), float(self.theta), int(self.n_leaf), int(self.n_grp),
-                          int(self.multipole), int(self.far_precision), 0, 0)
+                          int(self.multipole), int(self.far_precision), int(self.mac), 0)
 
 
 class Gravity:

@@ -167,7 +167,11 @@ int reuse(afd_ctx *c, const double *x, const double *y, const double *z, const d
 int calc_force(afd_ctx *c, float *acc4) {
   if (!c->have_lists) return c->have_tree ? AFD_ERR_NO_SAVED_LIST : AFD_ERR_NO_TREE;
   if (c->n > 0 && !acc4) return AFD_ERR_ARG;
-  return launch_force(c, acc4);
+  TRY(launch_force(c, acc4));
+  // the learned opening criterion scales cells by these magnitudes at the
+  // next construction step
+  if (c->cfg.mac) TRY(launch_amag(c, acc4));
+  return AFD_OK;
 }
 
 int calc_force_all(afd_ctx *c, const double *x, const double *y, const double *z,
@@ -220,7 +224,7 @@ int afd_create(afd_ctx **out, const afd_config *cfg, int device, void *stream) {
   if (!std::isfinite(cfg->eps) || cfg->eps < 0.0 || !std::isfinite(cfg->theta) ||
       cfg->theta < 0.0 || cfg->n_leaf < 1 || cfg->n_grp < 1 || cfg->n_grp > 1024 ||
       (cfg->multipole != 0 && cfg->multipole != 1) || cfg->far_precision < 0 ||
-      cfg->far_precision > 2 || cfg->mac != 0 || cfg->reserved != 0)
+      cfg->far_precision > 2 || (cfg->mac != 0 && cfg->mac != 1) || cfg->reserved != 0)
     return AFD_ERR_ARG;
   DeviceGuard g(device);
   if (!g.ok) return AFD_ERR_CUDA;
@@ -257,7 +261,9 @@ void afd_destroy(afd_ctx *c) {
                     &c->g_self, &c->u_cnt, &c->u_off, &c->u_info, &c->l_cnt_e,
                     &c->l_cnt_s, &c->epj_off, &c->spj_off, &c->epj, &c->spj, &c->scan_tmp,
                     &c->hx, &c->hy, &c->hz, &c->hm, &c->hacc, &c->sys_off_d,
-                    &c->sys_grp_d, &c->sys_of, &c->sys_s, &c->root_tiles, &c->g_root};
+                    &c->sys_grp_d, &c->sys_of, &c->sys_s, &c->root_tiles, &c->g_root,
+                    &c->mac_w, &c->amag, &c->amag_s, &c->g_amin, &c->mac_cnt,
+                    &c->band_cnt, &c->band_off};
   for (DevBuf *b : bufs) release(*b);
   if (c->pinned) cudaFreeHost(c->pinned);
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -443,6 +449,7 @@ int afd_graph_capture_step(afd_ctx *c, double *x, double *y, double *z, double *
   DeviceGuard g(c->device);
   graph_release(c);
   const int64_t n = c->n;
+  if (c->cfg.mac) TRY(reserve(c->amag, sizeof(float) * (size_t)n));  // no allocation in capture
   TRY(cuda_ok(cudaStreamSynchronize(c->stream)));
   if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaGetLastError();
@@ -625,6 +632,8 @@ const char *afd_error_string(int status) {
     case AFD_ERR_OOM: return "device allocation failed";
     case AFD_ERR_WALK_STACK: return "tree walk overflowed its stack";
     case AFD_ERR_TOO_LARGE: return "problem size above the static scratch limit (n <= 2^31 - 1)";
+    case AFD_ERR_NO_REFERENCE:
+      return "no reference accelerations for the current particles (learned opening criterion)";
     default: return "unknown status";
   }
 }

@@ -111,6 +111,18 @@ struct afd_ctx {
   int64_t eval_counter = 0;
   int64_t launches = 0;  // kernels queued by this context so far
 
+  // learned opening criterion (afd_mac.cuh): FP16-valued weights, band and
+  // threshold, reference |a| per particle (caller order) and its Morton-order
+  // copy and per-group minimum for the current tree
+  afd::DevBuf mac_w;
+  bool mac_ready = false;
+  float mac_lo2 = 0.0f, mac_hi2 = 0.0f, mac_tau = 0.0f;
+  afd::DevBuf amag, amag_s, g_amin;
+  int64_t amag_n = -1;
+  bool walk_learned = false;  // the last walk used the learned criterion
+  afd::DevBuf mac_cnt;        // u64[2]: network evaluations, accepted (count pass)
+  afd::DevBuf band_cnt, band_off;
+
   // captured reusing timestep (afd_graph_capture_step / afd_graph_launch)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -138,6 +150,11 @@ int launch_group_boxes(afd_ctx *c);
 
 // ---- walk (afd_walk.cu) ----
 int launch_walk(afd_ctx *c);  // lists; sets n_epj, n_spj, interactions (syncs)
+
+// ---- learned opening criterion (afd_mac.cu) ----
+bool mac_usable(const afd_ctx *c);   // weights, reference |a| and quadrupoles present
+int launch_group_amin(afd_ctx *c);   // amag_s and g_amin for the current tree
+int launch_amag(afd_ctx *c, const float *acc4);  // reference |a| from a force result
 
 // ---- force (afd_force.cu) ----
 int launch_force(afd_ctx *c, float *acc4);

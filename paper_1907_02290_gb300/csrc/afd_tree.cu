@@ -1032,7 +1032,9 @@ int launch_moments(afd_ctx *c, bool child_blocks) {
   if (nc == 0) return AFD_OK;
   if (cudaMemsetAsync(c->c_arrive.p, 0, sizeof(unsigned) * nc, c->stream) != cudaSuccess)
     return AFD_ERR_CUDA;
-  if (!c->cfg.multipole) {
+  // quadrupoles for the far field, and for the learned opening criterion
+  const bool quad_on = c->cfg.multipole || c->cfg.mac;
+  if (!quad_on) {
     if (cudaMemsetAsync(c->c_quad.p, 0, sizeof(double) * 6 * nc, c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->s_q0.p, 0, sizeof(float4) * nc, c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->s_q1.p, 0, sizeof(float4) * nc, c->stream) != cudaSuccess)
@@ -1064,7 +1066,7 @@ int launch_moments(afd_ctx *c, bool child_blocks) {
   a.node_f = ptr<float4>(c->node_f);
   a.node_i = ptr<uint2>(c->node_i);
   a.block = child_blocks ? ptr<uint4>(c->c_block) : nullptr;
-  a.quad_on = c->cfg.multipole;
+  a.quad_on = quad_on;
   k_moments<<<blocks_for(nc), kThreads, 0, c->stream>>>(a);
   c->launches++;
   return ck();

@@ -18,7 +18,12 @@
 // distance from the cell's centre of mass to the group's bounding box (0
 // inside) and s the cell side, the cell is accepted iff s^2 < theta^2 d^2,
 // computed as ((dx*dx + dy*dy) + dz*dz) and theta2 * d2 in that order.
+//
+// With the learned criterion (afd_mac.cuh) the same walk decides each cell
+// by decide_learned(): the band tests in FP32 and, inside the band, the
+// network evaluated by the deciding lane with the weights in shared memory.
 #include "afd_internal.cuh"
+#include "afd_mac.cuh"
 
 namespace afd {
 namespace {
@@ -42,6 +47,11 @@ struct WalkArgs {
   uint32_t *epj, *spj;
   int *status;
   uint32_t iter_cap;
+  // learned criterion
+  const float *mac_w, *g_amin;
+  const float4 *s_hi, *s_q0, *s_q1;
+  float lo2, hi2, tau, eps2;
+  unsigned long long *mac_cnt;
 };
 
 __device__ __forceinline__ float sep_axis(float c, float lo, float hi) {
@@ -65,6 +75,34 @@ __device__ __forceinline__ uint32_t decide(const float *bmin, const float *bmax,
   return leaf ? kLeaf : kOpen;
 }
 
+__device__ __forceinline__ uint32_t decide_learned(const WalkArgs &a, const float *w,
+                                                   const float *bmin, const float *bmax, float cx,
+                                                   float cy, float cz, float s2, bool leaf,
+                                                   uint32_t id, uint32_t first, uint32_t count,
+                                                   uint32_t gfirst, float amin, uint32_t &evals,
+                                                   uint32_t &accepts) {
+  const uint32_t closed = leaf ? kLeaf : kOpen;
+  if (gfirst >= first && gfirst - first < count) return closed;  // holds the group
+  const float dx = sep_axis(cx, bmin[0], bmax[0]);
+  const float dy = sep_axis(cy, bmin[1], bmax[1]);
+  const float dz = sep_axis(cz, bmin[2], bmax[2]);
+  float d2 = __fmul_rn(dx, dx);
+  d2 = __fadd_rn(d2, __fmul_rn(dy, dy));
+  d2 = __fadd_rn(d2, __fmul_rn(dz, dz));
+  if (s2 < __fmul_rn(a.lo2, d2)) return kAccept;
+  if (!(s2 < __fmul_rn(a.hi2, d2))) return closed;
+  const float4 sh = a.s_hi[id], q0 = a.s_q0[id], q1 = a.s_q1[id];
+  float f[kMacNF];
+  mac_features(bmin, bmax, cx, cy, cz, s2, sh.w, q0, make_float2(q1.x, q1.y), count, a.eps2,
+               amin, f);
+  evals++;
+  if (mac_mlp(w, f) < a.tau) {
+    accepts++;
+    return kAccept;
+  }
+  return closed;
+}
+
 // Stack entry: x = cell id (open / accepted) or first particle (leaf);
 // y = decision << 30 | particle count (leaf).
 __device__ __forceinline__ uint2 make_entry(uint32_t dec, uint32_t id, uint32_t first,
@@ -72,12 +110,18 @@ __device__ __forceinline__ uint2 make_entry(uint32_t dec, uint32_t id, uint32_t 
   return dec == kLeaf ? make_uint2(first, (dec << 30) | count) : make_uint2(id, dec << 30);
 }
 
-template <bool FILL>
+template <bool FILL, bool LEARNED>
 __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
   __shared__ uint2 stk_all[kWalkWarps][kStack];
+  __shared__ float wsm[LEARNED ? kMacNP : 1];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
   uint2 *stk = stk_all[wib];
+  uint32_t evals = 0, accepts = 0;
+  if (LEARNED) {
+    for (int i = threadIdx.x; i < kMacNP; i += kWalkThreads) wsm[i] = a.mac_w[i];
+    __syncthreads();
+  }
   for (int64_t g = (int64_t)blockIdx.x * kWalkWarps + wib; g < a.n_groups;
        g += (int64_t)gridDim.x * kWalkWarps) {
     float bmin[3], bmax[3];
@@ -87,6 +131,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
       bmax[k] = a.boxf[g * 6 + 3 + k];
     }
     const uint32_t gfirst = a.g_first[g];
+    const float amin = LEARNED ? a.g_amin[g] : 0.0f;
     const uint64_t be = FILL ? a.off_e[g] : 0, bs = FILL ? a.off_s[g] : 0;
     uint64_t ne = 0, ns = 0;
     uint32_t self_pos = 0;  // 1 + EPJ-list position of the group's first particle
@@ -94,8 +139,13 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
       const uint32_t root = a.g_root[g];
       const float4 nf = a.node_f[root];
       const uint2 ni = a.node_i[root];
-      const uint32_t d = decide(bmin, bmax, nf.x, nf.y, nf.z, nf.w, (ni.y >> 31) != 0, a.theta2);
-      stk[0] = make_entry(d, root, ni.x, ni.y & 0x7fffffffu);
+      const bool leaf = (ni.y >> 31) != 0;
+      const uint32_t cnt = ni.y & 0x7fffffffu;
+      const uint32_t d =
+          LEARNED ? decide_learned(a, wsm, bmin, bmax, nf.x, nf.y, nf.z, nf.w, leaf, root, ni.x,
+                                   cnt, gfirst, amin, evals, accepts)
+                  : decide(bmin, bmax, nf.x, nf.y, nf.z, nf.w, leaf, a.theta2);
+      stk[0] = make_entry(d, root, ni.x, cnt);
     }
     int sp = 1;
     uint32_t iters = 0;
@@ -175,10 +225,15 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
         const uint4 nf = blk[0], meta = blk[1];
         valid = meta.z != kNone;
         if (valid) {
-          const uint32_t d = decide(bmin, bmax, __uint_as_float(nf.x), __uint_as_float(nf.y),
-                                    __uint_as_float(nf.z), __uint_as_float(nf.w),
-                                    (meta.y >> 31) != 0, a.theta2);
-          child_entry = make_entry(d, meta.z, meta.x, meta.y & 0x7fffffffu);
+          const bool leaf = (meta.y >> 31) != 0;
+          const uint32_t cnt = meta.y & 0x7fffffffu;
+          const float cx = __uint_as_float(nf.x), cy = __uint_as_float(nf.y),
+                      cz = __uint_as_float(nf.z), s2 = __uint_as_float(nf.w);
+          const uint32_t d =
+              LEARNED ? decide_learned(a, wsm, bmin, bmax, cx, cy, cz, s2, leaf, meta.z, meta.x,
+                                       cnt, gfirst, amin, evals, accepts)
+                      : decide(bmin, bmax, cx, cy, cz, s2, leaf, a.theta2);
+          child_entry = make_entry(d, meta.z, meta.x, cnt);
         }
       }
       const unsigned vm = __ballot_sync(0xffffffffu, valid);
@@ -223,6 +278,17 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
       a.gself[g] = self_pos;
     }
     __syncwarp();
+  }
+  if (LEARNED && !FILL) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      evals += __shfl_xor_sync(0xffffffffu, evals, o);
+      accepts += __shfl_xor_sync(0xffffffffu, accepts, o);
+    }
+    if (lane == 0 && evals) {
+      atomicAdd(&a.mac_cnt[0], (unsigned long long)evals);
+      atomicAdd(&a.mac_cnt[1], (unsigned long long)accepts);
+    }
   }
 }
 
@@ -299,9 +365,34 @@ int launch_walk(afd_ctx *c) {
   a.spj = nullptr;
   a.status = ptr<int>(c->status);
   a.iter_cap = (uint32_t)(2 * c->n_cells + 64);
+  const bool learned = mac_usable(c);
+  a.mac_w = nullptr;
+  a.g_amin = nullptr;
+  a.s_hi = a.s_q0 = a.s_q1 = nullptr;
+  a.lo2 = a.hi2 = a.tau = a.eps2 = 0.0f;
+  a.mac_cnt = nullptr;
+  if (learned) {
+    if ((st = launch_group_amin(c))) return st;
+    if ((st = reserve(c->mac_cnt, 2 * sizeof(unsigned long long)))) return st;
+    if (cudaMemsetAsync(c->mac_cnt.p, 0, 2 * sizeof(unsigned long long), c->stream) != cudaSuccess)
+      return AFD_ERR_CUDA;
+    a.mac_w = ptr<float>(c->mac_w);
+    a.g_amin = ptr<float>(c->g_amin);
+    a.s_hi = ptr<float4>(c->s_hi);
+    a.s_q0 = ptr<float4>(c->s_q0);
+    a.s_q1 = ptr<float4>(c->s_q1);
+    a.lo2 = c->mac_lo2;
+    a.hi2 = c->mac_hi2;
+    a.tau = c->mac_tau;
+    const float e = (float)c->cfg.eps;
+    a.eps2 = e * e;
+    a.mac_cnt = ptr<unsigned long long>(c->mac_cnt);
+  }
+  c->walk_learned = learned;
   int64_t nb = (ng + kWalkWarps - 1) / kWalkWarps;
   if (nb > 152 * 32) nb = 152 * 32;
-  k_walk<false><<<(unsigned)nb, kWalkThreads, 0, c->stream>>>(a);
+  if (learned) k_walk<false, true><<<(unsigned)nb, kWalkThreads, 0, c->stream>>>(a);
+  else k_walk<false, false><<<(unsigned)nb, kWalkThreads, 0, c->stream>>>(a);
   c->launches++;
   if (cudaGetLastError() != cudaSuccess) return AFD_ERR_CUDA;
   if ((st = scan_u32_to_u64(c, a.cnt_e, ptr<uint64_t>(c->epj_off), ng))) return st;
@@ -328,7 +419,8 @@ int launch_walk(afd_ctx *c) {
   if ((st = reserve(c->spj, sizeof(uint32_t) * c->n_spj))) return st;
   a.epj = ptr<uint32_t>(c->epj);
   a.spj = ptr<uint32_t>(c->spj);
-  k_walk<true><<<(unsigned)nb, kWalkThreads, 0, c->stream>>>(a);
+  if (learned) k_walk<true, true><<<(unsigned)nb, kWalkThreads, 0, c->stream>>>(a);
+  else k_walk<true, false><<<(unsigned)nb, kWalkThreads, 0, c->stream>>>(a);
   c->launches++;
   return cudaGetLastError() == cudaSuccess ? AFD_OK : AFD_ERR_CUDA;
 }

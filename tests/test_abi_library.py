@@ -53,11 +53,22 @@ def test_host_side_validation_without_gpu(libpath):
     assert "saved" in afd.afd_error_string(-4)
     h = ctypes.c_void_p()
     for bad in (afd.Config(n_grp=0), afd.Config(n_grp=2048), afd.Config(eps=-1.0),
-                afd.Config(theta=float("nan")), afd.Config(n_leaf=0), afd.Config(multipole=2)):
+                afd.Config(theta=float("nan")), afd.Config(n_leaf=0), afd.Config(multipole=2),
+                afd.Config(mac=2)):
         assert L.afd_create(ctypes.byref(h), ctypes.byref(bad.c()), 0, None) == -1
     assert L.afd_create(None, None, 0, None) == -1
     assert L.afd_calc_force(None, None) == -1
     assert L.afd_stats(None, None) == -1
+    # learned criterion: argument checks happen before any device work
+    assert L.afd_mac_set(None, None, 0.0, 0.0, 0.0) == -1
+    assert L.afd_mac_set_reference(None, None, 0) == -1
+    assert L.afd_mac_info(None, None) == -1
+    assert L.afd_mlp_forward(None, None, 0, None, None) == -1
+    assert L.afd_mlp_loss_grad(None, None, None, 0, None, None, None) == -1
+    assert L.afd_mlp_train(None, None, 0, 1, 1, 1e-3, 0, None, None, None) == -1
+    assert L.afd_direct_sum(None, None, None, None, 10, None, 0, 0.0, None, None) == 0
+    assert L.afd_direct_sum(None, None, None, None, 10, None, 5, -1.0, None, None) == -1
+    assert afd.afd_error_string(-12).startswith("no reference accelerations")
 
 
 def test_product_path_never_touches_the_oracle():
