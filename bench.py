@@ -63,6 +63,11 @@ def parse():
                     help="far-field precision of quadrupole superparticles: 0 fp32, 1 bf16, 2 fp16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-criterion form and the equal-error comparison")
+    ap.add_argument("--mac-samples", type=int, default=1_000_000)
+    ap.add_argument("--mac-band", default="0.25,1.0",
+                    help="theta_lo,theta_hi of the learned criterion's band")
     return ap.parse_args()
 
 
@@ -252,6 +257,214 @@ def run_reference(args, wl):
     print(json.dumps(line))
 
 
+def run_loop(afd, torch, ctx, g, st, *, steps, warmup, batch, R, dt, flush, stream, dev,
+             before_timed=None):
+    """Warm-up, then `steps` timed KDK steps (CUDA events around each, L2
+    flushed in between). st: dict of the state tensors and the evaluation
+    counter. Returns per-step ms, force ms, interactions, modes, launches."""
+    x, y, z, vx, vy, vz, m, acc = (st[k] for k in ("x", "y", "z", "vx", "vy", "vz", "m", "acc"))
+
+    def step():
+        k = st["k"]
+        mode = afd.AFD_MAKE_LIST_FOR_REUSE if k % R == 0 else afd.AFD_REUSE_LIST
+        if batch and mode == afd.AFD_REUSE_LIST:
+            afd.afd_graph_launch(ctx)  # kick-drift, reusing step, force, kick
+        else:
+            afd.afd_kick_drift(ctx, x, y, z, vx, vy, vz, acc, 0.5 * dt, dt)
+            afd.afd_calc_force_all(ctx, x, y, z, m, acc, mode)
+            afd.afd_kick(ctx, vx, vy, vz, acc, 0.5 * dt)
+            if batch:  # buffers may have moved: capture the new reusing step
+                afd.afd_graph_capture_step(ctx, x, y, z, vx, vy, vz, m, acc, dt)
+        st["k"] = k + 1
+        return mode
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if before_timed:
+        before_timed()
+    launches0 = g.stats()["launches"]
+    step_ms, force_ms, inter, modes = [], [], [], []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mode = step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        if not (batch and mode == afd.AFD_REUSE_LIST):  # graph replays carry no events
+            force_ms.append(afd.afd_last_force_ms(ctx))
+        inter.append(g.stats()["interactions"])
+        modes.append(mode)
+    torch.cuda.synchronize(dev)
+    return step_ms, force_ms, inter, modes, g.stats()["launches"] - launches0
+
+
+def learned_study(args, wl, afd, torch, np, dev, stream, local, p, tuned, flush, plain):
+    """The learned opening criterion against the plain theta form at equal
+    rms force error (error against the FP64 direct sum of sampled
+    particles): train the network on the GPU from a sphere like the N = 2^20
+    workload, calibrate tau so the learned form's error matches the plain
+    form's, then time the learned form's steps like the plain ones."""
+    import ics
+
+    t0 = time.perf_counter()
+    lo, hi = (float(v) for v in args.mac_band.split(","))
+    T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    batch = wl["model"] == "batch"
+    R, dt = wl["n_reuse"], wl["dt"]
+    base = dict(n_leaf=16, multipole=int(wl["quad"]), far_precision=int(wl.get("far", 0)))
+
+    # ---- training samples from a sphere like the N = 2^20 workload ----
+    tw = dict(ics.WORKLOADS["plummer_1m"])
+    q = ics.plummer(tw["n"], tw["seed"] + 1000)
+    qx = [T(a) for a in (q.x, q.y, q.z, q.m)]
+    gt = afd.Gravity(afd.Config(eps=tw["eps"], theta=tw["theta"], n_grp=tw["n_grp"], mac=1,
+                                **base), local, stream)
+    acc_t = torch.empty(q.n, 4, dtype=torch.float32, device=dev)
+    gt.force_all(*qx, acc_t, afd.AFD_MAKE_LIST)  # the plain form's |a| becomes the reference
+    cap = int(args.mac_samples)
+    feat = torch.empty(cap, 8, dtype=torch.float32, device=dev)
+    lab = torch.empty(cap, dtype=torch.float32, device=dev)
+    total = afd.afd_mac_samples(gt.ctx, lo, hi, 1.0, 0, feat[:0], lab[:0])
+    keep = min(1.0, cap / max(total, 1))
+    n_s = afd.afd_mac_samples(gt.ctx, lo, hi, keep, 7, feat, lab)
+    n_s = min(n_s, cap)
+    gt.close()
+    t_samp = time.perf_counter() - t0
+    epochs = 12
+    params, hist = afd.afd_mlp_train(feat[:n_s], lab[:n_s], epochs=epochs, batch=1024, lr=2e-3,
+                                     seed=5, stream=stream)
+    t_train = time.perf_counter() - t0 - t_samp
+    del feat, lab
+
+    # ---- exact forces of sampled particles (FP64 direct sum per system) ----
+    off = wl["sys_off"] if batch else np.array([0, p.n])
+    n_sys = len(off) - 1
+    per = max(1, 4096 // n_sys)
+    xs0 = [T(a) for a in (p.x, p.y, p.z, p.m)]
+    tg_all, ex = [], []
+    for s_ in range(n_sys):
+        a, b = int(off[s_]), int(off[s_ + 1])
+        loc = np.unique(np.linspace(0, b - a - 1, min(per, b - a)).astype(np.int64))
+        out = torch.empty(len(loc), 4, dtype=torch.float64, device=dev)
+        afd.afd_direct_sum(*(v[a:b] for v in xs0),
+                           torch.tensor(loc.astype(np.int32), device=dev), wl["eps"], out, stream)
+        tg_all.append(loc + a)
+        ex.append(out)
+    tg = np.concatenate(tg_all)
+    ex = torch.cat(ex).cpu().numpy()
+    tg_t = torch.tensor(tg, device=dev)
+
+    def rms_err(acc):
+        a = acc[tg_t].double().cpu().numpy()
+        num = ((a[:, :3] - ex[:, :3]) ** 2).sum(1)
+        return float(np.sqrt(np.mean(num / (ex[:, :3] ** 2).sum(1))))
+
+    def ctx_for(mac):
+        cfg = afd.Config(eps=wl["eps"], theta=wl["theta"], n_grp=wl["n_grp"], mac=mac, **base)
+        gg = afd.Gravity(cfg, local, stream)
+        if batch:
+            afd.afd_set_systems(gg.ctx, wl["sys_off"], tuned)
+        return gg
+
+    # plain form at the initial positions; its |a| is the learned form's reference
+    gp = ctx_for(0)
+    acc_p = torch.empty(p.n, 4, dtype=torch.float32, device=dev)
+    gp.force_all(*xs0, acc_p, afd.AFD_MAKE_LIST)
+    e_plain = rms_err(acc_p)
+    i_plain0 = gp.stats()["interactions"]
+    gp.close()
+    amag = torch.sqrt((acc_p[:, :3].double() ** 2).sum(1)).float().contiguous()
+
+    gl = ctx_for(1)
+    acc_l = torch.empty(p.n, 4, dtype=torch.float32, device=dev)
+
+    def learned_err(tau):
+        afd.afd_mac_set(gl.ctx, params, lo, hi, tau)
+        afd.afd_tree_build(gl.ctx, *xs0)
+        afd.afd_mac_set_reference(gl.ctx, amag)
+        afd.afd_make_interaction_lists(gl.ctx, afd.AFD_MAKE_LIST)
+        afd.afd_calc_force(gl.ctx, acc_l)
+        return rms_err(acc_l), gl.stats()["interactions"]
+
+    # tau: coarse grid, then bisection on log error toward e_plain
+    grid = {}
+    for tau in np.arange(-18.0, -6.0, 1.0):
+        grid[float(tau)] = learned_err(float(tau))
+    taus = sorted(grid)
+    lo_t, hi_t = None, None
+    for a_, b_ in zip(taus, taus[1:]):
+        if grid[a_][0] <= e_plain <= grid[b_][0]:
+            lo_t, hi_t = a_, b_
+    if lo_t is None:  # no crossing: the most accurate tau below the plain error
+        ok = [t_ for t_ in taus if grid[t_][0] <= e_plain]
+        tau_star = max(ok) if ok else min(taus)
+    else:
+        for _ in range(6):
+            mid = 0.5 * (lo_t + hi_t)
+            grid[mid] = learned_err(mid)
+            if grid[mid][0] <= e_plain:
+                lo_t = mid
+            else:
+                hi_t = mid
+        tau_star = lo_t  # error not above the plain form's
+    e_learned, i_learned0 = grid[tau_star]
+    gl.close()
+    t_cal = time.perf_counter() - t0 - t_samp - t_train
+
+    # ---- the learned form timed like the plain one ----
+    gl = ctx_for(1)
+    afd.afd_mac_set(gl.ctx, params, lo, hi, tau_star)
+    st = {k: T(getattr(p, k)) for k in ("x", "y", "z", "vx", "vy", "vz", "m")}
+    st["acc"] = torch.zeros(p.n, 4, dtype=torch.float32, device=dev)
+    st["k"] = 1
+    # evaluation 0 has no reference accelerations yet: theta lists; the
+    # learned criterion decides every later construction step
+    afd.afd_calc_force_all(gl.ctx, st["x"], st["y"], st["z"], st["m"], st["acc"],
+                           afd.AFD_MAKE_LIST_FOR_REUSE)
+    if batch:
+        afd.afd_graph_capture_step(gl.ctx, st["x"], st["y"], st["z"], st["vx"], st["vy"],
+                                   st["vz"], st["m"], st["acc"], dt)
+    step_ms, force_ms, inter, modes, launches = run_loop(
+        afd, torch, gl.ctx, gl, st, steps=args.steps, warmup=args.warmup, batch=batch, R=R,
+        dt=dt, flush=flush, stream=stream, dev=dev)
+    info = afd.afd_mac_info(gl.ctx)
+    gl.close()
+    cons = [v for v, md in zip(step_ms, modes) if md == afd.AFD_MAKE_LIST_FOR_REUSE]
+    reus = [v for v, md in zip(step_ms, modes) if md == afd.AFD_REUSE_LIST]
+    ms_l = float(np.mean(step_ms))
+    return {
+        "criterion": "8-32-32-1 network (FP16 weights, FP32 arithmetic) inside the walk for "
+                     f"cells with theta_lo={lo} <= s/d < theta_hi={hi}; accepted below, opened "
+                     "above; reference |a| from the previous force evaluation",
+        "tau": tau_star,
+        "equal_error": {"plain_rms_rel_err": e_plain, "learned_rms_rel_err": e_learned,
+                        "targets": int(len(tg)), "reference": "FP64 direct sum (afd_direct_sum)",
+                        "plain_interactions": i_plain0, "learned_interactions": i_learned0},
+        "ms_per_step": ms_l,
+        "ms_per_construction_step": float(np.mean(cons)) if cons else None,
+        "ms_per_reuse_step": float(np.mean(reus)) if reus else None,
+        "interactions_per_step": float(np.mean(inter)),
+        "interactions_per_s": float(sum(inter)) / (sum(step_ms) * 1e-3),
+        "force_ms_mean": float(np.mean(force_ms)) if force_ms else None,
+        "plain_ms_per_step": plain["ms_per_step"],
+        "speedup_ms_per_step_vs_plain": plain["ms_per_step"] / ms_l,
+        "interaction_ratio_plain_over_learned": plain["interactions_per_step"] / float(np.mean(inter)),
+        "gpu_launches": launches,
+        "walk_network_evaluations_last_construction": info["evaluations"],
+        "walk_network_accepts_last_construction": info["accepted"],
+        "training": {"samples": n_s, "band_pairs_total": total, "epochs": epochs,
+                     "batch": 1024, "final_mse_log2": float(hist[-1]),
+                     "first_epoch_mse_log2": float(hist[0]), "sample_s": t_samp,
+                     "train_s": t_train, "calibrate_s": t_cal,
+                     "data": f"Plummer N={tw['n']} seed {tw['seed'] + 1000}, eps={tw['eps']:.6g}, "
+                             f"n_grp={tw['n_grp']}, reference |a| from theta={tw['theta']}"},
+    }
+
+
 def main():
     args = parse()
     wl = workload(args.workload)
@@ -304,49 +517,21 @@ def main():
     afd.afd_calc_force_all(ctx, x, y, z, m, acc, afd.AFD_MAKE_LIST_FOR_REUSE)  # evaluation 0
     if batch:
         afd.afd_graph_capture_step(ctx, x, y, z, vx, vy, vz, m, acc, dt)
-    state = {"k": 1}
-
-    def step():
-        k = state["k"]
-        mode = afd.AFD_MAKE_LIST_FOR_REUSE if k % R == 0 else afd.AFD_REUSE_LIST
-        if batch and mode == afd.AFD_REUSE_LIST:
-            afd.afd_graph_launch(ctx)  # kick-drift, reusing step, force, kick
-        else:
-            afd.afd_kick_drift(ctx, x, y, z, vx, vy, vz, acc, 0.5 * dt, dt)
-            afd.afd_calc_force_all(ctx, x, y, z, m, acc, mode)
-            afd.afd_kick(ctx, vx, vy, vz, acc, 0.5 * dt)
-            if batch:  # buffers may have moved: capture the new reusing step
-                afd.afd_graph_capture_step(ctx, x, y, z, vx, vy, vz, m, acc, dt)
-        state["k"] = k + 1
-        return mode
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize(dev)
-    if dist:
-        dist.barrier()
+    state = {"x": x, "y": y, "z": z, "vx": vx, "vy": vy, "vz": vz, "m": m, "acc": acc, "k": 1}
     sampler = ClockSampler(local)
-    sampler.start()
-    time.sleep(0.3)
-    launches0 = g.stats()["launches"]
-    step_ms, force_ms, inter, modes = [], [], [], []
-    t_wall = time.perf_counter()
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        mode = step()
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        if not (batch and mode == afd.AFD_REUSE_LIST):  # graph replays carry no events
-            force_ms.append(afd.afd_last_force_ms(ctx))
-        inter.append(g.stats()["interactions"])
-        modes.append(mode)
-    torch.cuda.synchronize(dev)
-    t_wall = time.perf_counter() - t_wall
-    launches = g.stats()["launches"] - launches0
+    t_wall = [0.0]
+
+    def before_timed():
+        if dist:
+            dist.barrier()
+        sampler.start()
+        time.sleep(0.3)
+        t_wall[0] = time.perf_counter()
+
+    step_ms, force_ms, inter, modes, launches = run_loop(
+        afd, torch, ctx, g, state, steps=args.steps, warmup=args.warmup, batch=batch, R=R, dt=dt,
+        flush=flush, stream=stream, dev=dev, before_timed=before_timed)
+    t_wall = time.perf_counter() - t_wall[0]
     clocks = sampler.stop()
     total_ms = float(sum(step_ms))
     total_i = float(sum(inter))
@@ -441,6 +626,9 @@ def main():
     }
     if e2e:
         line["e2e"] = e2e
+    if not args.no_learned and world == 1 and not wl["quad"]:
+        line["learned_mac"] = learned_study(args, wl, afd, torch, np, dev, stream, local, p,
+                                            tuned, flush, line)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line))

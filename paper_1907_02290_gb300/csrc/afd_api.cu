@@ -263,7 +263,8 @@ void afd_destroy(afd_ctx *c) {
                     &c->hx, &c->hy, &c->hz, &c->hm, &c->hacc, &c->sys_off_d,
                     &c->sys_grp_d, &c->sys_of, &c->sys_s, &c->root_tiles, &c->g_root,
                     &c->mac_w, &c->amag, &c->amag_s, &c->g_amin, &c->mac_cnt,
-                    &c->band_cnt, &c->band_off};
+                    &c->band_cnt, &c->band_off, &c->l_nrec, &c->l_head_s, &c->l_head_l,
+                    &c->arena_s, &c->arena_l, &c->next_s, &c->next_l, &c->arena_cur};
   for (DevBuf *b : bufs) release(*b);
   if (c->pinned) cudaFreeHost(c->pinned);
   if (c->ev0) cudaEventDestroy(c->ev0);

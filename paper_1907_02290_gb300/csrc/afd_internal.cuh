@@ -84,6 +84,11 @@ struct afd_ctx {
 
   // lists (CSR)
   afd::DevBuf l_cnt_e, l_cnt_s, epj_off, spj_off, epj, spj;
+  // walk record arena: per group leaf-record count and chunk-chain heads;
+  // chunks of cell ids / leaf records, chain links, cursors (capacity in chunks)
+  afd::DevBuf l_nrec, l_head_s, l_head_l;
+  afd::DevBuf arena_s, arena_l, next_s, next_l, arena_cur;
+  uint32_t arena_cap_s = 0, arena_cap_l = 0;
 
   // scan scratch
   afd::DevBuf scan_tmp;

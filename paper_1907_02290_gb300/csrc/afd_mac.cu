@@ -344,15 +344,15 @@ __global__ void k_fp16_round(float *w, int n) {
 __global__ void __launch_bounds__(256) k_mlp_forward(const float *__restrict__ w,
                                                      const float *__restrict__ feat, int64_t n,
                                                      float *__restrict__ out) {
-  __shared__ float wsm[kMacNP];
-  for (int i = threadIdx.x; i < kMacNP; i += blockDim.x) wsm[i] = w[i];
+  __shared__ __align__(16) float wsm[kMacNP + 3];
+  mac_load_transposed(wsm, w, threadIdx.x, blockDim.x);
   __syncthreads();
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   float f[kMacNF];
 #pragma unroll
   for (int k = 0; k < kMacNF; k++) f[k] = feat[s * kMacNF + k];
-  out[s] = mac_mlp(wsm, f);
+  out[s] = mac_mlp_t(wsm, f);
 }
 
 // Per-block FP64 sums of each feature, its square and the target.

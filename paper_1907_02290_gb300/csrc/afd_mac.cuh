@@ -135,4 +135,100 @@ __device__ __forceinline__ float mac_mlp(const float *w, const float *f) {
   return y;
 }
 
+// ---- the same network on transposed weights, two units per instruction ----
+// Shared-memory layout for mac_mlp_t (offsets as in the flat vector, the two
+// weight matrices transposed to [input][unit]): mu, isd, W1T[8][32], b1,
+// W2T[32][32], b2, w3, b3. Each unit still accumulates its bias and then its
+// inputs in index order with one rounding per fused multiply-add, so the
+// result equals mac_mlp's bit for bit; the packed FMA (fma.rn.f32x2) rounds
+// each half exactly like the scalar one.
+__device__ __forceinline__ void mac_load_transposed(float *wt, const float *w, int tid, int nt) {
+  for (int i = tid; i < kMacNP; i += nt) {
+    float v;
+    if (i >= kMacOffW1 && i < kMacOffB1) {  // W1T[k][j] = W1[j][k]
+      const int k = (i - kMacOffW1) / kMacNH, j = (i - kMacOffW1) % kMacNH;
+      v = w[kMacOffW1 + j * kMacNF + k];
+    } else if (i >= kMacOffW2 && i < kMacOffB2) {  // W2T[k][j] = W2[j][k]
+      const int k = (i - kMacOffW2) / kMacNH, j = (i - kMacOffW2) % kMacNH;
+      v = w[kMacOffW2 + j * kMacNH + k];
+    } else {
+      v = w[i];
+    }
+    wt[i] = v;
+  }
+}
+
+__device__ __forceinline__ unsigned long long mac_pk(float lo, float hi) {
+  return ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
+}
+__device__ __forceinline__ float mac_lo(unsigned long long v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float mac_hi(unsigned long long v) {
+  return __uint_as_float((uint32_t)(v >> 32));
+}
+__device__ __forceinline__ unsigned long long mac_fma2(unsigned long long a, unsigned long long b,
+                                                       unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// wt: shared memory in the mac_load_transposed layout, 16-byte aligned.
+__device__ __forceinline__ float mac_mlp_t(const float *wt, const float *f) {
+  float x[kMacNF];
+#pragma unroll
+  for (int k = 0; k < kMacNF; k++) x[k] = __fmul_rn(__fsub_rn(f[k], wt[k]), wt[kMacNF + k]);
+  unsigned long long acc[kMacNH / 2];
+  const float4 *b1 = reinterpret_cast<const float4 *>(wt + kMacOffB1);
+#pragma unroll
+  for (int q = 0; q < kMacNH / 4; q++) {
+    const float4 b = b1[q];
+    acc[2 * q] = mac_pk(b.x, b.y);
+    acc[2 * q + 1] = mac_pk(b.z, b.w);
+  }
+#pragma unroll
+  for (int k = 0; k < kMacNF; k++) {
+    const unsigned long long xk = mac_pk(x[k], x[k]);
+    const float4 *row = reinterpret_cast<const float4 *>(wt + kMacOffW1 + k * kMacNH);
+#pragma unroll
+    for (int q = 0; q < kMacNH / 4; q++) {
+      const float4 r = row[q];
+      acc[2 * q] = mac_fma2(mac_pk(r.x, r.y), xk, acc[2 * q]);
+      acc[2 * q + 1] = mac_fma2(mac_pk(r.z, r.w), xk, acc[2 * q + 1]);
+    }
+  }
+  float h1[kMacNH];
+#pragma unroll
+  for (int q = 0; q < kMacNH / 2; q++) {
+    const float a = mac_lo(acc[q]), b = mac_hi(acc[q]);
+    h1[2 * q] = a > 0.0f ? a : 0.0f;
+    h1[2 * q + 1] = b > 0.0f ? b : 0.0f;
+  }
+  const float4 *b2 = reinterpret_cast<const float4 *>(wt + kMacOffB2);
+#pragma unroll
+  for (int q = 0; q < kMacNH / 4; q++) {
+    const float4 b = b2[q];
+    acc[2 * q] = mac_pk(b.x, b.y);
+    acc[2 * q + 1] = mac_pk(b.z, b.w);
+  }
+#pragma unroll
+  for (int k = 0; k < kMacNH; k++) {
+    const unsigned long long hk = mac_pk(h1[k], h1[k]);
+    const float4 *row = reinterpret_cast<const float4 *>(wt + kMacOffW2 + k * kMacNH);
+#pragma unroll
+    for (int q = 0; q < kMacNH / 4; q++) {
+      const float4 r = row[q];
+      acc[2 * q] = mac_fma2(mac_pk(r.x, r.y), hk, acc[2 * q]);
+      acc[2 * q + 1] = mac_fma2(mac_pk(r.z, r.w), hk, acc[2 * q + 1]);
+    }
+  }
+  float y = wt[kMacOffB3];
+#pragma unroll
+  for (int q = 0; q < kMacNH / 2; q++) {
+    const float a = mac_lo(acc[q]), b = mac_hi(acc[q]);
+    y = __fmaf_rn(wt[kMacOffW3 + 2 * q], a > 0.0f ? a : 0.0f, y);
+    y = __fmaf_rn(wt[kMacOffW3 + 2 * q + 1], b > 0.0f ? b : 0.0f, y);
+  }
+  return y;
+}
+
 }  // namespace afd

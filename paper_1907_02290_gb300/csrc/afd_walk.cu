@@ -11,8 +11,13 @@
 // children keeps the depth-first order, whichever entries are expanded
 // first. The children of an expanded cell come from one 256-byte block of
 // walk records (written by the moments kernel), eight lanes per cell, so an
-// expansion costs one coalesced load. Two passes: counts, then (after a
-// scan) the fill.
+// expansion costs one coalesced load. One pass: each group appends its
+// accepted cell ids and its opened leaves (first particle, count) to two
+// record streams in an arena of 64-record chunks (taken from a global
+// cursor, linked per group); after a scan of the per-group counts a
+// compaction kernel writes the CSR lists -- leaf records expanded into
+// particle indices -- in the same depth-first order. An arena that proves
+// too small is grown to the size the cursors report and the pass repeated.
 //
 // The opening criterion is evaluated in FP32 without contraction: with d the
 // distance from the cell's centre of mass to the group's bounding box (0
@@ -25,6 +30,8 @@
 #include "afd_internal.cuh"
 #include "afd_mac.cuh"
 
+#include <algorithm>
+
 namespace afd {
 namespace {
 
@@ -33,6 +40,7 @@ constexpr int kWalkThreads = 32 * kWalkWarps;
 constexpr int kStack = 512;  // entries per warp; >= 8 * 23 + 4 * 32 needed
 constexpr int kExpand = 4;   // cells expanded per step at most
 constexpr uint32_t kOpen = 0u, kAccept = 1u, kLeaf = 2u;
+constexpr uint32_t kChunk = 64;  // records per arena chunk
 
 struct WalkArgs {
   int64_t n_groups;
@@ -42,9 +50,11 @@ struct WalkArgs {
   const uint2 *node_i;
   const uint4 *block;
   float theta2;
-  uint32_t *cnt_e, *cnt_s, *gself;
-  const uint64_t *off_e, *off_s;
-  uint32_t *epj, *spj;
+  uint32_t *cnt_e, *cnt_s, *gself, *n_lrec;
+  // record arena: cell ids (SPJ stream) and leaf records (EPJ stream)
+  uint32_t *arena_s, *next_s, *next_l, *head_s, *head_l, *cursor;
+  uint2 *arena_l;
+  uint32_t cap_s, cap_l;
   int *status;
   uint32_t iter_cap;
   // learned criterion
@@ -96,7 +106,7 @@ __device__ __forceinline__ uint32_t decide_learned(const WalkArgs &a, const floa
   mac_features(bmin, bmax, cx, cy, cz, s2, sh.w, q0, make_float2(q1.x, q1.y), count, a.eps2,
                amin, f);
   evals++;
-  if (mac_mlp(w, f) < a.tau) {
+  if (mac_mlp_t(w, f) < a.tau) {
     accepts++;
     return kAccept;
   }
@@ -110,16 +120,59 @@ __device__ __forceinline__ uint2 make_entry(uint32_t dec, uint32_t id, uint32_t 
   return dec == kLeaf ? make_uint2(first, (dec << 30) | count) : make_uint2(id, dec << 30);
 }
 
-template <bool FILL, bool LEARNED>
+// Warp-uniform state of one record stream of one group.
+struct RecStream {
+  uint32_t chunk;  // current chunk (kNone before the first)
+  uint32_t fill;   // records in it
+};
+
+// Append the records of the lanes with `on`, in lane order. A chunk index at
+// or above the capacity is not written (the cursor still counts it, which
+// tells the host how large the arena must be).
+template <class T>
+__device__ __forceinline__ void rec_put(RecStream &st, bool on, T rec, T *arena, uint32_t *next,
+                                        uint32_t *cursor, uint32_t cap, uint32_t *head,
+                                        int lane, unsigned lt) {
+  const unsigned m = __ballot_sync(0xffffffffu, on);
+  const uint32_t n = __popc(m);
+  if (n == 0) return;
+  const bool grow = st.fill + n > kChunk;
+  uint32_t nc = kNone;
+  if (grow) {
+    if (lane == 0) {
+      const uint32_t c = atomicAdd(cursor, 1u);
+      nc = c < cap ? c : kNone;
+      if (st.chunk == kNone) *head = nc;
+      else next[st.chunk] = nc;
+    }
+    nc = __shfl_sync(0xffffffffu, nc, 0);
+  }
+  if (on) {
+    const uint32_t p = st.fill + __popc(m & lt);
+    if (p < kChunk) {
+      if (st.chunk != kNone) arena[(size_t)st.chunk * kChunk + p] = rec;
+    } else if (nc != kNone) {
+      arena[(size_t)nc * kChunk + (p - kChunk)] = rec;
+    }
+  }
+  if (grow) {
+    st.chunk = nc;
+    st.fill = st.fill + n - kChunk;
+  } else {
+    st.fill += n;
+  }
+}
+
+template <bool LEARNED>
 __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
   __shared__ uint2 stk_all[kWalkWarps][kStack];
-  __shared__ float wsm[LEARNED ? kMacNP : 1];
+  __shared__ __align__(16) float wsm[LEARNED ? kMacNP + 3 : 1];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
   uint2 *stk = stk_all[wib];
   uint32_t evals = 0, accepts = 0;
   if (LEARNED) {
-    for (int i = threadIdx.x; i < kMacNP; i += kWalkThreads) wsm[i] = a.mac_w[i];
+    mac_load_transposed(wsm, a.mac_w, threadIdx.x, kWalkThreads);
     __syncthreads();
   }
   for (int64_t g = (int64_t)blockIdx.x * kWalkWarps + wib; g < a.n_groups;
@@ -132,8 +185,9 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
     }
     const uint32_t gfirst = a.g_first[g];
     const float amin = LEARNED ? a.g_amin[g] : 0.0f;
-    const uint64_t be = FILL ? a.off_e[g] : 0, bs = FILL ? a.off_s[g] : 0;
     uint64_t ne = 0, ns = 0;
+    uint32_t nl = 0;  // leaf records
+    RecStream rs{kNone, kChunk}, rl{kNone, kChunk};
     uint32_t self_pos = 0;  // 1 + EPJ-list position of the group's first particle
     if (lane == 0) {
       const uint32_t root = a.g_root[g];
@@ -164,7 +218,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
       const bool acc = lane < f && dec == kAccept;
       const bool lf = lane < f && dec == kLeaf;
       const unsigned am = __ballot_sync(0xffffffffu, acc);
-      if (FILL && acc) a.spj[bs + ns + __popc(am & lt)] = e.x;
+      rec_put(rs, acc, e.x, a.arena_s, a.next_s, a.cursor, a.cap_s, a.head_s + g, lane, lt);
       ns += __popc(am);
       const uint32_t lfirst = lf ? e.x : 0u, lcnt = lf ? (e.y & 0x3fffffffu) : 0u;
       uint32_t inc = lcnt;
@@ -178,18 +232,9 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
       // group's particles follow it contiguously)
       if (lf && gfirst >= lfirst && gfirst - lfirst < lcnt)
         self_pos = (uint32_t)(ne + (inc - lcnt) + (gfirst - lfirst)) + 1u;
-      if (FILL) {
-        const uint32_t ex = inc - lcnt;
-        unsigned lm = __ballot_sync(0xffffffffu, lf);
-        while (lm) {
-          const int src = __ffs(lm) - 1;
-          lm &= lm - 1;
-          const uint32_t f0 = __shfl_sync(0xffffffffu, lfirst, src);
-          const uint32_t c0 = __shfl_sync(0xffffffffu, lcnt, src);
-          const uint32_t x0 = __shfl_sync(0xffffffffu, ex, src);
-          for (uint32_t k = lane; k < c0; k += 32) a.epj[be + ne + x0 + k] = f0 + k;
-        }
-      }
+      rec_put(rl, lf, make_uint2(lfirst, lcnt), a.arena_l, a.next_l, a.cursor + 1, a.cap_l,
+              a.head_l + g, lane, lt);
+      nl += __popc(__ballot_sync(0xffffffffu, lf));
       ne += tot;
       if (!om) {  // nothing open among the top entries: all emitted
         sp -= nv;
@@ -272,14 +317,17 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) self_pos = max(self_pos, __shfl_xor_sync(0xffffffffu, self_pos, o));
-    if (!FILL && lane == 0) {
+    if (lane == 0) {
       a.cnt_e[g] = (uint32_t)ne;
       a.cnt_s[g] = (uint32_t)ns;
+      a.n_lrec[g] = nl;
       a.gself[g] = self_pos;
+      if (ns == 0) a.head_s[g] = kNone;
+      if (nl == 0) a.head_l[g] = kNone;
     }
     __syncwarp();
   }
-  if (LEARNED && !FILL) {
+  if (LEARNED) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       evals += __shfl_xor_sync(0xffffffffu, evals, o);
@@ -303,6 +351,59 @@ __global__ void k_interactions(int64_t n_groups, const uint32_t *__restrict__ g_
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
+}
+
+// The CSR lists from the record arena, one warp per group: cell ids copied,
+// leaf records expanded into their particles' Morton positions.
+struct CompactArgs {
+  int64_t n_groups;
+  const uint32_t *cnt_s, *n_lrec, *head_s, *head_l, *next_s, *next_l, *arena_s;
+  const uint2 *arena_l;
+  const uint64_t *off_e, *off_s;
+  uint32_t *epj, *spj;
+};
+
+__global__ void __launch_bounds__(256) k_compact(CompactArgs a) {
+  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (g >= a.n_groups) return;
+  const uint32_t ms = a.cnt_s[g];
+  uint32_t c = a.head_s[g];
+  const uint64_t os = a.off_s[g];
+  for (uint32_t i0 = 0; i0 < ms; i0 += kChunk) {
+    const uint32_t nn = min(kChunk, ms - i0);
+    for (uint32_t k = lane; k < nn; k += 32) a.spj[os + i0 + k] = a.arena_s[(size_t)c * kChunk + k];
+    if (i0 + kChunk < ms) c = a.next_s[c];
+  }
+  const uint32_t r = a.n_lrec[g];
+  c = a.head_l[g];
+  uint64_t pos = a.off_e[g];
+  for (uint32_t i0 = 0; i0 < r; i0 += kChunk) {
+    const uint32_t nrec = min(kChunk, r - i0);
+    for (uint32_t j0 = 0; j0 < nrec; j0 += 32) {
+      const bool on = lane < nrec - j0;
+      const uint2 rec = on ? a.arena_l[(size_t)c * kChunk + j0 + lane] : make_uint2(0u, 0u);
+      uint32_t inc = rec.y;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+      }
+      const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
+      const uint32_t ex = inc - rec.y;
+      unsigned lm = __ballot_sync(0xffffffffu, on && rec.y > 0);
+      while (lm) {
+        const int src = __ffs(lm) - 1;
+        lm &= lm - 1;
+        const uint32_t f0 = __shfl_sync(0xffffffffu, rec.x, src);
+        const uint32_t c0 = __shfl_sync(0xffffffffu, rec.y, src);
+        const uint32_t x0 = __shfl_sync(0xffffffffu, ex, src);
+        for (uint32_t k = lane; k < c0; k += 32) a.epj[pos + x0 + k] = f0 + k;
+      }
+      pos += tot;
+    }
+    if (i0 + kChunk < r) c = a.next_l[c];
+  }
 }
 
 __global__ void k_sys_stats(int64_t n_groups, const uint32_t *__restrict__ g_first,
@@ -336,16 +437,21 @@ int launch_sys_stats(afd_ctx *c, unsigned long long *inter, unsigned long long *
 int launch_walk(afd_ctx *c) {
   const int64_t ng = c->n_groups;
   int st;
-  for (afd::DevBuf *b : {&c->l_cnt_e, &c->l_cnt_s})
+  for (afd::DevBuf *b : {&c->l_cnt_e, &c->l_cnt_s, &c->l_nrec, &c->l_head_s, &c->l_head_l})
     if ((st = reserve(*b, sizeof(uint32_t) * ng))) return st;
   for (afd::DevBuf *b : {&c->epj_off, &c->spj_off})
     if ((st = reserve(*b, sizeof(uint64_t) * (ng + 1)))) return st;
+  if ((st = reserve(c->arena_cur, 2 * sizeof(uint32_t)))) return st;
   if (ng == 0) {
     c->n_epj = c->n_spj = c->interactions = 0;
     cudaMemsetAsync(c->epj_off.p, 0, sizeof(uint64_t), c->stream);
     cudaMemsetAsync(c->spj_off.p, 0, sizeof(uint64_t), c->stream);
     return cudaGetLastError() == cudaSuccess ? AFD_OK : AFD_ERR_CUDA;
   }
+  // arena capacity in chunks: kept from earlier walks, first guess from the
+  // group count (about 1500 cell ids and 130 leaves per group of 256)
+  if (c->arena_cap_s == 0) c->arena_cap_s = (uint32_t)std::min<int64_t>(ng * 24 + 4096, 1u << 30);
+  if (c->arena_cap_l == 0) c->arena_cap_l = (uint32_t)std::min<int64_t>(ng * 4 + 4096, 1u << 30);
   WalkArgs a;
   a.n_groups = ng;
   a.boxf = ptr<float>(c->g_boxf);
@@ -358,11 +464,11 @@ int launch_walk(afd_ctx *c) {
   a.theta2 = th * th;
   a.cnt_e = ptr<uint32_t>(c->l_cnt_e);
   a.cnt_s = ptr<uint32_t>(c->l_cnt_s);
+  a.n_lrec = ptr<uint32_t>(c->l_nrec);
+  a.head_s = ptr<uint32_t>(c->l_head_s);
+  a.head_l = ptr<uint32_t>(c->l_head_l);
   a.gself = ptr<uint32_t>(c->g_self);
-  a.off_e = ptr<uint64_t>(c->epj_off);
-  a.off_s = ptr<uint64_t>(c->spj_off);
-  a.epj = nullptr;
-  a.spj = nullptr;
+  a.cursor = ptr<uint32_t>(c->arena_cur);
   a.status = ptr<int>(c->status);
   a.iter_cap = (uint32_t)(2 * c->n_cells + 64);
   const bool learned = mac_usable(c);
@@ -374,8 +480,6 @@ int launch_walk(afd_ctx *c) {
   if (learned) {
     if ((st = launch_group_amin(c))) return st;
     if ((st = reserve(c->mac_cnt, 2 * sizeof(unsigned long long)))) return st;
-    if (cudaMemsetAsync(c->mac_cnt.p, 0, 2 * sizeof(unsigned long long), c->stream) != cudaSuccess)
-      return AFD_ERR_CUDA;
     a.mac_w = ptr<float>(c->mac_w);
     a.g_amin = ptr<float>(c->g_amin);
     a.s_hi = ptr<float4>(c->s_hi);
@@ -391,36 +495,73 @@ int launch_walk(afd_ctx *c) {
   c->walk_learned = learned;
   int64_t nb = (ng + kWalkWarps - 1) / kWalkWarps;
   if (nb > 152 * 32) nb = 152 * 32;
-  if (learned) k_walk<false, true><<<(unsigned)nb, kWalkThreads, 0, c->stream>>>(a);
-  else k_walk<false, false><<<(unsigned)nb, kWalkThreads, 0, c->stream>>>(a);
-  c->launches++;
-  if (cudaGetLastError() != cudaSuccess) return AFD_ERR_CUDA;
-  if ((st = scan_u32_to_u64(c, a.cnt_e, ptr<uint64_t>(c->epj_off), ng))) return st;
-  if ((st = scan_u32_to_u64(c, a.cnt_s, ptr<uint64_t>(c->spj_off), ng))) return st;
   unsigned long long *inter = ptr<unsigned long long>(c->u64acc) + 1;
-  cudaMemsetAsync(inter, 0, sizeof(unsigned long long), c->stream);
-  k_interactions<<<152, 256, 0, c->stream>>>(ng, ptr<uint32_t>(c->g_count), a.cnt_e, a.cnt_s,
-                                              inter);
-  c->launches++;
   uint64_t *pin = static_cast<uint64_t *>(c->pinned);
-  cudaMemcpyAsync(pin, ptr<uint64_t>(c->epj_off) + ng, sizeof(uint64_t), cudaMemcpyDeviceToHost,
-                  c->stream);
-  cudaMemcpyAsync(pin + 1, ptr<uint64_t>(c->spj_off) + ng, sizeof(uint64_t),
-                  cudaMemcpyDeviceToHost, c->stream);
-  cudaMemcpyAsync(pin + 2, inter, sizeof(uint64_t), cudaMemcpyDeviceToHost, c->stream);
-  cudaMemcpyAsync(pin + 3, c->status.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
-  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return AFD_ERR_CUDA;
-  const int bits = (int)(pin[3] & 0xffffffffu);
-  if (bits) return status_to_error(bits);
+  for (int attempt = 0;; attempt++) {
+    if ((st = reserve(c->arena_s, sizeof(uint32_t) * kChunk * (size_t)c->arena_cap_s))) return st;
+    if ((st = reserve(c->arena_l, sizeof(uint2) * kChunk * (size_t)c->arena_cap_l))) return st;
+    if ((st = reserve(c->next_s, sizeof(uint32_t) * (size_t)c->arena_cap_s))) return st;
+    if ((st = reserve(c->next_l, sizeof(uint32_t) * (size_t)c->arena_cap_l))) return st;
+    a.arena_s = ptr<uint32_t>(c->arena_s);
+    a.arena_l = ptr<uint2>(c->arena_l);
+    a.next_s = ptr<uint32_t>(c->next_s);
+    a.next_l = ptr<uint32_t>(c->next_l);
+    a.cap_s = c->arena_cap_s;
+    a.cap_l = c->arena_cap_l;
+    if (cudaMemsetAsync(c->arena_cur.p, 0, 2 * sizeof(uint32_t), c->stream) != cudaSuccess)
+      return AFD_ERR_CUDA;
+    if (learned && cudaMemsetAsync(c->mac_cnt.p, 0, 2 * sizeof(unsigned long long),
+                                   c->stream) != cudaSuccess)
+      return AFD_ERR_CUDA;
+    if (learned) k_walk<true><<<(unsigned)nb, kWalkThreads, 0, c->stream>>>(a);
+    else k_walk<false><<<(unsigned)nb, kWalkThreads, 0, c->stream>>>(a);
+    c->launches++;
+    if (cudaGetLastError() != cudaSuccess) return AFD_ERR_CUDA;
+    if ((st = scan_u32_to_u64(c, a.cnt_e, ptr<uint64_t>(c->epj_off), ng))) return st;
+    if ((st = scan_u32_to_u64(c, a.cnt_s, ptr<uint64_t>(c->spj_off), ng))) return st;
+    cudaMemsetAsync(inter, 0, sizeof(unsigned long long), c->stream);
+    k_interactions<<<152, 256, 0, c->stream>>>(ng, ptr<uint32_t>(c->g_count), a.cnt_e, a.cnt_s,
+                                                inter);
+    c->launches++;
+    cudaMemcpyAsync(pin, ptr<uint64_t>(c->epj_off) + ng, sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                    c->stream);
+    cudaMemcpyAsync(pin + 1, ptr<uint64_t>(c->spj_off) + ng, sizeof(uint64_t),
+                    cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(pin + 2, inter, sizeof(uint64_t), cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(pin + 3, c->status.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(pin + 4, c->arena_cur.p, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                    c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return AFD_ERR_CUDA;
+    const int bits = (int)(pin[3] & 0xffffffffu);
+    if (bits) return status_to_error(bits);
+    const uint32_t need_s = (uint32_t)(pin[4] & 0xffffffffu), need_l = (uint32_t)(pin[4] >> 32);
+    if (need_s <= c->arena_cap_s && need_l <= c->arena_cap_l) break;
+    if (attempt > 0) return AFD_ERR_LIST_OVERFLOW;  // cannot happen: sized from the cursors
+    if (need_s > c->arena_cap_s)
+      c->arena_cap_s = (uint32_t)std::min<uint64_t>((uint64_t)need_s * 5 / 4 + 1024, 1u << 30);
+    if (need_l > c->arena_cap_l)
+      c->arena_cap_l = (uint32_t)std::min<uint64_t>((uint64_t)need_l * 5 / 4 + 1024, 1u << 30);
+  }
   c->n_epj = pin[0];
   c->n_spj = pin[1];
   c->interactions = pin[2];
   if ((st = reserve(c->epj, sizeof(uint32_t) * c->n_epj))) return st;
   if ((st = reserve(c->spj, sizeof(uint32_t) * c->n_spj))) return st;
-  a.epj = ptr<uint32_t>(c->epj);
-  a.spj = ptr<uint32_t>(c->spj);
-  if (learned) k_walk<true, true><<<(unsigned)nb, kWalkThreads, 0, c->stream>>>(a);
-  else k_walk<true, false><<<(unsigned)nb, kWalkThreads, 0, c->stream>>>(a);
+  CompactArgs k;
+  k.n_groups = ng;
+  k.cnt_s = a.cnt_s;
+  k.n_lrec = a.n_lrec;
+  k.head_s = a.head_s;
+  k.head_l = a.head_l;
+  k.next_s = a.next_s;
+  k.next_l = a.next_l;
+  k.arena_s = a.arena_s;
+  k.arena_l = a.arena_l;
+  k.off_e = ptr<uint64_t>(c->epj_off);
+  k.off_s = ptr<uint64_t>(c->spj_off);
+  k.epj = ptr<uint32_t>(c->epj);
+  k.spj = ptr<uint32_t>(c->spj);
+  k_compact<<<(unsigned)((ng * 32 + 255) / 256), 256, 0, c->stream>>>(k);
   c->launches++;
   return cudaGetLastError() == cudaSuccess ? AFD_OK : AFD_ERR_CUDA;
 }
