@@ -49,7 +49,7 @@ L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one force-kernel launch on
 # this workload, from the capture summarised in profiles/ (None until taken
 # on the current kernel).
-FORCE_TRAFFIC_BYTES = None
+FORCE_TRAFFIC_BYTES = 310_964_736  # 291.38 MB read + 19.59 MB written (k_force, --set full)
 
 
 def parse():
@@ -66,7 +66,7 @@ def parse():
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-criterion form and the equal-error comparison")
     ap.add_argument("--mac-samples", type=int, default=1_000_000)
-    ap.add_argument("--mac-band", default="0.25,1.0",
+    ap.add_argument("--mac-band", default="0.3,1.0",
                     help="theta_lo,theta_hi of the learned criterion's band")
     return ap.parse_args()
 

@@ -401,6 +401,14 @@ int afd_mlp_train(const float *feat, const float *label, int64_t n, int epochs, 
 int afd_direct_sum(const double *x, const double *y, const double *z, const double *m, int64_t n,
                    const uint32_t *targets, int64_t n_t, double eps, double *out, void *stream);
 
+/* Measured rates of the instruction streams the kernels use, each from
+ * independent chains timed with CUDA events on `stream` (best of three
+ * launches; synchronises; allocates 4 bytes): out (host, 4 doubles) = [0]
+ * packed fma.rn.f32x2 TFLOP/s, [1] scalar FP32 FMA TFLOP/s, [2] MUFU
+ * rsqrt.approx.f32 lane-operations per second / 1e12, [3] packed
+ * fma.rn.f16x2 TFLOP/s (2 flops per lane-FMA). */
+int afd_pipe_rates(int device, void *stream, double *out);
+
 /* Human-readable text for a status code (static storage). */
 const char *afd_error_string(int status);
 

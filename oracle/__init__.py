@@ -99,6 +99,7 @@ def lib():
         L.afo_band_pairs.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_int64, _I64]
         L.afo_band_pairs.restype = ctypes.c_int64
+        L.afo_relist.argtypes = [ctypes.c_void_p]
     return _lib
 
 
@@ -265,6 +266,11 @@ class Tree:
         x, y, z, m = map(_f64, (x, y, z, m))
         if lib().afo_update(self._h, _p(x, _D), _p(y, _D), _p(z, _D), _p(m, _D)) != 0:
             raise ValueError("non-finite particle data")
+
+    def relist(self):
+        """Lists made again on the current topology and moments (a list
+        construction after reusing steps, without a new tree)."""
+        lib().afo_relist(self._h)
 
     def force(self):
         """FP64 force on the saved lists, caller order: (ax, ay, az, pot)."""

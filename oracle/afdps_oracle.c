@@ -76,8 +76,10 @@
  *     with fused multiply-adds); 0 or subnormal arguments give -127.
  *  R13 network: 8-32-32-1 perceptron with ReLU on both hidden layers; input
  *     k is normalised as (f_k - mu_k) * isd_k; every parameter (mu and isd
- *     included) is an FP16 value; each unit is its bias followed by fused
- *     multiply-adds over its inputs in index order, in FP32.
+ *     included) is an FP16 value; each hidden unit is its bias followed by
+ *     fused multiply-adds over its inputs in index order, in FP32; the
+ *     output unit forms the 32 products w3_j h2_j, sums them pairwise by
+ *     halving (p_j += p_{j+16} for j < 16, then 8, 4, 2, 1) and adds b3.
  *  R14 learned decision for cell c and group g: open if c contains the
  *     group's first particle; accept if s^2 < theta_lo^2 d^2; open if not
  *     s^2 < theta_hi^2 d^2; otherwise accept iff the network's output is
@@ -667,9 +669,11 @@ float afo_mlp_forward(const float *p, const float f[AFO_MAC_NF]) {
     for (int k = 0; k < AFO_MAC_NH; k++) acc = fmaf(W2[j * AFO_MAC_NH + k], h1[k], acc);
     h2[j] = acc > 0.0f ? acc : 0.0f;
   }
-  float y = b3[0];
-  for (int k = 0; k < AFO_MAC_NH; k++) y = fmaf(w3[k], h2[k], y);
-  return y;
+  float prod[AFO_MAC_NH];
+  for (int k = 0; k < AFO_MAC_NH; k++) prod[k] = w3[k] * h2[k];
+  for (int half = AFO_MAC_NH / 2; half > 0; half /= 2)
+    for (int k = 0; k < half; k++) prod[k] = prod[k] + prod[k + half];
+  return prod[0] + b3[0];
 }
 
 void afo_mlp_forward_batch(const float *p, int64_t n, const float *feat, float *out) {
@@ -1000,6 +1004,13 @@ int afo_update(afo_tree *t, const double *x, const double *y, const double *z,
   moments(t);
   group_boxes(t);
   return 0;
+}
+
+/* Lists made again on the current topology, moments and group boxes (a
+ * MAKE_LIST after reusing steps, without a new tree). */
+void afo_relist(afo_tree *t) {
+  free(t->epj_off); free(t->spj_off); free(t->epj); free(t->spj);
+  make_lists(t);
 }
 
 /* Force on the saved lists (Section 5: interaction of the EPJs and SPJs of a

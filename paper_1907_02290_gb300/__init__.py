@@ -90,6 +90,7 @@ def lib():
         "afd_error_string": ([ctypes.c_int], ctypes.c_char_p),
         "afd_root_cell_static": ([_VP, _VP, _VP, _VP, _I64, _VP, _VP, _VP], ctypes.c_int),
         "afd_fp32_peak": ([ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "afd_pipe_rates": ([ctypes.c_int, _VP, _VP], ctypes.c_int),
         "afd_system_stats": ([_VP, _VP, _VP], ctypes.c_int),
         "afd_graph_capture_step": ([_VP] + [_VP] * 8 + [_D], ctypes.c_int),
         "afd_graph_launch": ([_VP], ctypes.c_int),
@@ -333,6 +334,15 @@ def afd_fp32_peak(device: int = 0, stream=None) -> float:
     v = ctypes.c_double(0.0)
     _check(lib().afd_fp32_peak(int(device), _stream_ptr(stream), ctypes.byref(v)), "afd_fp32_peak")
     return float(v.value)
+
+
+def afd_pipe_rates(device: int = 0, stream=None) -> dict:
+    """Measured packed/scalar FP32 FMA, MUFU rsqrt and packed FP16 FMA rates."""
+    out = np.zeros(4)
+    _check(lib().afd_pipe_rates(int(device), _stream_ptr(stream), _VP(out.ctypes.data)),
+           "afd_pipe_rates")
+    return {"f32x2_fma_tflops": float(out[0]), "f32_fma_tflops": float(out[1]),
+            "rsqrt_tops": float(out[2]), "f16x2_fma_tflops": float(out[3])}
 
 
 # ---------------------------------------------------------------- learned criterion

@@ -138,7 +138,7 @@ int tree_build(afd_ctx *c, const double *x, const double *y, const double *z, co
   TRY(launch_reorder(c, x, y, z, m, n));
   TRY(launch_link(c, n));
   TRY(read_status(c));
-  TRY(launch_moments(c, true));
+  TRY(launch_moments(c, true, c->cfg.mac != 0));
   TRY(launch_groups(c));
   TRY(launch_group_boxes(c));
   c->n = n;
@@ -160,7 +160,7 @@ int reuse(afd_ctx *c, const double *x, const double *y, const double *z, const d
   if (!c->saved || !c->have_lists) return AFD_ERR_NO_SAVED_LIST;
   if (c->n > 0 && (!x || !y || !z || !m)) return AFD_ERR_ARG;
   TRY(launch_reorder(c, x, y, z, m, c->n));
-  TRY(launch_moments(c, false));
+  TRY(launch_moments(c, false, false));  // lists are kept: no criterion runs
   return AFD_OK;
 }
 

@@ -124,6 +124,8 @@ struct afd_ctx {
   float mac_lo2 = 0.0f, mac_hi2 = 0.0f, mac_tau = 0.0f;
   afd::DevBuf amag, amag_s, g_amin;
   int64_t amag_n = -1;
+  bool q_current = false;       // the cell quadrupoles match the current positions
+  bool blocks_current = false;  // the walk's child records match them too
   bool walk_learned = false;  // the last walk used the learned criterion
   afd::DevBuf mac_cnt;        // u64[2]: network evaluations, accepted (count pass)
   afd::DevBuf band_cnt, band_off;
@@ -149,7 +151,9 @@ int launch_sort(afd_ctx *c, int64_t n);  // sorts keys/perm in place (result in 
 int launch_reorder(afd_ctx *c, const double *x, const double *y, const double *z,
                    const double *m, int64_t n);
 int launch_link(afd_ctx *c, int64_t n);        // sets c->n_cells, c->max_level (syncs)
-int launch_moments(afd_ctx *c, bool child_blocks);  // bottom-up moments + superparticle data
+// bottom-up moments + superparticle data; quadrupoles when the far field
+// uses them or need_q
+int launch_moments(afd_ctx *c, bool child_blocks, bool need_q);
 int launch_groups(afd_ctx *c);                 // sets c->n_groups, c->n_units (syncs)
 int launch_group_boxes(afd_ctx *c);
 

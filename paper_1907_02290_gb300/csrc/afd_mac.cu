@@ -678,7 +678,7 @@ int upload_rounded(const float *params, float *w, cudaStream_t s) {
 }  // namespace
 
 bool mac_usable(const afd_ctx *c) {
-  return c->cfg.mac && c->mac_ready && c->n > 0 && c->amag_n == c->n;
+  return c->cfg.mac && c->mac_ready && c->n > 0 && c->amag_n == c->n && c->q_current;
 }
 
 int launch_group_amin(afd_ctx *c) {
@@ -786,6 +786,7 @@ int afd_mac_samples(afd_ctx *c, double theta_lo, double theta_hi, double keep, u
   *n_out = 0;
   const int64_t ng = c->n_groups;
   if (ng == 0) return AFD_OK;
+  if (!c->q_current) MAC_TRY(launch_moments(c, false, true));  // after reusing steps
   MAC_TRY(launch_group_amin(c));
   MAC_TRY(reserve(c->band_cnt, sizeof(uint32_t) * (size_t)ng));
   MAC_TRY(reserve(c->band_off, sizeof(uint64_t) * (size_t)(ng + 1)));

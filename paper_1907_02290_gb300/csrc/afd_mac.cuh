@@ -15,8 +15,10 @@
 //  1 + t, p a least-squares quartic, Horner with fused multiply-adds.
 //
 //  network: 8-32-32-1, ReLU, inputs normalised as (f - mu) * isd, every
-//  parameter an FP16 value held as FP32, each unit its bias followed by
-//  fused multiply-adds in input order.
+//  parameter an FP16 value held as FP32, each hidden unit its bias followed
+//  by fused multiply-adds in input order; the output sums the 32 products
+//  w3_j h2_j pairwise by halving (j += j + 16, then 8, 4, 2, 1 -- the order
+//  of a warp's xor butterfly) and adds b3.
 //
 //  decision: open a cell holding the group's first particle; accept when
 //  s^2 < theta_lo^2 d^2; open unless s^2 < theta_hi^2 d^2; otherwise accept
@@ -111,37 +113,12 @@ __device__ __forceinline__ void mac_features(const float *bmin, const float *bma
   for (int k = 0; k < kMacNF; k++) f[k] = mac_clamp(f[k]);
 }
 
-// Network output for one feature vector; w: kMacNP FP16-valued floats
-// (shared memory in the walk: every lane reads the same address).
-__device__ __forceinline__ float mac_mlp(const float *w, const float *f) {
-  float x[kMacNF], h1[kMacNH];
-#pragma unroll
-  for (int k = 0; k < kMacNF; k++) x[k] = __fmul_rn(__fsub_rn(f[k], w[k]), w[kMacNF + k]);
-#pragma unroll
-  for (int j = 0; j < kMacNH; j++) {
-    float acc = w[kMacOffB1 + j];
-#pragma unroll
-    for (int k = 0; k < kMacNF; k++) acc = __fmaf_rn(w[kMacOffW1 + j * kMacNF + k], x[k], acc);
-    h1[j] = acc > 0.0f ? acc : 0.0f;
-  }
-  float y = w[kMacOffB3];
-#pragma unroll 2
-  for (int j = 0; j < kMacNH; j++) {
-    float acc = w[kMacOffB2 + j];
-#pragma unroll
-    for (int k = 0; k < kMacNH; k++) acc = __fmaf_rn(w[kMacOffW2 + j * kMacNH + k], h1[k], acc);
-    y = __fmaf_rn(w[kMacOffW3 + j], acc > 0.0f ? acc : 0.0f, y);
-  }
-  return y;
-}
-
-// ---- the same network on transposed weights, two units per instruction ----
+// ---- one lane evaluates the network, two units per instruction ----
 // Shared-memory layout for mac_mlp_t (offsets as in the flat vector, the two
 // weight matrices transposed to [input][unit]): mu, isd, W1T[8][32], b1,
-// W2T[32][32], b2, w3, b3. Each unit still accumulates its bias and then its
-// inputs in index order with one rounding per fused multiply-add, so the
-// result equals mac_mlp's bit for bit; the packed FMA (fma.rn.f32x2) rounds
-// each half exactly like the scalar one.
+// W2T[32][32], b2, w3, b3. Each unit accumulates its bias and then its
+// inputs in index order with one rounding per fused multiply-add; the packed
+// FMA (fma.rn.f32x2) rounds each half exactly like the scalar one.
 __device__ __forceinline__ void mac_load_transposed(float *wt, const float *w, int tid, int nt) {
   for (int i = tid; i < kMacNP; i += nt) {
     float v;
@@ -221,14 +198,18 @@ __device__ __forceinline__ float mac_mlp_t(const float *wt, const float *f) {
       acc[2 * q + 1] = mac_fma2(mac_pk(r.z, r.w), hk, acc[2 * q + 1]);
     }
   }
-  float y = wt[kMacOffB3];
+  float p[kMacNH];
 #pragma unroll
   for (int q = 0; q < kMacNH / 2; q++) {
     const float a = mac_lo(acc[q]), b = mac_hi(acc[q]);
-    y = __fmaf_rn(wt[kMacOffW3 + 2 * q], a > 0.0f ? a : 0.0f, y);
-    y = __fmaf_rn(wt[kMacOffW3 + 2 * q + 1], b > 0.0f ? b : 0.0f, y);
+    p[2 * q] = __fmul_rn(wt[kMacOffW3 + 2 * q], a > 0.0f ? a : 0.0f);
+    p[2 * q + 1] = __fmul_rn(wt[kMacOffW3 + 2 * q + 1], b > 0.0f ? b : 0.0f);
   }
-  return y;
+#pragma unroll
+  for (int half = kMacNH / 2; half > 0; half /= 2)
+#pragma unroll
+    for (int k = 0; k < half; k++) p[k] = __fadd_rn(p[k], p[k + half]);
+  return __fadd_rn(p[0], wt[kMacOffB3]);
 }
 
 }  // namespace afd

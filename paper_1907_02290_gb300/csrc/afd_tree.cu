@@ -1019,7 +1019,7 @@ int launch_link(afd_ctx *c, int64_t n) {
   return ck();
 }
 
-int launch_moments(afd_ctx *c, bool child_blocks) {
+int launch_moments(afd_ctx *c, bool child_blocks, bool need_q) {
   const int64_t nc = c->n_cells;
   if (child_blocks) AFD_TRY(reserve(c->c_block, sizeof(uint4) * 16 * (size_t)nc));
   AFD_TRY(reserve(c->c_mass, sizeof(double) * nc));
@@ -1032,9 +1032,12 @@ int launch_moments(afd_ctx *c, bool child_blocks) {
   if (nc == 0) return AFD_OK;
   if (cudaMemsetAsync(c->c_arrive.p, 0, sizeof(unsigned) * nc, c->stream) != cudaSuccess)
     return AFD_ERR_CUDA;
-  // quadrupoles for the far field, and for the learned opening criterion
-  const bool quad_on = c->cfg.multipole || c->cfg.mac;
-  if (!quad_on) {
+  // quadrupoles for the far field, and (construction steps) for the learned
+  // opening criterion; without either they are zero in the exports
+  const bool quad_on = c->cfg.multipole || need_q;
+  c->q_current = quad_on;
+  c->blocks_current = child_blocks;
+  if (!quad_on && !c->cfg.mac) {
     if (cudaMemsetAsync(c->c_quad.p, 0, sizeof(double) * 6 * nc, c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->s_q0.p, 0, sizeof(float4) * nc, c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->s_q1.p, 0, sizeof(float4) * nc, c->stream) != cudaSuccess)

@@ -85,12 +85,14 @@ __device__ __forceinline__ uint32_t decide(const float *bmin, const float *bmax,
   return leaf ? kLeaf : kOpen;
 }
 
-__device__ __forceinline__ uint32_t decide_learned(const WalkArgs &a, const float *w,
-                                                   const float *bmin, const float *bmax, float cx,
-                                                   float cy, float cz, float s2, bool leaf,
-                                                   uint32_t id, uint32_t first, uint32_t count,
-                                                   uint32_t gfirst, float amin, uint32_t &evals,
-                                                   uint32_t &accepts) {
+// Learned decision without the network: kAccept, kOpen / kLeaf, or kBand
+// when the network decides (then f receives the features).
+constexpr uint32_t kBand = 3u;
+__device__ __forceinline__ uint32_t learned_pre(const WalkArgs &a, const float *bmin,
+                                                const float *bmax, float cx, float cy, float cz,
+                                                float s2, bool leaf, uint32_t id, uint32_t first,
+                                                uint32_t count, uint32_t gfirst, float amin,
+                                                float *f) {
   const uint32_t closed = leaf ? kLeaf : kOpen;
   if (gfirst >= first && gfirst - first < count) return closed;  // holds the group
   const float dx = sep_axis(cx, bmin[0], bmax[0]);
@@ -102,15 +104,9 @@ __device__ __forceinline__ uint32_t decide_learned(const WalkArgs &a, const floa
   if (s2 < __fmul_rn(a.lo2, d2)) return kAccept;
   if (!(s2 < __fmul_rn(a.hi2, d2))) return closed;
   const float4 sh = a.s_hi[id], q0 = a.s_q0[id], q1 = a.s_q1[id];
-  float f[kMacNF];
   mac_features(bmin, bmax, cx, cy, cz, s2, sh.w, q0, make_float2(q1.x, q1.y), count, a.eps2,
                amin, f);
-  evals++;
-  if (mac_mlp_t(w, f) < a.tau) {
-    accepts++;
-    return kAccept;
-  }
-  return closed;
+  return kBand;
 }
 
 // Stack entry: x = cell id (open / accepted) or first particle (leaf);
@@ -195,10 +191,9 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
       const uint2 ni = a.node_i[root];
       const bool leaf = (ni.y >> 31) != 0;
       const uint32_t cnt = ni.y & 0x7fffffffu;
-      const uint32_t d =
-          LEARNED ? decide_learned(a, wsm, bmin, bmax, nf.x, nf.y, nf.z, nf.w, leaf, root, ni.x,
-                                   cnt, gfirst, amin, evals, accepts)
-                  : decide(bmin, bmax, nf.x, nf.y, nf.z, nf.w, leaf, a.theta2);
+      // a system's root holds all its groups: the learned rule opens it
+      const uint32_t d = LEARNED ? (leaf ? kLeaf : kOpen)
+                                 : decide(bmin, bmax, nf.x, nf.y, nf.z, nf.w, leaf, a.theta2);
       stk[0] = make_entry(d, root, ni.x, cnt);
     }
     int sp = 1;
@@ -263,24 +258,35 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
       for (int q = 0; q < kExpand; q++)
         if (q == q_me) p_me = pos_q[q];
       const uint32_t cid_me = __shfl_sync(0xffffffffu, e.x, p_me < 0 ? 0 : p_me);
-      bool valid = false;
+      bool valid = false, leaf_me = false;
       uint2 child_entry = make_uint2(0u, 0u);
+      uint32_t d = 0, c_id = 0, c_first = 0, c_cnt = 0;
+      float feat[kMacNF];
+#pragma unroll
+      for (int k = 0; k < kMacNF; k++) feat[k] = 0.0f;
       if (q_me < E) {
         const uint4 *blk = a.block + ((size_t)cid_me * 8 + c_me) * 2;
         const uint4 nf = blk[0], meta = blk[1];
         valid = meta.z != kNone;
         if (valid) {
-          const bool leaf = (meta.y >> 31) != 0;
-          const uint32_t cnt = meta.y & 0x7fffffffu;
+          leaf_me = (meta.y >> 31) != 0;
+          c_id = meta.z;
+          c_first = meta.x;
+          c_cnt = meta.y & 0x7fffffffu;
           const float cx = __uint_as_float(nf.x), cy = __uint_as_float(nf.y),
                       cz = __uint_as_float(nf.z), s2 = __uint_as_float(nf.w);
-          const uint32_t d =
-              LEARNED ? decide_learned(a, wsm, bmin, bmax, cx, cy, cz, s2, leaf, meta.z, meta.x,
-                                       cnt, gfirst, amin, evals, accepts)
-                      : decide(bmin, bmax, cx, cy, cz, s2, leaf, a.theta2);
-          child_entry = make_entry(d, meta.z, meta.x, cnt);
+          d = LEARNED ? learned_pre(a, bmin, bmax, cx, cy, cz, s2, leaf_me, c_id, c_first, c_cnt,
+                                    gfirst, amin, feat)
+                      : decide(bmin, bmax, cx, cy, cz, s2, leaf_me, a.theta2);
         }
       }
+      if (LEARNED && valid && d == kBand) {  // each band cell's lane runs the network
+        const bool acc_me = mac_mlp_t(wsm, feat) < a.tau;
+        evals++;
+        accepts += acc_me ? 1u : 0u;
+        d = acc_me ? kAccept : (leaf_me ? kLeaf : kOpen);
+      }
+      if (valid) child_entry = make_entry(d, c_id, c_first, c_cnt);
       const unsigned vm = __ballot_sync(0xffffffffu, valid);
       // output count of each rewritten position [f, last]: children or itself
       int expanded_q = -1;
@@ -363,9 +369,13 @@ struct CompactArgs {
   uint32_t *epj, *spj;
 };
 
+constexpr int kCompactBuf = 1024;  // staged EPJ entries per warp
+
 __global__ void __launch_bounds__(256) k_compact(CompactArgs a) {
+  __shared__ uint32_t buf_all[8][kCompactBuf];
   const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
+  uint32_t *buf = buf_all[threadIdx.x >> 5];
   if (g >= a.n_groups) return;
   const uint32_t ms = a.cnt_s[g];
   uint32_t c = a.head_s[g];
@@ -391,14 +401,23 @@ __global__ void __launch_bounds__(256) k_compact(CompactArgs a) {
       }
       const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
       const uint32_t ex = inc - rec.y;
-      unsigned lm = __ballot_sync(0xffffffffu, on && rec.y > 0);
-      while (lm) {
-        const int src = __ffs(lm) - 1;
-        lm &= lm - 1;
-        const uint32_t f0 = __shfl_sync(0xffffffffu, rec.x, src);
-        const uint32_t c0 = __shfl_sync(0xffffffffu, rec.y, src);
-        const uint32_t x0 = __shfl_sync(0xffffffffu, ex, src);
-        for (uint32_t k = lane; k < c0; k += 32) a.epj[pos + x0 + k] = f0 + k;
+      if (tot <= (uint32_t)kCompactBuf) {
+        // each lane expands its own leaf into shared memory, then the warp
+        // stores the run with coalesced writes
+        for (uint32_t k = 0; k < rec.y; k++) buf[ex + k] = rec.x + k;
+        __syncwarp();
+        for (uint32_t i = lane; i < tot; i += 32) a.epj[pos + i] = buf[i];
+        __syncwarp();
+      } else {  // very large leaves (level 21): one leaf at a time
+        unsigned lm = __ballot_sync(0xffffffffu, on && rec.y > 0);
+        while (lm) {
+          const int src = __ffs(lm) - 1;
+          lm &= lm - 1;
+          const uint32_t f0 = __shfl_sync(0xffffffffu, rec.x, src);
+          const uint32_t c0 = __shfl_sync(0xffffffffu, rec.y, src);
+          const uint32_t x0 = __shfl_sync(0xffffffffu, ex, src);
+          for (uint32_t k = lane; k < c0; k += 32) a.epj[pos + x0 + k] = f0 + k;
+        }
       }
       pos += tot;
     }
@@ -442,6 +461,12 @@ int launch_walk(afd_ctx *c) {
   for (afd::DevBuf *b : {&c->epj_off, &c->spj_off})
     if ((st = reserve(*b, sizeof(uint64_t) * (ng + 1)))) return st;
   if ((st = reserve(c->arena_cur, 2 * sizeof(uint32_t)))) return st;
+  // after reusing steps the walk records, group boxes (and quadrupoles) lag
+  // the particles: refresh them before walking
+  if (c->n_cells > 0 && (!c->blocks_current || (c->cfg.mac && !c->q_current))) {
+    if ((st = launch_moments(c, true, c->cfg.mac != 0))) return st;
+    if ((st = launch_group_boxes(c))) return st;
+  }
   if (ng == 0) {
     c->n_epj = c->n_spj = c->interactions = 0;
     cudaMemsetAsync(c->epj_off.p, 0, sizeof(uint64_t), c->stream);

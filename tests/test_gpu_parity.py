@@ -217,6 +217,10 @@ def test_reuse_step_parity(env):
     ref = t.force()
     a = acc.cpu().numpy().astype(np.float64)
     assert rms_rel_acc(a, ref) <= FORCE_RMS_TOL
+    # a list construction on the moved particles without a new tree
+    afd.afd_make_interaction_lists(g.ctx, afd.AFD_MAKE_LIST_FOR_REUSE)
+    t.relist()
+    check_structure(g, t)
     g.close()
 
 
