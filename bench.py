@@ -66,7 +66,7 @@ def parse():
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-criterion form and the equal-error comparison")
     ap.add_argument("--mac-samples", type=int, default=1_000_000)
-    ap.add_argument("--mac-band", default="0.3,1.0",
+    ap.add_argument("--mac-band", default="0.4,1.0",
                     help="theta_lo,theta_hi of the learned criterion's band")
     return ap.parse_args()
 
