@@ -159,6 +159,48 @@ def particles(wl):
     return ics.make(wl["model"], wl["n"], wl["seed"])
 
 
+def shard_systems(sizes, world):
+    """Independent systems over ranks: largest first, each to the rank with
+    the fewest particles so far (ties to the lower rank). Returns one sorted
+    list of system indices per rank; every system lands on exactly one."""
+    load = [0] * world
+    out = [[] for _ in range(world)]
+    for s in sorted(range(len(sizes)), key=lambda k: (-int(sizes[k]), k)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        out[r].append(s)
+        load[r] += int(sizes[s])
+    return [sorted(o) for o in out]
+
+
+def rank_batch(wl, rank, world):
+    """This rank's share of a batched workload: its particles and system
+    offsets (the systems are independent, so ranks need no exchange)."""
+    import numpy as np
+
+    import ics
+
+    systems, sizes, _ = ics.batch(wl["n_systems"], wl["seed"])
+    mine = shard_systems(sizes, world)[rank]
+    cat = ics.Particles(*(np.concatenate([getattr(systems[k], a) for k in mine])
+                          for a in ("x", "y", "z", "vx", "vy", "vz", "m")))
+    off = np.concatenate([[0], np.cumsum([int(sizes[k]) for k in mine])]).astype(np.int64)
+    return cat, off, mine
+
+
+def aggregate(dist, device, ms, count):
+    """Whole-job figures over ranks: the slowest rank's time, the sum of the
+    units all ranks processed."""
+    if dist is None:
+        return ms, count
+    import torch
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(count)], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(c.item())
+
+
 def cpu_baseline(wl, max_groups_frac=0.25):
     """The FP64 oracle on the host cores: one construction step, one reusing
     step, and the force of a fraction of the groups; extrapolated to the
@@ -496,7 +538,13 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)  # a capturable (non-default) stream
     torch.cuda.set_stream(stream)
-    p = particles(wl)
+    shard = None
+    if wl["model"] == "batch" and world > 1:  # independent systems: shard them
+        p, wl["sys_off"], shard = rank_batch(wl, rank, world)
+        wl["n_systems"] = len(shard)
+        wl["n"] = p.n
+    else:  # one system: every rank runs a replica
+        p = particles(wl)
     n = p.n
     T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
     x, y, z, vx, vy, vz, m = (T(a) for a in (p.x, p.y, p.z, p.vx, p.vy, p.vz, p.m))
@@ -535,14 +583,7 @@ def main():
     clocks = sampler.stop()
     total_ms = float(sum(step_ms))
     total_i = float(sum(inter))
-    if dist:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ti = torch.tensor([total_i], device=dev, dtype=torch.float64)
-        dist.all_reduce(ti, op=dist.ReduceOp.SUM)
-        total_ms, total_i_all = float(tt.item()), float(ti.item())
-    else:
-        total_i_all = total_i
+    total_ms, total_i_all = aggregate(dist, dev, total_ms, total_i)
     value = total_i_all / (total_ms * 1e-3)
 
     # ---- roofline of the force kernel ----
@@ -586,13 +627,7 @@ def main():
                                         else afd.AFD_REUSE_LIST)
             e_i += g2.stats()["interactions"]
         e_s = time.perf_counter() - t0
-        if dist:
-            tt = torch.tensor([e_s], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e_s = float(tt.item())
-            ti = torch.tensor([e_i], device=dev, dtype=torch.float64)
-            dist.all_reduce(ti, op=dist.ReduceOp.SUM)
-            e_i = float(ti.item())
+        e_s, e_i = aggregate(dist, dev, e_s, e_i)
         e2e = {"value": e_i / e_s, "unit": "interactions/s", "h2d_bytes_per_step": 4 * 8 * n,
                "d2h_bytes_per_step": 16 * n, "ms_per_step": 1e3 * e_s / args.steps,
                "call": "afd_calc_force_all_host (force evaluation per step; integration not "
@@ -607,14 +642,16 @@ def main():
     line = {
         "metric": "force interactions/s", "value": value, "unit": "interactions/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "strong" if shard is not None else "weak",
         "vs_baseline": None, "dtype": "f32",
         "dtype_detail": "force kernel FP32 (hi/lo group-relative coordinates); tree, "
                         "moments and integration FP64",
         "data": "synthetic (seeded Plummer sphere)",
         "config": {"workload": describe(wl), "n": n, "l2": "flushed (256 MB write) between "
                    "timed steps, outside the timed events", "parallelism":
-                   "replicas" if world > 1 else "single GPU"},
+                   ("systems sharded over ranks" if shard is not None else "replicas")
+                   if world > 1 else "single GPU"},
         "ms_per_construction_step": float(np.mean(cons)) if cons else None,
         "ms_per_reuse_step": float(np.mean(reus)) if reus else None,
         "interactions_per_step": total_i / args.steps,
