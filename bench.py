@@ -344,7 +344,7 @@ def run_loop(afd, torch, ctx, g, st, *, steps, warmup, batch, R, dt, flush, stre
     return step_ms, force_ms, inter, modes, g.stats()["launches"] - launches0
 
 
-def learned_study(args, wl, afd, torch, np, dev, stream, local, p, tuned, flush, plain):
+def learned_study(args, wl, afd, torch, np, dev, stream, local, p, tuned, launch, flush, plain):
     """The learned opening criterion against the plain theta form at equal
     rms force error (error against the FP64 direct sum of sampled
     particles): train the network on the GPU from a sphere like the N = 2^20
@@ -410,6 +410,7 @@ def learned_study(args, wl, afd, torch, np, dev, stream, local, p, tuned, flush,
         gg = afd.Gravity(cfg, local, stream)
         if batch:
             afd.afd_set_systems(gg.ctx, wl["sys_off"], tuned)
+        afd.afd_set_launch(gg.ctx, *launch[:2])
         return gg
 
     # plain form at the initial positions; its |a| is the learned form's reference
@@ -563,6 +564,9 @@ def main():
                                        n_sys=wl["n_systems"])
 
     afd.afd_calc_force_all(ctx, x, y, z, m, acc, afd.AFD_MAKE_LIST_FOR_REUSE)  # evaluation 0
+    # force-kernel block shape and list-chunk size, timed on these lists
+    launch = afd.afd_autotune_launch(ctx, acc, reps=3)
+    afd.afd_calc_force(ctx, acc)  # evaluation 0's forces for the first kick
     if batch:
         afd.afd_graph_capture_step(ctx, x, y, z, vx, vy, vz, m, acc, dt)
     state = {"x": x, "y": y, "z": z, "vx": vx, "vy": vy, "vz": vz, "m": m, "acc": acc, "k": 1}
@@ -611,6 +615,7 @@ def main():
                           for a in (p.x, p.y, p.z, p.m))
         hacc = torch.zeros(n, 4, dtype=torch.float32).pin_memory()
         g2 = afd.Gravity(cfg, local, stream)
+        afd.afd_set_launch(g2.ctx, *launch[:2])
         if batch:
             afd.afd_set_systems(g2.ctx, wl["sys_off"], tuned)
         afd.afd_calc_force_all_host(g2.ctx, hx, hy, hz, hm, hacc, afd.AFD_MAKE_LIST_FOR_REUSE)
@@ -659,13 +664,16 @@ def main():
         "clocks": clocks,
         "gpu_launches": launches,
         "n_grp_autotuned": None if tuned is None else [int(v) for v in tuned],
+        "force_launch_autotuned": {"warps_per_block": launch[0], "chunk": launch[1],
+                                   "ms_chunk32_w2_4_8": [float(v) for v in launch[2][0]],
+                                   "ms_chunk64_w2_4_8": [float(v) for v in launch[2][1]]},
         "wall_s_timed_region": t_wall,
     }
     if e2e:
         line["e2e"] = e2e
     if not args.no_learned and world == 1 and not wl["quad"]:
         line["learned_mac"] = learned_study(args, wl, afd, torch, np, dev, stream, local, p,
-                                            tuned, flush, line)
+                                            tuned, launch, flush, line)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line))

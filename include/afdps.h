@@ -203,6 +203,20 @@ int afd_autotune_n_grp(afd_ctx *ctx, const double *x, const double *y, const dou
                        const double *m, int64_t n, const int32_t *cand, int n_cand, int n_reuse,
                        float *acc4, int32_t *best);
 
+/* Launch shape of the force kernel: warps per block (2, 4 or 8) and list
+ * entries staged per chunk by each warp (32 or 64). Defaults 4 and 32. The
+ * results do not depend on it beyond FP32 summation order within a chunk. */
+int afd_set_launch(afd_ctx *ctx, int warps_per_block, int chunk);
+int afd_get_launch(afd_ctx *ctx, int *warps_per_block, int *chunk);
+
+/* Autotune the force kernel's launch shape on the current lists: every
+ * (chunk, warps) in {32, 64} x {2, 4, 8} is launched once to warm up, then
+ * timed over `reps` launches with CUDA events on the context's stream; the
+ * fastest is installed. ms_out (host, 6 floats, may be NULL) receives the
+ * mean ms per launch, index chunk_index * 3 + warps_index. acc4 (device,
+ * n x 4 floats) receives the forces. Needs lists; synchronises. */
+int afd_autotune_launch(afd_ctx *ctx, float *acc4, int reps, float *ms_out);
+
 /* Wait for the context's stream and return the device status word. */
 int afd_sync(afd_ctx *ctx);
 

@@ -96,6 +96,9 @@ def lib():
         "afd_graph_launch": ([_VP], ctypes.c_int),
         "afd_autotune_n_grp": ([_VP, _VP, _VP, _VP, _VP, _I64, _VP, ctypes.c_int, ctypes.c_int, _VP,
                                 _VP], ctypes.c_int),
+        "afd_set_launch": ([_VP, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "afd_get_launch": ([_VP, _VP, _VP], ctypes.c_int),
+        "afd_autotune_launch": ([_VP, _VP, ctypes.c_int, _VP], ctypes.c_int),
         "afd_mac_set": ([_VP, _VP, _D, _D, _D], ctypes.c_int),
         "afd_mac_set_reference": ([_VP, _VP, _I64], ctypes.c_int),
         "afd_mac_samples": ([_VP, _D, _D, _D, ctypes.c_uint64, _I64, _VP, _VP, _VP, _VP],
@@ -327,6 +330,28 @@ def afd_autotune_n_grp(ctx, x, y, z, m, acc4, candidates, n_reuse, n_sys=1):
                                     int(n_reuse), _dptr(acc4, torch.float32, 4 * n, "acc4"),
                                     _VP(best.ctypes.data)), "afd_autotune_n_grp")
     return best
+
+
+def afd_set_launch(ctx, warps_per_block, chunk):
+    _check(lib().afd_set_launch(ctx, int(warps_per_block), int(chunk)), "afd_set_launch")
+
+
+def afd_get_launch(ctx):
+    w, c = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().afd_get_launch(ctx, ctypes.byref(w), ctypes.byref(c)), "afd_get_launch")
+    return int(w.value), int(c.value)
+
+
+def afd_autotune_launch(ctx, acc4, reps=5):
+    """Time the force kernel over (chunk, warps) in {32, 64} x {2, 4, 8} on
+    the current lists and install the fastest; returns (warps, chunk, ms
+    table of shape (2, 3))."""
+    import torch
+    ms = np.zeros(6, dtype=np.float32)
+    _check(lib().afd_autotune_launch(ctx, _dptr(acc4, torch.float32, what="acc4"), int(reps),
+                                     _VP(ms.ctypes.data)), "afd_autotune_launch")
+    w, c = afd_get_launch(ctx)
+    return w, c, ms.reshape(2, 3)
 
 
 def afd_fp32_peak(device: int = 0, stream=None) -> float:

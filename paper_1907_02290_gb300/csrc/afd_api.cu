@@ -548,6 +548,62 @@ int afd_autotune_n_grp(afd_ctx *c, const double *x, const double *y, const doubl
   return AFD_OK;
 }
 
+int afd_set_launch(afd_ctx *c, int warps_per_block, int chunk) {
+  if (!c || (warps_per_block != 2 && warps_per_block != 4 && warps_per_block != 8) ||
+      (chunk != 32 && chunk != 64))
+    return AFD_ERR_ARG;
+  c->force_warps = warps_per_block;
+  c->force_chunk = chunk;
+  return AFD_OK;
+}
+
+int afd_get_launch(afd_ctx *c, int *warps_per_block, int *chunk) {
+  if (!c || !warps_per_block || !chunk) return AFD_ERR_ARG;
+  *warps_per_block = c->force_warps;
+  *chunk = c->force_chunk;
+  return AFD_OK;
+}
+
+int afd_autotune_launch(afd_ctx *c, float *acc4, int reps, float *ms_out) {
+  if (!c || reps < 1 || (c->n > 0 && !acc4)) return AFD_ERR_ARG;
+  if (!c->have_lists) return c->have_tree ? AFD_ERR_NO_SAVED_LIST : AFD_ERR_NO_TREE;
+  DeviceGuard g(c->device);
+  const int shapes[3] = {2, 4, 8}, chunks[2] = {32, 64};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return AFD_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return AFD_ERR_CUDA;
+  }
+  int st = AFD_OK, bw = c->force_warps, bc = c->force_chunk;
+  float best = 1e30f;
+  for (int ci = 0; ci < 2 && st == AFD_OK; ci++)
+    for (int wi = 0; wi < 3 && st == AFD_OK; wi++) {
+      c->force_warps = shapes[wi];
+      c->force_chunk = chunks[ci];
+      st = launch_force(c, acc4);  // warm-up (and the one-time attribute set)
+      if (st != AFD_OK) break;
+      cudaEventRecord(e0, c->stream);
+      for (int r = 0; r < reps && st == AFD_OK; r++) st = launch_force(c, acc4);
+      cudaEventRecord(e1, c->stream);
+      float ms = 0.0f;
+      if (st == AFD_OK && (cudaEventSynchronize(e1) != cudaSuccess ||
+                           cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        st = AFD_ERR_CUDA;
+      if (ms_out) ms_out[ci * 3 + wi] = ms / (float)reps;
+      if (st == AFD_OK && ms < best) {
+        best = ms;
+        bw = shapes[wi];
+        bc = chunks[ci];
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->force_warps = bw;
+  c->force_chunk = bc;
+  return st;
+}
+
 int afd_sync(afd_ctx *c) {
   if (!c) return AFD_ERR_ARG;
   DeviceGuard g(c->device);

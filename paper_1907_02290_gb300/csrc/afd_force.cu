@@ -35,23 +35,15 @@ namespace {
 #ifndef AFD_FORCE_MIN_BLOCKS
 #define AFD_FORCE_MIN_BLOCKS 8  // resident blocks per SM the register budget targets
 #endif
-#ifndef AFD_FORCE_WARPS
-#define AFD_FORCE_WARPS 4
-#endif
 #ifndef AFD_FORCE_ILP2
 #define AFD_FORCE_ILP2 1  // two independent accumulator chains per lane
 #endif
 #ifndef AFD_FORCE_FLUSH_PAIRS
 #define AFD_FORCE_FLUSH_PAIRS 16  // pair-iterations per lane between Kahan flushes
 #endif
-#ifndef AFD_FORCE_CHUNK
-#define AFD_FORCE_CHUNK 32  // list entries staged per warp per step (32 or 64)
-#endif
 #ifndef AFD_FORCE_PERSISTENT
 #define AFD_FORCE_PERSISTENT 0  // warps take units from an atomic queue
 #endif
-constexpr int kForceWarps = AFD_FORCE_WARPS;
-constexpr int kForceThreads = 32 * kForceWarps;
 
 struct ForceArgs {
   int64_t n_units;
@@ -275,15 +267,14 @@ __device__ __forceinline__ void interact_quad2_half(float4 a, float4 b, uint4 qa
 // (double buffer filled by cp.async) and the packed pair layout of the chunk
 // being computed:
 //   P0[p] = (x_2p, x_2p+1, y_2p, y_2p+1), P1[p] = (z_2p, z_2p+1, m_2p, m_2p+1).
-constexpr int kChunk = AFD_FORCE_CHUNK;  // list entries per staged chunk
-constexpr int kPer = kChunk / 32;        // entries staged by each lane
-constexpr int kPairs = kChunk / 2;       // packed pairs per chunk
-
-template <bool QUAD>
+// CH: list entries per staged chunk (32 or 64, a launch choice); each lane
+// stages CH / 32 entries; CH / 2 packed pairs per chunk.
+template <bool QUAD, int CH>
 struct WarpStage {
-  float4 rh[2][kChunk], rl[2][kChunk];
-  float4 rq0[QUAD ? 2 : 1][QUAD ? kChunk : 1], rq1[QUAD ? 2 : 1][QUAD ? kChunk : 1];
-  float4 rnf[QUAD ? 2 : 1][QUAD ? kChunk : 1];  // cell walk data (s^2 in .w)
+  static constexpr int kPairs = CH / 2;
+  float4 rh[2][CH], rl[2][CH];
+  float4 rq0[QUAD ? 2 : 1][QUAD ? CH : 1], rq1[QUAD ? 2 : 1][QUAD ? CH : 1];
+  float4 rnf[QUAD ? 2 : 1][QUAD ? CH : 1];  // cell walk data (s^2 in .w)
   float4 P0[kPairs], P1[kPairs];
   // quadrupole pairs: QA = (xx, yy), QB = (zz, xy), QC = (xz, yz), each (even, odd)
   float4 QA[QUAD ? kPairs : 1], QB[QUAD ? kPairs : 1], QC[QUAD ? kPairs : 1];
@@ -319,16 +310,16 @@ __device__ __forceinline__ void kahan_fold(float &s, float &c, f2 v) {
   s = t;
 }
 
-// Issue the asynchronous gather of list entries [base, base + kChunk) into
+// Issue the asynchronous gather of list entries [base, base + CH) into
 // buffer b: lane l copies entries base + l + 32 r (lanes past the end copy
 // nothing). j[r] are the entries' indices.
-template <bool QUAD>
-__device__ __forceinline__ void gather(WarpStage<QUAD> &st, int b, int lane, uint64_t base,
+template <bool QUAD, int CH>
+__device__ __forceinline__ void gather(WarpStage<QUAD, CH> &st, int b, int lane, uint64_t base,
                                        uint64_t o1, const uint32_t *j, const float4 *hi,
                                        const float4 *lo, const float4 *sq0, const float4 *sq1,
                                        const float4 *nodef, bool quad_list) {
 #pragma unroll
-  for (int r = 0; r < kPer; r++) {
+  for (int r = 0; r < CH / 32; r++) {
     const int slot = lane + 32 * r;
     if (base + slot < o1) {
       cp_async16(&st.rh[b][slot], hi + j[r]);
@@ -343,30 +334,32 @@ __device__ __forceinline__ void gather(WarpStage<QUAD> &st, int b, int lane, uin
   cp_async_commit();
 }
 
+template <int CH>
 __device__ __forceinline__ void load_idx(uint32_t *j, const uint32_t *idx, uint64_t base,
                                          uint64_t o1, int lane) {
 #pragma unroll
-  for (int r = 0; r < kPer; r++) {
+  for (int r = 0; r < CH / 32; r++) {
     const uint64_t k = base + lane + 32 * r;
     j[r] = k < o1 ? idx[k] : 0u;
   }
 }
 
 // One list (EPJ or SPJ) of one group for one warp with S j-streams.
-template <bool GUARD, bool QUAD, int FAR, int S, int IPT>
-__device__ __forceinline__ void run_list(WarpStage<QUAD> &st, const Lane<IPT> &ln, Sums *sm,
+template <bool GUARD, bool QUAD, int FAR, int S, int IPT, int CH>
+__device__ __forceinline__ void run_list(WarpStage<QUAD, CH> &st, const Lane<IPT> &ln, Sums *sm,
                                          const uint32_t *idx, uint64_t o0, uint64_t o1,
                                          const float4 *hi, const float4 *lo, const float4 *sq0,
                                          const float4 *sq1, const float4 *nodef, bool quad_list,
                                          float eps2, int64_t self_at) {
   if (o0 >= o1) return;
+  constexpr int kChunk = CH, kPer = CH / 32, kPairs = CH / 2;
   const int lane = ln.lane;
   const f2 Z0 = pk(0.0f, 0.0f);
   // prologue: chunk 0 in flight, indices of chunk 1 in registers
   uint32_t j0[kPer], jn[kPer];
-  load_idx(j0, idx, o0, o1, lane);
-  gather<QUAD>(st, 0, lane, o0, o1, j0, hi, lo, sq0, sq1, FAR ? nodef : nullptr, quad_list);
-  load_idx(jn, idx, o0 + kChunk, o1, lane);
+  load_idx<CH>(j0, idx, o0, o1, lane);
+  gather<QUAD, CH>(st, 0, lane, o0, o1, j0, hi, lo, sq0, sq1, FAR ? nodef : nullptr, quad_list);
+  load_idx<CH>(jn, idx, o0 + kChunk, o1, lane);
   f2 AX[IPT], AY[IPT], AZ[IPT], PP[IPT];
 #pragma unroll
   for (int q = 0; q < IPT; q++) AX[q] = AY[q] = AZ[q] = PP[q] = Z0;
@@ -375,8 +368,9 @@ __device__ __forceinline__ void run_list(WarpStage<QUAD> &st, const Lane<IPT> &l
   for (uint64_t base = o0; base < o1; base += kChunk) {
     // next chunk in flight, indices of the one after in registers
     const uint64_t nb = base + kChunk;
-    gather<QUAD>(st, b ^ 1, lane, nb, o1, jn, hi, lo, sq0, sq1, FAR ? nodef : nullptr, quad_list);
-    load_idx(jn, idx, nb + kChunk, o1, lane);
+    gather<QUAD, CH>(st, b ^ 1, lane, nb, o1, jn, hi, lo, sq0, sq1, FAR ? nodef : nullptr,
+                     quad_list);
+    load_idx<CH>(jn, idx, nb + kChunk, o1, lane);
     cp_async_wait<1>();  // this lane's copies of the current chunk have landed
     float rx[kPer], ry[kPer], rz[kPer], rm[kPer];
     const float4 ch = st.ch, cl = st.cl;
@@ -506,19 +500,20 @@ __device__ __forceinline__ void run_list(WarpStage<QUAD> &st, const Lane<IPT> &l
   __syncwarp();
 }
 
-template <bool GUARD, bool QUAD, int FAR, int S, int IPT>
-__device__ __forceinline__ void run_unit(WarpStage<QUAD> &st, const ForceArgs &a, uint32_t g,
+template <bool GUARD, bool QUAD, int FAR, int S, int IPT, int CH>
+__device__ __forceinline__ void run_unit(WarpStage<QUAD, CH> &st, const ForceArgs &a, uint32_t g,
                                          const Lane<IPT> &ln, Sums *sm, int64_t self_at) {
-  run_list<GUARD, QUAD, FAR, S, IPT>(st, ln, sm, a.epj, a.off_e[g], a.off_e[g + 1], a.jhi, a.jlo,
-                                     nullptr, nullptr, nullptr, false, a.eps2, self_at);
-  run_list<GUARD, QUAD, FAR, S, IPT>(st, ln, sm, a.spj, a.off_s[g], a.off_s[g + 1], a.shi, a.slo,
-                                     a.sq0, a.sq1, a.nodef, QUAD, a.eps2, -1);
+  run_list<GUARD, QUAD, FAR, S, IPT, CH>(st, ln, sm, a.epj, a.off_e[g], a.off_e[g + 1], a.jhi,
+                                         a.jlo, nullptr, nullptr, nullptr, false, a.eps2,
+                                         self_at);
+  run_list<GUARD, QUAD, FAR, S, IPT, CH>(st, ln, sm, a.spj, a.off_s[g], a.off_s[g + 1], a.shi,
+                                         a.slo, a.sq0, a.sq1, a.nodef, QUAD, a.eps2, -1);
 }
 
 // One work unit with IPT particles per lane and S j-streams: set up the
 // lanes' i-particles, run both lists, combine the streams and write.
-template <bool GUARD, bool QUAD, int FAR, int S, int IPT>
-__device__ __forceinline__ void unit_body(const ForceArgs &a, WarpStage<QUAD> &st, int lane,
+template <bool GUARD, bool QUAD, int FAR, int S, int IPT, int CH>
+__device__ __forceinline__ void unit_body(const ForceArgs &a, WarpStage<QUAD, CH> &st, int lane,
                                           uint32_t g, uint32_t ioff) {
   constexpr int W = 32 / S;
   Lane<IPT> ln;
@@ -559,7 +554,7 @@ __device__ __forceinline__ void unit_body(const ForceArgs &a, WarpStage<QUAD> &s
   const uint32_t gs = a.g_self[g];
   const int64_t self_at =
       (gs && active[0]) ? (int64_t)a.off_e[g] + (int64_t)(gs - 1u) + (int64_t)il[0] : -1;
-  run_unit<GUARD, QUAD, FAR, S, IPT>(st, a, g, ln, sm, self_at);
+  run_unit<GUARD, QUAD, FAR, S, IPT, CH>(st, a, g, ln, sm, self_at);
 #pragma unroll
   for (int q = 0; q < IPT; q++) {
     float ax = sm[q].sx - sm[q].cx, ay = sm[q].sy - sm[q].cy, az = sm[q].sz - sm[q].cz;
@@ -581,36 +576,59 @@ __device__ __forceinline__ void unit_body(const ForceArgs &a, WarpStage<QUAD> &s
 // particles; lane = stream * W + particle).
 // Work unit u: group g = info.x; info.y holds the first particle offset
 // (bits 0-15) and log2 of the j-stream split S (bits 16-17).
-template <bool GUARD, bool QUAD, int FAR>
-__device__ __forceinline__ void force_unit(const ForceArgs &a, WarpStage<QUAD> &st, int lane,
+template <bool GUARD, bool QUAD, int FAR, int CH>
+__device__ __forceinline__ void force_unit(const ForceArgs &a, WarpStage<QUAD, CH> &st, int lane,
                                            int64_t u) {
   const uint2 info = a.u_info[u];
   const uint32_t g = info.x, ioff = info.y & 0xffffu;
   const int sidx = (int)((info.y >> 16) & 3u);
-  if (sidx == 0) unit_body<GUARD, QUAD, FAR, 1, 1>(a, st, lane, g, ioff);
-  else if (sidx == 1) unit_body<GUARD, QUAD, FAR, 2, 1>(a, st, lane, g, ioff);
-  else unit_body<GUARD, QUAD, FAR, 4, 1>(a, st, lane, g, ioff);
+  if (sidx == 0) unit_body<GUARD, QUAD, FAR, 1, 1, CH>(a, st, lane, g, ioff);
+  else if (sidx == 1) unit_body<GUARD, QUAD, FAR, 2, 1, CH>(a, st, lane, g, ioff);
+  else unit_body<GUARD, QUAD, FAR, 4, 1, CH>(a, st, lane, g, ioff);
 }
 
-template <bool GUARD, bool QUAD, int FAR>
-__global__ void __launch_bounds__(kForceThreads, QUAD ? 4 : AFD_FORCE_MIN_BLOCKS * 4 / AFD_FORCE_WARPS)
+// Block shape is a launch choice (2, 4 or 8 warps): each warp's staging area
+// lives in dynamic shared memory. The register budget is the same for every
+// shape: 64 per thread with FP32 monopoles, 128 with quadrupoles.
+constexpr int kForceMaxThreads = 256;
+
+template <bool GUARD, bool QUAD, int FAR, int CH>
+__global__ void __launch_bounds__(kForceMaxThreads, QUAD ? 2 : AFD_FORCE_MIN_BLOCKS / 2)
     k_force(ForceArgs a) {
-  __shared__ WarpStage<QUAD> stage[kForceWarps];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  extern __shared__ __align__(16) unsigned char force_smem[];
+  WarpStage<QUAD, CH> *stage = reinterpret_cast<WarpStage<QUAD, CH> *>(force_smem);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if (AFD_FORCE_PERSISTENT) {
     for (;;) {
       unsigned long long u = 0;
       if (lane == 0) u = atomicAdd(a.queue, 1ull);
       u = __shfl_sync(0xffffffffu, u, 0);
       if ((int64_t)u >= a.n_units) return;
-      force_unit<GUARD, QUAD, FAR>(a, stage[w], lane, (int64_t)u);
+      force_unit<GUARD, QUAD, FAR, CH>(a, stage[w], lane, (int64_t)u);
       __syncwarp();
     }
   } else {
-    const int64_t u = (int64_t)blockIdx.x * kForceWarps + w;
+    const int64_t u = (int64_t)blockIdx.x * nw + w;
     if (u >= a.n_units) return;
-    force_unit<GUARD, QUAD, FAR>(a, stage[w], lane, u);
+    force_unit<GUARD, QUAD, FAR, CH>(a, stage[w], lane, u);
   }
+}
+
+template <bool GUARD, bool QUAD, int FAR, int CH>
+int launch_k_force(const ForceArgs &a, unsigned nb, int warps, cudaStream_t s) {
+  const size_t smem = sizeof(WarpStage<QUAD, CH>) * (size_t)warps;
+  static bool attr_set[8] = {false, false, false, false, false, false, false, false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 8 && !attr_set[dev]) {
+    if (cudaFuncSetAttribute(k_force<GUARD, QUAD, FAR, CH>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(WarpStage<QUAD, CH>) * 8)) != cudaSuccess)
+      return AFD_ERR_CUDA;
+    attr_set[dev] = true;
+  }
+  k_force<GUARD, QUAD, FAR, CH><<<nb, 32 * warps, smem, s>>>(a);
+  return AFD_OK;
 }
 
 }  // namespace
@@ -640,14 +658,12 @@ int launch_force(afd_ctx *c, float *acc4) {
   a.eps2 = e * e;
   a.out = reinterpret_cast<float4 *>(acc4);
   a.queue = ptr<unsigned long long>(c->u64acc) + 2;
-  unsigned nb = (unsigned)((c->n_units + kForceWarps - 1) / kForceWarps);
+  const int warps = c->force_warps;
+  unsigned nb = (unsigned)((c->n_units + warps - 1) / warps);
   if (AFD_FORCE_PERSISTENT) {
     if (cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), c->stream) != cudaSuccess)
       return AFD_ERR_CUDA;
-    int per_sm = 0, sms = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force<false, false, 0>, kForceThreads, 0);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-    const unsigned cap = (unsigned)(per_sm > 0 ? per_sm : 1) * (unsigned)(sms > 0 ? sms : 1);
+    const unsigned cap = 152u * 32u / (unsigned)warps;  // resident warps per GPU at 64 registers
     if (nb > cap) nb = cap;
   }
   const bool guard = !(a.eps2 > 0.0f);
@@ -657,7 +673,11 @@ int launch_force(afd_ctx *c, float *acc4) {
   const bool timed = cap == cudaStreamCaptureStatusNone;
   if (timed) cudaEventRecord(c->ev0, c->stream);
   const int far = c->cfg.multipole ? c->cfg.far_precision : 0;
-#define AFD_LAUNCH_FORCE(G, Q, F) k_force<G, Q, F><<<nb, kForceThreads, 0, c->stream>>>(a)
+  const bool c64 = c->force_chunk == 64;
+  int st = AFD_OK;
+#define AFD_LAUNCH_FORCE(G, Q, F)                                                     \
+  st = c64 ? launch_k_force<G, Q, F, 64>(a, nb, warps, c->stream)                     \
+           : launch_k_force<G, Q, F, 32>(a, nb, warps, c->stream)
   if (!c->cfg.multipole) {
     if (guard) AFD_LAUNCH_FORCE(true, false, 0);
     else AFD_LAUNCH_FORCE(false, false, 0);
@@ -672,6 +692,7 @@ int launch_force(afd_ctx *c, float *acc4) {
     else AFD_LAUNCH_FORCE(false, true, 0);
   }
 #undef AFD_LAUNCH_FORCE
+  if (st != AFD_OK) return st;
   c->launches++;
   if (timed) {
     cudaEventRecord(c->ev1, c->stream);

@@ -100,6 +100,9 @@ struct afd_ctx {
   void *pinned = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool force_timed = false;
+  // force-kernel launch shape: warps per block (2, 4, 8), list entries staged
+  // per chunk (32, 64); set by afd_set_launch / afd_autotune_launch
+  int force_warps = 4, force_chunk = 32;
 
   // independent systems (a forest): particles [sys_off[s], sys_off[s+1]) form
   // system s, with its own root cell and group size. n_sys = 1: one system.

@@ -502,3 +502,29 @@ def test_mixed_precision_workload_against_direct_sum(env, capsys):
     # the far-field precision barely moves the tree's own error
     assert errs[0][0] < 5e-3
     assert errs[2][0] < 1.05 * errs[0][0] and errs[1][0] < 1.3 * errs[0][0]
+
+
+def test_force_launch_shapes(env):
+    """Every launch shape the autotuner can pick gives oracle-matching forces."""
+    torch, afd, orc = env
+    p = ics.plummer(20000 + 5, 61)
+    kw = dict(n_grp=128, theta=0.5, eps=1.0 / 256)
+    g, _, (x, y, z, m, acc) = run_gpu(env, p, **kw)
+    t = orc.Tree(p.x, p.y, p.z, p.m, **kw)
+    ref = t.force()
+    for chunk in (32, 64):
+        for warps in (2, 4, 8):
+            afd.afd_set_launch(g.ctx, warps, chunk)
+            acc.fill_(float("nan"))
+            afd.afd_calc_force(g.ctx, acc)
+            torch.cuda.synchronize()
+            a = acc.cpu().numpy().astype(np.float64)
+            assert np.all(np.isfinite(a)), (warps, chunk)
+            assert rms_rel_acc(a, ref) <= FORCE_RMS_TOL, (warps, chunk)
+    w, c, ms = afd.afd_autotune_launch(g.ctx, acc, reps=2)
+    assert (w, c) in [(ww, cc) for cc in (32, 64) for ww in (2, 4, 8)]
+    assert ms.shape == (2, 3) and np.all(ms > 0)
+    assert afd.afd_get_launch(g.ctx) == (w, c)
+    with pytest.raises(afd.AfdError):
+        afd.afd_set_launch(g.ctx, 3, 32)
+    g.close()
