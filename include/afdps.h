@@ -376,10 +376,11 @@ int afd_mac_set_reference(afd_ctx *ctx, const float *amag, int64_t n);
 int afd_mac_samples(afd_ctx *ctx, double theta_lo, double theta_hi, double keep, uint64_t seed,
                     int64_t cap, float *feat, float *label, uint32_t *pair, int64_t *n_out);
 
-/* out (host, 4 int64): [0] the last walk used the learned criterion (0/1),
+/* out (host, 5 int64): [0] the last walk used the learned criterion (0/1),
  * [1] network evaluations in it, [2] cells the network accepted, [3]
- * reference magnitudes present for the current particles (0/1).
- * Synchronises when [0] is 1. */
+ * reference magnitudes present for the current particles (0/1), [4] warp
+ * steps of the walk that evaluated the network (so [1] / [4] is the mean
+ * number of lanes busy per evaluation round). Synchronises when [0] is 1. */
 int afd_mac_info(afd_ctx *ctx, int64_t *out);
 
 /* The network's output for n feature rows (feat: device, n x 8 floats; out:

@@ -415,10 +415,10 @@ def afd_mac_samples(ctx, theta_lo, theta_hi, keep, seed, feat, label, pair=None)
 
 
 def afd_mac_info(ctx) -> dict:
-    out = np.zeros(4, dtype=np.int64)
+    out = np.zeros(5, dtype=np.int64)
     _check(lib().afd_mac_info(ctx, _VP(out.ctypes.data)), "afd_mac_info")
     return {"learned": int(out[0]), "evaluations": int(out[1]), "accepted": int(out[2]),
-            "reference": int(out[3])}
+            "reference": int(out[3]), "rounds": int(out[4])}
 
 
 def afd_mlp_forward(params, feat, out, stream=None):

@@ -875,16 +875,17 @@ int afd_mac_samples(afd_ctx *c, double theta_lo, double theta_hi, double keep, u
 int afd_mac_info(afd_ctx *c, int64_t *out) {
   if (!c || !out) return AFD_ERR_ARG;
   out[0] = c->walk_learned ? 1 : 0;
-  out[1] = out[2] = 0;
+  out[1] = out[2] = out[4] = 0;
   if (c->walk_learned && c->mac_cnt.p) {
     CtxDevice g(c->device);
     uint64_t *pin = static_cast<uint64_t *>(c->pinned);
-    if (cudaMemcpyAsync(pin, c->mac_cnt.p, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost,
+    if (cudaMemcpyAsync(pin, c->mac_cnt.p, 3 * sizeof(uint64_t), cudaMemcpyDeviceToHost,
                         c->stream) != cudaSuccess ||
         cudaStreamSynchronize(c->stream) != cudaSuccess)
       return AFD_ERR_CUDA;
     out[1] = (int64_t)pin[0];
     out[2] = (int64_t)pin[1];
+    out[4] = (int64_t)pin[2];
   }
   out[3] = (c->amag_n == c->n && c->n > 0) ? 1 : 0;
   return AFD_OK;

@@ -25,8 +25,15 @@
 // computed as ((dx*dx + dy*dy) + dz*dz) and theta2 * d2 in that order.
 //
 // With the learned criterion (afd_mac.cuh) the same walk decides each cell
-// by decide_learned(): the band tests in FP32 and, inside the band, the
-// network evaluated by the deciding lane with the weights in shared memory.
+// by learned_pre() (the band tests in FP32) and, for the cells inside the
+// band, by the network, which the whole warp evaluates for four band cells
+// at a time: lane j computes hidden unit j of both layers (its weights read
+// from shared memory, the cells' inputs and hidden values broadcast from
+// shared memory, one packed FMA covering two cells), and the 32 output
+// products are summed by an xor butterfly, which adds them in exactly the
+// defined pairwise-halving order. The arithmetic per unit is mac_mlp_t's, so
+// the decisions are the same bit for bit; the warp needs few registers and
+// no lane sits idle in the layers.
 #include "afd_internal.cuh"
 #include "afd_mac.cuh"
 
@@ -159,14 +166,22 @@ __device__ __forceinline__ void rec_put(RecStream &st, bool on, T rec, T *arena,
   }
 }
 
+// Per-warp scratch of the warp-wide network evaluation.
+struct MacScratch {
+  float4 xin[8][kMacNF];  // inputs: [band cell / 4][k] -> 4 cells
+  float4 hin[kMacNH];     // hidden layer 1 of the current 4 cells: [unit]
+};
+
 template <bool LEARNED>
 __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
   __shared__ uint2 stk_all[kWalkWarps][kStack];
   __shared__ __align__(16) float wsm[LEARNED ? kMacNP + 3 : 1];
+  __shared__ __align__(16) MacScratch msc_all[LEARNED ? kWalkWarps : 1];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
   uint2 *stk = stk_all[wib];
-  uint32_t evals = 0, accepts = 0;
+  MacScratch &msc = msc_all[LEARNED ? wib : 0];
+  uint32_t evals = 0, accepts = 0, rounds = 0;
   if (LEARNED) {
     mac_load_transposed(wsm, a.mac_w, threadIdx.x, kWalkThreads);
     __syncthreads();
@@ -280,11 +295,70 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
                       : decide(bmin, bmax, cx, cy, cz, s2, leaf_me, a.theta2);
         }
       }
-      if (LEARNED && valid && d == kBand) {  // each band cell's lane runs the network
-        const bool acc_me = mac_mlp_t(wsm, feat) < a.tau;
-        evals++;
-        accepts += acc_me ? 1u : 0u;
-        d = acc_me ? kAccept : (leaf_me ? kLeaf : kOpen);
+      if (LEARNED) {
+        const bool need = valid && d == kBand;
+        const unsigned bm = __ballot_sync(0xffffffffu, need);
+        if (bm) {  // warp-uniform: the network for every band cell of this step
+          const int nb = __popc(bm), rank = __popc(bm & lt);
+          float y_me = 0.0f;
+          if (lane == 0) rounds++;
+          float *xin = reinterpret_cast<float *>(msc.xin);
+          if (need)
+#pragma unroll
+            for (int k = 0; k < kMacNF; k++)
+              xin[((rank >> 2) * kMacNF + k) * 4 + (rank & 3)] =
+                  __fmul_rn(__fsub_rn(feat[k], wsm[k]), wsm[kMacNF + k]);
+          __syncwarp();
+          for (int g4 = 0; g4 < nb; g4 += 4) {
+            // layer 1, unit = lane, cells g4 .. g4 + 3 (pairs (0,1), (2,3))
+            const float b1 = wsm[kMacOffB1 + lane];
+            unsigned long long A01 = mac_pk(b1, b1), A23 = A01;
+#pragma unroll
+            for (int k = 0; k < kMacNF; k++) {
+              const float w = wsm[kMacOffW1 + k * kMacNH + lane];
+              const float4 x = msc.xin[g4 >> 2][k];
+              const unsigned long long W = mac_pk(w, w);
+              A01 = mac_fma2(W, mac_pk(x.x, x.y), A01);
+              A23 = mac_fma2(W, mac_pk(x.z, x.w), A23);
+            }
+            float h[4] = {mac_lo(A01), mac_hi(A01), mac_lo(A23), mac_hi(A23)};
+#pragma unroll
+            for (int c = 0; c < 4; c++) h[c] = h[c] > 0.0f ? h[c] : 0.0f;
+            msc.hin[lane] = make_float4(h[0], h[1], h[2], h[3]);
+            __syncwarp();
+            // layer 2, unit = lane
+            const float b2 = wsm[kMacOffB2 + lane];
+            unsigned long long B01 = mac_pk(b2, b2), B23 = B01;
+#pragma unroll 8
+            for (int k = 0; k < kMacNH; k++) {
+              const float w = wsm[kMacOffW2 + k * kMacNH + lane];
+              const float4 hk = msc.hin[k];
+              const unsigned long long W = mac_pk(w, w);
+              B01 = mac_fma2(W, mac_pk(hk.x, hk.y), B01);
+              B23 = mac_fma2(W, mac_pk(hk.z, hk.w), B23);
+            }
+            // output: products w3_j h2_j, xor butterfly (= pairwise halving), + b3
+            const float w3 = wsm[kMacOffW3 + lane];
+            float o[4] = {mac_lo(B01), mac_hi(B01), mac_lo(B23), mac_hi(B23)};
+#pragma unroll
+            for (int c = 0; c < 4; c++) o[c] = __fmul_rn(w3, o[c] > 0.0f ? o[c] : 0.0f);
+#pragma unroll
+            for (int off = kMacNH / 2; off > 0; off >>= 1)
+#pragma unroll
+              for (int c = 0; c < 4; c++) o[c] = __fadd_rn(o[c], __shfl_xor_sync(0xffffffffu, o[c], off));
+            const float b3 = wsm[kMacOffB3];
+#pragma unroll
+            for (int c = 0; c < 4; c++)
+              if (need && rank == g4 + c) y_me = __fadd_rn(o[c], b3);
+            __syncwarp();
+          }
+          if (need) {
+            const bool acc_me = y_me < a.tau;
+            evals++;
+            accepts += acc_me ? 1u : 0u;
+            d = acc_me ? kAccept : (leaf_me ? kLeaf : kOpen);
+          }
+        }
       }
       if (valid) child_entry = make_entry(d, c_id, c_first, c_cnt);
       const unsigned vm = __ballot_sync(0xffffffffu, valid);
@@ -342,6 +416,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
     if (lane == 0 && evals) {
       atomicAdd(&a.mac_cnt[0], (unsigned long long)evals);
       atomicAdd(&a.mac_cnt[1], (unsigned long long)accepts);
+      atomicAdd(&a.mac_cnt[2], (unsigned long long)rounds);
     }
   }
 }
@@ -504,7 +579,7 @@ int launch_walk(afd_ctx *c) {
   a.mac_cnt = nullptr;
   if (learned) {
     if ((st = launch_group_amin(c))) return st;
-    if ((st = reserve(c->mac_cnt, 2 * sizeof(unsigned long long)))) return st;
+    if ((st = reserve(c->mac_cnt, 3 * sizeof(unsigned long long)))) return st;
     a.mac_w = ptr<float>(c->mac_w);
     a.g_amin = ptr<float>(c->g_amin);
     a.s_hi = ptr<float4>(c->s_hi);
@@ -535,7 +610,7 @@ int launch_walk(afd_ctx *c) {
     a.cap_l = c->arena_cap_l;
     if (cudaMemsetAsync(c->arena_cur.p, 0, 2 * sizeof(uint32_t), c->stream) != cudaSuccess)
       return AFD_ERR_CUDA;
-    if (learned && cudaMemsetAsync(c->mac_cnt.p, 0, 2 * sizeof(unsigned long long),
+    if (learned && cudaMemsetAsync(c->mac_cnt.p, 0, 3 * sizeof(unsigned long long),
                                    c->stream) != cudaSuccess)
       return AFD_ERR_CUDA;
     if (learned) k_walk<true><<<(unsigned)nb, kWalkThreads, 0, c->stream>>>(a);
