@@ -24,6 +24,12 @@ LIB = os.path.join(PKG, "libafdps.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-Xptxas", "-v"]
+# AFD_CHECK=1 in the environment builds the self-checking variant: every
+# data-dependent index is tested in the kernels, violations are printed and
+# skipped. The flag is part of the up-to-date test.
+CHECK = os.environ.get("AFD_CHECK", "0") == "1"
+if CHECK:
+    NVCC_FLAGS = NVCC_FLAGS + ["-DAFD_CHECK=1"]
 
 
 def nvcc() -> str:
@@ -42,8 +48,13 @@ def _deps():
         [os.path.join(INCLUDE, "afdps.h")]
 
 
+STAMP = os.path.join(BUILD, "variant")
+
+
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(STAMP):
+        return False
+    if open(STAMP).read().strip() != ("check" if CHECK else "release"):
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(p) <= t for p in _deps())
@@ -78,6 +89,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write("check" if CHECK else "release")
     return LIB
 
 

@@ -132,6 +132,7 @@ int tree_build(afd_ctx *c, const double *x, const double *y, const double *z, co
   if (n > 0 && (!x || !y || !z || !m)) return AFD_ERR_ARG;
   if (c->n_sys > 1 && n != c->sys_off_h[c->n_sys]) return AFD_ERR_SHAPE;
   c->have_tree = c->have_lists = c->saved = false;
+  c->n = n;
   TRY(launch_root(c, x, y, z, m, n));
   TRY(launch_keys(c, x, y, z, n));
   TRY(launch_sort(c, n));
@@ -141,7 +142,6 @@ int tree_build(afd_ctx *c, const double *x, const double *y, const double *z, co
   TRY(launch_moments(c, true, c->cfg.mac != 0));
   TRY(launch_groups(c));
   TRY(launch_group_boxes(c));
-  c->n = n;
   c->have_tree = true;
   return AFD_OK;
 }

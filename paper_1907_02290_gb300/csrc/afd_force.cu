@@ -59,6 +59,8 @@ struct ForceArgs {
   const uint32_t *perm;
   float eps2;
   float4 *out;
+  // sizes, read only by the self-checking build
+  uint64_t n, n_cells, n_groups, n_epj, n_spj;
 };
 
 __device__ __forceinline__ float rsqrt_fast(float x) {
@@ -336,11 +338,12 @@ __device__ __forceinline__ void gather(WarpStage<QUAD, CH> &st, int b, int lane,
 
 template <int CH>
 __device__ __forceinline__ void load_idx(uint32_t *j, const uint32_t *idx, uint64_t base,
-                                         uint64_t o1, int lane) {
+                                         uint64_t o1, int lane, uint64_t jbound) {
 #pragma unroll
   for (int r = 0; r < CH / 32; r++) {
     const uint64_t k = base + lane + 32 * r;
     j[r] = k < o1 ? idx[k] : 0u;
+    if (!AFD_IN(j[r], jbound, "force list entry")) j[r] = 0u;
   }
 }
 
@@ -350,16 +353,18 @@ __device__ __forceinline__ void run_list(WarpStage<QUAD, CH> &st, const Lane<IPT
                                          const uint32_t *idx, uint64_t o0, uint64_t o1,
                                          const float4 *hi, const float4 *lo, const float4 *sq0,
                                          const float4 *sq1, const float4 *nodef, bool quad_list,
-                                         float eps2, int64_t self_at) {
+                                         float eps2, int64_t self_at, uint64_t nlist,
+                                         uint64_t jbound) {
   if (o0 >= o1) return;
+  if (!AFD_IN(o1 - 1, nlist, "force list range")) return;
   constexpr int kChunk = CH, kPer = CH / 32, kPairs = CH / 2;
   const int lane = ln.lane;
   const f2 Z0 = pk(0.0f, 0.0f);
   // prologue: chunk 0 in flight, indices of chunk 1 in registers
   uint32_t j0[kPer], jn[kPer];
-  load_idx<CH>(j0, idx, o0, o1, lane);
+  load_idx<CH>(j0, idx, o0, o1, lane, jbound);
   gather<QUAD, CH>(st, 0, lane, o0, o1, j0, hi, lo, sq0, sq1, FAR ? nodef : nullptr, quad_list);
-  load_idx<CH>(jn, idx, o0 + kChunk, o1, lane);
+  load_idx<CH>(jn, idx, o0 + kChunk, o1, lane, jbound);
   f2 AX[IPT], AY[IPT], AZ[IPT], PP[IPT];
 #pragma unroll
   for (int q = 0; q < IPT; q++) AX[q] = AY[q] = AZ[q] = PP[q] = Z0;
@@ -370,7 +375,7 @@ __device__ __forceinline__ void run_list(WarpStage<QUAD, CH> &st, const Lane<IPT
     const uint64_t nb = base + kChunk;
     gather<QUAD, CH>(st, b ^ 1, lane, nb, o1, jn, hi, lo, sq0, sq1, FAR ? nodef : nullptr,
                      quad_list);
-    load_idx<CH>(jn, idx, nb + kChunk, o1, lane);
+    load_idx<CH>(jn, idx, nb + kChunk, o1, lane, jbound);
     cp_async_wait<1>();  // this lane's copies of the current chunk have landed
     float rx[kPer], ry[kPer], rz[kPer], rm[kPer];
     const float4 ch = st.ch, cl = st.cl;
@@ -505,9 +510,10 @@ __device__ __forceinline__ void run_unit(WarpStage<QUAD, CH> &st, const ForceArg
                                          const Lane<IPT> &ln, Sums *sm, int64_t self_at) {
   run_list<GUARD, QUAD, FAR, S, IPT, CH>(st, ln, sm, a.epj, a.off_e[g], a.off_e[g + 1], a.jhi,
                                          a.jlo, nullptr, nullptr, nullptr, false, a.eps2,
-                                         self_at);
+                                         self_at, a.n_epj, a.n);
   run_list<GUARD, QUAD, FAR, S, IPT, CH>(st, ln, sm, a.spj, a.off_s[g], a.off_s[g + 1], a.shi,
-                                         a.slo, a.sq0, a.sq1, a.nodef, QUAD, a.eps2, -1);
+                                         a.slo, a.sq0, a.sq1, a.nodef, QUAD, a.eps2, -1, a.n_spj,
+                                         a.n_cells);
 }
 
 // One work unit with IPT particles per lane and S j-streams: set up the
@@ -521,7 +527,8 @@ __device__ __forceinline__ void unit_body(const ForceArgs &a, WarpStage<QUAD, CH
   ln.stream = lane / W;
   const uint32_t gf = a.g_first[g], gc = a.g_count[g];
   // origin of the relative coordinates: the group cell's centre of mass
-  const uint32_t gcell = a.g_cell[g];
+  uint32_t gcell = a.g_cell[g];
+  if (!AFD_IN(gcell, a.n_cells, "force group cell")) gcell = 0u;
   const float4 ch = a.shi[gcell], cl = a.slo[gcell];
   if (lane == 0) {
     st.ch = ch;
@@ -532,7 +539,7 @@ __device__ __forceinline__ void unit_body(const ForceArgs &a, WarpStage<QUAD, CH
 #pragma unroll
   for (int q = 0; q < IPT; q++) {
     il[q] = ioff + (uint32_t)(q * 32 + (lane & (W - 1)));
-    active[q] = il[q] < gc;
+    active[q] = il[q] < gc && AFD_IN(gf + il[q], a.n, "force i-particle");
     float xi = 0.f, yi = 0.f, zi = 0.f;
     if (active[q]) {
       const float4 h = a.jhi[gf + il[q]], l = a.jlo[gf + il[q]];
@@ -567,7 +574,10 @@ __device__ __forceinline__ void unit_body(const ForceArgs &a, WarpStage<QUAD, CH
       az += __shfl_xor_sync(0xffffffffu, az, o);
       pot += __shfl_xor_sync(0xffffffffu, pot, o);
     }
-    if (active[q] && ln.stream == 0) a.out[a.perm[gf + il[q]]] = make_float4(ax, ay, az, -pot);
+    if (active[q] && ln.stream == 0) {
+      const uint32_t o = a.perm[gf + il[q]];
+      if (AFD_IN(o, a.n, "force output")) a.out[o] = make_float4(ax, ay, az, -pot);
+    }
   }
 }
 
@@ -580,6 +590,7 @@ template <bool GUARD, bool QUAD, int FAR, int CH>
 __device__ __forceinline__ void force_unit(const ForceArgs &a, WarpStage<QUAD, CH> &st, int lane,
                                            int64_t u) {
   const uint2 info = a.u_info[u];
+  if (!AFD_IN(info.x, a.n_groups, "force unit group")) return;
   const uint32_t g = info.x, ioff = info.y & 0xffffu;
   const int sidx = (int)((info.y >> 16) & 3u);
   if (sidx == 0) unit_body<GUARD, QUAD, FAR, 1, 1, CH>(a, st, lane, g, ioff);
@@ -657,6 +668,11 @@ int launch_force(afd_ctx *c, float *acc4) {
   const float e = (float)c->cfg.eps;
   a.eps2 = e * e;
   a.out = reinterpret_cast<float4 *>(acc4);
+  a.n = (uint64_t)c->n;
+  a.n_cells = (uint64_t)c->n_cells;
+  a.n_groups = (uint64_t)c->n_groups;
+  a.n_epj = c->n_epj;
+  a.n_spj = c->n_spj;
   a.queue = ptr<unsigned long long>(c->u64acc) + 2;
   const int warps = c->force_warps;
   unsigned nb = (unsigned)((c->n_units + warps - 1) / warps);

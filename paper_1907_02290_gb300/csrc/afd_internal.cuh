@@ -40,6 +40,28 @@ int status_to_error(int bits);
 
 }  // namespace afd
 
+// Self-checking build (compile with -DAFD_CHECK=1): the kernels test every
+// index that comes from data (list entries, chunk links, tree links) before
+// using it, print each violation and skip the access. Off by default.
+#ifndef AFD_CHECK
+#define AFD_CHECK 0
+#endif
+#if AFD_CHECK
+#include <cstdio>
+static __device__ __noinline__ bool afd_check_fail(const char *where, unsigned long long i,
+                                                   unsigned long long bound) {
+  printf("AFD_CHECK %s: index %llu not below %llu (block %d thread %d)\n", where, i, bound,
+         (int)blockIdx.x, (int)threadIdx.x);
+  return false;
+}
+#define AFD_IN(i, bound, where)                                                   \
+  ((unsigned long long)(i) < (unsigned long long)(bound)                          \
+       ? true                                                                     \
+       : afd_check_fail(where, (unsigned long long)(i), (unsigned long long)(bound)))
+#else
+#define AFD_IN(i, bound, where) true
+#endif
+
 struct afd_ctx {
   afd_config cfg{};
   int device = 0;

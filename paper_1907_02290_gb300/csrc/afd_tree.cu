@@ -560,6 +560,7 @@ struct MomArgs {
   uint2 *node_i;
   uint4 *block;  // child walk records, 8 per cell (null: not written)
   int quad_on;
+  int64_t n_part;  // particles (read only by the self-checking build)
 };
 
 __device__ __forceinline__ int n_children(const uint32_t *child, uint32_t c) {
@@ -658,6 +659,7 @@ __global__ void __launch_bounds__(kThreads) k_moments(MomArgs a) {
   {
     double M = 0.0, S[3] = {0.0, 0.0, 0.0};
     const uint32_t f = a.first[c], e = f + a.count[c];
+    if (e > f && !AFD_IN(e - 1, a.n_part, "moments leaf range")) return;
     for (uint32_t k = f; k < e; k++) {
       const double mk = a.ms[k];
       M = __dadd_rn(M, mk);
@@ -671,6 +673,7 @@ __global__ void __launch_bounds__(kThreads) k_moments(MomArgs a) {
   for (;;) {
     const uint32_t p = a.parent[c];
     if (p == kNone) break;
+    if (!AFD_IN(p, a.n_cells, "moments parent")) break;
     __threadfence();
     const unsigned old = atomicAdd(&a.arrive[p], 1u);
     if ((int)old != n_children(a.child, p) - 1) break;
@@ -678,7 +681,7 @@ __global__ void __launch_bounds__(kThreads) k_moments(MomArgs a) {
     double M = 0.0, S[3] = {0.0, 0.0, 0.0};
     for (int o = 0; o < 8; o++) {
       const uint32_t cc = __ldg(&a.child[(size_t)p * 8 + o]);
-      if (cc == kNone) continue;
+      if (cc == kNone || !AFD_IN(cc, a.n_cells, "moments child")) continue;
       M = __dadd_rn(M, __ldcg(&a.mass[cc]));
       for (int d = 0; d < 3; d++) S[d] = __dadd_rn(S[d], __ldcg(&a.smom[(size_t)cc * 3 + d]));
     }
@@ -1070,6 +1073,7 @@ int launch_moments(afd_ctx *c, bool child_blocks, bool need_q) {
   a.node_i = ptr<uint2>(c->node_i);
   a.block = child_blocks ? ptr<uint4>(c->c_block) : nullptr;
   a.quad_on = quad_on;
+  a.n_part = c->n;
   k_moments<<<blocks_for(nc), kThreads, 0, c->stream>>>(a);
   c->launches++;
   return ck();

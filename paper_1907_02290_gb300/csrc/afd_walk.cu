@@ -64,6 +64,7 @@ struct WalkArgs {
   uint32_t cap_s, cap_l;
   int *status;
   uint32_t iter_cap;
+  uint32_t n_cells;  // read only by the self-checking build
   // learned criterion
   const float *mac_w, *g_amin;
   const float4 *s_hi, *s_q0, *s_q1;
@@ -201,7 +202,8 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
     RecStream rs{kNone, kChunk}, rl{kNone, kChunk};
     uint32_t self_pos = 0;  // 1 + EPJ-list position of the group's first particle
     if (lane == 0) {
-      const uint32_t root = a.g_root[g];
+      uint32_t root = a.g_root[g];
+      if (!AFD_IN(root, a.n_cells, "walk root")) root = 0u;
       const float4 nf = a.node_f[root];
       const uint2 ni = a.node_i[root];
       const bool leaf = (ni.y >> 31) != 0;
@@ -272,7 +274,8 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
 #pragma unroll
       for (int q = 0; q < kExpand; q++)
         if (q == q_me) p_me = pos_q[q];
-      const uint32_t cid_me = __shfl_sync(0xffffffffu, e.x, p_me < 0 ? 0 : p_me);
+      uint32_t cid_me = __shfl_sync(0xffffffffu, e.x, p_me < 0 ? 0 : p_me);
+      if (q_me < E && !AFD_IN(cid_me, a.n_cells, "walk expanded cell")) cid_me = 0u;
       bool valid = false, leaf_me = false;
       uint2 child_entry = make_uint2(0u, 0u);
       uint32_t d = 0, c_id = 0, c_first = 0, c_cnt = 0;
@@ -282,7 +285,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
       if (q_me < E) {
         const uint4 *blk = a.block + ((size_t)cid_me * 8 + c_me) * 2;
         const uint4 nf = blk[0], meta = blk[1];
-        valid = meta.z != kNone;
+        valid = meta.z != kNone && AFD_IN(meta.z, a.n_cells, "walk child");
         if (valid) {
           leaf_me = (meta.y >> 31) != 0;
           c_id = meta.z;
@@ -442,6 +445,8 @@ struct CompactArgs {
   const uint2 *arena_l;
   const uint64_t *off_e, *off_s;
   uint32_t *epj, *spj;
+  uint32_t cap_s, cap_l;  // read only by the self-checking build
+  uint64_t n_epj, n_spj;
 };
 
 constexpr int kCompactBuf = 1024;  // staged EPJ entries per warp
@@ -456,14 +461,18 @@ __global__ void __launch_bounds__(256) k_compact(CompactArgs a) {
   uint32_t c = a.head_s[g];
   const uint64_t os = a.off_s[g];
   for (uint32_t i0 = 0; i0 < ms; i0 += kChunk) {
+    if (!AFD_IN(c, a.cap_s, "compact cell chunk")) return;
     const uint32_t nn = min(kChunk, ms - i0);
-    for (uint32_t k = lane; k < nn; k += 32) a.spj[os + i0 + k] = a.arena_s[(size_t)c * kChunk + k];
+    for (uint32_t k = lane; k < nn; k += 32)
+      if (AFD_IN(os + i0 + k, a.n_spj, "compact spj write"))
+        a.spj[os + i0 + k] = a.arena_s[(size_t)c * kChunk + k];
     if (i0 + kChunk < ms) c = a.next_s[c];
   }
   const uint32_t r = a.n_lrec[g];
   c = a.head_l[g];
   uint64_t pos = a.off_e[g];
   for (uint32_t i0 = 0; i0 < r; i0 += kChunk) {
+    if (!AFD_IN(c, a.cap_l, "compact leaf chunk")) return;
     const uint32_t nrec = min(kChunk, r - i0);
     for (uint32_t j0 = 0; j0 < nrec; j0 += 32) {
       const bool on = lane < nrec - j0;
@@ -481,7 +490,8 @@ __global__ void __launch_bounds__(256) k_compact(CompactArgs a) {
         // stores the run with coalesced writes
         for (uint32_t k = 0; k < rec.y; k++) buf[ex + k] = rec.x + k;
         __syncwarp();
-        for (uint32_t i = lane; i < tot; i += 32) a.epj[pos + i] = buf[i];
+        for (uint32_t i = lane; i < tot; i += 32)
+          if (AFD_IN(pos + i, a.n_epj, "compact epj write")) a.epj[pos + i] = buf[i];
         __syncwarp();
       } else {  // very large leaves (level 21): one leaf at a time
         unsigned lm = __ballot_sync(0xffffffffu, on && rec.y > 0);
@@ -491,7 +501,8 @@ __global__ void __launch_bounds__(256) k_compact(CompactArgs a) {
           const uint32_t f0 = __shfl_sync(0xffffffffu, rec.x, src);
           const uint32_t c0 = __shfl_sync(0xffffffffu, rec.y, src);
           const uint32_t x0 = __shfl_sync(0xffffffffu, ex, src);
-          for (uint32_t k = lane; k < c0; k += 32) a.epj[pos + x0 + k] = f0 + k;
+          for (uint32_t k = lane; k < c0; k += 32)
+            if (AFD_IN(pos + x0 + k, a.n_epj, "compact epj write")) a.epj[pos + x0 + k] = f0 + k;
         }
       }
       pos += tot;
@@ -571,6 +582,7 @@ int launch_walk(afd_ctx *c) {
   a.cursor = ptr<uint32_t>(c->arena_cur);
   a.status = ptr<int>(c->status);
   a.iter_cap = (uint32_t)(2 * c->n_cells + 64);
+  a.n_cells = (uint32_t)c->n_cells;
   const bool learned = mac_usable(c);
   a.mac_w = nullptr;
   a.g_amin = nullptr;
@@ -661,6 +673,10 @@ int launch_walk(afd_ctx *c) {
   k.off_s = ptr<uint64_t>(c->spj_off);
   k.epj = ptr<uint32_t>(c->epj);
   k.spj = ptr<uint32_t>(c->spj);
+  k.cap_s = c->arena_cap_s;
+  k.cap_l = c->arena_cap_l;
+  k.n_epj = c->n_epj;
+  k.n_spj = c->n_spj;
   k_compact<<<(unsigned)((ng * 32 + 255) / 256), 256, 0, c->stream>>>(k);
   c->launches++;
   return cudaGetLastError() == cudaSuccess ? AFD_OK : AFD_ERR_CUDA;
