@@ -88,3 +88,23 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(afd._build, "LIB", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         afd.lib()
+
+
+def test_self_checking_variant_compiles(tmp_path):
+    """The AFD_CHECK=1 variant (index checks in the kernels) still builds."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from paper_1907_02290_gb300 import build
+
+    def compile_one(name):
+        src = os.path.join(PKG, "csrc", name)
+        cmd = [build.nvcc(), "-c", src, "-o", str(tmp_path / (name + ".o")), "-I",
+               os.path.join(ROOT, "include")] + build.ARCH + \
+            ["-O1", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+             "-DAFD_CHECK=1"]
+        return subprocess.run(cmd, capture_output=True, text=True)
+
+    with ThreadPoolExecutor(3) as ex:
+        res = list(ex.map(compile_one, ["afd_force.cu", "afd_walk.cu", "afd_tree.cu"]))
+    for r in res:
+        assert r.returncode == 0, r.stderr[-2000:]
