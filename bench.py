@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--mac-samples", type=int, default=1_000_000)
     ap.add_argument("--mac-band", default="0.4,1.0",
                     help="theta_lo,theta_hi of the learned criterion's band")
+    ap.add_argument("--sweep", action="store_true",
+                    help="instead of the benchmark line: theta x n_grp and n_reuse sweeps of "
+                         "the workload, one JSON line per configuration")
     return ap.parse_args()
 
 
@@ -508,6 +511,95 @@ def learned_study(args, wl, afd, torch, np, dev, stream, local, p, tuned, launch
     }
 
 
+def sweep(args, wl):
+    """The method's two knobs on this GPU (the paper's Section 6 measures the
+    same dependences on its systems): for theta x n_grp, the construction
+    time (tree + lists), the force-kernel time, interactions, mean group size
+    <n_i> and list length, time per interaction and the rms force error
+    against the FP64 direct sum of 4096 particles; then ms per KDK step for
+    n_reuse in 1, 2, 4, 8, 16 (32 steps each)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1907_02290_gb300 as afd
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    p = particles(wl)
+    n = p.n
+    T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    xs = [T(a) for a in (p.x, p.y, p.z, p.m)]
+    tg = np.unique(np.linspace(0, n - 1, 4096).astype(np.int64))
+    ex = torch.empty(len(tg), 4, dtype=torch.float64, device=dev)
+    afd.afd_direct_sum(*xs, torch.tensor(tg.astype(np.int32), device=dev), wl["eps"], ex, stream)
+    ex = ex.cpu().numpy()
+    tg_t = torch.tensor(tg, device=dev)
+    acc = torch.empty(n, 4, dtype=torch.float32, device=dev)
+
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        return e
+
+    for theta in (0.3, 0.4, 0.5, 0.6, 0.7):
+        for n_grp in (32, 64, 128, 256, 512, 1024):
+            cfg = afd.Config(eps=wl["eps"], theta=theta, n_leaf=16, n_grp=n_grp,
+                             multipole=int(wl["quad"]))
+            g = afd.Gravity(cfg, 0, stream)
+            afd.afd_set_launch(g.ctx, 2, 32)
+            t_cons, t_force = [], []
+            for rep in range(4):
+                e0 = ev()
+                afd.afd_tree_build(g.ctx, *xs)
+                afd.afd_make_interaction_lists(g.ctx, afd.AFD_MAKE_LIST_FOR_REUSE)
+                e1 = ev()
+                afd.afd_calc_force(g.ctx, acc)
+                e2 = ev()
+                e2.synchronize()
+                if rep:  # the first pass warms up
+                    t_cons.append(e0.elapsed_time(e1))
+                    t_force.append(e1.elapsed_time(e2))
+            st = g.stats()
+            a = acc[tg_t].double().cpu().numpy()
+            err = float(np.sqrt(np.mean(((a[:, :3] - ex[:, :3]) ** 2).sum(1)
+                                        / (ex[:, :3] ** 2).sum(1))))
+            tf = float(np.median(t_force))
+            print(json.dumps({
+                "sweep": "theta_n_grp", "workload": wl["name"], "theta": theta, "n_grp": n_grp,
+                "construction_ms": float(np.median(t_cons)), "force_ms": tf,
+                "interactions": st["interactions"], "groups": st["n_groups"],
+                "mean_n_i": n / st["n_groups"],
+                "mean_list": (st["n_epj"] + st["n_spj"]) / st["n_groups"],
+                "ns_per_interaction": 1e6 * tf / st["interactions"],
+                "rms_rel_force_error": err}), flush=True)
+            g.close()
+
+    R_list = (1, 2, 4, 8, 16)
+    for R in R_list:
+        cfg = afd.Config(eps=wl["eps"], theta=wl["theta"], n_leaf=16, n_grp=wl["n_grp"],
+                         multipole=int(wl["quad"]))
+        g = afd.Gravity(cfg, 0, stream)
+        afd.afd_set_launch(g.ctx, 2, 32)
+        st = {k: T(getattr(p, k)) for k in ("x", "y", "z", "vx", "vy", "vz", "m")}
+        st["acc"] = torch.zeros(n, 4, dtype=torch.float32, device=dev)
+        st["k"] = 1
+        afd.afd_calc_force_all(g.ctx, st["x"], st["y"], st["z"], st["m"], st["acc"],
+                               afd.AFD_MAKE_LIST_FOR_REUSE)
+        flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+        step_ms, _, inter, _, _ = run_loop(afd, torch, g.ctx, g, st, steps=32, warmup=R,
+                                           batch=False, R=R, dt=wl["dt"], flush=flush,
+                                           stream=stream, dev=dev)
+        print(json.dumps({"sweep": "n_reuse", "workload": wl["name"], "n_reuse": R,
+                          "theta": wl["theta"], "n_grp": wl["n_grp"],
+                          "ms_per_step": float(np.mean(step_ms)),
+                          "interactions_per_step": float(np.mean(inter))}), flush=True)
+        g.close()
+
+
 def main():
     args = parse()
     wl = workload(args.workload)
@@ -519,6 +611,10 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             run_reference(args, wl)
+        return
+    if args.sweep:
+        if rank == 0:
+            sweep(args, wl)
         return
 
     import numpy as np

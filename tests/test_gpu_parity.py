@@ -306,10 +306,13 @@ def test_full_size_plummer_1m(env):
     g.close()
 
 
-def test_batched_systems_match_per_system_oracle(env):
+@pytest.mark.parametrize("learned", [False, True])
+def test_batched_systems_match_per_system_oracle(env, learned):
     """Several independent systems in one context (one set of launches): each
     system's root, keys, tree, groups, lists and forces equal those of an
-    oracle run on that system alone (ids shifted by the system's offsets)."""
+    oracle run on that system alone (ids shifted by the system's offsets) --
+    with the theta criterion, and with the learned criterion (reference |a|
+    per system from the oracle's direct sum, random FP16 network)."""
     torch, afd, orc = env
     sizes = [3000, 17, 1, 12000, 5000, 0, 700]
     n_grp = [64, 8, 64, 128, 32, 16, 256]
@@ -324,9 +327,24 @@ def test_batched_systems_match_per_system_oracle(env):
     X = [np.concatenate([q[i] for q in parts]) for i in range(4)]
     kw = dict(theta=0.5, eps=1.0 / 256)
     dev = torch.device("cuda:0")
-    g = afd.Gravity(afd.Config(n_grp=64, **kw), 0, torch.cuda.current_stream())
+    g = afd.Gravity(afd.Config(n_grp=64, mac=int(learned), **kw), 0, torch.cuda.current_stream())
     afd.afd_set_systems(g.ctx, off, n_grp)
     x, y, z, m = (torch.tensor(a, device=dev) for a in X)
+    mac, amags = None, []
+    if learned:
+        gen = np.random.default_rng(77)
+        w = gen.normal(0.0, 0.3, orc.MAC_NP).astype(np.float32)
+        w[:8] = gen.normal(0.0, 2.0, 8)
+        w[8:16] = 0.25
+        mac = dict(params=orc.fp16_round(w), theta_lo=0.25, theta_hi=1.0, tau=0.0)
+        for q in parts:
+            if len(q[0]) == 0:
+                amags.append(np.zeros(0, np.float32))
+                continue
+            ax, ay, az, _ = orc.direct_sum(*q, kw["eps"])
+            amags.append(np.sqrt(ax * ax + ay * ay + az * az).astype(np.float32))
+        afd.afd_mac_set(g.ctx, w, 0.25, 1.0, 0.0)
+        afd.afd_mac_set_reference(g.ctx, torch.tensor(np.concatenate(amags), device=dev))
     acc = torch.full((off[-1], 4), float("nan"), dtype=torch.float32, device=dev)
     g.force_all(x, y, z, m, acc, afd.AFD_MAKE_LIST_FOR_REUSE)
     torch.cuda.synchronize()
@@ -341,7 +359,7 @@ def test_batched_systems_match_per_system_oracle(env):
     for k, n in enumerate(sizes):
         sl = slice(off[k], off[k + 1])
         q = parts[k]
-        t = orc.Tree(*q, n_grp=n_grp[k], **kw)
+        t = orc.Tree(*q, n_grp=n_grp[k], mac=mac, amag=amags[k] if learned else None, **kw)
         if n == 0:
             assert t.sizes()["n_cells"] == 0
             continue
@@ -383,7 +401,8 @@ def test_batched_systems_match_per_system_oracle(env):
         if n < 2:
             continue
         sl = slice(off[k], off[k + 1])
-        t = orc.Tree(*parts[k], n_grp=n_grp[k], **kw)
+        t = orc.Tree(*parts[k], n_grp=n_grp[k], mac=mac, amag=amags[k] if learned else None,
+                     **kw)
         t.update(parts[k][0] + 1e-3, parts[k][1], parts[k][2], parts[k][3])
         assert rms_rel_acc(a2[sl], t.force()) <= FORCE_RMS_TOL
     g.close()
