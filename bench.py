@@ -578,6 +578,34 @@ def sweep(args, wl):
                 "rms_rel_force_error": err}), flush=True)
             g.close()
 
+    # the non-indirect ablation: j-data copied into list order every
+    # evaluation (the copy must follow the particles), then read without
+    # indices; the indirect kernel reads the same data by index
+    cfg = afd.Config(eps=wl["eps"], theta=wl["theta"], n_leaf=16, n_grp=wl["n_grp"])
+    g = afd.Gravity(cfg, 0, stream)
+    afd.afd_set_launch(g.ctx, 2, 32)
+    afd.afd_tree_build(g.ctx, *xs)
+    afd.afd_make_interaction_lists(g.ctx, afd.AFD_MAKE_LIST_FOR_REUSE)
+    t_ind, t_copy, t_dir = [], [], []
+    for rep in range(6):
+        e0 = ev()
+        afd.afd_calc_force(g.ctx, acc)
+        e1 = ev()
+        e1.synchronize()
+        c_ms, f_ms = afd.afd_calc_force_materialized(g.ctx, acc)
+        if rep:
+            t_ind.append(e0.elapsed_time(e1))
+            t_copy.append(c_ms)
+            t_dir.append(f_ms)
+    st = g.stats()
+    print(json.dumps({"sweep": "indirect_ablation", "workload": wl["name"], "theta": wl["theta"],
+                      "n_grp": wl["n_grp"], "list_entries": st["n_epj"] + st["n_spj"],
+                      "indirect_force_ms": float(np.median(t_ind)),
+                      "materialize_ms": float(np.median(t_copy)),
+                      "materialized_force_ms": float(np.median(t_dir)),
+                      "materialized_bytes": 32 * (st["n_epj"] + st["n_spj"])}), flush=True)
+    g.close()
+
     R_list = (1, 2, 4, 8, 16)
     for R in R_list:
         cfg = afd.Config(eps=wl["eps"], theta=wl["theta"], n_leaf=16, n_grp=wl["n_grp"],

@@ -217,6 +217,16 @@ int afd_get_launch(afd_ctx *ctx, int *warps_per_block, int *chunk);
  * n x 4 floats) receives the forces. Needs lists; synchronises. */
 int afd_autotune_launch(afd_ctx *ctx, float *acc4, int reps, float *ms_out);
 
+/* The non-indirect ablation of the force calculation (the paper compares
+ * the indirect scheme with sending each group's j-data itself, Section 4.1):
+ * copy the j-data (hi/lo float4 pairs) of every EPJ and SPJ list entry into
+ * list order (device buffers owned by the context, 32 bytes per entry), then
+ * run the same force kernel reading those copies contiguously instead of by
+ * index. The forces equal afd_calc_force's bit for bit. Monopole lists only
+ * (AFD_ERR_ARG with quadrupoles). ms_out (host, 2 floats, may be NULL): the
+ * copy and the force kernel, CUDA-event milliseconds. Synchronises. */
+int afd_calc_force_materialized(afd_ctx *ctx, float *acc4, float *ms_out);
+
 /* Wait for the context's stream and return the device status word. */
 int afd_sync(afd_ctx *ctx);
 

@@ -97,6 +97,7 @@ def lib():
         "afd_autotune_n_grp": ([_VP, _VP, _VP, _VP, _VP, _I64, _VP, ctypes.c_int, ctypes.c_int, _VP,
                                 _VP], ctypes.c_int),
         "afd_set_launch": ([_VP, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "afd_calc_force_materialized": ([_VP, _VP, _VP], ctypes.c_int),
         "afd_get_launch": ([_VP, _VP, _VP], ctypes.c_int),
         "afd_autotune_launch": ([_VP, _VP, ctypes.c_int, _VP], ctypes.c_int),
         "afd_mac_set": ([_VP, _VP, _D, _D, _D], ctypes.c_int),
@@ -330,6 +331,15 @@ def afd_autotune_n_grp(ctx, x, y, z, m, acc4, candidates, n_reuse, n_sys=1):
                                     int(n_reuse), _dptr(acc4, torch.float32, 4 * n, "acc4"),
                                     _VP(best.ctypes.data)), "afd_autotune_n_grp")
     return best
+
+
+def afd_calc_force_materialized(ctx, acc4):
+    """Non-indirect ablation; returns (copy ms, force ms)."""
+    import torch
+    ms = np.zeros(2, dtype=np.float32)
+    _check(lib().afd_calc_force_materialized(ctx, _dptr(acc4, torch.float32, what="acc4"),
+                                             _VP(ms.ctypes.data)), "afd_calc_force_materialized")
+    return float(ms[0]), float(ms[1])
 
 
 def afd_set_launch(ctx, warps_per_block, chunk):

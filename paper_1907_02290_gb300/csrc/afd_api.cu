@@ -264,7 +264,8 @@ void afd_destroy(afd_ctx *c) {
                     &c->sys_grp_d, &c->sys_of, &c->sys_s, &c->root_tiles, &c->g_root,
                     &c->mac_w, &c->amag, &c->amag_s, &c->g_amin, &c->mac_cnt,
                     &c->band_cnt, &c->band_off, &c->l_nrec, &c->l_head_s, &c->l_head_l,
-                    &c->arena_s, &c->arena_l, &c->next_s, &c->next_l, &c->arena_cur};
+                    &c->arena_s, &c->arena_l, &c->next_s, &c->next_l, &c->arena_cur,
+                    &c->m_ehi, &c->m_elo, &c->m_shi, &c->m_slo};
   for (DevBuf *b : bufs) release(*b);
   if (c->pinned) cudaFreeHost(c->pinned);
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -601,6 +602,28 @@ int afd_autotune_launch(afd_ctx *c, float *acc4, int reps, float *ms_out) {
   cudaEventDestroy(e1);
   c->force_warps = bw;
   c->force_chunk = bc;
+  return st;
+}
+
+int afd_calc_force_materialized(afd_ctx *c, float *acc4, float *ms_out) {
+  if (!c || (c->n > 0 && !acc4)) return AFD_ERR_ARG;
+  if (!c->have_lists) return c->have_tree ? AFD_ERR_NO_SAVED_LIST : AFD_ERR_NO_TREE;
+  if (c->cfg.multipole) return AFD_ERR_ARG;  // monopole lists only
+  DeviceGuard g(c->device);
+  cudaEvent_t e[3];
+  for (auto &ev : e)
+    if (cudaEventCreate(&ev) != cudaSuccess) return AFD_ERR_CUDA;
+  cudaEventRecord(e[0], c->stream);
+  int st = launch_materialize(c);
+  cudaEventRecord(e[1], c->stream);
+  if (st == AFD_OK) st = launch_force_materialized(c, acc4);
+  cudaEventRecord(e[2], c->stream);
+  if (st == AFD_OK && cudaEventSynchronize(e[2]) != cudaSuccess) st = AFD_ERR_CUDA;
+  if (st == AFD_OK && ms_out) {
+    cudaEventElapsedTime(&ms_out[0], e[0], e[1]);
+    cudaEventElapsedTime(&ms_out[1], e[1], e[2]);
+  }
+  for (auto &ev : e) cudaEventDestroy(ev);
   return st;
 }
 

@@ -50,7 +50,9 @@ struct ForceArgs {
   unsigned long long *queue;  // work counter of the persistent variant (zeroed per launch)
   const uint2 *u_info;
   const uint32_t *g_first, *g_count, *g_self, *g_cell;
-  const float4 *jhi, *jlo;  // particles, Morton order
+  const float4 *jhi, *jlo;  // j-particles, Morton order (or materialised lists)
+  const float4 *ihi, *ilo;  // i-particles, Morton order
+  const float4 *ohi, *olo;  // cells, for the group origin
   const float4 *shi, *slo;  // cells
   const float4 *sq0, *sq1;  // cell quadrupoles
   const float4 *nodef;      // cell walk data (s^2 in .w)
@@ -342,7 +344,9 @@ __device__ __forceinline__ void load_idx(uint32_t *j, const uint32_t *idx, uint6
 #pragma unroll
   for (int r = 0; r < CH / 32; r++) {
     const uint64_t k = base + lane + 32 * r;
-    j[r] = k < o1 ? idx[k] : 0u;
+    // idx null: the j-data are materialised in list order (the non-indirect
+    // ablation), so the entry's own position is its index
+    j[r] = k < o1 ? (idx ? idx[k] : (uint32_t)k) : 0u;
     if (!AFD_IN(j[r], jbound, "force list entry")) j[r] = 0u;
   }
 }
@@ -510,10 +514,10 @@ __device__ __forceinline__ void run_unit(WarpStage<QUAD, CH> &st, const ForceArg
                                          const Lane<IPT> &ln, Sums *sm, int64_t self_at) {
   run_list<GUARD, QUAD, FAR, S, IPT, CH>(st, ln, sm, a.epj, a.off_e[g], a.off_e[g + 1], a.jhi,
                                          a.jlo, nullptr, nullptr, nullptr, false, a.eps2,
-                                         self_at, a.n_epj, a.n);
+                                         self_at, a.n_epj, a.epj ? a.n : a.n_epj);
   run_list<GUARD, QUAD, FAR, S, IPT, CH>(st, ln, sm, a.spj, a.off_s[g], a.off_s[g + 1], a.shi,
                                          a.slo, a.sq0, a.sq1, a.nodef, QUAD, a.eps2, -1, a.n_spj,
-                                         a.n_cells);
+                                         a.spj ? a.n_cells : a.n_spj);
 }
 
 // One work unit with IPT particles per lane and S j-streams: set up the
@@ -529,7 +533,7 @@ __device__ __forceinline__ void unit_body(const ForceArgs &a, WarpStage<QUAD, CH
   // origin of the relative coordinates: the group cell's centre of mass
   uint32_t gcell = a.g_cell[g];
   if (!AFD_IN(gcell, a.n_cells, "force group cell")) gcell = 0u;
-  const float4 ch = a.shi[gcell], cl = a.slo[gcell];
+  const float4 ch = a.ohi[gcell], cl = a.olo[gcell];
   if (lane == 0) {
     st.ch = ch;
     st.cl = cl;
@@ -542,7 +546,7 @@ __device__ __forceinline__ void unit_body(const ForceArgs &a, WarpStage<QUAD, CH
     active[q] = il[q] < gc && AFD_IN(gf + il[q], a.n, "force i-particle");
     float xi = 0.f, yi = 0.f, zi = 0.f;
     if (active[q]) {
-      const float4 h = a.jhi[gf + il[q]], l = a.jlo[gf + il[q]];
+      const float4 h = a.ihi[gf + il[q]], l = a.ilo[gf + il[q]];
       xi = (h.x - ch.x) + (l.x - cl.x);
       yi = (h.y - ch.y) + (l.y - cl.y);
       zi = (h.z - ch.z) + (l.z - cl.z);
@@ -644,7 +648,49 @@ int launch_k_force(const ForceArgs &a, unsigned nb, int warps, cudaStream_t s) {
 
 }  // namespace
 
-int launch_force(afd_ctx *c, float *acc4) {
+namespace {
+
+// Non-indirect ablation: copy every list entry's j-data into list order.
+__global__ void k_materialize(uint64_t n, const uint32_t *__restrict__ idx,
+                              const float4 *__restrict__ hi, const float4 *__restrict__ lo,
+                              float4 *__restrict__ ohi, float4 *__restrict__ olo) {
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t j = idx[k];
+    ohi[k] = hi[j];
+    olo[k] = lo[j];
+  }
+}
+
+}  // namespace
+
+int launch_force_impl(afd_ctx *c, float *acc4, bool materialized);
+
+int launch_force(afd_ctx *c, float *acc4) { return launch_force_impl(c, acc4, false); }
+
+int launch_materialize(afd_ctx *c) {
+  const size_t ne = (size_t)c->n_epj, ns = (size_t)c->n_spj;
+  for (afd::DevBuf *b : {&c->m_ehi, &c->m_elo})
+    if (reserve(*b, sizeof(float4) * ne) != AFD_OK) return AFD_ERR_OOM;
+  for (afd::DevBuf *b : {&c->m_shi, &c->m_slo})
+    if (reserve(*b, sizeof(float4) * ns) != AFD_OK) return AFD_ERR_OOM;
+  if (ne)
+    k_materialize<<<152 * 16, 256, 0, c->stream>>>(ne, ptr<uint32_t>(c->epj), ptr<float4>(c->jhi),
+                                                   ptr<float4>(c->jlo), ptr<float4>(c->m_ehi),
+                                                   ptr<float4>(c->m_elo));
+  if (ns)
+    k_materialize<<<152 * 16, 256, 0, c->stream>>>(ns, ptr<uint32_t>(c->spj), ptr<float4>(c->s_hi),
+                                                   ptr<float4>(c->s_lo), ptr<float4>(c->m_shi),
+                                                   ptr<float4>(c->m_slo));
+  c->launches += (ne ? 1 : 0) + (ns ? 1 : 0);
+  return cudaGetLastError() == cudaSuccess ? AFD_OK : AFD_ERR_CUDA;
+}
+
+int launch_force_materialized(afd_ctx *c, float *acc4) {
+  return launch_force_impl(c, acc4, true);
+}
+
+int launch_force_impl(afd_ctx *c, float *acc4, bool materialized) {
   if (c->n == 0 || c->n_units == 0) return AFD_OK;
   ForceArgs a;
   a.n_units = c->n_units;
@@ -653,17 +699,23 @@ int launch_force(afd_ctx *c, float *acc4) {
   a.g_count = ptr<uint32_t>(c->g_count);
   a.g_self = ptr<uint32_t>(c->g_self);
   a.g_cell = ptr<uint32_t>(c->g_cell);
-  a.jhi = ptr<float4>(c->jhi);
-  a.jlo = ptr<float4>(c->jlo);
-  a.shi = ptr<float4>(c->s_hi);
-  a.slo = ptr<float4>(c->s_lo);
+  a.jhi = a.ihi = ptr<float4>(c->jhi);
+  a.jlo = a.ilo = ptr<float4>(c->jlo);
+  a.shi = a.ohi = ptr<float4>(c->s_hi);
+  a.slo = a.olo = ptr<float4>(c->s_lo);
+  if (materialized) {  // j-data in list order, no index indirection
+    a.jhi = ptr<float4>(c->m_ehi);
+    a.jlo = ptr<float4>(c->m_elo);
+    a.shi = ptr<float4>(c->m_shi);
+    a.slo = ptr<float4>(c->m_slo);
+  }
   a.sq0 = ptr<float4>(c->s_q0);
   a.sq1 = ptr<float4>(c->s_q1);
   a.nodef = ptr<float4>(c->node_f);
   a.off_e = ptr<uint64_t>(c->epj_off);
   a.off_s = ptr<uint64_t>(c->spj_off);
-  a.epj = ptr<uint32_t>(c->epj);
-  a.spj = ptr<uint32_t>(c->spj);
+  a.epj = materialized ? nullptr : ptr<uint32_t>(c->epj);
+  a.spj = materialized ? nullptr : ptr<uint32_t>(c->spj);
   a.perm = ptr<uint32_t>(c->perm);
   const float e = (float)c->cfg.eps;
   a.eps2 = e * e;

@@ -106,6 +106,8 @@ struct afd_ctx {
 
   // lists (CSR)
   afd::DevBuf l_cnt_e, l_cnt_s, epj_off, spj_off, epj, spj;
+  // the non-indirect ablation: list entries' j-data copied into list order
+  afd::DevBuf m_ehi, m_elo, m_shi, m_slo;
   // walk record arena: per group leaf-record count and chunk-chain heads;
   // chunks of cell ids / leaf records, chain links, cursors (capacity in chunks)
   afd::DevBuf l_nrec, l_head_s, l_head_l;
@@ -192,6 +194,8 @@ int launch_amag(afd_ctx *c, const float *acc4);  // reference |a| from a force r
 
 // ---- force (afd_force.cu) ----
 int launch_force(afd_ctx *c, float *acc4);
+int launch_materialize(afd_ctx *c);                    // j-data of every list entry, list order
+int launch_force_materialized(afd_ctx *c, float *acc4);  // force kernel reading those copies
 
 // ---- per-system statistics (afd_walk.cu) ----
 // inter[s] = sum over system s's groups of n_i (n_epj + n_spj); entries[s] =

@@ -547,3 +547,21 @@ def test_force_launch_shapes(env):
     with pytest.raises(afd.AfdError):
         afd.afd_set_launch(g.ctx, 3, 32)
     g.close()
+
+
+def test_materialized_lists_ablation_is_bit_identical(env):
+    """The non-indirect ablation (j-data copied into list order, read without
+    indices) computes the same forces as the indirect kernel, bit for bit."""
+    torch, afd, orc = env
+    p = ics.plummer(20000 + 11, 71)
+    kw = dict(n_grp=64, theta=0.5, eps=1.0 / 256)
+    g, a_ind, (x, y, z, m, acc) = run_gpu(env, p, **kw)
+    acc.fill_(float("nan"))
+    t_copy, t_force = afd.afd_calc_force_materialized(g.ctx, acc)
+    assert t_copy > 0 and t_force > 0
+    assert np.array_equal(acc.cpu().numpy().astype(np.float64), a_ind)
+    g.close()
+    gq, _, (_, _, _, _, accq) = run_gpu(env, p, quad=True, **kw)
+    with pytest.raises(afd.AfdError):
+        afd.afd_calc_force_materialized(gq.ctx, accq)
+    gq.close()
