@@ -100,6 +100,9 @@ def lib():
                                      ctypes.c_int64, _I64]
         L.afo_band_pairs.restype = ctypes.c_int64
         L.afo_relist.argtypes = [ctypes.c_void_p]
+        L.afo_let_export.argtypes = [ctypes.c_void_p, _D, ctypes.c_double, ctypes.c_int64, _D, _D,
+                                     _D, _D, _I32]
+        L.afo_let_export.restype = ctypes.c_int64
     return _lib
 
 
@@ -266,6 +269,19 @@ class Tree:
         x, y, z, m = map(_f64, (x, y, z, m))
         if lib().afo_update(self._h, _p(x, _D), _p(y, _D), _p(z, _D), _p(m, _D)) != 0:
             raise ValueError("non-finite particle data")
+
+    def let_export(self, box, theta=None):
+        """LET of reading R16 for a remote domain box (min xyz, max xyz):
+        (x, y, z, m, kind) with kind 0 for particles, 1 for superparticles."""
+        th = self._args["theta"] if theta is None else theta
+        b = _f64(box)
+        n = int(lib().afo_let_export(self._h, _p(b, _D), float(th), 0, None, None, None, None,
+                                     None))
+        out = [np.zeros(max(n, 1)) for _ in range(4)]
+        kind = np.zeros(max(n, 1), np.int32)
+        lib().afo_let_export(self._h, _p(b, _D), float(th), n, *(_p(o, _D) for o in out),
+                             _p(kind, _I32))
+        return (*(o[:n] for o in out), kind[:n])
 
     def relist(self):
         """Lists made again on the current topology and moments (a list

@@ -90,6 +90,13 @@
  *     superparticle term (R1, plus R10 with quadrupoles), a_i^exact the
  *     direct sum over the cell's particles and A_i particle i's reference
  *     acceleration magnitude; clamped to [-40, 8].
+ *  R16 local essential tree (Section 3 and Section 4.3: the global tree is
+ *     built over local particles and the superparticles and particles
+ *     imported from other domains): the LET of a tree for a remote domain
+ *     box B is what a walk from the root under R8, with B as the group box,
+ *     would put on a list: each accepted cell as one superparticle (its
+ *     COM and monopole), each opened leaf as its particles; in depth-first
+ *     order, children in Morton order.
  */
 #include <float.h>
 #include <math.h>
@@ -798,6 +805,56 @@ double afo_pair_label(const afo_tree *t, int64_t g, int64_t c) {
   return afo_mac_label(ni, t->xs + f, t->ys + f, t->zs + f, ai, t->count[c], t->xs + fc,
                        t->ys + fc, t->zs + fc, t->ms + fc, t->mass[c], &t->com[c * 3],
                        &t->qmom[c * 6], t->eps, t->quad);
+}
+
+/* LET of reading R16 for the domain box (min x y z, max x y z): writes up
+ * to cap elements (x, y, z, m, kind: 0 particle, 1 superparticle) and
+ * returns their count. */
+int64_t afo_let_export(const afo_tree *t, const double box[6], double theta, int64_t cap,
+                       double *x, double *y, double *z, double *m, int32_t *kind) {
+  float bmin[3], bmax[3];
+  for (int k = 0; k < 3; k++) {
+    bmin[k] = (float)box[k];
+    bmax[k] = (float)box[3 + k];
+  }
+  const float theta2 = (float)theta * (float)theta;
+  const float L = (float)t->root[3];
+  int64_t ne = 0;
+  int64_t *stack = malloc(sizeof(int64_t) * (size_t)(8 * t->n_cells + 8));
+  int64_t sp = 0;
+  if (t->n_cells > 0) stack[sp++] = 0;
+  while (sp > 0) {
+    const int64_t c = stack[--sp];
+    const float s = ldexpf(L, -t->level[c]);
+    float com[3];
+    for (int k = 0; k < 3; k++) com[k] = (float)t->com[c * 3 + k];
+    if (mac_accept(bmin, bmax, com, s * s, theta2)) {
+      if (ne < cap) {
+        x[ne] = t->com[c * 3];
+        y[ne] = t->com[c * 3 + 1];
+        z[ne] = t->com[c * 3 + 2];
+        m[ne] = t->mass[c];
+        kind[ne] = 1;
+      }
+      ne++;
+    } else if (is_leaf(t, c)) {
+      for (int64_t k = t->first[c]; k < t->first[c] + t->count[c]; k++) {
+        if (ne < cap) {
+          x[ne] = t->xs[k];
+          y[ne] = t->ys[k];
+          z[ne] = t->zs[k];
+          m[ne] = t->ms[k];
+          kind[ne] = 0;
+        }
+        ne++;
+      }
+    } else {
+      for (int o = 7; o >= 0; o--)
+        if (t->child[c * 8 + o] >= 0) stack[sp++] = t->child[c * 8 + o];
+    }
+  }
+  free(stack);
+  return ne;
 }
 
 void afo_pair_features_batch(const afo_tree *t, int64_t n, const int64_t *pairs, float *f) {
