@@ -606,6 +606,43 @@ def sweep(args, wl):
                       "materialized_bytes": 32 * (st["n_epj"] + st["n_spj"])}), flush=True)
     g.close()
 
+    # local essential tree: the domain x >= 0 exports to the domain x < 0; a
+    # tree over x < 0 plus the imports gives the forces there
+    A = p.x < 0.0
+    B = ~A
+    box = [p.x[A].min(), p.y[A].min(), p.z[A].min(), p.x[A].max(), p.y[A].max(), p.z[A].max()]
+    cfg = afd.Config(eps=wl["eps"], theta=wl["theta"], n_leaf=16, n_grp=wl["n_grp"])
+    gb = afd.Gravity(cfg, 0, stream)
+    afd.afd_tree_build(gb.ctx, T(p.x[B]), T(p.y[B]), T(p.z[B]), T(p.m[B]))
+    t_let = []
+    for rep in range(4):
+        e0 = ev()
+        lx, ly, lz, lm, lk = afd.afd_let_export(gb.ctx, box, wl["theta"])
+        e1 = ev()
+        e1.synchronize()
+        if rep:
+            t_let.append(e0.elapsed_time(e1))
+    gb.close()
+    na = int(A.sum())
+    ga = afd.Gravity(cfg, 0, stream)
+    afd.afd_set_launch(ga.ctx, 2, 32)
+    XA = [torch.cat([T(getattr(p, k)[A]), v]) for k, v in zip("xyzm", (lx, ly, lz, lm))]
+    acc_a = torch.empty(len(XA[0]), 4, dtype=torch.float32, device=dev)
+    ga.force_all(*XA, acc_a, afd.AFD_MAKE_LIST)
+    ia = np.nonzero(A)[0]
+    sel = np.isin(tg, ia)
+    pos = np.searchsorted(ia, tg[sel])
+    a = acc_a[torch.tensor(pos, device=dev)].double().cpu().numpy()
+    exa = ex[sel]
+    err_split = float(np.sqrt(np.mean(((a[:, :3] - exa[:, :3]) ** 2).sum(1)
+                                      / (exa[:, :3] ** 2).sum(1))))
+    ga.close()
+    print(json.dumps({"sweep": "let_split", "workload": wl["name"], "theta": wl["theta"],
+                      "exporting_particles": int(B.sum()), "exported_elements": int(len(lm)),
+                      "exported_superparticles": int(lk.sum().item()),
+                      "export_ms": float(np.median(t_let)), "receiving_particles": na,
+                      "rms_rel_force_error_split": err_split}), flush=True)
+
     R_list = (1, 2, 4, 8, 16)
     for R in R_list:
         cfg = afd.Config(eps=wl["eps"], theta=wl["theta"], n_leaf=16, n_grp=wl["n_grp"],

@@ -227,6 +227,23 @@ int afd_autotune_launch(afd_ctx *ctx, float *acc4, int reps, float *ms_out);
  * copy and the force kernel, CUDA-event milliseconds. Synchronises. */
 int afd_calc_force_materialized(afd_ctx *ctx, float *acc4, float *ms_out);
 
+/* Local essential tree of the current tree for a remote domain (Section 3;
+ * Section 4.3: the global tree is built over the local particles and the
+ * superparticles and particles imported from other domains). box (host, 6
+ * doubles: min x y z, max x y z) is the remote domain; the export is what
+ * the interaction-list walk with that box as the group box and opening
+ * angle theta puts on a list: each accepted cell as one superparticle (its
+ * FP64 COM and monopole), each opened leaf as its particles, in depth-first
+ * order (children in Morton order). The first min(total, cap) elements go to
+ * x, y, z, m (device doubles, cap each) and kind (device u32, 0 particle,
+ * 1 superparticle; may be NULL); *n_out (host) = total. A receiving
+ * context builds its tree over its own particles followed by the imported
+ * elements (afd_tree_build) and keeps the forces of its own particles.
+ * Monopole superparticles; one system per context (AFD_ERR_ARG otherwise);
+ * needs a tree. Synchronises. */
+int afd_let_export(afd_ctx *ctx, const double *box, double theta, int64_t cap, double *x,
+                   double *y, double *z, double *m, uint32_t *kind, int64_t *n_out);
+
 /* Wait for the context's stream and return the device status word. */
 int afd_sync(afd_ctx *ctx);
 

@@ -98,6 +98,7 @@ def lib():
                                 _VP], ctypes.c_int),
         "afd_set_launch": ([_VP, ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "afd_calc_force_materialized": ([_VP, _VP, _VP], ctypes.c_int),
+        "afd_let_export": ([_VP, _VP, _D, _I64, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
         "afd_get_launch": ([_VP, _VP, _VP], ctypes.c_int),
         "afd_autotune_launch": ([_VP, _VP, ctypes.c_int, _VP], ctypes.c_int),
         "afd_mac_set": ([_VP, _VP, _D, _D, _D], ctypes.c_int),
@@ -340,6 +341,26 @@ def afd_calc_force_materialized(ctx, acc4):
     _check(lib().afd_calc_force_materialized(ctx, _dptr(acc4, torch.float32, what="acc4"),
                                              _VP(ms.ctypes.data)), "afd_calc_force_materialized")
     return float(ms[0]), float(ms[1])
+
+
+def afd_let_export(ctx, box, theta, cap=None):
+    """Local essential tree for a remote domain box: (x, y, z, m, kind)
+    device tensors (float64, float64, float64, float64, int32 viewed u32)."""
+    import torch
+    b = np.ascontiguousarray(box, dtype=np.float64)
+    n = ctypes.c_int64(0)
+    if cap is None:
+        _check(lib().afd_let_export(ctx, _VP(b.ctypes.data), float(theta), 0, None, None, None,
+                                    None, None, ctypes.byref(n)), "afd_let_export")
+        cap = int(n.value)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = [torch.empty(max(cap, 1), dtype=torch.float64, device=dev) for _ in range(4)]
+    kind = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    _check(lib().afd_let_export(ctx, _VP(b.ctypes.data), float(theta), int(cap),
+                                *(_VP(o.data_ptr()) for o in out), _VP(kind.data_ptr()),
+                                ctypes.byref(n)), "afd_let_export")
+    k = min(int(n.value), cap)
+    return (*(o[:k] for o in out), kind[:k])
 
 
 def afd_set_launch(ctx, warps_per_block, chunk):

@@ -265,7 +265,8 @@ void afd_destroy(afd_ctx *c) {
                     &c->mac_w, &c->amag, &c->amag_s, &c->g_amin, &c->mac_cnt,
                     &c->band_cnt, &c->band_off, &c->l_nrec, &c->l_head_s, &c->l_head_l,
                     &c->arena_s, &c->arena_l, &c->next_s, &c->next_l, &c->arena_cur,
-                    &c->m_ehi, &c->m_elo, &c->m_shi, &c->m_slo};
+                    &c->m_ehi, &c->m_elo, &c->m_shi, &c->m_slo, &c->let_mark,
+                    &c->let_cnt, &c->let_off};
   for (DevBuf *b : bufs) release(*b);
   if (c->pinned) cudaFreeHost(c->pinned);
   if (c->ev0) cudaEventDestroy(c->ev0);

@@ -108,6 +108,8 @@ struct afd_ctx {
   afd::DevBuf l_cnt_e, l_cnt_s, epj_off, spj_off, epj, spj;
   // the non-indirect ablation: list entries' j-data copied into list order
   afd::DevBuf m_ehi, m_elo, m_shi, m_slo;
+  // local essential tree export: per-cell marks, element counts and offsets
+  afd::DevBuf let_mark, let_cnt, let_off;
   // walk record arena: per group leaf-record count and chunk-chain heads;
   // chunks of cell ids / leaf records, chain links, cursors (capacity in chunks)
   afd::DevBuf l_nrec, l_head_s, l_head_l;
