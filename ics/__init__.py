@@ -187,6 +187,15 @@ def make_batch(n_systems: int = 32, seed_base: int = 100):
     return cat, off, qs
 
 
+def plummer_search_radii(p: Particles, n_nb: float) -> np.ndarray:
+    """Search radii for a Plummer sphere of scale radius 1: h_i such that a
+    sphere of radius h_i around particle i holds n_nb particles on average
+    under the analytic number density N (3 / 4 pi) (1 + r^2)^(-5/2), i.e.
+    h_i = (n_nb / N)^(1/3) (1 + r_i^2)^(5/6). Input generation only."""
+    r2 = p.x * p.x + p.y * p.y + p.z * p.z
+    return (n_nb / p.n) ** (1.0 / 3.0) * (1.0 + r2) ** (5.0 / 6.0)
+
+
 def make(model: str, n: int, seed: int) -> Particles:
     if model == "plummer":
         return plummer(n, seed)

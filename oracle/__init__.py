@@ -103,6 +103,14 @@ def lib():
         L.afo_let_export.argtypes = [ctypes.c_void_p, _D, ctypes.c_double, ctypes.c_int64, _D, _D,
                                      _D, _D, _I32]
         L.afo_let_export.restype = ctypes.c_int64
+        L.afo_nbr_lists.argtypes = [ctypes.c_void_p, _D, ctypes.c_double]
+        L.afo_nbr_lists.restype = ctypes.c_int
+        L.afo_sph_density.argtypes = [ctypes.c_void_p, _D, _D, _D]
+        L.afo_sph_density_direct.argtypes = [ctypes.c_int64, _D, _D, _D, _D, _D,
+                                             ctypes.c_int64, _I64, _D, _D]
+        L.afo_get_nbr.argtypes = [ctypes.c_void_p, _I64, _I32, _F32, _F32]
+        L.afo_nbr_total.argtypes = [ctypes.c_void_p]
+        L.afo_nbr_total.restype = ctypes.c_int64
     return _lib
 
 
@@ -128,6 +136,19 @@ def direct_sum(x, y, z, m, eps, targets=None):
     lib().afo_direct_sum(n, _p(x, _D), _p(y, _D), _p(z, _D), _p(m, _D), float(eps),
                          tgt.shape[0], _p(tgt, _I64), *(_p(o, _D) for o in out))
     return tuple(out)
+
+
+def density_direct(x, y, z, m, h, targets=None):
+    """Density and smooth neighbour number of reading R18 summed over every
+    particle (the definition, no tree) for the targets (all by default)."""
+    x, y, z, m, h = map(_f64, (x, y, z, m, h))
+    n = x.shape[0]
+    tgt = np.arange(n, dtype=np.int64) if targets is None else np.ascontiguousarray(
+        targets, dtype=np.int64)
+    rho, nnb = np.zeros(tgt.shape[0]), np.zeros(tgt.shape[0])
+    lib().afo_sph_density_direct(n, _p(x, _D), _p(y, _D), _p(z, _D), _p(m, _D), _p(h, _D),
+                                 tgt.shape[0], _p(tgt, _I64), _p(rho, _D), _p(nnb, _D))
+    return rho, nnb
 
 
 def root_cell(x, y, z):
@@ -282,6 +303,39 @@ class Tree:
         lib().afo_let_export(self._h, _p(b, _D), float(th), n, *(_p(o, _D) for o in out),
                              _p(kind, _I32))
         return (*(o[:n] for o in out), kind[:n])
+
+    def neighbour_lists(self, h, skin=0.0):
+        """Neighbour lists of reading R17 (Section 2, short-range walk) for
+        search radii ``h`` (caller order) and margin ``skin``; they replace
+        earlier ones and survive ``update``. Returns (off, idx): CSR lists of
+        Morton positions per group."""
+        self._nbr_h = _f64(h)
+        if lib().afo_nbr_lists(self._h, _p(self._nbr_h, _D), float(skin)) != 0:
+            raise ValueError("search radii must be finite and positive, skin finite and >= 0")
+        off, idx, _, _ = self.neighbour_data()
+        return off, idx
+
+    def neighbour_data(self):
+        """(off, idx, cell tight boxes (n_cells, 6), group search boxes
+        (n_groups, 6)); boxes FP32, min x y z then max x y z."""
+        s = self.sizes()
+        total = int(lib().afo_nbr_total(self._h))
+        if total < 0:
+            raise RuntimeError("no neighbour lists")
+        off = np.zeros(s["n_groups"] + 1, np.int64)
+        idx = np.zeros(max(total, 1), np.int32)
+        tb = np.zeros((max(s["n_cells"], 1), 6), np.float32)
+        sb = np.zeros((max(s["n_groups"], 1), 6), np.float32)
+        lib().afo_get_nbr(self._h, _p(off, _I64), _p(idx, _I32), _p(tb, _F32), _p(sb, _F32))
+        return off, idx[:total], tb[:s["n_cells"]], sb[:s["n_groups"]]
+
+    def density(self, h):
+        """Density and smooth neighbour number of reading R18 over the
+        neighbour lists (current positions), caller order."""
+        hh = _f64(h)
+        rho, nnb = np.zeros(self.n), np.zeros(self.n)
+        lib().afo_sph_density(self._h, _p(hh, _D), _p(rho, _D), _p(nnb, _D))
+        return rho, nnb
 
     def relist(self):
         """Lists made again on the current topology and moments (a list

@@ -97,6 +97,35 @@
  *     would put on a list: each accepted cell as one superparticle (its
  *     COM and monopole), each opened leaf as its particles; in depth-first
  *     order, children in Morton order.
+ *
+ * Short-range interactions (Section 2: the same walk with a cell-opening
+ * criterion other than the opening angle; Section 4.2: their lists can be
+ * kept over steps since particles move a small fraction of their spacing):
+ *  R17 neighbour lists (gather form). Every particle i carries a search
+ *     radius h_i > 0; the lists are made with a margin skin >= 0. The
+ *     search box of group g is, per axis, [min_i (x_i - (h_i + skin)),
+ *     max_i (x_i + (h_i + skin))] over its particles, each bound computed
+ *     in FP64 (round to nearest) and then rounded outward to FP32 (the lower
+ *     bound down, the upper bound up). The tight box of a cell is the
+ *     min / max of its particles' coordinates, rounded outward to FP32 the
+ *     same way. A cell whose tight box meets the search box (closed
+ *     intervals on every axis, compared in FP32) is opened when internal
+ *     and listed when a leaf; any other cell is dropped with its subtree.
+ *     The list of a group is the particles of its listed leaves, depth
+ *     first with children in Morton order, which is ascending Morton
+ *     position. Every j within h_i + skin of a particle i of the group is
+ *     on the list (up to the FP64 rounding of the bounds).
+ *  R18 density over a neighbour list (gather form, the usual first pass of
+ *     an SPH step): rho_i = sum_j m_j W(|x_j - x_i|, h_i), the particle
+ *     itself included, with the M4 cubic spline of support radius h in
+ *     three dimensions, W(r, h) = 8 / (pi h^3) w(r / h),
+ *       w(q) = 1 - 6 q^2 + 6 q^3   for 0 <= q <= 1/2,
+ *       w(q) = 2 (1 - q)^3         for 1/2 < q < 1,
+ *       w(q) = 0                   for q >= 1,
+ *     normalised so that its integral over space is 1. Also the smooth
+ *     neighbour number nnb_i = (4 pi / 3) h_i^3 sum_j W(|x_j - x_i|, h_i)
+ *     = (32 / 3) sum_j w(|x_j - x_i| / h_i), which a uniform medium of
+ *     number density n takes to (4 pi / 3) h_i^3 n.
  */
 #include <float.h>
 #include <math.h>
@@ -289,6 +318,11 @@ typedef struct afo_tree {
   float mac_lo2, mac_hi2, mac_tau;
   float *amag_s; /* reference |a| per particle, Morton order */
   float *g_amin; /* smallest of them per group */
+  /* neighbour lists (R17): per-cell tight boxes and per-group search boxes
+   * (FP32, min x y z then max x y z), CSR lists of Morton positions */
+  float *c_tbox, *g_sbox;
+  int64_t *nbr_off;
+  int32_t *nbr;
 } afo_tree;
 
 static void *xcalloc(size_t count, size_t size) {
@@ -303,6 +337,7 @@ void afo_free(afo_tree *t) {
   free(t->g_first); free(t->g_count); free(t->g_cell); free(t->g_box); free(t->g_self);
   free(t->epj_off); free(t->spj_off); free(t->epj); free(t->spj);
   free(t->amag_s); free(t->g_amin);
+  free(t->c_tbox); free(t->g_sbox); free(t->nbr_off); free(t->nbr);
   free(t);
 }
 
@@ -1233,6 +1268,164 @@ void afo_get_lists(const afo_tree *t, int64_t *epj_off, int32_t *epj, int64_t *s
     memcpy(epj, t->epj, sizeof(int32_t) * (size_t)t->epj_off[ng]);
     memcpy(spj, t->spj, sizeof(int32_t) * (size_t)t->spj_off[ng]);
   }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Short-range neighbour walk and density (Section 2, Section 4.2;          */
+/* readings R17, R18).                                                      */
+/* ------------------------------------------------------------------------ */
+
+/* FP64 to FP32 rounded toward -inf / +inf. */
+static float f32_down(double v) {
+  float f = (float)v;
+  if ((double)f > v) f = nextafterf(f, -INFINITY);
+  return f;
+}
+
+static float f32_up(double v) {
+  float f = (float)v;
+  if ((double)f < v) f = nextafterf(f, INFINITY);
+  return f;
+}
+
+static int boxes_meet(const float *a, const float *b) {
+  for (int k = 0; k < 3; k++)
+    if (a[k] > b[3 + k] || a[3 + k] < b[k]) return 0;
+  return 1;
+}
+
+/* The neighbour lists of R17 for search radii h (caller order) and margin
+ * skin, replacing any earlier ones. Returns 0, or -1 when a radius is not
+ * finite or not positive, or skin is not finite or negative. */
+int afo_nbr_lists(afo_tree *t, const double *h, double skin) {
+  if (!isfinite(skin) || skin < 0.0) return -1;
+  for (int64_t i = 0; i < t->n; i++)
+    if (!isfinite(h[i]) || !(h[i] > 0.0)) return -1;
+  free(t->c_tbox); free(t->g_sbox); free(t->nbr_off); free(t->nbr);
+  t->c_tbox = xcalloc(t->n_cells * 6, sizeof(float));
+  t->g_sbox = xcalloc(t->n_groups * 6, sizeof(float));
+  const double *pos[3] = {t->xs, t->ys, t->zs};
+  for (int64_t c = 0; c < t->n_cells; c++) {
+    double lo[3], hi[3];
+    const int64_t f = t->first[c];
+    for (int k = 0; k < 3; k++) lo[k] = hi[k] = pos[k][f];
+    for (int64_t i = f + 1; i < f + t->count[c]; i++)
+      for (int k = 0; k < 3; k++) {
+        if (pos[k][i] < lo[k]) lo[k] = pos[k][i];
+        if (pos[k][i] > hi[k]) hi[k] = pos[k][i];
+      }
+    for (int k = 0; k < 3; k++) {
+      t->c_tbox[c * 6 + k] = f32_down(lo[k]);
+      t->c_tbox[c * 6 + 3 + k] = f32_up(hi[k]);
+    }
+  }
+  for (int64_t g = 0; g < t->n_groups; g++) {
+    double lo[3], hi[3];
+    for (int64_t i = t->g_first[g]; i < t->g_first[g] + t->g_count[g]; i++) {
+      const double r = h[t->perm[i]] + skin;
+      for (int k = 0; k < 3; k++) {
+        const double a = pos[k][i] - r, b = pos[k][i] + r;
+        if (i == t->g_first[g] || a < lo[k]) lo[k] = a;
+        if (i == t->g_first[g] || b > hi[k]) hi[k] = b;
+      }
+    }
+    for (int k = 0; k < 3; k++) {
+      t->g_sbox[g * 6 + k] = f32_down(lo[k]);
+      t->g_sbox[g * 6 + 3 + k] = f32_up(hi[k]);
+    }
+  }
+  /* the walk, once to count and once to write */
+  int64_t *stack = malloc(sizeof(int64_t) * (size_t)(8 * (AFO_LEVELS + 2)));
+  t->nbr_off = xcalloc(t->n_groups + 1, sizeof(int64_t));
+  for (int pass = 0; pass < 2; pass++) {
+    if (pass == 1) t->nbr = xcalloc(t->nbr_off[t->n_groups], sizeof(int32_t));
+    for (int64_t g = 0; g < t->n_groups; g++) {
+      const float *sb = &t->g_sbox[g * 6];
+      int64_t ne = 0;
+      int64_t sp = 0;
+      if (t->n_cells > 0) stack[sp++] = 0;
+      while (sp > 0) {
+        const int64_t c = stack[--sp];
+        if (!boxes_meet(&t->c_tbox[c * 6], sb)) continue;
+        if (is_leaf(t, c)) {
+          for (int64_t k = t->first[c]; k < t->first[c] + t->count[c]; k++) {
+            if (pass == 1) t->nbr[t->nbr_off[g] + ne] = (int32_t)k;
+            ne++;
+          }
+        } else {
+          for (int o = 7; o >= 0; o--)
+            if (t->child[c * 8 + o] >= 0) stack[sp++] = t->child[c * 8 + o];
+        }
+      }
+      if (pass == 0) t->nbr_off[g + 1] = t->nbr_off[g] + ne;
+    }
+  }
+  free(stack);
+  return 0;
+}
+
+/* w(q) of R18. */
+static double spline_w(double q) {
+  if (q <= 0.5) return 1.0 - 6.0 * q * q + 6.0 * q * q * q;
+  if (q < 1.0) {
+    const double u = 1.0 - q;
+    return 2.0 * u * u * u;
+  }
+  return 0.0;
+}
+
+/* Density and smooth neighbour number of R18 over the neighbour lists
+ * (current positions: after afo_update the lists are kept), caller order. */
+void afo_sph_density(const afo_tree *t, const double *h, double *rho, double *nnb) {
+  const double pi = 3.14159265358979323846;
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t g = 0; g < t->n_groups; g++) {
+    for (int64_t i = t->g_first[g]; i < t->g_first[g] + t->g_count[g]; i++) {
+      const double hi = h[t->perm[i]];
+      double sm = 0.0, sw = 0.0;
+      for (int64_t e = t->nbr_off[g]; e < t->nbr_off[g + 1]; e++) {
+        const int64_t j = t->nbr[e];
+        const double dx = t->xs[j] - t->xs[i], dy = t->ys[j] - t->ys[i],
+                     dz = t->zs[j] - t->zs[i];
+        const double w = spline_w(sqrt(dx * dx + dy * dy + dz * dz) / hi);
+        sm += t->ms[j] * w;
+        sw += w;
+      }
+      rho[t->perm[i]] = 8.0 / (pi * hi * hi * hi) * sm;
+      nnb[t->perm[i]] = 32.0 / 3.0 * sw;
+    }
+  }
+}
+
+/* The same sums over every particle j (the definition, no tree), for the
+ * targets tgt[0..n_tgt). */
+void afo_sph_density_direct(int64_t n, const double *x, const double *y, const double *z,
+                            const double *m, const double *h, int64_t n_tgt,
+                            const int64_t *tgt, double *rho, double *nnb) {
+  const double pi = 3.14159265358979323846;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t t = 0; t < n_tgt; t++) {
+    const int64_t i = tgt[t];
+    const double hi = h[i];
+    double sm = 0.0, sw = 0.0;
+    for (int64_t j = 0; j < n; j++) {
+      const double dx = x[j] - x[i], dy = y[j] - y[i], dz = z[j] - z[i];
+      const double w = spline_w(sqrt(dx * dx + dy * dy + dz * dz) / hi);
+      sm += m[j] * w;
+      sw += w;
+    }
+    rho[t] = 8.0 / (pi * hi * hi * hi) * sm;
+    nnb[t] = 32.0 / 3.0 * sw;
+  }
+}
+
+int64_t afo_nbr_total(const afo_tree *t) { return t->nbr_off ? t->nbr_off[t->n_groups] : -1; }
+
+void afo_get_nbr(const afo_tree *t, int64_t *off, int32_t *idx, float *tbox, float *sbox) {
+  memcpy(off, t->nbr_off, sizeof(int64_t) * (size_t)(t->n_groups + 1));
+  memcpy(idx, t->nbr, sizeof(int32_t) * (size_t)t->nbr_off[t->n_groups]);
+  memcpy(tbox, t->c_tbox, sizeof(float) * (size_t)(6 * t->n_cells));
+  memcpy(sbox, t->g_sbox, sizeof(float) * (size_t)(6 * t->n_groups));
 }
 
 int afo_num_threads(void) {
