@@ -45,6 +45,10 @@ sys.path.insert(0, ROOT)
 
 FLOPS_PER_INTERACTION = 23  # n_op, Section 6.2 / Appendix A
 SMS, FP32_LANES = 152, 128
+# FP32 operations of the distance test k_density makes for every candidate
+# pair (3 differences, 3 for r^2, 1 for q^2 = r^2 / h^2, in packed f32x2);
+# the spline itself runs only for the pairs inside the support
+DENSITY_OPS_PER_PAIR = 7
 L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one force-kernel launch on
 # this workload, from the capture summarised in profiles/ (None until taken
@@ -71,6 +75,9 @@ def parse():
     ap.add_argument("--sweep", action="store_true",
                     help="instead of the benchmark line: theta x n_grp and n_reuse sweeps of "
                          "the workload, one JSON line per configuration")
+    ap.add_argument("--sph", action="store_true",
+                    help="instead of the benchmark line: the short-range neighbour walk and "
+                         "gather density on the workload's particles, one line per n_grp")
     return ap.parse_args()
 
 
@@ -511,7 +518,59 @@ def learned_study(args, wl, afd, torch, np, dev, stream, local, p, tuned, launch
     }
 
 
-def sweep(args, wl):
+def sph_study(wl, afd, torch, np, dev, stream, ev, T, p):
+    """Short-range neighbour walk and gather density (Section 2 /
+    Section 4.2) on the workload's particles with search radii for 64
+    neighbours under the Plummer sphere's analytic density: per n_grp the
+    list construction (cell and search boxes, walk, compaction) and the
+    density kernel, CUDA events, median of five after a warm-up."""
+    import ics
+
+    xs = [T(a) for a in (p.x, p.y, p.z, p.m)]
+    h = T(ics.plummer_search_radii(p, 64))
+    rho = torch.empty(p.n, dtype=torch.float32, device=dev)
+    nnb = torch.empty_like(rho)
+    mhz = 2070.0
+    for n_grp in (32, 64, 128, 256):
+        g = afd.Gravity(afd.Config(eps=wl["eps"], theta=wl["theta"], n_grp=n_grp), 0, stream)
+        t_tree, t_list, t_dens = [], [], []
+        for rep in range(6):
+            e0 = ev()
+            afd.afd_tree_build(g.ctx, *xs)
+            e1 = ev()
+            afd.afd_make_neighbour_lists(g.ctx, h, 0.0)
+            e2 = ev()
+            afd.afd_calc_density(g.ctx, h, rho, nnb)
+            e3 = ev()
+            e3.synchronize()
+            if rep:
+                t_tree.append(e0.elapsed_time(e1))
+                t_list.append(e1.elapsed_time(e2))
+                t_dens.append(e2.elapsed_time(e3))
+        st = afd.afd_neighbour_stats(g.ctx)
+        gs = g.stats()
+        td = float(np.median(t_dens))
+        pairs_s = st["pairs"] / (td * 1e-3)
+        peak_ops = SMS * FP32_LANES * mhz * 1e6
+        print(json.dumps({
+            "sweep": "sph_density", "workload": wl["name"], "n_nb_target": 64, "n_grp": n_grp,
+            "groups": gs["n_groups"], "tree_ms": float(np.median(t_tree)),
+            "neighbour_lists_ms": float(np.median(t_list)), "density_ms": td,
+            "list_entries": st["entries"], "candidate_pairs": st["pairs"],
+            "candidates_per_particle": st["pairs"] / p.n,
+            "mean_smooth_neighbours": float(nnb.double().mean().item()),
+            "pairs_per_s": pairs_s,
+            "roofline": {"bound": "alu", "kernel": "k_density",
+                         "ops_per_pair": DENSITY_OPS_PER_PAIR,
+                         "achieved_ops_per_s": pairs_s * DENSITY_OPS_PER_PAIR,
+                         "peak_ops_per_s": peak_ops,
+                         "frac": pairs_s * DENSITY_OPS_PER_PAIR / peak_ops,
+                         "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x {mhz:.0f} MHz"}}),
+              flush=True)
+        g.close()
+
+
+def sweep(args, wl, sph_only=False):
     """The method's two knobs on this GPU (the paper's Section 6 measures the
     same dependences on its systems): for theta x n_grp, the construction
     time (tree + lists), the force-kernel time, interactions, mean group size
@@ -533,17 +592,20 @@ def sweep(args, wl):
     n = p.n
     T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
     xs = [T(a) for a in (p.x, p.y, p.z, p.m)]
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        return e
+
+    if sph_only:
+        sph_study(wl, afd, torch, np, dev, stream, ev, T, p)
+        return
     tg = np.unique(np.linspace(0, n - 1, 4096).astype(np.int64))
     ex = torch.empty(len(tg), 4, dtype=torch.float64, device=dev)
     afd.afd_direct_sum(*xs, torch.tensor(tg.astype(np.int32), device=dev), wl["eps"], ex, stream)
     ex = ex.cpu().numpy()
     tg_t = torch.tensor(tg, device=dev)
     acc = torch.empty(n, 4, dtype=torch.float32, device=dev)
-
-    def ev():
-        e = torch.cuda.Event(enable_timing=True)
-        e.record(stream)
-        return e
 
     for theta in (0.3, 0.4, 0.5, 0.6, 0.7):
         for n_grp in (32, 64, 128, 256, 512, 1024):
@@ -643,6 +705,8 @@ def sweep(args, wl):
                       "export_ms": float(np.median(t_let)), "receiving_particles": na,
                       "rms_rel_force_error_split": err_split}), flush=True)
 
+    sph_study(wl, afd, torch, np, dev, stream, ev, T, p)
+
     R_list = (1, 2, 4, 8, 16)
     for R in R_list:
         cfg = afd.Config(eps=wl["eps"], theta=wl["theta"], n_leaf=16, n_grp=wl["n_grp"],
@@ -677,9 +741,9 @@ def main():
         if rank == 0:
             run_reference(args, wl)
         return
-    if args.sweep:
+    if args.sweep or args.sph:
         if rank == 0:
-            sweep(args, wl)
+            sweep(args, wl, sph_only=args.sph)
         return
 
     import numpy as np

@@ -65,7 +65,8 @@ typedef enum {
   AFD_ERR_OOM = -9,           /* device allocation failed */
   AFD_ERR_WALK_STACK = -10,   /* a tree walk overflowed its per-warp stack */
   AFD_ERR_TOO_LARGE = -11,    /* problem size above the limit of afd_root_cell_static */
-  AFD_ERR_NO_REFERENCE = -12  /* learned-criterion sampling without reference accelerations */
+  AFD_ERR_NO_REFERENCE = -12, /* learned-criterion sampling without reference accelerations */
+  AFD_ERR_BAD_RADIUS = -13    /* a search radius is not finite and positive */
 } afd_status;
 
 /* Method parameters. Paper values: n_leaf = 16, theta in [0.25, 1]
@@ -244,6 +245,52 @@ int afd_calc_force_materialized(afd_ctx *ctx, float *acc4, float *ms_out);
 int afd_let_export(afd_ctx *ctx, const double *box, double theta, int64_t cap, double *x,
                    double *y, double *z, double *m, uint32_t *kind, int64_t *n_out);
 
+/* ---------------------------------------------------------------------------
+ * Short-range neighbour walk (Section 2: short-range interactions such as
+ * SPH use the same tree walk with a cell-opening criterion other than the
+ * opening angle; Section 4.2: their lists can be kept over several steps,
+ * since particles move a small fraction of their spacing per step).
+ * ------------------------------------------------------------------------- */
+
+/* Neighbour lists of the current tree, one per i-group, for the search
+ * radii h (device, n doubles, caller order, each finite and > 0) and the
+ * margin skin (host double, finite, >= 0). The search box of a group is,
+ * per axis, [min_i (x_i - (h_i + skin)), max_i (x_i + (h_i + skin))] over
+ * its particles, each bound computed in FP64 and rounded outward to FP32;
+ * the tight box of a cell is the min / max of its particles' coordinates
+ * rounded outward to FP32. A cell whose tight box meets the search box is
+ * opened (or listed, when a leaf); any other cell is dropped with its
+ * subtree. A group's list is the particles of its listed leaves in
+ * depth-first order, which is ascending Morton position: every particle
+ * within h_i + skin of a particle i is on the list of i's group. Lists
+ * stay in the context until the next afd_tree_build and are kept by
+ * afd_reuse_lists (moves of less than skin / 2 keep every neighbour within
+ * h_i). Independent systems (afd_set_systems) get lists of their own
+ * particles. Needs a tree; synchronises. AFD_ERR_BAD_RADIUS if a radius is
+ * not finite and positive, AFD_ERR_ARG for a bad skin. */
+int afd_make_neighbour_lists(afd_ctx *ctx, const double *h, double skin);
+
+/* Gather-form SPH density over the neighbour lists, with the current
+ * positions and masses: rho_i = sum_j m_j W(|x_j - x_i|, h_i), the particle
+ * itself included, W the M4 cubic spline of support radius h in three
+ * dimensions, W(r, h) = 8 / (pi h^3) w(r / h) with w(q) = 1 - 6 q^2 + 6 q^3
+ * for q <= 1/2, 2 (1 - q)^3 for 1/2 < q < 1 and 0 beyond; and the smooth
+ * neighbour number nnb_i = (32 / 3) sum_j w(|x_j - x_i| / h_i). h (device,
+ * n doubles, caller order) are this evaluation's radii; they may differ
+ * from the lists' as long as every neighbour is still on the lists (h_i
+ * below the list radius + skin - twice the largest move since the lists
+ * were made). rho, nnb (device, n floats each, caller order; nnb may be
+ * NULL). FP32 arithmetic on coordinates relative to the group's first
+ * particle. Stream-ordered, does not synchronise; a radius that is not
+ * finite and positive gives NaN there and AFD_ERR_BAD_RADIUS at the next
+ * afd_sync. AFD_ERR_NO_SAVED_LIST without neighbour lists. */
+int afd_calc_density(afd_ctx *ctx, const double *h, float *rho, float *nnb);
+
+/* Sizes of the neighbour lists (host int64[2]): out[0] list entries,
+ * out[1] candidate pairs of one density evaluation (sum over groups of
+ * n_i x list length). Zeros without lists. */
+int afd_neighbour_stats(afd_ctx *ctx, int64_t *out);
+
 /* Wait for the context's stream and return the device status word. */
 int afd_sync(afd_ctx *ctx);
 
@@ -273,6 +320,9 @@ int afd_stats(afd_ctx *ctx, int64_t *out);
  *               its EPJ list (its particles follow contiguously; the force
  *               kernel skips each particle's own pair there), 0 if absent
  *   EPJ_OFF / SPJ_OFF (groups + 1) x u64, EPJ_IDX / SPJ_IDX entries x u32
+ *   NBR_OFF (groups + 1) x u64, NBR_IDX entries x u32 (neighbour lists)
+ *   CELL_TBOX   cells x 8 x f32 (tight box: min x y z, 0, max x y z, 0)
+ *   GROUP_SBOX  groups x 6 x f32 (search box: min x y z, max x y z)
  * Cells are numbered in depth-first pre-order, children in Morton order. */
 typedef enum {
   AFD_EXPORT_ROOT = 0,
@@ -294,7 +344,11 @@ typedef enum {
   AFD_EXPORT_EPJ_OFF = 16,
   AFD_EXPORT_EPJ_IDX = 17,
   AFD_EXPORT_SPJ_OFF = 18,
-  AFD_EXPORT_SPJ_IDX = 19
+  AFD_EXPORT_SPJ_IDX = 19,
+  AFD_EXPORT_NBR_OFF = 20,
+  AFD_EXPORT_NBR_IDX = 21,
+  AFD_EXPORT_CELL_TBOX = 22,
+  AFD_EXPORT_GROUP_SBOX = 23
 } afd_export_item;
 
 int afd_export(afd_ctx *ctx, int what, void *host_buf, size_t *bytes);

@@ -32,6 +32,8 @@ EXPORT = {
     "group_box": (14, np.float64), "group_self": (15, np.uint32),
     "epj_off": (16, np.uint64), "epj_idx": (17, np.uint32),
     "spj_off": (18, np.uint64), "spj_idx": (19, np.uint32),
+    "nbr_off": (20, np.uint64), "nbr_idx": (21, np.uint32),
+    "cell_tbox": (22, np.float32), "group_sbox": (23, np.float32),
 }
 
 
@@ -99,6 +101,9 @@ def lib():
         "afd_set_launch": ([_VP, ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "afd_calc_force_materialized": ([_VP, _VP, _VP], ctypes.c_int),
         "afd_let_export": ([_VP, _VP, _D, _I64, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+        "afd_make_neighbour_lists": ([_VP, _VP, _D], ctypes.c_int),
+        "afd_calc_density": ([_VP, _VP, _VP, _VP], ctypes.c_int),
+        "afd_neighbour_stats": ([_VP, _VP], ctypes.c_int),
         "afd_get_launch": ([_VP, _VP, _VP], ctypes.c_int),
         "afd_autotune_launch": ([_VP, _VP, ctypes.c_int, _VP], ctypes.c_int),
         "afd_mac_set": ([_VP, _VP, _D, _D, _D], ctypes.c_int),
@@ -363,6 +368,32 @@ def afd_let_export(ctx, box, theta, cap=None):
     return (*(o[:k] for o in out), kind[:k])
 
 
+def afd_make_neighbour_lists(ctx, h, skin=0.0):
+    """Neighbour lists for search radii h (CUDA float64, caller order) and
+    margin skin (short-range walk, Section 2)."""
+    import torch
+    n = afd_stats(ctx)["n"]
+    _check(lib().afd_make_neighbour_lists(ctx, _dptr(h, torch.float64, n, "h"), float(skin)),
+           "afd_make_neighbour_lists")
+
+
+def afd_calc_density(ctx, h, rho, nnb=None):
+    """Gather density (and smooth neighbour number) over the neighbour
+    lists into rho / nnb (CUDA float32, caller order)."""
+    import torch
+    n = afd_stats(ctx)["n"]
+    _check(lib().afd_calc_density(ctx, _dptr(h, torch.float64, n, "h"),
+                                  _dptr(rho, torch.float32, n, "rho"),
+                                  None if nnb is None else _dptr(nnb, torch.float32, n, "nnb")),
+           "afd_calc_density")
+
+
+def afd_neighbour_stats(ctx) -> dict:
+    out = (ctypes.c_int64 * 2)()
+    _check(lib().afd_neighbour_stats(ctx, ctypes.cast(out, _VP)), "afd_neighbour_stats")
+    return {"entries": int(out[0]), "pairs": int(out[1])}
+
+
 def afd_set_launch(ctx, warps_per_block, chunk):
     _check(lib().afd_set_launch(ctx, int(warps_per_block), int(chunk)), "afd_set_launch")
 
@@ -544,3 +575,9 @@ class Gravity:
 
     def export(self, what):
         return afd_export(self.ctx, what)
+
+    def neighbour_lists(self, h, skin=0.0):
+        afd_make_neighbour_lists(self.ctx, h, skin)
+
+    def density(self, h, rho, nnb=None):
+        afd_calc_density(self.ctx, h, rho, nnb)

@@ -131,7 +131,7 @@ int tree_build(afd_ctx *c, const double *x, const double *y, const double *z, co
   if (n < 0 || n >= ((int64_t)1 << 30)) return AFD_ERR_ARG;
   if (n > 0 && (!x || !y || !z || !m)) return AFD_ERR_ARG;
   if (c->n_sys > 1 && n != c->sys_off_h[c->n_sys]) return AFD_ERR_SHAPE;
-  c->have_tree = c->have_lists = c->saved = false;
+  c->have_tree = c->have_lists = c->saved = c->have_nbr = false;
   c->n = n;
   TRY(launch_root(c, x, y, z, m, n));
   TRY(launch_keys(c, x, y, z, n));
@@ -157,8 +157,10 @@ int make_lists(afd_ctx *c, int mode) {
 }
 
 int reuse(afd_ctx *c, const double *x, const double *y, const double *z, const double *m) {
-  if (!c->saved || !c->have_lists) return AFD_ERR_NO_SAVED_LIST;
+  // kept gravity lists or neighbour lists (both survive the move)
+  if (!(c->saved && c->have_lists) && !c->have_nbr) return AFD_ERR_NO_SAVED_LIST;
   if (c->n > 0 && (!x || !y || !z || !m)) return AFD_ERR_ARG;
+  if (!c->saved) c->have_lists = false;  // gravity lists not made for reuse end here
   TRY(launch_reorder(c, x, y, z, m, c->n));
   TRY(launch_moments(c, false, false));  // lists are kept: no criterion runs
   return AFD_OK;
@@ -266,7 +268,11 @@ void afd_destroy(afd_ctx *c) {
                     &c->band_cnt, &c->band_off, &c->l_nrec, &c->l_head_s, &c->l_head_l,
                     &c->arena_s, &c->arena_l, &c->next_s, &c->next_l, &c->arena_cur,
                     &c->m_ehi, &c->m_elo, &c->m_shi, &c->m_slo, &c->let_mark,
-                    &c->let_cnt, &c->let_off};
+                    &c->let_cnt, &c->let_off, &c->c_tbox, &c->nbr_arrive, &c->g_sbox,
+                    &c->nbr_cnt, &c->nbr_off, &c->nbr, &c->nbr_blk, &c->nbr_seg_cnt,
+                    &c->nbr_seg_off, &c->nbr_items, &c->nbr_part, &c->nbr_seedf,
+                    &c->nbr_seedo, &c->nbr_seeds, &c->nbr_icnt, &c->nbr_igoff, &c->nbr_itg,
+                    &c->nbr_itr, &c->nbr_ioff, &c->nbr_sbb};
   for (DevBuf *b : bufs) release(*b);
   if (c->pinned) cudaFreeHost(c->pinned);
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -676,6 +682,10 @@ int afd_export(afd_ctx *c, int what, void *host_buf, size_t *bytes) {
     case AFD_EXPORT_EPJ_IDX: src = c->epj.p; sz = lists ? (size_t)c->n_epj * 4 : 0; break;
     case AFD_EXPORT_SPJ_OFF: src = c->spj_off.p; sz = lists ? (ng + 1) * 8 : 0; break;
     case AFD_EXPORT_SPJ_IDX: src = c->spj.p; sz = lists ? (size_t)c->n_spj * 4 : 0; break;
+    case AFD_EXPORT_NBR_OFF: src = c->nbr_off.p; sz = c->have_nbr ? (ng + 1) * 8 : 0; break;
+    case AFD_EXPORT_NBR_IDX: src = c->nbr.p; sz = c->have_nbr ? (size_t)c->n_nbr * 4 : 0; break;
+    case AFD_EXPORT_CELL_TBOX: src = c->c_tbox.p; sz = c->have_nbr ? nc * 32 : 0; break;
+    case AFD_EXPORT_GROUP_SBOX: src = c->g_sbox.p; sz = c->have_nbr ? ng * 24 : 0; break;
     default: return AFD_ERR_ARG;
   }
   if (!host_buf) {
@@ -715,6 +725,7 @@ const char *afd_error_string(int status) {
     case AFD_ERR_TOO_LARGE: return "problem size above the static scratch limit (n <= 2^31 - 1)";
     case AFD_ERR_NO_REFERENCE:
       return "no reference accelerations for the current particles (learned opening criterion)";
+    case AFD_ERR_BAD_RADIUS: return "search radius not finite and positive";
     default: return "unknown status";
   }
 }

@@ -35,6 +35,7 @@ enum : int {
   kStWalkStack = 2,
   kStWalkIter = 4,
   kStOverflow = 8,
+  kStBadRadius = 16,
 };
 int status_to_error(int bits);
 
@@ -110,6 +111,23 @@ struct afd_ctx {
   afd::DevBuf m_ehi, m_elo, m_shi, m_slo;
   // local essential tree export: per-cell marks, element counts and offsets
   afd::DevBuf let_mark, let_cnt, let_off;
+  // short-range neighbour lists: per-cell tight boxes (float4 lo, hi) and
+  // their bottom-up arrival counters, per-group search boxes (float[6]),
+  // per-group counts (and a zero SPJ-count scratch), CSR offsets and lists
+  afd::DevBuf c_tbox, nbr_arrive, g_sbox, nbr_cnt, nbr_off, nbr;
+  // the walk's view of a cell's children's tight boxes: 8 x (lo, hi) per cell
+  afd::DevBuf nbr_blk;
+  // the walk's work items: seed cells (flags, offsets, ids), per group its
+  // item count and first item, per item its group, seed and CSR offset
+  afd::DevBuf nbr_seedf, nbr_seedo, nbr_seeds, nbr_icnt, nbr_igoff, nbr_itg, nbr_itr, nbr_ioff;
+  afd::DevBuf nbr_sbb;  // union boxes of blocks of 32 seeds
+  // density work items (unit, list segment), per-unit segment counts and
+  // first items, partial sums of units with several segments
+  afd::DevBuf nbr_seg_cnt, nbr_seg_off, nbr_items, nbr_part;
+  uint64_t n_nbr = 0, nbr_pairs = 0;
+  int64_t n_items = 0;
+  bool nbr_multi = false;  // some unit has several segments
+  bool have_nbr = false;
   // walk record arena: per group leaf-record count and chunk-chain heads;
   // chunks of cell ids / leaf records, chain links, cursors (capacity in chunks)
   afd::DevBuf l_nrec, l_head_s, l_head_l;
@@ -188,6 +206,8 @@ int launch_group_boxes(afd_ctx *c);
 
 // ---- walk (afd_walk.cu) ----
 int launch_walk(afd_ctx *c);  // lists; sets n_epj, n_spj, interactions (syncs)
+// neighbour lists from c_tbox and g_sbox; sets n_nbr, nbr_pairs (syncs)
+int launch_nbr_walk(afd_ctx *c);
 
 // ---- learned opening criterion (afd_mac.cu) ----
 bool mac_usable(const afd_ctx *c);   // weights, reference |a| and quadrupoles present

@@ -33,6 +33,7 @@ int status_to_error(int bits) {
   if (bits & kStWalkStack) return AFD_ERR_WALK_STACK;
   if (bits & kStWalkIter) return AFD_ERR_TIMEOUT;
   if (bits & kStOverflow) return AFD_ERR_LIST_OVERFLOW;
+  if (bits & kStBadRadius) return AFD_ERR_BAD_RADIUS;
   return AFD_OK;
 }
 

@@ -24,6 +24,15 @@
 // inside) and s the cell side, the cell is accepted iff s^2 < theta^2 d^2,
 // computed as ((dx*dx + dy*dy) + dz*dz) and theta2 * d2 in that order.
 //
+// The short-range neighbour walk (Section 2: the same walk with a criterion
+// other than the opening angle) is a third mode of the same kernel: a cell
+// whose tight box (FP32, rounded outward) meets the group's search box is
+// opened, or listed when a leaf; any other cell is dropped with its
+// subtree, so the SPJ stream stays empty and the EPJ stream holds the
+// candidate neighbours in ascending Morton position. A cell whose tight
+// box lies inside the search box is listed whole, as one record of its
+// particle range, which is what its leaves would give in order.
+//
 // With the learned criterion (afd_mac.cuh) the same walk decides each cell
 // by learned_pre() (the band tests in FP32) and, for the cells inside the
 // band, by the network, which the whole warp evaluates for four band cells
@@ -38,6 +47,7 @@
 #include "afd_mac.cuh"
 
 #include <algorithm>
+#include <cstring>
 
 namespace afd {
 namespace {
@@ -70,7 +80,16 @@ struct WalkArgs {
   const float4 *s_hi, *s_q0, *s_q1;
   float lo2, hi2, tau, eps2;
   unsigned long long *mac_cnt;
+  // neighbour walk: per-cell tight boxes (lo, hi) and per cell its
+  // children's (8 x (lo, hi), by octant); boxf then holds the groups'
+  // search boxes
+  const float4 *tbox, *nblk;
+  // neighbour walk: n_groups counts work items (group, seed cell); their
+  // group and the cell the walk starts from
+  const uint32_t *it_group, *it_root;
 };
+
+enum : int { kModeTheta = 0, kModeLearned = 1, kModeNeighbour = 2 };
 
 __device__ __forceinline__ float sep_axis(float c, float lo, float hi) {
   float d = 0.0f;
@@ -91,6 +110,22 @@ __device__ __forceinline__ uint32_t decide(const float *bmin, const float *bmax,
   const float rhs = __fmul_rn(theta2, d2);
   if (s2 < rhs) return kAccept;
   return leaf ? kLeaf : kOpen;
+}
+
+// Neighbour decision: kAccept ("drop") when the cell's tight box misses the
+// search box (closed intervals on every axis); kLeaf when the cell is a leaf
+// or its tight box lies inside the search box -- then every leaf below it is
+// listed, and in depth-first order those leaves' particles are exactly the
+// cell's range [first, first + count), so one record stands for the whole
+// subtree and the list is the same; kOpen otherwise.
+__device__ __forceinline__ uint32_t decide_nbr(const float *bmin, const float *bmax, float4 lo,
+                                               float4 hi, bool leaf) {
+  const bool meet = lo.x <= bmax[0] && hi.x >= bmin[0] && lo.y <= bmax[1] && hi.y >= bmin[1] &&
+                    lo.z <= bmax[2] && hi.z >= bmin[2];
+  if (!meet) return kAccept;
+  const bool inside = lo.x >= bmin[0] && hi.x <= bmax[0] && lo.y >= bmin[1] &&
+                      hi.y <= bmax[1] && lo.z >= bmin[2] && hi.z <= bmax[2];
+  return (leaf || inside) ? kLeaf : kOpen;
 }
 
 // Learned decision without the network: kAccept, kOpen / kLeaf, or kBand
@@ -185,8 +220,9 @@ struct MacScratch {
   float4 hin[kMacNH];     // hidden layer 1 of the current 4 cells: [unit]
 };
 
-template <bool LEARNED>
+template <int MODE>
 __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
+  constexpr bool LEARNED = MODE == kModeLearned, NBR = MODE == kModeNeighbour;
   __shared__ uint2 stk_all[kWalkWarps][kStack];
   __shared__ __align__(16) MacWeights mw_all[1];  // unused (and dropped) without LEARNED
   __shared__ __align__(16) MacScratch msc_all[LEARNED ? kWalkWarps : 1];
@@ -213,30 +249,36 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
   for (int64_t g = (int64_t)blockIdx.x * kWalkWarps + wib; g < a.n_groups;
        g += (int64_t)gridDim.x * kWalkWarps) {
     float bmin[3], bmax[3];
+    const int64_t gb = NBR ? (int64_t)a.it_group[g] : g;  // the box's group
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-      bmin[k] = a.boxf[g * 6 + k];
-      bmax[k] = a.boxf[g * 6 + 3 + k];
+      bmin[k] = a.boxf[gb * 6 + k];
+      bmax[k] = a.boxf[gb * 6 + 3 + k];
     }
-    const uint32_t gfirst = a.g_first[g];
+    const uint32_t gfirst = NBR ? 0u : a.g_first[g];
     const float amin = LEARNED ? a.g_amin[g] : 0.0f;
     uint64_t ne = 0, ns = 0;
     uint32_t nl = 0;  // leaf records
     RecStream rs{kNone, kChunk}, rl{kNone, kChunk};
     uint32_t self_pos = 0;  // 1 + EPJ-list position of the group's first particle
+    uint32_t root_drop = 0;
     if (lane == 0) {
-      uint32_t root = a.g_root[g];
+      uint32_t root = NBR ? a.it_root[g] : a.g_root[g];
       if (!AFD_IN(root, a.n_cells, "walk root")) root = 0u;
       const float4 nf = a.node_f[root];
       const uint2 ni = a.node_i[root];
       const bool leaf = (ni.y >> 31) != 0;
       const uint32_t cnt = ni.y & 0x7fffffffu;
       // a system's root holds all its groups: the learned rule opens it
-      const uint32_t d = LEARNED ? (leaf ? kLeaf : kOpen)
-                                 : decide(bmin, bmax, nf.x, nf.y, nf.z, nf.w, leaf, a.theta2);
+      const uint32_t d =
+          NBR ? decide_nbr(bmin, bmax, a.tbox[(size_t)root * 2], a.tbox[(size_t)root * 2 + 1], leaf)
+          : LEARNED ? (leaf ? kLeaf : kOpen)
+                    : decide(bmin, bmax, nf.x, nf.y, nf.z, nf.w, leaf, a.theta2);
       stk[0] = make_entry(d, root, ni.x, cnt);
+      root_drop = (NBR && d == kAccept) ? 1u : 0u;
     }
-    int sp = 1;
+    // the neighbour walk drops a root that does not meet the search box
+    int sp = NBR ? (__shfl_sync(0xffffffffu, root_drop, 0) ? 0 : 1) : 1;
     uint32_t iters = 0;
     __syncwarp();
     while (sp > 0) {
@@ -308,6 +350,13 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
       if (q_me < E) {
         const uint4 *blk = a.block + ((size_t)cid_me * 8 + c_me) * 2;
         const uint4 nf = blk[0], meta = blk[1];
+        // the neighbour walk's child box comes with the child record (one
+        // round trip per step)
+        float4 nlo = make_float4(0.0f, 0.0f, 0.0f, 0.0f), nhi = nlo;
+        if (NBR) {
+          nlo = a.nblk[((size_t)cid_me * 8 + c_me) * 2];
+          nhi = a.nblk[((size_t)cid_me * 8 + c_me) * 2 + 1];
+        }
         valid = meta.z != kNone && AFD_IN(meta.z, a.n_cells, "walk child");
         if (valid) {
           leaf_me = (meta.y >> 31) != 0;
@@ -316,9 +365,14 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
           c_cnt = meta.y & 0x7fffffffu;
           const float cx = __uint_as_float(nf.x), cy = __uint_as_float(nf.y),
                       cz = __uint_as_float(nf.z), s2 = __uint_as_float(nf.w);
-          d = LEARNED ? learned_pre(a, bmin, bmax, cx, cy, cz, s2, leaf_me, c_id, c_first, c_cnt,
-                                    gfirst, amin, feat)
-                      : decide(bmin, bmax, cx, cy, cz, s2, leaf_me, a.theta2);
+          if (NBR) {
+            d = decide_nbr(bmin, bmax, nlo, nhi, leaf_me);
+            valid = d != kAccept;  // a dropped cell takes no stack entry
+          } else {
+            d = LEARNED ? learned_pre(a, bmin, bmax, cx, cy, cz, s2, leaf_me, c_id, c_first,
+                                      c_cnt, gfirst, amin, feat)
+                        : decide(bmin, bmax, cx, cy, cz, s2, leaf_me, a.theta2);
+          }
         }
       }
       if (LEARNED) {
@@ -435,7 +489,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
       a.cnt_e[g] = (uint32_t)ne;
       a.cnt_s[g] = (uint32_t)ns;
       a.n_lrec[g] = nl;
-      a.gself[g] = self_pos;
+      if (!NBR) a.gself[g] = self_pos;
       if (ns == 0) a.head_s[g] = kNone;
       if (nl == 0) a.head_l[g] = kNone;
     }
@@ -462,7 +516,7 @@ __global__ void k_interactions(int64_t n_groups, const uint32_t *__restrict__ g_
   unsigned long long s = 0;
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_groups;
        g += (int64_t)gridDim.x * blockDim.x)
-    s += (unsigned long long)g_count[g] * ((unsigned long long)ce[g] + cs[g]);
+    s += (unsigned long long)g_count[g] * ((unsigned long long)ce[g] + (cs ? cs[g] : 0u));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
@@ -480,13 +534,18 @@ struct CompactArgs {
   uint64_t n_epj, n_spj;
 };
 
-constexpr int kCompactBuf = 1024;  // staged EPJ entries per warp
+// Leaf records are expanded 32 at a time. Records of kBigRec or more
+// entries (whole subtrees of the neighbour walk, level-21 leaves) are
+// written one by one with strided stores; for the others, after an inclusive
+// scan of their counts, lane t of each pass over their entries finds its
+// record by a binary search of the scanned counts (five shuffles) and writes
+// first + offset at the record's output position, so the writes stay
+// coalesced whatever the mix of sizes.
+constexpr uint32_t kBigRec = 64;
 
 __global__ void __launch_bounds__(256) k_compact(CompactArgs a) {
-  __shared__ uint32_t buf_all[8][kCompactBuf];
   const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  uint32_t *buf = buf_all[threadIdx.x >> 5];
   if (g >= a.n_groups) return;
   const uint32_t ms = a.cnt_s[g];
   uint32_t c = a.head_s[g];
@@ -516,25 +575,41 @@ __global__ void __launch_bounds__(256) k_compact(CompactArgs a) {
       }
       const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
       const uint32_t ex = inc - rec.y;
-      if (tot <= (uint32_t)kCompactBuf) {
-        // each lane expands its own leaf into shared memory, then the warp
-        // stores the run with coalesced writes
-        for (uint32_t k = 0; k < rec.y; k++) buf[ex + k] = rec.x + k;
-        __syncwarp();
-        for (uint32_t i = lane; i < tot; i += 32)
-          if (AFD_IN(pos + i, a.n_epj, "compact epj write")) a.epj[pos + i] = buf[i];
-        __syncwarp();
-      } else {  // very large leaves (level 21): one leaf at a time
-        unsigned lm = __ballot_sync(0xffffffffu, on && rec.y > 0);
-        while (lm) {
-          const int src = __ffs(lm) - 1;
-          lm &= lm - 1;
-          const uint32_t f0 = __shfl_sync(0xffffffffu, rec.x, src);
-          const uint32_t c0 = __shfl_sync(0xffffffffu, rec.y, src);
-          const uint32_t x0 = __shfl_sync(0xffffffffu, ex, src);
-          for (uint32_t k = lane; k < c0; k += 32)
-            if (AFD_IN(pos + x0 + k, a.n_epj, "compact epj write")) a.epj[pos + x0 + k] = f0 + k;
-        }
+      // records of kBigRec or more entries (whole subtrees of the neighbour
+      // walk, level-21 leaves): the warp writes each with strided stores
+      const bool big = rec.y >= kBigRec;
+      unsigned bm = __ballot_sync(0xffffffffu, big);
+      while (bm) {
+        const int src = __ffs(bm) - 1;
+        bm &= bm - 1;
+        const uint32_t f0 = __shfl_sync(0xffffffffu, rec.x, src);
+        const uint32_t c0 = __shfl_sync(0xffffffffu, rec.y, src);
+        const uint64_t o0 = pos + __shfl_sync(0xffffffffu, ex, src);
+        for (uint32_t k = lane; k < c0; k += 32)
+          if (AFD_IN(o0 + k, a.n_epj, "compact epj write")) a.epj[o0 + k] = f0 + k;
+      }
+      // the others: lane t of each pass over their entries finds its record
+      // by a binary search of their scanned counts
+      uint32_t sn = big ? 0u : rec.y;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, sn, o);
+        if (lane >= o) sn += t;
+      }
+      const uint32_t stot = __shfl_sync(0xffffffffu, sn, 31);
+      const uint32_t sex = sn - (big ? 0u : rec.y);
+      for (uint32_t t0 = 0; t0 < stot; t0 += 32) {
+        const uint32_t t = t0 + lane;
+        // the record holding entry t: the first whose inclusive count > t
+        int q = 0;
+#pragma unroll
+        for (int b = 16; b > 0; b >>= 1)
+          if (__shfl_sync(0xffffffffu, sn, q + b - 1) <= t) q += b;
+        const uint32_t f = __shfl_sync(0xffffffffu, rec.x, q & 31);
+        const uint32_t se = __shfl_sync(0xffffffffu, sex, q & 31);
+        const uint32_t e = __shfl_sync(0xffffffffu, ex, q & 31);
+        const uint64_t o = pos + e + (t - se);
+        if (t < stot && AFD_IN(o, a.n_epj, "compact epj write")) a.epj[o] = f + (t - se);
       }
       pos += tot;
     }
@@ -570,72 +645,37 @@ int launch_sys_stats(afd_ctx *c, unsigned long long *inter, unsigned long long *
   return cudaGetLastError() == cudaSuccess ? AFD_OK : AFD_ERR_CUDA;
 }
 
-int launch_walk(afd_ctx *c) {
-  const int64_t ng = c->n_groups;
+namespace {
+
+// The walk's outputs: per-group counts, offsets and CSR lists (no SPJ side
+// for the neighbour walk), and the totals read back.
+struct WalkOut {
+  uint32_t *cnt_e, *cnt_s;  // cnt_s: scratch for the neighbour walk (all zero)
+  DevBuf *off_e, *off_s, *epj, *spj;  // off_s, spj null for the neighbour walk
+  uint64_t n_e = 0, n_s = 0, inter = 0;
+};
+
+// One pass of k_walk<mode> into the record arena (grown to the size the
+// cursors report and the pass repeated when it was too small), the offset
+// scans, the interaction count and the compaction into CSR lists.
+// Synchronises once per pass.
+int run_walk(afd_ctx *c, WalkArgs &a, int mode, WalkOut &o, int64_t ng) {
   int st;
-  for (afd::DevBuf *b : {&c->l_cnt_e, &c->l_cnt_s, &c->l_nrec, &c->l_head_s, &c->l_head_l})
-    if ((st = reserve(*b, sizeof(uint32_t) * ng))) return st;
-  for (afd::DevBuf *b : {&c->epj_off, &c->spj_off})
-    if ((st = reserve(*b, sizeof(uint64_t) * (ng + 1)))) return st;
-  if ((st = reserve(c->arena_cur, 2 * sizeof(uint32_t)))) return st;
-  // after reusing steps the walk records, group boxes (and quadrupoles) lag
-  // the particles: refresh them before walking
-  if (c->n_cells > 0 && (!c->blocks_current || (c->cfg.mac && !c->q_current))) {
-    if ((st = launch_moments(c, true, c->cfg.mac != 0))) return st;
-    if ((st = launch_group_boxes(c))) return st;
-  }
-  if (ng == 0) {
-    c->n_epj = c->n_spj = c->interactions = 0;
-    cudaMemsetAsync(c->epj_off.p, 0, sizeof(uint64_t), c->stream);
-    cudaMemsetAsync(c->spj_off.p, 0, sizeof(uint64_t), c->stream);
-    return cudaGetLastError() == cudaSuccess ? AFD_OK : AFD_ERR_CUDA;
-  }
+  const bool nbr = mode == kModeNeighbour;
   // arena capacity in chunks: kept from earlier walks, first guess from the
   // group count (about 1500 cell ids and 130 leaves per group of 256)
   if (c->arena_cap_s == 0) c->arena_cap_s = (uint32_t)std::min<int64_t>(ng * 24 + 4096, 1u << 30);
   if (c->arena_cap_l == 0) c->arena_cap_l = (uint32_t)std::min<int64_t>(ng * 4 + 4096, 1u << 30);
-  WalkArgs a;
-  a.n_groups = ng;
-  a.boxf = ptr<float>(c->g_boxf);
-  a.g_first = ptr<uint32_t>(c->g_first);
-  a.g_root = ptr<uint32_t>(c->g_root);
-  a.node_f = ptr<float4>(c->node_f);
-  a.node_i = ptr<uint2>(c->node_i);
-  a.block = ptr<uint4>(c->c_block);
-  const float th = (float)c->cfg.theta;
-  a.theta2 = th * th;
-  a.cnt_e = ptr<uint32_t>(c->l_cnt_e);
-  a.cnt_s = ptr<uint32_t>(c->l_cnt_s);
+  a.cnt_e = o.cnt_e;
+  a.cnt_s = o.cnt_s;
   a.n_lrec = ptr<uint32_t>(c->l_nrec);
   a.head_s = ptr<uint32_t>(c->l_head_s);
   a.head_l = ptr<uint32_t>(c->l_head_l);
-  a.gself = ptr<uint32_t>(c->g_self);
   a.cursor = ptr<uint32_t>(c->arena_cur);
   a.status = ptr<int>(c->status);
   a.iter_cap = (uint32_t)(2 * c->n_cells + 64);
   a.n_cells = (uint32_t)c->n_cells;
-  const bool learned = mac_usable(c);
-  a.mac_w = nullptr;
-  a.g_amin = nullptr;
-  a.s_hi = a.s_q0 = a.s_q1 = nullptr;
-  a.lo2 = a.hi2 = a.tau = a.eps2 = 0.0f;
-  a.mac_cnt = nullptr;
-  if (learned) {
-    if ((st = launch_group_amin(c))) return st;
-    if ((st = reserve(c->mac_cnt, 3 * sizeof(unsigned long long)))) return st;
-    a.mac_w = ptr<float>(c->mac_w);
-    a.g_amin = ptr<float>(c->g_amin);
-    a.s_hi = ptr<float4>(c->s_hi);
-    a.s_q0 = ptr<float4>(c->s_q0);
-    a.s_q1 = ptr<float4>(c->s_q1);
-    a.lo2 = c->mac_lo2;
-    a.hi2 = c->mac_hi2;
-    a.tau = c->mac_tau;
-    const float e = (float)c->cfg.eps;
-    a.eps2 = e * e;
-    a.mac_cnt = ptr<unsigned long long>(c->mac_cnt);
-  }
-  c->walk_learned = learned;
+  a.n_groups = ng;
   int64_t nb = (ng + kWalkWarps - 1) / kWalkWarps;
   if (nb > 152 * 32) nb = 152 * 32;
   unsigned long long *inter = ptr<unsigned long long>(c->u64acc) + 1;
@@ -653,30 +693,37 @@ int launch_walk(afd_ctx *c) {
     a.cap_l = c->arena_cap_l;
     if (cudaMemsetAsync(c->arena_cur.p, 0, 2 * sizeof(uint32_t), c->stream) != cudaSuccess)
       return AFD_ERR_CUDA;
-    if (learned && cudaMemsetAsync(c->mac_cnt.p, 0, 3 * sizeof(unsigned long long),
-                                   c->stream) != cudaSuccess)
+    if (mode == kModeLearned && cudaMemsetAsync(c->mac_cnt.p, 0, 3 * sizeof(unsigned long long),
+                                                c->stream) != cudaSuccess)
       return AFD_ERR_CUDA;
-    if (learned) k_walk<true><<<(unsigned)nb, kWalkThreads, 0, c->stream>>>(a);
-    else k_walk<false><<<(unsigned)nb, kWalkThreads, 0, c->stream>>>(a);
+    if (mode == kModeLearned) k_walk<kModeLearned><<<(unsigned)nb, kWalkThreads, 0, c->stream>>>(a);
+    else if (nbr) k_walk<kModeNeighbour><<<(unsigned)nb, kWalkThreads, 0, c->stream>>>(a);
+    else k_walk<kModeTheta><<<(unsigned)nb, kWalkThreads, 0, c->stream>>>(a);
     c->launches++;
     if (cudaGetLastError() != cudaSuccess) return AFD_ERR_CUDA;
-    if ((st = scan_u32_to_u64(c, a.cnt_e, ptr<uint64_t>(c->epj_off), ng))) return st;
-    if ((st = scan_u32_to_u64(c, a.cnt_s, ptr<uint64_t>(c->spj_off), ng))) return st;
+    if ((st = scan_u32_to_u64(c, a.cnt_e, ptr<uint64_t>(*o.off_e), ng))) return st;
+    if (!nbr && (st = scan_u32_to_u64(c, a.cnt_s, ptr<uint64_t>(*o.off_s), ng))) return st;
     cudaMemsetAsync(inter, 0, sizeof(unsigned long long), c->stream);
-    k_interactions<<<152, 256, 0, c->stream>>>(ng, ptr<uint32_t>(c->g_count), a.cnt_e, a.cnt_s,
-                                                inter);
-    c->launches++;
-    cudaMemcpyAsync(pin, ptr<uint64_t>(c->epj_off) + ng, sizeof(uint64_t), cudaMemcpyDeviceToHost,
+    if (!nbr) {  // (the neighbour walk counts its pairs per group afterwards)
+      k_interactions<<<152, 256, 0, c->stream>>>(ng, ptr<uint32_t>(c->g_count), a.cnt_e,
+                                                  a.cnt_s, inter);
+      c->launches++;
+    }
+    cudaMemcpyAsync(pin, ptr<uint64_t>(*o.off_e) + ng, sizeof(uint64_t), cudaMemcpyDeviceToHost,
                     c->stream);
-    cudaMemcpyAsync(pin + 1, ptr<uint64_t>(c->spj_off) + ng, sizeof(uint64_t),
-                    cudaMemcpyDeviceToHost, c->stream);
+    if (!nbr)
+      cudaMemcpyAsync(pin + 1, ptr<uint64_t>(*o.off_s) + ng, sizeof(uint64_t),
+                      cudaMemcpyDeviceToHost, c->stream);
     cudaMemcpyAsync(pin + 2, inter, sizeof(uint64_t), cudaMemcpyDeviceToHost, c->stream);
     cudaMemcpyAsync(pin + 3, c->status.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     cudaMemcpyAsync(pin + 4, c->arena_cur.p, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost,
                     c->stream);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return AFD_ERR_CUDA;
     const int bits = (int)(pin[3] & 0xffffffffu);
-    if (bits) return status_to_error(bits);
+    if (bits) {
+      cudaMemsetAsync(c->status.p, 0, sizeof(int), c->stream);
+      return status_to_error(bits);
+    }
     const uint32_t need_s = (uint32_t)(pin[4] & 0xffffffffu), need_l = (uint32_t)(pin[4] >> 32);
     if (need_s <= c->arena_cap_s && need_l <= c->arena_cap_l) break;
     if (attempt > 0) return AFD_ERR_LIST_OVERFLOW;  // cannot happen: sized from the cursors
@@ -685,11 +732,11 @@ int launch_walk(afd_ctx *c) {
     if (need_l > c->arena_cap_l)
       c->arena_cap_l = (uint32_t)std::min<uint64_t>((uint64_t)need_l * 5 / 4 + 1024, 1u << 30);
   }
-  c->n_epj = pin[0];
-  c->n_spj = pin[1];
-  c->interactions = pin[2];
-  if ((st = reserve(c->epj, sizeof(uint32_t) * c->n_epj))) return st;
-  if ((st = reserve(c->spj, sizeof(uint32_t) * c->n_spj))) return st;
+  o.n_e = pin[0];
+  o.n_s = nbr ? 0 : pin[1];
+  o.inter = pin[2];
+  if ((st = reserve(*o.epj, sizeof(uint32_t) * o.n_e))) return st;
+  if (!nbr && (st = reserve(*o.spj, sizeof(uint32_t) * o.n_s))) return st;
   CompactArgs k;
   k.n_groups = ng;
   k.cnt_s = a.cnt_s;
@@ -700,17 +747,359 @@ int launch_walk(afd_ctx *c) {
   k.next_l = a.next_l;
   k.arena_s = a.arena_s;
   k.arena_l = a.arena_l;
-  k.off_e = ptr<uint64_t>(c->epj_off);
-  k.off_s = ptr<uint64_t>(c->spj_off);
-  k.epj = ptr<uint32_t>(c->epj);
-  k.spj = ptr<uint32_t>(c->spj);
+  k.off_e = ptr<uint64_t>(*o.off_e);
+  k.off_s = ptr<uint64_t>(nbr ? *o.off_e : *o.off_s);  // read, never used, without SPJs
+  k.epj = ptr<uint32_t>(*o.epj);
+  k.spj = nbr ? nullptr : ptr<uint32_t>(*o.spj);
   k.cap_s = c->arena_cap_s;
   k.cap_l = c->arena_cap_l;
-  k.n_epj = c->n_epj;
-  k.n_spj = c->n_spj;
+  k.n_epj = o.n_e;
+  k.n_spj = o.n_s;
   k_compact<<<(unsigned)((ng * 32 + 255) / 256), 256, 0, c->stream>>>(k);
   c->launches++;
   return cudaGetLastError() == cudaSuccess ? AFD_OK : AFD_ERR_CUDA;
+}
+
+int walk_scratch(afd_ctx *c, int64_t ng) {
+  int st;
+  for (afd::DevBuf *b : {&c->l_nrec, &c->l_head_s, &c->l_head_l})
+    if ((st = reserve(*b, sizeof(uint32_t) * ng))) return st;
+  return reserve(c->arena_cur, 2 * sizeof(uint32_t));
+}
+
+WalkArgs base_args(afd_ctx *c) {
+  WalkArgs a;
+  memset(&a, 0, sizeof(a));
+  a.n_groups = c->n_groups;
+  a.g_first = ptr<uint32_t>(c->g_first);
+  a.g_root = ptr<uint32_t>(c->g_root);
+  a.node_f = ptr<float4>(c->node_f);
+  a.node_i = ptr<uint2>(c->node_i);
+  a.block = ptr<uint4>(c->c_block);
+  return a;
+}
+
+}  // namespace
+
+int launch_walk(afd_ctx *c) {
+  const int64_t ng = c->n_groups;
+  int st;
+  for (afd::DevBuf *b : {&c->l_cnt_e, &c->l_cnt_s})
+    if ((st = reserve(*b, sizeof(uint32_t) * ng))) return st;
+  for (afd::DevBuf *b : {&c->epj_off, &c->spj_off})
+    if ((st = reserve(*b, sizeof(uint64_t) * (ng + 1)))) return st;
+  if ((st = walk_scratch(c, ng))) return st;
+  // after reusing steps the walk records, group boxes (and quadrupoles) lag
+  // the particles: refresh them before walking
+  if (c->n_cells > 0 && (!c->blocks_current || (c->cfg.mac && !c->q_current))) {
+    if ((st = launch_moments(c, true, c->cfg.mac != 0))) return st;
+    if ((st = launch_group_boxes(c))) return st;
+  }
+  if (ng == 0) {
+    c->n_epj = c->n_spj = c->interactions = 0;
+    cudaMemsetAsync(c->epj_off.p, 0, sizeof(uint64_t), c->stream);
+    cudaMemsetAsync(c->spj_off.p, 0, sizeof(uint64_t), c->stream);
+    return cudaGetLastError() == cudaSuccess ? AFD_OK : AFD_ERR_CUDA;
+  }
+  WalkArgs a = base_args(c);
+  a.boxf = ptr<float>(c->g_boxf);
+  const float th = (float)c->cfg.theta;
+  a.theta2 = th * th;
+  a.gself = ptr<uint32_t>(c->g_self);
+  const bool learned = mac_usable(c);
+  if (learned) {
+    if ((st = launch_group_amin(c))) return st;
+    if ((st = reserve(c->mac_cnt, 3 * sizeof(unsigned long long)))) return st;
+    a.mac_w = ptr<float>(c->mac_w);
+    a.g_amin = ptr<float>(c->g_amin);
+    a.s_hi = ptr<float4>(c->s_hi);
+    a.s_q0 = ptr<float4>(c->s_q0);
+    a.s_q1 = ptr<float4>(c->s_q1);
+    a.lo2 = c->mac_lo2;
+    a.hi2 = c->mac_hi2;
+    a.tau = c->mac_tau;
+    const float e = (float)c->cfg.eps;
+    a.eps2 = e * e;
+    a.mac_cnt = ptr<unsigned long long>(c->mac_cnt);
+  }
+  c->walk_learned = learned;
+  WalkOut o;
+  o.cnt_e = ptr<uint32_t>(c->l_cnt_e);
+  o.cnt_s = ptr<uint32_t>(c->l_cnt_s);
+  o.off_e = &c->epj_off;
+  o.off_s = &c->spj_off;
+  o.epj = &c->epj;
+  o.spj = &c->spj;
+  if ((st = run_walk(c, a, learned ? kModeLearned : kModeTheta, o, ng))) return st;
+  c->n_epj = o.n_e;
+  c->n_spj = o.n_s;
+  c->interactions = o.inter;
+  return AFD_OK;
+}
+
+namespace {
+
+// Seeds of the neighbour walk: the maximal cells holding at most K particles
+// (and any larger leaf), which in depth-first order partition each system's
+// particles. A group's walk is split into one item per seed whose tight box
+// meets the group's search box; an item walks the seed's subtree, and the
+// items' lists, concatenated in seed order, are the group's list -- the
+// leaves a walk from the root would list, in the same order (a seed that
+// meets the box has ancestors that meet it too). A group whose box reaches
+// across the system so becomes many short walks instead of one long one.
+__global__ void k_seed_mark(int64_t n_cells, const uint32_t *__restrict__ count,
+                            const uint32_t *__restrict__ parent,
+                            const uint32_t *__restrict__ child, uint32_t K,
+                            uint32_t *__restrict__ flag) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_cells) return;
+  const uint32_t cn = count[c], p = parent[c];
+  bool leaf = true;
+#pragma unroll
+  for (int o = 0; o < 8; o++) leaf = leaf && child[(size_t)c * 8 + o] == kNone;
+  flag[c] = ((cn <= K && (p == kNone || count[p] > K)) || (cn > K && leaf)) ? 1u : 0u;
+}
+
+__global__ void k_seed_fill(int64_t n_cells, const uint32_t *__restrict__ flag,
+                            const uint32_t *__restrict__ off, uint32_t *__restrict__ seeds) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < n_cells && flag[c]) seeds[off[c]] = (uint32_t)c;
+}
+
+// Union boxes of blocks of 32 consecutive seeds (one warp per block), the
+// first filter of k_items.
+__global__ void k_seed_blocks(uint32_t n_seeds, const uint32_t *__restrict__ seeds,
+                              const float4 *__restrict__ tbox, float4 *__restrict__ bbox) {
+  const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (b * 32 >= n_seeds) return;
+  const uint64_t k = (uint64_t)b * 32 + lane;
+  float4 lo = make_float4(INFINITY, INFINITY, INFINITY, 0.0f);
+  float4 hi = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.0f);
+  if (k < n_seeds) {
+    lo = tbox[(size_t)seeds[k] * 2];
+    hi = tbox[(size_t)seeds[k] * 2 + 1];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo.x = fminf(lo.x, __shfl_xor_sync(0xffffffffu, lo.x, o));
+    lo.y = fminf(lo.y, __shfl_xor_sync(0xffffffffu, lo.y, o));
+    lo.z = fminf(lo.z, __shfl_xor_sync(0xffffffffu, lo.z, o));
+    hi.x = fmaxf(hi.x, __shfl_xor_sync(0xffffffffu, hi.x, o));
+    hi.y = fmaxf(hi.y, __shfl_xor_sync(0xffffffffu, hi.y, o));
+    hi.z = fmaxf(hi.z, __shfl_xor_sync(0xffffffffu, hi.z, o));
+  }
+  if (lane == 0) {
+    bbox[b * 2] = make_float4(lo.x, lo.y, lo.z, 0.0f);
+    bbox[b * 2 + 1] = make_float4(hi.x, hi.y, hi.z, 0.0f);
+  }
+}
+
+__device__ __forceinline__ bool box_meets(float4 lo, float4 hi, const float *bmin,
+                                          const float *bmax) {
+  return lo.x <= bmax[0] && hi.x >= bmin[0] && lo.y <= bmax[1] && hi.y >= bmin[1] &&
+         lo.z <= bmax[2] && hi.z >= bmin[2];
+}
+
+struct ItemArgs {
+  int64_t n_groups;
+  const uint32_t *g_root, *skip, *seeds;
+  uint32_t n_seeds;
+  const float *sbox;
+  const float4 *tbox, *bbox;
+  uint32_t *cnt;                  // count pass: items per group
+  const uint32_t *off;            // fill pass: first item per group
+  uint32_t *it_group, *it_root;   // fill pass
+};
+
+__device__ __forceinline__ uint32_t lower_seed(const uint32_t *seeds, uint32_t n, uint32_t v) {
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (seeds[mid] < v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// One warp per group: the seeds of its system (cell ids in the root's
+// subtree range), their blocks' boxes tested 32 at a time and then the
+// seeds of each block that meets the search box; FILL writes the items in
+// seed order.
+template <bool FILL>
+__global__ void __launch_bounds__(256) k_items(ItemArgs a) {
+  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (g >= a.n_groups) return;
+  const uint32_t root = a.g_root[g];
+  const uint32_t s0 = lower_seed(a.seeds, a.n_seeds, root);
+  const uint32_t s1 = lower_seed(a.seeds, a.n_seeds, a.skip[root]);
+  float bmin[3], bmax[3];
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    bmin[k] = a.sbox[g * 6 + k];
+    bmax[k] = a.sbox[g * 6 + 3 + k];
+  }
+  uint32_t n = 0, o = FILL ? a.off[g] : 0u;
+  const uint32_t b0 = s0 / 32, b1 = (s1 + 31) / 32;
+  for (uint32_t bb = b0; bb < b1; bb += 32) {
+    const uint32_t bl = bb + lane;
+    const bool bmeet =
+        bl < b1 && box_meets(a.bbox[(size_t)bl * 2], a.bbox[(size_t)bl * 2 + 1], bmin, bmax);
+    unsigned bm = __ballot_sync(0xffffffffu, bmeet);
+    while (bm) {
+      const uint32_t blk = bb + (uint32_t)(__ffs(bm) - 1);
+      bm &= bm - 1;
+      const uint32_t k = blk * 32 + lane;
+      bool meet = false;
+      uint32_t sc = 0;
+      if (k >= s0 && k < s1) {
+        sc = a.seeds[k];
+        meet = box_meets(a.tbox[(size_t)sc * 2], a.tbox[(size_t)sc * 2 + 1], bmin, bmax);
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, meet);
+      if (FILL && meet) {
+        const uint32_t at = o + n + __popc(m & ((1u << lane) - 1u));
+        a.it_group[at] = (uint32_t)g;
+        a.it_root[at] = sc;
+      }
+      n += __popc(m);
+    }
+  }
+  if (!FILL && lane == 0) a.cnt[g] = n;
+}
+
+// Group offsets from the item offsets, and the candidate pairs
+// sum_g n_g * list length.
+__global__ void k_group_lists(int64_t n_groups, const uint32_t *__restrict__ item_off,
+                              const uint64_t *__restrict__ ioff,
+                              const uint32_t *__restrict__ g_count, uint64_t *__restrict__ off,
+                              unsigned long long *pairs) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long s = 0;
+  if (g < n_groups) {
+    const uint64_t b = ioff[item_off[g]], e = ioff[item_off[g + 1]];
+    off[g] = b;
+    if (g == n_groups - 1) off[n_groups] = e;
+    s = (unsigned long long)g_count[g] * (e - b);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(pairs, s);
+}
+
+inline unsigned nblocks256(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+}  // namespace
+
+int launch_nbr_walk(afd_ctx *c) {
+  const int64_t ng = c->n_groups, nc = c->n_cells;
+  int st;
+  if ((st = reserve(c->nbr_off, sizeof(uint64_t) * (ng + 1)))) return st;
+  if (ng == 0) {
+    c->n_nbr = c->nbr_pairs = 0;
+    cudaMemsetAsync(c->nbr_off.p, 0, sizeof(uint64_t), c->stream);
+    return cudaGetLastError() == cudaSuccess ? AFD_OK : AFD_ERR_CUDA;
+  }
+  uint32_t *pin = static_cast<uint32_t *>(c->pinned);
+  // seeds
+  const uint32_t K = (uint32_t)std::max<int64_t>(4 * (int64_t)c->cfg.n_grp, c->n / 256);
+  if ((st = reserve(c->nbr_seedf, sizeof(uint32_t) * (size_t)nc))) return st;
+  if ((st = reserve(c->nbr_seedo, sizeof(uint32_t) * (size_t)(nc + 1)))) return st;
+  k_seed_mark<<<nblocks256(nc), 256, 0, c->stream>>>(nc, ptr<uint32_t>(c->c_count),
+                                                     ptr<uint32_t>(c->c_parent),
+                                                     ptr<uint32_t>(c->c_child), K,
+                                                     ptr<uint32_t>(c->nbr_seedf));
+  c->launches++;
+  if ((st = scan_u32(c, ptr<uint32_t>(c->nbr_seedf), ptr<uint32_t>(c->nbr_seedo), nc))) return st;
+  if (cudaMemcpyAsync(pin, ptr<uint32_t>(c->nbr_seedo) + nc, sizeof(uint32_t),
+                      cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return AFD_ERR_CUDA;
+  const uint32_t n_seeds = pin[0];
+  if ((st = reserve(c->nbr_seeds, sizeof(uint32_t) * (size_t)n_seeds))) return st;
+  k_seed_fill<<<nblocks256(nc), 256, 0, c->stream>>>(nc, ptr<uint32_t>(c->nbr_seedf),
+                                                     ptr<uint32_t>(c->nbr_seedo),
+                                                     ptr<uint32_t>(c->nbr_seeds));
+  c->launches++;
+  const int64_t nsb = ((int64_t)n_seeds + 31) / 32;
+  if ((st = reserve(c->nbr_sbb, sizeof(float4) * 2 * (size_t)std::max<int64_t>(nsb, 1))))
+    return st;
+  if (nsb > 0) {
+    k_seed_blocks<<<nblocks256(nsb * 32), 256, 0, c->stream>>>(
+        n_seeds, ptr<uint32_t>(c->nbr_seeds), ptr<float4>(c->c_tbox), ptr<float4>(c->nbr_sbb));
+    c->launches++;
+  }
+  // items: per group the seeds its search box meets, in seed order
+  if ((st = reserve(c->nbr_icnt, sizeof(uint32_t) * (size_t)ng))) return st;
+  if ((st = reserve(c->nbr_igoff, sizeof(uint32_t) * (size_t)(ng + 1)))) return st;
+  ItemArgs ia;
+  ia.n_groups = ng;
+  ia.g_root = ptr<uint32_t>(c->g_root);
+  ia.skip = ptr<uint32_t>(c->c_skip);
+  ia.seeds = ptr<uint32_t>(c->nbr_seeds);
+  ia.n_seeds = n_seeds;
+  ia.sbox = ptr<float>(c->g_sbox);
+  ia.tbox = ptr<float4>(c->c_tbox);
+  ia.bbox = ptr<float4>(c->nbr_sbb);
+  ia.cnt = ptr<uint32_t>(c->nbr_icnt);
+  ia.off = ptr<uint32_t>(c->nbr_igoff);
+  ia.it_group = ia.it_root = nullptr;
+  k_items<false><<<nblocks256(ng * 32), 256, 0, c->stream>>>(ia);
+  c->launches++;
+  if ((st = scan_u32(c, ia.cnt, ptr<uint32_t>(c->nbr_igoff), ng))) return st;
+  if (cudaMemcpyAsync(pin, ptr<uint32_t>(c->nbr_igoff) + ng, sizeof(uint32_t),
+                      cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return AFD_ERR_CUDA;
+  const int64_t ni = pin[0];
+  if ((st = reserve(c->nbr_itg, sizeof(uint32_t) * (size_t)std::max<int64_t>(ni, 1)))) return st;
+  if ((st = reserve(c->nbr_itr, sizeof(uint32_t) * (size_t)std::max<int64_t>(ni, 1)))) return st;
+  ia.it_group = ptr<uint32_t>(c->nbr_itg);
+  ia.it_root = ptr<uint32_t>(c->nbr_itr);
+  k_items<true><<<nblocks256(ng * 32), 256, 0, c->stream>>>(ia);
+  c->launches++;
+  if (cudaGetLastError() != cudaSuccess) return AFD_ERR_CUDA;
+  // the walk over the items, into per-item CSR lists = per-group lists
+  if ((st = reserve(c->nbr_cnt, sizeof(uint32_t) * 2 * (size_t)std::max<int64_t>(ni, 1))))
+    return st;
+  if ((st = reserve(c->nbr_ioff, sizeof(uint64_t) * (size_t)(ni + 1)))) return st;
+  if ((st = walk_scratch(c, ni))) return st;
+  unsigned long long *pairs = ptr<unsigned long long>(c->u64acc) + 3;
+  if (cudaMemsetAsync(pairs, 0, sizeof(unsigned long long), c->stream) != cudaSuccess)
+    return AFD_ERR_CUDA;
+  uint64_t n_e = 0;
+  if (ni > 0) {
+    WalkArgs a = base_args(c);
+    a.boxf = ptr<float>(c->g_sbox);
+    a.tbox = ptr<float4>(c->c_tbox);
+    a.nblk = ptr<float4>(c->nbr_blk);
+    a.it_group = ia.it_group;
+    a.it_root = ia.it_root;
+    WalkOut o;
+    o.cnt_e = ptr<uint32_t>(c->nbr_cnt);
+    o.cnt_s = ptr<uint32_t>(c->nbr_cnt) + ni;
+    o.off_e = &c->nbr_ioff;
+    o.off_s = nullptr;
+    o.epj = &c->nbr;
+    o.spj = nullptr;
+    if ((st = run_walk(c, a, kModeNeighbour, o, ni))) return st;
+    n_e = o.n_e;
+  } else if (cudaMemsetAsync(c->nbr_ioff.p, 0, sizeof(uint64_t), c->stream) != cudaSuccess) {
+    return AFD_ERR_CUDA;
+  }
+  k_group_lists<<<nblocks256(ng), 256, 0, c->stream>>>(
+      ng, ptr<uint32_t>(c->nbr_igoff), ptr<uint64_t>(c->nbr_ioff), ptr<uint32_t>(c->g_count),
+      ptr<uint64_t>(c->nbr_off), pairs);
+  c->launches++;
+  uint64_t *pin64 = static_cast<uint64_t *>(c->pinned);
+  if (cudaMemcpyAsync(pin64, pairs, sizeof(uint64_t), cudaMemcpyDeviceToHost, c->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return AFD_ERR_CUDA;
+  c->n_nbr = n_e;
+  c->nbr_pairs = pin64[0];
+  return AFD_OK;
 }
 
 }  // namespace afd
