@@ -20,25 +20,26 @@
 //
 // Density (k_density). Work item = (force work unit, segment of at most
 // kSegLen list entries): a unit is a group's chunk of up to 32 particles (a
-// chunk of r <= 16 splits the warp into S = 2 or 4 j-streams, lane = stream
-// * (32 / S) + particle, as in the force kernel), and long lists -- sparse
-// outer groups whose search boxes reach far -- are spread over several
-// warps. One warp per item walks its segment 32 entries at a time: each lane
-// gathers one j by index (hi/lo float4 pair) one chunk ahead, forms its
-// coordinates relative to the group's first particle and stages them with
-// the mass in shared memory (two buffers, one __syncwarp per chunk; entries
-// past the end are padded far away and massless; coordinates in separate
-// arrays, each j-stream's entries consecutive). Every lane then tests its
-// i against the chunk's j's of its stream four at a time -- two 16-byte
-// loads per coordinate give two packed f32x2 pairs; r^2 and q^2 = r^2 / h_i^2
-// are 7 FP32 operations per pair in 3.5 issue slots -- and evaluates the
-// spline for the four only when one of them has q^2 < 1: 1 / h_i and
-// 8 / (pi h_i^3) in FP32, q by one sqrt.approx, 1 + 6 q^2 (q - 1) below
-// q = 1/2 and 2 (1 - q)^3 above. Sums per chunk, chunk sums added to the
-// item's totals, then across streams. A unit of one segment writes its
-// particles' results; a unit of several writes partial sums per item, which
-// k_density_fin adds in segment order -- the result does not depend on
-// scheduling.
+// chunk of r <= 16 splits the warp into S = 2 or 4 j-streams, lane = stream *
+// (32 / S) + particle, as in the force kernel), and long lists -- sparse outer
+// groups whose search boxes reach far -- are spread over several warps. One
+// warp per item walks its segment 32 entries at a time: each lane gathers one
+// j by index (hi/lo float4 pair) one chunk ahead and forms its coordinates
+// relative to the group's first particle; the entries inside the unit's reach
+// box (x_i -+ h_i over the unit's particles: the group's list is made for the
+// whole group's search box) are staged with their masses in shared memory,
+// compacted, the rest of the chunk padded far away and massless (two buffers,
+// one __syncwarp per chunk; coordinates in separate arrays, each j-stream's
+// entries consecutive). Every lane then tests its i against the chunk's j's of
+// its stream four at a time -- two 16-byte loads per coordinate give two
+// packed f32x2 pairs; r^2 and q^2 = r^2 / h_i^2 are 7 FP32 operations per pair
+// in 3.5 issue slots -- and evaluates the spline for the four only when one of
+// them has q^2 < 1: 1 / h_i and 8 / (pi h_i^3) in FP32, q by one sqrt.approx,
+// w = 2 ((1 - q)^3 - 4 max(1/2 - q, 0)^3) in packed arithmetic. Sums per
+// chunk, chunk sums added to the item's totals, then across streams. A unit of
+// one segment writes its particles' results; a unit of several writes partial
+// sums per item, which k_density_fin adds in segment order -- the result does
+// not depend on scheduling.
 #include <cfloat>
 #include <cmath>
 #include <cstring>
@@ -215,22 +216,18 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   return r;
 }
 
-// w of the spline for two pairs from their q^2 (clamped to 1 by the caller,
-// so that pairs beyond the support give w = 0) in packed arithmetic:
-// u = 1 - q, 2 u^3 above q = 1/2 and 1 - 6 q^2 u below; raw0 / raw1 are the
-// unclamped q^2 that pick the piece.
-__device__ __forceinline__ void spline_w2(float c0, float c1, float raw0, float raw1, float &w0,
-                                          float &w1) {
-  const f2 one = pk(1.0f, 1.0f), m6 = pk(-6.0f, -6.0f);
-  const f2 C = pk(c0, c1);
-  const f2 U = sub2(one, pk(sqrt_approx(c0), sqrt_approx(c1)));
-  const f2 wo = mul2(mul2(U, U), add2(U, U));
-  const f2 wi = fma2(mul2(C, m6), U, one);
-  float o0, o1, i0, i1;
-  upk(wo, o0, o1);
-  upk(wi, i0, i1);
-  w0 = raw0 < 0.25f ? i0 : o0;
-  w1 = raw1 < 0.25f ? i1 : o1;
+// w / 2 of the spline for two pairs from their q^2 clamped to 1 (so that
+// pairs beyond the support give 0), in packed arithmetic: with
+// u = 1 - q and v = max(1/2 - q, 0), w = 2 (u^3 - 4 v^3), which is
+// 1 - 6 q^2 + 6 q^3 for q <= 1/2 and 2 (1 - q)^3 above; the factor 2 is
+// applied to the sums.
+__device__ __forceinline__ f2 spline_half2(float c0, float c1) {
+  const f2 one = pk(1.0f, 1.0f), m4 = pk(-4.0f, -4.0f);
+  const float q0 = sqrt_approx(c0), q1 = sqrt_approx(c1);
+  const f2 U = sub2(one, pk(q0, q1));
+  const f2 V = pk(fmaxf(0.5f - q0, 0.0f), fmaxf(0.5f - q1, 0.0f));
+  const f2 U3 = mul2(mul2(U, U), U), V3 = mul2(mul2(V, V), V);
+  return fma2(V3, m4, U3);
 }
 
 // Density work item = (force work unit, segment of at most kSegLen list
@@ -263,7 +260,7 @@ struct DensArgs {
 struct IParticle {
   uint32_t i, oi;
   bool act, bad;
-  float xi, yi, zi, hinv, hinv2;
+  float xi, yi, zi, h, hinv, hinv2;
   float4 oh, ol;
 };
 
@@ -285,16 +282,18 @@ __device__ __forceinline__ IParticle i_particle(const DensArgs &a, uint32_t g, u
   double hh = a.h[r.oi];
   r.bad = !radius_ok(hh);
   if (r.bad) hh = 1.0;
-  r.hinv = __frcp_rn(__double2float_rn(hh));
+  r.h = __double2float_rn(hh);
+  r.hinv = __frcp_rn(r.h);
   r.hinv2 = r.hinv * r.hinv;
   return r;
 }
 
 __device__ __forceinline__ void density_out(const DensArgs &a, const IParticle &ip, float tm,
                                             float tw) {
-  const float eight_over_pi = 2.546479089470325f;  // 8 / pi
-  a.rho[ip.oi] = ip.bad ? NAN : eight_over_pi * (ip.hinv2 * ip.hinv) * tm;
-  if (a.nnb) a.nnb[ip.oi] = ip.bad ? NAN : (32.0f / 3.0f) * tw;
+  // tm, tw are the sums of m_j w / 2 and w / 2
+  const float sixteen_over_pi = 5.092958178940651f;  // 2 x 8 / pi
+  a.rho[ip.oi] = ip.bad ? NAN : sixteen_over_pi * (ip.hinv2 * ip.hinv) * tm;
+  if (a.nnb) a.nnb[ip.oi] = ip.bad ? NAN : (64.0f / 3.0f) * tw;
   if (ip.bad) atomicOr(a.status, kStBadRadius);
 }
 
@@ -331,15 +330,54 @@ __device__ __forceinline__ void density_item(const DensArgs &a, DensStage &st, i
     ph = a.jhi[j];
     pl = a.jlo[j];
   }
+  // the unit's reach box: x_i -+ h_i over its particles, widened by a
+  // relative 1e-5 (rounding slack; a pair dropped by it has q > 1 - 1e-5,
+  // where w < 1e-14)
+  float rb[6];
+  {
+    const bool use = ip.act && !ip.bad;
+    const float hr = use ? ip.h * 1.00001f : 0.0f;
+    rb[0] = use ? ip.xi - hr : INFINITY;
+    rb[1] = use ? ip.yi - hr : INFINITY;
+    rb[2] = use ? ip.zi - hr : INFINITY;
+    rb[3] = use ? ip.xi + hr : -INFINITY;
+    rb[4] = use ? ip.yi + hr : -INFINITY;
+    rb[5] = use ? ip.zi + hr : -INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int d = 0; d < 3; d++) {
+        rb[d] = fminf(rb[d], __shfl_xor_sync(0xffffffffu, rb[d], o));
+        rb[3 + d] = fmaxf(rb[3 + d], __shfl_xor_sync(0xffffffffu, rb[3 + d], o));
+      }
+  }
+  const unsigned lt = (1u << lane) - 1u;
   float tm = 0.0f, tw = 0.0f;
   int buf = 0;
   for (uint64_t base = b0; base < b1; base += 32) {
-    // stage this chunk (relative coordinates, mass; pads far away, massless)
-    const bool in = base + lane < b1;
-    st.x[buf][slot] = in ? __fadd_rn(__fsub_rn(ph.x, ip.oh.x), __fsub_rn(pl.x, ip.ol.x)) : kFar;
-    st.y[buf][slot] = in ? __fadd_rn(__fsub_rn(ph.y, ip.oh.y), __fsub_rn(pl.y, ip.ol.y)) : kFar;
-    st.z[buf][slot] = in ? __fadd_rn(__fsub_rn(ph.z, ip.oh.z), __fsub_rn(pl.z, ip.ol.z)) : kFar;
-    st.m[buf][slot] = in ? ph.w : 0.0f;
+    // stage the chunk's entries that reach the unit, compacted (relative
+    // coordinates, mass), and pad the rest far away and massless
+    const float rx = __fadd_rn(__fsub_rn(ph.x, ip.oh.x), __fsub_rn(pl.x, ip.ol.x));
+    const float ry = __fadd_rn(__fsub_rn(ph.y, ip.oh.y), __fsub_rn(pl.y, ip.ol.y));
+    const float rz = __fadd_rn(__fsub_rn(ph.z, ip.oh.z), __fsub_rn(pl.z, ip.ol.z));
+    const bool keep = base + lane < b1 && rx >= rb[0] && rx <= rb[3] && ry >= rb[1] &&
+                      ry <= rb[4] && rz >= rb[2] && rz <= rb[5];
+    const unsigned km = __ballot_sync(0xffffffffu, keep);
+    const int nkeep = __popc(km);
+    if (keep) {
+      const int e = __popc(km & lt);
+      const int sl = (e % S) * W + e / S;
+      st.x[buf][sl] = rx;
+      st.y[buf][sl] = ry;
+      st.z[buf][sl] = rz;
+      st.m[buf][sl] = ph.w;
+    }
+    if (lane >= nkeep) {
+      st.x[buf][slot] = kFar;
+      st.y[buf][slot] = kFar;
+      st.z[buf][slot] = kFar;
+      st.m[buf][slot] = 0.0f;
+    }
     __syncwarp();
     // the next chunk's gather, in flight while this one is evaluated
     const uint64_t nx = base + 32 + lane;
@@ -350,9 +388,10 @@ __device__ __forceinline__ void density_item(const DensArgs &a, DensStage &st, i
       ph = a.jhi[j];
       pl = a.jlo[j];
     }
-    float cm = 0.0f, cw = 0.0f;
-#pragma unroll
-    for (int k = 0; k < W; k += 4) {
+    f2 cm2 = pk(0.0f, 0.0f), cw2 = cm2;  // per chunk, halves of the sums in two lanes
+    // each stream's kept entries, four at a time (the pads make up the last four)
+    const int kk = (((nkeep + S - 1) / S) + 3) & ~3;
+    for (int k = 0; k < kk; k += 4) {
       const ulonglong2 xs = *reinterpret_cast<const ulonglong2 *>(&st.x[buf][s * W + k]);
       const ulonglong2 ys = *reinterpret_cast<const ulonglong2 *>(&st.y[buf][s * W + k]);
       const ulonglong2 zs = *reinterpret_cast<const ulonglong2 *>(&st.z[buf][s * W + k]);
@@ -364,19 +403,19 @@ __device__ __forceinline__ void density_item(const DensArgs &a, DensStage &st, i
       upk(q0, qa, qb);
       upk(q1, qc, qd);
       if (fminf(fminf(qa, qb), fminf(qc, qd)) < 1.0f) {  // one of the four is inside
-        const float4 ms = *reinterpret_cast<const float4 *>(&st.m[buf][s * W + k]);
-        float wa, wb, wc, wd;
-        spline_w2(fminf(qa, 1.0f), fminf(qb, 1.0f), qa, qb, wa, wb);
-        spline_w2(fminf(qc, 1.0f), fminf(qd, 1.0f), qc, qd, wc, wd);
-        cm = fmaf(ms.x, wa, cm);
-        cm = fmaf(ms.y, wb, cm);
-        cm = fmaf(ms.z, wc, cm);
-        cm = fmaf(ms.w, wd, cm);
-        cw += (wa + wb) + (wc + wd);
+        const ulonglong2 ms = *reinterpret_cast<const ulonglong2 *>(&st.m[buf][s * W + k]);
+        const f2 w01 = spline_half2(fminf(qa, 1.0f), fminf(qb, 1.0f));
+        const f2 w23 = spline_half2(fminf(qc, 1.0f), fminf(qd, 1.0f));
+        cm2 = fma2(ms.x, w01, cm2);
+        cm2 = fma2(ms.y, w23, cm2);
+        cw2 = add2(cw2, add2(w01, w23));
       }
     }
-    tm += cm;
-    tw += cw;
+    float m0, m1, w0, w1;
+    upk(cm2, m0, m1);
+    upk(cw2, w0, w1);
+    tm += m0 + m1;
+    tw += w0 + w1;
     buf ^= 1;
   }
 #pragma unroll

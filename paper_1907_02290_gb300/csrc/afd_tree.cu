@@ -31,6 +31,28 @@ inline unsigned blocks_for(int64_t n, int threads = kThreads) {
 // ---------------------------------------------------------------------------
 constexpr int kRootBlocks = 608;
 
+// Order-preserving 64-bit key of a double (for finite values: a < b iff
+// key(a) < key(b), except that -0 sorts below +0): min / max of positions
+// on the integer pipes, exact, instead of on GB300's narrow FP64 pipe.
+__device__ __forceinline__ unsigned long long okey(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return b ^ ((unsigned long long)((long long)b >> 63) | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double okey_value(unsigned long long k) {
+  const unsigned long long b = (k & 0x8000000000000000ull) ? (k ^ 0x8000000000000000ull) : ~k;
+  return __longlong_as_double((long long)b);
+}
+__device__ __forceinline__ unsigned long long warp_min_key(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ unsigned long long warp_max_key(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
 __device__ __forceinline__ double warp_min(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -49,7 +71,7 @@ __global__ void __launch_bounds__(kThreads) k_root(const double *__restrict__ x,
                                                    double *__restrict__ part,
                                                    unsigned *__restrict__ counter,
                                                    double *__restrict__ root, int *status) {
-  double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+  unsigned long long klo[3] = {~0ull, ~0ull, ~0ull}, khi[3] = {0ull, 0ull, 0ull};
   int bad = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -59,17 +81,21 @@ __global__ void __launch_bounds__(kThreads) k_root(const double *__restrict__ x,
 #pragma unroll
     for (int d = 0; d < 3; d++) {
       bad |= !isfinite(v[d]);
-      lo[d] = fmin(lo[d], v[d]);
-      hi[d] = fmax(hi[d], v[d]);
+      const unsigned long long k = okey(v[d]);
+      klo[d] = min(klo[d], k);
+      khi[d] = max(khi[d], k);
     }
   }
   __shared__ double sh[kThreads / 32][6];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double lo[3], hi[3];
 #pragma unroll
   for (int d = 0; d < 3; d++) {
-    lo[d] = warp_min(lo[d]);
-    hi[d] = warp_max(hi[d]);
+    // a thread without particles keeps the neutral keys, which decode to
+    // NaN; the other lanes' values win the reduction (n > 0 here)
+    lo[d] = okey_value(warp_min_key(klo[d]));
+    hi[d] = okey_value(warp_max_key(khi[d]));
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, kStNonFinite);
   if (lane == 0)
@@ -800,17 +826,21 @@ __global__ void __launch_bounds__(kThreads) k_group_box(
   const int lane = threadIdx.x & 31;
   if (g >= n_groups) return;
   const uint32_t f = g_first[g], e = f + g_count[g];
-  double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+  unsigned long long klo[3] = {~0ull, ~0ull, ~0ull}, khi[3] = {0ull, 0ull, 0ull};
   for (uint32_t k = f + lane; k < e; k += 32) {
     const double v[3] = {xs[k], ys[k], zs[k]};
+#pragma unroll
     for (int d = 0; d < 3; d++) {
-      lo[d] = fmin(lo[d], v[d]);
-      hi[d] = fmax(hi[d], v[d]);
+      const unsigned long long q = okey(v[d]);
+      klo[d] = min(klo[d], q);
+      khi[d] = max(khi[d], q);
     }
   }
+  double lo[3], hi[3];
+#pragma unroll
   for (int d = 0; d < 3; d++) {
-    lo[d] = warp_min(lo[d]);
-    hi[d] = warp_max(hi[d]);
+    lo[d] = okey_value(warp_min_key(klo[d]));
+    hi[d] = okey_value(warp_max_key(khi[d]));
   }
   if (lane != 0) return;
   for (int d = 0; d < 3; d++) {

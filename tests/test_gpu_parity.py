@@ -173,6 +173,36 @@ def test_tiny_sizes(env, n):
     g.close()
 
 
+def test_signed_zero_coordinates(env):
+    """Coordinates of exactly -0.0 and +0.0 on every axis (the root and group
+    boxes take min / max on an order-preserving integer key of each double,
+    which orders -0 below +0 while the oracle keeps the first of two equal
+    values): the boxes compare equal, and everything the method decides is
+    the oracle's."""
+    _, _, orc = env
+    gen = np.random.default_rng(14)
+    q = ics.plummer(3000, 14)
+    n = q.n
+    pos = np.stack([q.x, q.y, q.z], 1)
+    # 30% of the particles get one or two coordinates of -0.0 or +0.0 (none
+    # sits at the centre, where the net force vanishes and its relative
+    # error means nothing)
+    sel = gen.random(n) < 0.3
+    for i in np.nonzero(sel)[0]:
+        axes = gen.choice(3, size=gen.integers(1, 3), replace=False)
+        pos[i, axes] = np.where(gen.random(len(axes)) < 0.5, -0.0, 0.0)
+    zeros = pos[pos == 0.0]
+    assert np.signbit(zeros).any() and (~np.signbit(zeros)).any()
+    m = q.m
+    p = ics.Particles(pos[:, 0], pos[:, 1], pos[:, 2], m * 0, m * 0, m * 0, m)
+    kw = dict(n_grp=32, theta=0.5, eps=1.0 / 64)
+    g, acc, _ = run_gpu(env, p, **kw)
+    t = orc.Tree(p.x, p.y, p.z, m, **kw)
+    check_structure(g, t)
+    assert rms_rel_acc(acc, t.force()) <= FORCE_RMS_TOL
+    g.close()
+
+
 def test_zero_softening(env):
     """eps = 0 takes the guarded kernel: coincident pairs contribute nothing."""
     _, _, orc = env
