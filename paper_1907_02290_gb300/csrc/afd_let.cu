@@ -4,11 +4,11 @@
 // box as the group box, puts on a list: accepted cells as superparticles
 // (COM, monopole) and the particles of opened leaves, in depth-first order.
 //
-// One warp walks the tree (the cells a step pops, up to 32, are decided in
-// parallel) and marks each exported cell; a scan over the cell ids -- the
-// depth-first pre-order -- then gives every exported element its position,
-// so the export comes out in depth-first order whatever order the walk
-// visited the cells in.
+// The walk reaches a cell iff it opens every ancestor, so the export is
+// marked without walking: one thread per cell tests the criterion on the
+// cell's ancestors (at most 21) and on the cell itself. A scan over the cell
+// ids -- the depth-first pre-order -- then gives every exported element its
+// position, so the export comes out in the walk's depth-first order.
 #include <cmath>
 
 #include "afd_internal.cuh"
@@ -16,16 +16,13 @@
 namespace afd {
 namespace {
 
-constexpr int kLetStack = 8192;  // cell ids on the walking warp's stack
-
 struct LetArgs {
   float bmin[3], bmax[3], theta2;
   const float4 *node_f;
   const uint2 *node_i;
-  const uint32_t *child;
+  const uint32_t *parent;
   uint32_t *mark;  // per cell: 0 no, 1 superparticle, 2 leaf particles
-  int *status;
-  uint32_t iter_cap, n_cells;
+  uint32_t n_cells;
 };
 
 __device__ __forceinline__ float let_sep(float c, float lo, float hi) {
@@ -35,66 +32,36 @@ __device__ __forceinline__ float let_sep(float c, float lo, float hi) {
   return d;
 }
 
-__global__ void __launch_bounds__(32) k_let_mark(LetArgs a) {
-  __shared__ uint32_t stk[kLetStack];
-  const int lane = threadIdx.x;
-  if (lane == 0) stk[0] = 0u;  // the root
-  int sp = 1;
-  uint32_t iters = 0;
-  __syncwarp();
-  while (sp > 0) {
-    if (++iters > a.iter_cap) {
-      if (lane == 0) atomicOr(a.status, kStWalkIter);
-      break;
+// The opening criterion of the walk (theta, the box as the group box).
+__device__ __forceinline__ bool let_accept(const LetArgs &a, uint32_t c) {
+  const float4 nf = a.node_f[c];
+  const float dx = let_sep(nf.x, a.bmin[0], a.bmax[0]);
+  const float dy = let_sep(nf.y, a.bmin[1], a.bmax[1]);
+  const float dz = let_sep(nf.z, a.bmin[2], a.bmax[2]);
+  float d2 = __fmul_rn(dx, dx);
+  d2 = __fadd_rn(d2, __fmul_rn(dy, dy));
+  d2 = __fadd_rn(d2, __fmul_rn(dz, dz));
+  return nf.w < __fmul_rn(a.theta2, d2);
+}
+
+// One thread per cell. The walk reaches a cell iff it opens every ancestor,
+// i.e. accepts none of them; a reached cell is exported as a superparticle
+// if accepted, as its particles if a leaf (mark 1, 2; 0 otherwise).
+__global__ void __launch_bounds__(256) k_let_mark(LetArgs a) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)a.n_cells) return;
+  const uint32_t c = (uint32_t)t;
+  uint32_t p = a.parent[c];
+  for (int up = 0; p != kNone && up <= kLevels; up++) {
+    if (!AFD_IN(p, a.n_cells, "let parent")) break;
+    if (let_accept(a, p)) {
+      a.mark[c] = 0u;
+      return;
     }
-    const int nv = sp < 32 ? sp : 32;
-    uint32_t c = lane < nv ? stk[sp - 1 - lane] : 0u;
-    bool open = false;
-    if (lane < nv && AFD_IN(c, a.n_cells, "let cell")) {
-      const float4 nf = a.node_f[c];
-      const uint2 ni = a.node_i[c];
-      const bool leaf = (ni.y >> 31) != 0;
-      // the opening criterion of the walk (theta, the box as the group box)
-      const float dx = let_sep(nf.x, a.bmin[0], a.bmax[0]);
-      const float dy = let_sep(nf.y, a.bmin[1], a.bmax[1]);
-      const float dz = let_sep(nf.z, a.bmin[2], a.bmax[2]);
-      float d2 = __fmul_rn(dx, dx);
-      d2 = __fadd_rn(d2, __fmul_rn(dy, dy));
-      d2 = __fadd_rn(d2, __fmul_rn(dz, dz));
-      if (nf.w < __fmul_rn(a.theta2, d2)) a.mark[c] = 1u;
-      else if (leaf) a.mark[c] = 2u;
-      else open = true;
-    }
-    uint32_t ch[8];
-    uint32_t nch = 0;
-    if (open) {
-      const uint4 c0 = reinterpret_cast<const uint4 *>(a.child)[2 * (size_t)c];
-      const uint4 c1 = reinterpret_cast<const uint4 *>(a.child)[2 * (size_t)c + 1];
-      const uint32_t all[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
-#pragma unroll
-      for (int o = 0; o < 8; o++)
-        if (all[o] != kNone) ch[nch++] = all[o];
-    }
-    uint32_t inc = nch;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += t;
-    }
-    const uint32_t K = __shfl_sync(0xffffffffu, inc, 31);
-    const int spn = sp - nv;
-    if (spn + (int)K > kLetStack) {
-      if (lane == 0) atomicOr(a.status, kStWalkStack);
-      break;
-    }
-    __syncwarp();
-    const uint32_t o0 = inc - nch;
-#pragma unroll
-    for (int o = 0; o < 8; o++)
-      if ((uint32_t)o < nch) stk[spn + o0 + o] = ch[o];
-    sp = spn + (int)K;
-    __syncwarp();
+    p = a.parent[p];
   }
+  const bool leaf = (a.node_i[c].y >> 31) != 0;
+  a.mark[c] = let_accept(a, c) ? 1u : (leaf ? 2u : 0u);
 }
 
 // Elements per cell: 1 for a superparticle, the particle count for a leaf.
@@ -173,8 +140,6 @@ extern "C" int afd_let_export(afd_ctx *c, const double *box, double theta, int64
       (st = reserve(c->let_cnt, sizeof(uint32_t) * (size_t)nc)) ||
       (st = reserve(c->let_off, sizeof(uint64_t) * (size_t)(nc + 1))))
     return st;
-  if (cudaMemsetAsync(c->let_mark.p, 0, sizeof(uint32_t) * (size_t)nc, c->stream) != cudaSuccess)
-    return AFD_ERR_CUDA;
   LetArgs a;
   for (int k = 0; k < 3; k++) {
     a.bmin[k] = (float)box[k];
@@ -184,13 +149,11 @@ extern "C" int afd_let_export(afd_ctx *c, const double *box, double theta, int64
   a.theta2 = th * th;
   a.node_f = ptr<float4>(c->node_f);
   a.node_i = ptr<uint2>(c->node_i);
-  a.child = ptr<uint32_t>(c->c_child);
+  a.parent = ptr<uint32_t>(c->c_parent);
   a.mark = ptr<uint32_t>(c->let_mark);
-  a.status = ptr<int>(c->status);
-  a.iter_cap = (uint32_t)(nc + 64);
   a.n_cells = (uint32_t)nc;
-  k_let_mark<<<1, 32, 0, c->stream>>>(a);
   const unsigned nb = (unsigned)((nc + 255) / 256);
+  k_let_mark<<<nb, 256, 0, c->stream>>>(a);
   k_let_count<<<nb, 256, 0, c->stream>>>(nc, a.mark, ptr<uint32_t>(c->c_count),
                                          ptr<uint32_t>(c->let_cnt));
   c->launches += 2;
