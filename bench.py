@@ -552,6 +552,24 @@ def sph_study(wl, afd, torch, np, dev, stream, ev, T, p):
         td = float(np.median(t_dens))
         pairs_s = st["pairs"] / (td * 1e-3)
         peak_ops = SMS * FP32_LANES * mhz * 1e6
+        # lists kept over steps (Section 4.2): made with a margin of a tenth of
+        # the median radius, then reusing steps = reorder + density
+        reuse = None
+        if n_grp in (128, 256):
+            skin = 0.1 * float(h.median().item())
+            afd.afd_make_neighbour_lists(g.ctx, h, skin)
+            st_s = afd.afd_neighbour_stats(g.ctx)
+            t_re = []
+            for rep in range(6):
+                e0 = ev()
+                afd.afd_reuse_lists(g.ctx, *xs)
+                afd.afd_calc_density(g.ctx, h, rho, nnb)
+                e1 = ev()
+                e1.synchronize()
+                if rep:
+                    t_re.append(e0.elapsed_time(e1))
+            reuse = {"skin": skin, "candidate_pairs": st_s["pairs"],
+                     "reusing_step_ms": float(np.median(t_re))}
         print(json.dumps({
             "sweep": "sph_density", "workload": wl["name"], "n_nb_target": 64, "n_grp": n_grp,
             "groups": gs["n_groups"], "tree_ms": float(np.median(t_tree)),
@@ -565,7 +583,8 @@ def sph_study(wl, afd, torch, np, dev, stream, ev, T, p):
                          "achieved_ops_per_s": pairs_s * DENSITY_OPS_PER_PAIR,
                          "peak_ops_per_s": peak_ops,
                          "frac": pairs_s * DENSITY_OPS_PER_PAIR / peak_ops,
-                         "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x {mhz:.0f} MHz"}}),
+                         "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x {mhz:.0f} MHz"},
+            "lists_kept": reuse}),
               flush=True)
         g.close()
 

@@ -125,7 +125,13 @@ int afd_make_interaction_lists(afd_ctx *ctx, int mode);
 /* Reusing step (Section 4.2): keep the topology, groups and lists; reorder
  * the new particle data with the saved permutation and recompute the cell
  * moments bottom-up. x, y, z, m: device doubles, same n as the saved tree.
- * Does not synchronise. AFD_ERR_NO_SAVED_LIST without lists kept for reuse. */
+ * With neighbour lists kept but no interaction lists made for reuse, only
+ * the particles are reordered (the density needs nothing else); the moments
+ * are then recomputed by the next call that reads them (a list walk, the
+ * local essential tree export, learned-criterion sampling). Interaction
+ * lists made with AFD_MAKE_LIST end here. Does not synchronise.
+ * AFD_ERR_NO_SAVED_LIST without interaction lists kept for reuse or
+ * neighbour lists. */
 int afd_reuse_lists(afd_ctx *ctx, const double *x, const double *y, const double *z,
                     const double *m);
 

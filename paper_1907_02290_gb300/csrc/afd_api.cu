@@ -162,7 +162,13 @@ int reuse(afd_ctx *c, const double *x, const double *y, const double *z, const d
   if (c->n > 0 && (!x || !y || !z || !m)) return AFD_ERR_ARG;
   if (!c->saved) c->have_lists = false;  // gravity lists not made for reuse end here
   TRY(launch_reorder(c, x, y, z, m, c->n));
-  TRY(launch_moments(c, false, false));  // lists are kept: no criterion runs
+  if (c->have_lists) {
+    TRY(launch_moments(c, false, false));  // lists are kept: no criterion runs
+  } else {
+    // only neighbour lists are kept, and the density needs positions alone:
+    // the moments wait until something reads them
+    c->moments_current = c->blocks_current = c->q_current = false;
+  }
   return AFD_OK;
 }
 

@@ -171,6 +171,7 @@ struct afd_ctx {
   float mac_lo2 = 0.0f, mac_hi2 = 0.0f, mac_tau = 0.0f;
   afd::DevBuf amag, amag_s, g_amin;
   int64_t amag_n = -1;
+  bool moments_current = false;  // the cell moments match the current positions
   bool q_current = false;       // the cell quadrupoles match the current positions
   bool blocks_current = false;  // the walk's child records match them too
   bool walk_learned = false;  // the last walk used the learned criterion

@@ -135,7 +135,9 @@ extern "C" int afd_let_export(afd_ctx *c, const double *box, double theta, int64
   *n_out = 0;
   const int64_t nc = c->n_cells;
   if (nc == 0) return AFD_OK;
-  int st;  // (node_f, node_i hold the current moments after reusing steps too)
+  int st;
+  // after reusing steps that kept only neighbour lists the moments lag
+  if (!c->moments_current && (st = launch_moments(c, false, false))) return st;
   if ((st = reserve(c->let_mark, sizeof(uint32_t) * (size_t)nc)) ||
       (st = reserve(c->let_cnt, sizeof(uint32_t) * (size_t)nc)) ||
       (st = reserve(c->let_off, sizeof(uint64_t) * (size_t)(nc + 1))))

@@ -1068,6 +1068,7 @@ int launch_moments(afd_ctx *c, bool child_blocks, bool need_q) {
   // quadrupoles for the far field, and (construction steps) for the learned
   // opening criterion; without either they are zero in the exports
   const bool quad_on = c->cfg.multipole || need_q;
+  c->moments_current = true;
   c->q_current = quad_on;
   c->blocks_current = child_blocks;
   if (!quad_on && !c->cfg.mac) {

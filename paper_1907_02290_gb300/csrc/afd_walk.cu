@@ -791,7 +791,8 @@ int launch_walk(afd_ctx *c) {
   if ((st = walk_scratch(c, ng))) return st;
   // after reusing steps the walk records, group boxes (and quadrupoles) lag
   // the particles: refresh them before walking
-  if (c->n_cells > 0 && (!c->blocks_current || (c->cfg.mac && !c->q_current))) {
+  if (c->n_cells > 0 &&
+      (!c->moments_current || !c->blocks_current || (c->cfg.mac && !c->q_current))) {
     if ((st = launch_moments(c, true, c->cfg.mac != 0))) return st;
     if ((st = launch_group_boxes(c))) return st;
   }

@@ -256,3 +256,45 @@ def test_full_size_density_on_sampled_particles(env):
         assert np.all(np.diff(lst.astype(np.int64)) > 0)
         assert np.all(np.isin(np.arange(gf[k], gf[k] + gc[k]), lst))
     g.close()
+
+
+def test_moments_follow_a_neighbour_only_reuse(env):
+    """A reusing step that keeps only neighbour lists reorders the particles
+    and leaves the moments for later: interaction lists made afterwards, and
+    a local essential tree export, see the moved particles' moments -- the
+    oracle's update, relist and export on the same data."""
+    torch, afd, orc = env
+    p = ics.plummer(12000, 98)
+    h = ics.plummer_search_radii(p, 32)
+    kw = dict(theta=0.5, eps=1.0 / 256, n_grp=64)
+    g = afd.Gravity(afd.Config(**kw), 0, torch.cuda.current_stream())
+    X = [_T(torch, a) for a in (p.x, p.y, p.z, p.m)]
+    afd.afd_tree_build(g.ctx, *X)
+    g.neighbour_lists(_T(torch, h), 0.02)
+    gen = np.random.default_rng(8)
+    q = [v + gen.normal(0.0, 1e-3, p.n) for v in (p.x, p.y, p.z)]
+    afd.afd_reuse_lists(g.ctx, *(_T(torch, a) for a in q), X[3])
+    t = orc.Tree(p.x, p.y, p.z, p.m, **kw)
+    t.update(*q, p.m)
+    # the LET export reads the refreshed moments
+    box = [-0.3, -0.3, -0.3, 0.3, 0.3, 0.3]
+    lx, _, _, lm, lk = afd.afd_let_export(g.ctx, box, 0.5)
+    want = t.let_export(box, theta=0.5)
+    assert np.array_equal(lx.cpu().numpy(), want[0]) and np.array_equal(lm.cpu().numpy(), want[3])
+    # so do lists made now
+    afd.afd_make_interaction_lists(g.ctx, afd.AFD_MAKE_LIST)
+    acc = torch.empty(p.n, 4, dtype=torch.float32, device="cuda:0")
+    afd.afd_calc_force(g.ctx, acc)
+    torch.cuda.synchronize()
+    t.relist()
+    eo, e, so, sp = t.lists()
+    assert np.array_equal(g.export("epj_idx").astype(np.int64), e)
+    assert np.array_equal(g.export("spj_idx").astype(np.int64), sp)
+    from test_gpu_parity import rms_rel_acc
+    assert rms_rel_acc(acc.cpu().numpy().astype(np.float64), t.force()) <= 1e-6
+    # the density still reads the moved particles through the kept lists
+    rho = torch.empty(p.n, dtype=torch.float32, device="cuda:0")
+    g.density(_T(torch, h), rho)
+    r_ref, _ = orc.density_direct(*q, p.m, h)
+    assert _rel(rho.cpu().numpy().astype(np.float64), r_ref) <= RHO_TOL
+    g.close()
