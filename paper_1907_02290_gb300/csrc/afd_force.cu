@@ -27,6 +27,7 @@
 //
 // Per interaction: 3 FADD (dx), 3 FFMA (r^2), 1 MUFU.RSQ, 3 FMUL, 3 FFMA (a),
 // 1 FADD (phi) -- 23 flops by the paper's convention (Section 6.2, n_op).
+#include "afd_f32x2.cuh"
 #include "afd_internal.cuh"
 
 namespace afd {
@@ -71,37 +72,6 @@ __device__ __forceinline__ float rsqrt_fast(float x) {
   return r;
 }
 
-// ---- packed FP32 pairs (two lanes of work in one 64-bit register) ----
-typedef unsigned long long f2;
-
-__device__ __forceinline__ f2 pk(float a, float b) {
-  f2 r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-  return r;
-}
-__device__ __forceinline__ void upk(f2 v, float &a, float &b) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
-  f2 d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ f2 add2(f2 a, f2 b) {
-  f2 d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
-  f2 d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
-  f2 d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
 // One lane, one i-particle, two j's (an even and an odd slot of the chunk)
 // per packed instruction: 13 f32x2 operations and 2 MUFU.RSQ for two
 // interactions.

@@ -294,11 +294,21 @@ __device__ __forceinline__ uint64_t spread3(uint32_t v) {
   return x;
 }
 
-__device__ __forceinline__ uint32_t grid_coord(double v, double corner, double scale) {
-  const double t = floor(__dmul_rn(__dsub_rn(v, corner), scale));
-  if (!(t > 0.0)) return 0u;
-  if (t > 2097151.0) return 2097151u;
-  return (uint32_t)t;
+// clamp(floor((v - corner) * 2^s), 0, 2^21 - 1) with 2^s = 2^21 / L (L a
+// power of two, so the product is exact unless it underflows, and then it
+// is below 1): the difference in FP64, its integer part from its exponent
+// and mantissa on the integer pipes (GB300's FP64 rate is low).
+__device__ __forceinline__ uint32_t grid_coord(double v, double corner, int s) {
+  const double d = __dsub_rn(v, corner);
+  if (!(d > 0.0)) return 0u;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const int e = (int)((b >> 52) & 0x7ffu);
+  if (e == 0) return 0u;          // subnormal: the product is below 1
+  const int k = e - 1023 + s;     // d * 2^s = 1.m x 2^k
+  if (k < 0) return 0u;
+  if (k >= 21) return 2097151u;
+  const unsigned long long mant = (b & 0xfffffffffffffull) | (1ull << 52);
+  return (uint32_t)(mant >> (52 - k));
 }
 
 __global__ void __launch_bounds__(kThreads) k_keys(const double *__restrict__ x,
@@ -313,10 +323,11 @@ __global__ void __launch_bounds__(kThreads) k_keys(const double *__restrict__ x,
   const double *root = roots + (sys_of ? 4 * (size_t)sys_of[i] : 0);
   const double L = root[3];
   const double half = __dmul_rn(L, 0.5);
-  const double scale = __ddiv_rn(2097152.0, L);
-  const uint32_t qx = grid_coord(x[i], __dsub_rn(root[0], half), scale);
-  const uint32_t qy = grid_coord(y[i], __dsub_rn(root[1], half), scale);
-  const uint32_t qz = grid_coord(z[i], __dsub_rn(root[2], half), scale);
+  // 2^21 / L = 2^s: L = 2^(e_L - 1023)
+  const int s = 1044 - (int)(((unsigned long long)__double_as_longlong(L) >> 52) & 0x7ffu);
+  const uint32_t qx = grid_coord(x[i], __dsub_rn(root[0], half), s);
+  const uint32_t qy = grid_coord(y[i], __dsub_rn(root[1], half), s);
+  const uint32_t qz = grid_coord(z[i], __dsub_rn(root[2], half), s);
   keys[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
   perm[i] = (uint32_t)i;
 }
