@@ -298,3 +298,25 @@ def test_moments_follow_a_neighbour_only_reuse(env):
     r_ref, _ = orc.density_direct(*q, p.m, h)
     assert _rel(rho.cpu().numpy().astype(np.float64), r_ref) <= RHO_TOL
     g.close()
+
+
+@pytest.mark.parametrize("h_value,n_grp", [(1000.0, 1024), (1000.0, 16), (1e-4, 64)])
+def test_extreme_radii(env, h_value, n_grp):
+    """A radius that puts every particle in every group's search box (each
+    list is all N particles: whole-subtree records, the compaction's strided
+    path, lists of several density segments) and one so small that lists
+    hold little beyond the group's own leaves: lists bit for bit and the
+    density within the bound, against the oracle."""
+    torch, afd, orc = env
+    p = ics.plummer(5000, 99)
+    h = np.full(p.n, h_value)
+    g, _, _, rho, nnb = _run(env, p, h, n_grp=n_grp)
+    t = orc.Tree(p.x, p.y, p.z, p.m, n_grp=n_grp)
+    t.neighbour_lists(h, 0.0)
+    _check_lists(g, t)
+    if h_value > 1.0:
+        off = g.export("nbr_off")
+        assert np.all(np.diff(off.astype(np.int64)) == p.n)
+    r_ref, n_ref = t.density(h)
+    assert _rel(rho, r_ref) <= RHO_TOL and _rel(nnb, n_ref) <= RHO_TOL
+    g.close()
