@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-criterion form and the equal-error comparison")
     ap.add_argument("--mac-samples", type=int, default=1_000_000)
+    ap.add_argument("--mac-epochs", type=int, default=12)
+    ap.add_argument("--mac-lr", type=float, default=2e-3)
     ap.add_argument("--mac-band", default="0.4,1.0",
                     help="theta_lo,theta_hi of the learned criterion's band")
     ap.add_argument("--sweep", action="store_true",
@@ -386,8 +388,9 @@ def learned_study(args, wl, afd, torch, np, dev, stream, local, p, tuned, launch
     n_s = min(n_s, cap)
     gt.close()
     t_samp = time.perf_counter() - t0
-    epochs = 12
-    params, hist = afd.afd_mlp_train(feat[:n_s], lab[:n_s], epochs=epochs, batch=1024, lr=2e-3,
+    epochs = int(args.mac_epochs)
+    params, hist = afd.afd_mlp_train(feat[:n_s], lab[:n_s], epochs=epochs, batch=1024,
+                                     lr=float(args.mac_lr),
                                      seed=5, stream=stream)
     t_train = time.perf_counter() - t0 - t_samp
     del feat, lab
