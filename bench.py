@@ -77,6 +77,10 @@ def parse():
     ap.add_argument("--sweep", action="store_true",
                     help="instead of the benchmark line: theta x n_grp and n_reuse sweeps of "
                          "the workload, one JSON line per configuration")
+    ap.add_argument("--shard", choices=("replica", "groups"), default="replica",
+                    help="one system on N > 1 ranks: an independent replica per rank, or "
+                         "disjoint slices of its i-groups with the forces combined by an "
+                         "all-reduce (strong scaling)")
     ap.add_argument("--sph", action="store_true",
                     help="instead of the benchmark line: the short-range neighbour walk and "
                          "gather density on the workload's particles, one line per n_grp")
@@ -199,6 +203,14 @@ def rank_batch(wl, rank, world):
     return cat, off, mine
 
 
+def combine_forces(dist, acc):
+    """The whole system's forces from the ranks' disjoint group slices: each
+    rank's rows of its own groups, zero elsewhere, summed over the ranks
+    (x + 0 = x exactly, so every rank ends with the same bits)."""
+    if dist is not None:
+        dist.all_reduce(acc)
+
+
 def aggregate(dist, device, ms, count):
     """Whole-job figures over ranks: the slowest rank's time, the sum of the
     units all ranks processed."""
@@ -312,10 +324,13 @@ def run_reference(args, wl):
 
 
 def run_loop(afd, torch, ctx, g, st, *, steps, warmup, batch, R, dt, flush, stream, dev,
-             before_timed=None):
+             before_timed=None, combine=None, count=None):
     """Warm-up, then `steps` timed KDK steps (CUDA events around each, L2
     flushed in between). st: dict of the state tensors and the evaluation
-    counter. Returns per-step ms, force ms, interactions, modes, launches."""
+    counter. combine (optional): makes this rank's forces (its groups' rows,
+    the rest zero) the whole system's, e.g. an all-reduce; count (optional):
+    this rank's interactions of a step. Returns per-step ms, force ms,
+    interactions, modes, launches."""
     x, y, z, vx, vy, vz, m, acc = (st[k] for k in ("x", "y", "z", "vx", "vy", "vz", "m", "acc"))
 
     def step():
@@ -325,7 +340,11 @@ def run_loop(afd, torch, ctx, g, st, *, steps, warmup, batch, R, dt, flush, stre
             afd.afd_graph_launch(ctx)  # kick-drift, reusing step, force, kick
         else:
             afd.afd_kick_drift(ctx, x, y, z, vx, vy, vz, acc, 0.5 * dt, dt)
+            if combine:
+                acc.zero_()
             afd.afd_calc_force_all(ctx, x, y, z, m, acc, mode)
+            if combine:
+                combine(acc)
             afd.afd_kick(ctx, vx, vy, vz, acc, 0.5 * dt)
             if batch:  # buffers may have moved: capture the new reusing step
                 afd.afd_graph_capture_step(ctx, x, y, z, vx, vy, vz, m, acc, dt)
@@ -350,7 +369,7 @@ def run_loop(afd, torch, ctx, g, st, *, steps, warmup, batch, R, dt, flush, stre
         step_ms.append(e0.elapsed_time(e1))
         if not (batch and mode == afd.AFD_REUSE_LIST):  # graph replays carry no events
             force_ms.append(afd.afd_last_force_ms(ctx))
-        inter.append(g.stats()["interactions"])
+        inter.append(count() if count else g.stats()["interactions"])
         modes.append(mode)
     torch.cuda.synchronize(dev)
     return step_ms, force_ms, inter, modes, g.stats()["launches"] - launches0
@@ -810,10 +829,23 @@ def main():
         tuned = afd.afd_autotune_n_grp(ctx, x, y, z, m, acc, [32, 64, 128, 256, 512], R,
                                        n_sys=wl["n_systems"])
 
+    # one system over several ranks by group slices: each rank computes its
+    # part of the groups, the forces are combined by an all-reduce
+    groups_shared = args.shard == "groups" and world > 1 and not batch
+    combine = count = None
+    if groups_shared:
+        afd.afd_set_work_share(ctx, rank, world)
+        combine = lambda a: combine_forces(dist, a)
+        count = lambda: afd.afd_get_work_share(ctx)["interactions"]
+
     afd.afd_calc_force_all(ctx, x, y, z, m, acc, afd.AFD_MAKE_LIST_FOR_REUSE)  # evaluation 0
     # force-kernel block shape and list-chunk size, timed on these lists
     launch = afd.afd_autotune_launch(ctx, acc, reps=3)
+    if groups_shared:
+        acc.zero_()
     afd.afd_calc_force(ctx, acc)  # evaluation 0's forces for the first kick
+    if groups_shared:
+        combine(acc)
     if batch:
         afd.afd_graph_capture_step(ctx, x, y, z, vx, vy, vz, m, acc, dt)
     state = {"x": x, "y": y, "z": z, "vx": vx, "vy": vy, "vz": vz, "m": m, "acc": acc, "k": 1}
@@ -829,7 +861,8 @@ def main():
 
     step_ms, force_ms, inter, modes, launches = run_loop(
         afd, torch, ctx, g, state, steps=args.steps, warmup=args.warmup, batch=batch, R=R, dt=dt,
-        flush=flush, stream=stream, dev=dev, before_timed=before_timed)
+        flush=flush, stream=stream, dev=dev, before_timed=before_timed, combine=combine,
+        count=count)
     t_wall = time.perf_counter() - t_wall[0]
     clocks = sampler.stop()
     total_ms = float(sum(step_ms))
@@ -857,7 +890,7 @@ def main():
 
     # ---- end to end through the host-array entry point ----
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not groups_shared:
         hx, hy, hz, hm = (torch.tensor(a, dtype=torch.float64).pin_memory()
                           for a in (p.x, p.y, p.z, p.m))
         hacc = torch.zeros(n, 4, dtype=torch.float32).pin_memory()
@@ -895,14 +928,16 @@ def main():
         "metric": "force interactions/s", "value": value, "unit": "interactions/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "strong" if shard is not None else "weak",
+        "scaling": "strong" if (shard is not None or groups_shared) else "weak",
         "vs_baseline": None, "dtype": "f32",
         "dtype_detail": "force kernel FP32 (hi/lo group-relative coordinates); tree, "
                         "moments and integration FP64",
         "data": "synthetic (seeded Plummer sphere)",
         "config": {"workload": describe(wl), "n": n, "l2": "flushed (256 MB write) between "
                    "timed steps, outside the timed events", "parallelism":
-                   ("systems sharded over ranks" if shard is not None else "replicas")
+                   ("systems sharded over ranks" if shard is not None else
+                    "group slices over ranks, forces all-reduced" if groups_shared
+                    else "replicas")
                    if world > 1 else "single GPU"},
         "ms_per_construction_step": float(np.mean(cons)) if cons else None,
         "ms_per_reuse_step": float(np.mean(reus)) if reus else None,
@@ -918,6 +953,9 @@ def main():
     }
     if e2e:
         line["e2e"] = e2e
+    elif groups_shared:
+        line["e2e_skipped"] = ("group slices: a rank's host-array call computes its slice only; "
+                               "the forces are combined on the device")
     if not args.no_learned and world == 1 and not wl["quad"]:
         line["learned_mac"] = learned_study(args, wl, afd, torch, np, dev, stream, local, p,
                                             tuned, launch, flush, line)

@@ -297,6 +297,37 @@ int afd_calc_density(afd_ctx *ctx, const double *h, float *rho, float *nnb);
  * n_i x list length). Zeros without lists. */
 int afd_neighbour_stats(afd_ctx *ctx, int64_t *out);
 
+/* ---------------------------------------------------------------------------
+ * A force step split over several processes (one GPU each) by disjoint
+ * slices of i-groups: every process builds the same tree and lists, computes
+ * the forces of its part of the groups, and the parts' outputs are combined
+ * by the caller (zero-filled outputs summed, e.g. an all-reduce). The
+ * groups' outputs are disjoint, so the combined forces equal an unshared
+ * evaluation's bit for bit.
+ * ------------------------------------------------------------------------- */
+
+/* Contiguous, balanced parts of a work array (host memory, no GPU): bounds
+ * (host, parts + 1 int64) receives bounds[0] = 0 <= bounds[1] <= ... <=
+ * bounds[parts] = n, where bounds[p] is the first index whose prefix sum
+ * work[0] + ... + work[k - 1] reaches total * p / parts; each part's work is
+ * within one element's work of total / parts. All-zero work is split by
+ * count. AFD_ERR_ARG for n < 0, parts < 1 or null pointers. */
+int afd_partition_work(const uint64_t *work, int64_t n, int parts, int64_t *bounds);
+
+/* Take part `part` of `parts` (0 <= part < parts) of every later force
+ * evaluation: at each list construction the groups are split by
+ * afd_partition_work over their work n_i x (EPJ + SPJ list length), and
+ * afd_calc_force (and the steps that call it) writes the forces of this
+ * part's groups only, leaving the other rows of acc4 untouched. parts = 1
+ * (the default) computes everything. With the learned criterion the caller
+ * passes the combined forces to afd_mac_set_reference. Synchronises when
+ * lists exist (the split of the current lists is made at once). */
+int afd_set_work_share(afd_ctx *ctx, int part, int parts);
+
+/* The current share (host int64[5]): part, parts, first and end group of
+ * this part's slice, and its interactions (sum of n_i x list length). */
+int afd_get_work_share(afd_ctx *ctx, int64_t *out);
+
 /* Wait for the context's stream and return the device status word. */
 int afd_sync(afd_ctx *ctx);
 

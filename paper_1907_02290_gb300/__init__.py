@@ -104,6 +104,9 @@ def lib():
         "afd_make_neighbour_lists": ([_VP, _VP, _D], ctypes.c_int),
         "afd_calc_density": ([_VP, _VP, _VP, _VP], ctypes.c_int),
         "afd_neighbour_stats": ([_VP, _VP], ctypes.c_int),
+        "afd_partition_work": ([_VP, _I64, ctypes.c_int, _VP], ctypes.c_int),
+        "afd_set_work_share": ([_VP, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "afd_get_work_share": ([_VP, _VP], ctypes.c_int),
         "afd_get_launch": ([_VP, _VP, _VP], ctypes.c_int),
         "afd_autotune_launch": ([_VP, _VP, ctypes.c_int, _VP], ctypes.c_int),
         "afd_mac_set": ([_VP, _VP, _D, _D, _D], ctypes.c_int),
@@ -392,6 +395,25 @@ def afd_neighbour_stats(ctx) -> dict:
     out = (ctypes.c_int64 * 2)()
     _check(lib().afd_neighbour_stats(ctx, ctypes.cast(out, _VP)), "afd_neighbour_stats")
     return {"entries": int(out[0]), "pairs": int(out[1])}
+
+
+def afd_partition_work(work, parts) -> np.ndarray:
+    """Contiguous balanced parts of a host work array: bounds (parts + 1)."""
+    w = np.ascontiguousarray(work, dtype=np.uint64)
+    bounds = np.zeros(int(parts) + 1, dtype=np.int64)
+    _check(lib().afd_partition_work(_VP(w.ctypes.data) if w.size else None, w.size, int(parts),
+                                    _VP(bounds.ctypes.data)), "afd_partition_work")
+    return bounds
+
+
+def afd_set_work_share(ctx, part, parts):
+    _check(lib().afd_set_work_share(ctx, int(part), int(parts)), "afd_set_work_share")
+
+
+def afd_get_work_share(ctx) -> dict:
+    out = (ctypes.c_int64 * 5)()
+    _check(lib().afd_get_work_share(ctx, ctypes.cast(out, _VP)), "afd_get_work_share")
+    return dict(zip(("part", "parts", "g0", "g1", "interactions"), (int(v) for v in out)))
 
 
 def afd_set_launch(ctx, warps_per_block, chunk):

@@ -151,6 +151,7 @@ int make_lists(afd_ctx *c, int mode) {
   if (!c->have_tree) return AFD_ERR_NO_TREE;
   c->have_lists = c->saved = false;
   TRY(launch_walk(c));
+  if (c->share_parts > 1) TRY(compute_share(c));
   c->have_lists = true;
   c->saved = mode == AFD_MAKE_LIST_FOR_REUSE;
   return AFD_OK;
@@ -177,8 +178,9 @@ int calc_force(afd_ctx *c, float *acc4) {
   if (c->n > 0 && !acc4) return AFD_ERR_ARG;
   TRY(launch_force(c, acc4));
   // the learned opening criterion scales cells by these magnitudes at the
-  // next construction step
-  if (c->cfg.mac) TRY(launch_amag(c, acc4));
+  // next construction step (with a work share the other parts' rows are not
+  // here yet: the caller passes the combined forces to afd_mac_set_reference)
+  if (c->cfg.mac && c->share_parts == 1) TRY(launch_amag(c, acc4));
   return AFD_OK;
 }
 
@@ -224,7 +226,90 @@ void graph_release(afd_ctx *c) {
 
 }  // namespace
 
+namespace afd {
+
+// Contiguous parts of a work array: bounds[p] is the first index k whose
+// prefix sum (work[0] + ... + work[k - 1]) reaches total * p / parts, so each
+// part's work is within one element's work of total / parts. All-zero work
+// is split by count.
+void partition_work(const uint64_t *work, int64_t n, int parts, int64_t *bounds) {
+  uint64_t total = 0;
+  for (int64_t i = 0; i < n; i++) total += work[i];
+  const bool by_count = total == 0;
+  if (by_count) total = (uint64_t)n;
+  bounds[0] = 0;
+  int64_t k = 0;
+  uint64_t prefix = 0;
+  for (int p = 1; p < parts; p++) {
+    const unsigned __int128 target = (unsigned __int128)total * (unsigned)p;
+    while (k < n && (unsigned __int128)prefix * (unsigned)parts < target) {
+      prefix += by_count ? 1u : work[k];
+      k++;
+    }
+    bounds[p] = k;
+  }
+  bounds[parts] = n;
+}
+
+int compute_share(afd_ctx *c) {
+  const int64_t ng = c->n_groups;
+  c->share_g0 = c->share_g1 = c->share_u0 = c->share_u1 = 0;
+  c->share_inter = 0;
+  if (ng == 0) return AFD_OK;
+  std::vector<uint32_t> ce(ng), cs(ng), gc(ng), uo(ng + 1);
+  const size_t b = sizeof(uint32_t) * (size_t)ng;
+  if (cudaMemcpyAsync(ce.data(), c->l_cnt_e.p, b, cudaMemcpyDeviceToHost, c->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(cs.data(), c->l_cnt_s.p, b, cudaMemcpyDeviceToHost, c->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(gc.data(), c->g_count.p, b, cudaMemcpyDeviceToHost, c->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(uo.data(), c->u_off.p, b + sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                      c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return AFD_ERR_CUDA;
+  std::vector<uint64_t> w(ng);
+  for (int64_t g = 0; g < ng; g++) w[g] = (uint64_t)gc[g] * ((uint64_t)ce[g] + cs[g]);
+  std::vector<int64_t> bounds(c->share_parts + 1);
+  partition_work(w.data(), ng, c->share_parts, bounds.data());
+  c->share_g0 = bounds[c->share_part];
+  c->share_g1 = bounds[c->share_part + 1];
+  c->share_u0 = uo[c->share_g0];
+  c->share_u1 = uo[c->share_g1];
+  for (int64_t g = c->share_g0; g < c->share_g1; g++) c->share_inter += w[g];
+  return AFD_OK;
+}
+
+}  // namespace afd
+
 extern "C" {
+
+int afd_partition_work(const uint64_t *work, int64_t n, int parts, int64_t *bounds) {
+  if (n < 0 || parts < 1 || !bounds || (n > 0 && !work)) return AFD_ERR_ARG;
+  partition_work(work, n, parts, bounds);
+  return AFD_OK;
+}
+
+int afd_set_work_share(afd_ctx *c, int part, int parts) {
+  if (!c || parts < 1 || part < 0 || part >= parts) return AFD_ERR_ARG;
+  DeviceGuard g(c->device);
+  c->share_part = part;
+  c->share_parts = parts;
+  if (parts > 1 && c->have_lists) return compute_share(c);
+  return AFD_OK;
+}
+
+int afd_get_work_share(afd_ctx *c, int64_t *out) {
+  if (!c || !out) return AFD_ERR_ARG;
+  const bool all = c->share_parts == 1 || !c->have_lists;
+  out[0] = c->share_part;
+  out[1] = c->share_parts;
+  out[2] = all ? 0 : c->share_g0;
+  out[3] = all ? (c->have_tree ? c->n_groups : 0) : c->share_g1;
+  out[4] = all ? (c->have_lists ? (int64_t)c->interactions : 0) : (int64_t)c->share_inter;
+  return AFD_OK;
+}
+
 
 int afd_create(afd_ctx **out, const afd_config *cfg, int device, void *stream) {
   if (!out || !cfg) return AFD_ERR_ARG;

@@ -47,7 +47,8 @@ namespace {
 #endif
 
 struct ForceArgs {
-  int64_t n_units;
+  int64_t n_units;  // the launch covers units [u_base, n_units)
+  int64_t u_base;
   unsigned long long *queue;  // work counter of the persistent variant (zeroed per launch)
   const uint2 *u_info;
   const uint32_t *g_first, *g_count, *g_self, *g_cell;
@@ -587,13 +588,13 @@ __global__ void __launch_bounds__(kForceMaxThreads, QUAD ? 2 : AFD_FORCE_MIN_BLO
     for (;;) {
       unsigned long long u = 0;
       if (lane == 0) u = atomicAdd(a.queue, 1ull);
-      u = __shfl_sync(0xffffffffu, u, 0);
+      u = __shfl_sync(0xffffffffu, u, 0) + (unsigned long long)a.u_base;
       if ((int64_t)u >= a.n_units) return;
       force_unit<GUARD, QUAD, FAR, CH>(a, stage[w], lane, (int64_t)u);
       __syncwarp();
     }
   } else {
-    const int64_t u = (int64_t)blockIdx.x * nw + w;
+    const int64_t u = a.u_base + (int64_t)blockIdx.x * nw + w;
     if (u >= a.n_units) return;
     force_unit<GUARD, QUAD, FAR, CH>(a, stage[w], lane, u);
   }
@@ -662,8 +663,13 @@ int launch_force_materialized(afd_ctx *c, float *acc4) {
 
 int launch_force_impl(afd_ctx *c, float *acc4, bool materialized) {
   if (c->n == 0 || c->n_units == 0) return AFD_OK;
+  // the units of this context's work share (all of them without a share)
+  const int64_t u0 = c->share_parts > 1 ? c->share_u0 : 0;
+  const int64_t u1 = c->share_parts > 1 ? c->share_u1 : c->n_units;
+  if (u1 <= u0) return AFD_OK;
   ForceArgs a;
-  a.n_units = c->n_units;
+  a.n_units = u1;
+  a.u_base = u0;
   a.u_info = ptr<uint2>(c->u_info);
   a.g_first = ptr<uint32_t>(c->g_first);
   a.g_count = ptr<uint32_t>(c->g_count);
@@ -697,7 +703,7 @@ int launch_force_impl(afd_ctx *c, float *acc4, bool materialized) {
   a.n_spj = c->n_spj;
   a.queue = ptr<unsigned long long>(c->u64acc) + 2;
   const int warps = c->force_warps;
-  unsigned nb = (unsigned)((c->n_units + warps - 1) / warps);
+  unsigned nb = (unsigned)((u1 - u0 + warps - 1) / warps);
   if (AFD_FORCE_PERSISTENT) {
     if (cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), c->stream) != cudaSuccess)
       return AFD_ERR_CUDA;

@@ -148,6 +148,14 @@ struct afd_ctx {
   // per chunk (32, 64); set by afd_set_launch / afd_autotune_launch
   int force_warps = 4, force_chunk = 32;
 
+  // work share of a force step split over several processes (one system,
+  // disjoint slices of groups): part share_part of share_parts; the groups
+  // [share_g0, share_g1) and their units [share_u0, share_u1) of the current
+  // lists, and their interactions. share_parts = 1: everything.
+  int share_part = 0, share_parts = 1;
+  int64_t share_g0 = 0, share_g1 = 0, share_u0 = 0, share_u1 = 0;
+  uint64_t share_inter = 0;
+
   // independent systems (a forest): particles [sys_off[s], sys_off[s+1]) form
   // system s, with its own root cell and group size. n_sys = 1: one system.
   int n_sys = 1;
@@ -214,6 +222,11 @@ int launch_nbr_walk(afd_ctx *c);
 bool mac_usable(const afd_ctx *c);   // weights, reference |a| and quadrupoles present
 int launch_group_amin(afd_ctx *c);   // amag_s and g_amin for the current tree
 int launch_amag(afd_ctx *c, const float *acc4);  // reference |a| from a force result
+
+// ---- work share (afd_api.cu) ----
+// The groups and units of this context's part of the current lists (syncs
+// when the share has more than one part).
+int compute_share(afd_ctx *c);
 
 // ---- force (afd_force.cu) ----
 int launch_force(afd_ctx *c, float *acc4);

@@ -71,6 +71,35 @@ def test_host_side_validation_without_gpu(libpath):
     assert afd.afd_error_string(-12).startswith("no reference accelerations")
 
 
+def test_work_partition_is_contiguous_covering_and_balanced(libpath):
+    """afd_partition_work (host only): bounds run from 0 to n without going
+    back, every part's work is within one element of total / parts, each
+    bound is the first index whose prefix reaches its share, and all-zero
+    work is split by count."""
+    import numpy as np
+
+    import paper_1907_02290_gb300 as afd
+
+    gen = np.random.default_rng(3)
+    for n, parts in ((1, 1), (7, 2), (1000, 8), (14270, 8), (5, 9), (300, 3)):
+        w = gen.integers(0, 10**6, n).astype(np.uint64)
+        w[gen.random(n) < 0.1] = 0
+        b = afd.afd_partition_work(w, parts)
+        assert b[0] == 0 and b[-1] == n and np.all(np.diff(b) >= 0)
+        pre = np.concatenate([[0], np.cumsum(w.astype(np.float64))])
+        tot = pre[-1]
+        share = np.array([pre[b[p + 1]] - pre[b[p]] for p in range(parts)])
+        assert np.all(np.abs(share - tot / parts) <= w.max() + 1e-6 * tot)
+        for p in range(1, parts):
+            k = b[p]
+            assert pre[k] * parts >= tot * p and (k == 0 or pre[k - 1] * parts < tot * p)
+    assert list(afd.afd_partition_work(np.zeros(4, np.uint64), 3)) == [0, 2, 3, 4]
+    assert list(afd.afd_partition_work(np.zeros(0, np.uint64), 3)) == [0, 0, 0, 0]
+    L = afd.lib()
+    assert L.afd_partition_work(None, 3, 2, None) == -1
+    assert L.afd_set_work_share(None, 0, 1) == -1
+
+
 def test_product_path_never_touches_the_oracle():
     """The package and its sources neither import nor link the oracle."""
     for dirpath, _, files in os.walk(PKG):

@@ -595,3 +595,44 @@ def test_materialized_lists_ablation_is_bit_identical(env):
     with pytest.raises(afd.AfdError):
         afd.afd_calc_force_materialized(gq.ctx, accq)
     gq.close()
+
+
+@pytest.mark.parametrize("parts", [2, 3, 8])
+def test_work_share_slices_sum_to_the_whole_force(env, parts):
+    """A force step split by group slices (afd_set_work_share): every part
+    writes only its groups' rows; the parts summed equal the unshared forces
+    bit for bit, the slices tile the groups, and their interactions add up --
+    also on a reusing step."""
+    torch, afd, orc = env
+    p = ics.plummer(20000, 41)
+    kw = dict(n_grp=64, theta=0.5, eps=1.0 / 256)
+    dev = torch.device("cuda:0")
+    X = [torch.tensor(a, device=dev) for a in (p.x, p.y, p.z, p.m)]
+    whole = afd.Gravity(afd.Config(**kw), 0, torch.cuda.current_stream())
+    ref = torch.zeros(p.n, 4, dtype=torch.float32, device=dev)
+    whole.force_all(*X, ref, afd.AFD_MAKE_LIST_FOR_REUSE)
+    n_groups, inter = whole.stats()["n_groups"], whole.stats()["interactions"]
+    moved = [X[0] + 1e-4, X[1], X[2], X[3]]
+    ref2 = torch.zeros_like(ref)
+    afd.afd_calc_force_all(whole.ctx, *moved, ref2, afd.AFD_REUSE_LIST)
+    tot = torch.zeros_like(ref)
+    tot2 = torch.zeros_like(ref)
+    bounds, inters = [0], 0
+    for part in range(parts):
+        g = afd.Gravity(afd.Config(**kw), 0, torch.cuda.current_stream())
+        afd.afd_set_work_share(g.ctx, part, parts)
+        acc = torch.zeros_like(ref)
+        g.force_all(*X, acc, afd.AFD_MAKE_LIST_FOR_REUSE)
+        sh = afd.afd_get_work_share(g.ctx)
+        assert sh["g0"] == bounds[-1]
+        bounds.append(sh["g1"])
+        inters += sh["interactions"]
+        tot += acc
+        acc2 = torch.zeros_like(ref)
+        afd.afd_calc_force_all(g.ctx, *moved, acc2, afd.AFD_REUSE_LIST)
+        tot2 += acc2
+        g.close()
+    torch.cuda.synchronize()
+    assert bounds[-1] == n_groups and inters == inter
+    assert torch.equal(tot, ref) and torch.equal(tot2, ref2)
+    whole.close()

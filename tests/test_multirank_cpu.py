@@ -80,3 +80,46 @@ def test_shard_assignment_edge_cases():
     assert bench.shard_systems([5, 3, 3], 2) == [[0], [1, 2]]
     assert bench.shard_systems([1, 1], 4) == [[0], [1], [], []]
     assert bench.aggregate(None, None, 3.5, 7) == (3.5, 7)
+
+
+def _combine_worker(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import bench
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=world)
+    try:
+        gen = np.random.default_rng(11)
+        full = torch.tensor(gen.normal(size=(1000, 4)).astype(np.float32))
+        owner = torch.tensor(gen.integers(0, world, 1000))  # disjoint rows per rank
+        acc = full.clone()
+        acc[owner != rank] = 0.0
+        bench.combine_forces(dist, acc)
+        q.put((rank, bool(torch.equal(acc, full))))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_group_slices_combine_to_the_whole_system():
+    """The N > 1 group-slice mode: each rank holds the forces of its own
+    groups and zeros elsewhere; the all-reduce gives every rank the whole
+    system's forces bit for bit."""
+    pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_combine_worker, args=(r, world, port, q)) for r in range(world)]
+    for pr in procs:
+        pr.start()
+    out = sorted(q.get(timeout=300) for _ in range(world))
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    assert [ok for _, ok in out] == [True, True]
