@@ -932,7 +932,10 @@ def main():
         "vs_baseline": None, "dtype": "f32",
         "dtype_detail": "force kernel FP32 (hi/lo group-relative coordinates); tree, "
                         "moments and integration FP64",
-        "data": "synthetic (seeded Plummer sphere)",
+        "data": "synthetic (seeded " + {"plummer": "Plummer sphere", "batch": "Plummer spheres",
+                                        "uniform_sphere": "cold uniform sphere",
+                                        "galaxy": "halo + disk galaxy"}.get(wl["model"],
+                                                                            wl["model"]) + ")",
         "config": {"workload": describe(wl), "n": n, "l2": "flushed (256 MB write) between "
                    "timed steps, outside the timed events", "parallelism":
                    ("systems sharded over ranks" if shard is not None else
