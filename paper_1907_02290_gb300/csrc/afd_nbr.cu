@@ -16,7 +16,9 @@
 // miss it are dropped with their subtrees, and a cell inside it is listed
 // whole as its contiguous particle range. Outward rounding is monotone, so
 // a parent's FP32 box contains its children's and the walk finds exactly
-// the leaves a scan over all leaves would.
+// the leaves a scan over all leaves would. Each group's walk is split into
+// items, one per seed cell its search box meets (afd_walk.cu), so that a
+// group whose box reaches across the system is walked by many warps.
 //
 // Density (k_density). Work item = (force work unit, segment of at most
 // kSegLen list entries): a unit is a group's chunk of up to 32 particles (a
