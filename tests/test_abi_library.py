@@ -100,6 +100,50 @@ def test_work_partition_is_contiguous_covering_and_balanced(libpath):
     assert L.afd_set_work_share(None, 0, 1) == -1
 
 
+C_CLIENT = r"""
+/* A plain C99 client of the library: only include/afdps.h, no C++ and no
+ * Python. Without a GPU it exercises the host-side calls. */
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "afdps.h"
+
+int main(void) {
+  if (strcmp(afd_error_string(AFD_OK), "ok") != 0) return 1;
+  afd_config bad;
+  memset(&bad, 0, sizeof(bad));
+  bad.n_grp = 0; /* invalid */
+  afd_ctx *ctx = NULL;
+  if (afd_create(&ctx, &bad, 0, NULL) != AFD_ERR_ARG) return 2;
+  if (afd_calc_force(NULL, NULL) != AFD_ERR_ARG) return 3;
+  const uint64_t work[6] = {4, 4, 4, 4, 4, 4};
+  int64_t bounds[4];
+  if (afd_partition_work(work, 6, 3, bounds) != AFD_OK) return 4;
+  if (bounds[0] != 0 || bounds[1] != 2 || bounds[2] != 4 || bounds[3] != 6) return 5;
+  printf("c client ok\n");
+  return 0;
+}
+"""
+
+
+def test_plain_c_client_compiles_links_and_runs(libpath, tmp_path):
+    """The boundary is a C ABI: a C99 program that includes only the header
+    compiles with -Werror, links against the shared library and runs its
+    host-side calls."""
+    src = tmp_path / "client.c"
+    src.write_text(C_CLIENT)
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(libpath)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I",
+                    os.path.join(ROOT, "include"), str(src), "-o", str(exe), "-L", libdir,
+                    "-l:" + os.path.basename(libpath), "-Wl,-rpath," + libdir],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, (out.returncode, out.stderr)
+    assert "c client ok" in out.stdout
+
+
 def test_product_path_never_touches_the_oracle():
     """The package and its sources neither import nor link the oracle."""
     for dirpath, _, files in os.walk(PKG):
