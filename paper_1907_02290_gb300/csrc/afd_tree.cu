@@ -745,6 +745,121 @@ __global__ void __launch_bounds__(kThreads) k_moments(MomArgs a) {
   }
 }
 
+// Monopole moments in passes. The climb above does, for every internal
+// cell, three correctly rounded FP64 divisions and the FP32 splits on a warp
+// that has one lane active (the last child to arrive), and GB300's FP64 pipe
+// takes as long for a one-lane warp instruction as for a full one. Without
+// quadrupoles (which need the children's centres of mass bottom-up) only the
+// ordered sums M and S climb (k_moments_sums); the centres of mass and the
+// FP32 superparticle data follow in one thread per cell on full warps
+// (k_moments_finish), and the walk's child records in another pass
+// (k_moments_blocks, construction steps). Each cell's arithmetic is the
+// definition's, in the same order.
+__global__ void __launch_bounds__(kThreads) k_moments_sums(MomArgs a) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  uint32_t c = (uint32_t)t;
+  // climbing: this lane holds a finished cell whose parent it reports to
+  bool climbing = t < a.n_cells && n_children(a.child, c) == 0;
+  if (climbing) {
+    double M = 0.0, S[3] = {0.0, 0.0, 0.0};
+    const uint32_t f = a.first[c], e = f + a.count[c];
+    if (e > f && !AFD_IN(e - 1, a.n_part, "moments leaf range")) {
+      climbing = false;
+    } else {
+      for (uint32_t k = f; k < e; k++) {
+        const double mk = a.ms[k];
+        M = __dadd_rn(M, mk);
+        S[0] = __dadd_rn(S[0], __dmul_rn(mk, a.xs[k]));
+        S[1] = __dadd_rn(S[1], __dmul_rn(mk, a.ys[k]));
+        S[2] = __dadd_rn(S[2], __dmul_rn(mk, a.zs[k]));
+      }
+      a.mass[c] = M;
+      for (int d = 0; d < 3; d++) a.smom[(size_t)c * 3 + d] = S[d];
+    }
+  }
+  // The warp climbs together: each lane reports its cell at the parent; the
+  // parents this warp completes are summed four lanes each (M, S_x, S_y,
+  // S_z: one ordered chain over the octants per lane), eight at a time.
+  while (__any_sync(0xffffffffu, climbing)) {
+    uint32_t p = kNone;
+    bool won = false;
+    if (climbing) {
+      p = a.parent[c];
+      if (p == kNone || !AFD_IN(p, a.n_cells, "moments parent")) {
+        climbing = false;
+      } else {
+        __threadfence();
+        const unsigned old = atomicAdd(&a.arrive[p], 1u);
+        won = (int)old == n_children(a.child, p) - 1;
+        climbing = won;
+        if (won) c = p;
+      }
+    }
+    __threadfence();
+    __syncwarp();  // the winners' view of the children reaches the lanes summing them
+    unsigned wm = __ballot_sync(0xffffffffu, won);
+    while (wm) {
+      // the next (up to) eight completed parents: lane 4j + ch takes chain ch
+      // of the j-th
+      const int j = lane >> 2, ch = lane & 3;
+      unsigned rest = wm;
+      int src = -1;
+      for (int q = 0; q <= j && rest; q++) {
+        src = __ffs(rest) - 1;
+        rest &= rest - 1;
+      }
+      const bool mine = src >= 0 && __popc(wm & ((2u << src) - 1u)) == j + 1;
+      const uint32_t pj = __shfl_sync(0xffffffffu, c, src < 0 ? 0 : src);
+      if (mine) {
+        double acc = 0.0;
+        for (int o = 0; o < 8; o++) {
+          const uint32_t cc = __ldg(&a.child[(size_t)pj * 8 + o]);
+          if (cc == kNone || !AFD_IN(cc, a.n_cells, "moments child")) continue;
+          acc = __dadd_rn(acc, ch == 0 ? __ldcg(&a.mass[cc])
+                                       : __ldcg(&a.smom[(size_t)cc * 3 + (ch - 1)]));
+        }
+        if (ch == 0) a.mass[pj] = acc;
+        else a.smom[(size_t)pj * 3 + (ch - 1)] = acc;
+      }
+      // drop the parents just summed
+      for (int q = 0; q < 8 && wm; q++) wm &= wm - 1;
+    }
+    __syncwarp();  // the sums are ordered before the climbing lane's fence and arrival
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_moments_finish(MomArgs a) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.n_cells) return;
+  const uint32_t c = (uint32_t)t;
+  const double S[3] = {a.smom[(size_t)c * 3], a.smom[(size_t)c * 3 + 1],
+                       a.smom[(size_t)c * 3 + 2]};
+  finish_cell(a, c, a.mass[c], S, n_children(a.child, c) == 0);
+}
+
+__global__ void __launch_bounds__(kThreads) k_moments_blocks(MomArgs a) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.n_cells) return;
+  const uint32_t p = (uint32_t)t;
+  if (n_children(a.child, p) == 0) return;
+  // the walk's view of p's children: (COM_f32, s^2) and (first, count |
+  // leaf, id, 0) per octant slot, id = kNone when empty
+  for (int o = 0; o < 8; o++) {
+    const uint32_t cc = __ldg(&a.child[(size_t)p * 8 + o]);
+    uint4 nf = make_uint4(0u, 0u, 0u, 0u), meta = make_uint4(0u, 0u, kNone, 0u);
+    if (cc != kNone && AFD_IN(cc, a.n_cells, "moments block child")) {
+      const float4 f = a.node_f[cc];
+      const uint2 ni = a.node_i[cc];
+      nf = make_uint4(__float_as_uint(f.x), __float_as_uint(f.y), __float_as_uint(f.z),
+                      __float_as_uint(f.w));
+      meta = make_uint4(ni.x, ni.y, cc, 0u);
+    }
+    a.block[((size_t)p * 8 + o) * 2] = nf;
+    a.block[((size_t)p * 8 + o) * 2 + 1] = meta;
+  }
+}
+
 // Force-kernel work units of a group of cn particles (see k_unit_fill).
 __device__ __forceinline__ uint32_t unit_count(uint32_t cn) { return (cn + 31u) / 32u; }
 
@@ -1116,8 +1231,18 @@ int launch_moments(afd_ctx *c, bool child_blocks, bool need_q) {
   a.block = child_blocks ? ptr<uint4>(c->c_block) : nullptr;
   a.quad_on = quad_on;
   a.n_part = c->n;
-  k_moments<<<blocks_for(nc), kThreads, 0, c->stream>>>(a);
-  c->launches++;
+  if (quad_on) {
+    k_moments<<<blocks_for(nc), kThreads, 0, c->stream>>>(a);
+    c->launches++;
+  } else {
+    k_moments_sums<<<blocks_for(nc), kThreads, 0, c->stream>>>(a);
+    k_moments_finish<<<blocks_for(nc), kThreads, 0, c->stream>>>(a);
+    c->launches += 2;
+    if (a.block) {
+      k_moments_blocks<<<blocks_for(nc), kThreads, 0, c->stream>>>(a);
+      c->launches++;
+    }
+  }
   return ck();
 }
 
