@@ -556,11 +556,9 @@ __device__ __forceinline__ void unit_body(const ForceArgs &a, WarpStage<QUAD, CH
   }
 }
 
-// Work unit u: group g = info.x, first particle offset = info.y & 0xffff,
-// j-stream split sidx = info.y >> 16 (S = 1 << sidx streams of W = 32 >> sidx
-// particles; lane = stream * W + particle).
 // Work unit u: group g = info.x; info.y holds the first particle offset
-// (bits 0-15) and log2 of the j-stream split S (bits 16-17).
+// (bits 0-15) and log2 of the j-stream split S (bits 16-17): S = 1 << sidx
+// streams of W = 32 >> sidx particles, lane = stream * W + particle.
 template <bool GUARD, bool QUAD, int FAR, int CH>
 __device__ __forceinline__ void force_unit(const ForceArgs &a, WarpStage<QUAD, CH> &st, int lane,
                                            int64_t u) {
