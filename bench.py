@@ -53,7 +53,7 @@ L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one force-kernel launch on
 # this workload, from the capture summarised in profiles/ (None until taken
 # on the current kernel).
-FORCE_TRAFFIC_BYTES = 310_964_736  # 291.38 MB read + 19.59 MB written (k_force, --set full)
+FORCE_TRAFFIC_BYTES = 309_900_032  # 291.35 MB read + 18.55 MB written (k_force, --set full)
 
 
 def parse():
@@ -81,6 +81,10 @@ def parse():
                     help="one system on N > 1 ranks: an independent replica per rank, or "
                          "disjoint slices of its i-groups with the forces combined by an "
                          "all-reduce (strong scaling)")
+    ap.add_argument("--launch", default=None, metavar="WARPS,CHUNK",
+                    help="fix the force kernel's block shape and list-chunk size instead of "
+                         "timing the six candidates (for profiler runs, where the candidates' "
+                         "event timings are not meaningful)")
     ap.add_argument("--sph", action="store_true",
                     help="instead of the benchmark line: the short-range neighbour walk and "
                          "gather density on the workload's particles, one line per n_grp")
@@ -840,7 +844,12 @@ def main():
 
     afd.afd_calc_force_all(ctx, x, y, z, m, acc, afd.AFD_MAKE_LIST_FOR_REUSE)  # evaluation 0
     # force-kernel block shape and list-chunk size, timed on these lists
-    launch = afd.afd_autotune_launch(ctx, acc, reps=3)
+    if args.launch:
+        w_fix, ch_fix = (int(v) for v in args.launch.split(","))
+        afd.afd_set_launch(ctx, w_fix, ch_fix)
+        launch = (w_fix, ch_fix, None)
+    else:
+        launch = afd.afd_autotune_launch(ctx, acc, reps=3)
     if groups_shared:
         acc.zero_()
     afd.afd_calc_force(ctx, acc)  # evaluation 0's forces for the first kick
@@ -949,9 +958,12 @@ def main():
         "clocks": clocks,
         "gpu_launches": launches,
         "n_grp_autotuned": None if tuned is None else [int(v) for v in tuned],
-        "force_launch_autotuned": {"warps_per_block": launch[0], "chunk": launch[1],
-                                   "ms_chunk32_w2_4_8": [float(v) for v in launch[2][0]],
-                                   "ms_chunk64_w2_4_8": [float(v) for v in launch[2][1]]},
+        "force_launch_autotuned": ({"warps_per_block": launch[0], "chunk": launch[1],
+                                    "ms_chunk32_w2_4_8": [float(v) for v in launch[2][0]],
+                                    "ms_chunk64_w2_4_8": [float(v) for v in launch[2][1]]}
+                                   if launch[2] is not None else
+                                   {"warps_per_block": launch[0], "chunk": launch[1],
+                                    "fixed": "--launch"}),
         "wall_s_timed_region": t_wall,
     }
     if e2e:

@@ -34,13 +34,13 @@ namespace afd {
 namespace {
 
 #ifndef AFD_FORCE_MIN_BLOCKS
-#define AFD_FORCE_MIN_BLOCKS 8  // resident blocks per SM the register budget targets
+#define AFD_FORCE_MIN_BLOCKS 6  // resident 128-thread blocks per SM the register budget targets (80 registers)
 #endif
 #ifndef AFD_FORCE_ILP2
 #define AFD_FORCE_ILP2 1  // two independent accumulator chains per lane
 #endif
 #ifndef AFD_FORCE_FLUSH_PAIRS
-#define AFD_FORCE_FLUSH_PAIRS 16  // pair-iterations per lane between Kahan flushes
+#define AFD_FORCE_FLUSH_PAIRS 128  // pair-iterations per lane between Kahan flushes
 #endif
 #ifndef AFD_FORCE_PERSISTENT
 #define AFD_FORCE_PERSISTENT 0  // warps take units from an atomic queue
@@ -573,7 +573,7 @@ __device__ __forceinline__ void force_unit(const ForceArgs &a, WarpStage<QUAD, C
 
 // Block shape is a launch choice (2, 4 or 8 warps): each warp's staging area
 // lives in dynamic shared memory. The register budget is the same for every
-// shape: 64 per thread with FP32 monopoles, 128 with quadrupoles.
+// shape: 80 per thread with FP32 monopoles, 128 with quadrupoles.
 constexpr int kForceMaxThreads = 256;
 
 template <bool GUARD, bool QUAD, int FAR, int CH>
@@ -705,7 +705,7 @@ int launch_force_impl(afd_ctx *c, float *acc4, bool materialized) {
   if (AFD_FORCE_PERSISTENT) {
     if (cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), c->stream) != cudaSuccess)
       return AFD_ERR_CUDA;
-    const unsigned cap = 152u * 32u / (unsigned)warps;  // resident warps per GPU at 64 registers
+    const unsigned cap = 152u * 4u * AFD_FORCE_MIN_BLOCKS / (unsigned)warps;  // resident warps per GPU
     if (nb > cap) nb = cap;
   }
   const bool guard = !(a.eps2 > 0.0f);
