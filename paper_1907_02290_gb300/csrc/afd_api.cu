@@ -131,7 +131,7 @@ int tree_build(afd_ctx *c, const double *x, const double *y, const double *z, co
   if (n < 0 || n >= ((int64_t)1 << 30)) return AFD_ERR_ARG;
   if (n > 0 && (!x || !y || !z || !m)) return AFD_ERR_ARG;
   if (c->n_sys > 1 && n != c->sys_off_h[c->n_sys]) return AFD_ERR_SHAPE;
-  c->have_tree = c->have_lists = c->saved = c->have_nbr = false;
+  c->have_tree = c->have_lists = c->saved = c->have_nbr = c->u_order_ok = false;
   c->n = n;
   TRY(launch_root(c, x, y, z, m, n));
   TRY(launch_keys(c, x, y, z, n));
@@ -149,9 +149,10 @@ int tree_build(afd_ctx *c, const double *x, const double *y, const double *z, co
 int make_lists(afd_ctx *c, int mode) {
   if (mode != AFD_MAKE_LIST && mode != AFD_MAKE_LIST_FOR_REUSE) return AFD_ERR_ARG;
   if (!c->have_tree) return AFD_ERR_NO_TREE;
-  c->have_lists = c->saved = false;
+  c->have_lists = c->saved = c->u_order_ok = false;
   TRY(launch_walk(c));
   if (c->share_parts > 1) TRY(compute_share(c));
+  TRY(order_units(c));
   c->have_lists = true;
   c->saved = mode == AFD_MAKE_LIST_FOR_REUSE;
   return AFD_OK;
@@ -295,7 +296,10 @@ int afd_set_work_share(afd_ctx *c, int part, int parts) {
   DeviceGuard g(c->device);
   c->share_part = part;
   c->share_parts = parts;
-  if (parts > 1 && c->have_lists) return compute_share(c);
+  if (c->have_lists) {
+    if (parts > 1) TRY(compute_share(c));
+    return order_units(c);
+  }
   return AFD_OK;
 }
 
@@ -380,7 +384,7 @@ int afd_set_systems(afd_ctx *c, const int64_t *sys_off, int n_sys, const int32_t
     for (int s = 0; s < n_sys; s++)
       if (n_grp[s] < 1 || n_grp[s] > 1024) return AFD_ERR_ARG;
   DeviceGuard g(c->device);
-  c->have_tree = c->have_lists = c->saved = false;
+  c->have_tree = c->have_lists = c->saved = c->u_order_ok = false;
   c->n_sys = n_sys;
   c->sys_off_h.assign(sys_off, sys_off + n_sys + 1);
   if (n_grp) c->sys_grp_h.assign(n_grp, n_grp + n_sys);
@@ -643,7 +647,7 @@ int afd_autotune_n_grp(afd_ctx *c, const double *x, const double *y, const doubl
   }
   if (ns > 1) return afd_set_systems(c, off.data(), ns, best);
   c->cfg.n_grp = best[0];
-  c->have_tree = c->have_lists = c->saved = false;
+  c->have_tree = c->have_lists = c->saved = c->u_order_ok = false;
   return AFD_OK;
 }
 

@@ -48,6 +48,7 @@ namespace {
 
 struct ForceArgs {
   int64_t n_units;  // the launch covers units [u_base, n_units)
+  const uint32_t *u_order;  // their launch order (null: index order)
   int64_t u_base;
   unsigned long long *queue;  // work counter of the persistent variant (zeroed per launch)
   const uint2 *u_info;
@@ -571,6 +572,13 @@ __device__ __forceinline__ void force_unit(const ForceArgs &a, WarpStage<QUAD, C
   else unit_body<GUARD, QUAD, FAR, 4, 1, CH>(a, st, lane, g, ioff);
 }
 
+// The unit at launch position k of [u_base, n_units).
+__device__ __forceinline__ int64_t launch_unit(const ForceArgs &a, int64_t k) {
+  if (!a.u_order) return a.u_base + k;
+  const int64_t u = (int64_t)a.u_order[k];
+  return AFD_IN(u, (uint64_t)a.n_units, "force unit order") ? u : a.u_base + k;
+}
+
 // Block shape is a launch choice (2, 4 or 8 warps): each warp's staging area
 // lives in dynamic shared memory. The register budget is the same for every
 // shape: 80 per thread with FP32 monopoles, 128 with quadrupoles.
@@ -586,15 +594,15 @@ __global__ void __launch_bounds__(kForceMaxThreads, QUAD ? 2 : AFD_FORCE_MIN_BLO
     for (;;) {
       unsigned long long u = 0;
       if (lane == 0) u = atomicAdd(a.queue, 1ull);
-      u = __shfl_sync(0xffffffffu, u, 0) + (unsigned long long)a.u_base;
-      if ((int64_t)u >= a.n_units) return;
-      force_unit<GUARD, QUAD, FAR, CH>(a, stage[w], lane, (int64_t)u);
+      u = __shfl_sync(0xffffffffu, u, 0);
+      if ((int64_t)u + a.u_base >= a.n_units) return;
+      force_unit<GUARD, QUAD, FAR, CH>(a, stage[w], lane, launch_unit(a, (int64_t)u));
       __syncwarp();
     }
   } else {
-    const int64_t u = a.u_base + (int64_t)blockIdx.x * nw + w;
-    if (u >= a.n_units) return;
-    force_unit<GUARD, QUAD, FAR, CH>(a, stage[w], lane, u);
+    const int64_t k = (int64_t)blockIdx.x * nw + w;
+    if (a.u_base + k >= a.n_units) return;
+    force_unit<GUARD, QUAD, FAR, CH>(a, stage[w], lane, launch_unit(a, k));
   }
 }
 
@@ -631,7 +639,112 @@ __global__ void k_materialize(uint64_t n, const uint32_t *__restrict__ idx,
   }
 }
 
+// Launch order of the force units. A unit's warp streams its group's whole
+// list (split over S j-streams for the last, partial unit), so its time
+// follows the list work L / S. Blocks are dispatched in index order; with
+// the units in group order the longest ones can come last and leave SMs
+// idle at the end of the launch, so the launch takes them longest first:
+// a counting sort over 256 buckets of L / S (bucket 0 = the most work).
+// The order only schedules: every unit writes its own particles.
+constexpr int kOrderBuckets = 256;
+
+__device__ __forceinline__ uint32_t unit_work(const uint2 *u_info, const uint64_t *off_e,
+                                              const uint64_t *off_s, int64_t u) {
+  const uint2 info = u_info[u];
+  const uint32_t g = info.x;
+  const uint64_t L = (off_e[g + 1] - off_e[g]) + (off_s[g + 1] - off_s[g]);
+  const uint64_t w = L >> ((info.y >> 16) & 3u);
+  return w > 0xffffffffull ? 0xffffffffu : (uint32_t)w;
+}
+
+// hist[0 .. kOrderBuckets): bucket counts, hist[kOrderBuckets]: the largest work
+__global__ void k_unit_work(int64_t u0, int64_t nu, const uint2 *__restrict__ u_info,
+                            const uint64_t *__restrict__ off_e, const uint64_t *__restrict__ off_s,
+                            uint32_t *__restrict__ work, uint32_t *__restrict__ hist) {
+  uint32_t wmax = 0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nu;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t w = unit_work(u_info, off_e, off_s, u0 + k);
+    work[k] = w;
+    wmax = max(wmax, w);
+  }
+  for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(&hist[kOrderBuckets], wmax);
+}
+
+__device__ __forceinline__ int order_bucket(uint32_t w, uint32_t wmax) {
+  const int b = (int)(((uint64_t)w * kOrderBuckets) / ((uint64_t)wmax + 1u));
+  return kOrderBuckets - 1 - b;
+}
+
+__global__ void k_unit_hist(int64_t nu, const uint32_t *__restrict__ work,
+                            uint32_t *__restrict__ hist) {
+  __shared__ uint32_t h[kOrderBuckets];
+  for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) h[b] = 0u;
+  __syncthreads();
+  const uint32_t wmax = hist[kOrderBuckets];
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nu;
+       k += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&h[order_bucket(work[k], wmax)], 1u);
+  __syncthreads();
+  for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x)
+    if (h[b]) atomicAdd(&hist[b], h[b]);
+}
+
+// one block of kOrderBuckets threads: bucket counts -> first position of
+// each bucket (exclusive scan), in place
+__global__ void k_unit_scan(uint32_t *__restrict__ hist) {
+  __shared__ uint32_t v[kOrderBuckets];
+  const int t = threadIdx.x;
+  v[t] = hist[t];
+  __syncthreads();
+  for (int o = 1; o < kOrderBuckets; o <<= 1) {
+    const uint32_t add = t >= o ? v[t - o] : 0u;
+    __syncthreads();
+    v[t] += add;
+    __syncthreads();
+  }
+  hist[t] = t > 0 ? v[t - 1] : 0u;
+}
+
+__global__ void k_unit_scatter(int64_t u0, int64_t nu, const uint32_t *__restrict__ work,
+                               uint32_t *__restrict__ hist, uint32_t *__restrict__ order) {
+  const uint32_t wmax = hist[kOrderBuckets];
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nu;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t pos = atomicAdd(&hist[order_bucket(work[k], wmax)], 1u);
+    if (AFD_IN(pos, (uint64_t)nu, "unit order position")) order[pos] = (uint32_t)(u0 + k);
+  }
+}
+
 }  // namespace
+
+int order_units(afd_ctx *c) {
+  c->u_order_ok = false;
+  const int64_t u0 = c->share_parts > 1 ? c->share_u0 : 0;
+  const int64_t u1 = c->share_parts > 1 ? c->share_u1 : c->n_units;
+  const int64_t nu = u1 - u0;
+  if (nu <= 0) return AFD_OK;
+  if (reserve(c->u_order, sizeof(uint32_t) * (size_t)nu) != AFD_OK ||
+      reserve(c->u_work, sizeof(uint32_t) * (size_t)nu) != AFD_OK ||
+      reserve(c->u_hist, sizeof(uint32_t) * (kOrderBuckets + 1)) != AFD_OK)
+    return AFD_ERR_OOM;
+  uint32_t *hist = ptr<uint32_t>(c->u_hist), *work = ptr<uint32_t>(c->u_work);
+  if (cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (kOrderBuckets + 1), c->stream) != cudaSuccess)
+    return AFD_ERR_CUDA;
+  constexpr int kT = 256;
+  const int64_t want = (nu + kT - 1) / kT;
+  const unsigned nb = (unsigned)(want < 152 * 8 ? want : 152 * 8);
+  k_unit_work<<<nb, kT, 0, c->stream>>>(u0, nu, ptr<uint2>(c->u_info), ptr<uint64_t>(c->epj_off),
+                                        ptr<uint64_t>(c->spj_off), work, hist);
+  k_unit_hist<<<nb, kT, 0, c->stream>>>(nu, work, hist);
+  k_unit_scan<<<1, kOrderBuckets, 0, c->stream>>>(hist);
+  k_unit_scatter<<<nb, kT, 0, c->stream>>>(u0, nu, work, hist, ptr<uint32_t>(c->u_order));
+  c->launches += 4;
+  if (cudaGetLastError() != cudaSuccess) return AFD_ERR_CUDA;
+  c->u_order_ok = true;
+  return AFD_OK;
+}
 
 int launch_force_impl(afd_ctx *c, float *acc4, bool materialized);
 
@@ -668,6 +781,7 @@ int launch_force_impl(afd_ctx *c, float *acc4, bool materialized) {
   ForceArgs a;
   a.n_units = u1;
   a.u_base = u0;
+  a.u_order = c->u_order_ok ? ptr<uint32_t>(c->u_order) : nullptr;
   a.u_info = ptr<uint2>(c->u_info);
   a.g_first = ptr<uint32_t>(c->g_first);
   a.g_count = ptr<uint32_t>(c->g_count);

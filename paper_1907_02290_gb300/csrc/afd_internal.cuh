@@ -104,6 +104,10 @@ struct afd_ctx {
   afd::DevBuf g_cnt, g_off;
   afd::DevBuf g_first, g_count, g_cell, g_box, g_boxf, g_self;
   afd::DevBuf u_cnt, u_off, u_info;
+  // force-kernel launch order of the units of the work share, longest list
+  // work first (u_work, u_hist: its per-unit work and bucket counters)
+  afd::DevBuf u_order, u_work, u_hist;
+  bool u_order_ok = false;
 
   // lists (CSR)
   afd::DevBuf l_cnt_e, l_cnt_s, epj_off, spj_off, epj, spj;
@@ -229,6 +233,7 @@ int launch_amag(afd_ctx *c, const float *acc4);  // reference |a| from a force r
 int compute_share(afd_ctx *c);
 
 // ---- force (afd_force.cu) ----
+int order_units(afd_ctx *c);  // the force launch order of the current lists' units
 int launch_force(afd_ctx *c, float *acc4);
 int launch_materialize(afd_ctx *c);                    // j-data of every list entry, list order
 int launch_force_materialized(afd_ctx *c, float *acc4);  // force kernel reading those copies
