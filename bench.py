@@ -53,7 +53,7 @@ L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one force-kernel launch on
 # this workload, from the capture summarised in profiles/ (None until taken
 # on the current kernel).
-FORCE_TRAFFIC_BYTES = 309_900_032  # 291.35 MB read + 18.55 MB written (k_force, --set full)
+FORCE_TRAFFIC_BYTES = 530_831_872  # 495.96 MB read + 34.87 MB written (k_force, --set full)
 
 
 def parse():
@@ -491,11 +491,18 @@ def learned_study(args, wl, afd, torch, np, dev, stream, local, p, tuned, launch
                 hi_t = mid
         tau_star = lo_t  # error not above the plain form's
     e_learned, i_learned0 = grid[tau_star]
+    # the learned lists are shorter: their own force-kernel launch shape,
+    # timed on the calibrated lists (unless the shape is fixed by --launch)
+    launch_l = launch
+    if launch[2] is not None:
+        learned_err(tau_star)
+        launch_l = afd.afd_autotune_launch(gl.ctx, acc_l, reps=3)
     gl.close()
     t_cal = time.perf_counter() - t0 - t_samp - t_train
 
     # ---- the learned form timed like the plain one ----
     gl = ctx_for(1)
+    afd.afd_set_launch(gl.ctx, *launch_l[:2])
     afd.afd_mac_set(gl.ctx, params, lo, hi, tau_star)
     st = {k: T(getattr(p, k)) for k in ("x", "y", "z", "vx", "vy", "vz", "m")}
     st["acc"] = torch.zeros(p.n, 4, dtype=torch.float32, device=dev)
@@ -533,6 +540,9 @@ def learned_study(args, wl, afd, torch, np, dev, stream, local, p, tuned, launch
         "speedup_ms_per_step_vs_plain": plain["ms_per_step"] / ms_l,
         "interaction_ratio_plain_over_learned": plain["interactions_per_step"] / float(np.mean(inter)),
         "gpu_launches": launches,
+        "force_launch": {"warps_per_block": launch_l[0], "chunk": launch_l[1],
+                         "tuned_on": "the calibrated learned lists" if launch_l is not launch
+                         else "the plain lists (--launch)"},
         "walk_network_evaluations_last_construction": info["evaluations"],
         "walk_network_accepts_last_construction": info["accepted"],
         "training": {"samples": n_s, "band_pairs_total": total, "epochs": epochs,
