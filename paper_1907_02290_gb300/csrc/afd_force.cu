@@ -641,11 +641,12 @@ __global__ void k_materialize(uint64_t n, const uint32_t *__restrict__ idx,
 
 // Launch order of the force units. A unit's warp streams its group's whole
 // list (split over S j-streams for the last, partial unit), so its time
-// follows the list work L / S. Blocks are dispatched in index order; with
-// the units in group order the longest ones can come last and leave SMs
-// idle at the end of the launch, so the launch takes them longest first:
-// a counting sort over 256 buckets of L / S (bucket 0 = the most work).
-// The order only schedules: every unit writes its own particles.
+// follows the list work L / S. A block's warp slots are freed only when its
+// slowest warp ends, and blocks are dispatched in index order: sorted by
+// work, the warps of a block carry equal work, and longest first the launch
+// also ends without a few long units running alone. A counting sort over
+// 256 buckets of L / S (bucket 0 = the most work). The order only
+// schedules: every unit writes its own particles.
 constexpr int kOrderBuckets = 256;
 
 __device__ __forceinline__ uint32_t unit_work(const uint2 *u_info, const uint64_t *off_e,
