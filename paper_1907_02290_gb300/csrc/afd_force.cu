@@ -42,6 +42,9 @@ namespace {
 #ifndef AFD_FORCE_FLUSH_PAIRS
 #define AFD_FORCE_FLUSH_PAIRS 128  // pair-iterations per lane between Kahan flushes
 #endif
+#ifndef AFD_FORCE_PAIRS
+#define AFD_FORCE_PAIRS 1  // two full units of a group per warp (monopole lists)
+#endif
 #ifndef AFD_FORCE_PERSISTENT
 #define AFD_FORCE_PERSISTENT 0  // warps take units from an atomic queue
 #endif
@@ -49,6 +52,7 @@ namespace {
 struct ForceArgs {
   int64_t n_units;  // the launch covers units [u_base, n_units)
   const uint32_t *u_order;  // their launch order (null: index order)
+  const uint32_t *n_items;  // entries of the launch order (device)
   int64_t u_base;
   unsigned long long *queue;  // work counter of the persistent variant (zeroed per launch)
   const uint2 *u_info;
@@ -329,8 +333,9 @@ __device__ __forceinline__ void run_list(WarpStage<QUAD, CH> &st, const Lane<IPT
                                          const uint32_t *idx, uint64_t o0, uint64_t o1,
                                          const float4 *hi, const float4 *lo, const float4 *sq0,
                                          const float4 *sq1, const float4 *nodef, bool quad_list,
-                                         float eps2, int64_t self_at, uint64_t nlist,
+                                         float eps2, const int64_t *self_at, uint64_t nlist,
                                          uint64_t jbound) {
+  static_assert(IPT == 1 || (!QUAD && S == 1), "two i-particles per lane: monopole, one stream");
   if (o0 >= o1) return;
   if (!AFD_IN(o1 - 1, nlist, "force list range")) return;
   constexpr int kChunk = CH, kPer = CH / 32, kPairs = CH / 2;
@@ -420,7 +425,10 @@ __device__ __forceinline__ void run_list(WarpStage<QUAD, CH> &st, const Lane<IPT
     }
     __syncwarp();
     // does some lane's own particle sit in this chunk? (every lane votes)
-    const bool self_here = self_at >= (int64_t)base && self_at < (int64_t)base + kChunk;
+    bool self_here = false;
+#pragma unroll
+    for (int q = 0; q < IPT; q++)
+      self_here |= self_at[q] >= (int64_t)base && self_at[q] < (int64_t)base + kChunk;
     const bool any_self = __any_sync(0xffffffffu, self_here);
     if (QUAD && quad_list && FAR) {
 #pragma unroll 4
@@ -435,14 +443,33 @@ __device__ __forceinline__ void run_list(WarpStage<QUAD, CH> &st, const Lane<IPT
                               ln.YI[0], ln.ZI[0], ln.E2, AX[0], AY[0], AZ[0], PP[0]);
     } else if (any_self) {
       // a chunk holding some lane's own particle: that pair gets zero mass
-      const int ts = self_here ? (int)(self_at - (int64_t)base) : -1;
+      int ts[IPT];
+#pragma unroll
+      for (int q = 0; q < IPT; q++) {
+        const bool h = self_at[q] >= (int64_t)base && self_at[q] < (int64_t)base + kChunk;
+        ts[q] = h ? (int)(self_at[q] - (int64_t)base) : -1;
+      }
 #pragma unroll
       for (int t = ln.stream; t < kPairs; t += S) {
-        float4 p1 = st.P1[t];
-        if (ts == 2 * t) p1.z = 0.0f;
-        if (ts == 2 * t + 1) p1.w = 0.0f;
-        interact2<GUARD>(st.P0[t], p1, ln.XI[0], ln.YI[0], ln.ZI[0], ln.E2, AX[0], AY[0], AZ[0],
-                         PP[0]);
+        const float4 p0 = st.P0[t], p1 = st.P1[t];
+#pragma unroll
+        for (int q = 0; q < IPT; q++) {
+          float4 p1q = p1;
+          if (ts[q] == 2 * t) p1q.z = 0.0f;
+          if (ts[q] == 2 * t + 1) p1q.w = 0.0f;
+          interact2<GUARD>(p0, p1q, ln.XI[q], ln.YI[q], ln.ZI[q], ln.E2, AX[q], AY[q], AZ[q],
+                           PP[q]);
+        }
+      }
+    } else if (IPT == 2) {
+      // two i-particles per lane: each staged pair serves both (two chains)
+#pragma unroll 1
+      for (int t = 0; t < kPairs; t++) {
+        const float4 p0 = st.P0[t], p1 = st.P1[t];
+#pragma unroll
+        for (int q = 0; q < IPT; q++)
+          interact2<GUARD>(p0, p1, ln.XI[q], ln.YI[q], ln.ZI[q], ln.E2, AX[q], AY[q], AZ[q],
+                           PP[q]);
       }
     } else if (AFD_FORCE_ILP2 && S == 1) {
       f2 BX = Z0, BY = Z0, BZ = Z0, BP = Z0;
@@ -483,12 +510,15 @@ __device__ __forceinline__ void run_list(WarpStage<QUAD, CH> &st, const Lane<IPT
 
 template <bool GUARD, bool QUAD, int FAR, int S, int IPT, int CH>
 __device__ __forceinline__ void run_unit(WarpStage<QUAD, CH> &st, const ForceArgs &a, uint32_t g,
-                                         const Lane<IPT> &ln, Sums *sm, int64_t self_at) {
+                                         const Lane<IPT> &ln, Sums *sm, const int64_t *self_at) {
   run_list<GUARD, QUAD, FAR, S, IPT, CH>(st, ln, sm, a.epj, a.off_e[g], a.off_e[g + 1], a.jhi,
                                          a.jlo, nullptr, nullptr, nullptr, false, a.eps2,
                                          self_at, a.n_epj, a.epj ? a.n : a.n_epj);
+  int64_t none[IPT];
+#pragma unroll
+  for (int q = 0; q < IPT; q++) none[q] = -1;
   run_list<GUARD, QUAD, FAR, S, IPT, CH>(st, ln, sm, a.spj, a.off_s[g], a.off_s[g + 1], a.shi,
-                                         a.slo, a.sq0, a.sq1, a.nodef, QUAD, a.eps2, -1, a.n_spj,
+                                         a.slo, a.sq0, a.sq1, a.nodef, QUAD, a.eps2, none, a.n_spj,
                                          a.spj ? a.n_cells : a.n_spj);
 }
 
@@ -533,10 +563,13 @@ __device__ __forceinline__ void unit_body(const ForceArgs &a, WarpStage<QUAD, CH
   for (int q = 0; q < IPT; q++)
     sm[q].sx = sm[q].sy = sm[q].sz = sm[q].sp = sm[q].cx = sm[q].cy = sm[q].cz = sm[q].cp = 0.0f;
   __syncwarp();
-  // EPJ-list position of this lane's own particle (-1: not on the list)
+  // EPJ-list positions of this lane's own particles (-1: not on the list)
   const uint32_t gs = a.g_self[g];
-  const int64_t self_at =
-      (gs && active[0]) ? (int64_t)a.off_e[g] + (int64_t)(gs - 1u) + (int64_t)il[0] : -1;
+  int64_t self_at[IPT];
+#pragma unroll
+  for (int q = 0; q < IPT; q++)
+    self_at[q] =
+        (gs && active[q]) ? (int64_t)a.off_e[g] + (int64_t)(gs - 1u) + (int64_t)il[q] : -1;
   run_unit<GUARD, QUAD, FAR, S, IPT, CH>(st, a, g, ln, sm, self_at);
 #pragma unroll
   for (int q = 0; q < IPT; q++) {
@@ -562,21 +595,37 @@ __device__ __forceinline__ void unit_body(const ForceArgs &a, WarpStage<QUAD, CH
 // streams of W = 32 >> sidx particles, lane = stream * W + particle.
 template <bool GUARD, bool QUAD, int FAR, int CH>
 __device__ __forceinline__ void force_unit(const ForceArgs &a, WarpStage<QUAD, CH> &st, int lane,
-                                           int64_t u) {
+                                           int64_t u, bool pair) {
   const uint2 info = a.u_info[u];
   if (!AFD_IN(info.x, a.n_groups, "force unit group")) return;
   const uint32_t g = info.x, ioff = info.y & 0xffffu;
   const int sidx = (int)((info.y >> 16) & 3u);
+  if constexpr (!QUAD) {
+    if (pair) {
+      unit_body<GUARD, QUAD, FAR, 1, 2, CH>(a, st, lane, g, ioff);
+      return;
+    }
+  }
   if (sidx == 0) unit_body<GUARD, QUAD, FAR, 1, 1, CH>(a, st, lane, g, ioff);
   else if (sidx == 1) unit_body<GUARD, QUAD, FAR, 2, 1, CH>(a, st, lane, g, ioff);
   else unit_body<GUARD, QUAD, FAR, 4, 1, CH>(a, st, lane, g, ioff);
 }
 
-// The unit at launch position k of [u_base, n_units).
-__device__ __forceinline__ int64_t launch_unit(const ForceArgs &a, int64_t k) {
-  if (!a.u_order) return a.u_base + k;
-  const int64_t u = (int64_t)a.u_order[k];
-  return AFD_IN(u, (uint64_t)a.n_units, "force unit order") ? u : a.u_base + k;
+// The work item at launch position k: without a launch order, unit
+// u_base + k; with one, entry k of the order (false: past the last item).
+// An entry is a unit index, bit 31 set when the warp also takes the group's
+// next unit (two i-particles per lane).
+__device__ __forceinline__ bool launch_item(const ForceArgs &a, int64_t k, int64_t &u, bool &pair) {
+  pair = false;
+  if (!a.u_order) {
+    u = a.u_base + k;
+    return u < a.n_units;
+  }
+  if (k >= (int64_t)*a.n_items) return false;
+  const uint32_t e = a.u_order[k];
+  u = (int64_t)(e & 0x7fffffffu);
+  pair = (e >> 31) != 0u;
+  return AFD_IN(u, (uint64_t)a.n_units, "force unit order");
 }
 
 // Block shape is a launch choice (2, 4 or 8 warps): each warp's staging area
@@ -592,17 +641,21 @@ __global__ void __launch_bounds__(kForceMaxThreads, QUAD ? 2 : AFD_FORCE_MIN_BLO
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if (AFD_FORCE_PERSISTENT) {
     for (;;) {
-      unsigned long long u = 0;
-      if (lane == 0) u = atomicAdd(a.queue, 1ull);
-      u = __shfl_sync(0xffffffffu, u, 0);
-      if ((int64_t)u + a.u_base >= a.n_units) return;
-      force_unit<GUARD, QUAD, FAR, CH>(a, stage[w], lane, launch_unit(a, (int64_t)u));
+      unsigned long long k = 0;
+      if (lane == 0) k = atomicAdd(a.queue, 1ull);
+      k = __shfl_sync(0xffffffffu, k, 0);
+      int64_t u;
+      bool pair;
+      if ((int64_t)k + a.u_base >= a.n_units || !launch_item(a, (int64_t)k, u, pair)) return;
+      force_unit<GUARD, QUAD, FAR, CH>(a, stage[w], lane, u, pair);
       __syncwarp();
     }
   } else {
     const int64_t k = (int64_t)blockIdx.x * nw + w;
-    if (a.u_base + k >= a.n_units) return;
-    force_unit<GUARD, QUAD, FAR, CH>(a, stage[w], lane, launch_unit(a, k));
+    int64_t u;
+    bool pair;
+    if (a.u_base + k >= a.n_units || !launch_item(a, k, u, pair)) return;
+    force_unit<GUARD, QUAD, FAR, CH>(a, stage[w], lane, u, pair);
   }
 }
 
@@ -639,42 +692,70 @@ __global__ void k_materialize(uint64_t n, const uint32_t *__restrict__ idx,
   }
 }
 
-// Launch order of the force units. A unit's warp streams its group's whole
-// list (split over S j-streams for the last, partial unit), so its time
-// follows the list work L / S. A block's warp slots are freed only when its
-// slowest warp ends, and blocks are dispatched in index order: sorted by
-// work, the warps of a block carry equal work, and longest first the launch
-// also ends without a few long units running alone. A counting sort over
-// 256 buckets of L / S (bucket 0 = the most work). The order only
-// schedules: every unit writes its own particles.
+// Launch order of the force units. A warp takes one work item: a unit, or
+// (monopole lists) two consecutive full units of one group, which share the
+// group's list -- each lane then carries two i-particles, and every staged
+// j-pair serves 64 particles instead of 32. An item's warp streams its
+// group's whole list (split over S j-streams for the last, partial unit), so
+// its time follows the list work L * IPT / S. A block's warp slots are freed
+// only when its slowest warp ends, and blocks are dispatched in index order:
+// sorted by work, the warps of a block carry equal work, and longest first
+// the launch also ends without a few long items running alone. A counting
+// sort over 256 buckets of that work (bucket 0 = the most work). The order
+// only schedules: every item writes its own particles.
 constexpr int kOrderBuckets = 256;
+constexpr uint32_t kNoItem = 0xffffffffu;  // the second unit of a pair
+constexpr uint32_t kPairBit = 0x80000000u;
 
-__device__ __forceinline__ uint32_t unit_work(const uint2 *u_info, const uint64_t *off_e,
-                                              const uint64_t *off_s, int64_t u) {
+// The item unit u starts: its work, kPairBit when it takes the group's next
+// unit too, or kNoItem when the previous unit took it.
+__device__ __forceinline__ uint32_t unit_item(const uint2 *u_info, const uint32_t *g_count,
+                                              const uint64_t *off_e, const uint64_t *off_s,
+                                              int64_t u, bool pairs) {
   const uint2 info = u_info[u];
-  const uint32_t g = info.x;
+  const uint32_t g = info.x, ioff = info.y & 0xffffu;
+  const uint32_t sidx = (info.y >> 16) & 3u;
+  bool pair = false;
+  if (pairs && sidx == 0u) {
+    const uint32_t cn = g_count[g];
+    const bool full = ioff + 32u <= cn;
+    if ((ioff & 32u) != 0u && full) return kNoItem;  // odd slot, full: its even neighbour pairs it
+    pair = (ioff & 32u) == 0u && ioff + 64u <= cn;
+  }
   const uint64_t L = (off_e[g + 1] - off_e[g]) + (off_s[g + 1] - off_s[g]);
-  const uint64_t w = L >> ((info.y >> 16) & 3u);
-  return w > 0xffffffffull ? 0xffffffffu : (uint32_t)w;
+  uint64_t w = pair ? 2u * L : (L >> sidx);
+  if (w > 0x7ffffffeull) w = 0x7ffffffeull;
+  return (uint32_t)w | (pair ? kPairBit : 0u);
 }
 
-// hist[0 .. kOrderBuckets): bucket counts, hist[kOrderBuckets]: the largest work
+// hist[0 .. kOrderBuckets): bucket counts, hist[kOrderBuckets]: the largest
+// work, hist[kOrderBuckets + 1]: the number of items
 __global__ void k_unit_work(int64_t u0, int64_t nu, const uint2 *__restrict__ u_info,
+                            const uint32_t *__restrict__ g_count,
                             const uint64_t *__restrict__ off_e, const uint64_t *__restrict__ off_s,
-                            uint32_t *__restrict__ work, uint32_t *__restrict__ hist) {
-  uint32_t wmax = 0;
+                            bool pairs, uint32_t *__restrict__ work, uint32_t *__restrict__ hist) {
+  uint32_t wmax = 0, items = 0;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nu;
        k += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t w = unit_work(u_info, off_e, off_s, u0 + k);
+    const uint32_t w = unit_item(u_info, g_count, off_e, off_s, u0 + k, pairs);
     work[k] = w;
-    wmax = max(wmax, w);
+    if (w != kNoItem) {
+      wmax = max(wmax, w & ~kPairBit);
+      items++;
+    }
   }
-  for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(&hist[kOrderBuckets], wmax);
+  for (int o = 16; o > 0; o >>= 1) {
+    wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+    items += __shfl_xor_sync(0xffffffffu, items, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&hist[kOrderBuckets], wmax);
+    if (items) atomicAdd(&hist[kOrderBuckets + 1], items);
+  }
 }
 
 __device__ __forceinline__ int order_bucket(uint32_t w, uint32_t wmax) {
-  const int b = (int)(((uint64_t)w * kOrderBuckets) / ((uint64_t)wmax + 1u));
+  const int b = (int)(((uint64_t)(w & ~kPairBit) * kOrderBuckets) / ((uint64_t)wmax + 1u));
   return kOrderBuckets - 1 - b;
 }
 
@@ -686,7 +767,7 @@ __global__ void k_unit_hist(int64_t nu, const uint32_t *__restrict__ work,
   const uint32_t wmax = hist[kOrderBuckets];
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nu;
        k += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(&h[order_bucket(work[k], wmax)], 1u);
+    if (work[k] != kNoItem) atomicAdd(&h[order_bucket(work[k], wmax)], 1u);
   __syncthreads();
   for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x)
     if (h[b]) atomicAdd(&hist[b], h[b]);
@@ -713,8 +794,11 @@ __global__ void k_unit_scatter(int64_t u0, int64_t nu, const uint32_t *__restric
   const uint32_t wmax = hist[kOrderBuckets];
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nu;
        k += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t pos = atomicAdd(&hist[order_bucket(work[k], wmax)], 1u);
-    if (AFD_IN(pos, (uint64_t)nu, "unit order position")) order[pos] = (uint32_t)(u0 + k);
+    const uint32_t w = work[k];
+    if (w == kNoItem) continue;
+    const uint32_t pos = atomicAdd(&hist[order_bucket(w, wmax)], 1u);
+    if (AFD_IN(pos, (uint64_t)nu, "unit order position"))
+      order[pos] = (uint32_t)(u0 + k) | (w & kPairBit);
   }
 }
 
@@ -726,18 +810,23 @@ int order_units(afd_ctx *c) {
   const int64_t u1 = c->share_parts > 1 ? c->share_u1 : c->n_units;
   const int64_t nu = u1 - u0;
   if (nu <= 0) return AFD_OK;
+  if (c->n_units >= (int64_t)kPairBit) return AFD_OK;  // unit ids need bit 31: index order
   if (reserve(c->u_order, sizeof(uint32_t) * (size_t)nu) != AFD_OK ||
       reserve(c->u_work, sizeof(uint32_t) * (size_t)nu) != AFD_OK ||
-      reserve(c->u_hist, sizeof(uint32_t) * (kOrderBuckets + 1)) != AFD_OK)
+      reserve(c->u_hist, sizeof(uint32_t) * (kOrderBuckets + 2)) != AFD_OK)
     return AFD_ERR_OOM;
   uint32_t *hist = ptr<uint32_t>(c->u_hist), *work = ptr<uint32_t>(c->u_work);
-  if (cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (kOrderBuckets + 1), c->stream) != cudaSuccess)
+  if (cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (kOrderBuckets + 2), c->stream) != cudaSuccess)
     return AFD_ERR_CUDA;
+  // two i-particles per lane for the monopole kernel only (the quadrupole
+  // kernel's registers are spent on the far-field terms)
+  const bool pairs = AFD_FORCE_PAIRS && !c->cfg.multipole;
   constexpr int kT = 256;
   const int64_t want = (nu + kT - 1) / kT;
   const unsigned nb = (unsigned)(want < 152 * 8 ? want : 152 * 8);
-  k_unit_work<<<nb, kT, 0, c->stream>>>(u0, nu, ptr<uint2>(c->u_info), ptr<uint64_t>(c->epj_off),
-                                        ptr<uint64_t>(c->spj_off), work, hist);
+  k_unit_work<<<nb, kT, 0, c->stream>>>(u0, nu, ptr<uint2>(c->u_info), ptr<uint32_t>(c->g_count),
+                                        ptr<uint64_t>(c->epj_off), ptr<uint64_t>(c->spj_off),
+                                        pairs, work, hist);
   k_unit_hist<<<nb, kT, 0, c->stream>>>(nu, work, hist);
   k_unit_scan<<<1, kOrderBuckets, 0, c->stream>>>(hist);
   k_unit_scatter<<<nb, kT, 0, c->stream>>>(u0, nu, work, hist, ptr<uint32_t>(c->u_order));
@@ -783,6 +872,7 @@ int launch_force_impl(afd_ctx *c, float *acc4, bool materialized) {
   a.n_units = u1;
   a.u_base = u0;
   a.u_order = c->u_order_ok ? ptr<uint32_t>(c->u_order) : nullptr;
+  a.n_items = c->u_order_ok ? ptr<uint32_t>(c->u_hist) + kOrderBuckets + 1 : nullptr;
   a.u_info = ptr<uint2>(c->u_info);
   a.g_first = ptr<uint32_t>(c->g_first);
   a.g_count = ptr<uint32_t>(c->g_count);
