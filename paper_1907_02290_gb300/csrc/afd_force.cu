@@ -33,8 +33,8 @@
 namespace afd {
 namespace {
 
-#ifndef AFD_FORCE_MIN_BLOCKS
-#define AFD_FORCE_MIN_BLOCKS 6  // resident 128-thread blocks per SM the register budget targets (80 registers)
+#ifndef AFD_FORCE_MAX_REGS
+#define AFD_FORCE_MAX_REGS 96  // register budget of the monopole kernel (5 blocks of 4 warps per SM)
 #endif
 #ifndef AFD_FORCE_ILP2
 #define AFD_FORCE_ILP2 1  // two independent accumulator chains per lane
@@ -630,11 +630,11 @@ __device__ __forceinline__ bool launch_item(const ForceArgs &a, int64_t k, int64
 
 // Block shape is a launch choice (2, 4 or 8 warps): each warp's staging area
 // lives in dynamic shared memory. The register budget is the same for every
-// shape: 80 per thread with FP32 monopoles, 128 with quadrupoles.
+// shape: 96 per thread with FP32 monopoles, 128 with quadrupoles.
 constexpr int kForceMaxThreads = 256;
 
 template <bool GUARD, bool QUAD, int FAR, int CH>
-__global__ void __launch_bounds__(kForceMaxThreads, QUAD ? 2 : AFD_FORCE_MIN_BLOCKS / 2)
+__global__ void __launch_bounds__(kForceMaxThreads) __maxnreg__(QUAD ? 128 : AFD_FORCE_MAX_REGS)
     k_force(ForceArgs a) {
   extern __shared__ __align__(16) unsigned char force_smem[];
   WarpStage<QUAD, CH> *stage = reinterpret_cast<WarpStage<QUAD, CH> *>(force_smem);
@@ -910,7 +910,7 @@ int launch_force_impl(afd_ctx *c, float *acc4, bool materialized) {
   if (AFD_FORCE_PERSISTENT) {
     if (cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), c->stream) != cudaSuccess)
       return AFD_ERR_CUDA;
-    const unsigned cap = 152u * 4u * AFD_FORCE_MIN_BLOCKS / (unsigned)warps;  // resident warps per GPU
+    const unsigned cap = 152u * (65536u / (32u * AFD_FORCE_MAX_REGS)) / (unsigned)warps;  // resident warps per GPU
     if (nb > cap) nb = cap;
   }
   const bool guard = !(a.eps2 > 0.0f);
