@@ -463,7 +463,7 @@ __device__ __forceinline__ void run_list(WarpStage<QUAD, CH> &st, const Lane<IPT
       }
     } else if (IPT == 2) {
       // two i-particles per lane: each staged pair serves both (two chains)
-#pragma unroll 1
+#pragma unroll 2
       for (int t = 0; t < kPairs; t++) {
         const float4 p0 = st.P0[t], p1 = st.P1[t];
 #pragma unroll
