@@ -119,7 +119,9 @@ int afd_tree_build(afd_ctx *ctx, const double *x, const double *y, const double 
  * walk under the opening-angle criterion producing, per group, a list of
  * particle indices (EPJ) and a list of cell indices (SPJ) into the device
  * arrays. mode is AFD_MAKE_LIST or AFD_MAKE_LIST_FOR_REUSE; the latter keeps
- * the lists for later AFD_REUSE_LIST steps. Needs a tree. Synchronises once. */
+ * the lists for later AFD_REUSE_LIST steps. Also orders the force kernel's
+ * work items by list work, longest first (a launch order only: the forces do
+ * not depend on it). Needs a tree. Synchronises once. */
 int afd_make_interaction_lists(afd_ctx *ctx, int mode);
 
 /* Reusing step (Section 4.2): keep the topology, groups and lists; reorder
@@ -137,8 +139,10 @@ int afd_reuse_lists(afd_ctx *ctx, const double *x, const double *y, const double
 
 /* Force kernel (Section 5, the indirect-index dispatch): for every group and
  * every EPJ / SPJ index of its list, sum the softened attraction on each of
- * the group's particles. acc4: device, n x (ax, ay, az, phi) floats, caller
- * order, overwritten. Does not synchronise. */
+ * the group's particles. One warp takes 32 of a group's particles, or 64
+ * (two full 32-particle units of one group, monopole lists), in the launch
+ * order set by afd_make_interaction_lists. acc4: device, n x (ax, ay, az,
+ * phi) floats, caller order, overwritten. Does not synchronise. */
 int afd_calc_force(afd_ctx *ctx, float *acc4);
 
 /* The top-level call of Section 5 (calcForceAllAndWriteBackMultiWalkIndex):
