@@ -29,6 +29,7 @@
 // 1 FADD (phi) -- 23 flops by the paper's convention (Section 6.2, n_op).
 #include "afd_f32x2.cuh"
 #include "afd_internal.cuh"
+#include "afd_order.cuh"
 
 namespace afd {
 namespace {
@@ -692,23 +693,16 @@ __global__ void k_materialize(uint64_t n, const uint32_t *__restrict__ idx,
   }
 }
 
-// Launch order of the force units. A warp takes one work item: a unit, or
+// Launch order of the force work items. A warp takes one item: a unit, or
 // (monopole lists) two consecutive full units of one group, which share the
 // group's list -- each lane then carries two i-particles, and every staged
 // j-pair serves 64 particles instead of 32. An item's warp streams its
 // group's whole list (split over S j-streams for the last, partial unit), so
-// its time follows the list work L * IPT / S. A block's warp slots are freed
-// only when its slowest warp ends, and blocks are dispatched in index order:
-// sorted by work, the warps of a block carry equal work, and longest first
-// the launch also ends without a few long items running alone. A counting
-// sort over 256 buckets of that work (bucket 0 = the most work). The order
-// only schedules: every item writes its own particles.
-constexpr int kOrderBuckets = 256;
-constexpr uint32_t kNoItem = 0xffffffffu;  // the second unit of a pair
-constexpr uint32_t kPairBit = 0x80000000u;
+// its time follows the list work L * IPT / S; the items are launched largest
+// work first (afd_order.cuh). Every item writes its own particles.
 
-// The item unit u starts: its work, kPairBit when it takes the group's next
-// unit too, or kNoItem when the previous unit took it.
+// The item unit u starts: its work, kOrderFlag when it takes the group's
+// next unit too, or kNoItem when the previous unit took it.
 __device__ __forceinline__ uint32_t unit_item(const uint2 *u_info, const uint32_t *g_count,
                                               const uint64_t *off_e, const uint64_t *off_s,
                                               int64_t u, bool pairs) {
@@ -724,12 +718,10 @@ __device__ __forceinline__ uint32_t unit_item(const uint2 *u_info, const uint32_
   }
   const uint64_t L = (off_e[g + 1] - off_e[g]) + (off_s[g + 1] - off_s[g]);
   uint64_t w = pair ? 2u * L : (L >> sidx);
-  if (w > 0x7ffffffeull) w = 0x7ffffffeull;
-  return (uint32_t)w | (pair ? kPairBit : 0u);
+  if (w > kOrderWorkMax) w = kOrderWorkMax;
+  return (uint32_t)w | (pair ? kOrderFlag : 0u);
 }
 
-// hist[0 .. kOrderBuckets): bucket counts, hist[kOrderBuckets]: the largest
-// work, hist[kOrderBuckets + 1]: the number of items
 __global__ void k_unit_work(int64_t u0, int64_t nu, const uint2 *__restrict__ u_info,
                             const uint32_t *__restrict__ g_count,
                             const uint64_t *__restrict__ off_e, const uint64_t *__restrict__ off_s,
@@ -740,66 +732,11 @@ __global__ void k_unit_work(int64_t u0, int64_t nu, const uint2 *__restrict__ u_
     const uint32_t w = unit_item(u_info, g_count, off_e, off_s, u0 + k, pairs);
     work[k] = w;
     if (w != kNoItem) {
-      wmax = max(wmax, w & ~kPairBit);
+      wmax = max(wmax, w & ~kOrderFlag);
       items++;
     }
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
-    items += __shfl_xor_sync(0xffffffffu, items, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicMax(&hist[kOrderBuckets], wmax);
-    if (items) atomicAdd(&hist[kOrderBuckets + 1], items);
-  }
-}
-
-__device__ __forceinline__ int order_bucket(uint32_t w, uint32_t wmax) {
-  const int b = (int)(((uint64_t)(w & ~kPairBit) * kOrderBuckets) / ((uint64_t)wmax + 1u));
-  return kOrderBuckets - 1 - b;
-}
-
-__global__ void k_unit_hist(int64_t nu, const uint32_t *__restrict__ work,
-                            uint32_t *__restrict__ hist) {
-  __shared__ uint32_t h[kOrderBuckets];
-  for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x) h[b] = 0u;
-  __syncthreads();
-  const uint32_t wmax = hist[kOrderBuckets];
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nu;
-       k += (int64_t)gridDim.x * blockDim.x)
-    if (work[k] != kNoItem) atomicAdd(&h[order_bucket(work[k], wmax)], 1u);
-  __syncthreads();
-  for (int b = threadIdx.x; b < kOrderBuckets; b += blockDim.x)
-    if (h[b]) atomicAdd(&hist[b], h[b]);
-}
-
-// one block of kOrderBuckets threads: bucket counts -> first position of
-// each bucket (exclusive scan), in place
-__global__ void k_unit_scan(uint32_t *__restrict__ hist) {
-  __shared__ uint32_t v[kOrderBuckets];
-  const int t = threadIdx.x;
-  v[t] = hist[t];
-  __syncthreads();
-  for (int o = 1; o < kOrderBuckets; o <<= 1) {
-    const uint32_t add = t >= o ? v[t - o] : 0u;
-    __syncthreads();
-    v[t] += add;
-    __syncthreads();
-  }
-  hist[t] = t > 0 ? v[t - 1] : 0u;
-}
-
-__global__ void k_unit_scatter(int64_t u0, int64_t nu, const uint32_t *__restrict__ work,
-                               uint32_t *__restrict__ hist, uint32_t *__restrict__ order) {
-  const uint32_t wmax = hist[kOrderBuckets];
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nu;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t w = work[k];
-    if (w == kNoItem) continue;
-    const uint32_t pos = atomicAdd(&hist[order_bucket(w, wmax)], 1u);
-    if (AFD_IN(pos, (uint64_t)nu, "unit order position"))
-      order[pos] = (uint32_t)(u0 + k) | (w & kPairBit);
-  }
+  order_reduce(hist, wmax, items);
 }
 
 }  // namespace
@@ -810,7 +747,7 @@ int order_units(afd_ctx *c) {
   const int64_t u1 = c->share_parts > 1 ? c->share_u1 : c->n_units;
   const int64_t nu = u1 - u0;
   if (nu <= 0) return AFD_OK;
-  if (c->n_units >= (int64_t)kPairBit) return AFD_OK;  // unit ids need bit 31: index order
+  if (c->n_units >= (int64_t)kOrderFlag) return AFD_OK;  // unit ids need bit 31: index order
   if (reserve(c->u_order, sizeof(uint32_t) * (size_t)nu) != AFD_OK ||
       reserve(c->u_work, sizeof(uint32_t) * (size_t)nu) != AFD_OK ||
       reserve(c->u_hist, sizeof(uint32_t) * (kOrderBuckets + 2)) != AFD_OK)
@@ -827,11 +764,10 @@ int order_units(afd_ctx *c) {
   k_unit_work<<<nb, kT, 0, c->stream>>>(u0, nu, ptr<uint2>(c->u_info), ptr<uint32_t>(c->g_count),
                                         ptr<uint64_t>(c->epj_off), ptr<uint64_t>(c->spj_off),
                                         pairs, work, hist);
-  k_unit_hist<<<nb, kT, 0, c->stream>>>(nu, work, hist);
-  k_unit_scan<<<1, kOrderBuckets, 0, c->stream>>>(hist);
-  k_unit_scatter<<<nb, kT, 0, c->stream>>>(u0, nu, work, hist, ptr<uint32_t>(c->u_order));
-  c->launches += 4;
-  if (cudaGetLastError() != cudaSuccess) return AFD_ERR_CUDA;
+  c->launches++;
+  if (order_by_work(c->stream, nu, u0, work, hist, ptr<uint32_t>(c->u_order), &c->launches) !=
+      cudaSuccess)
+    return AFD_ERR_CUDA;
   c->u_order_ok = true;
   return AFD_OK;
 }

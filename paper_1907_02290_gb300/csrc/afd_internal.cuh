@@ -128,6 +128,10 @@ struct afd_ctx {
   // density work items (unit, list segment), per-unit segment counts and
   // first items, partial sums of units with several segments
   afd::DevBuf nbr_seg_cnt, nbr_seg_off, nbr_items, nbr_part;
+  // density items' launch order, largest work first (with its work and
+  // bucket scratch)
+  afd::DevBuf nbr_order, nbr_work, nbr_hist;
+  bool nbr_order_ok = false;
   uint64_t n_nbr = 0, nbr_pairs = 0;
   int64_t n_items = 0;
   bool nbr_multi = false;  // some unit has several segments

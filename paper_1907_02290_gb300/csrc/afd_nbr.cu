@@ -48,6 +48,7 @@
 
 #include "afd_f32x2.cuh"
 #include "afd_internal.cuh"
+#include "afd_order.cuh"
 
 namespace afd {
 namespace {
@@ -214,6 +215,7 @@ constexpr float kFar = 1e18f;  // staging pad: a massless j far outside any supp
 struct DensArgs {
   int64_t n_items;
   const uint2 *items;        // (unit, segment)
+  const uint32_t *order;     // launch order of the items (null: index order)
   const uint32_t *seg_cnt;   // per unit: its segments
   const uint32_t *seg_off;   // per unit: its first item
   const uint2 *u_info;
@@ -407,8 +409,10 @@ __device__ __forceinline__ void density_item(const DensArgs &a, DensStage &st, i
 __global__ void __launch_bounds__(kDensWarps * 32) k_density(DensArgs a) {
   __shared__ __align__(16) DensStage stage[kDensWarps];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t item = (int64_t)blockIdx.x * kDensWarps + w;
-  if (item >= a.n_items) return;
+  const int64_t k = (int64_t)blockIdx.x * kDensWarps + w;
+  if (k >= a.n_items) return;
+  const int64_t item = a.order ? (int64_t)a.order[k] : k;
+  if (!AFD_IN(item, (uint64_t)a.n_items, "density item order")) return;
   const uint32_t u = a.items[item].x;
   if (!AFD_IN(u, a.n_units, "density item unit")) return;
   const int sidx = (int)((a.u_info[u].y >> 16) & 3u);
@@ -457,6 +461,28 @@ __global__ void k_seg_fill(int64_t n_units, const uint32_t *__restrict__ seg_cnt
   for (uint32_t k = 0; k < seg_cnt[u]; k++) items[seg_off[u] + k] = make_uint2((uint32_t)u, k);
 }
 
+// Work of each density item: its segment's list entries per j-stream (the
+// reach-box test runs over every entry); the items are launched largest
+// work first (afd_order.cuh).
+__global__ void k_dens_work(int64_t n_items, const uint2 *__restrict__ items,
+                            const uint2 *__restrict__ u_info, const uint64_t *__restrict__ off,
+                            uint32_t *__restrict__ work, uint32_t *__restrict__ hist) {
+  uint32_t wmax = 0, cnt = 0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_items;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const uint2 it = items[k];
+    const uint2 info = u_info[it.x];
+    const uint32_t g = info.x;
+    const uint64_t b0 = off[g] + (uint64_t)it.y * kSegLen, e = off[g + 1];
+    const uint64_t len = e > b0 ? (e - b0 < kSegLen ? e - b0 : kSegLen) : 0u;
+    const uint32_t w = (uint32_t)(len >> ((info.y >> 16) & 3u));
+    work[k] = w;
+    wmax = max(wmax, w);
+    cnt++;
+  }
+  order_reduce(hist, wmax, cnt);
+}
+
 inline unsigned blocks_for(int64_t threads) { return (unsigned)((threads + kThreads - 1) / kThreads); }
 
 int nbr_boxes(afd_ctx *c, const double *h, double skin) {
@@ -500,6 +526,7 @@ int nbr_items(afd_ctx *c) {
   int st;
   c->n_items = 0;
   c->nbr_multi = false;
+  c->nbr_order_ok = false;
   if (nu == 0) return AFD_OK;
   if ((st = reserve(c->nbr_seg_cnt, sizeof(uint32_t) * (size_t)nu))) return st;
   if ((st = reserve(c->nbr_seg_off, sizeof(uint32_t) * (size_t)(nu + 1)))) return st;
@@ -524,7 +551,25 @@ int nbr_items(afd_ctx *c) {
     return st;
   k_seg_fill<<<blocks_for(nu), kThreads, 0, c->stream>>>(nu, cnt, off, ptr<uint2>(c->nbr_items));
   c->launches++;
-  return cudaGetLastError() == cudaSuccess ? AFD_OK : AFD_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return AFD_ERR_CUDA;
+  // the items' launch order, largest work first
+  const int64_t ni = c->n_items;
+  if (ni >= (int64_t)kOrderFlag) return AFD_OK;  // item ids need bit 31: index order
+  if ((st = reserve(c->nbr_order, sizeof(uint32_t) * (size_t)ni))) return st;
+  if ((st = reserve(c->nbr_work, sizeof(uint32_t) * (size_t)ni))) return st;
+  if ((st = reserve(c->nbr_hist, sizeof(uint32_t) * (kOrderBuckets + 2)))) return st;
+  uint32_t *hist = ptr<uint32_t>(c->nbr_hist), *work = ptr<uint32_t>(c->nbr_work);
+  if (cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (kOrderBuckets + 2), c->stream) != cudaSuccess)
+    return AFD_ERR_CUDA;
+  const int64_t want = (ni + kThreads - 1) / kThreads;
+  k_dens_work<<<(unsigned)(want < 152 * 8 ? want : 152 * 8), kThreads, 0, c->stream>>>(
+      ni, ptr<uint2>(c->nbr_items), ptr<uint2>(c->u_info), ptr<uint64_t>(c->nbr_off), work, hist);
+  c->launches++;
+  if (order_by_work(c->stream, ni, 0, work, hist, ptr<uint32_t>(c->nbr_order), &c->launches) !=
+      cudaSuccess)
+    return AFD_ERR_CUDA;
+  c->nbr_order_ok = true;
+  return AFD_OK;
 }
 
 // Make the device current for the call and restore the caller's afterwards.
@@ -577,6 +622,7 @@ int afd_calc_density(afd_ctx *c, const double *h, float *rho, float *nnb) {
   DensArgs a;
   a.n_items = c->n_items;
   a.items = ptr<uint2>(c->nbr_items);
+  a.order = c->nbr_order_ok ? ptr<uint32_t>(c->nbr_order) : nullptr;
   a.seg_cnt = ptr<uint32_t>(c->nbr_seg_cnt);
   a.seg_off = ptr<uint32_t>(c->nbr_seg_off);
   a.u_info = ptr<uint2>(c->u_info);
