@@ -1,14 +1,17 @@
 // Force kernel (Section 5: the indirect-index dispatch; Eq. kernel of
-// Section 6.2). Work unit = (i-group, chunk of 32 of its particles); one
-// warp per unit. The warp walks the group's EPJ list, then its SPJ list, 32
-// entries at a time: each lane gathers one j by index (float4 hi + float4 lo
-// of a particle or of a cell's centre of mass), forms its coordinates
-// relative to the group origin, stages them in shared memory, and then every
-// lane runs the 32 interactions against its own i-particle. The gathers of
-// the next chunk are issued before the current chunk is computed.
+// Section 6.2). Work unit = (i-group, chunk of 32 of its particles); a warp
+// takes one work item: a unit, or two consecutive full units of one group
+// (monopole lists), which share the group's list, each lane then holding two
+// i-particles. The warp walks the group's EPJ list, then its SPJ list, 32 or
+// 64 entries at a time (a launch choice): each lane gathers its j's by index
+// (float4 hi + float4 lo of a particle or of a cell's centre of mass), forms
+// their coordinates relative to the group origin, stages them in shared
+// memory, and then every lane runs the chunk's interactions against its own
+// i-particle(s). The gathers of the next chunk are issued before the current
+// chunk is computed. The items are launched largest list work first.
 //
 // Packed arithmetic: each lane evaluates two j's (an even and an odd slot
-// of the chunk) against its i in one pass of f32x2 instructions -- 13
+// of the chunk) against an i in one pass of f32x2 instructions -- 13
 // packed FP32 operations and two MUFU.RSQ per two interactions -- which
 // halves the issue slots of the scalar loop.
 //
@@ -21,9 +24,10 @@
 // hi/lo FP32 pairs, (x_hi - c_hi) + (x_lo - c_lo): when x and c are close
 // the hi difference is exact (Sterbenz) and the result equals the FP64
 // difference rounded to FP32 up to the tiny lo terms; when they are far
-// apart the relative rounding error is that of one FP32 operation. Each
-// chunk's terms are summed in FP32 (one sum per even/odd stream) and the
-// chunk sums are accumulated with Kahan compensation.
+// apart the relative rounding error is that of one FP32 operation. The
+// terms are summed in packed FP32 accumulators (with one i-particle per
+// lane, two of them over alternate j-pairs), and every 128 packed pairs the
+// partial sums are folded into Kahan-compensated accumulators.
 //
 // Per interaction: 3 FADD (dx), 3 FFMA (r^2), 1 MUFU.RSQ, 3 FMUL, 3 FFMA (a),
 // 1 FADD (phi) -- 23 flops by the paper's convention (Section 6.2, n_op).
