@@ -87,6 +87,7 @@ struct afd_ctx {
   // keys, sort and reorder
   afd::DevBuf keys, keys2, perm, perm2, sort_cnt, sort_off;
   afd::DevBuf xs, ys, zs, ms;  // FP64 Morton order
+  afd::DevBuf mxyz;            // m x, m y, m z (3 x n FP64, Morton order): the leaf products of S
   afd::DevBuf jhi, jlo;        // float4 (hi xyz, m) and (lo xyz, 0) per particle
 
   // link

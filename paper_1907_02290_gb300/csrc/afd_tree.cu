@@ -430,7 +430,8 @@ __global__ void __launch_bounds__(kThreads) k_reorder(
     const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
     const double *__restrict__ m, int64_t n, const uint32_t *__restrict__ perm,
     double *__restrict__ xs, double *__restrict__ ys, double *__restrict__ zs,
-    double *__restrict__ ms, float4 *__restrict__ jhi, float4 *__restrict__ jlo, int *status) {
+    double *__restrict__ ms, float4 *__restrict__ jhi, float4 *__restrict__ jlo,
+    double *__restrict__ mxyz, int *status) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const uint32_t i = perm[k];
@@ -441,6 +442,10 @@ __global__ void __launch_bounds__(kThreads) k_reorder(
   ys[k] = vy;
   zs[k] = vz;
   ms[k] = vm;
+  // the mass moment's products, each rounded as the leaf sum takes them
+  mxyz[k] = __dmul_rn(vm, vx);
+  mxyz[n + k] = __dmul_rn(vm, vy);
+  mxyz[2 * n + k] = __dmul_rn(vm, vz);
   float hx, hy, hz, lx, ly, lz;
   split2(vx, hx, lx);
   split2(vy, hy, ly);
@@ -588,6 +593,7 @@ struct MomArgs {
   int64_t n_cells;
   const uint32_t *level, *first, *count, *parent, *child;
   const double *xs, *ys, *zs, *ms;
+  const double *mxyz;  // m x, m y, m z per particle (3 x n_part)
   const uint64_t *keys;
   const double *root;       // 4 doubles per system
   const uint32_t *sys_s;    // system of each sorted particle (null: one system)
@@ -767,12 +773,14 @@ __global__ void __launch_bounds__(kThreads) k_moments_sums(MomArgs a) {
     if (e > f && !AFD_IN(e - 1, a.n_part, "moments leaf range")) {
       climbing = false;
     } else {
+      // the products m x, m y, m z were rounded by the reorder (full warps);
+      // here only the ordered sums run on the leaf's lane
+      const double *mx = a.mxyz, *my = a.mxyz + a.n_part, *mz = a.mxyz + 2 * a.n_part;
       for (uint32_t k = f; k < e; k++) {
-        const double mk = a.ms[k];
-        M = __dadd_rn(M, mk);
-        S[0] = __dadd_rn(S[0], __dmul_rn(mk, a.xs[k]));
-        S[1] = __dadd_rn(S[1], __dmul_rn(mk, a.ys[k]));
-        S[2] = __dadd_rn(S[2], __dmul_rn(mk, a.zs[k]));
+        M = __dadd_rn(M, a.ms[k]);
+        S[0] = __dadd_rn(S[0], mx[k]);
+        S[1] = __dadd_rn(S[1], my[k]);
+        S[2] = __dadd_rn(S[2], mz[k]);
       }
       a.mass[c] = M;
       for (int d = 0; d < 3; d++) a.smom[(size_t)c * 3 + d] = S[d];
@@ -1118,11 +1126,12 @@ int launch_reorder(afd_ctx *c, const double *x, const double *y, const double *z
   for (afd::DevBuf *b : {&c->xs, &c->ys, &c->zs, &c->ms}) AFD_TRY(reserve(*b, sizeof(double) * n));
   AFD_TRY(reserve(c->jhi, sizeof(float4) * n));
   AFD_TRY(reserve(c->jlo, sizeof(float4) * n));
+  AFD_TRY(reserve(c->mxyz, sizeof(double) * 3 * n));
   if (n == 0) return AFD_OK;
   k_reorder<<<blocks_for(n), kThreads, 0, c->stream>>>(
       x, y, z, m, n, ptr<uint32_t>(c->perm), ptr<double>(c->xs), ptr<double>(c->ys),
       ptr<double>(c->zs), ptr<double>(c->ms), ptr<float4>(c->jhi), ptr<float4>(c->jlo),
-      ptr<int>(c->status));
+      ptr<double>(c->mxyz), ptr<int>(c->status));
   c->launches++;
   return ck();
 }
@@ -1214,6 +1223,7 @@ int launch_moments(afd_ctx *c, bool child_blocks, bool need_q) {
   a.ys = ptr<double>(c->ys);
   a.zs = ptr<double>(c->zs);
   a.ms = ptr<double>(c->ms);
+  a.mxyz = ptr<double>(c->mxyz);
   a.keys = ptr<uint64_t>(c->keys);
   a.root = ptr<double>(c->root);
   a.sys_s = c->n_sys > 1 ? ptr<uint32_t>(c->sys_s) : nullptr;
