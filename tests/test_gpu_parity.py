@@ -151,6 +151,35 @@ def test_clustered_and_coincident(env):
     g.close()
 
 
+@pytest.mark.parametrize("sizes,n_grp", [
+    ([33, 63, 64, 65, 95, 96, 97, 128], 128),
+    ([129, 159, 160, 161, 191, 192, 193, 256], 256),
+])
+def test_group_sizes_around_the_unit_pairing(env, sizes, n_grp):
+    """One clump per octant of the root, so each clump is one group of the
+    given size: groups of 63, 64, 65, 95, 96, 97, 128 ... particles cover
+    every case of the force kernel's work items (a 32-particle unit alone,
+    two full units taken by one warp, a partial last unit split into
+    j-streams). Structure bit-exact, forces against the oracle."""
+    _, _, orc = env
+    rng = np.random.default_rng(31)
+    xs, ys, zs = [], [], []
+    for o, k in enumerate(sizes):
+        c = np.array([(o >> 2) & 1, (o >> 1) & 1, o & 1], dtype=np.float64) - 0.5
+        d = rng.normal(scale=0.02, size=(k, 3))
+        xs.append(c[0] + d[:, 0]); ys.append(c[1] + d[:, 1]); zs.append(c[2] + d[:, 2])
+    x, y, z = (np.concatenate(a) for a in (xs, ys, zs))
+    n = x.size
+    p = ics.Particles(x, y, z, np.zeros(n), np.zeros(n), np.zeros(n), np.full(n, 1.0 / n))
+    kw = dict(n_grp=n_grp, theta=0.5, eps=1.0 / 256)
+    g, acc, _ = run_gpu(env, p, **kw)
+    t = orc.Tree(p.x, p.y, p.z, p.m, **kw)
+    check_structure(g, t)
+    assert sorted(t.groups()["count"].tolist()) == sorted(sizes)
+    assert rms_rel_acc(acc, t.force()) <= FORCE_RMS_TOL
+    g.close()
+
+
 @pytest.mark.parametrize("n", [0, 1, 2, 16, 17, 33])
 def test_tiny_sizes(env, n):
     _, _, orc = env
