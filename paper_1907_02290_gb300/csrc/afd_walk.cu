@@ -61,6 +61,7 @@ constexpr uint32_t kChunk = 64;  // records per arena chunk
 
 struct WalkArgs {
   int64_t n_groups;
+  unsigned long long *queue;  // next group (or item) to take, zeroed before each launch
   const float *boxf;
   const uint32_t *g_first, *g_root;
   const float4 *node_f;
@@ -220,6 +221,16 @@ struct MacScratch {
   float4 hin[kMacNH];     // hidden layer 1 of the current 4 cells: [unit]
 };
 
+// The next group (neighbour walk: work item) for this warp. The grid holds
+// only as many warps as are resident at once, and a warp takes its next
+// group when it finishes one: with a fixed group per warp, a block's warp
+// slots stay held until its slowest group is walked.
+__device__ __forceinline__ int64_t take_group(const WalkArgs &a, int lane) {
+  unsigned long long v = 0;
+  if (lane == 0) v = atomicAdd(a.queue, 1ull);
+  return (int64_t)__shfl_sync(0xffffffffu, v, 0);
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
   constexpr bool LEARNED = MODE == kModeLearned, NBR = MODE == kModeNeighbour;
@@ -246,8 +257,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
     if (threadIdx.x == 0) mw.vec[kVecB3] = a.mac_w[kMacOffB3];
     __syncthreads();
   }
-  for (int64_t g = (int64_t)blockIdx.x * kWalkWarps + wib; g < a.n_groups;
-       g += (int64_t)gridDim.x * kWalkWarps) {
+  for (int64_t g = take_group(a, lane); g < a.n_groups; g = take_group(a, lane)) {
     float bmin[3], bmax[3];
     const int64_t gb = NBR ? (int64_t)a.it_group[g] : g;  // the box's group
 #pragma unroll
@@ -655,6 +665,28 @@ struct WalkOut {
   uint64_t n_e = 0, n_s = 0, inter = 0;
 };
 
+// Blocks of k_walk<MODE> resident at once on the device (at most one per
+// four groups): the grid of the dynamically scheduled walk.
+template <int MODE>
+int64_t walk_blocks(int64_t ng) {
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_walk<MODE>, kWalkThreads, 0) !=
+            cudaSuccess ||
+        b < 1)
+      b = 1;
+    per_sm = b;
+  }
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+    sms = 152;
+  const int64_t want = (ng + kWalkWarps - 1) / kWalkWarps;
+  const int64_t cap = (int64_t)per_sm * sms;
+  return want < cap ? want : cap;
+}
+
 // One pass of k_walk<mode> into the record arena (grown to the size the
 // cursors report and the pass repeated when it was too small), the offset
 // scans, the interaction count and the compaction into CSR lists.
@@ -676,8 +708,10 @@ int run_walk(afd_ctx *c, WalkArgs &a, int mode, WalkOut &o, int64_t ng) {
   a.iter_cap = (uint32_t)(2 * c->n_cells + 64);
   a.n_cells = (uint32_t)c->n_cells;
   a.n_groups = ng;
-  int64_t nb = (ng + kWalkWarps - 1) / kWalkWarps;
-  if (nb > 152 * 32) nb = 152 * 32;
+  const int64_t nb = mode == kModeLearned ? walk_blocks<kModeLearned>(ng)
+                     : nbr                ? walk_blocks<kModeNeighbour>(ng)
+                                          : walk_blocks<kModeTheta>(ng);
+  a.queue = ptr<unsigned long long>(c->u64acc) + 4;
   unsigned long long *inter = ptr<unsigned long long>(c->u64acc) + 1;
   uint64_t *pin = static_cast<uint64_t *>(c->pinned);
   for (int attempt = 0;; attempt++) {
@@ -691,7 +725,8 @@ int run_walk(afd_ctx *c, WalkArgs &a, int mode, WalkOut &o, int64_t ng) {
     a.next_l = ptr<uint32_t>(c->next_l);
     a.cap_s = c->arena_cap_s;
     a.cap_l = c->arena_cap_l;
-    if (cudaMemsetAsync(c->arena_cur.p, 0, 2 * sizeof(uint32_t), c->stream) != cudaSuccess)
+    if (cudaMemsetAsync(c->arena_cur.p, 0, 2 * sizeof(uint32_t), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), c->stream) != cudaSuccess)
       return AFD_ERR_CUDA;
     if (mode == kModeLearned && cudaMemsetAsync(c->mac_cnt.p, 0, 3 * sizeof(unsigned long long),
                                                 c->stream) != cudaSuccess)
