@@ -111,7 +111,8 @@ int afd_set_stream(afd_ctx *ctx, void *stream);
  * n device doubles each (caller order), 0 <= n < 2^30 (n = 0 gives an empty
  * tree).
  * Synchronises once. Invalidates saved lists. AFD_ERR_NONFINITE if a
- * coordinate or mass is not finite. */
+ * coordinate or mass is not finite, or if a system's extent has no finite
+ * power-of-two side (1.000001 x the extent above 2^1023). */
 int afd_tree_build(afd_ctx *ctx, const double *x, const double *y, const double *z,
                    const double *m, int64_t n);
 
@@ -406,15 +407,18 @@ int afd_last_force_ms(afd_ctx *ctx, float *ms);
  * must not call cudaMalloc / cudaFree after start-up because those calls can
  * synchronise the device. It needs no context (afd_create allocates).
  *
- * Computes the same root cell as afd_tree_build -- centre (min + max) / 2 per
- * axis, side = the smallest power of two >= 1.000001 x the largest extent
- * (1 for a zero extent; root (0, 0, 0, 1) for n = 0) -- from x, y, z (n
- * device doubles each, caller order), and checks m (n device doubles) for
- * finiteness. root_out: device, 4 doubles (centre x, y, z, side).
- * nonfinite_out: device int, set to 1 when a coordinate or mass is NaN or
- * infinite (NaN coordinates are then left out of the box), else 0. Queued on
- * `stream` (a cudaStream_t; NULL = the legacy default stream); the call does
- * not synchronise.
+ * Computes the same root cell as afd_tree_build, bit for bit (the same
+ * reduction on order-preserving integer keys of the doubles, so a zero
+ * centre has the same sign) -- centre (min + max) / 2 per axis, side = the
+ * smallest power of two >= 1.000001 x the largest extent (1 for a zero
+ * extent; root (0, 0, 0, 1) for n = 0) -- from x, y, z (n device doubles
+ * each, caller order), and checks m (n device doubles) for finiteness.
+ * root_out: device, 4 doubles (centre x, y, z, side). nonfinite_out: device
+ * int, set to 1 when a coordinate or mass is NaN or infinite (NaN
+ * coordinates are then left out of the box) or when no finite power of two
+ * reaches 1.000001 x the extent (finite coordinates such as +-1e308; the
+ * side is then +inf), else 0. Queued on `stream` (a cudaStream_t; NULL = the
+ * legacy default stream); the call does not synchronise.
  *
  * Scratch: a file-scope static device array of 29,440 bytes, which every GPU
  * that loads the library keeps until the process exits. All calls on a
@@ -423,7 +427,9 @@ int afd_last_force_ms(afd_ctx *ctx, float *ms);
  * (different streams or host threads) race on it: serialise them. The first
  * call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; the lookup is not
- * stream-ordered, so make that first call before any stream capture.
+ * stream-ordered, so make that first call before any stream capture. The
+ * address is kept for the life of the process: do not use this entry point
+ * on a device after cudaDeviceReset in the same process.
  *
  * n must lie in 0 .. 2^31 - 1 (the library's particle index range); a larger
  * n returns AFD_ERR_TOO_LARGE before the device is touched. The call makes no

@@ -184,7 +184,10 @@ void afo_direct_sum(int64_t n, const double *x, const double *y, const double *z
 /* ------------------------------------------------------------------------ */
 
 /* root[0..2] = centre, root[3] = side L (a power of two). Returns 0, or -1
- * when a coordinate is not finite. */
+ * when a coordinate is not finite or when no finite power of two reaches
+ * 1.000001 x the extent (finite coordinates whose extent overflows, or
+ * an extent above 2^1023 / 1.000001): such a set has no root cell in
+ * doubles, and counts as non-finite input. */
 int afo_root_cell(int64_t n, const double *x, const double *y, const double *z,
                   double root[4]) {
   double lo[3] = {0.0, 0.0, 0.0}, hi[3] = {0.0, 0.0, 0.0};
@@ -207,9 +210,12 @@ int afo_root_cell(int64_t n, const double *x, const double *y, const double *z,
     if (e > ext) ext = e;
   }
   const double target = ext * 1.000001;
+  if (!(target <= DBL_MAX)) return -1;
   double L = 1.0;
   if (target > 0.0) {
+    /* at most 1024 doublings: L reaches target, or overflows to inf */
     while (L < target) L *= 2.0;
+    if (isinf(L)) return -1;
     while (L * 0.5 >= target) L *= 0.5;
   }
   root[3] = L;

@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cfloat>
 #include <cstddef>
 #include <cstdint>
 #include <vector>
@@ -38,6 +39,78 @@ enum : int {
   kStBadRadius = 16,
 };
 int status_to_error(int bits);
+
+// Side of the root cell for a scaled largest extent `target` (1.000001 x the
+// extent, Section 4.3 root rule): the smallest power of two >= target; 1 when
+// target is not positive (a zero extent) or NaN; +inf when no finite power of
+// two reaches it (an infinite coordinate, or an extent that overflows). Read
+// off the bits of the double with no loop, so every input ends in a fixed
+// number of steps. The callers flag a side that is not finite as non-finite
+// input.
+__device__ __forceinline__ double root_side(double target) {
+  if (!(target > 0.0)) return 1.0;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(target);
+  const unsigned e = (unsigned)((b >> 52) & 0x7ffu);
+  const unsigned long long f = b & 0xfffffffffffffull;
+  if (e == 0x7ffu) return __longlong_as_double(0x7ff0000000000000ll);  // +inf
+  if (e == 0u) {
+    // subnormal target = f x 2^-1074, 0 < f < 2^52: the power of two 2^k >= f
+    // as a subnormal, or 2^52 x 2^-1074 = the smallest normal, whose bits are
+    // 2^52 as well
+    const unsigned long long p = f <= 1ull ? 1ull : 1ull << (64 - __clzll((long long)(f - 1ull)));
+    return __longlong_as_double((long long)p);
+  }
+  if (f == 0ull) return target;  // already a power of two
+  if (e + 1u == 0x7ffu) return __longlong_as_double(0x7ff0000000000000ll);  // above 2^1023
+  return __longlong_as_double((long long)((unsigned long long)(e + 1u) << 52));
+}
+
+// Order-preserving 64-bit key of a double (for finite values: a < b iff
+// key(a) < key(b), except that -0 sorts below +0): min / max of positions
+// on the integer pipes, exact, instead of on GB300's narrow FP64 pipe.
+__device__ __forceinline__ unsigned long long okey(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return b ^ ((unsigned long long)((long long)b >> 63) | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double okey_value(unsigned long long k) {
+  const unsigned long long b = (k & 0x8000000000000000ull) ? (k ^ 0x8000000000000000ull) : ~k;
+  return __longlong_as_double((long long)b);
+}
+__device__ __forceinline__ unsigned long long warp_min_key(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ unsigned long long warp_max_key(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// The key of a coordinate for the box reduction; NaN is left out (the
+// neutral keys), and is flagged by the finiteness check.
+__device__ __forceinline__ void box_keys(double v, unsigned long long &lo, unsigned long long &hi) {
+  if (v != v) return;
+  const unsigned long long k = okey(v);
+  lo = min(lo, k);
+  hi = max(hi, k);
+}
+
+// Centre and side of a root cell from the box keys (rule of R2, with the
+// side from root_side); returns false when the side is not finite.
+__device__ __forceinline__ bool root_from_keys(const unsigned long long *klo,
+                                               const unsigned long long *khi, double *r) {
+  double ext = 0.0;
+  for (int d = 0; d < 3; d++) {
+    const double lo = okey_value(klo[d]), hi = okey_value(khi[d]);
+    r[d] = __dmul_rn(__dadd_rn(lo, hi), 0.5);
+    const double e = __dsub_rn(hi, lo);
+    if (e > ext) ext = e;
+  }
+  const double L = root_side(__dmul_rn(ext, 1.000001));
+  r[3] = L;
+  return L <= DBL_MAX;
+}
 
 }  // namespace afd
 

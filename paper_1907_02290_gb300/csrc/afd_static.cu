@@ -18,7 +18,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kBlocks = 608;  // grid cap: one partial slot per block
-constexpr size_t kPartBytes = sizeof(double) * 6 * kBlocks;          // 29184
+constexpr size_t kPartBytes = sizeof(unsigned long long) * 6 * kBlocks;  // 29184
 constexpr size_t kCounterOffset = (kPartBytes + 255) / 256 * 256;    // 29184 (256-aligned)
 constexpr size_t kScratchBytes = kCounterOffset + 256;               // 29440
 constexpr int64_t kMaxParticles = ((int64_t)1 << 31) - 1;
@@ -34,28 +34,19 @@ struct DeviceScratch {
 DeviceScratch g_scratch[kMaxDevices];
 std::mutex g_scratch_mu;
 
-__device__ __forceinline__ double warp_min(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-__device__ __forceinline__ double warp_max(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
-// Same reduction and root rule as the context path: centre (min+max)/2 per
-// axis, side = smallest power of two >= 1.000001 * largest extent (1 when
-// the extent is 0, and the root (0, 0, 0, 1) when n = 0).
+// Same reduction and root rule as the context path (the order-preserving
+// integer keys of the doubles, so that -0 and +0 come out as afd_tree_build
+// gives them, and the side from root_side): centre (min+max)/2 per axis,
+// side = smallest power of two >= 1.000001 * largest extent (1 when the
+// extent is 0, and the root (0, 0, 0, 1) when n = 0).
 __global__ void __launch_bounds__(kThreads) k_root_static(
     const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
     const double *__restrict__ m, int64_t n, unsigned char *scratch, double *__restrict__ root,
     int *__restrict__ nonfinite) {
-  double *part = reinterpret_cast<double *>(scratch);
+  unsigned long long *part = reinterpret_cast<unsigned long long *>(scratch);
   unsigned *counter = reinterpret_cast<unsigned *>(scratch + kCounterOffset);
   unsigned *flag = counter + 1;
-  double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+  unsigned long long klo[3] = {~0ull, ~0ull, ~0ull}, khi[3] = {0ull, 0ull, 0ull};
   int bad = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -64,32 +55,31 @@ __global__ void __launch_bounds__(kThreads) k_root_static(
 #pragma unroll
     for (int d = 0; d < 3; d++) {
       bad |= !isfinite(v[d]);
-      lo[d] = fmin(lo[d], v[d]);
-      hi[d] = fmax(hi[d], v[d]);
+      afd::box_keys(v[d], klo[d], khi[d]);
     }
   }
-  __shared__ double sh[kThreads / 32][6];
+  __shared__ unsigned long long sh[kThreads / 32][6];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int d = 0; d < 3; d++) {
-    lo[d] = warp_min(lo[d]);
-    hi[d] = warp_max(hi[d]);
+    klo[d] = afd::warp_min_key(klo[d]);
+    khi[d] = afd::warp_max_key(khi[d]);
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, 1u);
   if (lane == 0)
     for (int d = 0; d < 3; d++) {
-      sh[warp][d] = lo[d];
-      sh[warp][3 + d] = hi[d];
+      sh[warp][d] = klo[d];
+      sh[warp][3 + d] = khi[d];
     }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double b[6];
+    unsigned long long b[6];
     for (int d = 0; d < 6; d++) b[d] = sh[0][d];
     for (int w = 1; w < kThreads / 32; w++)
       for (int d = 0; d < 3; d++) {
-        b[d] = fmin(b[d], sh[w][d]);
-        b[3 + d] = fmax(b[3 + d], sh[w][3 + d]);
+        b[d] = min(b[d], sh[w][d]);
+        b[3 + d] = max(b[3 + d], sh[w][3 + d]);
       }
     for (int d = 0; d < 6; d++) part[blockIdx.x * 6 + d] = b[d];
     __threadfence();
@@ -104,27 +94,15 @@ __global__ void __launch_bounds__(kThreads) k_root_static(
     *nonfinite = 0;
     return;
   }
-  double b[6];
+  unsigned long long b[6];
   for (int d = 0; d < 6; d++) b[d] = __ldcg(&part[d]);
   for (unsigned k = 1; k < gridDim.x; k++)
     for (int d = 0; d < 3; d++) {
-      b[d] = fmin(b[d], __ldcg(&part[k * 6 + d]));
-      b[3 + d] = fmax(b[3 + d], __ldcg(&part[k * 6 + 3 + d]));
+      b[d] = min(b[d], __ldcg(&part[k * 6 + d]));
+      b[3 + d] = max(b[3 + d], __ldcg(&part[k * 6 + 3 + d]));
     }
-  double ext = 0.0;
-  for (int d = 0; d < 3; d++) {
-    root[d] = __dmul_rn(__dadd_rn(b[d], b[3 + d]), 0.5);
-    const double e = __dsub_rn(b[3 + d], b[d]);
-    if (e > ext) ext = e;
-  }
-  const double target = __dmul_rn(ext, 1.000001);
-  double L = 1.0;
-  if (target > 0.0) {
-    while (L < target) L = __dmul_rn(L, 2.0);
-    while (__dmul_rn(L, 0.5) >= target) L = __dmul_rn(L, 0.5);
-  }
-  root[3] = L;
-  *nonfinite = __ldcg(flag) ? 1 : 0;
+  const bool side_ok = afd::root_from_keys(b, b + 3, root);
+  *nonfinite = (__ldcg(flag) || !side_ok) ? 1 : 0;
 }
 
 // Device address of the static array on the current device, looked up once

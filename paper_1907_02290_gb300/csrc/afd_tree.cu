@@ -31,44 +31,11 @@ inline unsigned blocks_for(int64_t n, int threads = kThreads) {
 // ---------------------------------------------------------------------------
 constexpr int kRootBlocks = 608;
 
-// Order-preserving 64-bit key of a double (for finite values: a < b iff
-// key(a) < key(b), except that -0 sorts below +0): min / max of positions
-// on the integer pipes, exact, instead of on GB300's narrow FP64 pipe.
-__device__ __forceinline__ unsigned long long okey(double v) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  return b ^ ((unsigned long long)((long long)b >> 63) | 0x8000000000000000ull);
-}
-__device__ __forceinline__ double okey_value(unsigned long long k) {
-  const unsigned long long b = (k & 0x8000000000000000ull) ? (k ^ 0x8000000000000000ull) : ~k;
-  return __longlong_as_double((long long)b);
-}
-__device__ __forceinline__ unsigned long long warp_min_key(unsigned long long v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-__device__ __forceinline__ unsigned long long warp_max_key(unsigned long long v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
-__device__ __forceinline__ double warp_min(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-__device__ __forceinline__ double warp_max(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
 __global__ void __launch_bounds__(kThreads) k_root(const double *__restrict__ x,
                                                    const double *__restrict__ y,
                                                    const double *__restrict__ z,
                                                    const double *__restrict__ m, int64_t n,
-                                                   double *__restrict__ part,
+                                                   unsigned long long *__restrict__ part,
                                                    unsigned *__restrict__ counter,
                                                    double *__restrict__ root, int *status) {
   unsigned long long klo[3] = {~0ull, ~0ull, ~0ull}, khi[3] = {0ull, 0ull, 0ull};
@@ -81,36 +48,31 @@ __global__ void __launch_bounds__(kThreads) k_root(const double *__restrict__ x,
 #pragma unroll
     for (int d = 0; d < 3; d++) {
       bad |= !isfinite(v[d]);
-      const unsigned long long k = okey(v[d]);
-      klo[d] = min(klo[d], k);
-      khi[d] = max(khi[d], k);
+      box_keys(v[d], klo[d], khi[d]);
     }
   }
-  __shared__ double sh[kThreads / 32][6];
+  __shared__ unsigned long long sh[kThreads / 32][6];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double lo[3], hi[3];
 #pragma unroll
   for (int d = 0; d < 3; d++) {
-    // a thread without particles keeps the neutral keys, which decode to
-    // NaN; the other lanes' values win the reduction (n > 0 here)
-    lo[d] = okey_value(warp_min_key(klo[d]));
-    hi[d] = okey_value(warp_max_key(khi[d]));
+    klo[d] = warp_min_key(klo[d]);
+    khi[d] = warp_max_key(khi[d]);
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, kStNonFinite);
   if (lane == 0)
     for (int d = 0; d < 3; d++) {
-      sh[warp][d] = lo[d];
-      sh[warp][3 + d] = hi[d];
+      sh[warp][d] = klo[d];
+      sh[warp][3 + d] = khi[d];
     }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double b[6];
+    unsigned long long b[6];
     for (int d = 0; d < 6; d++) b[d] = sh[0][d];
     for (int w = 1; w < kThreads / 32; w++)
       for (int d = 0; d < 3; d++) {
-        b[d] = fmin(b[d], sh[w][d]);
-        b[3 + d] = fmax(b[3 + d], sh[w][3 + d]);
+        b[d] = min(b[d], sh[w][d]);
+        b[3 + d] = max(b[3 + d], sh[w][3 + d]);
       }
     for (int d = 0; d < 6; d++) part[blockIdx.x * 6 + d] = b[d];
     __threadfence();
@@ -121,46 +83,34 @@ __global__ void __launch_bounds__(kThreads) k_root(const double *__restrict__ x,
   __threadfence();
   // the last block reduces all partials, every thread a strided share
   for (int d = 0; d < 3; d++) {
-    lo[d] = DBL_MAX;
-    hi[d] = -DBL_MAX;
+    klo[d] = ~0ull;
+    khi[d] = 0ull;
   }
   for (unsigned k = threadIdx.x; k < gridDim.x; k += blockDim.x)
     for (int d = 0; d < 3; d++) {
-      lo[d] = fmin(lo[d], __ldcg(&part[k * 6 + d]));
-      hi[d] = fmax(hi[d], __ldcg(&part[k * 6 + 3 + d]));
+      klo[d] = min(klo[d], __ldcg(&part[k * 6 + d]));
+      khi[d] = max(khi[d], __ldcg(&part[k * 6 + 3 + d]));
     }
   for (int d = 0; d < 3; d++) {
-    lo[d] = warp_min(lo[d]);
-    hi[d] = warp_max(hi[d]);
+    klo[d] = warp_min_key(klo[d]);
+    khi[d] = warp_max_key(khi[d]);
   }
   __syncthreads();
   if (lane == 0)
     for (int d = 0; d < 3; d++) {
-      sh[warp][d] = lo[d];
-      sh[warp][3 + d] = hi[d];
+      sh[warp][d] = klo[d];
+      sh[warp][3 + d] = khi[d];
     }
   __syncthreads();
   if (threadIdx.x != 0) return;
-  double b[6];
+  unsigned long long b[6];
   for (int d = 0; d < 6; d++) b[d] = sh[0][d];
   for (int w = 1; w < kThreads / 32; w++)
     for (int d = 0; d < 3; d++) {
-      b[d] = fmin(b[d], sh[w][d]);
-      b[3 + d] = fmax(b[3 + d], sh[w][3 + d]);
+      b[d] = min(b[d], sh[w][d]);
+      b[3 + d] = max(b[3 + d], sh[w][3 + d]);
     }
-  double ext = 0.0;
-  for (int d = 0; d < 3; d++) {
-    root[d] = __dmul_rn(__dadd_rn(b[d], b[3 + d]), 0.5);
-    const double e = __dsub_rn(b[3 + d], b[d]);
-    if (e > ext) ext = e;
-  }
-  const double target = __dmul_rn(ext, 1.000001);
-  double L = 1.0;
-  if (target > 0.0) {
-    while (L < target) L = __dmul_rn(L, 2.0);
-    while (__dmul_rn(L, 0.5) >= target) L = __dmul_rn(L, 0.5);
-  }
-  root[3] = L;
+  if (!root_from_keys(b, b + 3, root)) atomicOr(status, kStNonFinite);
   *counter = 0u;  // ready for the next launch
 }
 
@@ -174,10 +124,10 @@ __global__ void __launch_bounds__(kThreads) k_root_tiles(const double *__restric
                                                          const double *__restrict__ z,
                                                          const double *__restrict__ m,
                                                          const int4 *__restrict__ tiles,
-                                                         double *__restrict__ part,
+                                                         unsigned long long *__restrict__ part,
                                                          int *status) {
   const int4 t = tiles[blockIdx.x];
-  double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+  unsigned long long klo[3] = {~0ull, ~0ull, ~0ull}, khi[3] = {0ull, 0ull, 0ull};
   int bad = 0;
   for (int64_t i = (int64_t)t.y + threadIdx.x; i < (int64_t)t.z; i += blockDim.x) {
     const double v[3] = {x[i], y[i], z[i]};
@@ -185,56 +135,55 @@ __global__ void __launch_bounds__(kThreads) k_root_tiles(const double *__restric
 #pragma unroll
     for (int d = 0; d < 3; d++) {
       bad |= !isfinite(v[d]);
-      lo[d] = fmin(lo[d], v[d]);
-      hi[d] = fmax(hi[d], v[d]);
+      box_keys(v[d], klo[d], khi[d]);
     }
   }
-  __shared__ double sh[kThreads / 32][6];
+  __shared__ unsigned long long sh[kThreads / 32][6];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int d = 0; d < 3; d++) {
-    lo[d] = warp_min(lo[d]);
-    hi[d] = warp_max(hi[d]);
+    klo[d] = warp_min_key(klo[d]);
+    khi[d] = warp_max_key(khi[d]);
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, kStNonFinite);
   if (lane == 0)
     for (int d = 0; d < 3; d++) {
-      sh[warp][d] = lo[d];
-      sh[warp][3 + d] = hi[d];
+      sh[warp][d] = klo[d];
+      sh[warp][3 + d] = khi[d];
     }
   __syncthreads();
   if (threadIdx.x != 0) return;
-  double b[6];
+  unsigned long long b[6];
   for (int d = 0; d < 6; d++) b[d] = sh[0][d];
   for (int w = 1; w < kThreads / 32; w++)
     for (int d = 0; d < 3; d++) {
-      b[d] = fmin(b[d], sh[w][d]);
-      b[3 + d] = fmax(b[3 + d], sh[w][3 + d]);
+      b[d] = min(b[d], sh[w][d]);
+      b[3 + d] = max(b[3 + d], sh[w][3 + d]);
     }
   for (int d = 0; d < 6; d++) part[(size_t)blockIdx.x * 6 + d] = b[d];
 }
 
-__global__ void __launch_bounds__(kThreads) k_root_final(const double *__restrict__ part,
+__global__ void __launch_bounds__(kThreads) k_root_final(const unsigned long long *__restrict__ part,
                                                          const int *__restrict__ tile_first,
-                                                         double *__restrict__ root) {
+                                                         double *__restrict__ root, int *status) {
   const int sys = blockIdx.x;
   const int t0 = tile_first[sys], t1 = tile_first[sys + 1];
-  double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+  unsigned long long klo[3] = {~0ull, ~0ull, ~0ull}, khi[3] = {0ull, 0ull, 0ull};
   for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x)
     for (int d = 0; d < 3; d++) {
-      lo[d] = fmin(lo[d], part[(size_t)t * 6 + d]);
-      hi[d] = fmax(hi[d], part[(size_t)t * 6 + 3 + d]);
+      klo[d] = min(klo[d], part[(size_t)t * 6 + d]);
+      khi[d] = max(khi[d], part[(size_t)t * 6 + 3 + d]);
     }
-  __shared__ double sh[kThreads / 32][6];
+  __shared__ unsigned long long sh[kThreads / 32][6];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int d = 0; d < 3; d++) {
-    lo[d] = warp_min(lo[d]);
-    hi[d] = warp_max(hi[d]);
+    klo[d] = warp_min_key(klo[d]);
+    khi[d] = warp_max_key(khi[d]);
   }
   if (lane == 0)
     for (int d = 0; d < 3; d++) {
-      sh[warp][d] = lo[d];
-      sh[warp][3 + d] = hi[d];
+      sh[warp][d] = klo[d];
+      sh[warp][3 + d] = khi[d];
     }
   __syncthreads();
   if (threadIdx.x != 0) return;
@@ -244,26 +193,14 @@ __global__ void __launch_bounds__(kThreads) k_root_final(const double *__restric
     r[3] = 1.0;
     return;
   }
-  double b[6];
+  unsigned long long b[6];
   for (int d = 0; d < 6; d++) b[d] = sh[0][d];
   for (int w = 1; w < kThreads / 32; w++)
     for (int d = 0; d < 3; d++) {
-      b[d] = fmin(b[d], sh[w][d]);
-      b[3 + d] = fmax(b[3 + d], sh[w][3 + d]);
+      b[d] = min(b[d], sh[w][d]);
+      b[3 + d] = max(b[3 + d], sh[w][3 + d]);
     }
-  double ext = 0.0;
-  for (int d = 0; d < 3; d++) {
-    r[d] = __dmul_rn(__dadd_rn(b[d], b[3 + d]), 0.5);
-    const double e = __dsub_rn(b[3 + d], b[d]);
-    if (e > ext) ext = e;
-  }
-  const double target = __dmul_rn(ext, 1.000001);
-  double L = 1.0;
-  if (target > 0.0) {
-    while (L < target) L = __dmul_rn(L, 2.0);
-    while (__dmul_rn(L, 0.5) >= target) L = __dmul_rn(L, 0.5);
-  }
-  r[3] = L;
+  if (!root_from_keys(b, b + 3, r)) atomicOr(status, kStNonFinite);
 }
 
 // System of each particle (caller order) from the system offsets.
@@ -1023,12 +960,13 @@ int launch_root(afd_ctx *c, const double *x, const double *y, const double *z, c
       return AFD_ERR_CUDA;
     if (!tiles.empty()) {
       k_root_tiles<<<(unsigned)tiles.size(), kThreads, 0, c->stream>>>(
-          x, y, z, m, reinterpret_cast<const int4 *>(tp), ptr<double>(c->red_part),
+          x, y, z, m, reinterpret_cast<const int4 *>(tp), ptr<unsigned long long>(c->red_part),
           ptr<int>(c->status));
       c->launches++;
     }
     k_root_final<<<(unsigned)c->n_sys, kThreads, 0, c->stream>>>(
-        ptr<double>(c->red_part), reinterpret_cast<const int *>(tp + tb), ptr<double>(c->root));
+        ptr<unsigned long long>(c->red_part), reinterpret_cast<const int *>(tp + tb),
+        ptr<double>(c->root), ptr<int>(c->status));
     c->launches++;
     if (n > 0) {
       k_sys_of<<<blocks_for(n), kThreads, 0, c->stream>>>(ptr<int64_t>(c->sys_off_d), c->n_sys, n,
@@ -1045,7 +983,8 @@ int launch_root(afd_ctx *c, const double *x, const double *y, const double *z, c
   }
   int64_t nb = (n + kThreads * 4 - 1) / (kThreads * 4);
   if (nb > kRootBlocks) nb = kRootBlocks;
-  k_root<<<(unsigned)nb, kThreads, 0, c->stream>>>(x, y, z, m, n, ptr<double>(c->red_part),
+  k_root<<<(unsigned)nb, kThreads, 0, c->stream>>>(x, y, z, m, n,
+                                                  ptr<unsigned long long>(c->red_part),
                                                   ptr<unsigned>(c->red_count),
                                                   ptr<double>(c->root), ptr<int>(c->status));
   c->launches++;

@@ -41,6 +41,24 @@ def test_root_cell_hand_cases(orc):
         orc.root_cell([0.0, np.nan], [0.0, 0.0], [0.0, 0.0])
 
 
+def test_root_cell_rejects_sets_no_double_cube_holds(orc):
+    """An infinite coordinate, or finite coordinates whose extent overflows a
+    double or needs a side above 2^1023, have no root cell in doubles: the
+    oracle reports them as non-finite input (and ends)."""
+    for xs in ([0.0, np.inf], [-np.inf, 0.0], [-1e308, 1e308], [0.0, 2.0 ** 1023],
+               [0.0, 1.7976931348623157e308]):
+        with pytest.raises(ValueError):
+            orc.root_cell(xs, [0.0, 0.0], [0.0, 0.0])
+    # the largest side that still exists: an extent of 2^1022 needs 2^1023
+    r = orc.root_cell([0.0, 2.0 ** 1022], [0.0, 0.0], [0.0, 0.0])
+    assert r[3] == 2.0 ** 1023
+    # subnormal extents reach the smallest powers of two exactly
+    r = orc.root_cell([0.0, 5e-324], [0.0, 0.0], [0.0, 0.0])
+    assert r[3] == 5e-324  # 1.000001 x 2^-1074 rounds back to 2^-1074
+    r = orc.root_cell([0.0, 3 * 5e-324], [0.0, 0.0], [0.0, 0.0])
+    assert r[3] == 4 * 5e-324
+
+
 def test_root_cell_contains_and_is_minimal(orc):
     p = ics.plummer(5000, 11)
     c = orc.root_cell(p.x, p.y, p.z)

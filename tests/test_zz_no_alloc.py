@@ -82,3 +82,60 @@ def test_static_root_rejects_sizes_above_the_limit(env):
                                 ctypes.c_void_p(flag.data_ptr()), None)
     assert rc == -11
     assert "limit" in afd.afd_error_string(rc)
+
+
+def test_static_root_matches_context_path_bit_for_bit_on_signed_zeros(env):
+    """Coordinates of -0.0 and +0.0 (and a box whose lower and upper bounds are
+    zeros of opposite sign): both paths reduce the box on the same
+    order-preserving integer keys of the doubles, so the centre's sign of zero
+    agrees bit for bit, not only as equal values."""
+    torch, afd = env
+    stream = torch.cuda.current_stream()
+    gen = np.random.default_rng(64)
+    n = 40000
+    for case in range(3):
+        pos = gen.normal(size=(n, 3))
+        if case == 0:  # every coordinate a zero of either sign on the x axis
+            pos[:, 0] = np.where(gen.random(n) < 0.5, -0.0, 0.0)
+        elif case == 1:  # only -0.0 on y, only +0.0 on z
+            pos[:, 1] = -0.0
+            pos[:, 2] = 0.0
+        else:  # zeros of both signs sprinkled through, the rest symmetric
+            sel = gen.random((n, 3)) < 0.2
+            pos[sel] = np.where(gen.random(sel.sum()) < 0.5, -0.0, 0.0)
+        m = np.full(n, 1.0 / n)
+        x, y, z, md = _dev(torch, (pos[:, 0], pos[:, 1], pos[:, 2], m))
+        root = torch.full((4,), float("nan"), dtype=torch.float64, device="cuda:0")
+        flag = torch.full((1,), -1, dtype=torch.int32, device="cuda:0")
+        afd.afd_root_cell_static(x, y, z, md, root, flag, stream)
+        torch.cuda.synchronize()
+        ref = _context_root(afd, torch, x, y, z, md)
+        got = root.cpu().numpy()
+        assert np.array_equal(got.view(np.uint64), np.asarray(ref, np.float64).view(np.uint64)), case
+        assert int(flag.item()) == 0
+
+
+def test_static_root_flags_sets_without_a_root_cell(env):
+    """An infinite coordinate, or finite coordinates whose extent has no
+    power-of-two side in doubles, set the flag (the side is read off the bits
+    of the extent, so the call ends); the next call on a good set is clean."""
+    torch, afd = env
+    stream = torch.cuda.current_stream()
+    p = ics.plummer(7000, 65)
+    root = torch.zeros(4, dtype=torch.float64, device="cuda:0")
+    flag = torch.zeros(1, dtype=torch.int32, device="cuda:0")
+    for v0, v1 in ((float("inf"), None), (float("-inf"), None), (-1e308, 1e308),
+                   (0.0, 2.0 ** 1023)):
+        x, y, z, m = _dev(torch, (p.x, p.y, p.z, p.m))
+        z[11] = v0
+        if v1 is not None:
+            z[4000] = v1
+        flag.fill_(-1)
+        afd.afd_root_cell_static(x, y, z, m, root, flag, stream)
+        torch.cuda.synchronize()
+        assert int(flag.item()) == 1, (v0, v1)
+    x, y, z, m = _dev(torch, (p.x, p.y, p.z, p.m))
+    afd.afd_root_cell_static(x, y, z, m, root, flag, stream)
+    torch.cuda.synchronize()
+    assert int(flag.item()) == 0
+    assert np.array_equal(root.cpu().numpy(), _context_root(afd, torch, x, y, z, m))
