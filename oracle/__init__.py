@@ -100,6 +100,8 @@ def lib():
                                      ctypes.c_int64, _I64]
         L.afo_band_pairs.restype = ctypes.c_int64
         L.afo_relist.argtypes = [ctypes.c_void_p]
+        L.afo_relist_band.argtypes = [ctypes.c_void_p, _I64, _I32, _I64]
+        L.afo_mlp_forward_bound_batch.argtypes = [_F32, ctypes.c_int64, _F32, _F32, _D]
         L.afo_let_export.argtypes = [ctypes.c_void_p, _D, ctypes.c_double, ctypes.c_int64, _D, _D,
                                      _D, _D, _I32]
         L.afo_let_export.restype = ctypes.c_int64
@@ -285,6 +287,23 @@ class Tree:
         lib().afo_get_lists(self._h, _p(eo, _I64), _p(e, _I32), _p(so, _I64), _p(sp, _I32))
         return eo, e, so, sp
 
+    def relist_band(self, spj_off, spj):
+        """Make the learned-criterion lists again, taking another
+        implementation's decisions (its SPJ lists: CSR offsets per group and
+        cell ids in this tree's numbering) for the pairs whose network output
+        lies within the rounding bound of R13 from tau -- the only pairs two
+        correct FP32 implementations may decide differently. Returns
+        (band pairs visited, those decided otherwise than by this oracle);
+        ``lists()`` then equals the other implementation's lists iff it agrees
+        on every other pair."""
+        off = np.ascontiguousarray(spj_off, dtype=np.int64)
+        idx = np.ascontiguousarray(spj, dtype=np.int32)
+        assert off.shape[0] == self.sizes()["n_groups"] + 1 and idx.shape[0] == off[-1]
+        cnt = np.zeros(2, np.int64)
+        lib().afo_relist_band(self._h, _p(off, _I64), _p(idx if idx.size else np.zeros(1, np.int32),
+                                                         _I32), _p(cnt, _I64))
+        return int(cnt[0]), int(cnt[1])
+
     def update(self, x, y, z, m):
         """Reusing step (Section 4.2): new particle data, same topology/lists."""
         x, y, z, m = map(_f64, (x, y, z, m))
@@ -447,12 +466,26 @@ def fp16_round(params):
 
 
 def mlp_forward(params, feats):
-    """R13 network in FP32 (fused multiply-adds, fixed order) per feature row."""
+    """R13 network in FP32 (bias, then fused multiply-adds in input order, for
+    every unit) per feature row."""
     p = np.ascontiguousarray(params, dtype=np.float32)
     f = np.ascontiguousarray(feats, dtype=np.float32).reshape(-1, MAC_NF)
     out = np.zeros(f.shape[0], dtype=np.float32)
     lib().afo_mlp_forward_batch(_p(p, _F32), f.shape[0], _p(f, _F32), _p(out, _F32))
     return out
+
+
+def mlp_forward_bound(params, feats):
+    """R13 network per feature row and, per row, the rounding bound
+    2 gamma_32 (|b3| + sum_j |w3_j h2_j|) within which any other FP32
+    summation order of the output unit's terms lands."""
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    f = np.ascontiguousarray(feats, dtype=np.float32).reshape(-1, MAC_NF)
+    out = np.zeros(f.shape[0], dtype=np.float32)
+    bound = np.zeros(f.shape[0], dtype=np.float64)
+    lib().afo_mlp_forward_bound_batch(_p(p, _F32), f.shape[0], _p(f, _F32), _p(out, _F32),
+                                      _p(bound, _D))
+    return out, bound
 
 
 def mlp_unpack(params):

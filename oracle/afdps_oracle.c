@@ -76,10 +76,14 @@
  *     with fused multiply-adds); 0 or subnormal arguments give -127.
  *  R13 network: 8-32-32-1 perceptron with ReLU on both hidden layers; input
  *     k is normalised as (f_k - mu_k) * isd_k; every parameter (mu and isd
- *     included) is an FP16 value; each hidden unit is its bias followed by
- *     fused multiply-adds over its inputs in index order, in FP32; the
- *     output unit forms the 32 products w3_j h2_j, sums them pairwise by
- *     halving (p_j += p_{j+16} for j < 16, then 8, 4, 2, 1) and adds b3.
+ *     included) is an FP16 value; every unit, the output unit included, is
+ *     its bias followed by fused multiply-adds over its inputs in index
+ *     order, in FP32. Another implementation may sum the output unit's 32
+ *     terms in another order: two FP32 sums of the same terms differ by at
+ *     most 2 gamma_32 (|b3| + sum_j |w3_j h2_j|), gamma_k = k u / (1 - k u),
+ *     u = 2^-24 (the standard bound for recursive or pairwise summation), so
+ *     a decision of R14 is fixed by the definition only when the output lies
+ *     further than that from tau; afo_mlp_forward_bound returns the bound.
  *  R14 learned decision for cell c and group g: open if c contains the
  *     group's first particle; accept if s^2 < theta_lo^2 d^2; open if not
  *     s^2 < theta_hi^2 d^2; otherwise accept iff the network's output is
@@ -324,6 +328,14 @@ typedef struct afo_tree {
   float mac_lo2, mac_hi2, mac_tau;
   float *amag_s; /* reference |a| per particle, Morton order */
   float *g_amin; /* smallest of them per group */
+  /* comparison with another implementation of R14 (afo_relist_band): for a
+   * pair whose output lies within the rounding bound of R13 from tau, the
+   * decision is read from that implementation's SPJ lists (accepted iff the
+   * cell is on the group's list); per group, such pairs and those among
+   * them decided otherwise than here */
+  const int64_t *ovr_off;
+  const int32_t *ovr_spj;
+  int64_t *band_cnt, *flip_cnt;
   /* neighbour lists (R17): per-cell tight boxes and per-group search boxes
    * (FP32, min x y z then max x y z), CSR lists of Morton positions */
   float *c_tbox, *g_sbox;
@@ -699,8 +711,11 @@ void afo_mac_features(const float bmin[3], const float bmax[3], const float com[
   for (int k = 0; k < AFO_MAC_NF; k++) f[k] = clamp32(f[k]);
 }
 
-/* Network of R13 on one feature vector; p holds FP16-representable values. */
-float afo_mlp_forward(const float *p, const float f[AFO_MAC_NF]) {
+/* Network of R13 on one feature vector; p holds FP16-representable values.
+ * *bound (may be NULL) receives 2 gamma_32 (|b3| + sum_j |w3_j h2_j|): the
+ * largest difference between this output and the same terms summed in any
+ * other FP32 order. */
+float afo_mlp_forward_bound(const float *p, const float f[AFO_MAC_NF], double *bound) {
   const float *mu = p, *isd = p + AFO_MAC_NF;
   const float *W1 = p + 2 * AFO_MAC_NF, *b1 = W1 + AFO_MAC_NH * AFO_MAC_NF;
   const float *W2 = b1 + AFO_MAC_NH, *b2 = W2 + AFO_MAC_NH * AFO_MAC_NH;
@@ -717,15 +732,29 @@ float afo_mlp_forward(const float *p, const float f[AFO_MAC_NF]) {
     for (int k = 0; k < AFO_MAC_NH; k++) acc = fmaf(W2[j * AFO_MAC_NH + k], h1[k], acc);
     h2[j] = acc > 0.0f ? acc : 0.0f;
   }
-  float prod[AFO_MAC_NH];
-  for (int k = 0; k < AFO_MAC_NH; k++) prod[k] = w3[k] * h2[k];
-  for (int half = AFO_MAC_NH / 2; half > 0; half /= 2)
-    for (int k = 0; k < half; k++) prod[k] = prod[k] + prod[k + half];
-  return prod[0] + b3[0];
+  float y = b3[0];
+  for (int k = 0; k < AFO_MAC_NH; k++) y = fmaf(w3[k], h2[k], y);
+  if (bound) {
+    double a = fabs((double)b3[0]);
+    for (int k = 0; k < AFO_MAC_NH; k++) a += fabs((double)w3[k] * (double)h2[k]);
+    const double u = ldexp(1.0, -24), g32 = 32.0 * u / (1.0 - 32.0 * u);
+    *bound = 2.0 * g32 * a;
+  }
+  return y;
+}
+
+float afo_mlp_forward(const float *p, const float f[AFO_MAC_NF]) {
+  return afo_mlp_forward_bound(p, f, NULL);
 }
 
 void afo_mlp_forward_batch(const float *p, int64_t n, const float *feat, float *out) {
   for (int64_t i = 0; i < n; i++) out[i] = afo_mlp_forward(p, feat + i * AFO_MAC_NF);
+}
+
+void afo_mlp_forward_bound_batch(const float *p, int64_t n, const float *feat, float *out,
+                                 double *bound) {
+  for (int64_t i = 0; i < n; i++)
+    out[i] = afo_mlp_forward_bound(p, feat + i * AFO_MAC_NF, &bound[i]);
 }
 
 /* Training target of R15 for n_i group particles (xi, yi, zi, reference
@@ -834,7 +863,16 @@ static int learned_accept(const afo_tree *t, int64_t g, int64_t c, const float b
   if (!(s2 < hi)) return 0;
   float f[AFO_MAC_NF];
   afo_pair_features(t, g, c, f);
-  return afo_mlp_forward(t->mac_w, f) < t->mac_tau;
+  double bound;
+  const float y = afo_mlp_forward_bound(t->mac_w, f, &bound);
+  const int own = y < t->mac_tau;
+  if (!t->ovr_off || !(fabs((double)y - (double)t->mac_tau) <= bound)) return own;
+  int other = 0;
+  for (int64_t k = t->ovr_off[g]; k < t->ovr_off[g + 1]; k++)
+    if (t->ovr_spj[k] == (int32_t)c) other = 1;
+  t->band_cnt[g]++;
+  if (other != own) t->flip_cnt[g]++;
+  return other;
 }
 
 /* Training target of R15 for the pair (g, c). */
@@ -964,6 +1002,7 @@ static void walk_group(const afo_tree *t, int64_t g, int32_t *epj, int32_t *spj,
   const float L = (float)t->root[3];
   int64_t ne = 0, ns = 0;
   int32_t self = 0;
+  if (t->band_cnt) t->band_cnt[g] = t->flip_cnt[g] = 0;
   int64_t stack[8 * (AFO_LEVELS + 2)];
   int sp = 0;
   if (t->n_cells > 0) stack[sp++] = 0;
@@ -1109,6 +1148,34 @@ int afo_update(afo_tree *t, const double *x, const double *y, const double *z,
 void afo_relist(afo_tree *t) {
   free(t->epj_off); free(t->spj_off); free(t->epj); free(t->spj);
   make_lists(t);
+}
+
+/* Lists made again (as afo_relist) with the learned criterion, taking the
+ * decisions of another implementation -- given as its SPJ lists, CSR with
+ * spj_off[n_groups + 1], cell ids in this tree's numbering -- for the pairs
+ * whose network output lies within the rounding bound of R13 from tau, the
+ * pairs where two correct FP32 implementations may decide differently.
+ * counts[0] receives the number of such pairs visited, counts[1] those the
+ * other implementation decided otherwise than this oracle. The lists then
+ * equal the other implementation's exactly iff it agrees on every other
+ * pair. */
+void afo_relist_band(afo_tree *t, const int64_t *spj_off, const int32_t *spj,
+                     int64_t counts[2]) {
+  t->ovr_off = spj_off;
+  t->ovr_spj = spj;
+  t->band_cnt = xcalloc(t->n_groups, sizeof(int64_t));
+  t->flip_cnt = xcalloc(t->n_groups, sizeof(int64_t));
+  afo_relist(t);
+  counts[0] = counts[1] = 0;
+  for (int64_t g = 0; g < t->n_groups; g++) {
+    counts[0] += t->band_cnt[g];
+    counts[1] += t->flip_cnt[g];
+  }
+  free(t->band_cnt);
+  free(t->flip_cnt);
+  t->band_cnt = t->flip_cnt = NULL;
+  t->ovr_off = NULL;
+  t->ovr_spj = NULL;
 }
 
 /* Force on the saved lists (Section 5: interaction of the EPJs and SPJs of a

@@ -16,9 +16,13 @@
 //
 //  network: 8-32-32-1, ReLU, inputs normalised as (f - mu) * isd, every
 //  parameter an FP16 value held as FP32, each hidden unit its bias followed
-//  by fused multiply-adds in input order; the output sums the 32 products
-//  w3_j h2_j pairwise by halving (j += j + 16, then 8, 4, 2, 1 -- the order
-//  of a warp's xor butterfly) and adds b3.
+//  by fused multiply-adds in input order. The output unit is b3 plus the 32
+//  terms w3_j h2_j; this code sums the rounded products pairwise by halving
+//  (j += j + 16, then 8, 4, 2, 1: a warp's xor butterfly, five shuffles
+//  instead of a 32-step chain) and then adds b3. Any FP32 order of those
+//  terms lies within 2 gamma_32 (|b3| + sum |w3_j h2_j|) of any other
+//  (gamma_k = k 2^-24 / (1 - k 2^-24)), so a decision is fixed by the
+//  network only when its output is further than that from tau.
 //
 //  decision: open a cell holding the group's first particle; accept when
 //  s^2 < theta_lo^2 d^2; open unless s^2 < theta_hi^2 d^2; otherwise accept

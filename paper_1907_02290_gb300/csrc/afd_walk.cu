@@ -39,10 +39,10 @@
 // at a time: lane j computes hidden unit j of both layers (its weights read
 // from shared memory, the cells' inputs and hidden values broadcast from
 // shared memory, one packed FMA covering two cells), and the 32 output
-// products are summed by an xor butterfly, which adds them in exactly the
-// defined pairwise-halving order. The arithmetic per unit is mac_mlp_t's, so
-// the decisions are the same bit for bit; the warp needs few registers and
-// no lane sits idle in the layers.
+// products are summed by an xor butterfly in the pairwise-halving order of
+// mac_mlp_t. The arithmetic per unit is mac_mlp_t's, so the walk and the
+// inference entry point give the same outputs bit for bit; the warp needs
+// few registers and no lane sits idle in the layers.
 #include "afd_internal.cuh"
 #include "afd_mac.cuh"
 

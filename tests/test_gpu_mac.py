@@ -2,15 +2,19 @@
 falls back to the paper's theta criterion, Section 2) against the oracle's
 readings R12-R15, through the C ABI.
 
-Bit-exact: quadrupole moments (the criterion reads them), the network's
-output with FP16 weights, the features of every sampled pair, the set of
-pairs the band leaves to the network, and the interaction lists the
-learned walk makes (both sides decide in FP32 with the same operations).
-Within tolerance: the targets (GPU FP32 compensated sums vs oracle FP64) and
-the network gradients of the GPU backward pass (vs the oracle's FP64 chain
-rule, itself pinned by finite differences). Finally the trained network is
-judged by brute force: its force error against the direct sum, compared
-with the theta criterion at equal error.
+Bit-exact: quadrupole moments (the criterion reads them), the features of
+every sampled pair and the set of pairs the band leaves to the network.
+The network's output: the oracle sums the output unit's terms in index
+order (R13), the kernel by a warp butterfly; the two must lie within the
+FP32 rounding bound of R13 of each other. The interaction lists of the
+learned walk: equal to the oracle's, except that for pairs whose oracle
+output lies within that bound of tau (where two correct FP32 orders may
+decide differently) the oracle takes the kernel's decision; those pairs are
+counted and reported. Within tolerance: the targets (GPU FP32 compensated
+sums vs oracle FP64) and the network gradients of the GPU backward pass (vs
+the oracle's FP64 chain rule, itself pinned by finite differences). Finally
+the trained network is judged by brute force: its force error against the
+direct sum, compared with the theta criterion at equal error.
 """
 import numpy as np
 import pytest
@@ -59,7 +63,10 @@ def gpu_ctx(env, p, amag, *, n_grp=64, theta=0.5, quad=False):
 # ---------------------------------------------------------------- network
 
 
-def test_forward_bit_exact_with_fp16_weights(env):
+def test_forward_within_the_summation_bound_with_fp16_weights(env):
+    """Same FP16-rounded parameters, same hidden-layer arithmetic; the output
+    unit's 32 terms summed in another order: every output within the FP32
+    bound of R13 of the oracle's, and most of them equal."""
     torch, afd, orc = env
     p = rand_params(orc, 3)
     f = np.random.default_rng(4).normal(0.0, 4.0, (20000, 8)).astype(np.float32)
@@ -67,8 +74,14 @@ def test_forward_bit_exact_with_fp16_weights(env):
     f[100:200] = -32.0
     out = torch.empty(f.shape[0], dtype=torch.float32, device="cuda:0")
     afd.afd_mlp_forward(p, dev(torch, f, torch.float32), out)
-    ref = orc.mlp_forward(orc.fp16_round(p), f)
-    assert np.array_equal(out.cpu().numpy(), ref)
+    ref, bound = orc.mlp_forward_bound(orc.fp16_round(p), f)
+    got = out.cpu().numpy()
+    diff = np.abs(got.astype(np.float64) - ref.astype(np.float64))
+    assert np.all(diff <= bound), float(np.max(diff / bound))
+    equal = float(np.mean(got == ref))
+    print(f"network output: {equal:.3f} of rows equal, largest difference "
+          f"{float(np.max(diff / bound)):.3f} of the bound")
+    assert equal > 0.3
 
 
 def test_gradient_matches_oracle_backward(env):
@@ -193,6 +206,10 @@ def test_learned_lists_bit_exact_and_forces(env, plummer, case):
         assert info["accepted"] == 0
     mac = dict(params=orc.fp16_round(params), theta_lo=lo, theta_hi=hi, tau=tau)
     t = orc.Tree(p.x, p.y, p.z, p.m, n_grp=64, eps=EPS, quad=quad, mac=mac, amag=amag)
+    band, flips = t.relist_band(g.export("spj_off"), g.export("spj_idx"))
+    print(f"learned walk ({case}): {info['evaluations']} network evaluations, "
+          f"{band} within the rounding bound of tau, {flips} decided otherwise than the oracle")
+    assert flips <= band and band <= max(10, info["evaluations"] // 1000)
     check_structure(g, t, quad=quad)
     ref = t.force()
     assert rms_rel_acc(acc.cpu().numpy().astype(np.float64), ref) <= 1e-6

@@ -345,6 +345,43 @@ def test_errors_are_reported(env):
     g.close()
 
 
+def test_sets_without_a_root_cell_are_nonfinite(env):
+    """An infinite coordinate, or finite coordinates whose extent has no
+    power-of-two side in doubles (+-1e308, or an extent just above 2^1023),
+    end the tree build with AFD_ERR_NONFINITE -- the root side is read off the
+    bits of the extent, with no loop -- for one system and for a forest, and
+    the context stays usable."""
+    torch, afd, _ = env
+    dev = torch.device("cuda:0")
+    n = 3000
+    x = torch.rand(n, dtype=torch.float64, device=dev)
+    m = torch.full((n,), 1.0 / n, dtype=torch.float64, device=dev)
+    acc = torch.zeros(n, 4, dtype=torch.float32, device=dev)
+    cases = []
+    for v0, v1 in ((float("inf"), None), (float("-inf"), None), (-1e308, 1e308),
+                   (0.0, 2.0 ** 1023), (0.0, 1.7976931348623157e308)):
+        b = x.clone()
+        b[5] = v0
+        if v1 is not None:
+            b[2000] = v1
+        cases.append(b)
+    for forest in (False, True):
+        g = afd.Gravity(afd.Config(eps=0.01, theta=0.5, n_grp=32), 0, torch.cuda.current_stream())
+        if forest:
+            afd.afd_set_systems(g.ctx, [0, 1000, n])
+        for b in cases:
+            for axis in range(3):
+                xyz = [x, x, x]
+                xyz[axis] = b
+                with pytest.raises(afd.AfdError) as e:
+                    afd.afd_calc_force_all(g.ctx, *xyz, m, acc, afd.AFD_MAKE_LIST)
+                assert e.value.status == -3
+        afd.afd_calc_force_all(g.ctx, x, x, x, m, acc, afd.AFD_MAKE_LIST)  # still usable
+        torch.cuda.synchronize()
+        assert torch.isfinite(acc).all()
+        g.close()
+
+
 def test_full_size_plummer_1m(env):
     """The 2^20-particle Plummer workload in the bench's launch configuration:
     keys, topology, groups and lists bit-exact; forces of sampled groups."""
@@ -415,6 +452,7 @@ def test_batched_systems_match_per_system_oracle(env, learned):
     gf, gc = g.export("group_first"), g.export("group_count")
     eo, e, so, s = (g.export(k) for k in ("epj_off", "epj_idx", "spj_off", "spj_idx"))
     cbase = gbase = 0
+    gspj = {}
     for k, n in enumerate(sizes):
         sl = slice(off[k], off[k + 1])
         q = parts[k]
@@ -437,6 +475,13 @@ def test_batched_systems_match_per_system_oracle(env, learned):
         gs = slice(gbase, gbase + ng)
         assert np.array_equal(gf[gs].astype(np.int64), gr["first"] + off[k])
         assert np.array_equal(gc[gs], gr["count"].astype(np.uint32))
+        if learned:
+            # pairs within the rounding bound of tau take the kernel's
+            # decision (two FP32 summation orders of the network's output)
+            gspj[k] = (so[gbase:gbase + ng + 1].astype(np.int64) - int(so[gbase]),
+                       s[so[gbase]:so[gbase + ng]].astype(np.int64) - cbase)
+            band, flips = t.relist_band(*gspj[k])
+            assert flips <= band <= max(10, len(gspj[k][1]) // 100)
         teo, te, tso, ts = t.lists()
         assert np.array_equal(np.diff(eo[gbase:gbase + ng + 1]).astype(np.int64), np.diff(teo))
         assert np.array_equal(np.diff(so[gbase:gbase + ng + 1]).astype(np.int64), np.diff(tso))
@@ -462,6 +507,8 @@ def test_batched_systems_match_per_system_oracle(env, learned):
         sl = slice(off[k], off[k + 1])
         t = orc.Tree(*parts[k], n_grp=n_grp[k], mac=mac, amag=amags[k] if learned else None,
                      **kw)
+        if learned:
+            t.relist_band(*gspj[k])
         t.update(parts[k][0] + 1e-3, parts[k][1], parts[k][2], parts[k][3])
         assert rms_rel_acc(a2[sl], t.force()) <= FORCE_RMS_TOL
     g.close()

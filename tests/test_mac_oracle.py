@@ -117,6 +117,27 @@ def test_mlp_forward_hand_worked(orc):
     assert orc.mlp_forward(p, f)[0] == np.float32(expect)
 
 
+def test_mlp_output_unit_is_the_plain_sequential_sum(orc):
+    """R13: the output unit is b3 followed by fused multiply-adds in index
+    order. With b3 = 1 and 32 terms of 2^-25 each, every step rounds back to
+    1 (a term is below half an ulp of 1), so the definition gives exactly 1;
+    a pairwise order would first add the terms exactly (2^-20) and give
+    1 + 2^-20. The returned bound covers that other order's result."""
+    p = np.zeros(orc.MAC_NP, np.float32)
+    mu, isd, W1, b1, W2, b2, w3, b3 = orc.mlp_unpack(p)
+    b2[:] = 2.0 ** -13  # h2_j = 2^-13 (all inputs and hidden layers zero)
+    w3[:] = 2.0 ** -12  # w3_j h2_j = 2^-25
+    b3[0] = 1.0
+    f = np.zeros((1, 8), np.float32)
+    y, bound = orc.mlp_forward_bound(p, f)
+    assert y[0] == np.float32(1.0)
+    pairwise = 1.0 + 2.0 ** -20  # exact in FP32
+    assert abs(pairwise - float(y[0])) <= bound[0]
+    u = 2.0 ** -24
+    assert bound[0] == pytest.approx(2 * 32 * u / (1 - 32 * u) * (1.0 + 32 * 2.0 ** -25), rel=1e-12)
+    assert orc.mlp_forward(p, f)[0] == y[0]
+
+
 def test_mlp_forward_matches_fp64_network(orc):
     p = _rand_params(orc, 5)
     f = np.random.default_rng(6).normal(0.0, 3.0, (500, 8)).astype(np.float32)
@@ -299,3 +320,50 @@ def test_pair_features_and_labels_gather_the_right_data(orc, plummer_ref):
         cj = slice(c.first[k], c.first[k] + c.count[k])
         ref_l = orc.mac_label(xs[gi], am[gi], xs[cj], ms[cj], M[k], com[k], Q[k], 1.0 / 256, 0)
         assert lk == ref_l
+
+
+def test_band_relist_takes_the_other_decision_only_within_the_bound(orc, plummer_ref):
+    """The comparison the GPU tests make with the learned walk. A constant
+    network b3 = tau puts every band pair exactly on tau (inside the
+    rounding bound): the oracle then follows another implementation's
+    decisions -- here one that accepts every band cell -- and counts every
+    such pair as in the band and as flipped. With b3 = 1, tau = 2 the output
+    lies further than the bound from tau: the other implementation's
+    decisions (opening every band cell) are ignored, so a kernel that
+    decides differently there would show as different lists."""
+    p, amag = plummer_ref
+    kw = dict(n_grp=32, eps=1.0 / 256)
+    lo, hi = 0.3, 0.55
+
+    def const_net(b3):
+        w = np.zeros(orc.MAC_NP, np.float32)
+        w[8:16] = 1.0
+        w[-1] = b3
+        return w
+
+    acc = orc.Tree(p.x, p.y, p.z, p.m, mac=_mac(const_net(0.0), lo, hi, 1.0), amag=amag, **kw)
+    opn = orc.Tree(p.x, p.y, p.z, p.m, mac=_mac(const_net(2.0), lo, hi, 1.0), amag=amag, **kw)
+    a_eo, a_e, a_so, a_s = acc.lists()
+    o_eo, o_e, o_so, o_s = opn.lists()
+    assert len(a_s) != len(o_s)
+    # output on tau: the other (accept-all) decisions are taken, every one a flip
+    t = orc.Tree(p.x, p.y, p.z, p.m, mac=_mac(const_net(1.0), lo, hi, 1.0), amag=amag, **kw)
+    own = t.lists()
+    for a, b in zip(own, opn.lists()):
+        assert np.array_equal(a, b)  # its own decision: 1 < 1 is false, open
+    band, flips = t.relist_band(a_so, a_s)
+    assert band > 0 and flips == band
+    for a, b in zip(t.lists(), acc.lists()):
+        assert np.array_equal(a, b)
+    # every band pair the accept-all walk accepted was visited in the band
+    bp = acc.band_pairs(lo, hi)
+    band_set = set(zip(bp[:, 0].tolist(), bp[:, 1].tolist()))
+    grp = np.repeat(np.arange(len(a_so) - 1), np.diff(a_so))
+    accepted_in_band = sum(1 for g, c in zip(grp.tolist(), a_s.tolist()) if (g, c) in band_set)
+    assert band >= accepted_in_band > 0
+    # output away from tau: the override does not apply
+    t2 = orc.Tree(p.x, p.y, p.z, p.m, mac=_mac(const_net(1.0), lo, hi, 2.0), amag=amag, **kw)
+    band2, flips2 = t2.relist_band(o_so, o_s)
+    assert band2 == 0 and flips2 == 0
+    for a, b in zip(t2.lists(), acc.lists()):
+        assert np.array_equal(a, b)
