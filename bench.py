@@ -23,8 +23,9 @@ n_i * (n_epj + n_spj)) over the timed steps, plus ms per step.
             is reported beside it.
   cpu_baseline  the FP64 CPU oracle on the host cores, bounded sample.
 
-``--impl reference`` times the oracle itself on the same workload (each step
-a bounded sample, extrapolated to the full step) and prints its own line.
+``--impl reference`` times the oracle itself on the same workload (whole
+measured steps; a stated sample of the i-groups only when K + W whole steps
+would take more than about two minutes) and prints its own line.
 Multi-GPU (torchrun): every rank runs an independent replica of the
 workload (the path has no exchange step at one tree per GPU); value is the
 sum of all ranks' interactions over the slowest rank's time.
@@ -121,7 +122,7 @@ def describe(wl):
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -137,12 +138,14 @@ class ClockSampler:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                 "--format=csv,noheader,nounits", "-lms", "20"], stdout=self.f,
                 stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
 
-    def stop(self):
+    def stop(self, window=None):
+        """Summary of the samples taken inside window = (t0, t1) (time.time()
+        seconds; all samples when none falls inside)."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -151,24 +154,35 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.f.close()
-        mhz, mx, reasons = [], [], set()
+        import datetime
+
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                mhz.append(float(parts[1]))
-                mx.append(float(parts[2]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = None
+            try:
+                sm, smx = float(parts[2]), float(parts[3])
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
+            act = {nm for nm, v in zip(names, parts[6:10]) if v.lower() == "active"}
+            rows.append((ts, sm, smx, act))
         os.unlink(self.path)
+        inside = [r for r in rows if window and r[0] is not None
+                  and window[0] <= r[0] <= window[1]]
+        use = inside or rows
+        mhz = [r[1] for r in use]
         return {"sm_mhz": statistics.median(mhz) if mhz else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
-                "samples": len(mhz)}
+                "sm_max_mhz": max(r[2] for r in use) if use else None,
+                "reasons": sorted(set().union(*(r[3] for r in use))) if use else [],
+                "samples": len(use),
+                "samples_in": "timed region" if inside else "sampler run (none inside the "
+                                                             "timed region)"}
 
 
 def particles(wl):
@@ -229,10 +243,46 @@ def aggregate(dist, device, ms, count):
     return float(t.item()), float(c.item())
 
 
-def cpu_baseline(wl, max_groups_frac=0.25):
-    """The FP64 oracle on the host cores: one construction step, one reusing
-    step, and the force of a fraction of the groups; extrapolated to the
-    interactions/s of the full reuse window."""
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), and nproc."""
+    name = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() in ("Model name", "Model"):
+                name = ln.split(":", 1)[1].strip()
+                if not name.isdigit():
+                    break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not name:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith(("model name", "cpu model")):
+                    name = ln.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return name or "unknown", os.cpu_count()
+
+
+def bench_config(wl, world, *, shard=False, groups_shared=False):
+    """The ``config`` object of the bench line; both arms print this one."""
+    return {"workload": describe(wl), "n": int(wl["n"]),
+            "l2": "flushed (256 MB write) between timed steps, outside the timed events",
+            "parallelism": ("systems sharded over ranks" if shard else
+                            "group slices over ranks, forces all-reduced" if groups_shared
+                            else "replicas") if world > 1 else "single GPU"}
+
+
+def oracle_steps(wl, steps, warmup, budget_s):
+    """The FP64 oracle on the host cores, timed on whole KDK steps of the
+    workload: kick-drift (numpy), force evaluation k -- a new tree and lists
+    when k % n_reuse == 0, else the reusing step on the kept lists -- and
+    kick. Every step is measured; nothing is extrapolated. The force runs on
+    every s-th i-group: s = 1 (whole steps) unless the run's estimated
+    length exceeds budget_s, then the smallest power of two that fits, and
+    the line states it. Returns the measured totals."""
     import numpy as np
 
     import ics
@@ -243,85 +293,97 @@ def cpu_baseline(wl, max_groups_frac=0.25):
     if wl["model"] == "batch":  # the largest system stands for the batch
         off = wl["sys_off"]
         k = int(np.argmax(np.diff(off)))
-        p = ics.Particles(*(getattr(p, a)[off[k]:off[k + 1]]
+        p = ics.Particles(*(getattr(p, a)[off[k]:off[k + 1]].copy()
                             for a in ("x", "y", "z", "vx", "vy", "vz", "m")))
         label = f"{wl['name']} (largest system, N={p.n})"
     kw = dict(n_grp=wl["n_grp"], theta=wl["theta"], eps=wl["eps"], quad=wl["quad"])
-    t0 = time.perf_counter()
-    t = oracle.Tree(p.x, p.y, p.z, p.m, **kw)
-    t_build = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    t.update(p.x, p.y, p.z, p.m)
-    t_update = time.perf_counter() - t0
-    g = t.groups()
-    eo, _, so, _ = t.lists()
-    per_group = g["count"] * ((eo[1:] - eo[:-1]) + (so[1:] - so[:-1]))
-    stride = max(1, int(round(1.0 / max_groups_frac)))
-    sel = np.arange(0, len(per_group), stride)
-    t0 = time.perf_counter()
-    t.force_groups(sel)
-    t_force = time.perf_counter() - t0
-    i_total = float(per_group.sum())
-    i_sel = float(per_group[sel].sum())
-    r = wl["n_reuse"]
-    window = t_build + (r - 1) * t_update + r * t_force * (i_total / i_sel)
-    value = r * i_total / window
-    sample = (f"{label}: one construction step ({t_build:.2f} s) and one reusing step "
-              f"({t_update:.2f} s) on all N, force on every {stride}th group ({t_force:.2f} s, "
-              f"{i_sel:.3g} of {i_total:.3g} interactions), extrapolated to a {r}-step window")
-    return {"value": value, "unit": "interactions/s", "cores": oracle.num_threads(),
-            "kind": "oracle", "sample": sample,
-            "ms_per_step": 1e3 * window / r}
-
-
-def run_reference(args, wl):
-    """--impl reference: the oracle as it stands, K timed bounded steps."""
-    import numpy as np
-
-    import oracle
-
-    p = particles(wl)
-    if wl["model"] == "batch":  # the largest system stands for the batch
-        off = wl["sys_off"]
-        k = int(np.argmax(np.diff(off)))
-        p = type(p)(*(getattr(p, a)[off[k]:off[k + 1]]
-                      for a in ("x", "y", "z", "vx", "vy", "vz", "m")))
-    kw = dict(n_grp=wl["n_grp"], theta=wl["theta"], eps=wl["eps"], quad=wl["quad"])
-    stride = 32
+    R, dt = wl["n_reuse"], wl["dt"]
+    x, y, z = p.x.copy(), p.y.copy(), p.z.copy()
+    vx, vy, vz, m = p.vx.copy(), p.vy.copy(), p.vz.copy(), p.m
+    ax = ay = az = np.zeros(p.n)
     t = None
-    tot_i, tot_s = 0.0, 0.0
-    for k in range(args.warmup + args.steps):
+    stride = None
+    tot = {"s": 0.0, "tree_s": 0.0, "force_s": 0.0, "inter": 0.0, "inter_all": 0.0}
+    for k in range(warmup + steps):
         t0 = time.perf_counter()
-        if t is None or k % wl["n_reuse"] == 0:
-            t = oracle.Tree(p.x, p.y, p.z, p.m, **kw)
+        vx += 0.5 * dt * ax
+        vy += 0.5 * dt * ay
+        vz += 0.5 * dt * az
+        x += dt * vx
+        y += dt * vy
+        z += dt * vz
+        if t is None or k % R == 0:
+            t = oracle.Tree(x, y, z, m, **kw)
         else:
-            t.update(p.x, p.y, p.z, p.m)
-        t_tree = time.perf_counter() - t0
+            t.update(x, y, z, m)
+        t1 = time.perf_counter()
         g = t.groups()
         eo, _, so, _ = t.lists()
         per_group = g["count"] * ((eo[1:] - eo[:-1]) + (so[1:] - so[:-1]))
+        if stride is None:  # a probe on every 16th group sets the sample
+            probe = np.arange(0, len(per_group), 16)
+            tp = time.perf_counter()
+            t.force_groups(probe)
+            rate = float(per_group[probe].sum()) / max(time.perf_counter() - tp, 1e-9)
+            full = float(per_group.sum()) / rate
+            tree = t1 - t0
+            stride = 1
+            while (warmup + steps) * (tree / R + full / stride) > budget_s and stride < 64:
+                stride *= 2
+            t1 = time.perf_counter()  # the probe is not part of the step
         sel = np.arange(k % stride, len(per_group), stride)
-        t0 = time.perf_counter()
-        t.force_groups(sel)
-        t_force = time.perf_counter() - t0
-        i_total, i_sel = float(per_group.sum()), float(per_group[sel].sum())
-        step_s = t_tree + t_force * i_total / max(i_sel, 1.0)
-        if k >= args.warmup:
-            tot_i += i_total
-            tot_s += step_s
-    value = tot_i / tot_s
-    ms = 1e3 * tot_s / args.steps
-    sample = (f"each step: full tree build or reuse update on all N, force on every {stride}th "
-              f"group, extrapolated to all groups")
+        t2 = time.perf_counter()
+        fx, fy, fz, _ = t.force_groups(sel) if stride > 1 else t.force()
+        if stride > 1:
+            fx, fy, fz = (np.nan_to_num(a) for a in (fx, fy, fz))
+        ax, ay, az = fx, fy, fz
+        vx += 0.5 * dt * ax
+        vy += 0.5 * dt * ay
+        vz += 0.5 * dt * az
+        t3 = time.perf_counter()
+        if k >= warmup:
+            tot["s"] += t3 - t0 - (t2 - t1)
+            tot["tree_s"] += t1 - t0
+            tot["force_s"] += t3 - t2
+            tot["inter"] += float(per_group[sel].sum())
+            tot["inter_all"] += float(per_group.sum())
+    model, nproc = cpu_model()
+    frac = "all i-groups" if stride == 1 else f"every {stride}th i-group"
+    sample = (f"{label}: {steps} whole KDK steps after {warmup} warm-up (a new tree and lists "
+              f"every {R}th step, reusing steps between), tree and integration on all N, force "
+              f"on {frac}; measured {tot['s']:.2f} s for {tot['inter']:.4g} interactions "
+              f"({tot['inter'] / max(tot['inter_all'], 1):.3f} of the steps' interactions), "
+              f"nothing extrapolated")
+    return {"value": tot["inter"] / tot["s"], "unit": "interactions/s",
+            "cores": oracle.num_threads(), "cpu_model": model, "nproc": nproc,
+            "kind": "oracle", "sample": sample, "ms_per_step": 1e3 * tot["s"] / steps,
+            "measured_s": tot["s"], "tree_s": tot["tree_s"], "force_s": tot["force_s"],
+            "group_stride": stride, "interactions_computed": tot["inter"],
+            "interactions_of_whole_steps": tot["inter_all"]}
+
+
+def cpu_baseline(wl):
+    """The oracle on the host cores over one list-reuse window of whole
+    steps (about 5-10 s of CPU work on the 2^20 workload)."""
+    return oracle_steps(wl, wl["n_reuse"], 0, budget_s=30.0)
+
+
+def run_reference(args, wl):
+    """--impl reference: the oracle as it stands, K timed steps after W
+    warm-up steps, whole steps while the run stays within about two
+    minutes (a stated group sample beyond that)."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    r = oracle_steps(wl, args.steps, args.warmup, budget_s=120.0)
+    base = {k: r[k] for k in ("value", "unit", "cores", "cpu_model", "nproc", "kind", "sample",
+                              "measured_s", "group_stride")}
     line = {
-        "impl": "reference", "metric": "force interactions/s", "value": value,
+        "impl": "reference", "metric": "force interactions/s", "value": r["value"],
         "unit": "interactions/s", "n_gpus": args.gpus, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": describe(wl)},
-        "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": oracle.num_threads(),
-                         "kind": "oracle", "sample": sample},
-        "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0,
+        "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": bench_config(wl, world, shard=wl["model"] == "batch" and world > 1),
+        "cpu_baseline": base,
+        "e2e": {"value": r["value"], "unit": "interactions/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -531,8 +593,11 @@ def learned_study(args, wl, afd, torch, np, dev, stream, local, p, tuned, launch
                         "targets": int(len(tg)), "reference": "FP64 direct sum (afd_direct_sum)",
                         "plain_interactions": i_plain0, "learned_interactions": i_learned0},
         "ms_per_step": ms_l,
+        "ms_per_step_median": float(np.median(step_ms)),
         "ms_per_construction_step": float(np.mean(cons)) if cons else None,
         "ms_per_reuse_step": float(np.mean(reus)) if reus else None,
+        "ms_per_construction_step_median": float(np.median(cons)) if cons else None,
+        "ms_per_reuse_step_median": float(np.median(reus)) if reus else None,
         "interactions_per_step": float(np.mean(inter)),
         "interactions_per_s": float(sum(inter)) / (sum(step_ms) * 1e-3),
         "force_ms_mean": float(np.mean(force_ms)) if force_ms else None,
@@ -820,6 +885,9 @@ def main():
     stream = torch.cuda.Stream(dev)  # a capturable (non-default) stream
     torch.cuda.set_stream(stream)
     shard = None
+    config = bench_config(wl, world, shard=wl["model"] == "batch" and world > 1,
+                          groups_shared=args.shard == "groups" and world > 1
+                          and wl["model"] != "batch")
     if wl["model"] == "batch" and world > 1:  # independent systems: shard them
         p, wl["sys_off"], shard = rank_batch(wl, rank, world)
         wl["n_systems"] = len(shard)
@@ -869,7 +937,7 @@ def main():
         afd.afd_graph_capture_step(ctx, x, y, z, vx, vy, vz, m, acc, dt)
     state = {"x": x, "y": y, "z": z, "vx": vx, "vy": vy, "vz": vz, "m": m, "acc": acc, "k": 1}
     sampler = ClockSampler(local)
-    t_wall = [0.0]
+    t_wall = [0.0, 0.0]
 
     def before_timed():
         if dist:
@@ -877,13 +945,15 @@ def main():
         sampler.start()
         time.sleep(0.3)
         t_wall[0] = time.perf_counter()
+        t_wall[1] = time.time()
 
     step_ms, force_ms, inter, modes, launches = run_loop(
         afd, torch, ctx, g, state, steps=args.steps, warmup=args.warmup, batch=batch, R=R, dt=dt,
         flush=flush, stream=stream, dev=dev, before_timed=before_timed, combine=combine,
         count=count)
+    t_epoch = (t_wall[1], time.time())
     t_wall = time.perf_counter() - t_wall[0]
-    clocks = sampler.stop()
+    clocks = sampler.stop(t_epoch)
     total_ms = float(sum(step_ms))
     total_i = float(sum(inter))
     total_ms, total_i_all = aggregate(dist, dev, total_ms, total_i)
@@ -934,8 +1004,9 @@ def main():
         e_s, e_i = aggregate(dist, dev, e_s, e_i)
         e2e = {"value": e_i / e_s, "unit": "interactions/s", "h2d_bytes_per_step": 4 * 8 * n,
                "d2h_bytes_per_step": 16 * n, "ms_per_step": 1e3 * e_s / args.steps,
-               "call": "afd_calc_force_all_host (force evaluation per step; integration not "
-                       "included)"}
+               "call": "afd_calc_force_all_host: per step the force evaluation with its "
+                       "copies (x, y, z, m in, n x 4 floats out); the kick and drift that value's "
+                       "steps include are not in it (device kernels, about 1% of a step)"}
         g2.close()
 
     if rank != 0:
@@ -955,14 +1026,12 @@ def main():
                                         "uniform_sphere": "cold uniform sphere",
                                         "galaxy": "halo + disk galaxy"}.get(wl["model"],
                                                                             wl["model"]) + ")",
-        "config": {"workload": describe(wl), "n": n, "l2": "flushed (256 MB write) between "
-                   "timed steps, outside the timed events", "parallelism":
-                   ("systems sharded over ranks" if shard is not None else
-                    "group slices over ranks, forces all-reduced" if groups_shared
-                    else "replicas")
-                   if world > 1 else "single GPU"},
+        "config": config,
+        "ms_per_step_median": float(np.median(step_ms)),
         "ms_per_construction_step": float(np.mean(cons)) if cons else None,
         "ms_per_reuse_step": float(np.mean(reus)) if reus else None,
+        "ms_per_construction_step_median": float(np.median(cons)) if cons else None,
+        "ms_per_reuse_step_median": float(np.median(reus)) if reus else None,
         "interactions_per_step": total_i / args.steps,
         "roofline": roofline,
         "clocks": clocks,
