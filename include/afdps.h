@@ -143,7 +143,12 @@ int afd_reuse_lists(afd_ctx *ctx, const double *x, const double *y, const double
  * the group's particles. One warp takes 32 of a group's particles, or 64
  * (two full 32-particle units of one group, monopole lists), in the launch
  * order set by afd_make_interaction_lists. acc4: device, n x (ax, ay, az,
- * phi) floats, caller order, overwritten. Does not synchronise. */
+ * phi) floats, caller order, overwritten. Does not synchronise.
+ * The potential is the FP32 kernel's (compensated sums, rms relative
+ * difference from an FP64 sum over the same lists about 1e-7, far below the
+ * tree's own approximation error of 1e-4 .. 1e-3 at theta 0.3 .. 0.7); no
+ * FP64 potential is written, since an FP64 copy of it would carry no more
+ * correct digits. Energies are summed in FP64 by afd_energy. */
 int afd_calc_force(afd_ctx *ctx, float *acc4);
 
 /* The top-level call of Section 5 (calcForceAllAndWriteBackMultiWalkIndex):
@@ -332,6 +337,22 @@ int afd_set_work_share(afd_ctx *ctx, int part, int parts);
 /* The current share (host int64[5]): part, parts, first and end group of
  * this part's slice, and its interactions (sum of n_i x list length). */
 int afd_get_work_share(afd_ctx *ctx, int64_t *out);
+
+/* Limits of the tree walks' bounded device loops, for tests of the error
+ * paths (the defaults never bind on valid input). iter_cap: warp steps a
+ * walk may take for one group (or neighbour-walk item) before it stops and
+ * the call returns AFD_ERR_TIMEOUT (default 2 x cells + 64, which a walk
+ * never reaches: every step removes at least one stack entry or expands a
+ * cell). stack_cap: stack entries per warp, 1 .. 448 (the shared-memory
+ * stack); a walk that would need more stops with AFD_ERR_WALK_STACK
+ * (default 448, above what a depth-21 tree can need). arena_chunks_max:
+ * the largest record arena of the list construction, in chunks of 64
+ * records, 1 .. 2^30 (default 2^30); lists that do not fit return
+ * AFD_ERR_LIST_OVERFLOW. 0 restores a default. A walk that stops leaves
+ * the context without lists and usable. Host only; no synchronisation.
+ * AFD_ERR_ARG outside those ranges. */
+int afd_set_walk_limits(afd_ctx *ctx, int64_t iter_cap, int32_t stack_cap,
+                        int64_t arena_chunks_max);
 
 /* Wait for the context's stream and return the device status word. */
 int afd_sync(afd_ctx *ctx);

@@ -99,6 +99,7 @@ def lib():
         "afd_autotune_n_grp": ([_VP, _VP, _VP, _VP, _VP, _I64, _VP, ctypes.c_int, ctypes.c_int, _VP,
                                 _VP], ctypes.c_int),
         "afd_set_launch": ([_VP, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "afd_set_walk_limits": ([_VP, _I64, ctypes.c_int32, _I64], ctypes.c_int),
         "afd_calc_force_materialized": ([_VP, _VP, _VP], ctypes.c_int),
         "afd_let_export": ([_VP, _VP, _D, _I64, _VP, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
         "afd_make_neighbour_lists": ([_VP, _VP, _D], ctypes.c_int),
@@ -265,6 +266,12 @@ def afd_energy(ctx, vx, vy, vz, m, acc4):
     _check(lib().afd_energy(ctx, *p, _dptr(acc4, torch.float32, 4 * n), n,
                             ctypes.cast(out, _VP)), "afd_energy")
     return float(out[0]), float(out[1])
+
+
+def afd_set_walk_limits(ctx, iter_cap=0, stack_cap=0, arena_chunks_max=0):
+    """Limits of the walks' bounded loops (0: defaults); for error-path tests."""
+    _check(lib().afd_set_walk_limits(ctx, int(iter_cap), int(stack_cap), int(arena_chunks_max)),
+           "afd_set_walk_limits")
 
 
 def afd_sync(ctx):

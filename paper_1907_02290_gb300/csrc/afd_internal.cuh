@@ -215,6 +215,9 @@ struct afd_ctx {
   afd::DevBuf l_nrec, l_head_s, l_head_l;
   afd::DevBuf arena_s, arena_l, next_s, next_l, arena_cur;
   uint32_t arena_cap_s = 0, arena_cap_l = 0;
+  // limits of the walks' bounded loops (afd_set_walk_limits; 0: defaults)
+  uint32_t walk_iter_cap = 0, walk_arena_max = 0;
+  int walk_stack_cap = 0;
 
   // scan scratch
   afd::DevBuf scan_tmp;

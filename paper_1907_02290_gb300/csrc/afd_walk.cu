@@ -74,7 +74,8 @@ struct WalkArgs {
   uint2 *arena_l;
   uint32_t cap_s, cap_l;
   int *status;
-  uint32_t iter_cap;
+  uint32_t iter_cap;   // warp steps per group (or item) before the walk gives up
+  int stack_cap;       // stack entries per warp a walk may use, 1 .. kStack
   uint32_t n_cells;  // read only by the self-checking build
   // learned criterion
   const float *mac_w, *g_amin;
@@ -340,7 +341,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
       }
       int last = pos_q[E - 1];
       // keep the stack bounded: fall back to one expansion near the limit
-      if ((sp - (last + 1)) + 8 * E + (last + 1 - f - E) > kStack) {
+      if ((sp - (last + 1)) + 8 * E + (last + 1 - f - E) > a.stack_cap) {
         E = 1;
         last = pos_q[0];
       }
@@ -477,7 +478,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
       const uint32_t K = __shfl_sync(0xffffffffu, oinc, 31);
       const uint32_t off_me = oinc - cnt;
       const int spn = sp - (last + 1);
-      if (spn + (int)K > kStack) {
+      if (spn + (int)K > a.stack_cap) {
         if (lane == 0) atomicOr(a.status, kStWalkStack);
         break;
       }
@@ -696,8 +697,11 @@ int run_walk(afd_ctx *c, WalkArgs &a, int mode, WalkOut &o, int64_t ng) {
   const bool nbr = mode == kModeNeighbour;
   // arena capacity in chunks: kept from earlier walks, first guess from the
   // group count (about 1500 cell ids and 130 leaves per group of 256)
+  const uint32_t cap_max = c->walk_arena_max > 0 ? c->walk_arena_max : (1u << 30);
   if (c->arena_cap_s == 0) c->arena_cap_s = (uint32_t)std::min<int64_t>(ng * 24 + 4096, 1u << 30);
   if (c->arena_cap_l == 0) c->arena_cap_l = (uint32_t)std::min<int64_t>(ng * 4 + 4096, 1u << 30);
+  c->arena_cap_s = std::min(c->arena_cap_s, cap_max);
+  c->arena_cap_l = std::min(c->arena_cap_l, cap_max);
   a.cnt_e = o.cnt_e;
   a.cnt_s = o.cnt_s;
   a.n_lrec = ptr<uint32_t>(c->l_nrec);
@@ -705,7 +709,8 @@ int run_walk(afd_ctx *c, WalkArgs &a, int mode, WalkOut &o, int64_t ng) {
   a.head_l = ptr<uint32_t>(c->l_head_l);
   a.cursor = ptr<uint32_t>(c->arena_cur);
   a.status = ptr<int>(c->status);
-  a.iter_cap = (uint32_t)(2 * c->n_cells + 64);
+  a.iter_cap = c->walk_iter_cap > 0 ? c->walk_iter_cap : (uint32_t)(2 * c->n_cells + 64);
+  a.stack_cap = c->walk_stack_cap > 0 ? c->walk_stack_cap : kStack;
   a.n_cells = (uint32_t)c->n_cells;
   a.n_groups = ng;
   const int64_t nb = mode == kModeLearned ? walk_blocks<kModeLearned>(ng)
@@ -761,11 +766,13 @@ int run_walk(afd_ctx *c, WalkArgs &a, int mode, WalkOut &o, int64_t ng) {
     }
     const uint32_t need_s = (uint32_t)(pin[4] & 0xffffffffu), need_l = (uint32_t)(pin[4] >> 32);
     if (need_s <= c->arena_cap_s && need_l <= c->arena_cap_l) break;
-    if (attempt > 0) return AFD_ERR_LIST_OVERFLOW;  // cannot happen: sized from the cursors
+    // the second pass is sized from the cursors: still too small only at the
+    // capacity limit
+    if (attempt > 0) return AFD_ERR_LIST_OVERFLOW;
     if (need_s > c->arena_cap_s)
-      c->arena_cap_s = (uint32_t)std::min<uint64_t>((uint64_t)need_s * 5 / 4 + 1024, 1u << 30);
+      c->arena_cap_s = (uint32_t)std::min<uint64_t>((uint64_t)need_s * 5 / 4 + 1024, cap_max);
     if (need_l > c->arena_cap_l)
-      c->arena_cap_l = (uint32_t)std::min<uint64_t>((uint64_t)need_l * 5 / 4 + 1024, 1u << 30);
+      c->arena_cap_l = (uint32_t)std::min<uint64_t>((uint64_t)need_l * 5 / 4 + 1024, cap_max);
   }
   o.n_e = pin[0];
   o.n_s = nbr ? 0 : pin[1];
@@ -1139,3 +1146,14 @@ int launch_nbr_walk(afd_ctx *c) {
 }
 
 }  // namespace afd
+
+extern "C" int afd_set_walk_limits(afd_ctx *c, int64_t iter_cap, int32_t stack_cap,
+                                   int64_t arena_chunks_max) {
+  if (!c || iter_cap < 0 || iter_cap > 0xffffffffll || stack_cap < 0 ||
+      stack_cap > afd::kStack || arena_chunks_max < 0 || arena_chunks_max > (1ll << 30))
+    return AFD_ERR_ARG;
+  c->walk_iter_cap = (uint32_t)iter_cap;
+  c->walk_stack_cap = stack_cap;
+  c->walk_arena_max = (uint32_t)arena_chunks_max;
+  return AFD_OK;
+}

@@ -657,15 +657,22 @@ def test_force_launch_shapes(env):
 
 def test_materialized_lists_ablation_is_bit_identical(env):
     """The non-indirect ablation (j-data copied into list order, read without
-    indices) computes the same forces as the indirect kernel, bit for bit."""
+    indices) computes the same forces as the indirect kernel, bit for bit,
+    and both match the oracle's FP64 force on the oracle's own lists."""
     torch, afd, orc = env
     p = ics.plummer(20000 + 11, 71)
     kw = dict(n_grp=64, theta=0.5, eps=1.0 / 256)
     g, a_ind, (x, y, z, m, acc) = run_gpu(env, p, **kw)
+    t = orc.Tree(p.x, p.y, p.z, p.m, **kw)
+    check_structure(g, t)
     acc.fill_(float("nan"))
     t_copy, t_force = afd.afd_calc_force_materialized(g.ctx, acc)
     assert t_copy > 0 and t_force > 0
-    assert np.array_equal(acc.cpu().numpy().astype(np.float64), a_ind)
+    a_mat = acc.cpu().numpy().astype(np.float64)
+    assert np.array_equal(a_mat, a_ind)
+    ref = t.force()
+    assert rms_rel_acc(a_mat, ref) <= FORCE_RMS_TOL
+    assert rms_rel_pot(a_mat, ref) <= POT_RMS_TOL
     g.close()
     gq, _, (_, _, _, _, accq) = run_gpu(env, p, quad=True, **kw)
     with pytest.raises(afd.AfdError):
@@ -712,3 +719,46 @@ def test_work_share_slices_sum_to_the_whole_force(env, parts):
     assert bounds[-1] == n_groups and inters == inter
     assert torch.equal(tot, ref) and torch.equal(tot2, ref2)
     whole.close()
+
+
+def test_bounded_walk_loops_stop_with_a_status(env):
+    """The walks' bounded device loops, made to run out on a small tree by
+    lowered limits: the iteration cap returns AFD_ERR_TIMEOUT (gravity and
+    neighbour walks), the stack bound AFD_ERR_WALK_STACK, a record arena
+    capped below what the lists need AFD_ERR_LIST_OVERFLOW; after each the
+    context has no lists, and with the limits restored it makes the oracle's
+    lists again."""
+    torch, afd, orc = env
+    p = ics.plummer(20000, 81)
+    kw = dict(n_grp=64, theta=0.5, eps=1.0 / 256)
+    dev = torch.device("cuda:0")
+    X = [torch.tensor(a, device=dev) for a in (p.x, p.y, p.z, p.m)]
+    g = afd.Gravity(afd.Config(**kw), 0, torch.cuda.current_stream())
+    afd.afd_tree_build(g.ctx, *X)
+    acc = torch.zeros(p.n, 4, dtype=torch.float32, device=dev)
+    h = torch.full((p.n,), 0.05, dtype=torch.float64, device=dev)
+    t = orc.Tree(p.x, p.y, p.z, p.m, **kw)
+    for limits, status in (((3, 0, 0), -7), ((0, 12, 0), -10), ((0, 0, 8), -6)):
+        afd.afd_set_walk_limits(g.ctx, *limits)
+        with pytest.raises(afd.AfdError) as e:
+            afd.afd_make_interaction_lists(g.ctx, afd.AFD_MAKE_LIST_FOR_REUSE)
+        assert e.value.status == status, limits
+        assert g.stats()["saved"] == 0
+        with pytest.raises(afd.AfdError) as e:
+            afd.afd_calc_force(g.ctx, acc)
+        assert e.value.status == -4  # no lists
+        if status == -7:
+            with pytest.raises(afd.AfdError) as e:
+                afd.afd_make_neighbour_lists(g.ctx, h, 0.0)
+            assert e.value.status == -7
+        afd.afd_set_walk_limits(g.ctx, 0, 0, 0)
+        afd.afd_make_interaction_lists(g.ctx, afd.AFD_MAKE_LIST_FOR_REUSE)
+        afd.afd_calc_force(g.ctx, acc)
+        torch.cuda.synchronize()
+        check_structure(g, t)
+        assert rms_rel_acc(acc.cpu().numpy().astype(np.float64), t.force()) <= FORCE_RMS_TOL
+    for bad in ((-1, 0, 0), (0, 449, 0), (0, -1, 0), (0, 0, (1 << 30) + 1)):
+        with pytest.raises(afd.AfdError) as e:
+            afd.afd_set_walk_limits(g.ctx, *bad)
+        assert e.value.status == -1
+    g.close()
