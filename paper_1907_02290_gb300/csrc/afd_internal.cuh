@@ -37,6 +37,7 @@ enum : int {
   kStWalkIter = 4,
   kStOverflow = 8,
   kStBadRadius = 16,
+  kStSpin = 32,  // a bounded wait on another block of the same launch gave up
 };
 int status_to_error(int bits);
 

@@ -270,15 +270,25 @@ __global__ void __launch_bounds__(kThreads) k_keys(const double *__restrict__ x,
 }
 
 // ---------------------------------------------------------------------------
-// Stable LSD radix sort of (key, index), 8-bit digits, 8 passes. Each pass:
-// per-tile digit histogram, exclusive scan in digit-major order, then a
-// stable scatter in which every tile ranks its keys in input order
-// (warp match for lanes, shared counters for warps and rounds).
+// Stable LSD radix sort of (key, index), 8-bit digits, 8 passes (Section 6.2
+// sorts with 8-bit chunks). One launch counts the digits of every pass;
+// then each pass is one launch: tiles of kSortTile keys, taken in input
+// order from a counter, count their digits, publish the counts, and find
+// each digit's offset among the preceding tiles by decoupled look-back
+// (a tile adds its predecessors' published counts back to the first
+// inclusive prefix it meets), then scatter their keys stably -- every tile
+// ranks its keys in input order (warp match for lanes, shared counters for
+// warps and rounds).
 // ---------------------------------------------------------------------------
 constexpr int kSortThreads = 256;
 constexpr int kSortRounds = 16;
 constexpr int kSortTile = kSortThreads * kSortRounds;
 constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortMaxPasses = 10;  // 8 key bytes + up to 2 bytes of system id
+// look-back words: the count (or inclusive prefix) in bits 0-29, the state
+// in bits 30-31
+constexpr uint32_t kLookAgg = 1u << 30, kLookPrefix = 2u << 30, kLookValue = (1u << 30) - 1u;
+constexpr uint32_t kSpinLimit = 1u << 22;  // polls of one predecessor's word before giving up
 
 // SYS: the digit is byte (shift / 8) of the payload's system id instead of
 // the key (the extra passes that order several systems).
@@ -288,38 +298,121 @@ __device__ __forceinline__ uint32_t sort_digit(uint64_t key, uint32_t val, int s
   return SYS ? ((sys_of[val] >> shift) & 255u) : (uint32_t)((key >> shift) & 255u);
 }
 
-template <bool SYS>
-__global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint64_t *__restrict__ keys,
-                                                            const uint32_t *__restrict__ vals,
-                                                            const uint32_t *__restrict__ sys_of,
-                                                            int64_t n, int shift,
-                                                            uint32_t *__restrict__ cnt,
-                                                            int num_tiles) {
-  __shared__ uint32_t h[256];
-  h[threadIdx.x] = 0;
+// Digit counts of every pass: hist[p * 256 + d], pass p < 8 the key's byte
+// p, passes 8, 9 the bytes of the system id. Counts of equal digits in a
+// warp are added by one lane.
+__global__ void __launch_bounds__(kSortThreads) k_sort_hist_all(
+    const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+    const uint32_t *__restrict__ sys_of, int64_t n, int passes, uint32_t *__restrict__ hist) {
+  __shared__ uint32_t h[kSortMaxPasses][256];
+  for (int k = threadIdx.x; k < kSortMaxPasses * 256; k += kSortThreads) (&h[0][0])[k] = 0;
   __syncthreads();
-  const int64_t base = (int64_t)blockIdx.x * kSortTile;
-  for (int k = threadIdx.x; k < kSortTile; k += kSortThreads) {
-    const int64_t i = base + k;
-    if (i < n) atomicAdd(&h[sort_digit<SYS>(SYS ? 0ull : keys[i], SYS ? vals[i] : 0u, shift, sys_of)], 1u);
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t stride = (int64_t)gridDim.x * kSortThreads;
+  for (int64_t b = (int64_t)blockIdx.x * kSortThreads; b < n; b += stride) {
+    const int64_t i = b + threadIdx.x;
+    const bool valid = i < n;
+    const uint64_t key = valid ? keys[i] : 0ull;
+    const uint32_t sys = (valid && passes > 8) ? sys_of[vals[i]] : 0u;
+    for (int p = 0; p < passes; p++) {
+      const uint32_t d = !valid ? 256u : p < 8 ? (uint32_t)((key >> (8 * p)) & 255u)
+                                               : (sys >> (8 * (p - 8))) & 255u;
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      if (valid && (peers & lt) == 0u) atomicAdd(&h[p][d], (uint32_t)__popc(peers));
+    }
   }
   __syncthreads();
-  cnt[(int64_t)threadIdx.x * num_tiles + blockIdx.x] = h[threadIdx.x];
+  for (int k = threadIdx.x; k < passes * 256; k += kSortThreads) {
+    const uint32_t v = (&h[0][0])[k];
+    if (v) atomicAdd(&hist[k], v);
+  }
 }
 
+// Exclusive scan of one value per thread of a 256-thread block.
+__device__ __forceinline__ uint32_t block_excl_256(uint32_t v, uint32_t *warp_sums) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) warp_sums[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t w = lane < kSortWarps ? warp_sums[lane] : 0u;
+    uint32_t winc = w;
+#pragma unroll
+    for (int o = 1; o < kSortWarps; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, winc, o);
+      if (lane >= o) winc += t;
+    }
+    if (lane < kSortWarps) warp_sums[lane] = winc - w;
+  }
+  __syncthreads();
+  return warp_sums[warp] + inc - v;
+}
+
+// One pass: look[t * 256 + d] are the tiles' look-back words and *ctr the
+// tile counter, both zero at launch; hist the pass's 256 digit counts.
 template <bool SYS>
-__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
+__global__ void __launch_bounds__(kSortThreads) k_sort_pass(
     const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const uint32_t *__restrict__ sys_of, int64_t n, int shift,
-    const uint32_t *__restrict__ off, int num_tiles) {
+    const uint32_t *__restrict__ hist, uint32_t *look, uint32_t *ctr, int *status) {
+  __shared__ uint32_t s_tile;
+  __shared__ uint32_t cnt[256];
   __shared__ uint32_t gbase[256];
   __shared__ uint32_t run[256];
+  __shared__ uint32_t wsum[kSortWarps];
   __shared__ uint32_t wcnt[kSortWarps][256];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  gbase[tid] = off[(int64_t)tid * num_tiles + blockIdx.x];
-  run[tid] = 0;
   const unsigned lt = (1u << lane) - 1u;
-  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  if (tid == 0) s_tile = atomicAdd(ctr, 1u);
+  cnt[tid] = 0;
+  run[tid] = 0;
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const int64_t base = (int64_t)tile * kSortTile;
+  // the tile's digit counts
+  for (int r = 0; r < kSortRounds; r++) {
+    const int64_t i = base + (int64_t)r * kSortThreads + tid;
+    const bool valid = i < n;
+    const uint32_t digit = valid ? sort_digit<SYS>(SYS ? 0ull : kin[i], SYS ? vin[i] : 0u, shift,
+                                                   sys_of)
+                                 : 256u;
+    const unsigned peers = __match_any_sync(0xffffffffu, digit);
+    if (valid && (peers & lt) == 0u) atomicAdd(&cnt[digit], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+  // publish, then look back over the preceding tiles (thread tid: digit tid)
+  const uint32_t mine = cnt[tid];
+  volatile uint32_t *vl = look;
+  uint32_t excl = 0;
+  if (tile == 0) {
+    vl[tid] = kLookPrefix | mine;
+  } else {
+    vl[(size_t)tile * 256 + tid] = kLookAgg | mine;
+    for (int64_t t = (int64_t)tile - 1; t >= 0; t--) {
+      uint32_t w = vl[(size_t)t * 256 + tid];
+      for (uint32_t k = 0; (w & ~kLookValue) == 0u; k++) {
+        if (k == kSpinLimit) {  // give up: the pass's result is wrong, the call fails
+          atomicOr(status, kStSpin);
+          w = kLookPrefix;
+          break;
+        }
+        __nanosleep(32);
+        w = vl[(size_t)t * 256 + tid];
+      }
+      excl += w & kLookValue;
+      if ((w & ~kLookValue) == kLookPrefix) break;
+    }
+    vl[(size_t)tile * 256 + tid] = kLookPrefix | ((excl + mine) & kLookValue);
+  }
+  gbase[tid] = block_excl_256(hist[tid], wsum) + excl;
+  __syncthreads();
+  // stable scatter, round by round in input order
   for (int r = 0; r < kSortRounds; r++) {
     const int64_t i = base + (int64_t)r * kSortThreads + tid;
     const bool valid = i < n;
@@ -1013,35 +1106,49 @@ int launch_sort(afd_ctx *c, int64_t n) {
     return ck();
   }
   const int num_tiles = (int)((n + kSortTile - 1) / kSortTile);
-  const int64_t nc = (int64_t)256 * num_tiles;
-  AFD_TRY(reserve(c->keys2, sizeof(uint64_t) * n));
-  AFD_TRY(reserve(c->perm2, sizeof(uint32_t) * n));
-  AFD_TRY(reserve(c->sort_cnt, sizeof(uint32_t) * nc));
-  AFD_TRY(reserve(c->sort_off, sizeof(uint32_t) * (nc + 1)));
-  uint64_t *ka = ptr<uint64_t>(c->keys), *kb = ptr<uint64_t>(c->keys2);
-  uint32_t *va = ptr<uint32_t>(c->perm), *vb = ptr<uint32_t>(c->perm2);
   // eight passes over the key, then (several systems) one or two passes over
   // the system id: stable, so the result is ordered by (system, key)
   const int sys_passes = c->n_sys > 256 ? 2 : (c->n_sys > 1 ? 1 : 0);
+  const int passes = 8 + sys_passes;
+  // look-back words of one pass (256 per tile) and its tile counter; all
+  // passes' at once when that stays small, else one pass's, cleared per pass
+  const size_t look_words = (size_t)256 * num_tiles + 64;
+  const bool per_pass = (size_t)passes * look_words * sizeof(uint32_t) > ((size_t)32 << 20);
+  const int slices = per_pass ? 1 : passes;
+  AFD_TRY(reserve(c->keys2, sizeof(uint64_t) * n));
+  AFD_TRY(reserve(c->perm2, sizeof(uint32_t) * n));
+  AFD_TRY(reserve(c->sort_cnt, sizeof(uint32_t) * 256 * kSortMaxPasses));
+  AFD_TRY(reserve(c->sort_off, sizeof(uint32_t) * look_words * slices));
+  uint64_t *ka = ptr<uint64_t>(c->keys), *kb = ptr<uint64_t>(c->keys2);
+  uint32_t *va = ptr<uint32_t>(c->perm), *vb = ptr<uint32_t>(c->perm2);
   const uint32_t *sys_of = c->n_sys > 1 ? ptr<uint32_t>(c->sys_of) : nullptr;
-  for (int pass = 0; pass < 8 + sys_passes; pass++) {
-    const bool sys = pass >= 8;
-    const int shift = sys ? 8 * (pass - 8) : 8 * pass;
-    if (sys)
-      k_sort_hist<true><<<num_tiles, kSortThreads, 0, c->stream>>>(
-          ka, va, sys_of, n, shift, ptr<uint32_t>(c->sort_cnt), num_tiles);
-    else
-      k_sort_hist<false><<<num_tiles, kSortThreads, 0, c->stream>>>(
-          ka, va, sys_of, n, shift, ptr<uint32_t>(c->sort_cnt), num_tiles);
+  uint32_t *hist = ptr<uint32_t>(c->sort_cnt), *look = ptr<uint32_t>(c->sort_off);
+  if (cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 256 * passes, c->stream) != cudaSuccess)
+    return AFD_ERR_CUDA;
+  if (!per_pass &&
+      cudaMemsetAsync(look, 0, sizeof(uint32_t) * look_words * slices, c->stream) != cudaSuccess)
+    return AFD_ERR_CUDA;
+  {
+    const int64_t want = (n + kSortThreads - 1) / kSortThreads;
+    const unsigned nb = (unsigned)(want < 152 * 4 ? want : 152 * 4);
+    k_sort_hist_all<<<nb, kSortThreads, 0, c->stream>>>(ka, va, sys_of, n, passes, hist);
     c->launches++;
     AFD_TRY(ck());
-    AFD_TRY(scan_u32(c, ptr<uint32_t>(c->sort_cnt), ptr<uint32_t>(c->sort_off), nc));
+  }
+  for (int pass = 0; pass < passes; pass++) {
+    const bool sys = pass >= 8;
+    const int shift = sys ? 8 * (pass - 8) : 8 * pass;
+    uint32_t *lk = look + (per_pass ? 0 : (size_t)pass * look_words);
+    if (per_pass &&
+        cudaMemsetAsync(lk, 0, sizeof(uint32_t) * look_words, c->stream) != cudaSuccess)
+      return AFD_ERR_CUDA;
+    uint32_t *ctr = lk + (size_t)256 * num_tiles;
     if (sys)
-      k_sort_scatter<true><<<num_tiles, kSortThreads, 0, c->stream>>>(
-          ka, va, kb, vb, sys_of, n, shift, ptr<uint32_t>(c->sort_off), num_tiles);
+      k_sort_pass<true><<<num_tiles, kSortThreads, 0, c->stream>>>(
+          ka, va, kb, vb, sys_of, n, shift, hist + 256 * pass, lk, ctr, ptr<int>(c->status));
     else
-      k_sort_scatter<false><<<num_tiles, kSortThreads, 0, c->stream>>>(
-          ka, va, kb, vb, sys_of, n, shift, ptr<uint32_t>(c->sort_off), num_tiles);
+      k_sort_pass<false><<<num_tiles, kSortThreads, 0, c->stream>>>(
+          ka, va, kb, vb, sys_of, n, shift, hist + 256 * pass, lk, ctr, ptr<int>(c->status));
     c->launches++;
     AFD_TRY(ck());
     uint64_t *tk = ka; ka = kb; kb = tk;

@@ -1,5 +1,6 @@
-// Device buffers and device-wide exclusive scans (three phases: per-tile
-// totals, one-block scan of the totals, per-tile scan with its base).
+// Device buffers and device-wide exclusive scans (one launch: tiles taken in
+// input order from a counter publish their totals and find their bases by
+// decoupled look-back over the preceding tiles).
 #include "afd_internal.cuh"
 
 namespace afd {
@@ -31,7 +32,7 @@ void release(DevBuf &b) {
 int status_to_error(int bits) {
   if (bits & kStNonFinite) return AFD_ERR_NONFINITE;
   if (bits & kStWalkStack) return AFD_ERR_WALK_STACK;
-  if (bits & kStWalkIter) return AFD_ERR_TIMEOUT;
+  if (bits & (kStWalkIter | kStSpin)) return AFD_ERR_TIMEOUT;
   if (bits & kStOverflow) return AFD_ERR_LIST_OVERFLOW;
   if (bits & kStBadRadius) return AFD_ERR_BAD_RADIUS;
   return AFD_OK;
@@ -42,7 +43,6 @@ namespace {
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;
-constexpr int kScanOneBlock = 1024;
 
 // Exclusive scan of one value per thread across the block; the block total
 // is returned through *total. NT <= 1024.
@@ -77,41 +77,24 @@ __device__ T block_exclusive(T v, T *total) {
   return res;
 }
 
-template <class Tin, class Tout>
-__global__ void k_scan_reduce(const Tin *__restrict__ in, int64_t n, Tout *__restrict__ part) {
-  const int64_t base = (int64_t)blockIdx.x * kScanTile;
-  Tout s = 0;
-  for (int k = threadIdx.x; k < kScanTile; k += kScanThreads) {
-    const int64_t i = base + k;
-    if (i < n) s += (Tout)in[i];
-  }
-  Tout total;
-  block_exclusive<Tout, kScanThreads>(s, &total);
-  if (threadIdx.x == 0) part[blockIdx.x] = total;
-}
+// Look-back words: the tile total (or inclusive prefix) in bits 0-61, the
+// state in bits 62-63 (0: not yet published).
+constexpr unsigned long long kScanAgg = 1ull << 62, kScanPrefix = 2ull << 62;
+constexpr unsigned long long kScanValue = (1ull << 62) - 1ull;
+constexpr uint32_t kScanSpinLimit = 1u << 22;  // polls of one predecessor's word
 
-template <class Tout>
-__global__ void k_scan_single(Tout *__restrict__ part, int64_t nb, Tout *__restrict__ out_total) {
-  const int64_t per = (nb + kScanOneBlock - 1) / kScanOneBlock;
-  const int64_t b0 = (int64_t)threadIdx.x * per;
-  Tout s = 0;
-  for (int64_t k = 0; k < per; k++)
-    if (b0 + k < nb) s += part[b0 + k];
-  Tout total;
-  Tout ex = block_exclusive<Tout, kScanOneBlock>(s, &total);
-  for (int64_t k = 0; k < per; k++)
-    if (b0 + k < nb) {
-      Tout v = part[b0 + k];
-      part[b0 + k] = ex;
-      ex += v;
-    }
-  if (threadIdx.x == 0) *out_total = total;
-}
-
+// look[t] are the tiles' look-back words and look[nb] the tile counter, all
+// zero at launch; out[n] receives the total.
 template <class Tin, class Tout>
-__global__ void k_scan_down(const Tin *__restrict__ in, int64_t n, const Tout *__restrict__ part,
-                            Tout *__restrict__ out) {
-  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+__global__ void __launch_bounds__(kScanThreads) k_scan(const Tin *__restrict__ in, int64_t n,
+                                                       Tout *__restrict__ out,
+                                                       unsigned long long *look, int64_t nb,
+                                                       int *status) {
+  __shared__ unsigned long long s_tile, s_base;
+  if (threadIdx.x == 0) s_tile = atomicAdd(&look[nb], 1ull);
+  __syncthreads();
+  const int64_t tile = (int64_t)s_tile;
+  const int64_t base = tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
   Tout v[kScanItems];
   Tout s = 0;
 #pragma unroll
@@ -121,7 +104,35 @@ __global__ void k_scan_down(const Tin *__restrict__ in, int64_t n, const Tout *_
     s += v[k];
   }
   Tout total;
-  Tout ex = block_exclusive<Tout, kScanThreads>(s, &total) + part[blockIdx.x];
+  Tout ex = block_exclusive<Tout, kScanThreads>(s, &total);
+  if (threadIdx.x == 0) {
+    volatile unsigned long long *vl = look;
+    unsigned long long excl = 0;
+    if (tile == 0) {
+      vl[0] = kScanPrefix | ((unsigned long long)total & kScanValue);
+    } else {
+      vl[tile] = kScanAgg | ((unsigned long long)total & kScanValue);
+      for (int64_t t = tile - 1; t >= 0; t--) {
+        unsigned long long w = vl[t];
+        for (uint32_t k = 0; (w & ~kScanValue) == 0ull; k++) {
+          if (k == kScanSpinLimit) {  // give up: the result is wrong, the call fails
+            atomicOr(status, kStSpin);
+            w = kScanPrefix;
+            break;
+          }
+          __nanosleep(32);
+          w = vl[t];
+        }
+        excl += w & kScanValue;
+        if ((w & ~kScanValue) == kScanPrefix) break;
+      }
+      vl[tile] = kScanPrefix | ((excl + (unsigned long long)total) & kScanValue);
+    }
+    s_base = excl;
+    if (tile == nb - 1) out[n] = (Tout)(excl + (unsigned long long)total);
+  }
+  __syncthreads();
+  ex += (Tout)s_base;
 #pragma unroll
   for (int k = 0; k < kScanItems; k++) {
     const int64_t i = base + k;
@@ -137,14 +148,14 @@ int scan_impl(afd_ctx *c, const Tin *in, Tout *out, int64_t n) {
     if (cudaMemsetAsync(out, 0, sizeof(Tout), c->stream) != cudaSuccess) return AFD_ERR_CUDA;
     return AFD_OK;
   }
-  int st = reserve(c->scan_tmp, sizeof(Tout) * (size_t)(nb + 1));
+  int st = reserve(c->scan_tmp, sizeof(unsigned long long) * (size_t)(nb + 1));
   if (st) return st;
-  Tout *part = ptr<Tout>(c->scan_tmp);
-  k_scan_reduce<Tin, Tout><<<(unsigned)nb, kScanThreads, 0, c->stream>>>(in, n, part);
-  c->launches++;
-  k_scan_single<Tout><<<1, kScanOneBlock, 0, c->stream>>>(part, nb, out + n);
-  c->launches++;
-  k_scan_down<Tin, Tout><<<(unsigned)nb, kScanThreads, 0, c->stream>>>(in, n, part, out);
+  unsigned long long *look = ptr<unsigned long long>(c->scan_tmp);
+  if (cudaMemsetAsync(look, 0, sizeof(unsigned long long) * (size_t)(nb + 1), c->stream) !=
+      cudaSuccess)
+    return AFD_ERR_CUDA;
+  k_scan<Tin, Tout><<<(unsigned)nb, kScanThreads, 0, c->stream>>>(in, n, out, look, nb,
+                                                                  ptr<int>(c->status));
   c->launches++;
   return cudaGetLastError() == cudaSuccess ? AFD_OK : AFD_ERR_CUDA;
 }
