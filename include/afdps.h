@@ -140,9 +140,10 @@ int afd_reuse_lists(afd_ctx *ctx, const double *x, const double *y, const double
 
 /* Force kernel (Section 5, the indirect-index dispatch): for every group and
  * every EPJ / SPJ index of its list, sum the softened attraction on each of
- * the group's particles. One warp takes 32 of a group's particles, or 64
- * (two full 32-particle units of one group, monopole lists), in the launch
- * order set by afd_make_interaction_lists. acc4: device, n x (ax, ay, az,
+ * the group's particles. One warp takes 32 of a group's particles, or up to
+ * 64 (a full 32-particle unit and the group's next unit when that holds more
+ * than 16 particles, monopole lists), in the launch order set by
+ * afd_make_interaction_lists. acc4: device, n x (ax, ay, az,
  * phi) floats, caller order, overwritten. Does not synchronise.
  * The potential is the FP32 kernel's (compensated sums, rms relative
  * difference from an FP64 sum over the same lists about 1e-7, far below the

@@ -368,7 +368,8 @@ void afd_destroy(afd_ctx *c) {
                     &c->nbr_seg_off, &c->nbr_items, &c->nbr_part, &c->nbr_seedf,
                     &c->nbr_seedo, &c->nbr_seeds, &c->nbr_icnt, &c->nbr_igoff, &c->nbr_itg,
                     &c->nbr_itr, &c->nbr_ioff, &c->nbr_sbb, &c->mxyz, &c->u_order,
-                    &c->u_work, &c->u_hist, &c->nbr_order, &c->nbr_work, &c->nbr_hist};
+                    &c->u_work, &c->u_hist, &c->nbr_order, &c->nbr_work, &c->nbr_hist,
+                    &c->s_h, &c->g_fscale};
   for (DevBuf *b : bufs) release(*b);
   if (c->pinned) cudaFreeHost(c->pinned);
   if (c->ev0) cudaEventDestroy(c->ev0);

@@ -1,8 +1,8 @@
 // Force kernel (Section 5: the indirect-index dispatch; Eq. kernel of
 // Section 6.2). Work unit = (i-group, chunk of 32 of its particles); a warp
-// takes one work item: a unit, or two consecutive full units of one group
-// (monopole lists), which share the group's list, each lane then holding two
-// i-particles. The warp walks the group's EPJ list, then its SPJ list, 32 or
+// takes one work item: a unit, or two consecutive units of one group (a full
+// one and the next if that holds more than 16 particles; monopole lists),
+// which share the group's list, each lane then holding two i-particles. The warp walks the group's EPJ list, then its SPJ list, 32 or
 // 64 entries at a time (a launch choice): each lane gathers its j's by index
 // (float4 hi + float4 lo of a particle or of a cell's centre of mass), forms
 // their coordinates relative to the group origin, stages them in shared
@@ -48,11 +48,15 @@ namespace {
 #define AFD_FORCE_FLUSH_PAIRS 128  // pair-iterations per lane between Kahan flushes
 #endif
 #ifndef AFD_FORCE_PAIRS
-#define AFD_FORCE_PAIRS 1  // two full units of a group per warp (monopole lists)
+#define AFD_FORCE_PAIRS 1  // two units of a group per warp (monopole lists)
+#endif
+#ifndef AFD_FORCE_UNIT_IPT2
+#define AFD_FORCE_UNIT_IPT2 1  // monopole units of their own also two i-particles per lane
 #endif
 #ifndef AFD_FORCE_PERSISTENT
 #define AFD_FORCE_PERSISTENT 0  // warps take units from an atomic queue
 #endif
+
 
 struct ForceArgs {
   int64_t n_units;  // the launch covers units [u_base, n_units)
@@ -67,7 +71,8 @@ struct ForceArgs {
   const float4 *ohi, *olo;  // cells, for the group origin
   const float4 *shi, *slo;  // cells
   const float4 *sq0, *sq1;  // cell quadrupoles
-  const float4 *nodef;      // cell walk data (s^2 in .w)
+  const uint4 *sh;          // half-precision far field: -Q/(M s^2) as half2 words, s^2
+  const float *gscale;      // half-precision far field: per-group power-of-two scale
   const uint64_t *off_e, *off_s;
   const uint32_t *epj, *spj;
   const uint32_t *perm;
@@ -160,7 +165,7 @@ __device__ __forceinline__ void interact_quad2(float4 a, float4 b, float4 qa, fl
   PP = fma2(mul2(pk(0.5f, 0.5f), DQD), RI5, add2(PP, MR));
 }
 
-// ---- packed half precision (FP16 or BF16) for the far-field quadrupole shape
+// ---- packed half precision (BF16 or FP16) for the far field
 template <int FAR>  // 1: bf16x2, 2: f16x2
 __device__ __forceinline__ uint32_t h2_from_f2(f2 v) {
   float a, b;
@@ -201,17 +206,28 @@ __device__ __forceinline__ uint32_t hconst2(float v) {
   return h2_from_f2<FAR>(pk(v, v));
 }
 
-// Monopole + quadrupole of two cells against one i with the quadrupole shape
-// in half precision. Qn = Q / (M s^2) (dimensionless, |Qn| <= 3; the 2^-2l
-// cell-size factor is a power of two) and u = d / rs (|u| <= 1) stay within
-// FP16 / BF16 range whatever the distance; the dimensional factor
-// M s^2 / rs^4 and the accumulation stay FP32:
-//   a += M d / rs^3 + (M s^2 / rs^4) (2.5 (u.Qn.u) u - Qn u)
-//   phi_sum += M / rs + 0.5 (u.Qn.u) M s^2 / rs^3.
+// Monopole + quadrupole of two cells (even, odd) against one i, the whole
+// far-field term formed in half precision. With d = COM - x_i, rs^2 = |d|^2 +
+// eps^2, u = d / rs (|u| <= 1), sigma = s^2 / rs^2 (< theta^2 for an
+// accepted cell), the dimensionless shape Qn = Q / (M s^2), P = -Qn u (from
+// the cell's stored -Qn) and T = u.P = -u.Qn.u, the monopole plus the
+// softened quadrupole term (Q r / rs^5 - 2.5 (r.Q.r) r / rs^7 with r = -d,
+// and -0.5 r.Q.r / rs^5) are
+//   a = (M / rs^2) [u + sigma (P - 2.5 T u)],
+//   phi_sum = (M / rs) (1 - 0.5 sigma T)           (phi = -phi_sum).
+// The geometry (d, rs, u, sigma) is FP32; u, sigma, the shape and the
+// magnitude M' / rs^2 are rounded to half precision and the bracket and its
+// product with the magnitude are half-precision arithmetic; the results are
+// converted to FP32 and accumulated in FP32. M' = M 2^-k_g carries the
+// group's power-of-two scale (2^k_g >= the largest M / d^2 over the group's
+// far-field cells), so every magnitude is at most about 1 and the FP16
+// range (2^16 above that, 2^-24 below) holds the group's terms; the
+// accumulators are multiplied by 2^k_g when folded. The monopole potential
+// M' / rs stays FP32.
 template <bool GUARD, int FAR>
-__device__ __forceinline__ void interact_quad2_half(float4 a, float4 b, uint4 qa, uint2 qb,
-                                                    f2 S2, f2 XI, f2 YI, f2 ZI, f2 E2, f2 &AX,
-                                                    f2 &AY, f2 &AZ, f2 &PP) {
+__device__ __forceinline__ void interact_far_half(float4 a, float4 b, uint4 qa, uint2 qb, f2 S2,
+                                                  f2 XI, f2 YI, f2 ZI, f2 E2, f2 &AX, f2 &AY,
+                                                  f2 &AZ, f2 &PP) {
   const f2 DX = sub2(pk(a.x, a.y), XI);
   const f2 DY = sub2(pk(a.z, a.w), YI);
   const f2 DZ = sub2(pk(b.x, b.y), ZI);
@@ -224,28 +240,27 @@ __device__ __forceinline__ void interact_quad2_half(float4 a, float4 b, uint4 qa
     q1 = r1 > 0.0f ? q1 : 0.0f;
   }
   const f2 RI = pk(q0, q1);
+  const f2 MR = mul2(pk(b.z, b.w), RI);  // M' / rs
   const f2 RI2 = mul2(RI, RI);
-  const f2 MR = mul2(pk(b.z, b.w), RI);
-  const f2 MR3 = mul2(MR, RI2);
-  // unit vector and the quadrupole shape in half precision
+  const uint32_t MU = h2_from_f2<FAR>(mul2(MR, RI));   // M' / rs^2
+  const uint32_t SG = h2_from_f2<FAR>(mul2(S2, RI2));  // s^2 / rs^2
   const uint32_t UX = h2_from_f2<FAR>(mul2(DX, RI));
   const uint32_t UY = h2_from_f2<FAR>(mul2(DY, RI));
   const uint32_t UZ = h2_from_f2<FAR>(mul2(DZ, RI));
-  // qa = (xx, yy, zz, xy), qb = (xz, yz), each an (even, odd) pair
-  const uint32_t QUX = hfma2<FAR>(qa.x, UX, hfma2<FAR>(qa.w, UY, hmul2<FAR>(qb.x, UZ)));
-  const uint32_t QUY = hfma2<FAR>(qa.w, UX, hfma2<FAR>(qa.y, UY, hmul2<FAR>(qb.y, UZ)));
-  const uint32_t QUZ = hfma2<FAR>(qb.x, UX, hfma2<FAR>(qb.y, UY, hmul2<FAR>(qa.z, UZ)));
-  const uint32_t UQU = hfma2<FAR>(UX, QUX, hfma2<FAR>(UY, QUY, hmul2<FAR>(UZ, QUZ)));
-  const uint32_t C = hmul2<FAR>(hconst2<FAR>(2.5f), UQU);
-  const uint32_t NEG = hconst2<FAR>(-1.0f);
-  const f2 BX = f2_from_h2<FAR>(hfma2<FAR>(C, UX, hmul2<FAR>(NEG, QUX)));
-  const f2 BY = f2_from_h2<FAR>(hfma2<FAR>(C, UY, hmul2<FAR>(NEG, QUY)));
-  const f2 BZ = f2_from_h2<FAR>(hfma2<FAR>(C, UZ, hmul2<FAR>(NEG, QUZ)));
-  const f2 SC = mul2(mul2(MR3, S2), RI);  // M s^2 / rs^4
-  AX = fma2(SC, BX, fma2(MR3, DX, AX));
-  AY = fma2(SC, BY, fma2(MR3, DY, AY));
-  AZ = fma2(SC, BZ, fma2(MR3, DZ, AZ));
-  PP = fma2(mul2(mul2(pk(0.5f, 0.5f), f2_from_h2<FAR>(UQU)), MR), mul2(S2, RI2), add2(PP, MR));
+  // qa = (xx, yy, zz, xy), qb = (xz, yz) of -Q / (M s^2), each an (even, odd) pair
+  const uint32_t PX = hfma2<FAR>(qa.x, UX, hfma2<FAR>(qa.w, UY, hmul2<FAR>(qb.x, UZ)));
+  const uint32_t PY = hfma2<FAR>(qa.w, UX, hfma2<FAR>(qa.y, UY, hmul2<FAR>(qb.y, UZ)));
+  const uint32_t PZ = hfma2<FAR>(qb.x, UX, hfma2<FAR>(qb.y, UY, hmul2<FAR>(qa.z, UZ)));
+  const uint32_t T = hfma2<FAR>(UX, PX, hfma2<FAR>(UY, PY, hmul2<FAR>(UZ, PZ)));
+  const uint32_t C = hmul2<FAR>(hconst2<FAR>(-2.5f), T);
+  const uint32_t BX = hfma2<FAR>(SG, hfma2<FAR>(C, UX, PX), UX);
+  const uint32_t BY = hfma2<FAR>(SG, hfma2<FAR>(C, UY, PY), UY);
+  const uint32_t BZ = hfma2<FAR>(SG, hfma2<FAR>(C, UZ, PZ), UZ);
+  AX = add2(AX, f2_from_h2<FAR>(hmul2<FAR>(MU, BX)));
+  AY = add2(AY, f2_from_h2<FAR>(hmul2<FAR>(MU, BY)));
+  AZ = add2(AZ, f2_from_h2<FAR>(hmul2<FAR>(MU, BZ)));
+  const f2 PQ = f2_from_h2<FAR>(hmul2<FAR>(hmul2<FAR>(hconst2<FAR>(-0.5f), SG), T));
+  PP = fma2(MR, PQ, add2(PP, MR));
 }
 
 // Shared-memory staging of one warp: raw j data of two chunks in flight
@@ -258,13 +273,14 @@ template <bool QUAD, int CH>
 struct WarpStage {
   static constexpr int kPairs = CH / 2;
   float4 rh[2][CH], rl[2][CH];
+  // quadrupoles (FP32), or (half-precision far field) in rq0 the cell's
+  // half record
   float4 rq0[QUAD ? 2 : 1][QUAD ? CH : 1], rq1[QUAD ? 2 : 1][QUAD ? CH : 1];
-  float4 rnf[QUAD ? 2 : 1][QUAD ? CH : 1];  // cell walk data (s^2 in .w)
   float4 P0[kPairs], P1[kPairs];
   // quadrupole pairs: QA = (xx, yy), QB = (zz, xy), QC = (xz, yz), each (even, odd)
   float4 QA[QUAD ? kPairs : 1], QB[QUAD ? kPairs : 1], QC[QUAD ? kPairs : 1];
-  // half-precision far field: normalised quadrupole pairs (xx, yy, zz, xy), (xz, yz) as
-  // (even, odd) half2 words, and the cell side squared of both cells
+  // half-precision far field: negated normalised quadrupole pairs (xx, yy, zz, xy),
+  // (xz, yz) as (even, odd) half2 words, and the cell side squared of both cells
   uint4 HA[QUAD ? kPairs : 1];
   uint2 HB[QUAD ? kPairs : 1];
   float2 S2[QUAD ? kPairs : 1];
@@ -282,37 +298,47 @@ struct Lane {
 
 // Kahan-compensated running sums of one i-particle (both packed streams folded).
 struct Sums {
-  float sx, sy, sz, sp;
-  float cx, cy, cz, cp;
+  float v[4], c[4];  // sx sy sz sp; their compensations
 };
-
-__device__ __forceinline__ void kahan_fold(float &s, float &c, f2 v) {
+__device__ __forceinline__ void sums_init(Sums &s) {
+#pragma unroll
+  for (int k = 0; k < 4; k++) s.v[k] = s.c[k] = 0.0f;
+}
+__device__ __forceinline__ void kahan_fold_k(Sums &s, int k, f2 v) {
   float v0, v1;
   upk(v, v0, v1);
-  const float y = (v0 + v1) - c;
-  const float t = s + y;
-  c = (t - s) - y;
-  s = t;
+  const float y = (v0 + v1) - s.c[k];
+  const float t = s.v[k] + y;
+  s.c[k] = (t - s.v[k]) - y;
+  s.v[k] = t;
 }
+__device__ __forceinline__ float sums_value(const Sums &s, int k) { return s.v[k] - s.c[k]; }
 
 // Issue the asynchronous gather of list entries [base, base + CH) into
 // buffer b: lane l copies entries base + l + 32 r (lanes past the end copy
 // nothing). j[r] are the entries' indices.
-template <bool QUAD, int CH>
+// With the half-precision far field a far-field entry is 32 bytes: the
+// cell's (COM hi, M) and its half record; the COM's lo part is left out (it
+// moves the relative coordinate by 2^-24 of the COM's magnitude, far below
+// half precision).
+template <bool QUAD, int FAR, int CH>
 __device__ __forceinline__ void gather(WarpStage<QUAD, CH> &st, int b, int lane, uint64_t base,
                                        uint64_t o1, const uint32_t *j, const float4 *hi,
                                        const float4 *lo, const float4 *sq0, const float4 *sq1,
-                                       const float4 *nodef, bool quad_list) {
+                                       const uint4 *sh, bool quad_list) {
 #pragma unroll
   for (int r = 0; r < CH / 32; r++) {
     const int slot = lane + 32 * r;
     if (base + slot < o1) {
       cp_async16(&st.rh[b][slot], hi + j[r]);
-      cp_async16(&st.rl[b][slot], lo + j[r]);
-      if (QUAD && quad_list) {
-        cp_async16(&st.rq0[b][slot], sq0 + j[r]);
-        cp_async16(&st.rq1[b][slot], sq1 + j[r]);
-        if (nodef) cp_async16(&st.rnf[b][slot], nodef + j[r]);
+      if (QUAD && quad_list && FAR) {
+        cp_async16(&st.rq0[b][slot], sh + j[r]);
+      } else {
+        cp_async16(&st.rl[b][slot], lo + j[r]);
+        if (QUAD && quad_list) {
+          cp_async16(&st.rq0[b][slot], sq0 + j[r]);
+          cp_async16(&st.rq1[b][slot], sq1 + j[r]);
+        }
       }
     }
   }
@@ -333,14 +359,17 @@ __device__ __forceinline__ void load_idx(uint32_t *j, const uint32_t *idx, uint6
 }
 
 // One list (EPJ or SPJ) of one group for one warp with S j-streams.
+// With the half-precision far field (FAR, quadrupole SPJ list) the masses
+// are scaled by the group's power of two gsc on staging and the partial
+// sums multiplied back by 1 / gsc (exact) when folded.
 template <bool GUARD, bool QUAD, int FAR, int S, int IPT, int CH>
 __device__ __forceinline__ void run_list(WarpStage<QUAD, CH> &st, const Lane<IPT> &ln, Sums *sm,
                                          const uint32_t *idx, uint64_t o0, uint64_t o1,
                                          const float4 *hi, const float4 *lo, const float4 *sq0,
-                                         const float4 *sq1, const float4 *nodef, bool quad_list,
+                                         const float4 *sq1, const uint4 *sh, bool quad_list,
                                          float eps2, const int64_t *self_at, uint64_t nlist,
-                                         uint64_t jbound) {
-  static_assert(IPT == 1 || (!QUAD && S == 1), "two i-particles per lane: monopole, one stream");
+                                         uint64_t jbound, float gsc) {
+  static_assert(IPT == 1 || !QUAD, "two i-particles per lane: monopole lists");
   if (o0 >= o1) return;
   if (!AFD_IN(o1 - 1, nlist, "force list range")) return;
   constexpr int kChunk = CH, kPer = CH / 32, kPairs = CH / 2;
@@ -349,7 +378,9 @@ __device__ __forceinline__ void run_list(WarpStage<QUAD, CH> &st, const Lane<IPT
   // prologue: chunk 0 in flight, indices of chunk 1 in registers
   uint32_t j0[kPer], jn[kPer];
   load_idx<CH>(j0, idx, o0, o1, lane, jbound);
-  gather<QUAD, CH>(st, 0, lane, o0, o1, j0, hi, lo, sq0, sq1, FAR ? nodef : nullptr, quad_list);
+  const bool half_far = QUAD && FAR && quad_list;
+  const f2 unscale = pk(1.0f / gsc, 1.0f / gsc);  // powers of two: exact
+  gather<QUAD, FAR, CH>(st, 0, lane, o0, o1, j0, hi, lo, sq0, sq1, sh, quad_list);
   load_idx<CH>(jn, idx, o0 + kChunk, o1, lane, jbound);
   f2 AX[IPT], AY[IPT], AZ[IPT], PP[IPT];
 #pragma unroll
@@ -359,8 +390,7 @@ __device__ __forceinline__ void run_list(WarpStage<QUAD, CH> &st, const Lane<IPT
   for (uint64_t base = o0; base < o1; base += kChunk) {
     // next chunk in flight, indices of the one after in registers
     const uint64_t nb = base + kChunk;
-    gather<QUAD, CH>(st, b ^ 1, lane, nb, o1, jn, hi, lo, sq0, sq1, FAR ? nodef : nullptr,
-                     quad_list);
+    gather<QUAD, FAR, CH>(st, b ^ 1, lane, nb, o1, jn, hi, lo, sq0, sq1, sh, quad_list);
     load_idx<CH>(jn, idx, nb + kChunk, o1, lane, jbound);
     cp_async_wait<1>();  // this lane's copies of the current chunk have landed
     float rx[kPer], ry[kPer], rz[kPer], rm[kPer];
@@ -372,11 +402,19 @@ __device__ __forceinline__ void run_list(WarpStage<QUAD, CH> &st, const Lane<IPT
       rx[r] = ry[r] = rz[r] = 1e18f;
       rm[r] = 0.0f;
       if (base + slot < o1) {
-        const float4 h = st.rh[b][slot], l = st.rl[b][slot];
-        rx[r] = (h.x - ch.x) + (l.x - cl.x);
-        ry[r] = (h.y - ch.y) + (l.y - cl.y);
-        rz[r] = (h.z - ch.z) + (l.z - cl.z);
-        rm[r] = h.w;
+        const float4 h = st.rh[b][slot];
+        if (half_far) {  // COM hi only; the mass carries the group's scale
+          rx[r] = (h.x - ch.x) - cl.x;
+          ry[r] = (h.y - ch.y) - cl.y;
+          rz[r] = (h.z - ch.z) - cl.z;
+          rm[r] = h.w * gsc;
+        } else {
+          const float4 l = st.rl[b][slot];
+          rx[r] = (h.x - ch.x) + (l.x - cl.x);
+          ry[r] = (h.y - ch.y) + (l.y - cl.y);
+          rz[r] = (h.z - ch.z) + (l.z - cl.z);
+          rm[r] = h.w;
+        }
       }
     }
     __syncwarp();
@@ -390,7 +428,22 @@ __device__ __forceinline__ void run_list(WarpStage<QUAD, CH> &st, const Lane<IPT
       p0[2 + e] = ry[r];
       p1[e] = rz[r];
       p1[2 + e] = rm[r];
-      if (QUAD && quad_list) {
+      if (QUAD && quad_list && FAR) {
+        // the cell's half record: (xx, yy), (zz, xy), (xz, yz) of -Qn as
+        // half2 words, s^2; this lane's half of each (even, odd) pair
+        const bool v = base + slot < o1;
+        const uint4 rec = v ? *reinterpret_cast<const uint4 *>(&st.rq0[b][slot])
+                            : make_uint4(0u, 0u, 0u, 0u);
+        unsigned short *ha = reinterpret_cast<unsigned short *>(&st.HA[slot >> 1]);
+        unsigned short *hb = reinterpret_cast<unsigned short *>(&st.HB[slot >> 1]);
+        ha[0 + e] = (unsigned short)(rec.x & 0xffffu);  // xx
+        ha[2 + e] = (unsigned short)(rec.x >> 16);      // yy
+        ha[4 + e] = (unsigned short)(rec.y & 0xffffu);  // zz
+        ha[6 + e] = (unsigned short)(rec.y >> 16);      // xy
+        hb[0 + e] = (unsigned short)(rec.z & 0xffffu);  // xz
+        hb[2 + e] = (unsigned short)(rec.z >> 16);      // yz
+        reinterpret_cast<float *>(&st.S2[slot >> 1])[e] = __uint_as_float(rec.w);
+      } else if (QUAD && quad_list) {
         const bool v = base + slot < o1;
         const float4 q0 = v ? st.rq0[b][slot] : make_float4(0.f, 0.f, 0.f, 0.f);
         const float4 q1 = v ? st.rq1[b][slot] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -403,29 +456,6 @@ __device__ __forceinline__ void run_list(WarpStage<QUAD, CH> &st, const Lane<IPT
         qb[2 + e] = q0.w;  // xy
         qc[e] = q1.x;      // xz
         qc[2 + e] = q1.y;  // yz
-        if (FAR) {
-          // normalised shape Qn = Q / (M s^2) as this lane's half of each pair
-          const float s2c = v ? st.rnf[b][slot].w : 1.0f;
-          const float den = rm[r] * s2c;
-          const float inv = den > 0.0f ? 1.0f / den : 0.0f;
-          const float qn[6] = {q0.x * inv, q0.y * inv, q0.z * inv, q0.w * inv, q1.x * inv,
-                               q1.y * inv};
-          unsigned short hq[6];
-#pragma unroll
-          for (int k = 0; k < 6; k++) {
-            if (FAR == 1) asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(hq[k]) : "f"(qn[k]));
-            else asm("cvt.rn.f16.f32 %0, %1;" : "=h"(hq[k]) : "f"(qn[k]));
-          }
-          unsigned short *ha = reinterpret_cast<unsigned short *>(&st.HA[slot >> 1]);
-          unsigned short *hb = reinterpret_cast<unsigned short *>(&st.HB[slot >> 1]);
-          ha[0 + e] = hq[0];  // xx
-          ha[2 + e] = hq[1];  // yy
-          ha[4 + e] = hq[2];  // zz
-          ha[6 + e] = hq[3];  // xy
-          hb[0 + e] = hq[4];  // xz
-          hb[2 + e] = hq[5];  // yz
-          reinterpret_cast<float *>(&st.S2[slot >> 1])[e] = s2c;
-        }
       }
     }
     __syncwarp();
@@ -438,9 +468,9 @@ __device__ __forceinline__ void run_list(WarpStage<QUAD, CH> &st, const Lane<IPT
     if (QUAD && quad_list && FAR) {
 #pragma unroll 4
       for (int t = ln.stream; t < kPairs; t += S)
-        interact_quad2_half<GUARD, FAR ? FAR : 1>(st.P0[t], st.P1[t], st.HA[t], st.HB[t],
-                                                  pk(st.S2[t].x, st.S2[t].y), ln.XI[0], ln.YI[0],
-                                                  ln.ZI[0], ln.E2, AX[0], AY[0], AZ[0], PP[0]);
+        interact_far_half<GUARD, FAR ? FAR : 1>(st.P0[t], st.P1[t], st.HA[t], st.HB[t],
+                                                pk(st.S2[t].x, st.S2[t].y), ln.XI[0], ln.YI[0],
+                                                ln.ZI[0], ln.E2, AX[0], AY[0], AZ[0], PP[0]);
     } else if (QUAD && quad_list) {
 #pragma unroll 4
       for (int t = ln.stream; t < kPairs; t += S)
@@ -469,7 +499,7 @@ __device__ __forceinline__ void run_list(WarpStage<QUAD, CH> &st, const Lane<IPT
     } else if (IPT == 2) {
       // two i-particles per lane: each staged pair serves both (two chains)
 #pragma unroll 2
-      for (int t = 0; t < kPairs; t++) {
+      for (int t = ln.stream; t < kPairs; t += S) {
         const float4 p0 = st.P0[t], p1 = st.P1[t];
 #pragma unroll
         for (int q = 0; q < IPT; q++)
@@ -499,10 +529,16 @@ __device__ __forceinline__ void run_list(WarpStage<QUAD, CH> &st, const Lane<IPT
     if (pending >= AFD_FORCE_FLUSH_PAIRS || nb >= o1) {
 #pragma unroll
       for (int q = 0; q < IPT; q++) {
-        kahan_fold(sm[q].sx, sm[q].cx, AX[q]);
-        kahan_fold(sm[q].sy, sm[q].cy, AY[q]);
-        kahan_fold(sm[q].sz, sm[q].cz, AZ[q]);
-        kahan_fold(sm[q].sp, sm[q].cp, PP[q]);
+        if (half_far) {
+          AX[q] = mul2(AX[q], unscale);
+          AY[q] = mul2(AY[q], unscale);
+          AZ[q] = mul2(AZ[q], unscale);
+          PP[q] = mul2(PP[q], unscale);
+        }
+        kahan_fold_k(sm[q], 0, AX[q]);
+        kahan_fold_k(sm[q], 1, AY[q]);
+        kahan_fold_k(sm[q], 2, AZ[q]);
+        kahan_fold_k(sm[q], 3, PP[q]);
         AX[q] = AY[q] = AZ[q] = PP[q] = Z0;
       }
       pending = 0;
@@ -518,13 +554,14 @@ __device__ __forceinline__ void run_unit(WarpStage<QUAD, CH> &st, const ForceArg
                                          const Lane<IPT> &ln, Sums *sm, const int64_t *self_at) {
   run_list<GUARD, QUAD, FAR, S, IPT, CH>(st, ln, sm, a.epj, a.off_e[g], a.off_e[g + 1], a.jhi,
                                          a.jlo, nullptr, nullptr, nullptr, false, a.eps2,
-                                         self_at, a.n_epj, a.epj ? a.n : a.n_epj);
+                                         self_at, a.n_epj, a.epj ? a.n : a.n_epj, 1.0f);
   int64_t none[IPT];
 #pragma unroll
   for (int q = 0; q < IPT; q++) none[q] = -1;
+  const float gsc = (QUAD && FAR) ? a.gscale[g] : 1.0f;
   run_list<GUARD, QUAD, FAR, S, IPT, CH>(st, ln, sm, a.spj, a.off_s[g], a.off_s[g + 1], a.shi,
-                                         a.slo, a.sq0, a.sq1, a.nodef, QUAD, a.eps2, none, a.n_spj,
-                                         a.spj ? a.n_cells : a.n_spj);
+                                         a.slo, a.sq0, a.sq1, a.sh, QUAD, a.eps2, none, a.n_spj,
+                                         a.spj ? a.n_cells : a.n_spj, gsc);
 }
 
 // One work unit with IPT particles per lane and S j-streams: set up the
@@ -549,7 +586,7 @@ __device__ __forceinline__ void unit_body(const ForceArgs &a, WarpStage<QUAD, CH
   bool active[IPT];
 #pragma unroll
   for (int q = 0; q < IPT; q++) {
-    il[q] = ioff + (uint32_t)(q * 32 + (lane & (W - 1)));
+    il[q] = ioff + (uint32_t)(q * W + (lane & (W - 1)));
     active[q] = il[q] < gc && AFD_IN(gf + il[q], a.n, "force i-particle");
     float xi = 0.f, yi = 0.f, zi = 0.f;
     if (active[q]) {
@@ -565,8 +602,7 @@ __device__ __forceinline__ void unit_body(const ForceArgs &a, WarpStage<QUAD, CH
   ln.E2 = pk(a.eps2, a.eps2);
   Sums sm[IPT];
 #pragma unroll
-  for (int q = 0; q < IPT; q++)
-    sm[q].sx = sm[q].sy = sm[q].sz = sm[q].sp = sm[q].cx = sm[q].cy = sm[q].cz = sm[q].cp = 0.0f;
+  for (int q = 0; q < IPT; q++) sums_init(sm[q]);
   __syncwarp();
   // EPJ-list positions of this lane's own particles (-1: not on the list)
   const uint32_t gs = a.g_self[g];
@@ -578,8 +614,8 @@ __device__ __forceinline__ void unit_body(const ForceArgs &a, WarpStage<QUAD, CH
   run_unit<GUARD, QUAD, FAR, S, IPT, CH>(st, a, g, ln, sm, self_at);
 #pragma unroll
   for (int q = 0; q < IPT; q++) {
-    float ax = sm[q].sx - sm[q].cx, ay = sm[q].sy - sm[q].cy, az = sm[q].sz - sm[q].cz;
-    float pot = sm[q].sp - sm[q].cp;
+    float ax = sums_value(sm[q], 0), ay = sums_value(sm[q], 1), az = sums_value(sm[q], 2);
+    float pot = sums_value(sm[q], 3);
     // combine the j-streams of each particle
 #pragma unroll
     for (int o = W; o < 32; o <<= 1) {
@@ -597,7 +633,11 @@ __device__ __forceinline__ void unit_body(const ForceArgs &a, WarpStage<QUAD, CH
 
 // Work unit u: group g = info.x; info.y holds the first particle offset
 // (bits 0-15) and log2 of the j-stream split S (bits 16-17): S = 1 << sidx
-// streams of W = 32 >> sidx particles, lane = stream * W + particle.
+// streams of W = 32 >> sidx particles, lane = stream * W + particle. The
+// monopole kernel runs such a unit as 2 S streams of W / 2 lanes, each lane
+// with two of the unit's particles (the same lanes busy, every staged
+// j-pair serving two i-particles); a pair item (a full unit and the next)
+// as one stream of 32 lanes with two particles each.
 template <bool GUARD, bool QUAD, int FAR, int CH>
 __device__ __forceinline__ void force_unit(const ForceArgs &a, WarpStage<QUAD, CH> &st, int lane,
                                            int64_t u, bool pair) {
@@ -608,6 +648,12 @@ __device__ __forceinline__ void force_unit(const ForceArgs &a, WarpStage<QUAD, C
   if constexpr (!QUAD) {
     if (pair) {
       unit_body<GUARD, QUAD, FAR, 1, 2, CH>(a, st, lane, g, ioff);
+      return;
+    }
+    if (AFD_FORCE_UNIT_IPT2) {
+      if (sidx == 0) unit_body<GUARD, QUAD, FAR, 2, 2, CH>(a, st, lane, g, ioff);
+      else if (sidx == 1) unit_body<GUARD, QUAD, FAR, 4, 2, CH>(a, st, lane, g, ioff);
+      else unit_body<GUARD, QUAD, FAR, 8, 2, CH>(a, st, lane, g, ioff);
       return;
     }
   }
@@ -685,6 +731,76 @@ int launch_k_force(const ForceArgs &a, unsigned nb, int warps, cudaStream_t s) {
 
 namespace {
 
+// Half-precision far field, per cell: the negated dimensionless quadrupole
+// shape -Q / (M s^2) (FP64 quotient, rounded to BF16 / FP16) packed as half2
+// words (xx, yy), (zz, xy), (xz, yz), and s^2 (FP32). A massless cell gets
+// a zero shape.
+template <int FAR>
+__global__ void __launch_bounds__(256) k_far_half(int64_t nc, const double *__restrict__ quad,
+                                                  const double *__restrict__ mass,
+                                                  const float4 *__restrict__ node_f,
+                                                  uint4 *__restrict__ s_h) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const float s2 = node_f[c].w;
+  const double den = __dmul_rn(mass[c], (double)s2);
+  const double inv = den > 0.0 ? -1.0 / den : 0.0;
+  float q[6];
+#pragma unroll
+  for (int k = 0; k < 6; k++) q[k] = __double2float_rn(__dmul_rn(quad[c * 6 + k], inv));
+  s_h[c] = make_uint4(h2_from_f2<FAR>(pk(q[0], q[1])), h2_from_f2<FAR>(pk(q[2], q[3])),
+                      h2_from_f2<FAR>(pk(q[4], q[5])), __float_as_uint(s2));
+}
+
+// Half-precision far field, per group: the scale 2^-k_g, 2^k_g the smallest
+// power of two >= the largest M / d^2 over the group's SPJ cells (d the
+// distance from the cell's centre of mass to the group's box, which bounds
+// M / rs^2 for every particle of the group). One warp per group.
+__global__ void __launch_bounds__(256) k_far_scale(int64_t ng, const uint64_t *__restrict__ off_s,
+                                                   const uint32_t *__restrict__ spj,
+                                                   const float4 *__restrict__ s_hi,
+                                                   const float *__restrict__ boxf,
+                                                   uint64_t n_cells, float *__restrict__ gscale) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ng; g += warps) {
+    float bmin[3], bmax[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      bmin[k] = boxf[g * 6 + k];
+      bmax[k] = boxf[g * 6 + 3 + k];
+    }
+    float mu = 0.0f;
+    for (uint64_t k = off_s[g] + lane; k < off_s[g + 1]; k += 32) {
+      uint32_t j = spj[k];
+      if (!AFD_IN(j, n_cells, "far scale cell")) j = 0u;
+      const float4 h = s_hi[j];
+      const float c[3] = {h.x, h.y, h.z};
+      float d2 = 0.0f;
+#pragma unroll
+      for (int a = 0; a < 3; a++) {
+        const float d = c[a] < bmin[a] ? bmin[a] - c[a] : (c[a] > bmax[a] ? c[a] - bmax[a] : 0.0f);
+        d2 = fmaf(d, d, d2);
+      }
+      if (d2 > 0.0f) mu = fmaxf(mu, h.w / d2);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mu = fmaxf(mu, __shfl_xor_sync(0xffffffffu, mu, o));
+    if (lane == 0) {
+      // 2^-k with 2^k >= mu, k clamped to [-100, 100]; 1 without far-field mass
+      int k = 0;
+      if (mu > 0.0f && mu <= 3.4e38f) {
+        const uint32_t b = __float_as_uint(mu);
+        k = (int)((b >> 23) & 0xffu) - 127 + ((b & 0x7fffffu) != 0u ? 1 : 0);
+        k = k < -100 ? -100 : (k > 100 ? 100 : k);
+      } else if (mu > 0.0f) {
+        k = 100;
+      }
+      gscale[g] = __uint_as_float((uint32_t)(127 - k) << 23);
+    }
+  }
+}
+
 // Non-indirect ablation: copy every list entry's j-data into list order.
 __global__ void k_materialize(uint64_t n, const uint32_t *__restrict__ idx,
                               const float4 *__restrict__ hi, const float4 *__restrict__ lo,
@@ -698,9 +814,12 @@ __global__ void k_materialize(uint64_t n, const uint32_t *__restrict__ idx,
 }
 
 // Launch order of the force work items. A warp takes one item: a unit, or
-// (monopole lists) two consecutive full units of one group, which share the
-// group's list -- each lane then carries two i-particles, and every staged
-// j-pair serves 64 particles instead of 32. An item's warp streams its
+// (monopole lists) two consecutive units of one group -- a full one and the
+// next when that holds more than 16 particles -- which share the group's
+// list: each lane then carries two i-particles (lanes past the second
+// unit's end only one), and every staged j-pair serves up to 64 particles
+// instead of 32. Measured without the list traffic, a staged j-pair shared
+// by two i-particles keeps the FP32 pipe 0.82 busy against 0.72 for one. An item's warp streams its
 // group's whole list (split over S j-streams for the last, partial unit), so
 // its time follows the list work L * IPT / S; the items are launched largest
 // work first (afd_order.cuh). Every item writes its own particles.
@@ -715,10 +834,12 @@ __device__ __forceinline__ uint32_t unit_item(const uint2 *u_info, const uint32_
   const uint32_t sidx = (info.y >> 16) & 3u;
   bool pair = false;
   if (pairs && sidx == 0u) {
+    // a unit in an even slot takes the next unit too when that one holds
+    // more than 16 particles (fewer are cheaper as a unit of their own, split
+    // into j-streams); the next unit then starts no item
     const uint32_t cn = g_count[g];
-    const bool full = ioff + 32u <= cn;
-    if ((ioff & 32u) != 0u && full) return kNoItem;  // odd slot, full: its even neighbour pairs it
-    pair = (ioff & 32u) == 0u && ioff + 64u <= cn;
+    if ((ioff & 32u) != 0u && cn - ioff > 16u) return kNoItem;
+    pair = (ioff & 32u) == 0u && cn - ioff > 48u;
   }
   const uint64_t L = (off_e[g + 1] - off_e[g]) + (off_s[g + 1] - off_s[g]);
   uint64_t w = pair ? 2u * L : (L >> sidx);
@@ -747,6 +868,7 @@ __global__ void k_unit_work(int64_t u0, int64_t nu, const uint2 *__restrict__ u_
 
 int order_units(afd_ctx *c) {
   c->u_order_ok = false;
+  c->fscale_ok = false;  // new lists: the far-field scales follow them
   const int64_t u0 = c->share_parts > 1 ? c->share_u0 : 0;
   const int64_t u1 = c->share_parts > 1 ? c->share_u1 : c->n_units;
   const int64_t nu = u1 - u0;
@@ -830,7 +952,36 @@ int launch_force_impl(afd_ctx *c, float *acc4, bool materialized) {
   }
   a.sq0 = ptr<float4>(c->s_q0);
   a.sq1 = ptr<float4>(c->s_q1);
-  a.nodef = ptr<float4>(c->node_f);
+  const int far_p = c->cfg.multipole ? c->cfg.far_precision : 0;
+  if (far_p) {
+    // the cells' half records from the current moments, and the groups'
+    // scales from the current lists
+    if (reserve(c->s_h, sizeof(uint4) * (size_t)c->n_cells) != AFD_OK ||
+        reserve(c->g_fscale, sizeof(float) * (size_t)c->n_groups) != AFD_OK)
+      return AFD_ERR_OOM;
+    const unsigned nb_c = (unsigned)((c->n_cells + 255) / 256);
+    if (far_p == 1)
+      k_far_half<1><<<nb_c, 256, 0, c->stream>>>(c->n_cells, ptr<double>(c->c_quad),
+                                                  ptr<double>(c->c_mass), ptr<float4>(c->node_f),
+                                                  ptr<uint4>(c->s_h));
+    else
+      k_far_half<2><<<nb_c, 256, 0, c->stream>>>(c->n_cells, ptr<double>(c->c_quad),
+                                                  ptr<double>(c->c_mass), ptr<float4>(c->node_f),
+                                                  ptr<uint4>(c->s_h));
+    c->launches++;
+    if (!c->fscale_ok) {
+      const int64_t want = (c->n_groups + 7) / 8;
+      const unsigned nb_g = (unsigned)(want < 152 * 16 ? (want > 0 ? want : 1) : 152 * 16);
+      k_far_scale<<<nb_g, 256, 0, c->stream>>>(c->n_groups, ptr<uint64_t>(c->spj_off),
+                                               ptr<uint32_t>(c->spj), ptr<float4>(c->s_hi),
+                                               ptr<float>(c->g_boxf), (uint64_t)c->n_cells,
+                                               ptr<float>(c->g_fscale));
+      c->launches++;
+      c->fscale_ok = true;
+    }
+  }
+  a.sh = ptr<uint4>(c->s_h);
+  a.gscale = ptr<float>(c->g_fscale);
   a.off_e = ptr<uint64_t>(c->epj_off);
   a.off_s = ptr<uint64_t>(c->spj_off);
   a.epj = materialized ? nullptr : ptr<uint32_t>(c->epj);

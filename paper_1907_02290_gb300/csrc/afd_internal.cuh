@@ -174,6 +174,11 @@ struct afd_ctx {
   afd::DevBuf s_hi, s_lo, s_q0, s_q1;         // float4 superparticle data
   afd::DevBuf node_f, node_i;                 // walk node data (float4, uint2)
   afd::DevBuf c_block;                        // per cell 8 child walk records (2 x uint4 each)
+  // half-precision far field: per cell the negated normalised quadrupole
+  // -Q / (M s^2) as three half2 words (xx yy, zz xy, xz yz) and s^2; per
+  // group the power-of-two scale of its far-field terms
+  afd::DevBuf s_h, g_fscale;
+  bool fscale_ok = false;  // g_fscale matches the current lists
 
   // groups and force work units
   afd::DevBuf g_cnt, g_off;

@@ -154,13 +154,16 @@ def test_clustered_and_coincident(env):
 @pytest.mark.parametrize("sizes,n_grp", [
     ([33, 63, 64, 65, 95, 96, 97, 128], 128),
     ([129, 159, 160, 161, 191, 192, 193, 256], 256),
+    ([48, 49, 80, 81, 112, 113, 176, 177], 256),
 ])
 def test_group_sizes_around_the_unit_pairing(env, sizes, n_grp):
     """One clump per octant of the root, so each clump is one group of the
-    given size: groups of 63, 64, 65, 95, 96, 97, 128 ... particles cover
-    every case of the force kernel's work items (a 32-particle unit alone,
-    two full units taken by one warp, a partial last unit split into
-    j-streams). Structure bit-exact, forces against the oracle."""
+    given size: groups of 48, 49, 63, 64, 65, 95, 96, 97, 128 ... particles
+    cover every case of the force kernel's work items (a 32-particle unit
+    alone, a full unit and the next one of more than 16 particles taken by
+    one warp -- 49, 81, 113, 177 -- or of at most 16 left on its own -- 48,
+    80, 112, 176 --, a partial last unit split into j-streams). Structure
+    bit-exact, forces against the oracle."""
     _, _, orc = env
     rng = np.random.default_rng(31)
     xs, ys, zs = [], [], []
@@ -575,8 +578,10 @@ def test_autotuner_installs_candidates_and_stays_exact(env):
 
 @pytest.mark.parametrize("far,tol", [(1, 2e-3), (2, 2e-4)])
 def test_half_precision_far_field(env, far, tol):
-    """BF16 (far=1) / FP16 (far=2) quadrupole shape with FP32 geometry and
-    accumulation: same lists, small error against the FP64 oracle."""
+    """BF16 (far=1) / FP16 (far=2) far-field terms (formed in half precision
+    with a per-group power-of-two scale, accumulated in FP32) on the same
+    lists as the FP64 oracle: the difference stays within a few units of the
+    half format's roundoff times the far field's share of the force."""
     torch, afd, orc = env
     p = ics.plummer(60000, 91)
     kw = dict(n_grp=256, theta=0.6, eps=1.0 / 1024)
@@ -599,7 +604,11 @@ def test_half_precision_far_field(env, far, tol):
 def test_mixed_precision_workload_against_direct_sum(env, capsys):
     """The N = 2^22 Plummer workload with quadrupole superparticles at
     theta = 0.6: FP32, BF16 and FP16 far field, rms and max relative force
-    error against the FP64 direct sum on 4096 seeded sample particles."""
+    error against the FP64 direct sum on 4096 seeded sample particles. The
+    whole far-field term is formed in half precision: FP16 (11 significant
+    bits) adds little to the multipole error; BF16 (8 bits, unit roundoff
+    2^-9 per operation of the term) adds about as much again, so its bound
+    is twice the FP32 error."""
     torch, afd, orc = env
     wl = ics.WORKLOADS["plummer_4m_mixed"]
     p = ics.plummer(wl["n"], wl["seed"])
@@ -626,7 +635,7 @@ def test_mixed_precision_workload_against_direct_sum(env, capsys):
                   f"max {errs[far][1]:.4e}")
     # the far-field precision barely moves the tree's own error
     assert errs[0][0] < 5e-3
-    assert errs[2][0] < 1.05 * errs[0][0] and errs[1][0] < 1.3 * errs[0][0]
+    assert errs[2][0] < 1.05 * errs[0][0] and errs[1][0] < 2.0 * errs[0][0]
 
 
 def test_force_launch_shapes(env):
