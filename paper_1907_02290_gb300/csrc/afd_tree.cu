@@ -698,99 +698,17 @@ __device__ void leaf_quad(const MomArgs &a, uint32_t c) {
   a.s_q1[c] = make_float4(__double2float_rn(Q[4]), __double2float_rn(Q[5]), 0.0f, 0.0f);
 }
 
-__device__ void internal_quad(const MomArgs &a, uint32_t c) {
-  const double *g = &a.com[(size_t)c * 3];
-  double Q[6] = {0, 0, 0, 0, 0, 0};
-  for (int o = 0; o < 8; o++) {
-    const uint32_t cc = __ldg(&a.child[(size_t)c * 8 + o]);
-    if (cc == kNone) continue;
-    const double D0 = __dsub_rn(__ldcg(&a.com[(size_t)cc * 3 + 0]), g[0]);
-    const double D1 = __dsub_rn(__ldcg(&a.com[(size_t)cc * 3 + 1]), g[1]);
-    const double D2 = __dsub_rn(__ldcg(&a.com[(size_t)cc * 3 + 2]), g[2]);
-    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(D0, D0), __dmul_rn(D1, D1)), __dmul_rn(D2, D2));
-    const double mc = __ldcg(&a.mass[cc]);
-    double qc[6];
-    for (int q = 0; q < 6; q++) qc[q] = __ldcg(&a.quad[(size_t)cc * 6 + q]);
-    Q[0] = __dadd_rn(Q[0], __dadd_rn(qc[0], __dmul_rn(mc, __dsub_rn(__dmul_rn(__dmul_rn(3.0, D0), D0), r2))));
-    Q[1] = __dadd_rn(Q[1], __dadd_rn(qc[1], __dmul_rn(mc, __dsub_rn(__dmul_rn(__dmul_rn(3.0, D1), D1), r2))));
-    Q[2] = __dadd_rn(Q[2], __dadd_rn(qc[2], __dmul_rn(mc, __dsub_rn(__dmul_rn(__dmul_rn(3.0, D2), D2), r2))));
-    Q[3] = __dadd_rn(Q[3], __dadd_rn(qc[3], __dmul_rn(mc, __dmul_rn(__dmul_rn(3.0, D0), D1))));
-    Q[4] = __dadd_rn(Q[4], __dadd_rn(qc[4], __dmul_rn(mc, __dmul_rn(__dmul_rn(3.0, D0), D2))));
-    Q[5] = __dadd_rn(Q[5], __dadd_rn(qc[5], __dmul_rn(mc, __dmul_rn(__dmul_rn(3.0, D1), D2))));
-  }
-  for (int q = 0; q < 6; q++) a.quad[(size_t)c * 6 + q] = Q[q];
-  a.s_q0[c] = make_float4(__double2float_rn(Q[0]), __double2float_rn(Q[1]),
-                          __double2float_rn(Q[2]), __double2float_rn(Q[3]));
-  a.s_q1[c] = make_float4(__double2float_rn(Q[4]), __double2float_rn(Q[5]), 0.0f, 0.0f);
-}
-
-__global__ void __launch_bounds__(kThreads) k_moments(MomArgs a) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= a.n_cells) return;
-  uint32_t c = (uint32_t)t;
-  if (n_children(a.child, c) != 0) return;
-  {
-    double M = 0.0, S[3] = {0.0, 0.0, 0.0};
-    const uint32_t f = a.first[c], e = f + a.count[c];
-    if (e > f && !AFD_IN(e - 1, a.n_part, "moments leaf range")) return;
-    for (uint32_t k = f; k < e; k++) {
-      const double mk = a.ms[k];
-      M = __dadd_rn(M, mk);
-      S[0] = __dadd_rn(S[0], __dmul_rn(mk, a.xs[k]));
-      S[1] = __dadd_rn(S[1], __dmul_rn(mk, a.ys[k]));
-      S[2] = __dadd_rn(S[2], __dmul_rn(mk, a.zs[k]));
-    }
-    finish_cell(a, c, M, S, true);
-    if (a.quad_on) leaf_quad(a, c);
-  }
-  for (;;) {
-    const uint32_t p = a.parent[c];
-    if (p == kNone) break;
-    if (!AFD_IN(p, a.n_cells, "moments parent")) break;
-    __threadfence();
-    const unsigned old = atomicAdd(&a.arrive[p], 1u);
-    if ((int)old != n_children(a.child, p) - 1) break;
-    __threadfence();
-    double M = 0.0, S[3] = {0.0, 0.0, 0.0};
-    for (int o = 0; o < 8; o++) {
-      const uint32_t cc = __ldg(&a.child[(size_t)p * 8 + o]);
-      if (cc == kNone || !AFD_IN(cc, a.n_cells, "moments child")) continue;
-      M = __dadd_rn(M, __ldcg(&a.mass[cc]));
-      for (int d = 0; d < 3; d++) S[d] = __dadd_rn(S[d], __ldcg(&a.smom[(size_t)cc * 3 + d]));
-    }
-    finish_cell(a, p, M, S, false);
-    if (a.quad_on) internal_quad(a, p);
-    if (a.block) {
-      // the walk's view of p's children: (COM_f32, s^2) and (first,
-      // count | leaf, id, 0) per octant slot, id = kNone when empty
-      for (int o = 0; o < 8; o++) {
-        const uint32_t cc = __ldg(&a.child[(size_t)p * 8 + o]);
-        uint4 nf = make_uint4(0u, 0u, 0u, 0u), meta = make_uint4(0u, 0u, kNone, 0u);
-        if (cc != kNone) {
-          const float4 f = __ldcg(&a.node_f[cc]);
-          const uint2 ni = __ldcg(&a.node_i[cc]);
-          nf = make_uint4(__float_as_uint(f.x), __float_as_uint(f.y), __float_as_uint(f.z),
-                          __float_as_uint(f.w));
-          meta = make_uint4(ni.x, ni.y, cc, 0u);
-        }
-        a.block[((size_t)p * 8 + o) * 2] = nf;
-        a.block[((size_t)p * 8 + o) * 2 + 1] = meta;
-      }
-    }
-    c = p;
-  }
-}
-
-// Monopole moments in passes. The climb above does, for every internal
-// cell, three correctly rounded FP64 divisions and the FP32 splits on a warp
-// that has one lane active (the last child to arrive), and GB300's FP64 pipe
-// takes as long for a one-lane warp instruction as for a full one. Without
-// quadrupoles (which need the children's centres of mass bottom-up) only the
-// ordered sums M and S climb (k_moments_sums); the centres of mass and the
-// FP32 superparticle data follow in one thread per cell on full warps
-// (k_moments_finish), and the walk's child records in another pass
-// (k_moments_blocks, construction steps). Each cell's arithmetic is the
-// definition's, in the same order.
+// Moments in passes. A single climb that finished each cell on the lane of
+// its last arriving child would run three correctly rounded FP64 divisions,
+// the FP32 splits and the quadrupole sums on a warp with one lane active,
+// and GB300's FP64 pipe takes as long for a one-lane warp instruction as for
+// a full one. So only the ordered sums M and S climb (k_moments_sums); the
+// centres of mass and the FP32 superparticle data follow in one thread per
+// cell on full warps (k_moments_finish), the walk's child records in
+// another pass (k_moments_blocks, construction steps), and the quadrupoles
+// in a second climb (k_moments_quad) that sums six components of a parent
+// on six lanes. Each cell's arithmetic is the definition's, in the same
+// order.
 __global__ void __launch_bounds__(kThreads) k_moments_sums(MomArgs a) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
@@ -864,6 +782,91 @@ __global__ void __launch_bounds__(kThreads) k_moments_sums(MomArgs a) {
       for (int q = 0; q < 8 && wm; q++) wm &= wm - 1;
     }
     __syncwarp();  // the sums are ordered before the climbing lane's fence and arrival
+  }
+}
+
+// Quadrupoles after the monopole passes (every centre of mass known): leaves
+// sum their particles (leaf_quad, one lane per leaf, Morton order), then the
+// parents climb with arrival counters like the sums, the completed parents
+// of a warp summed six lanes each -- one quadrupole component per lane, its
+// chain over the children in octant order with internal_quad's operations
+// -- five parents at a time. The arithmetic of every cell is the single
+// climb's, so the results are the same bit for bit.
+__global__ void __launch_bounds__(kThreads) k_moments_quad(MomArgs a) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  uint32_t c = (uint32_t)t;
+  bool climbing = t < a.n_cells && n_children(a.child, c) == 0;
+  if (climbing) {
+    const uint32_t f = a.first[c], e = f + a.count[c];
+    if (e > f && !AFD_IN(e - 1, a.n_part, "quad leaf range")) climbing = false;
+    else leaf_quad(a, c);
+  }
+  while (__any_sync(0xffffffffu, climbing)) {
+    bool won = false;
+    if (climbing) {
+      const uint32_t p = a.parent[c];
+      if (p == kNone || !AFD_IN(p, a.n_cells, "quad parent")) {
+        climbing = false;
+      } else {
+        __threadfence();
+        const unsigned old = atomicAdd(&a.arrive[p], 1u);
+        won = (int)old == n_children(a.child, p) - 1;
+        climbing = won;
+        if (won) c = p;
+      }
+    }
+    __threadfence();
+    __syncwarp();
+    unsigned wm = __ballot_sync(0xffffffffu, won);
+    while (wm) {
+      // lane 6j + q takes component q of the j-th completed parent (j < 5)
+      const int j = lane / 6, q = lane - 6 * j;
+      unsigned rest = wm;
+      int src = -1;
+      for (int k = 0; k <= j && rest && j < 5; k++) {
+        src = __ffs(rest) - 1;
+        rest &= rest - 1;
+      }
+      const bool mine = j < 5 && src >= 0 && __popc(wm & ((2u << src) - 1u)) == j + 1;
+      const uint32_t pj = __shfl_sync(0xffffffffu, c, src < 0 ? 0 : src);
+      if (mine) {
+        const double g0 = __ldcg(&a.com[(size_t)pj * 3]), g1 = __ldcg(&a.com[(size_t)pj * 3 + 1]),
+                     g2 = __ldcg(&a.com[(size_t)pj * 3 + 2]);
+        // the component's two axes (diagonal q < 3: a = b = q)
+        const int ax = q < 3 ? q : (q == 5 ? 1 : 0), bx = q < 3 ? q : (q == 3 ? 1 : 2);
+        double acc = 0.0;
+        for (int o = 0; o < 8; o++) {
+          const uint32_t cc = __ldg(&a.child[(size_t)pj * 8 + o]);
+          if (cc == kNone || !AFD_IN(cc, a.n_cells, "quad child")) continue;
+          const double D0 = __dsub_rn(__ldcg(&a.com[(size_t)cc * 3 + 0]), g0);
+          const double D1 = __dsub_rn(__ldcg(&a.com[(size_t)cc * 3 + 1]), g1);
+          const double D2 = __dsub_rn(__ldcg(&a.com[(size_t)cc * 3 + 2]), g2);
+          const double mc = __ldcg(&a.mass[cc]);
+          const double qc = __ldcg(&a.quad[(size_t)cc * 6 + q]);
+          const double Da = ax == 0 ? D0 : (ax == 1 ? D1 : D2);
+          const double Db = bx == 0 ? D0 : (bx == 1 ? D1 : D2);
+          const double p3 = __dmul_rn(__dmul_rn(3.0, Da), Db);
+          double term;
+          if (q < 3) {
+            const double r2 =
+                __dadd_rn(__dadd_rn(__dmul_rn(D0, D0), __dmul_rn(D1, D1)), __dmul_rn(D2, D2));
+            term = __dsub_rn(p3, r2);
+          } else {
+            term = p3;
+          }
+          acc = __dadd_rn(acc, __dadd_rn(qc, __dmul_rn(mc, term)));
+        }
+        a.quad[(size_t)pj * 6 + q] = acc;
+        float *sq = q < 4 ? reinterpret_cast<float *>(&a.s_q0[pj]) + q
+                          : reinterpret_cast<float *>(&a.s_q1[pj]) + (q - 4);
+        *sq = __double2float_rn(acc);
+        if (q == 4) reinterpret_cast<float *>(&a.s_q1[pj])[2] = 0.0f;
+        if (q == 5) reinterpret_cast<float *>(&a.s_q1[pj])[3] = 0.0f;
+      }
+      for (int k = 0; k < 5 && wm; k++) wm &= wm - 1;
+    }
+    __syncwarp();
   }
 }
 
@@ -1287,17 +1290,18 @@ int launch_moments(afd_ctx *c, bool child_blocks, bool need_q) {
   a.block = child_blocks ? ptr<uint4>(c->c_block) : nullptr;
   a.quad_on = quad_on;
   a.n_part = c->n;
-  if (quad_on) {
-    k_moments<<<blocks_for(nc), kThreads, 0, c->stream>>>(a);
+  k_moments_sums<<<blocks_for(nc), kThreads, 0, c->stream>>>(a);
+  k_moments_finish<<<blocks_for(nc), kThreads, 0, c->stream>>>(a);
+  c->launches += 2;
+  if (a.block) {
+    k_moments_blocks<<<blocks_for(nc), kThreads, 0, c->stream>>>(a);
     c->launches++;
-  } else {
-    k_moments_sums<<<blocks_for(nc), kThreads, 0, c->stream>>>(a);
-    k_moments_finish<<<blocks_for(nc), kThreads, 0, c->stream>>>(a);
-    c->launches += 2;
-    if (a.block) {
-      k_moments_blocks<<<blocks_for(nc), kThreads, 0, c->stream>>>(a);
-      c->launches++;
-    }
+  }
+  if (quad_on) {
+    if (cudaMemsetAsync(c->c_arrive.p, 0, sizeof(unsigned) * nc, c->stream) != cudaSuccess)
+      return AFD_ERR_CUDA;
+    k_moments_quad<<<blocks_for(nc), kThreads, 0, c->stream>>>(a);
+    c->launches++;
   }
   return ck();
 }
