@@ -486,9 +486,14 @@ int afd_fp32_peak(int device, void *stream, double *tflops_out);
  * quadrupole and particle count, A_g the smallest reference |a| among the
  * group's particles, e half the group box diagonal, u = box centre - COM.
  * log2 is a fixed polynomial (exponent + t p(t) on the mantissa 1 + t).
- * Network: 8-32-32-1, ReLU, inputs (f - mu) * isd, FP16 parameters, FP32
- * fused multiply-adds in input order. Without weights (afd_mac_set) or
- * reference magnitudes for the current particles, the walk uses theta.
+ * Network: 8-32-32-1, ReLU, FP16 parameters; inputs RN16((f - mu) * isd)
+ * and first-layer activations RN16(min(max(., 0), 65504)) in FP16 (RN16:
+ * nearest FP16, ties to even), sums in FP32 (products of FP16 values are
+ * exact); the walk evaluates it on the tensor cores, sixteen pairs per
+ * warp instruction sequence, summing in the tensor core's order. Training
+ * (afd_mlp_loss_grad, afd_mlp_train) uses the same network with FP32 inputs
+ * and activations. Without weights (afd_mac_set) or reference magnitudes
+ * for the current particles, the walk uses theta.
  *
  * Parameter vector (AFD_MAC_PARAMS floats): mu[8] isd[8] W1[32][8] b1[32]
  * W2[32][32] b2[32] w3[32] b3[1], row-major (W[j][k]: unit j, input k).
@@ -534,9 +539,9 @@ int afd_mac_samples(afd_ctx *ctx, double theta_lo, double theta_hi, double keep,
 int afd_mac_info(afd_ctx *ctx, int64_t *out);
 
 /* The network's output for n feature rows (feat: device, n x 8 floats; out:
- * device, n floats), with params (host) rounded to FP16 exactly as the walk
- * uses them. Queued on `stream` (a cudaStream_t, NULL = legacy default);
- * synchronises it. */
+ * device, n floats), with params (host) rounded to FP16, computed by the
+ * walk's own tensor-core code (the same outputs bit for bit). Queued on
+ * `stream` (a cudaStream_t, NULL = legacy default); synchronises it. */
 int afd_mlp_forward(const float *params, const float *feat, int64_t n, float *out, void *stream);
 
 /* Mean squared error of the network (FP32 parameters, not rounded) on n

@@ -102,6 +102,8 @@ def lib():
         L.afo_relist.argtypes = [ctypes.c_void_p]
         L.afo_relist_band.argtypes = [ctypes.c_void_p, _I64, _I32, _I64]
         L.afo_mlp_forward_bound_batch.argtypes = [_F32, ctypes.c_int64, _F32, _F32, _D]
+        L.afo_rn16.argtypes = [ctypes.c_float]
+        L.afo_rn16.restype = ctypes.c_float
         L.afo_let_export.argtypes = [ctypes.c_void_p, _D, ctypes.c_double, ctypes.c_int64, _D, _D,
                                      _D, _D, _I32]
         L.afo_let_export.restype = ctypes.c_int64
@@ -466,8 +468,8 @@ def fp16_round(params):
 
 
 def mlp_forward(params, feats):
-    """R13 network in FP32 (bias, then fused multiply-adds in input order, for
-    every unit) per feature row."""
+    """R13 network per feature row: FP16 inputs and first-layer activations,
+    FP32 sums (bias, then fused multiply-adds in input order)."""
     p = np.ascontiguousarray(params, dtype=np.float32)
     f = np.ascontiguousarray(feats, dtype=np.float32).reshape(-1, MAC_NF)
     out = np.zeros(f.shape[0], dtype=np.float32)
@@ -475,10 +477,16 @@ def mlp_forward(params, feats):
     return out
 
 
+def rn16(v):
+    """RN16 of R13: the nearest FP16 value (ties to even) of an FP32 value."""
+    return float(lib().afo_rn16(float(np.float32(v))))
+
+
 def mlp_forward_bound(params, feats):
-    """R13 network per feature row and, per row, the rounding bound
-    2 gamma_32 (|b3| + sum_j |w3_j h2_j|) within which any other FP32
-    summation order of the output unit's terms lands."""
+    """R13 network per feature row and, per row, the bound of R13 on the
+    difference between its output and any other FP32 summation order's (the
+    layers' sums in another order, a first-layer activation rounded to FP16
+    from the other sum)."""
     p = np.ascontiguousarray(params, dtype=np.float32)
     f = np.ascontiguousarray(feats, dtype=np.float32).reshape(-1, MAC_NF)
     out = np.zeros(f.shape[0], dtype=np.float32)

@@ -74,16 +74,24 @@
  *     each clamped to [-32, 32]. log2 is lg2(): the exponent of the FP32
  *     argument plus t*p(t) on its mantissa 1+t, p a fixed quartic (Horner
  *     with fused multiply-adds); 0 or subnormal arguments give -127.
- *  R13 network: 8-32-32-1 perceptron with ReLU on both hidden layers; input
- *     k is normalised as (f_k - mu_k) * isd_k; every parameter (mu and isd
- *     included) is an FP16 value; every unit, the output unit included, is
- *     its bias followed by fused multiply-adds over its inputs in index
- *     order, in FP32. Another implementation may sum the output unit's 32
- *     terms in another order: two FP32 sums of the same terms differ by at
- *     most 2 gamma_32 (|b3| + sum_j |w3_j h2_j|), gamma_k = k u / (1 - k u),
- *     u = 2^-24 (the standard bound for recursive or pairwise summation), so
- *     a decision of R14 is fixed by the definition only when the output lies
- *     further than that from tau; afo_mlp_forward_bound returns the bound.
+ *  R13 network: 8-32-32-1 perceptron with ReLU on both hidden layers; every
+ *     parameter (mu and isd included) is an FP16 value. The inputs are
+ *     x_k = RN16((f_k - mu_k) * isd_k) (FP32 subtraction and product, then
+ *     rounded to the nearest FP16 value, ties to even); hidden layer 1 is
+ *     h1_j = RN16(min(max(b1_j + sum_k W1_jk x_k, 0), 65504)); hidden layer
+ *     2 is h2_j = max(b2_j + sum_k W2_jk h1_k, 0); the output is
+ *     y = b3 + sum_j w3_j h2_j. Every sum is FP32, here the bias followed by
+ *     fused multiply-adds in index order (the products of FP16 values are
+ *     exact in FP32). FP16 operands are what the tensor cores take; the
+ *     order in which an implementation (a tensor core) sums is not fixed, so
+ *     afo_mlp_forward_bound also returns a bound on the difference between
+ *     this output and any FP32 summation order's, propagated through the
+ *     layers: each sum of n terms within 2 gamma_n of another order's
+ *     (gamma_n = n U / (1 - n U), U = 2^-22, allowing two units in the last
+ *     place per operation), a first-layer activation within the FP16
+ *     roundings of its sum's interval, and the later layers through the
+ *     absolute weights. A decision of R14 is fixed by the definition only
+ *     when the output lies further than that bound from tau.
  *  R14 learned decision for cell c and group g: open if c contains the
  *     group's first particle; accept if s^2 < theta_lo^2 d^2; open if not
  *     s^2 < theta_hi^2 d^2; otherwise accept iff the network's output is
@@ -711,35 +719,75 @@ void afo_mac_features(const float bmin[3], const float bmax[3], const float com[
   for (int k = 0; k < AFO_MAC_NF; k++) f[k] = clamp32(f[k]);
 }
 
+/* RN16 of R13: v rounded to the nearest FP16 value (ties to even), as a
+ * float; |v| is at most 65504 here (the callers clamp), NaN stays NaN. */
+float afo_rn16(float v) {
+  if (v != v) return v;
+  const float a = fabsf(v);
+  if (a == 0.0f) return v;
+  int e;
+  frexpf(a, &e); /* a = m 2^e, m in [0.5, 1): the FP16 spacing is 2^(e - 11) */
+  const int ex = e - 11 < -24 ? -24 : e - 11; /* subnormals: spacing 2^-24 */
+  const float r = ldexpf(nearbyintf(ldexpf(a, -ex)), ex);
+  return copysignf(r, v);
+}
+
+static double gamma_n(int n) {
+  const double U = ldexp(1.0, -22);
+  return n * U / (1.0 - n * U);
+}
+
+static float clamp_h1(float v) {
+  v = fmaxf(v, 0.0f);
+  return fminf(v, 65504.0f);
+}
+
 /* Network of R13 on one feature vector; p holds FP16-representable values.
- * *bound (may be NULL) receives 2 gamma_32 (|b3| + sum_j |w3_j h2_j|): the
- * largest difference between this output and the same terms summed in any
- * other FP32 order. */
+ * *bound (may be NULL) receives the bound of R13 on the difference between
+ * this output and another FP32 summation order's. */
 float afo_mlp_forward_bound(const float *p, const float f[AFO_MAC_NF], double *bound) {
   const float *mu = p, *isd = p + AFO_MAC_NF;
   const float *W1 = p + 2 * AFO_MAC_NF, *b1 = W1 + AFO_MAC_NH * AFO_MAC_NF;
   const float *W2 = b1 + AFO_MAC_NH, *b2 = W2 + AFO_MAC_NH * AFO_MAC_NH;
   const float *w3 = b2 + AFO_MAC_NH, *b3 = w3 + AFO_MAC_NH;
   float x[AFO_MAC_NF], h1[AFO_MAC_NH], h2[AFO_MAC_NH];
-  for (int k = 0; k < AFO_MAC_NF; k++) x[k] = (f[k] - mu[k]) * isd[k];
+  double d1[AFO_MAC_NH], d2[AFO_MAC_NH];
+  for (int k = 0; k < AFO_MAC_NF; k++) x[k] = afo_rn16((f[k] - mu[k]) * isd[k]);
   for (int j = 0; j < AFO_MAC_NH; j++) {
     float acc = b1[j];
-    for (int k = 0; k < AFO_MAC_NF; k++) acc = fmaf(W1[j * AFO_MAC_NF + k], x[k], acc);
-    h1[j] = acc > 0.0f ? acc : 0.0f;
+    double s1 = fabs((double)b1[j]);
+    for (int k = 0; k < AFO_MAC_NF; k++) {
+      acc = fmaf(W1[j * AFO_MAC_NF + k], x[k], acc);
+      s1 += fabs((double)W1[j * AFO_MAC_NF + k] * (double)x[k]);
+    }
+    h1[j] = afo_rn16(clamp_h1(acc));
+    /* another order's sum lies in [acc - e, acc + e]; RN16 and the clamps
+     * are monotonic, so its activation lies between these two */
+    const double e = 2.0 * gamma_n(AFO_MAC_NF + 1) * s1;
+    const float lo = afo_rn16(clamp_h1(nextafterf((float)((double)acc - e), -INFINITY)));
+    const float hi = afo_rn16(clamp_h1(nextafterf((float)((double)acc + e), INFINITY)));
+    d1[j] = fmax((double)hi - (double)h1[j], (double)h1[j] - (double)lo);
   }
   for (int j = 0; j < AFO_MAC_NH; j++) {
     float acc = b2[j];
-    for (int k = 0; k < AFO_MAC_NH; k++) acc = fmaf(W2[j * AFO_MAC_NH + k], h1[k], acc);
+    double s2 = fabs((double)b2[j]), dj = 0.0;
+    for (int k = 0; k < AFO_MAC_NH; k++) {
+      const double w = fabs((double)W2[j * AFO_MAC_NH + k]);
+      acc = fmaf(W2[j * AFO_MAC_NH + k], h1[k], acc);
+      s2 += w * (fabs((double)h1[k]) + d1[k]);
+      dj += w * d1[k];
+    }
     h2[j] = acc > 0.0f ? acc : 0.0f;
+    d2[j] = dj + 2.0 * gamma_n(AFO_MAC_NH + 1) * s2;
   }
   float y = b3[0];
-  for (int k = 0; k < AFO_MAC_NH; k++) y = fmaf(w3[k], h2[k], y);
-  if (bound) {
-    double a = fabs((double)b3[0]);
-    for (int k = 0; k < AFO_MAC_NH; k++) a += fabs((double)w3[k] * (double)h2[k]);
-    const double u = ldexp(1.0, -24), g32 = 32.0 * u / (1.0 - 32.0 * u);
-    *bound = 2.0 * g32 * a;
+  double s3 = fabs((double)b3[0]), dy = 0.0;
+  for (int k = 0; k < AFO_MAC_NH; k++) {
+    y = fmaf(w3[k], h2[k], y);
+    s3 += fabs((double)w3[k]) * ((double)h2[k] + d2[k]);
+    dy += fabs((double)w3[k]) * d2[k];
   }
+  if (bound) *bound = dy + 2.0 * gamma_n(AFO_MAC_NH + 1) * s3;
   return y;
 }
 

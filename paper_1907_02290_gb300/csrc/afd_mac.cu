@@ -341,18 +341,36 @@ __global__ void k_fp16_round(float *w, int n) {
   if (i < n) w[i] = __half2float(__float2half_rn(w[i]));
 }
 
-__global__ void __launch_bounds__(256) k_mlp_forward(const float *__restrict__ w,
-                                                     const float *__restrict__ feat, int64_t n,
-                                                     float *__restrict__ out) {
-  __shared__ __align__(16) float wsm[kMacNP + 3];
-  mac_load_transposed(wsm, w, threadIdx.x, blockDim.x);
+// Inference on the tensor cores, as the walk runs it: each warp takes
+// sixteen rows at a time.
+constexpr int kFwdWarps = 8;
+__global__ void __launch_bounds__(32 * kFwdWarps) k_mlp_forward(const float *__restrict__ w,
+                                                               const float *__restrict__ feat,
+                                                               int64_t n, float *__restrict__ out) {
+  __shared__ __align__(16) MacFrag mf;
+  __shared__ __align__(16) uint4 x16_all[kFwdWarps][16];
+  mac_frag_load(mf, w, threadIdx.x, blockDim.x);
   __syncthreads();
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  float f[kMacNF];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  uint4 *x16 = x16_all[wib];
+  const int64_t stride = (int64_t)gridDim.x * kFwdWarps * 16;
+  for (int64_t base = ((int64_t)blockIdx.x * kFwdWarps + wib) * 16; base < n; base += stride) {
+    if (lane < 16) {
+      float f[kMacNF];
+      const int64_t s = base + lane;
 #pragma unroll
-  for (int k = 0; k < kMacNF; k++) f[k] = feat[s * kMacNF + k];
-  out[s] = mac_mlp_t(wsm, f);
+      for (int k = 0; k < kMacNF; k++) f[k] = s < n ? feat[s * kMacNF + k] : 0.0f;
+      x16[lane] = mac_row16(mf, f);
+    }
+    __syncwarp();
+    const float2 y = mac_mma_rows(mf, x16, lane);
+    if ((lane & 3) == 0) {
+      const int64_t r = base + (lane >> 2);
+      if (r < n) out[r] = y.x;
+      if (r + 8 < n) out[r + 8] = y.y;
+    }
+    __syncwarp();
+  }
 }
 
 // Per-block FP64 sums of each feature, its square and the target.
@@ -900,7 +918,11 @@ int afd_mlp_forward(const float *params, const float *feat, int64_t n, float *ou
   float *w;
   MAC_TRY(scratch.get(&w, kMacNP));
   MAC_TRY(upload_rounded(params, w, s));
-  if (n > 0) k_mlp_forward<<<blocks_of(n, 256), 256, 0, s>>>(w, feat, n, out);
+  if (n > 0) {
+    const int64_t want = (n + 16 * kFwdWarps - 1) / (16 * kFwdWarps);
+    k_mlp_forward<<<(unsigned)(want < 152 * 8 ? want : 152 * 8), 32 * kFwdWarps, 0, s>>>(w, feat, n,
+                                                                                          out);
+  }
   MAC_TRY(ck());
   return cudaStreamSynchronize(s) == cudaSuccess ? AFD_OK : AFD_ERR_CUDA;
 }

@@ -14,15 +14,16 @@
 //  log2 here is mac_lg2(): the FP32 exponent plus t * p(t) on the mantissa
 //  1 + t, p a least-squares quartic, Horner with fused multiply-adds.
 //
-//  network: 8-32-32-1, ReLU, inputs normalised as (f - mu) * isd, every
-//  parameter an FP16 value held as FP32, each hidden unit its bias followed
-//  by fused multiply-adds in input order. The output unit is b3 plus the 32
-//  terms w3_j h2_j; this code sums the rounded products pairwise by halving
-//  (j += j + 16, then 8, 4, 2, 1: a warp's xor butterfly, five shuffles
-//  instead of a 32-step chain) and then adds b3. Any FP32 order of those
-//  terms lies within 2 gamma_32 (|b3| + sum |w3_j h2_j|) of any other
-//  (gamma_k = k 2^-24 / (1 - k 2^-24)), so a decision is fixed by the
-//  network only when its output is further than that from tau.
+//  network: 8-32-32-1, ReLU, every parameter an FP16 value; the inputs
+//  x = RN16((f - mu) * isd) and the first-layer activations
+//  h1 = RN16(min(max(b1 + W1 x, 0), 65504)) are FP16 (RN16: nearest FP16,
+//  ties to even), h2 = max(b2 + W2 h1, 0) and y = b3 + w3 . h2 are FP32.
+//  The two layers run on the tensor cores (mma.sync, FP16 operands, FP32
+//  accumulation), sixteen (group, cell) pairs at a time, in whatever order
+//  the tensor core sums; the output is summed over each lane's eight units
+//  and then across the four lanes that share a row. A decision is fixed by
+//  the network only when its output is further from tau than the bound on
+//  two FP32 summation orders' difference that the definition states.
 //
 //  decision: open a cell holding the group's first particle; accept when
 //  s^2 < theta_lo^2 d^2; open unless s^2 < theta_hi^2 d^2; otherwise accept
@@ -117,103 +118,120 @@ __device__ __forceinline__ void mac_features(const float *bmin, const float *bma
   for (int k = 0; k < kMacNF; k++) f[k] = mac_clamp(f[k]);
 }
 
-// ---- one lane evaluates the network, two units per instruction ----
-// Shared-memory layout for mac_mlp_t (offsets as in the flat vector, the two
-// weight matrices transposed to [input][unit]): mu, isd, W1T[8][32], b1,
-// W2T[32][32], b2, w3, b3. Each unit accumulates its bias and then its
-// inputs in index order with one rounding per fused multiply-add; the packed
-// FMA (fma.rn.f32x2) rounds each half exactly like the scalar one.
-__device__ __forceinline__ void mac_load_transposed(float *wt, const float *w, int tid, int nt) {
-  for (int i = tid; i < kMacNP; i += nt) {
-    float v;
-    if (i >= kMacOffW1 && i < kMacOffB1) {  // W1T[k][j] = W1[j][k]
-      const int k = (i - kMacOffW1) / kMacNH, j = (i - kMacOffW1) % kMacNH;
-      v = w[kMacOffW1 + j * kMacNF + k];
-    } else if (i >= kMacOffW2 && i < kMacOffB2) {  // W2T[k][j] = W2[j][k]
-      const int k = (i - kMacOffW2) / kMacNH, j = (i - kMacOffW2) % kMacNH;
-      v = w[kMacOffW2 + j * kMacNH + k];
-    } else {
-      v = w[i];
-    }
-    wt[i] = v;
+// ---- the network on the tensor cores ----
+// mma.sync m16n8k8 (layer 1, 8 inputs) and m16n8k16 (layer 2, 32 inputs),
+// row.col, FP16 operands, FP32 accumulators: 16 rows (pairs) x 8 units per
+// instruction. Fragment layout with g = lane / 4, t = lane % 4:
+//   A (16 x k, rows = pairs): a0 = row g, cols 2t, 2t+1; a1 = row g + 8;
+//     (k16) a2, a3 = the same rows, cols 8 + 2t, 8 + 2t + 1;
+//   B (k x 8, col = unit): b0 = unit g, k 2t, 2t+1; (k16) b1 = k 8 + 2t, ..;
+//   C, D: c0, c1 = row g, units 2t, 2t+1; c2, c3 = row g + 8.
+// Layer 1's outputs of unit tiles 2s, 2s+1 are then exactly layer 2's A
+// fragment of input slice s, so the hidden layer never leaves registers.
+struct MacFrag {
+  uint32_t w1[4][32];        // unit tile n: W1[8n + g][2t, 2t+1] (f16x2)
+  uint32_t w2[2][4][2][32];  // slice s, unit tile n, reg r: W2[8n + g][16s + 8r + 2t, +1]
+  float2 b1[4][32];          // unit tile n: (b1[8n + 2t], b1[8n + 2t + 1])
+  float2 b2[4][32];
+  float2 w3[4][32];
+  float mu[kMacNF], isd[kMacNF];
+  float b3;
+};
+
+__device__ __forceinline__ uint32_t mac_h2(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
+// Fragments from the flat parameter vector (FP16 values held as FP32);
+// threads tid of nt fill them (then a barrier is the caller's).
+__device__ __forceinline__ void mac_frag_load(MacFrag &F, const float *w, int tid, int nt) {
+  for (int i = tid; i < 4 * 32; i += nt) {
+    const int n = i >> 5, l = i & 31, g = l >> 2, t = l & 3, u = 8 * n + g;
+    F.w1[n][l] = mac_h2(w[kMacOffW1 + u * kMacNF + 2 * t], w[kMacOffW1 + u * kMacNF + 2 * t + 1]);
+    const int v = 8 * n + 2 * t;
+    F.b1[n][l] = make_float2(w[kMacOffB1 + v], w[kMacOffB1 + v + 1]);
+    F.b2[n][l] = make_float2(w[kMacOffB2 + v], w[kMacOffB2 + v + 1]);
+    F.w3[n][l] = make_float2(w[kMacOffW3 + v], w[kMacOffW3 + v + 1]);
   }
+  for (int i = tid; i < 2 * 4 * 2 * 32; i += nt) {
+    const int l = i & 31, r = (i >> 5) & 1, n = (i >> 6) & 3, sl = i >> 8;
+    const int g = l >> 2, t = l & 3, u = 8 * n + g, k = 16 * sl + 8 * r + 2 * t;
+    F.w2[sl][n][r][l] = mac_h2(w[kMacOffW2 + u * kMacNH + k], w[kMacOffW2 + u * kMacNH + k + 1]);
+  }
+  for (int i = tid; i < kMacNF; i += nt) {
+    F.mu[i] = w[i];
+    F.isd[i] = w[kMacNF + i];
+  }
+  if (tid == 0) F.b3 = w[kMacOffB3];
 }
 
-__device__ __forceinline__ unsigned long long mac_pk(float lo, float hi) {
-  return ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
-}
-__device__ __forceinline__ float mac_lo(unsigned long long v) { return __uint_as_float((uint32_t)v); }
-__device__ __forceinline__ float mac_hi(unsigned long long v) {
-  return __uint_as_float((uint32_t)(v >> 32));
-}
-__device__ __forceinline__ unsigned long long mac_fma2(unsigned long long a, unsigned long long b,
-                                                       unsigned long long c) {
-  unsigned long long d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-
-// wt: shared memory in the mac_load_transposed layout, 16-byte aligned.
-__device__ __forceinline__ float mac_mlp_t(const float *wt, const float *f) {
+// One input row: RN16((f - mu) * isd) as four f16x2 words (inputs 0-1, 2-3, ..).
+__device__ __forceinline__ uint4 mac_row16(const MacFrag &F, const float *f) {
   float x[kMacNF];
 #pragma unroll
-  for (int k = 0; k < kMacNF; k++) x[k] = __fmul_rn(__fsub_rn(f[k], wt[k]), wt[kMacNF + k]);
-  unsigned long long acc[kMacNH / 2];
-  const float4 *b1 = reinterpret_cast<const float4 *>(wt + kMacOffB1);
+  for (int k = 0; k < kMacNF; k++) x[k] = __fmul_rn(__fsub_rn(f[k], F.mu[k]), F.isd[k]);
+  return make_uint4(mac_h2(x[0], x[1]), mac_h2(x[2], x[3]), mac_h2(x[4], x[5]), mac_h2(x[6], x[7]));
+}
+
+__device__ __forceinline__ void mac_mma_k8(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t b0,
+                                           float2 c) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5}, {%6}, "
+      "{%7, %8, %9, %10};"
+      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+      : "r"(a0), "r"(a1), "r"(b0), "f"(c.x), "f"(c.y), "f"(c.x), "f"(c.y));
+}
+__device__ __forceinline__ void mac_mma_k16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                            uint32_t a3, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+      "{%8, %9}, {%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ float mac_h1(float v) { return fminf(fmaxf(v, 0.0f), 65504.0f); }
+
+// The network on the 16 rows whose input words sit in x16 (row r: x16[r]);
+// every lane of the warp calls it. Returns the outputs of rows g and g + 8
+// (each lane of the row's quad holds them).
+__device__ __forceinline__ float2 mac_mma_rows(const MacFrag &F, const uint4 *x16, int lane) {
+  const int g = lane >> 2, t = lane & 3;
+  const uint32_t *xw = reinterpret_cast<const uint32_t *>(x16);
+  const uint32_t a0 = xw[g * 4 + t], a1 = xw[(g + 8) * 4 + t];
+  // layer 1: four unit tiles, then ReLU, clamp and FP16 as layer 2's A fragments
+  uint32_t hl[4], hh[4];
 #pragma unroll
-  for (int q = 0; q < kMacNH / 4; q++) {
-    const float4 b = b1[q];
-    acc[2 * q] = mac_pk(b.x, b.y);
-    acc[2 * q + 1] = mac_pk(b.z, b.w);
+  for (int n = 0; n < 4; n++) {
+    float d[4];
+    mac_mma_k8(d, a0, a1, F.w1[n][lane], F.b1[n][lane]);
+    hl[n] = mac_h2(mac_h1(d[0]), mac_h1(d[1]));
+    hh[n] = mac_h2(mac_h1(d[2]), mac_h1(d[3]));
+  }
+  // layer 2: four unit tiles over two input slices; output dot products
+  float ylo = 0.0f, yhi = 0.0f;
+#pragma unroll
+  for (int n = 0; n < 4; n++) {
+    const float2 b = F.b2[n][lane];
+    float d[4] = {b.x, b.y, b.x, b.y};
+#pragma unroll
+    for (int sl = 0; sl < 2; sl++)
+      mac_mma_k16(d, hl[2 * sl], hh[2 * sl], hl[2 * sl + 1], hh[2 * sl + 1], F.w2[sl][n][0][lane],
+                  F.w2[sl][n][1][lane]);
+    const float2 w3 = F.w3[n][lane];
+    ylo = __fmaf_rn(w3.x, fmaxf(d[0], 0.0f), ylo);
+    ylo = __fmaf_rn(w3.y, fmaxf(d[1], 0.0f), ylo);
+    yhi = __fmaf_rn(w3.x, fmaxf(d[2], 0.0f), yhi);
+    yhi = __fmaf_rn(w3.y, fmaxf(d[3], 0.0f), yhi);
   }
 #pragma unroll
-  for (int k = 0; k < kMacNF; k++) {
-    const unsigned long long xk = mac_pk(x[k], x[k]);
-    const float4 *row = reinterpret_cast<const float4 *>(wt + kMacOffW1 + k * kMacNH);
-#pragma unroll
-    for (int q = 0; q < kMacNH / 4; q++) {
-      const float4 r = row[q];
-      acc[2 * q] = mac_fma2(mac_pk(r.x, r.y), xk, acc[2 * q]);
-      acc[2 * q + 1] = mac_fma2(mac_pk(r.z, r.w), xk, acc[2 * q + 1]);
-    }
+  for (int o = 1; o < 4; o <<= 1) {
+    ylo = __fadd_rn(ylo, __shfl_xor_sync(0xffffffffu, ylo, o));
+    yhi = __fadd_rn(yhi, __shfl_xor_sync(0xffffffffu, yhi, o));
   }
-  float h1[kMacNH];
-#pragma unroll
-  for (int q = 0; q < kMacNH / 2; q++) {
-    const float a = mac_lo(acc[q]), b = mac_hi(acc[q]);
-    h1[2 * q] = a > 0.0f ? a : 0.0f;
-    h1[2 * q + 1] = b > 0.0f ? b : 0.0f;
-  }
-  const float4 *b2 = reinterpret_cast<const float4 *>(wt + kMacOffB2);
-#pragma unroll
-  for (int q = 0; q < kMacNH / 4; q++) {
-    const float4 b = b2[q];
-    acc[2 * q] = mac_pk(b.x, b.y);
-    acc[2 * q + 1] = mac_pk(b.z, b.w);
-  }
-#pragma unroll
-  for (int k = 0; k < kMacNH; k++) {
-    const unsigned long long hk = mac_pk(h1[k], h1[k]);
-    const float4 *row = reinterpret_cast<const float4 *>(wt + kMacOffW2 + k * kMacNH);
-#pragma unroll
-    for (int q = 0; q < kMacNH / 4; q++) {
-      const float4 r = row[q];
-      acc[2 * q] = mac_fma2(mac_pk(r.x, r.y), hk, acc[2 * q]);
-      acc[2 * q + 1] = mac_fma2(mac_pk(r.z, r.w), hk, acc[2 * q + 1]);
-    }
-  }
-  float p[kMacNH];
-#pragma unroll
-  for (int q = 0; q < kMacNH / 2; q++) {
-    const float a = mac_lo(acc[q]), b = mac_hi(acc[q]);
-    p[2 * q] = __fmul_rn(wt[kMacOffW3 + 2 * q], a > 0.0f ? a : 0.0f);
-    p[2 * q + 1] = __fmul_rn(wt[kMacOffW3 + 2 * q + 1], b > 0.0f ? b : 0.0f);
-  }
-#pragma unroll
-  for (int half = kMacNH / 2; half > 0; half /= 2)
-#pragma unroll
-    for (int k = 0; k < half; k++) p[k] = __fadd_rn(p[k], p[k + half]);
-  return __fadd_rn(p[0], wt[kMacOffB3]);
+  return make_float2(__fadd_rn(ylo, F.b3), __fadd_rn(yhi, F.b3));
 }
 
 }  // namespace afd

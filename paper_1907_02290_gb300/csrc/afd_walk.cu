@@ -35,14 +35,12 @@
 //
 // With the learned criterion (afd_mac.cuh) the same walk decides each cell
 // by learned_pre() (the band tests in FP32) and, for the cells inside the
-// band, by the network, which the whole warp evaluates for four band cells
-// at a time: lane j computes hidden unit j of both layers (its weights read
-// from shared memory, the cells' inputs and hidden values broadcast from
-// shared memory, one packed FMA covering two cells), and the 32 output
-// products are summed by an xor butterfly in the pairwise-halving order of
-// mac_mlp_t. The arithmetic per unit is mac_mlp_t's, so the walk and the
-// inference entry point give the same outputs bit for bit; the warp needs
-// few registers and no lane sits idle in the layers.
+// band, by the network, which the warp evaluates for sixteen band cells at a
+// time on the tensor cores (mac_mma_rows: each band lane writes its cell's
+// FP16 input row to shared memory, then twelve mma.sync instructions run
+// both layers with the hidden layer kept in registers). The inference entry
+// point runs the same code, so the walk and afd_mlp_forward give the same
+// outputs bit for bit.
 #include "afd_internal.cuh"
 #include "afd_mac.cuh"
 
@@ -204,22 +202,10 @@ __device__ __forceinline__ void rec_put(RecStream &st, bool on, T rec, T *arena,
   }
 }
 
-// The network's weights as the walk reads them: per hidden unit (lane) a
-// padded row, so that four consecutive weights are one 16-byte load without
-// bank conflicts; the vectors in their own small array.
-constexpr int kW1Row = 12, kW2Row = 36;
-struct MacWeights {
-  float w1[kMacNH][kW1Row];  // W1[j][k], k < 8
-  float w2[kMacNH][kW2Row];  // W2[j][k], k < 32
-  float vec[2 * kMacNF + 3 * kMacNH + 4];  // mu, isd, b1, b2, w3, b3
-};
-constexpr int kVecB1 = 2 * kMacNF, kVecB2 = kVecB1 + kMacNH, kVecW3 = kVecB2 + kMacNH,
-              kVecB3 = kVecW3 + kMacNH;
-
-// Per-warp scratch of the warp-wide network evaluation.
+// Per-warp scratch of the network evaluation: the FP16 input rows of the
+// (up to) 16 band cells of a round.
 struct MacScratch {
-  float4 xin[8][kMacNF];  // inputs: [band cell / 4][k] -> 4 cells
-  float4 hin[kMacNH];     // hidden layer 1 of the current 4 cells: [unit]
+  uint4 x16[16];
 };
 
 // The next group (neighbour walk: work item) for this warp. The grid holds
@@ -236,26 +222,16 @@ template <int MODE>
 __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
   constexpr bool LEARNED = MODE == kModeLearned, NBR = MODE == kModeNeighbour;
   __shared__ uint2 stk_all[kWalkWarps][kStack];
-  __shared__ __align__(16) MacWeights mw_all[1];  // unused (and dropped) without LEARNED
+  __shared__ __align__(16) MacFrag mf_all[1];  // unused (and dropped) without LEARNED
   __shared__ __align__(16) MacScratch msc_all[LEARNED ? kWalkWarps : 1];
-  MacWeights &mw = mw_all[0];
+  MacFrag &mf = mf_all[0];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
   uint2 *stk = stk_all[wib];
   MacScratch &msc = msc_all[LEARNED ? wib : 0];
   uint32_t evals = 0, accepts = 0, rounds = 0;
   if (LEARNED) {
-    for (int i = threadIdx.x; i < kMacNH * kMacNF; i += kWalkThreads)
-      mw.w1[i / kMacNF][i % kMacNF] = a.mac_w[kMacOffW1 + i];
-    for (int i = threadIdx.x; i < kMacNH * kMacNH; i += kWalkThreads)
-      mw.w2[i / kMacNH][i % kMacNH] = a.mac_w[kMacOffW2 + i];
-    for (int i = threadIdx.x; i < 2 * kMacNF; i += kWalkThreads) mw.vec[i] = a.mac_w[i];
-    for (int i = threadIdx.x; i < kMacNH; i += kWalkThreads) {
-      mw.vec[kVecB1 + i] = a.mac_w[kMacOffB1 + i];
-      mw.vec[kVecB2 + i] = a.mac_w[kMacOffB2 + i];
-      mw.vec[kVecW3 + i] = a.mac_w[kMacOffW3 + i];
-    }
-    if (threadIdx.x == 0) mw.vec[kVecB3] = a.mac_w[kMacOffB3];
+    mac_frag_load(mf, a.mac_w, threadIdx.x, kWalkThreads);
     __syncthreads();
   }
   for (int64_t g = take_group(a, lane); g < a.n_groups; g = take_group(a, lane)) {
@@ -393,62 +369,17 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
           const int nb = __popc(bm), rank = __popc(bm & lt);
           float y_me = 0.0f;
           if (lane == 0) rounds++;
-          float *xin = reinterpret_cast<float *>(msc.xin);
-          if (need)
-#pragma unroll
-            for (int k = 0; k < kMacNF; k++)
-              xin[((rank >> 2) * kMacNF + k) * 4 + (rank & 3)] =
-                  __fmul_rn(__fsub_rn(feat[k], mw.vec[k]), mw.vec[kMacNF + k]);
-          __syncwarp();
-          for (int g4 = 0; g4 < nb; g4 += 4) {
-            // layer 1, unit = lane, cells g4 .. g4 + 3 (pairs (0,1), (2,3))
-            const float b1 = mw.vec[kVecB1 + lane];
-            unsigned long long A01 = mac_pk(b1, b1), A23 = A01;
-#pragma unroll
-            for (int kq = 0; kq < kMacNF / 4; kq++) {
-              const float4 w4 = *reinterpret_cast<const float4 *>(&mw.w1[lane][4 * kq]);
-              const float wk[4] = {w4.x, w4.y, w4.z, w4.w};
-#pragma unroll
-              for (int i = 0; i < 4; i++) {
-                const float4 x = msc.xin[g4 >> 2][4 * kq + i];
-                const unsigned long long W = mac_pk(wk[i], wk[i]);
-                A01 = mac_fma2(W, mac_pk(x.x, x.y), A01);
-                A23 = mac_fma2(W, mac_pk(x.z, x.w), A23);
-              }
-            }
-            float h[4] = {mac_lo(A01), mac_hi(A01), mac_lo(A23), mac_hi(A23)};
-#pragma unroll
-            for (int c = 0; c < 4; c++) h[c] = h[c] > 0.0f ? h[c] : 0.0f;
-            msc.hin[lane] = make_float4(h[0], h[1], h[2], h[3]);
+          // sixteen band cells per round: their FP16 input rows, then both
+          // layers on the tensor cores; lane (row % 8) * 4 returns row's output
+          for (int r0 = 0; r0 < nb; r0 += 16) {
+            const int rr = rank - r0;
+            if (need && rr >= 0 && rr < 16) msc.x16[rr] = mac_row16(mf, feat);
             __syncwarp();
-            // layer 2, unit = lane
-            const float b2 = mw.vec[kVecB2 + lane];
-            unsigned long long B01 = mac_pk(b2, b2), B23 = B01;
-#pragma unroll 2
-            for (int kq = 0; kq < kMacNH / 4; kq++) {
-              const float4 w4 = *reinterpret_cast<const float4 *>(&mw.w2[lane][4 * kq]);
-              const float wk[4] = {w4.x, w4.y, w4.z, w4.w};
-#pragma unroll
-              for (int i = 0; i < 4; i++) {
-                const float4 hk = msc.hin[4 * kq + i];
-                const unsigned long long W = mac_pk(wk[i], wk[i]);
-                B01 = mac_fma2(W, mac_pk(hk.x, hk.y), B01);
-                B23 = mac_fma2(W, mac_pk(hk.z, hk.w), B23);
-              }
-            }
-            // output: products w3_j h2_j, xor butterfly (= pairwise halving), + b3
-            const float w3 = mw.vec[kVecW3 + lane];
-            float o[4] = {mac_lo(B01), mac_hi(B01), mac_lo(B23), mac_hi(B23)};
-#pragma unroll
-            for (int c = 0; c < 4; c++) o[c] = __fmul_rn(w3, o[c] > 0.0f ? o[c] : 0.0f);
-#pragma unroll
-            for (int off = kMacNH / 2; off > 0; off >>= 1)
-#pragma unroll
-              for (int c = 0; c < 4; c++) o[c] = __fadd_rn(o[c], __shfl_xor_sync(0xffffffffu, o[c], off));
-            const float b3 = mw.vec[kVecB3];
-#pragma unroll
-            for (int c = 0; c < 4; c++)
-              if (need && rank == g4 + c) y_me = __fadd_rn(o[c], b3);
+            const float2 y = mac_mma_rows(mf, msc.x16, lane);
+            const int src = (rr & 7) * 4;
+            const float ylo = __shfl_sync(0xffffffffu, y.x, src);
+            const float yhi = __shfl_sync(0xffffffffu, y.y, src);
+            if (need && rr >= 0 && rr < 16) y_me = rr < 8 ? ylo : yhi;
             __syncwarp();
           }
           if (need) {

@@ -4,13 +4,14 @@ readings R12-R15, through the C ABI.
 
 Bit-exact: quadrupole moments (the criterion reads them), the features of
 every sampled pair and the set of pairs the band leaves to the network.
-The network's output: the oracle sums the output unit's terms in index
-order (R13), the kernel by a warp butterfly; the two must lie within the
-FP32 rounding bound of R13 of each other. The interaction lists of the
-learned walk: equal to the oracle's, except that for pairs whose oracle
-output lies within that bound of tau (where two correct FP32 orders may
-decide differently) the oracle takes the kernel's decision; those pairs are
-counted and reported. Within tolerance: the targets (GPU FP32 compensated
+The network's output (R13: FP16 inputs and first-layer activations, FP32
+sums): the oracle sums in index order, the kernel on the tensor cores in the
+tensor core's order; the two must lie within the bound R13 states for two
+FP32 summation orders. The interaction lists of the learned walk: equal to
+the oracle's, except that for pairs whose oracle output lies within that
+bound of tau (where two correct implementations may decide differently)
+the oracle takes the kernel's decision; those pairs are counted and
+reported. Within tolerance: the targets (GPU FP32 compensated
 sums vs oracle FP64) and the network gradients of the GPU backward pass (vs
 the oracle's FP64 chain rule, itself pinned by finite differences). Finally
 the trained network is judged by brute force: its force error against the
@@ -64,9 +65,9 @@ def gpu_ctx(env, p, amag, *, n_grp=64, theta=0.5, quad=False):
 
 
 def test_forward_within_the_summation_bound_with_fp16_weights(env):
-    """Same FP16-rounded parameters, same hidden-layer arithmetic; the output
-    unit's 32 terms summed in another order: every output within the FP32
-    bound of R13 of the oracle's, and most of them equal."""
+    """Same FP16-rounded parameters and FP16 inputs; the layers' sums in the
+    tensor core's order: every output within the bound of R13 of the
+    oracle's (many rows of 16, a ragged last one, clamped features)."""
     torch, afd, orc = env
     p = rand_params(orc, 3)
     f = np.random.default_rng(4).normal(0.0, 4.0, (20000, 8)).astype(np.float32)
@@ -81,7 +82,10 @@ def test_forward_within_the_summation_bound_with_fp16_weights(env):
     equal = float(np.mean(got == ref))
     print(f"network output: {equal:.3f} of rows equal, largest difference "
           f"{float(np.max(diff / bound)):.3f} of the bound")
-    assert equal > 0.3
+    # a ragged count: 16 rows per warp step, the last rows padded
+    out2 = torch.empty(37, dtype=torch.float32, device="cuda:0")
+    afd.afd_mlp_forward(p, dev(torch, f[:37], torch.float32), out2)
+    assert np.array_equal(out2.cpu().numpy(), got[:37])
 
 
 def test_gradient_matches_oracle_backward(env):
@@ -209,7 +213,7 @@ def test_learned_lists_bit_exact_and_forces(env, plummer, case):
     band, flips = t.relist_band(g.export("spj_off"), g.export("spj_idx"))
     print(f"learned walk ({case}): {info['evaluations']} network evaluations, "
           f"{band} within the rounding bound of tau, {flips} decided otherwise than the oracle")
-    assert flips <= band and band <= max(10, info["evaluations"] // 1000)
+    assert flips <= band and band <= max(10, info["evaluations"] // 100)
     check_structure(g, t, quad=quad)
     ref = t.force()
     assert rms_rel_acc(acc.cpu().numpy().astype(np.float64), ref) <= 1e-6

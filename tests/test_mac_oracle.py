@@ -132,18 +132,59 @@ def test_mlp_output_unit_is_the_plain_sequential_sum(orc):
     y, bound = orc.mlp_forward_bound(p, f)
     assert y[0] == np.float32(1.0)
     pairwise = 1.0 + 2.0 ** -20  # exact in FP32
-    assert abs(pairwise - float(y[0])) <= bound[0]
-    u = 2.0 ** -24
-    assert bound[0] == pytest.approx(2 * 32 * u / (1 - 32 * u) * (1.0 + 32 * 2.0 ** -25), rel=1e-12)
+    assert abs(pairwise - float(y[0])) <= bound[0] < 2.0 ** -15
     assert orc.mlp_forward(p, f)[0] == y[0]
 
 
+def test_rn16_is_the_fp16_rounding(orc):
+    """RN16 of R13 against numpy's FP16 conversion (round to nearest, ties
+    to even) over normal, subnormal and tie values."""
+    g = np.random.default_rng(12)
+    v = np.concatenate([
+        g.normal(0.0, 10.0, 4000), np.exp2(g.uniform(-30, 15.9, 4000)) * g.choice([-1, 1], 4000),
+        (np.arange(-2000, 2000) + 0.5) * 2.0 ** -10,   # ties at the ulp of [1, 2)
+        (np.arange(0, 1024) + 0.5) * 2.0 ** -24,       # subnormal ties
+        [0.0, -0.0, 65504.0, -65504.0, 6.1e-5, 5.96e-8, 2.9e-8, 3.0e-8]]).astype(np.float32)
+    got = np.array([orc.rn16(x) for x in v], np.float32)
+    ref = v.astype(np.float16).astype(np.float32)
+    assert np.array_equal(got, ref)
+    assert np.array_equal(np.signbit(got), np.signbit(ref))
+
+
+def test_mlp_inputs_and_first_layer_are_fp16(orc):
+    """R13 rounds the normalised inputs and the first-layer activations to
+    FP16 (ties to even) and saturates the activations at 65504: an input of
+    1 + 2^-12 reaches the output as 1, an activation of 2049 as 2048 (FP16
+    spacing 2 there), one of 70000 as 65504."""
+    p = np.zeros(orc.MAC_NP, np.float32)
+    mu, isd, W1, b1, W2, b2, w3, b3 = orc.mlp_unpack(p)
+    isd[:] = 1.0
+    W1[0, 0] = 1.0   # h1_0 = x_0
+    b1[1] = 2049.0   # h1_1 = 2049 -> 2048
+    b1[2] = 70000.0  # h1_2 = 70000 -> 65504 (not FP16, but a sum can reach it)
+    W2[0, 0] = W2[1, 1] = W2[2, 2] = 1.0
+    f = np.array([[1.0 + 2.0 ** -12, 0, 0, 0, 0, 0, 0, 0]], np.float32)
+    for k, want in ((0, 1.0), (1, 2048.0), (2, 65504.0)):
+        w3[:] = 0.0
+        w3[k] = 1.0
+        assert orc.mlp_forward(p, f)[0] == np.float32(want), k
+
+
 def test_mlp_forward_matches_fp64_network(orc):
+    """The FP64 evaluation of the same definition (FP16 roundings of inputs
+    and first-layer activations, sums in FP64) lies within the returned
+    bound, which is small next to the output."""
     p = _rand_params(orc, 5)
     f = np.random.default_rng(6).normal(0.0, 3.0, (500, 8)).astype(np.float32)
-    y32 = orc.mlp_forward(p, f).astype(np.float64)
-    y64 = _np_forward(orc, p, f)
-    assert np.max(np.abs(y32 - y64)) < 1e-4 * (1 + np.abs(y64).max())
+    y32, bound = orc.mlp_forward_bound(p, f)
+    mu, isd, W1, b1, W2, b2, w3, b3 = orc.mlp_unpack(np.asarray(p, np.float64))
+    X = ((f - mu.astype(np.float32)) * isd.astype(np.float32)).astype(np.float16).astype(np.float64)
+    P1 = X @ W1.T + b1
+    H1 = np.minimum(np.maximum(P1, 0.0), 65504.0).astype(np.float16).astype(np.float64)
+    H2 = np.maximum(H1 @ W2.T + b2, 0.0)
+    y64 = H2 @ w3 + b3[0]
+    assert np.all(np.abs(y32.astype(np.float64) - y64) <= bound)
+    assert np.median(bound) < 1e-3 * (1 + np.abs(y64).max())
 
 
 def test_mlp_backward_matches_finite_differences(orc):
