@@ -54,7 +54,7 @@ L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one force-kernel launch on
 # this workload, from the capture summarised in profiles/ (None until taken
 # on the current kernel).
-FORCE_TRAFFIC_BYTES = 619_106_560  # 587.17 MB read + 31.93 MB written (k_force, --set full)
+FORCE_TRAFFIC_BYTES = 600_969_472  # 569.35 MB read + 31.62 MB written (k_force, --set full)
 
 
 def parse():
