@@ -280,8 +280,11 @@ __global__ void __launch_bounds__(kThreads) k_keys(const double *__restrict__ x,
 // ranks its keys in input order (warp match for lanes, shared counters for
 // warps and rounds).
 // ---------------------------------------------------------------------------
+#ifndef AFD_SORT_ROUNDS
+#define AFD_SORT_ROUNDS 16  // rounds of 256 keys per sort tile
+#endif
 constexpr int kSortThreads = 256;
-constexpr int kSortRounds = 16;
+constexpr int kSortRounds = AFD_SORT_ROUNDS;
 constexpr int kSortTile = kSortThreads * kSortRounds;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortMaxPasses = 10;  // 8 key bytes + up to 2 bytes of system id
@@ -568,6 +571,34 @@ __device__ __forceinline__ int64_t lower_bound_key(const uint64_t *K, int64_t lo
   return lo;
 }
 
+// The same position, found by galloping from lo (first index with K >= v in
+// [lo, hi)): cells are mostly small, so the bound is near lo and the probes
+// K[lo + 1], K[lo + 3], K[lo + 7], ... stay in a few cache lines before the
+// binary search over the last doubling.
+__device__ __forceinline__ int64_t gallop_up(const uint64_t *K, int64_t lo, int64_t hi, uint64_t v) {
+  int64_t step = 1, prev = lo;
+  while (lo < hi && K[lo] < v) {
+    prev = lo + 1;
+    lo = lo + step < hi ? lo + step : hi;
+    step <<= 1;
+  }
+  return lower_bound_key(K, prev, lo, v);
+}
+
+// The first index s in [lo, hi) with K[s] >= v, galloping down from hi - 1
+// (a parent cell usually starts a few particles before hi).
+__device__ __forceinline__ int64_t gallop_down(const uint64_t *K, int64_t lo, int64_t hi,
+                                               uint64_t v) {
+  int64_t step = 1, top = hi;
+  int64_t q = hi - 1;
+  while (q >= lo && K[q] >= v) {
+    top = q;
+    q = q - step >= lo ? q - step : lo - 1;
+    step <<= 1;
+  }
+  return lower_bound_key(K, q + 1, top, v);
+}
+
 __global__ void __launch_bounds__(kThreads) k_link_emit(
     const uint64_t *__restrict__ K, const uint8_t *__restrict__ dI, const uint8_t *__restrict__ eI,
     const uint32_t *__restrict__ off, int64_t n, const uint32_t *__restrict__ sys_s,
@@ -587,7 +618,7 @@ __global__ void __launch_bounds__(kThreads) k_link_emit(
     if (l > 0) {
       const int shift = 3 * (kLevels - l);
       const uint64_t P = ki >> shift;
-      end = lower_bound_key(K, i + 1, send, (P + 1) << shift);
+      end = gallop_up(K, i + 1, send, (P + 1) << shift);
     }
     level[id] = (uint32_t)l;
     first[id] = (uint32_t)i;
@@ -600,7 +631,7 @@ __global__ void __launch_bounds__(kThreads) k_link_emit(
       } else {
         const int pshift = 3 * (kLevels - l + 1);
         const uint64_t PP = ki >> pshift;
-        const int64_t s = lower_bound_key(K, sstart, i, PP << pshift);
+        const int64_t s = gallop_down(K, sstart, i, PP << pshift);
         const int ds = dI[s] == 255 ? -1 : (int)dI[s];
         par = off[s] + (uint32_t)((l - 1) - ds - 1);
       }

@@ -492,19 +492,23 @@ __global__ void __launch_bounds__(256) k_compact(CompactArgs a) {
   const uint32_t ms = a.cnt_s[g];
   uint32_t c = a.head_s[g];
   const uint64_t os = a.off_s[g];
+  // each chain's next link is loaded before the current chunk is copied, so
+  // its latency overlaps the copy
   for (uint32_t i0 = 0; i0 < ms; i0 += kChunk) {
     if (!AFD_IN(c, a.cap_s, "compact cell chunk")) return;
+    const uint32_t cn = i0 + kChunk < ms ? a.next_s[c] : kNone;
     const uint32_t nn = min(kChunk, ms - i0);
     for (uint32_t k = lane; k < nn; k += 32)
       if (AFD_IN(os + i0 + k, a.n_spj, "compact spj write"))
         a.spj[os + i0 + k] = a.arena_s[(size_t)c * kChunk + k];
-    if (i0 + kChunk < ms) c = a.next_s[c];
+    c = cn;
   }
   const uint32_t r = a.n_lrec[g];
   c = a.head_l[g];
   uint64_t pos = a.off_e[g];
   for (uint32_t i0 = 0; i0 < r; i0 += kChunk) {
     if (!AFD_IN(c, a.cap_l, "compact leaf chunk")) return;
+    const uint32_t cn = i0 + kChunk < r ? a.next_l[c] : kNone;
     const uint32_t nrec = min(kChunk, r - i0);
     for (uint32_t j0 = 0; j0 < nrec; j0 += 32) {
       const bool on = lane < nrec - j0;
@@ -555,7 +559,7 @@ __global__ void __launch_bounds__(256) k_compact(CompactArgs a) {
       }
       pos += tot;
     }
-    if (i0 + kChunk < r) c = a.next_l[c];
+    c = cn;
   }
 }
 
