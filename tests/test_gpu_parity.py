@@ -601,6 +601,33 @@ def test_half_precision_far_field(env, far, tol):
     g.close()
 
 
+def test_half_far_field_scale_holds_any_mass_unit(env):
+    """The per-group power-of-two scale of the half-precision far field: with
+    every mass multiplied by 2^-60 or 2^+60 the terms M / rs^2 lie far
+    outside FP16's range (2^-24 .. 2^16), yet the scaled terms do not: each
+    group's scale moves by exactly 2^-+60, so the half-precision operands are
+    the unit-mass run's bit for bit, and the forces scale exactly with the
+    masses (every other quantity stays a normal FP32 / FP64 number)."""
+    torch, afd, orc = env
+    p = ics.plummer(30000, 93)
+    kw = dict(n_grp=128, theta=0.6, eps=1.0 / 512)
+    dev = torch.device("cuda:0")
+    x, y, z = (torch.tensor(a, device=dev) for a in (p.x, p.y, p.z))
+    out = {}
+    for k in (0, -60, 60):
+        m = torch.tensor(p.m * 2.0 ** k, device=dev)
+        g = afd.Gravity(afd.Config(multipole=1, far_precision=2, **kw), 0,
+                        torch.cuda.current_stream())
+        acc = torch.zeros(p.n, 4, dtype=torch.float32, device=dev)
+        g.force_all(x, y, z, m, acc, afd.AFD_MAKE_LIST)
+        torch.cuda.synchronize()
+        out[k] = acc.cpu().numpy().astype(np.float64)
+        g.close()
+    assert np.all(np.isfinite(out[0]))
+    for k in (-60, 60):
+        assert np.array_equal(out[k] * 2.0 ** -k, out[0]), k
+
+
 def test_mixed_precision_workload_against_direct_sum(env, capsys):
     """The N = 2^22 Plummer workload with quadrupole superparticles at
     theta = 0.6: FP32, BF16 and FP16 far field, rms and max relative force
