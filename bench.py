@@ -86,6 +86,10 @@ def parse():
                     help="fix the force kernel's block shape and list-chunk size instead of "
                          "timing the six candidates (for profiler runs, where the candidates' "
                          "event timings are not meaningful)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other workloads' summary (batched systems with the learned "
+                         "criterion, the mixed-precision far field, the galaxy), each measured by a "
+                         "child run of this script after the main timing")
     ap.add_argument("--sph", action="store_true",
                     help="instead of the benchmark line: the short-range neighbour walk and "
                          "gather density on the workload's particles, one line per n_grp")
@@ -387,6 +391,54 @@ def run_reference(args, wl):
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
+
+
+def other_configs(args):
+    """The other workloads, each a child run of this script (its own CUDA
+    context) after the main timing, summarised: the 32 batched systems with
+    the learned criterion against the plain form at equal error, the 2^22
+    mixed-precision far field in FP32 / BF16 / FP16, the 2^23 galaxy with
+    quadrupoles."""
+    runs = [("batch32", ["--workload", "batch32", "--steps", "20", "--warmup", "5"]),
+            ("plummer_4m_mixed_fp32", ["--workload", "plummer_4m_mixed", "--far", "0", "--steps",
+                                       "20", "--warmup", "5", "--no-learned"]),
+            ("plummer_4m_mixed_bf16", ["--workload", "plummer_4m_mixed", "--far", "1", "--steps",
+                                       "20", "--warmup", "5", "--no-learned"]),
+            ("plummer_4m_mixed_fp16", ["--workload", "plummer_4m_mixed", "--far", "2", "--steps",
+                                       "20", "--warmup", "5", "--no-learned"]),
+            ("galaxy_8m", ["--workload", "galaxy_8m", "--steps", "12", "--warmup", "4",
+                           "--no-learned"])]
+    out = {}
+    for name, extra in runs:
+        cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--no-cpu-baseline", "--no-e2e",
+               "--no-configs"] + extra
+        t0 = time.perf_counter()
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)
+            lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+            if r.returncode != 0 or not lines:
+                out[name] = {"error": f"rc {r.returncode}: {r.stderr.strip()[-300:]}"}
+                continue
+            d = json.loads(lines[-1])
+        except (subprocess.SubprocessError, ValueError) as e:
+            out[name] = {"error": str(e)[:300]}
+            continue
+        o = {"workload": d["config"]["workload"], "interactions_per_s": d["value"],
+             "ms_per_step": d["ms_per_step"],
+             "ms_per_construction_step": d["ms_per_construction_step"],
+             "ms_per_reuse_step": d["ms_per_reuse_step"],
+             "force_kernel_ms": d["roofline"]["launch_ms"], "clocks": d["clocks"],
+             "wall_s": round(time.perf_counter() - t0, 1)}
+        L = d.get("learned_mac")
+        if L:
+            o["learned"] = {"ms_per_step": L["ms_per_step"],
+                            "speedup_ms_per_step_vs_plain": L["speedup_ms_per_step_vs_plain"],
+                            "rms_rel_err_plain": L["equal_error"]["plain_rms_rel_err"],
+                            "rms_rel_err_learned": L["equal_error"]["learned_rms_rel_err"],
+                            "interactions_plain": L["equal_error"]["plain_interactions"],
+                            "interactions_learned": L["equal_error"]["learned_interactions"]}
+        out[name] = o
+    return out
 
 
 def run_loop(afd, torch, ctx, g, st, *, steps, warmup, batch, R, dt, flush, stream, dev,
@@ -1053,6 +1105,9 @@ def main():
     if not args.no_learned and world == 1 and not wl["quad"]:
         line["learned_mac"] = learned_study(args, wl, afd, torch, np, dev, stream, local, p,
                                             tuned, launch, flush, line)
+    if not args.no_configs and world == 1 and args.workload == "plummer_1m" and args.far is None:
+        g.close()
+        line["configs"] = other_configs(args)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line))
