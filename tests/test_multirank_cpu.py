@@ -123,3 +123,28 @@ def test_group_slices_combine_to_the_whole_system():
         pr.join(timeout=60)
         assert pr.exitcode == 0
     assert [ok for _, ok in out] == [True, True]
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    """bench.py --impl reference launched as the driver launches N > 1 runs
+    (torchrun, two ranks, rendezvous on 127.0.0.1): rank 0 alone times the
+    oracle and prints one line with n_gpus = 2 and the GPU arm's config for
+    two ranks; every rank exits 0."""
+    import json
+    import subprocess
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
+           os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2", "--steps", "1",
+           "--warmup", "0"]
+    out = subprocess.run(cmd, capture_output=True, text=True, cwd=ROOT, timeout=900)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+    assert d["config"] == bench.bench_config(bench.workload("plummer_1m"), 2)
+    assert d["config"]["parallelism"] == "replicas"
