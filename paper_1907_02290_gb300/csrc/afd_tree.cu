@@ -276,10 +276,15 @@ __global__ void __launch_bounds__(kThreads) k_keys(const double *__restrict__ x,
 // order from a counter, count their digits, publish the counts, and find
 // each digit's offset among the preceding tiles by decoupled look-back
 // (a tile adds its predecessors' published counts back to the first
-// inclusive prefix it meets), then scatter their keys stably -- every tile
-// ranks its keys in input order (warp match for lanes, shared counters for
-// warps and rounds).
+// inclusive prefix it meets), then scatter their keys stably: each tile
+// reads its keys once, ranks them in input order (warp match for the lanes
+// of a round, warp-private counters for the rounds, offsets over the warps
+// per digit), places them in sorted order in shared memory and writes them
+// out in runs of equal digits.
 // ---------------------------------------------------------------------------
+#ifndef AFD_SORT_HIST_ATOMIC
+#define AFD_SORT_HIST_ATOMIC 0
+#endif
 #ifndef AFD_SORT_ROUNDS
 #define AFD_SORT_ROUNDS 16  // rounds of 256 keys per sort tile
 #endif
@@ -321,8 +326,12 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist_all(
     for (int p = 0; p < passes; p++) {
       const uint32_t d = !valid ? 256u : p < 8 ? (uint32_t)((key >> (8 * p)) & 255u)
                                                : (sys >> (8 * (p - 8))) & 255u;
+#if AFD_SORT_HIST_ATOMIC
+      if (valid) atomicAdd(&h[p][d], 1u);
+#else
       const unsigned peers = __match_any_sync(0xffffffffu, d);
       if (valid && (peers & lt) == 0u) atomicAdd(&h[p][d], (uint32_t)__popc(peers));
+#endif
     }
   }
   __syncthreads();
@@ -357,98 +366,135 @@ __device__ __forceinline__ uint32_t block_excl_256(uint32_t v, uint32_t *warp_su
   return warp_sums[warp] + inc - v;
 }
 
+// Publishes the tile's count of digit tid and returns the count of that
+// digit in all preceding tiles (decoupled look-back; look[t * 256 + d]).
+__device__ __forceinline__ uint32_t sort_look_back(uint32_t *look, uint32_t tile, uint32_t mine,
+                                                   int *status) {
+  const int tid = threadIdx.x;
+  volatile uint32_t *vl = look;
+  uint32_t excl = 0;
+  if (tile == 0) {
+    vl[tid] = kLookPrefix | mine;
+    return 0;
+  }
+  vl[(size_t)tile * 256 + tid] = kLookAgg | mine;
+  for (int64_t t = (int64_t)tile - 1; t >= 0; t--) {
+    uint32_t w = vl[(size_t)t * 256 + tid];
+    for (uint32_t k = 0; (w & ~kLookValue) == 0u; k++) {
+      if (k == kSpinLimit) {  // give up: the pass's result is wrong, the call fails
+        atomicOr(status, kStSpin);
+        w = kLookPrefix;
+        break;
+      }
+      __nanosleep(32);
+      w = vl[(size_t)t * 256 + tid];
+    }
+    excl += w & kLookValue;
+    if ((w & ~kLookValue) == kLookPrefix) break;
+  }
+  vl[(size_t)tile * 256 + tid] = kLookPrefix | ((excl + mine) & kLookValue);
+  return excl;
+}
+
+// Dynamic shared memory of one pass: the tile's keys, payloads and digits
+// in their sorted order (the warps' digit counters alias the key area
+// before the keys are placed).
+constexpr size_t kSortSmem = (size_t)kSortTile * (sizeof(uint64_t) + sizeof(uint32_t) + 1);
+constexpr int kSortPerWarp = kSortTile / kSortWarps;
+
 // One pass: look[t * 256 + d] are the tiles' look-back words and *ctr the
 // tile counter, both zero at launch; hist the pass's 256 digit counts.
+// Each warp reads a contiguous kSortPerWarp-key run of the tile once into
+// registers and ranks it in input order against warp-private digit
+// counters (a lane's rank among equal digits of its round from a warp
+// match, the round's base from the counter); after the look-back the tile
+// is placed in sorted order in shared memory and written out in runs of
+// equal digits, consecutive threads to consecutive addresses.
 template <bool SYS>
 __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
     const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const uint32_t *__restrict__ sys_of, int64_t n, int shift,
     const uint32_t *__restrict__ hist, uint32_t *look, uint32_t *ctr, int *status) {
+  extern __shared__ __align__(16) unsigned char sort_smem[];
+  uint64_t *skey = reinterpret_cast<uint64_t *>(sort_smem);
+  uint32_t *sval = reinterpret_cast<uint32_t *>(skey + kSortTile);
+  uint8_t *sdig = reinterpret_cast<uint8_t *>(sval + kSortTile);
+  uint32_t *wcnt = reinterpret_cast<uint32_t *>(sort_smem);  // [kSortWarps][256], before placement
   __shared__ uint32_t s_tile;
-  __shared__ uint32_t cnt[256];
-  __shared__ uint32_t gbase[256];
-  __shared__ uint32_t run[256];
-  __shared__ uint32_t wsum[kSortWarps];
-  __shared__ uint32_t wcnt[kSortWarps][256];
+  __shared__ uint32_t gbase[256], lstart[256];
+  __shared__ uint32_t wsum0[kSortWarps], wsum1[kSortWarps];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned lt = (1u << lane) - 1u;
   if (tid == 0) s_tile = atomicAdd(ctr, 1u);
-  cnt[tid] = 0;
-  run[tid] = 0;
+  for (int k = tid; k < kSortWarps * 256; k += kSortThreads) wcnt[k] = 0u;
   __syncthreads();
   const uint32_t tile = s_tile;
-  const int64_t base = (int64_t)tile * kSortTile;
-  // the tile's digit counts
+  const int64_t base = (int64_t)tile * kSortTile + (int64_t)warp * kSortPerWarp + lane;
+  uint64_t key[kSortRounds];
+  uint32_t val[kSortRounds];
+  uint32_t dr[kSortRounds];  // digit (256: no key) << 16 | rank
+#pragma unroll
   for (int r = 0; r < kSortRounds; r++) {
-    const int64_t i = base + (int64_t)r * kSortThreads + tid;
+    const int64_t i = base + r * 32;
     const bool valid = i < n;
-    const uint32_t digit = valid ? sort_digit<SYS>(SYS ? 0ull : kin[i], SYS ? vin[i] : 0u, shift,
-                                                   sys_of)
-                                 : 256u;
-    const unsigned peers = __match_any_sync(0xffffffffu, digit);
-    if (valid && (peers & lt) == 0u) atomicAdd(&cnt[digit], (uint32_t)__popc(peers));
+    key[r] = valid ? kin[i] : 0ull;
+    val[r] = valid ? vin[i] : 0u;
+  }
+#pragma unroll
+  for (int r = 0; r < kSortRounds; r++) {
+    const bool valid = base + r * 32 < n;
+    const uint32_t d = valid ? sort_digit<SYS>(key[r], val[r], shift, sys_of) : 256u;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const int leader = __ffs(peers) - 1;
+    uint32_t before = 0u;
+    if (lane == leader && d < 256u) {
+      before = wcnt[warp * 256 + d];
+      wcnt[warp * 256 + d] = before + (uint32_t)__popc(peers);
+    }
+    before = __shfl_sync(0xffffffffu, before, leader);
+    dr[r] = (d << 16) | (before + (uint32_t)__popc(peers & lt));
+    __syncwarp();
   }
   __syncthreads();
-  // publish, then look back over the preceding tiles (thread tid: digit tid)
-  const uint32_t mine = cnt[tid];
-  volatile uint32_t *vl = look;
-  uint32_t excl = 0;
-  if (tile == 0) {
-    vl[tid] = kLookPrefix | mine;
-  } else {
-    vl[(size_t)tile * 256 + tid] = kLookAgg | mine;
-    for (int64_t t = (int64_t)tile - 1; t >= 0; t--) {
-      uint32_t w = vl[(size_t)t * 256 + tid];
-      for (uint32_t k = 0; (w & ~kLookValue) == 0u; k++) {
-        if (k == kSpinLimit) {  // give up: the pass's result is wrong, the call fails
-          atomicOr(status, kStSpin);
-          w = kLookPrefix;
-          break;
-        }
-        __nanosleep(32);
-        w = vl[(size_t)t * 256 + tid];
-      }
-      excl += w & kLookValue;
-      if ((w & ~kLookValue) == kLookPrefix) break;
-    }
-    vl[(size_t)tile * 256 + tid] = kLookPrefix | ((excl + mine) & kLookValue);
+  // thread tid: digit tid -- the warps' counts become exclusive offsets
+  uint32_t mine = 0u;
+#pragma unroll
+  for (int w = 0; w < kSortWarps; w++) {
+    const uint32_t c = wcnt[w * 256 + tid];
+    wcnt[w * 256 + tid] = mine;
+    mine += c;
   }
-  gbase[tid] = block_excl_256(hist[tid], wsum) + excl;
+  const uint32_t excl = sort_look_back(look, tile, mine, status);
+  gbase[tid] = block_excl_256(hist[tid], wsum0) + excl;
+  lstart[tid] = block_excl_256(mine, wsum1);
   __syncthreads();
-  // stable scatter, round by round in input order
+  // each key's place in the tile's sorted order
+#pragma unroll
   for (int r = 0; r < kSortRounds; r++) {
-    const int64_t i = base + (int64_t)r * kSortThreads + tid;
-    const bool valid = i < n;
-    const uint64_t key = valid ? kin[i] : 0ull;
-    const uint32_t val = valid ? vin[i] : 0u;
-    const uint32_t digit = valid ? sort_digit<SYS>(key, val, shift, sys_of) : 256u;
+    const uint32_t d = dr[r] >> 16;
+    if (d < 256u) dr[r] = (d << 16) | (lstart[d] + wcnt[warp * 256 + d] + (dr[r] & 0xffffu));
+  }
+  __syncthreads();  // the counters' area now takes the keys
 #pragma unroll
-    for (int w = 0; w < kSortWarps; w++) wcnt[w][tid] = 0;
-    __syncthreads();
-    const unsigned peers = __match_any_sync(0xffffffffu, digit);
-    const uint32_t lrank = __popc(peers & lt);
-    if (valid && lane == __ffs(peers) - 1) wcnt[warp][digit] = __popc(peers);
-    __syncthreads();
-    {
-      uint32_t b = run[tid];
-#pragma unroll
-      for (int w = 0; w < kSortWarps; w++) {
-        const uint32_t c = wcnt[w][tid];
-        wcnt[w][tid] = b;
-        b += c;
-      }
-      run[tid] = b;
+  for (int r = 0; r < kSortRounds; r++) {
+    const uint32_t d = dr[r] >> 16;
+    if (d < 256u) {
+      const uint32_t p = dr[r] & 0xffffu;
+      skey[p] = key[r];
+      sval[p] = val[r];
+      sdig[p] = (uint8_t)d;
     }
-    __syncthreads();
-    if (valid) {
-      const uint32_t pos = gbase[digit] + wcnt[warp][digit] + lrank;
-      kout[pos] = key;
-      vout[pos] = val;
-    }
-    __syncthreads();
+  }
+  __syncthreads();
+  const int64_t rem = n - (int64_t)tile * kSortTile;
+  const int cnt = rem < kSortTile ? (int)rem : kSortTile;
+  for (int j = tid; j < cnt; j += kSortThreads) {
+    const uint32_t d = sdig[j];
+    const uint32_t pos = gbase[d] + ((uint32_t)j - lstart[d]);
+    kout[pos] = skey[j];
+    vout[pos] = sval[j];
   }
 }
-
 // ---------------------------------------------------------------------------
 // Reorder (Section 4.3 step 3): gather the caller-order FP64 data into Morton
 // order, and split positions into FP32 hi/lo pairs (hi = RN(x), lo =
@@ -1162,6 +1208,20 @@ int launch_sort(afd_ctx *c, int64_t n) {
   if (!per_pass &&
       cudaMemsetAsync(look, 0, sizeof(uint32_t) * look_words * slices, c->stream) != cudaSuccess)
     return AFD_ERR_CUDA;
+  const size_t sort_smem = kSortSmem;
+  {
+    static bool attr_set[8] = {false, false, false, false, false, false, false, false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 8 || !attr_set[dev]) {
+      if (cudaFuncSetAttribute(k_sort_pass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kSortSmem) != cudaSuccess ||
+          cudaFuncSetAttribute(k_sort_pass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kSortSmem) != cudaSuccess)
+        return AFD_ERR_CUDA;
+      if (dev >= 0 && dev < 8) attr_set[dev] = true;
+    }
+  }
   {
     const int64_t want = (n + kSortThreads - 1) / kSortThreads;
     const unsigned nb = (unsigned)(want < 152 * 4 ? want : 152 * 4);
@@ -1178,10 +1238,10 @@ int launch_sort(afd_ctx *c, int64_t n) {
       return AFD_ERR_CUDA;
     uint32_t *ctr = lk + (size_t)256 * num_tiles;
     if (sys)
-      k_sort_pass<true><<<num_tiles, kSortThreads, 0, c->stream>>>(
+      k_sort_pass<true><<<num_tiles, kSortThreads, sort_smem, c->stream>>>(
           ka, va, kb, vb, sys_of, n, shift, hist + 256 * pass, lk, ctr, ptr<int>(c->status));
     else
-      k_sort_pass<false><<<num_tiles, kSortThreads, 0, c->stream>>>(
+      k_sort_pass<false><<<num_tiles, kSortThreads, sort_smem, c->stream>>>(
           ka, va, kb, vb, sys_of, n, shift, hist + 256 * pass, lk, ctr, ptr<int>(c->status));
     c->launches++;
     AFD_TRY(ck());
