@@ -282,9 +282,6 @@ __global__ void __launch_bounds__(kThreads) k_keys(const double *__restrict__ x,
 // per digit), places them in sorted order in shared memory and writes them
 // out in runs of equal digits.
 // ---------------------------------------------------------------------------
-#ifndef AFD_SORT_HIST_ATOMIC
-#define AFD_SORT_HIST_ATOMIC 0
-#endif
 #ifndef AFD_SORT_ROUNDS
 #define AFD_SORT_ROUNDS 16  // rounds of 256 keys per sort tile
 #endif
@@ -307,16 +304,14 @@ __device__ __forceinline__ uint32_t sort_digit(uint64_t key, uint32_t val, int s
 }
 
 // Digit counts of every pass: hist[p * 256 + d], pass p < 8 the key's byte
-// p, passes 8, 9 the bytes of the system id. Counts of equal digits in a
-// warp are added by one lane.
+// p, passes 8, 9 the bytes of the system id; block counts in shared memory
+// (one shared atomic per key and pass), then added to the global counts.
 __global__ void __launch_bounds__(kSortThreads) k_sort_hist_all(
     const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
     const uint32_t *__restrict__ sys_of, int64_t n, int passes, uint32_t *__restrict__ hist) {
   __shared__ uint32_t h[kSortMaxPasses][256];
   for (int k = threadIdx.x; k < kSortMaxPasses * 256; k += kSortThreads) (&h[0][0])[k] = 0;
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
   const int64_t stride = (int64_t)gridDim.x * kSortThreads;
   for (int64_t b = (int64_t)blockIdx.x * kSortThreads; b < n; b += stride) {
     const int64_t i = b + threadIdx.x;
@@ -326,12 +321,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist_all(
     for (int p = 0; p < passes; p++) {
       const uint32_t d = !valid ? 256u : p < 8 ? (uint32_t)((key >> (8 * p)) & 255u)
                                                : (sys >> (8 * (p - 8))) & 255u;
-#if AFD_SORT_HIST_ATOMIC
       if (valid) atomicAdd(&h[p][d], 1u);
-#else
-      const unsigned peers = __match_any_sync(0xffffffffu, d);
-      if (valid && (peers & lt) == 0u) atomicAdd(&h[p][d], (uint32_t)__popc(peers));
-#endif
     }
   }
   __syncthreads();
@@ -720,6 +710,29 @@ __device__ __forceinline__ int n_children(const uint32_t *child, uint32_t c) {
   return k;
 }
 
+#ifndef AFD_MOM_ACQREL
+#define AFD_MOM_ACQREL 1
+#endif
+// A child's arrival at its parent: one more on the parent's counter; returns
+// the count before. With AFD_MOM_ACQREL the addition itself orders memory at
+// GPU scope: release for the writes that precede it (the child's sums,
+// written by this lane or by lanes of its warp before the warp's barrier),
+// acquire for the lane that completes the parent (it, and after the warp's
+// barrier the lanes that sum the parent, see every child's sums). Otherwise
+// a fence on either side of a relaxed addition does the same.
+__device__ __forceinline__ unsigned arrive_at(unsigned *ctr) {
+#if AFD_MOM_ACQREL
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(ctr) : "memory");
+  return old;
+#else
+  __threadfence();
+  const unsigned old = atomicAdd(ctr, 1u);
+  __threadfence();
+  return old;
+#endif
+}
+
 __device__ void finish_cell(const MomArgs &a, uint32_t c, double M, const double S[3], bool leaf) {
   const double *root = a.root + (a.sys_s ? 4 * (size_t)a.sys_s[a.first[c]] : 0);
   double g[3];
@@ -801,6 +814,7 @@ __global__ void __launch_bounds__(kThreads) k_moments_sums(MomArgs a) {
       // the products m x, m y, m z were rounded by the reorder (full warps);
       // here only the ordered sums run on the leaf's lane
       const double *mx = a.mxyz, *my = a.mxyz + a.n_part, *mz = a.mxyz + 2 * a.n_part;
+#pragma unroll 4
       for (uint32_t k = f; k < e; k++) {
         M = __dadd_rn(M, a.ms[k]);
         S[0] = __dadd_rn(S[0], mx[k]);
@@ -814,22 +828,23 @@ __global__ void __launch_bounds__(kThreads) k_moments_sums(MomArgs a) {
   // The warp climbs together: each lane reports its cell at the parent; the
   // parents this warp completes are summed four lanes each (M, S_x, S_y,
   // S_z: one ordered chain over the octants per lane), eight at a time.
+  uint32_t pc = climbing ? a.parent[c] : kNone;  // parent of the climbing cell
   while (__any_sync(0xffffffffu, climbing)) {
-    uint32_t p = kNone;
     bool won = false;
     if (climbing) {
-      p = a.parent[c];
+      const uint32_t p = pc;
       if (p == kNone || !AFD_IN(p, a.n_cells, "moments parent")) {
         climbing = false;
       } else {
-        __threadfence();
-        const unsigned old = atomicAdd(&a.arrive[p], 1u);
+        const unsigned old = arrive_at(&a.arrive[p]);
         won = (int)old == n_children(a.child, p) - 1;
         climbing = won;
-        if (won) c = p;
+        if (won) {
+          c = p;
+          pc = a.parent[p];  // for the next level, in flight while the sums run
+        }
       }
     }
-    __threadfence();
     __syncwarp();  // the winners' view of the children reaches the lanes summing them
     unsigned wm = __ballot_sync(0xffffffffu, won);
     while (wm) {
@@ -879,21 +894,23 @@ __global__ void __launch_bounds__(kThreads) k_moments_quad(MomArgs a) {
     if (e > f && !AFD_IN(e - 1, a.n_part, "quad leaf range")) climbing = false;
     else leaf_quad(a, c);
   }
+  uint32_t pc = climbing ? a.parent[c] : kNone;
   while (__any_sync(0xffffffffu, climbing)) {
     bool won = false;
     if (climbing) {
-      const uint32_t p = a.parent[c];
+      const uint32_t p = pc;
       if (p == kNone || !AFD_IN(p, a.n_cells, "quad parent")) {
         climbing = false;
       } else {
-        __threadfence();
-        const unsigned old = atomicAdd(&a.arrive[p], 1u);
+        const unsigned old = arrive_at(&a.arrive[p]);
         won = (int)old == n_children(a.child, p) - 1;
         climbing = won;
-        if (won) c = p;
+        if (won) {
+          c = p;
+          pc = a.parent[p];
+        }
       }
     }
-    __threadfence();
     __syncwarp();
     unsigned wm = __ballot_sync(0xffffffffu, won);
     while (wm) {
