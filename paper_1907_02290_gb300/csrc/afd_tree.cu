@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "afd_internal.cuh"
+#include "afd_split.cuh"
 
 namespace afd {
 namespace {
@@ -488,12 +489,11 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
 // ---------------------------------------------------------------------------
 // Reorder (Section 4.3 step 3): gather the caller-order FP64 data into Morton
 // order, and split positions into FP32 hi/lo pairs (hi = RN(x), lo =
-// RN(x - hi)) for the force kernel's group-relative coordinates.
+// RN(x - hi)) for the force kernel's group-relative coordinates. The
+// conversions run in integer arithmetic (afd_split.cuh), which leaves GB300's
+// narrow FP64 unit the three mass products.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void split2(double v, float &h, float &l) {
-  h = __double2float_rn(v);
-  l = __double2float_rn(__dsub_rn(v, (double)h));
-}
+__device__ __forceinline__ void split2(double v, float &h, float &l) { afd_split2(v, &h, &l); }
 
 __global__ void __launch_bounds__(kThreads) k_reorder(
     const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
@@ -505,7 +505,8 @@ __global__ void __launch_bounds__(kThreads) k_reorder(
   if (k >= n) return;
   const uint32_t i = perm[k];
   const double vx = x[i], vy = y[i], vz = z[i], vm = m[i];
-  if (!isfinite(vx) || !isfinite(vy) || !isfinite(vz) || !isfinite(vm))
+  if (!afd_finite_bits(vx) || !afd_finite_bits(vy) || !afd_finite_bits(vz) ||
+      !afd_finite_bits(vm))
     atomicOr(status, kStNonFinite);
   xs[k] = vx;
   ys[k] = vy;
@@ -519,7 +520,7 @@ __global__ void __launch_bounds__(kThreads) k_reorder(
   split2(vx, hx, lx);
   split2(vy, hy, ly);
   split2(vz, hz, lz);
-  jhi[k] = make_float4(hx, hy, hz, __double2float_rn(vm));
+  jhi[k] = make_float4(hx, hy, hz, afd_round_f32(vm));
   jlo[k] = make_float4(lx, ly, lz, 0.0f);
 }
 
@@ -759,7 +760,7 @@ __device__ void finish_cell(const MomArgs &a, uint32_t c, double M, const double
   }
   float h[3], lo[3];
   for (int d = 0; d < 3; d++) split2(g[d], h[d], lo[d]);
-  a.s_hi[c] = make_float4(h[0], h[1], h[2], __double2float_rn(M));
+  a.s_hi[c] = make_float4(h[0], h[1], h[2], afd_round_f32(M));
   a.s_lo[c] = make_float4(lo[0], lo[1], lo[2], 0.0f);
   const float sd = ldexpf(__double2float_rn(root[3]), -(int)a.level[c]);
   a.node_f[c] = make_float4(h[0], h[1], h[2], __fmul_rn(sd, sd));
@@ -836,8 +837,10 @@ __global__ void __launch_bounds__(kThreads) k_moments_sums(MomArgs a) {
       if (p == kNone || !AFD_IN(p, a.n_cells, "moments parent")) {
         climbing = false;
       } else {
+        // the child table is read-only here: its loads need not wait for the arrival
+        const int nch = n_children(a.child, p);
         const unsigned old = arrive_at(&a.arrive[p]);
-        won = (int)old == n_children(a.child, p) - 1;
+        won = (int)old == nch - 1;
         climbing = won;
         if (won) {
           c = p;
@@ -902,8 +905,10 @@ __global__ void __launch_bounds__(kThreads) k_moments_quad(MomArgs a) {
       if (p == kNone || !AFD_IN(p, a.n_cells, "quad parent")) {
         climbing = false;
       } else {
+        // the child table is read-only here: its loads need not wait for the arrival
+        const int nch = n_children(a.child, p);
         const unsigned old = arrive_at(&a.arrive[p]);
-        won = (int)old == n_children(a.child, p) - 1;
+        won = (int)old == nch - 1;
         climbing = won;
         if (won) {
           c = p;
