@@ -360,8 +360,8 @@ void afd_destroy(afd_ctx *c) {
                     &c->hx, &c->hy, &c->hz, &c->hm, &c->hacc, &c->sys_off_d,
                     &c->sys_grp_d, &c->sys_of, &c->sys_s, &c->root_tiles, &c->g_root,
                     &c->mac_w, &c->amag, &c->amag_s, &c->g_amin, &c->mac_cnt,
-                    &c->band_cnt, &c->band_off, &c->l_nrec, &c->l_head_s, &c->l_head_l,
-                    &c->arena_s, &c->arena_l, &c->next_s, &c->next_l, &c->arena_cur,
+                    &c->band_cnt, &c->band_off, &c->l_nrec,
+                    &c->arena_s, &c->arena_l, &c->hdr_s, &c->hdr_l, &c->arena_cur,
                     &c->m_ehi, &c->m_elo, &c->m_shi, &c->m_slo, &c->let_mark,
                     &c->let_cnt, &c->let_off, &c->c_tbox, &c->nbr_arrive, &c->g_sbox,
                     &c->nbr_cnt, &c->nbr_off, &c->nbr, &c->nbr_blk, &c->nbr_seg_cnt,

@@ -218,8 +218,8 @@ struct afd_ctx {
   bool have_nbr = false;
   // walk record arena: per group leaf-record count and chunk-chain heads;
   // chunks of cell ids / leaf records, chain links, cursors (capacity in chunks)
-  afd::DevBuf l_nrec, l_head_s, l_head_l;
-  afd::DevBuf arena_s, arena_l, next_s, next_l, arena_cur;
+  afd::DevBuf l_nrec;
+  afd::DevBuf arena_s, arena_l, hdr_s, hdr_l, arena_cur;
   uint32_t arena_cap_s = 0, arena_cap_l = 0;
   // limits of the walks' bounded loops (afd_set_walk_limits; 0: defaults)
   uint32_t walk_iter_cap = 0, walk_arena_max = 0;

@@ -67,9 +67,12 @@ struct WalkArgs {
   const uint4 *block;
   float theta2;
   uint32_t *cnt_e, *cnt_s, *gself, *n_lrec;
-  // record arena: cell ids (SPJ stream) and leaf records (EPJ stream)
-  uint32_t *arena_s, *next_s, *next_l, *head_s, *head_l, *cursor;
+  // record arena: cell ids (SPJ stream) and leaf records (EPJ stream), and
+  // per chunk its header (group, index of its first record in the group's
+  // stream, output position of that record in the group's list)
+  uint32_t *arena_s, *cursor;
   uint2 *arena_l;
+  uint4 *hdr_s, *hdr_l;
   uint32_t cap_s, cap_l;
   int *status;
   uint32_t iter_cap;   // warp steps per group (or item) before the walk gives up
@@ -167,11 +170,15 @@ struct RecStream {
 
 // Append the records of the lanes with `on`, in lane order. A chunk index at
 // or above the capacity is not written (the cursor still counts it, which
-// tells the host how large the arena must be).
+// tells the host how large the arena must be). The lane whose record opens a
+// new chunk writes the chunk's header hv: (group, the record's index in the
+// group's stream, its output position in the group's list), so that the
+// compaction places every chunk on its own, without following the group's
+// chunks in order.
 template <class T>
-__device__ __forceinline__ void rec_put(RecStream &st, bool on, T rec, T *arena, uint32_t *next,
-                                        uint32_t *cursor, uint32_t cap, uint32_t *head,
-                                        int lane, unsigned lt) {
+__device__ __forceinline__ void rec_put(RecStream &st, bool on, T rec, T *arena, uint4 *hdr,
+                                        uint4 hv, uint32_t *cursor, uint32_t cap, int lane,
+                                        unsigned lt) {
   const unsigned m = __ballot_sync(0xffffffffu, on);
   const uint32_t n = __popc(m);
   if (n == 0) return;
@@ -181,8 +188,6 @@ __device__ __forceinline__ void rec_put(RecStream &st, bool on, T rec, T *arena,
     if (lane == 0) {
       const uint32_t c = atomicAdd(cursor, 1u);
       nc = c < cap ? c : kNone;
-      if (st.chunk == kNone) *head = nc;
-      else next[st.chunk] = nc;
     }
     nc = __shfl_sync(0xffffffffu, nc, 0);
   }
@@ -192,6 +197,7 @@ __device__ __forceinline__ void rec_put(RecStream &st, bool on, T rec, T *arena,
       if (st.chunk != kNone) arena[(size_t)st.chunk * kChunk + p] = rec;
     } else if (nc != kNone) {
       arena[(size_t)nc * kChunk + (p - kChunk)] = rec;
+      if (p == kChunk) hdr[nc] = hv;
     }
   }
   if (grow) {
@@ -282,7 +288,11 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
       const bool acc = lane < f && dec == kAccept;
       const bool lf = lane < f && dec == kLeaf;
       const unsigned am = __ballot_sync(0xffffffffu, acc);
-      rec_put(rs, acc, e.x, a.arena_s, a.next_s, a.cursor, a.cap_s, a.head_s + g, lane, lt);
+      {
+        const uint32_t ri = (uint32_t)ns + __popc(am & lt);  // record index = list position
+        rec_put(rs, acc, e.x, a.arena_s, a.hdr_s, make_uint4((uint32_t)g, ri, ri, 0u), a.cursor,
+                a.cap_s, lane, lt);
+      }
       ns += __popc(am);
       const uint32_t lfirst = lf ? e.x : 0u, lcnt = lf ? (e.y & 0x3fffffffu) : 0u;
       uint32_t inc = lcnt;
@@ -296,9 +306,11 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
       // group's particles follow it contiguously)
       if (lf && gfirst >= lfirst && gfirst - lfirst < lcnt)
         self_pos = (uint32_t)(ne + (inc - lcnt) + (gfirst - lfirst)) + 1u;
-      rec_put(rl, lf, make_uint2(lfirst, lcnt), a.arena_l, a.next_l, a.cursor + 1, a.cap_l,
-              a.head_l + g, lane, lt);
-      nl += __popc(__ballot_sync(0xffffffffu, lf));
+      const unsigned lm = __ballot_sync(0xffffffffu, lf);
+      rec_put(rl, lf, make_uint2(lfirst, lcnt), a.arena_l, a.hdr_l,
+              make_uint4((uint32_t)g, nl + __popc(lm & lt), (uint32_t)(ne + (inc - lcnt)), 0u),
+              a.cursor + 1, a.cap_l, lane, lt);
+      nl += __popc(lm);
       ne += tot;
       if (!om) {  // nothing open among the top entries: all emitted
         sp -= nv;
@@ -432,8 +444,6 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
       a.cnt_s[g] = (uint32_t)ns;
       a.n_lrec[g] = nl;
       if (!NBR) a.gself[g] = self_pos;
-      if (ns == 0) a.head_s[g] = kNone;
-      if (nl == 0) a.head_l[g] = kNone;
     }
     __syncwarp();
   }
@@ -464,15 +474,19 @@ __global__ void k_interactions(int64_t n_groups, const uint32_t *__restrict__ g_
   if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
 }
 
-// The CSR lists from the record arena, one warp per group: cell ids copied,
-// leaf records expanded into their particles' Morton positions.
+// The CSR lists from the record arena, chunk by chunk: cell ids copied,
+// leaf records expanded into their particles' Morton positions. A chunk's
+// header gives its group, the index of its first record in the group's
+// stream (so the number of its records) and that record's output position,
+// so the chunks are placed independently of one another, in any order.
 struct CompactArgs {
-  int64_t n_groups;
-  const uint32_t *cnt_s, *n_lrec, *head_s, *head_l, *next_s, *next_l, *arena_s;
+  const uint32_t *cnt_s, *n_lrec, *arena_s;
   const uint2 *arena_l;
+  const uint4 *hdr_s, *hdr_l;
   const uint64_t *off_e, *off_s;
   uint32_t *epj, *spj;
-  uint32_t cap_s, cap_l;  // read only by the self-checking build
+  uint32_t nch_s, nch_l;  // chunks in use
+  int64_t n_groups;       // read only by the self-checking build
   uint64_t n_epj, n_spj;
 };
 
@@ -485,34 +499,63 @@ struct CompactArgs {
 // coalesced whatever the mix of sizes.
 constexpr uint32_t kBigRec = 64;
 
+// Each warp takes consecutive chunks, kCompactBatch cell-id chunks (warps
+// [0, ceil(nch_s / kCompactBatch))) or kCompactBatchL leaf-record chunks
+// (the next warps; a leaf chunk expands to about sixteen times as many
+// entries). Lane j loads chunk j's header and its group's count and list
+// offset (one coalesced load and two gathers for the batch), then the warp
+// copies or expands the chunks one after the other.
+constexpr uint32_t kCompactBatch = 32, kCompactBatchL = 4;
+
 __global__ void __launch_bounds__(256) k_compact(CompactArgs a) {
-  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (g >= a.n_groups) return;
-  const uint32_t ms = a.cnt_s[g];
-  uint32_t c = a.head_s[g];
-  const uint64_t os = a.off_s[g];
-  // each chain's next link is loaded before the current chunk is copied, so
-  // its latency overlaps the copy
-  for (uint32_t i0 = 0; i0 < ms; i0 += kChunk) {
-    if (!AFD_IN(c, a.cap_s, "compact cell chunk")) return;
-    const uint32_t cn = i0 + kChunk < ms ? a.next_s[c] : kNone;
-    const uint32_t nn = min(kChunk, ms - i0);
-    for (uint32_t k = lane; k < nn; k += 32)
-      if (AFD_IN(os + i0 + k, a.n_spj, "compact spj write"))
-        a.spj[os + i0 + k] = a.arena_s[(size_t)c * kChunk + k];
-    c = cn;
+  const int64_t nb_s = ((int64_t)a.nch_s + kCompactBatch - 1) / kCompactBatch;
+  if (w < nb_s) {
+    const int64_t c0 = w * kCompactBatch;
+    const int64_t cl = c0 + lane;
+    uint32_t nn = 0u;
+    uint64_t o = 0;
+    if (cl < (int64_t)a.nch_s) {
+      const uint4 h = a.hdr_s[cl];
+      if (AFD_IN(h.x, a.n_groups, "compact cell chunk group")) {
+        const uint32_t ms = a.cnt_s[h.x];
+        nn = h.y < ms ? min(kChunk, ms - h.y) : 0u;
+        o = a.off_s[h.x] + h.z;
+      }
+    }
+    const int nc = (int)min((int64_t)kCompactBatch, (int64_t)a.nch_s - c0);
+#pragma unroll 2
+    for (int j = 0; j < nc; j++) {
+      const uint32_t nj = __shfl_sync(0xffffffffu, nn, j);
+      const uint64_t oj = __shfl_sync(0xffffffffu, o, j);
+      const uint32_t *src = a.arena_s + (size_t)(c0 + j) * kChunk;
+      for (uint32_t k = lane; k < nj; k += 32)
+        if (AFD_IN(oj + k, a.n_spj, "compact spj write")) a.spj[oj + k] = src[k];
+    }
+    return;
   }
-  const uint32_t r = a.n_lrec[g];
-  c = a.head_l[g];
-  uint64_t pos = a.off_e[g];
-  for (uint32_t i0 = 0; i0 < r; i0 += kChunk) {
-    if (!AFD_IN(c, a.cap_l, "compact leaf chunk")) return;
-    const uint32_t cn = i0 + kChunk < r ? a.next_l[c] : kNone;
-    const uint32_t nrec = min(kChunk, r - i0);
+  const int64_t c0 = (w - nb_s) * kCompactBatchL;
+  if (c0 >= (int64_t)a.nch_l) return;
+  const int64_t cl = c0 + lane;
+  uint32_t nr = 0u;
+  uint64_t po = 0;
+  if (lane < (int)kCompactBatchL && cl < (int64_t)a.nch_l) {
+    const uint4 h = a.hdr_l[cl];
+    if (AFD_IN(h.x, a.n_groups, "compact leaf chunk group")) {
+      const uint32_t r = a.n_lrec[h.x];
+      nr = h.y < r ? min(kChunk, r - h.y) : 0u;
+      po = a.off_e[h.x] + h.z;
+    }
+  }
+  const int nc = (int)min((int64_t)kCompactBatchL, (int64_t)a.nch_l - c0);
+  for (int jc = 0; jc < nc; jc++) {
+    const uint32_t nrec = __shfl_sync(0xffffffffu, nr, jc);
+    uint64_t pos = __shfl_sync(0xffffffffu, po, jc);
+    const uint2 *recs = a.arena_l + (size_t)(c0 + jc) * kChunk;
     for (uint32_t j0 = 0; j0 < nrec; j0 += 32) {
       const bool on = lane < nrec - j0;
-      const uint2 rec = on ? a.arena_l[(size_t)c * kChunk + j0 + lane] : make_uint2(0u, 0u);
+      const uint2 rec = on ? recs[j0 + lane] : make_uint2(0u, 0u);
       uint32_t inc = rec.y;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -529,9 +572,9 @@ __global__ void __launch_bounds__(256) k_compact(CompactArgs a) {
         const int src = __ffs(bm) - 1;
         bm &= bm - 1;
         const uint32_t f0 = __shfl_sync(0xffffffffu, rec.x, src);
-        const uint32_t c0 = __shfl_sync(0xffffffffu, rec.y, src);
+        const uint32_t n0 = __shfl_sync(0xffffffffu, rec.y, src);
         const uint64_t o0 = pos + __shfl_sync(0xffffffffu, ex, src);
-        for (uint32_t k = lane; k < c0; k += 32)
+        for (uint32_t k = lane; k < n0; k += 32)
           if (AFD_IN(o0 + k, a.n_epj, "compact epj write")) a.epj[o0 + k] = f0 + k;
       }
       // the others: lane t of each pass over their entries finds its record
@@ -559,7 +602,6 @@ __global__ void __launch_bounds__(256) k_compact(CompactArgs a) {
       }
       pos += tot;
     }
-    c = cn;
   }
 }
 
@@ -640,8 +682,6 @@ int run_walk(afd_ctx *c, WalkArgs &a, int mode, WalkOut &o, int64_t ng) {
   a.cnt_e = o.cnt_e;
   a.cnt_s = o.cnt_s;
   a.n_lrec = ptr<uint32_t>(c->l_nrec);
-  a.head_s = ptr<uint32_t>(c->l_head_s);
-  a.head_l = ptr<uint32_t>(c->l_head_l);
   a.cursor = ptr<uint32_t>(c->arena_cur);
   a.status = ptr<int>(c->status);
   a.iter_cap = c->walk_iter_cap > 0 ? c->walk_iter_cap : (uint32_t)(2 * c->n_cells + 64);
@@ -654,15 +694,16 @@ int run_walk(afd_ctx *c, WalkArgs &a, int mode, WalkOut &o, int64_t ng) {
   a.queue = ptr<unsigned long long>(c->u64acc) + 4;
   unsigned long long *inter = ptr<unsigned long long>(c->u64acc) + 1;
   uint64_t *pin = static_cast<uint64_t *>(c->pinned);
+  uint32_t need_s = 0, need_l = 0;  // chunks the walk took from each stream
   for (int attempt = 0;; attempt++) {
     if ((st = reserve(c->arena_s, sizeof(uint32_t) * kChunk * (size_t)c->arena_cap_s))) return st;
     if ((st = reserve(c->arena_l, sizeof(uint2) * kChunk * (size_t)c->arena_cap_l))) return st;
-    if ((st = reserve(c->next_s, sizeof(uint32_t) * (size_t)c->arena_cap_s))) return st;
-    if ((st = reserve(c->next_l, sizeof(uint32_t) * (size_t)c->arena_cap_l))) return st;
+    if ((st = reserve(c->hdr_s, sizeof(uint4) * (size_t)c->arena_cap_s))) return st;
+    if ((st = reserve(c->hdr_l, sizeof(uint4) * (size_t)c->arena_cap_l))) return st;
     a.arena_s = ptr<uint32_t>(c->arena_s);
     a.arena_l = ptr<uint2>(c->arena_l);
-    a.next_s = ptr<uint32_t>(c->next_s);
-    a.next_l = ptr<uint32_t>(c->next_l);
+    a.hdr_s = ptr<uint4>(c->hdr_s);
+    a.hdr_l = ptr<uint4>(c->hdr_l);
     a.cap_s = c->arena_cap_s;
     a.cap_l = c->arena_cap_l;
     if (cudaMemsetAsync(c->arena_cur.p, 0, 2 * sizeof(uint32_t), c->stream) != cudaSuccess ||
@@ -699,7 +740,8 @@ int run_walk(afd_ctx *c, WalkArgs &a, int mode, WalkOut &o, int64_t ng) {
       cudaMemsetAsync(c->status.p, 0, sizeof(int), c->stream);
       return status_to_error(bits);
     }
-    const uint32_t need_s = (uint32_t)(pin[4] & 0xffffffffu), need_l = (uint32_t)(pin[4] >> 32);
+    need_s = (uint32_t)(pin[4] & 0xffffffffu);
+    need_l = (uint32_t)(pin[4] >> 32);
     if (need_s <= c->arena_cap_s && need_l <= c->arena_cap_l) break;
     // the second pass is sized from the cursors: still too small only at the
     // capacity limit
@@ -718,29 +760,30 @@ int run_walk(afd_ctx *c, WalkArgs &a, int mode, WalkOut &o, int64_t ng) {
   k.n_groups = ng;
   k.cnt_s = a.cnt_s;
   k.n_lrec = a.n_lrec;
-  k.head_s = a.head_s;
-  k.head_l = a.head_l;
-  k.next_s = a.next_s;
-  k.next_l = a.next_l;
   k.arena_s = a.arena_s;
   k.arena_l = a.arena_l;
+  k.hdr_s = a.hdr_s;
+  k.hdr_l = a.hdr_l;
   k.off_e = ptr<uint64_t>(*o.off_e);
   k.off_s = ptr<uint64_t>(nbr ? *o.off_e : *o.off_s);  // read, never used, without SPJs
   k.epj = ptr<uint32_t>(*o.epj);
   k.spj = nbr ? nullptr : ptr<uint32_t>(*o.spj);
-  k.cap_s = c->arena_cap_s;
-  k.cap_l = c->arena_cap_l;
+  k.nch_s = nbr ? 0u : need_s;  // the neighbour walk emits no cell ids
+  k.nch_l = need_l;
   k.n_epj = o.n_e;
   k.n_spj = o.n_s;
-  k_compact<<<(unsigned)((ng * 32 + 255) / 256), 256, 0, c->stream>>>(k);
-  c->launches++;
+  const uint64_t warps = ((uint64_t)k.nch_s + kCompactBatch - 1) / kCompactBatch +
+                         ((uint64_t)k.nch_l + kCompactBatchL - 1) / kCompactBatchL;
+  if (warps > 0) {
+    k_compact<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, c->stream>>>(k);
+    c->launches++;
+  }
   return cudaGetLastError() == cudaSuccess ? AFD_OK : AFD_ERR_CUDA;
 }
 
 int walk_scratch(afd_ctx *c, int64_t ng) {
   int st;
-  for (afd::DevBuf *b : {&c->l_nrec, &c->l_head_s, &c->l_head_l})
-    if ((st = reserve(*b, sizeof(uint32_t) * ng))) return st;
+  if ((st = reserve(c->l_nrec, sizeof(uint32_t) * ng))) return st;
   return reserve(c->arena_cur, 2 * sizeof(uint32_t));
 }
 
