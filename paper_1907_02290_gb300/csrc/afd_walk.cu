@@ -14,9 +14,11 @@
 // expansion costs one coalesced load. One pass: each group appends its
 // accepted cell ids and its opened leaves (first particle, count) to two
 // record streams in an arena of 64-record chunks (taken from a global
-// cursor, linked per group); after a scan of the per-group counts a
-// compaction kernel writes the CSR lists -- leaf records expanded into
-// particle indices -- in the same depth-first order. An arena that proves
+// cursor; each chunk's header names its group, its first record's index in
+// the group's stream and that record's position in the group's list); after
+// a scan of the per-group counts a compaction kernel places the chunks
+// independently into the CSR lists -- leaf records expanded into particle
+// indices -- in the same depth-first order. An arena that proves
 // too small is grown to the size the cursors report and the pass repeated.
 //
 // The opening criterion is evaluated in FP32 without contraction: with d the
