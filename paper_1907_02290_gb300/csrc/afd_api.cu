@@ -352,7 +352,7 @@ void afd_destroy(afd_ctx *c) {
                     &c->keys2, &c->perm, &c->perm2, &c->sort_cnt, &c->sort_off, &c->xs, &c->ys,
                     &c->zs, &c->ms, &c->jhi, &c->jlo, &c->lk_d, &c->lk_c, &c->lk_e, &c->lk_cnt,
                     &c->lk_off, &c->c_level, &c->c_first, &c->c_count, &c->c_skip, &c->c_parent,
-                    &c->c_child, &c->c_arrive, &c->c_mass, &c->c_smom, &c->c_com, &c->c_quad,
+                    &c->c_child, &c->c_arrive, &c->leaf_ord, &c->leaf_aux, &c->c_mass, &c->c_smom, &c->c_com, &c->c_quad,
                     &c->s_hi, &c->s_lo, &c->s_q0, &c->s_q1, &c->node_f, &c->node_i, &c->c_block, &c->g_cnt,
                     &c->g_off, &c->g_first, &c->g_count, &c->g_cell, &c->g_box, &c->g_boxf,
                     &c->g_self, &c->u_cnt, &c->u_off, &c->u_info, &c->l_cnt_e,

@@ -170,6 +170,7 @@ struct afd_ctx {
 
   // cells (depth-first pre-order)
   afd::DevBuf c_level, c_first, c_count, c_skip, c_parent, c_child, c_arrive;
+  afd::DevBuf leaf_ord, leaf_aux;  // leaves by particle count, and the bucket counters
   afd::DevBuf c_mass, c_smom, c_com, c_quad;  // f64
   afd::DevBuf s_hi, s_lo, s_q0, s_q1;         // float4 superparticle data
   afd::DevBuf node_f, node_i;                 // walk node data (float4, uint2)
@@ -270,6 +271,7 @@ struct afd_ctx {
   float mac_lo2 = 0.0f, mac_hi2 = 0.0f, mac_tau = 0.0f;
   afd::DevBuf amag, amag_s, g_amin;
   int64_t amag_n = -1;
+  bool leaf_ord_ok = false;      // leaf_ord holds the current tree's leaves
   bool moments_current = false;  // the cell moments match the current positions
   bool q_current = false;       // the cell quadrupoles match the current positions
   bool blocks_current = false;  // the walk's child records match them too

@@ -700,6 +700,8 @@ struct MomArgs {
   float4 *s_hi, *s_lo, *s_q0, *s_q1, *node_f;
   uint2 *node_i;
   uint4 *block;  // child walk records, 8 per cell (null: not written)
+  const uint32_t *leaf_ord;  // leaves by particle count (quadrupole climb only)
+  const uint32_t *n_leaves;  // their number (device)
   int quad_on;
   int64_t n_part;  // particles (read only by the self-checking build)
 };
@@ -709,6 +711,71 @@ __device__ __forceinline__ int n_children(const uint32_t *child, uint32_t c) {
 #pragma unroll
   for (int o = 0; o < 8; o++) k += __ldg(&child[(size_t)c * 8 + o]) != kNone;
   return k;
+}
+
+// Leaves ordered by particle count (buckets: counts 1 .. 31, then 32 or
+// more), so that the lanes of a warp in the quadrupole climb sum leaves of
+// nearly equal length: a leaf's quadrupole is about twenty FP64 operations
+// per particle on one lane, and a warp instruction costs GB300's narrow FP64
+// unit the same whatever its active lanes (2^22 particles: the tree build
+// with quadrupoles 2.97 -> 2.57 ms). The monopole sums keep the cell order:
+// there the neighbouring leaves of a warp read neighbouring particles, and
+// the count order was slower (87 -> 99 us). The order within a bucket is
+// that of the atomic cursors; the moments do not depend on it (every cell's
+// sums run in the definition's order on whichever lane takes the cell). aux[0, 32): the
+// bucket counts, aux[32, 64): the bucket cursors, aux[64]: the number of
+// leaves; all zero at launch.
+constexpr int kLeafBuckets = 32;
+
+__device__ __forceinline__ uint32_t leaf_bucket(uint32_t count) {
+  return count >= (uint32_t)kLeafBuckets ? (uint32_t)kLeafBuckets - 1u
+                                         : (count > 0u ? count - 1u : 0u);
+}
+
+__global__ void __launch_bounds__(kThreads) k_leaf_hist(int64_t nc,
+                                                        const uint32_t *__restrict__ child,
+                                                        const uint32_t *__restrict__ count,
+                                                        uint32_t *__restrict__ aux) {
+  __shared__ uint32_t h[kLeafBuckets];
+  if (threadIdx.x < kLeafBuckets) h[threadIdx.x] = 0u;
+  __syncthreads();
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < nc && n_children(child, (uint32_t)c) == 0) atomicAdd(&h[leaf_bucket(count[c])], 1u);
+  __syncthreads();
+  if (threadIdx.x < kLeafBuckets && h[threadIdx.x] != 0u) {
+    atomicAdd(&aux[threadIdx.x], h[threadIdx.x]);
+    atomicAdd(&aux[2 * kLeafBuckets], h[threadIdx.x]);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_leaf_scatter(int64_t nc,
+                                                           const uint32_t *__restrict__ child,
+                                                           const uint32_t *__restrict__ count,
+                                                           uint32_t *__restrict__ aux,
+                                                           uint32_t *__restrict__ ord) {
+  __shared__ uint32_t off[kLeafBuckets];
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  if (threadIdx.x < 32) {  // exclusive offsets of the buckets
+    const uint32_t v = aux[lane];
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    off[lane] = inc - v;
+  }
+  __syncthreads();
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool leaf = c < nc && n_children(child, (uint32_t)c) == 0;
+  const uint32_t b = leaf ? leaf_bucket(count[c]) : (uint32_t)kLeafBuckets;
+  const unsigned peers = __match_any_sync(0xffffffffu, b);
+  const int leader = __ffs(peers) - 1;
+  uint32_t base = 0u;
+  if (leaf && lane == leader) base = atomicAdd(&aux[kLeafBuckets + b], (uint32_t)__popc(peers));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (leaf) ord[off[b] + base + (uint32_t)__popc(peers & lt)] = (uint32_t)c;
 }
 
 #ifndef AFD_MOM_ACQREL
@@ -890,8 +957,9 @@ __global__ void __launch_bounds__(kThreads) k_moments_sums(MomArgs a) {
 __global__ void __launch_bounds__(kThreads) k_moments_quad(MomArgs a) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  uint32_t c = (uint32_t)t;
-  bool climbing = t < a.n_cells && n_children(a.child, c) == 0;
+  bool climbing = t < (int64_t)*a.n_leaves;
+  uint32_t c = climbing ? a.leaf_ord[t] : 0u;
+  if (climbing && !AFD_IN(c, a.n_cells, "quad leaf")) climbing = false;
   if (climbing) {
     const uint32_t f = a.first[c], e = f + a.count[c];
     if (e > f && !AFD_IN(e - 1, a.n_part, "quad leaf range")) climbing = false;
@@ -1346,6 +1414,7 @@ int launch_link(afd_ctx *c, int64_t n) {
       ptr<uint32_t>(c->c_count), ptr<uint32_t>(c->c_skip), ptr<uint32_t>(c->c_parent),
       ptr<uint32_t>(c->c_child));
   c->launches++;
+  c->leaf_ord_ok = false;  // a new topology: the leaf order is made when first needed
   return ck();
 }
 
@@ -1401,6 +1470,23 @@ int launch_moments(afd_ctx *c, bool child_blocks, bool need_q) {
   a.node_f = ptr<float4>(c->node_f);
   a.node_i = ptr<uint2>(c->node_i);
   a.block = child_blocks ? ptr<uint4>(c->c_block) : nullptr;
+  if (quad_on && !c->leaf_ord_ok) {  // the leaves by particle count, for the quadrupole climb
+    AFD_TRY(reserve(c->leaf_ord, sizeof(uint32_t) * (size_t)nc));
+    AFD_TRY(reserve(c->leaf_aux, sizeof(uint32_t) * (2 * kLeafBuckets + 1)));
+    if (cudaMemsetAsync(c->leaf_aux.p, 0, sizeof(uint32_t) * (2 * kLeafBuckets + 1),
+                        c->stream) != cudaSuccess)
+      return AFD_ERR_CUDA;
+    k_leaf_hist<<<blocks_for(nc), kThreads, 0, c->stream>>>(
+        nc, ptr<uint32_t>(c->c_child), ptr<uint32_t>(c->c_count), ptr<uint32_t>(c->leaf_aux));
+    k_leaf_scatter<<<blocks_for(nc), kThreads, 0, c->stream>>>(
+        nc, ptr<uint32_t>(c->c_child), ptr<uint32_t>(c->c_count), ptr<uint32_t>(c->leaf_aux),
+        ptr<uint32_t>(c->leaf_ord));
+    c->launches += 2;
+    AFD_TRY(ck());
+    c->leaf_ord_ok = true;
+  }
+  a.leaf_ord = quad_on ? ptr<uint32_t>(c->leaf_ord) : nullptr;
+  a.n_leaves = quad_on ? ptr<uint32_t>(c->leaf_aux) + 2 * kLeafBuckets : nullptr;
   a.quad_on = quad_on;
   a.n_part = c->n;
   k_moments_sums<<<blocks_for(nc), kThreads, 0, c->stream>>>(a);
