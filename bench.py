@@ -68,6 +68,9 @@ def parse():
                     help="far-field precision of quadrupole superparticles: 0 fp32, 1 bf16, 2 fp16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="run the reusing steps eagerly instead of replaying a captured "
+                         "CUDA graph of them")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-criterion form and the equal-error comparison")
     ap.add_argument("--mac-samples", type=int, default=1_000_000)
@@ -441,20 +444,23 @@ def other_configs(args):
     return out
 
 
-def run_loop(afd, torch, ctx, g, st, *, steps, warmup, batch, R, dt, flush, stream, dev,
+def run_loop(afd, torch, ctx, g, st, *, steps, warmup, graph, R, dt, flush, stream, dev,
              before_timed=None, combine=None, count=None):
     """Warm-up, then `steps` timed KDK steps (CUDA events around each, L2
     flushed in between). st: dict of the state tensors and the evaluation
     counter. combine (optional): makes this rank's forces (its groups' rows,
     the rest zero) the whole system's, e.g. an all-reduce; count (optional):
-    this rank's interactions of a step. Returns per-step ms, force ms,
-    interactions, modes, launches."""
+    this rank's interactions of a step. graph: the reusing steps replay the
+    context's captured graph (kick-drift, reorder, moments, force, kick),
+    captured again after each construction step while its force kernel
+    runs. Returns per-step ms, force ms (the eager steps'), interactions,
+    modes, launches."""
     x, y, z, vx, vy, vz, m, acc = (st[k] for k in ("x", "y", "z", "vx", "vy", "vz", "m", "acc"))
 
     def step():
         k = st["k"]
         mode = afd.AFD_MAKE_LIST_FOR_REUSE if k % R == 0 else afd.AFD_REUSE_LIST
-        if batch and mode == afd.AFD_REUSE_LIST:
+        if graph and mode == afd.AFD_REUSE_LIST:
             afd.afd_graph_launch(ctx)  # kick-drift, reusing step, force, kick
         else:
             afd.afd_kick_drift(ctx, x, y, z, vx, vy, vz, acc, 0.5 * dt, dt)
@@ -464,7 +470,7 @@ def run_loop(afd, torch, ctx, g, st, *, steps, warmup, batch, R, dt, flush, stre
             if combine:
                 combine(acc)
             afd.afd_kick(ctx, vx, vy, vz, acc, 0.5 * dt)
-            if batch:  # buffers may have moved: capture the new reusing step
+            if graph:  # buffers may have moved: capture the new reusing step
                 afd.afd_graph_capture_step(ctx, x, y, z, vx, vy, vz, m, acc, dt)
         st["k"] = k + 1
         return mode
@@ -485,7 +491,7 @@ def run_loop(afd, torch, ctx, g, st, *, steps, warmup, batch, R, dt, flush, stre
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        if not (batch and mode == afd.AFD_REUSE_LIST):  # graph replays carry no events
+        if not (graph and mode == afd.AFD_REUSE_LIST):  # graph replays carry no events
             force_ms.append(afd.afd_last_force_ms(ctx))
         inter.append(count() if count else g.stats()["interactions"])
         modes.append(mode)
@@ -625,12 +631,12 @@ def learned_study(args, wl, afd, torch, np, dev, stream, local, p, tuned, launch
     # learned criterion decides every later construction step
     afd.afd_calc_force_all(gl.ctx, st["x"], st["y"], st["z"], st["m"], st["acc"],
                            afd.AFD_MAKE_LIST_FOR_REUSE)
-    if batch:
+    if not args.no_graph:
         afd.afd_graph_capture_step(gl.ctx, st["x"], st["y"], st["z"], st["vx"], st["vy"],
                                    st["vz"], st["m"], st["acc"], dt)
     step_ms, force_ms, inter, modes, launches = run_loop(
-        afd, torch, gl.ctx, gl, st, steps=args.steps, warmup=args.warmup, batch=batch, R=R,
-        dt=dt, flush=flush, stream=stream, dev=dev)
+        afd, torch, gl.ctx, gl, st, steps=args.steps, warmup=args.warmup,
+        graph=not args.no_graph, R=R, dt=dt, flush=flush, stream=stream, dev=dev)
     info = afd.afd_mac_info(gl.ctx)
     gl.close()
     cons = [v for v, md in zip(step_ms, modes) if md == afd.AFD_MAKE_LIST_FOR_REUSE]
@@ -892,7 +898,7 @@ def sweep(args, wl, sph_only=False):
                                afd.AFD_MAKE_LIST_FOR_REUSE)
         flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
         step_ms, _, inter, _, _ = run_loop(afd, torch, g.ctx, g, st, steps=32, warmup=R,
-                                           batch=False, R=R, dt=wl["dt"], flush=flush,
+                                           graph=False, R=R, dt=wl["dt"], flush=flush,
                                            stream=stream, dev=dev)
         print(json.dumps({"sweep": "n_reuse", "workload": wl["name"], "n_reuse": R,
                           "theta": wl["theta"], "n_grp": wl["n_grp"],
@@ -985,7 +991,8 @@ def main():
     afd.afd_calc_force(ctx, acc)  # evaluation 0's forces for the first kick
     if groups_shared:
         combine(acc)
-    if batch:
+    use_graph = not args.no_graph and not groups_shared  # (the all-reduce is not captured)
+    if use_graph:
         afd.afd_graph_capture_step(ctx, x, y, z, vx, vy, vz, m, acc, dt)
     state = {"x": x, "y": y, "z": z, "vx": vx, "vy": vy, "vz": vz, "m": m, "acc": acc, "k": 1}
     sampler = ClockSampler(local)
@@ -1000,8 +1007,8 @@ def main():
         t_wall[1] = time.time()
 
     step_ms, force_ms, inter, modes, launches = run_loop(
-        afd, torch, ctx, g, state, steps=args.steps, warmup=args.warmup, batch=batch, R=R, dt=dt,
-        flush=flush, stream=stream, dev=dev, before_timed=before_timed, combine=combine,
+        afd, torch, ctx, g, state, steps=args.steps, warmup=args.warmup, graph=use_graph, R=R,
+        dt=dt, flush=flush, stream=stream, dev=dev, before_timed=before_timed, combine=combine,
         count=count)
     t_epoch = (t_wall[1], time.time())
     t_wall = time.perf_counter() - t_wall[0]
@@ -1012,6 +1019,11 @@ def main():
     value = total_i_all / (total_ms * 1e-3)
 
     # ---- roofline of the force kernel ----
+    if not force_ms:  # no eager step in a short timed region: time the kernel on its own
+        for _ in range(3):
+            flush.zero_()
+            afd.afd_calc_force(ctx, acc)
+            force_ms.append(afd.afd_last_force_ms(ctx))
     f_ms = float(np.mean(force_ms)) if force_ms else float("nan")
     i_launch = float(np.mean(inter))
     achieved = FLOPS_PER_INTERACTION * i_launch / (f_ms * 1e-3) / 1e12
@@ -1088,6 +1100,9 @@ def main():
         "roofline": roofline,
         "clocks": clocks,
         "gpu_launches": launches,
+        "reusing_steps": ("replayed from a CUDA graph of the step (afd_graph_capture_step after "
+                          "each construction step, afd_graph_launch); the force kernel's time "
+                          "from the construction steps' events" if use_graph else "eager"),
         "n_grp_autotuned": None if tuned is None else [int(v) for v in tuned],
         "force_launch_autotuned": ({"warps_per_block": launch[0], "chunk": launch[1],
                                     "ms_chunk32_w2_4_8": [float(v) for v in launch[2][0]],

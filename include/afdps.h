@@ -199,8 +199,11 @@ int afd_system_stats(afd_ctx *ctx, int64_t *inter, int64_t *entries);
  * saved lists, kick. The arrays (device, caller order) must keep their
  * addresses for every replay; the context's stream must not be the legacy
  * default stream; lists must have been made for reuse. Nothing runs at
- * capture time. Replay with afd_graph_launch; a new construction step
- * (afd_tree_build with more cells or groups) requires a new capture. */
+ * capture time, and work already queued on the stream keeps running (the
+ * call waits only for a replay of the context's previous graph); a replay
+ * is ordered after it on the stream. Replay with afd_graph_launch; a new
+ * construction step (afd_tree_build with more cells or groups) requires a
+ * new capture. */
 int afd_graph_capture_step(afd_ctx *ctx, double *x, double *y, double *z, double *vx,
                            double *vy, double *vz, const double *m, float *acc4, double dt);
 

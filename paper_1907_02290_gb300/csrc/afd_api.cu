@@ -219,6 +219,8 @@ int kick_launch(afd_ctx *c, double *vx, double *vy, double *vz, const float *acc
 }
 
 void graph_release(afd_ctx *c) {
+  // a replay still running finishes before its graph goes
+  if (c->graph_exec && c->graph_done) cudaEventSynchronize(c->graph_done);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->graph) cudaGraphDestroy(c->graph);
   c->graph_exec = nullptr;
@@ -348,6 +350,8 @@ void afd_destroy(afd_ctx *c) {
   DeviceGuard g(c->device);
   cudaStreamSynchronize(c->stream);
   graph_release(c);
+  if (c->graph_done) cudaEventDestroy(c->graph_done);
+  c->graph_done = nullptr;
   DevBuf *bufs[] = {&c->root, &c->status, &c->red_part, &c->red_count, &c->u64acc, &c->keys,
                     &c->keys2, &c->perm, &c->perm2, &c->sort_cnt, &c->sort_off, &c->xs, &c->ys,
                     &c->zs, &c->ms, &c->jhi, &c->jlo, &c->lk_d, &c->lk_c, &c->lk_e, &c->lk_cnt,
@@ -556,7 +560,11 @@ int afd_graph_capture_step(afd_ctx *c, double *x, double *y, double *z, double *
   graph_release(c);
   const int64_t n = c->n;
   if (c->cfg.mac) TRY(reserve(c->amag, sizeof(float) * (size_t)n));  // no allocation in capture
-  TRY(cuda_ok(cudaStreamSynchronize(c->stream)));
+  if (!c->graph_done &&
+      cudaEventCreateWithFlags(&c->graph_done, cudaEventDisableTiming) != cudaSuccess)
+    return AFD_ERR_CUDA;
+  // earlier work on the stream may still run: the capture records launches
+  // only, and a replay is ordered after it on the stream
   if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaGetLastError();
     return AFD_ERR_CUDA;
@@ -589,6 +597,7 @@ int afd_graph_launch(afd_ctx *c) {
   if (!c->graph_exec) return AFD_ERR_NO_SAVED_LIST;
   DeviceGuard g(c->device);
   TRY(cuda_ok(cudaGraphLaunch(c->graph_exec, c->stream)));
+  TRY(cuda_ok(cudaEventRecord(c->graph_done, c->stream)));
   c->launches += c->graph_launches;
   return AFD_OK;
 }

@@ -283,6 +283,7 @@ struct afd_ctx {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   int64_t graph_launches = 0;  // kernels inside the captured graph
+  cudaEvent_t graph_done = nullptr;  // recorded after each replay
 };
 
 namespace afd {
