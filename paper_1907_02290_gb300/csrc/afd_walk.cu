@@ -178,11 +178,10 @@ struct RecStream {
 // compaction places every chunk on its own, without following the group's
 // chunks in order.
 template <class T>
-__device__ __forceinline__ void rec_put(RecStream &st, bool on, T rec, T *arena, uint4 *hdr,
-                                        uint4 hv, uint32_t *cursor, uint32_t cap, int lane,
-                                        unsigned lt) {
-  const unsigned m = __ballot_sync(0xffffffffu, on);
-  const uint32_t n = __popc(m);
+__device__ __forceinline__ void rec_put(RecStream &st, bool on, unsigned m, T rec, T *arena,
+                                        uint4 *hdr, uint4 hv, uint32_t *cursor, uint32_t cap,
+                                        int lane, unsigned lt) {
+  const uint32_t n = __popc(m);  // m: the warp's ballot of `on`
   if (n == 0) return;
   const bool grow = st.fill + n > kChunk;
   uint32_t nc = kNone;
@@ -290,30 +289,32 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
       const bool acc = lane < f && dec == kAccept;
       const bool lf = lane < f && dec == kLeaf;
       const unsigned am = __ballot_sync(0xffffffffu, acc);
-      {
+      if (am) {  // warp-uniform
         const uint32_t ri = (uint32_t)ns + __popc(am & lt);  // record index = list position
-        rec_put(rs, acc, e.x, a.arena_s, a.hdr_s, make_uint4((uint32_t)g, ri, ri, 0u), a.cursor,
-                a.cap_s, lane, lt);
+        rec_put(rs, acc, am, e.x, a.arena_s, a.hdr_s, make_uint4((uint32_t)g, ri, ri, 0u),
+                a.cursor, a.cap_s, lane, lt);
+        ns += __popc(am);
       }
-      ns += __popc(am);
-      const uint32_t lfirst = lf ? e.x : 0u, lcnt = lf ? (e.y & 0x3fffffffu) : 0u;
-      uint32_t inc = lcnt;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += t;
-      }
-      const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
-      // the group's own first particle: remember its EPJ-list position (the
-      // group's particles follow it contiguously)
-      if (lf && gfirst >= lfirst && gfirst - lfirst < lcnt)
-        self_pos = (uint32_t)(ne + (inc - lcnt) + (gfirst - lfirst)) + 1u;
       const unsigned lm = __ballot_sync(0xffffffffu, lf);
-      rec_put(rl, lf, make_uint2(lfirst, lcnt), a.arena_l, a.hdr_l,
-              make_uint4((uint32_t)g, nl + __popc(lm & lt), (uint32_t)(ne + (inc - lcnt)), 0u),
-              a.cursor + 1, a.cap_l, lane, lt);
-      nl += __popc(lm);
-      ne += tot;
+      if (lm) {  // warp-uniform: leaves among the emitted run
+        const uint32_t lfirst = lf ? e.x : 0u, lcnt = lf ? (e.y & 0x3fffffffu) : 0u;
+        uint32_t inc = lcnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+          if (lane >= o) inc += t;
+        }
+        const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
+        // the group's own first particle: remember its EPJ-list position (the
+        // group's particles follow it contiguously)
+        if (lf && gfirst >= lfirst && gfirst - lfirst < lcnt)
+          self_pos = (uint32_t)(ne + (inc - lcnt) + (gfirst - lfirst)) + 1u;
+        rec_put(rl, lf, lm, make_uint2(lfirst, lcnt), a.arena_l, a.hdr_l,
+                make_uint4((uint32_t)g, nl + __popc(lm & lt), (uint32_t)(ne + (inc - lcnt)), 0u),
+                a.cursor + 1, a.cap_l, lane, lt);
+        nl += __popc(lm);
+        ne += tot;
+      }
       if (!om) {  // nothing open among the top entries: all emitted
         sp -= nv;
         __syncwarp();
@@ -406,31 +407,39 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
       }
       if (valid) child_entry = make_entry(d, c_id, c_first, c_cnt);
       const unsigned vm = __ballot_sync(0xffffffffu, valid);
-      // output count of each rewritten position [f, last]: children or itself
-      int expanded_q = -1;
+      // The rewritten positions [f, last] in output order: a position kept
+      // (not expanded) counts one, an expanded one its valid children. The
+      // offsets come from masks (the same for every lane): kept positions
+      // below a lane, plus the children of the expanded positions below it.
+      const unsigned upto = last == 31 ? 0xffffffffu : ((2u << last) - 1u);
+      unsigned xm = 0u;  // expanded positions
+      uint32_t pc[kExpand];
 #pragma unroll
-      for (int q = 0; q < kExpand; q++)
-        if (q < E && pos_q[q] == lane) expanded_q = q;
-      uint32_t cnt = 0;
-      if (lane >= f && lane <= last)
-        cnt = expanded_q >= 0 ? __popc((vm >> (8 * expanded_q)) & 0xffu) : 1u;
-      uint32_t oinc = cnt;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, oinc, o);
-        if (lane >= o) oinc += t;
+      for (int q = 0; q < kExpand; q++) {
+        pc[q] = __popc((vm >> (8 * q)) & 0xffu);  // zero for q >= E
+        if (q < E) xm |= 1u << pos_q[q];
       }
-      const uint32_t K = __shfl_sync(0xffffffffu, oinc, 31);
-      const uint32_t off_me = oinc - cnt;
+      const unsigned kept = upto & ~((1u << f) - 1u) & ~xm;
+      uint32_t K = __popc(kept);
+      uint32_t below = 0u;  // children of the expanded positions below this lane
+#pragma unroll
+      for (int q = 0; q < kExpand; q++) {
+        K += pc[q];
+        if (q < E && pos_q[q] < lane) below += pc[q];
+      }
       const int spn = sp - (last + 1);
       if (spn + (int)K > a.stack_cap) {
         if (lane == 0) atomicOr(a.status, kStWalkStack);
         break;
       }
-      // output offset of this lane's parent position (child lanes)
-      const uint32_t off_par = __shfl_sync(0xffffffffu, off_me, p_me < 0 ? 0 : p_me);
+      // output offset of this lane's parent position (child lanes): the kept
+      // positions below it and the children of the expanded ones before it
+      uint32_t off_par = __popc(kept & ((1u << (p_me < 0 ? 0 : p_me)) - 1u));
+#pragma unroll
+      for (int q = 0; q < kExpand; q++)
+        if (q < q_me) off_par += pc[q];
       __syncwarp();
-      if (lane >= f && lane <= last && expanded_q < 0) stk[spn + K - 1 - off_me] = e;
+      if ((kept >> lane) & 1u) stk[spn + K - 1 - (__popc(kept & lt) + below)] = e;
       if (valid) {
         const unsigned mine = (vm >> (8 * q_me)) & 0xffu;
         const uint32_t o = off_par + __popc(mine & ((1u << c_me) - 1u));
