@@ -298,17 +298,22 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
       const unsigned lm = __ballot_sync(0xffffffffu, lf);
       if (lm) {  // warp-uniform: leaves among the emitted run
         const uint32_t lfirst = lf ? e.x : 0u, lcnt = lf ? (e.y & 0x3fffffffu) : 0u;
-        uint32_t inc = lcnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
-          if (lane >= o) inc += t;
-        }
-        const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
+        const uint32_t tot = __reduce_add_sync(0xffffffffu, lcnt);
         // the group's own first particle: remember its EPJ-list position (the
         // group's particles follow it contiguously)
-        if (lf && gfirst >= lfirst && gfirst - lfirst < lcnt)
-          self_pos = (uint32_t)(ne + (inc - lcnt) + (gfirst - lfirst)) + 1u;
+        const bool own = lf && gfirst >= lfirst && gfirst - lfirst < lcnt;
+        // the lanes' list positions (an inclusive scan of the counts) are
+        // needed only for the own particle's position and for the header of
+        // a new chunk: most steps skip the scan
+        uint32_t inc = lcnt;
+        if (__any_sync(0xffffffffu, own) || rl.fill + __popc(lm) > kChunk) {
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+          }
+        }
+        if (own) self_pos = (uint32_t)(ne + (inc - lcnt) + (gfirst - lfirst)) + 1u;
         rec_put(rl, lf, lm, make_uint2(lfirst, lcnt), a.arena_l, a.hdr_l,
                 make_uint4((uint32_t)g, nl + __popc(lm & lt), (uint32_t)(ne + (inc - lcnt)), 0u),
                 a.cursor + 1, a.cap_l, lane, lt);
