@@ -79,22 +79,37 @@ __device__ __forceinline__ float mac_sq3(float a, float b, float c) {
   return __fadd_rn(s, __fmul_rn(c, c));
 }
 
-// q = (xx, yy, zz, xy), q1 = (xz, yz, -, -)
-__device__ __forceinline__ void mac_features(const float *bmin, const float *bmax, float cx,
-                                             float cy, float cz, float s2, float M, float4 q,
-                                             float2 q1, uint32_t count, float eps2, float amin,
-                                             float *f) {
-  const float com[3] = {cx, cy, cz};
-  float d[3], u[3], w[3];
+// The features' terms that depend only on the group (and eps): log2 of the
+// group's smallest reference |a|, of its box's half diagonal squared e^2,
+// and of eps^2 -- a walk computes them once per group.
+struct MacGroup {
+  float lg_amin, lg_e2, lg_eps2;
+};
+
+__device__ __forceinline__ MacGroup mac_group(const float *bmin, const float *bmax, float amin,
+                                              float eps2) {
+  float w[3];
 #pragma unroll
-  for (int k = 0; k < 3; k++) {
-    d[k] = mac_sep(com[k], bmin[k], bmax[k]);
-    u[k] = __fsub_rn(__fmul_rn(__fadd_rn(bmin[k], bmax[k]), 0.5f), com[k]);
-    w[k] = __fsub_rn(bmax[k], bmin[k]);
-  }
-  const float d2 = mac_sq3(d[0], d[1], d[2]);
-  const float u2 = mac_sq3(u[0], u[1], u[2]);
+  for (int k = 0; k < 3; k++) w[k] = __fsub_rn(bmax[k], bmin[k]);
   const float e2 = __fmul_rn(mac_sq3(w[0], w[1], w[2]), 0.25f);
+  MacGroup g;
+  g.lg_amin = mac_lg2(amin);
+  g.lg_e2 = mac_lg2(e2);
+  g.lg_eps2 = mac_lg2(eps2);
+  return g;
+}
+
+// q = (xx, yy, zz, xy), q1 = (xz, yz, -, -); d2 = mac_sq3 of the COM's
+// separations from the box (mac_sep per axis), as the criterion has it.
+__device__ __forceinline__ void mac_features_g(const float *bmin, const float *bmax, float cx,
+                                               float cy, float cz, float s2, float M, float4 q,
+                                               float2 q1, uint32_t count, float d2,
+                                               const MacGroup &G, float *f) {
+  const float com[3] = {cx, cy, cz};
+  float u[3];
+#pragma unroll
+  for (int k = 0; k < 3; k++) u[k] = __fsub_rn(__fmul_rn(__fadd_rn(bmin[k], bmax[k]), 0.5f), com[k]);
+  const float u2 = mac_sq3(u[0], u[1], u[2]);
   const float off = mac_sq3(q.w, q1.x, q1.y);
   const float q2 = __fadd_rn(mac_sq3(q.x, q.y, q.z), __fadd_rn(off, off));
   const float Qu0 = __fadd_rn(__fadd_rn(__fmul_rn(q.x, u[0]), __fmul_rn(q.w, u[1])), __fmul_rn(q1.x, u[2]));
@@ -103,11 +118,11 @@ __device__ __forceinline__ void mac_features(const float *bmin, const float *bma
   const float uQu = __fadd_rn(__fadd_rn(__fmul_rn(u[0], Qu0), __fmul_rn(u[1], Qu1)), __fmul_rn(u[2], Qu2));
   const float ld = mac_lg2(d2), ls = mac_lg2(s2), lm = mac_lg2(M);
   f[0] = __fmul_rn(0.5f, __fsub_rn(ls, ld));
-  f[1] = __fsub_rn(__fsub_rn(lm, ld), mac_lg2(amin));
+  f[1] = __fsub_rn(__fsub_rn(lm, ld), G.lg_amin);
   f[2] = __fsub_rn(__fsub_rn(__fmul_rn(0.5f, mac_lg2(q2)), lm), ls);
-  f[3] = __fmul_rn(0.5f, __fsub_rn(mac_lg2(e2), ld));
+  f[3] = __fmul_rn(0.5f, __fsub_rn(G.lg_e2, ld));
   f[4] = mac_lg2(__uint2float_rn(count));
-  f[5] = __fmul_rn(0.5f, __fsub_rn(mac_lg2(eps2), ld));
+  f[5] = __fmul_rn(0.5f, __fsub_rn(G.lg_eps2, ld));
   f[6] = 0.0f;
   if (u2 > 0.0f && q2 > 0.0f) {
     const float den = __fmul_rn(u2, __fsqrt_rn(q2));
@@ -116,6 +131,17 @@ __device__ __forceinline__ void mac_features(const float *bmin, const float *bma
   f[7] = __fmul_rn(0.5f, __fsub_rn(mac_lg2(u2), ld));
 #pragma unroll
   for (int k = 0; k < kMacNF; k++) f[k] = mac_clamp(f[k]);
+}
+
+// The features of one pair from scratch (the group's terms included).
+__device__ __forceinline__ void mac_features(const float *bmin, const float *bmax, float cx,
+                                             float cy, float cz, float s2, float M, float4 q,
+                                             float2 q1, uint32_t count, float eps2, float amin,
+                                             float *f) {
+  const float d2 = mac_sq3(mac_sep(cx, bmin[0], bmax[0]), mac_sep(cy, bmin[1], bmax[1]),
+                           mac_sep(cz, bmin[2], bmax[2]));
+  mac_features_g(bmin, bmax, cx, cy, cz, s2, M, q, q1, count, d2,
+                 mac_group(bmin, bmax, amin, eps2), f);
 }
 
 // ---- the network on the tensor cores ----

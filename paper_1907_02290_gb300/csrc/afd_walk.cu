@@ -139,8 +139,8 @@ constexpr uint32_t kBand = 3u;
 __device__ __forceinline__ uint32_t learned_pre(const WalkArgs &a, const float *bmin,
                                                 const float *bmax, float cx, float cy, float cz,
                                                 float s2, bool leaf, uint32_t id, uint32_t first,
-                                                uint32_t count, uint32_t gfirst, float amin,
-                                                float *f) {
+                                                uint32_t count, uint32_t gfirst,
+                                                const MacGroup &G, float *f) {
   const uint32_t closed = leaf ? kLeaf : kOpen;
   if (gfirst >= first && gfirst - first < count) return closed;  // holds the group
   const float dx = sep_axis(cx, bmin[0], bmax[0]);
@@ -152,8 +152,7 @@ __device__ __forceinline__ uint32_t learned_pre(const WalkArgs &a, const float *
   if (s2 < __fmul_rn(a.lo2, d2)) return kAccept;
   if (!(s2 < __fmul_rn(a.hi2, d2))) return closed;
   const float4 sh = a.s_hi[id], q0 = a.s_q0[id], q1 = a.s_q1[id];
-  mac_features(bmin, bmax, cx, cy, cz, s2, sh.w, q0, make_float2(q1.x, q1.y), count, a.eps2,
-               amin, f);
+  mac_features_g(bmin, bmax, cx, cy, cz, s2, sh.w, q0, make_float2(q1.x, q1.y), count, d2, G, f);
   return kBand;
 }
 
@@ -250,7 +249,8 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
       bmax[k] = a.boxf[gb * 6 + 3 + k];
     }
     const uint32_t gfirst = NBR ? 0u : a.g_first[g];
-    const float amin = LEARNED ? a.g_amin[g] : 0.0f;
+    MacGroup mg = {0.0f, 0.0f, 0.0f};  // the features' per-group terms (learned walk)
+    if (LEARNED) mg = mac_group(bmin, bmax, a.g_amin[g], a.eps2);
     uint64_t ne = 0, ns = 0;
     uint32_t nl = 0;  // leaf records
     RecStream rs{kNone, kChunk}, rl{kNone, kChunk};
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(kWalkThreads) k_walk(WalkArgs a) {
             valid = d != kAccept;  // a dropped cell takes no stack entry
           } else {
             d = LEARNED ? learned_pre(a, bmin, bmax, cx, cy, cz, s2, leaf_me, c_id, c_first,
-                                      c_cnt, gfirst, amin, feat)
+                                      c_cnt, gfirst, mg, feat)
                         : decide(bmin, bmax, cx, cy, cz, s2, leaf_me, a.theta2);
           }
         }
