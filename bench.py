@@ -1069,8 +1069,10 @@ def main():
         e2e = {"value": e_i / e_s, "unit": "interactions/s", "h2d_bytes_per_step": 4 * 8 * n,
                "d2h_bytes_per_step": 16 * n, "ms_per_step": 1e3 * e_s / args.steps,
                "call": "afd_calc_force_all_host: per step the force evaluation with its "
-                       "copies (x, y, z, m in, n x 4 floats out); the kick and drift that value's "
-                       "steps include are not in it (device kernels, about 1% of a step)"}
+                       "copies (x, y, z, m in from pinned memory; the n x 4 floats out written "
+                       "into the pinned output by the force kernel over the host link); the kick "
+                       "and drift that value's steps include are not in it (device kernels, about "
+                       "1% of a step)"}
         g2.close()
 
     if rank != 0:

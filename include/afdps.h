@@ -159,8 +159,13 @@ int afd_calc_force_all(afd_ctx *ctx, const double *x, const double *y, const dou
                        const double *m, int64_t n, float *acc4, int mode);
 
 /* The same top-level call on HOST arrays (caller order): copies x, y, z, m
- * to the device, runs afd_calc_force_all, copies the n x 4 floats back to
- * acc4_host and synchronises. Pinned host memory gives the fastest copies. */
+ * to the device, runs afd_calc_force_all, returns the n x 4 floats in
+ * acc4_host and synchronises. Pinned host memory gives the fastest copies;
+ * when acc4_host is pinned and mapped (cudaHostAlloc, or registered with a
+ * device pointer) and neither the learned criterion nor a work share is
+ * set, the force kernel writes it directly over the host link while it
+ * runs, with no copy after it. The contents of acc4_host are undefined
+ * while the call runs. */
 int afd_calc_force_all_host(afd_ctx *ctx, const double *x, const double *y, const double *z,
                             const double *m, int64_t n, float *acc4_host, int mode);
 

@@ -465,9 +465,25 @@ int afd_calc_force_all_host(afd_ctx *c, const double *x, const double *y, const 
     TRY(cuda_ok(cudaMemcpyAsync(c->hz.p, z, bd, cudaMemcpyHostToDevice, c->stream)));
     TRY(cuda_ok(cudaMemcpyAsync(c->hm.p, m, bd, cudaMemcpyHostToDevice, c->stream)));
   }
+  // Pinned (page-locked, mapped) output: the force kernel writes the
+  // accelerations straight into it over the host link while it runs, instead
+  // of a copy after it. Not with the learned criterion (its |a| pass reads
+  // the forces back) nor with a work share.
+  float *dev_out = ptr<float>(c->hacc);
+  bool direct = false;
+  if (n > 0 && !c->cfg.mac && c->share_parts == 1) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, acc4_host) == cudaSuccess &&
+        at.type == cudaMemoryTypeHost && at.devicePointer != nullptr) {
+      dev_out = static_cast<float *>(at.devicePointer);
+      direct = true;
+    } else {
+      cudaGetLastError();
+    }
+  }
   TRY(calc_force_all(c, ptr<double>(c->hx), ptr<double>(c->hy), ptr<double>(c->hz),
-                     ptr<double>(c->hm), n, ptr<float>(c->hacc), mode));
-  if (n > 0)
+                     ptr<double>(c->hm), n, dev_out, mode));
+  if (n > 0 && !direct)
     TRY(cuda_ok(cudaMemcpyAsync(acc4_host, c->hacc.p, sizeof(float4) * (size_t)n,
                                 cudaMemcpyDeviceToHost, c->stream)));
   TRY(cuda_ok(cudaStreamSynchronize(c->stream)));

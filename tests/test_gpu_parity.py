@@ -294,6 +294,14 @@ def test_host_entry_point_matches_device(env):
     out = np.zeros((p.n, 4), dtype=np.float32)
     afd.afd_calc_force_all_host(g.ctx, p.x, p.y, p.z, p.m, out, afd.AFD_MAKE_LIST_FOR_REUSE)
     assert np.array_equal(out.astype(np.float64), a_dev)
+    # pinned arrays: the force kernel writes the pinned output directly
+    # (construction and reusing steps), the same numbers
+    hx, hy, hz, hm = (torch.tensor(a).pin_memory() for a in (p.x, p.y, p.z, p.m))
+    pout = torch.full((p.n, 4), float("nan"), dtype=torch.float32).pin_memory()
+    for mode in (afd.AFD_MAKE_LIST_FOR_REUSE, afd.AFD_REUSE_LIST):
+        pout.fill_(float("nan"))
+        afd.afd_calc_force_all_host(g.ctx, hx, hy, hz, hm, pout, mode)
+        assert np.array_equal(pout.numpy().astype(np.float64), a_dev)
     g.close()
 
 
