@@ -668,6 +668,7 @@ def learned_study(args, wl, afd, torch, np, dev, stream, local, p, tuned, launch
                          else "the plain lists (--launch)"},
         "walk_network_evaluations_last_construction": info["evaluations"],
         "walk_network_accepts_last_construction": info["accepted"],
+        "walk_steps_with_network_last_construction": info["rounds"],
         "training": {"samples": n_s, "band_pairs_total": total, "epochs": epochs,
                      "batch": 1024, "final_mse_log2": float(hist[-1]),
                      "first_epoch_mse_log2": float(hist[0]), "sample_s": t_samp,

@@ -949,12 +949,14 @@ __global__ void __launch_bounds__(kThreads) k_moments_sums(MomArgs a) {
 
 // Quadrupoles after the monopole passes (every centre of mass known): leaves
 // sum their particles (leaf_quad, one lane per leaf, Morton order), then the
-// parents climb with arrival counters like the sums, the completed parents
-// of a warp summed six lanes each -- one quadrupole component per lane, its
-// chain over the children in octant order with internal_quad's operations
-// -- five parents at a time. The arithmetic of every cell is the single
-// climb's, so the results are the same bit for bit.
+// parents climb with arrival counters like the sums. The completed parents
+// of a warp are summed four at a time: a lane per child forms the child's
+// six shifted terms Q_c + M_c (3 D_a D_b - r^2 delta_ab) (D = COM_c -
+// COM_p), a lane per component adds them in octant order. Every cell's
+// arithmetic is the definition's, in the same order, whichever lanes run it.
 __global__ void __launch_bounds__(kThreads) k_moments_quad(MomArgs a) {
+  // per warp: the shifted terms of the children of four parents
+  __shared__ double qstage[kThreads / 32][4][8][6];
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   bool climbing = t < (int64_t)*a.n_leaves;
@@ -987,43 +989,51 @@ __global__ void __launch_bounds__(kThreads) k_moments_quad(MomArgs a) {
     __syncwarp();
     unsigned wm = __ballot_sync(0xffffffffu, won);
     while (wm) {
-      // lane 6j + q takes component q of the j-th completed parent (j < 5)
-      const int j = lane / 6, q = lane - 6 * j;
+      // The next (up to) four completed parents: lane 8j + o computes the six
+      // shifted terms of child o of the j-th (once per child, not once per
+      // component), then lane 8j + q (q < 6) chains component q over the
+      // children in octant order, reading the terms from shared memory.
+      const int j = lane >> 3, o = lane & 7;
       unsigned rest = wm;
       int src = -1;
-      for (int k = 0; k <= j && rest && j < 5; k++) {
+      for (int k = 0; k <= j && rest; k++) {
         src = __ffs(rest) - 1;
         rest &= rest - 1;
       }
-      const bool mine = j < 5 && src >= 0 && __popc(wm & ((2u << src) - 1u)) == j + 1;
+      const bool mine = src >= 0 && __popc(wm & ((2u << src) - 1u)) == j + 1;
       const uint32_t pj = __shfl_sync(0xffffffffu, c, src < 0 ? 0 : src);
+      bool has = false;
       if (mine) {
-        const double g0 = __ldcg(&a.com[(size_t)pj * 3]), g1 = __ldcg(&a.com[(size_t)pj * 3 + 1]),
-                     g2 = __ldcg(&a.com[(size_t)pj * 3 + 2]);
-        // the component's two axes (diagonal q < 3: a = b = q)
-        const int ax = q < 3 ? q : (q == 5 ? 1 : 0), bx = q < 3 ? q : (q == 3 ? 1 : 2);
-        double acc = 0.0;
-        for (int o = 0; o < 8; o++) {
-          const uint32_t cc = __ldg(&a.child[(size_t)pj * 8 + o]);
-          if (cc == kNone || !AFD_IN(cc, a.n_cells, "quad child")) continue;
+        const uint32_t cc = __ldg(&a.child[(size_t)pj * 8 + o]);
+        if (cc != kNone && AFD_IN(cc, a.n_cells, "quad child")) {
+          has = true;
+          const double g0 = __ldcg(&a.com[(size_t)pj * 3]), g1 = __ldcg(&a.com[(size_t)pj * 3 + 1]),
+                       g2 = __ldcg(&a.com[(size_t)pj * 3 + 2]);
           const double D0 = __dsub_rn(__ldcg(&a.com[(size_t)cc * 3 + 0]), g0);
           const double D1 = __dsub_rn(__ldcg(&a.com[(size_t)cc * 3 + 1]), g1);
           const double D2 = __dsub_rn(__ldcg(&a.com[(size_t)cc * 3 + 2]), g2);
           const double mc = __ldcg(&a.mass[cc]);
-          const double qc = __ldcg(&a.quad[(size_t)cc * 6 + q]);
-          const double Da = ax == 0 ? D0 : (ax == 1 ? D1 : D2);
-          const double Db = bx == 0 ? D0 : (bx == 1 ? D1 : D2);
-          const double p3 = __dmul_rn(__dmul_rn(3.0, Da), Db);
-          double term;
-          if (q < 3) {
-            const double r2 =
-                __dadd_rn(__dadd_rn(__dmul_rn(D0, D0), __dmul_rn(D1, D1)), __dmul_rn(D2, D2));
-            term = __dsub_rn(p3, r2);
-          } else {
-            term = p3;
+          const double r2 =
+              __dadd_rn(__dadd_rn(__dmul_rn(D0, D0), __dmul_rn(D1, D1)), __dmul_rn(D2, D2));
+          const double D[3] = {D0, D1, D2};
+          double *tq = qstage[threadIdx.x >> 5][j][o];
+#pragma unroll
+          for (int q = 0; q < 6; q++) {
+            // the component's two axes (diagonal q < 3: a = b = q)
+            const int ax = q < 3 ? q : (q == 5 ? 1 : 0), bx = q < 3 ? q : (q == 3 ? 1 : 2);
+            const double p3 = __dmul_rn(__dmul_rn(3.0, D[ax]), D[bx]);
+            const double term = q < 3 ? __dsub_rn(p3, r2) : p3;
+            tq[q] = __dadd_rn(__ldcg(&a.quad[(size_t)cc * 6 + q]), __dmul_rn(mc, term));
           }
-          acc = __dadd_rn(acc, __dadd_rn(qc, __dmul_rn(mc, term)));
         }
+      }
+      const unsigned hm = __ballot_sync(0xffffffffu, has);
+      __syncwarp();
+      if (mine && o < 6) {
+        const int q = o;
+        double acc = 0.0;
+        for (int k = 0; k < 8; k++)
+          if ((hm >> (8 * j + k)) & 1u) acc = __dadd_rn(acc, qstage[threadIdx.x >> 5][j][k][q]);
         a.quad[(size_t)pj * 6 + q] = acc;
         float *sq = q < 4 ? reinterpret_cast<float *>(&a.s_q0[pj]) + q
                           : reinterpret_cast<float *>(&a.s_q1[pj]) + (q - 4);
@@ -1031,7 +1041,8 @@ __global__ void __launch_bounds__(kThreads) k_moments_quad(MomArgs a) {
         if (q == 4) reinterpret_cast<float *>(&a.s_q1[pj])[2] = 0.0f;
         if (q == 5) reinterpret_cast<float *>(&a.s_q1[pj])[3] = 0.0f;
       }
-      for (int k = 0; k < 5 && wm; k++) wm &= wm - 1;
+      __syncwarp();  // the stage is free for the next parents
+      for (int k = 0; k < 4 && wm; k++) wm &= wm - 1;
     }
     __syncwarp();
   }
