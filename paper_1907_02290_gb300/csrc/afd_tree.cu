@@ -715,16 +715,14 @@ __device__ __forceinline__ int n_children(const uint32_t *child, uint32_t c) {
 
 // Leaves ordered by particle count (buckets: counts 1 .. 31, then 32 or
 // more), so that the lanes of a warp in the quadrupole climb sum leaves of
-// nearly equal length: a leaf's quadrupole is about twenty FP64 operations
+// nearly equal length: a leaf's quadrupole is about thirty FP64 operations
 // per particle on one lane, and a warp instruction costs GB300's narrow FP64
 // unit the same whatever its active lanes (2^22 particles: the tree build
-// with quadrupoles 2.97 -> 2.57 ms). The monopole sums keep the cell order:
+// with quadrupoles 2.97 -> 2.54 ms). The monopole sums keep the cell order:
 // there the neighbouring leaves of a warp read neighbouring particles, and
-// the count order was slower (87 -> 99 us). The order within a bucket is
-// that of the atomic cursors; the moments do not depend on it (every cell's
-// sums run in the definition's order on whichever lane takes the cell). aux[0, 32): the
-// bucket counts, aux[32, 64): the bucket cursors, aux[64]: the number of
-// leaves; all zero at launch.
+// the count order was not faster. The moments do not depend on the order
+// (every cell's sums run in the definition's order on whichever lane takes
+// the cell).
 constexpr int kLeafBuckets = 32;
 
 __device__ __forceinline__ uint32_t leaf_bucket(uint32_t count) {
@@ -732,50 +730,50 @@ __device__ __forceinline__ uint32_t leaf_bucket(uint32_t count) {
                                          : (count > 0u ? count - 1u : 0u);
 }
 
-__global__ void __launch_bounds__(kThreads) k_leaf_hist(int64_t nc,
-                                                        const uint32_t *__restrict__ child,
-                                                        const uint32_t *__restrict__ count,
-                                                        uint32_t *__restrict__ aux) {
+// The order is stable: within a bucket the leaves keep their cell
+// (depth-first) order, so a warp's leaves lie close together in space.
+// Block b's count of bucket k goes to cnt[k * nb + b]; an exclusive scan of
+// cnt (bucket-major) gives every (bucket, block) its first position.
+__global__ void __launch_bounds__(kThreads) k_leaf_count(int64_t nc,
+                                                         const uint32_t *__restrict__ child,
+                                                         const uint32_t *__restrict__ count,
+                                                         uint32_t *__restrict__ cnt) {
   __shared__ uint32_t h[kLeafBuckets];
   if (threadIdx.x < kLeafBuckets) h[threadIdx.x] = 0u;
   __syncthreads();
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c < nc && n_children(child, (uint32_t)c) == 0) atomicAdd(&h[leaf_bucket(count[c])], 1u);
   __syncthreads();
-  if (threadIdx.x < kLeafBuckets && h[threadIdx.x] != 0u) {
-    atomicAdd(&aux[threadIdx.x], h[threadIdx.x]);
-    atomicAdd(&aux[2 * kLeafBuckets], h[threadIdx.x]);
-  }
+  if (threadIdx.x < kLeafBuckets) cnt[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(kThreads) k_leaf_scatter(int64_t nc,
-                                                           const uint32_t *__restrict__ child,
-                                                           const uint32_t *__restrict__ count,
-                                                           uint32_t *__restrict__ aux,
-                                                           uint32_t *__restrict__ ord) {
-  __shared__ uint32_t off[kLeafBuckets];
-  const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(kThreads) k_leaf_place(int64_t nc,
+                                                         const uint32_t *__restrict__ child,
+                                                         const uint32_t *__restrict__ count,
+                                                         const uint32_t *__restrict__ off,
+                                                         uint32_t *__restrict__ ord) {
+  __shared__ uint32_t wc[kThreads / 32][kLeafBuckets];  // per warp and bucket: leaves, then offsets
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
-  if (threadIdx.x < 32) {  // exclusive offsets of the buckets
-    const uint32_t v = aux[lane];
-    uint32_t inc = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += t;
-    }
-    off[lane] = inc - v;
-  }
+  for (int k = threadIdx.x; k < (kThreads / 32) * kLeafBuckets; k += kThreads) (&wc[0][0])[k] = 0u;
   __syncthreads();
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool leaf = c < nc && n_children(child, (uint32_t)c) == 0;
   const uint32_t b = leaf ? leaf_bucket(count[c]) : (uint32_t)kLeafBuckets;
   const unsigned peers = __match_any_sync(0xffffffffu, b);
-  const int leader = __ffs(peers) - 1;
-  uint32_t base = 0u;
-  if (leaf && lane == leader) base = atomicAdd(&aux[kLeafBuckets + b], (uint32_t)__popc(peers));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  if (leaf) ord[off[b] + base + (uint32_t)__popc(peers & lt)] = (uint32_t)c;
+  if (leaf && lane == __ffs(peers) - 1) wc[warp][b] = (uint32_t)__popc(peers);
+  __syncthreads();
+  if (threadIdx.x < kLeafBuckets) {  // exclusive over the warps, then the block's first position
+    uint32_t run = off[(size_t)threadIdx.x * gridDim.x + blockIdx.x];
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; w++) {
+      const uint32_t v = wc[w][threadIdx.x];
+      wc[w][threadIdx.x] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  if (leaf) ord[wc[warp][b] + (uint32_t)__popc(peers & lt)] = (uint32_t)c;
 }
 
 #ifndef AFD_MOM_ACQREL
@@ -1481,23 +1479,27 @@ int launch_moments(afd_ctx *c, bool child_blocks, bool need_q) {
   a.node_f = ptr<float4>(c->node_f);
   a.node_i = ptr<uint2>(c->node_i);
   a.block = child_blocks ? ptr<uint4>(c->c_block) : nullptr;
-  if (quad_on && !c->leaf_ord_ok) {  // the leaves by particle count, for the quadrupole climb
+  const bool leaf_order = quad_on;
+  const unsigned nbl = blocks_for(nc);
+  if (leaf_order && !c->leaf_ord_ok) {  // the leaves by particle count (stable), for the quadrupoles
+    const size_t m = (size_t)kLeafBuckets * nbl;
     AFD_TRY(reserve(c->leaf_ord, sizeof(uint32_t) * (size_t)nc));
-    AFD_TRY(reserve(c->leaf_aux, sizeof(uint32_t) * (2 * kLeafBuckets + 1)));
-    if (cudaMemsetAsync(c->leaf_aux.p, 0, sizeof(uint32_t) * (2 * kLeafBuckets + 1),
-                        c->stream) != cudaSuccess)
-      return AFD_ERR_CUDA;
-    k_leaf_hist<<<blocks_for(nc), kThreads, 0, c->stream>>>(
-        nc, ptr<uint32_t>(c->c_child), ptr<uint32_t>(c->c_count), ptr<uint32_t>(c->leaf_aux));
-    k_leaf_scatter<<<blocks_for(nc), kThreads, 0, c->stream>>>(
-        nc, ptr<uint32_t>(c->c_child), ptr<uint32_t>(c->c_count), ptr<uint32_t>(c->leaf_aux),
-        ptr<uint32_t>(c->leaf_ord));
-    c->launches += 2;
+    AFD_TRY(reserve(c->leaf_aux, sizeof(uint32_t) * (2 * m + 1)));
+    uint32_t *cnt = ptr<uint32_t>(c->leaf_aux), *off = cnt + m;
+    k_leaf_count<<<nbl, kThreads, 0, c->stream>>>(nc, ptr<uint32_t>(c->c_child),
+                                                   ptr<uint32_t>(c->c_count), cnt);
+    c->launches++;
+    AFD_TRY(ck());
+    AFD_TRY(scan_u32(c, cnt, off, (int64_t)m));
+    k_leaf_place<<<nbl, kThreads, 0, c->stream>>>(nc, ptr<uint32_t>(c->c_child),
+                                                   ptr<uint32_t>(c->c_count), off,
+                                                   ptr<uint32_t>(c->leaf_ord));
+    c->launches++;
     AFD_TRY(ck());
     c->leaf_ord_ok = true;
   }
-  a.leaf_ord = quad_on ? ptr<uint32_t>(c->leaf_ord) : nullptr;
-  a.n_leaves = quad_on ? ptr<uint32_t>(c->leaf_aux) + 2 * kLeafBuckets : nullptr;
+  a.leaf_ord = leaf_order ? ptr<uint32_t>(c->leaf_ord) : nullptr;
+  a.n_leaves = leaf_order ? ptr<uint32_t>(c->leaf_aux) + 2 * (size_t)kLeafBuckets * nbl : nullptr;
   a.quad_on = quad_on;
   a.n_part = c->n;
   k_moments_sums<<<blocks_for(nc), kThreads, 0, c->stream>>>(a);
