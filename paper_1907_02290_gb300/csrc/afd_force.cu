@@ -1,8 +1,8 @@
 // Force kernel (Section 5: the indirect-index dispatch; Eq. kernel of
 // Section 6.2). Work unit = (i-group, chunk of 32 of its particles); a warp
 // takes one work item: a unit, or two consecutive units of one group (a full
-// one and the next if that holds more than 16 particles; monopole lists),
-// which share the group's list, each lane then holding two i-particles. The warp walks the group's EPJ list, then its SPJ list, 32 or
+// one and the next if that holds more than 16 particles), which share the
+// group's list, each lane then holding two i-particles. The warp walks the group's EPJ list, then its SPJ list, 32 or
 // 64 entries at a time (a launch choice): each lane gathers its j's by index
 // (float4 hi + float4 lo of a particle or of a cell's centre of mass), forms
 // their coordinates relative to the group origin, stages them in shared
@@ -48,10 +48,16 @@ namespace {
 #define AFD_FORCE_FLUSH_PAIRS 128  // pair-iterations per lane between Kahan flushes
 #endif
 #ifndef AFD_FORCE_PAIRS
-#define AFD_FORCE_PAIRS 1  // two units of a group per warp (monopole lists)
+#define AFD_FORCE_PAIRS 1  // two units of a group per warp
 #endif
 #ifndef AFD_FORCE_UNIT_IPT2
-#define AFD_FORCE_UNIT_IPT2 1  // monopole units of their own also two i-particles per lane
+#define AFD_FORCE_UNIT_IPT2 1  // units of their own also two i-particles per lane
+#endif
+#ifndef AFD_FORCE_QUAD_IPT2
+#define AFD_FORCE_QUAD_IPT2 1  // the quadrupole kernel also two i-particles per lane
+#endif
+#ifndef AFD_FORCE_QUAD_REGS
+#define AFD_FORCE_QUAD_REGS 128  // register budget of the quadrupole kernel
 #endif
 #ifndef AFD_FORCE_PERSISTENT
 #define AFD_FORCE_PERSISTENT 0  // warps take units from an atomic queue
@@ -369,7 +375,6 @@ __device__ __forceinline__ void run_list(WarpStage<QUAD, CH> &st, const Lane<IPT
                                          const float4 *sq1, const uint4 *sh, bool quad_list,
                                          float eps2, const int64_t *self_at, uint64_t nlist,
                                          uint64_t jbound, float gsc) {
-  static_assert(IPT == 1 || !QUAD, "two i-particles per lane: monopole lists");
   if (o0 >= o1) return;
   if (!AFD_IN(o1 - 1, nlist, "force list range")) return;
   constexpr int kChunk = CH, kPer = CH / 32, kPairs = CH / 2;
@@ -466,16 +471,26 @@ __device__ __forceinline__ void run_list(WarpStage<QUAD, CH> &st, const Lane<IPT
       self_here |= self_at[q] >= (int64_t)base && self_at[q] < (int64_t)base + kChunk;
     const bool any_self = __any_sync(0xffffffffu, self_here);
     if (QUAD && quad_list && FAR) {
-#pragma unroll 4
-      for (int t = ln.stream; t < kPairs; t += S)
-        interact_far_half<GUARD, FAR ? FAR : 1>(st.P0[t], st.P1[t], st.HA[t], st.HB[t],
-                                                pk(st.S2[t].x, st.S2[t].y), ln.XI[0], ln.YI[0],
-                                                ln.ZI[0], ln.E2, AX[0], AY[0], AZ[0], PP[0]);
+#pragma unroll (IPT == 1 ? 4 : 2)
+      for (int t = ln.stream; t < kPairs; t += S) {
+        const float4 p0 = st.P0[t], p1 = st.P1[t];
+        const uint4 ha = st.HA[t];
+        const uint2 hb = st.HB[t];
+        const f2 s2 = pk(st.S2[t].x, st.S2[t].y);
+#pragma unroll
+        for (int q = 0; q < IPT; q++)
+          interact_far_half<GUARD, FAR ? FAR : 1>(p0, p1, ha, hb, s2, ln.XI[q], ln.YI[q],
+                                                  ln.ZI[q], ln.E2, AX[q], AY[q], AZ[q], PP[q]);
+      }
     } else if (QUAD && quad_list) {
-#pragma unroll 4
-      for (int t = ln.stream; t < kPairs; t += S)
-        interact_quad2<GUARD>(st.P0[t], st.P1[t], st.QA[t], st.QB[t], st.QC[t], ln.XI[0],
-                              ln.YI[0], ln.ZI[0], ln.E2, AX[0], AY[0], AZ[0], PP[0]);
+#pragma unroll (IPT == 1 ? 4 : 2)
+      for (int t = ln.stream; t < kPairs; t += S) {
+        const float4 p0 = st.P0[t], p1 = st.P1[t], qa = st.QA[t], qb = st.QB[t], qc = st.QC[t];
+#pragma unroll
+        for (int q = 0; q < IPT; q++)
+          interact_quad2<GUARD>(p0, p1, qa, qb, qc, ln.XI[q], ln.YI[q], ln.ZI[q], ln.E2, AX[q],
+                                AY[q], AZ[q], PP[q]);
+      }
     } else if (any_self) {
       // a chunk holding some lane's own particle: that pair gets zero mass
       int ts[IPT];
@@ -645,7 +660,7 @@ __device__ __forceinline__ void force_unit(const ForceArgs &a, WarpStage<QUAD, C
   if (!AFD_IN(info.x, a.n_groups, "force unit group")) return;
   const uint32_t g = info.x, ioff = info.y & 0xffffu;
   const int sidx = (int)((info.y >> 16) & 3u);
-  if constexpr (!QUAD) {
+  if (!QUAD || AFD_FORCE_QUAD_IPT2) {
     if (pair) {
       unit_body<GUARD, QUAD, FAR, 1, 2, CH>(a, st, lane, g, ioff);
       return;
@@ -681,11 +696,12 @@ __device__ __forceinline__ bool launch_item(const ForceArgs &a, int64_t k, int64
 
 // Block shape is a launch choice (2, 4 or 8 warps): each warp's staging area
 // lives in dynamic shared memory. The register budget is the same for every
-// shape: 96 per thread with FP32 monopoles, 128 with quadrupoles.
+// shape: 96 per thread with FP32 monopoles, 128 with quadrupoles (two
+// i-particles per lane in both).
 constexpr int kForceMaxThreads = 256;
 
 template <bool GUARD, bool QUAD, int FAR, int CH>
-__global__ void __launch_bounds__(kForceMaxThreads) __maxnreg__(QUAD ? 128 : AFD_FORCE_MAX_REGS)
+__global__ void __launch_bounds__(kForceMaxThreads) __maxnreg__(QUAD ? AFD_FORCE_QUAD_REGS : AFD_FORCE_MAX_REGS)
     k_force(ForceArgs a) {
   extern __shared__ __align__(16) unsigned char force_smem[];
   WarpStage<QUAD, CH> *stage = reinterpret_cast<WarpStage<QUAD, CH> *>(force_smem);
@@ -814,12 +830,13 @@ __global__ void k_materialize(uint64_t n, const uint32_t *__restrict__ idx,
 }
 
 // Launch order of the force work items. A warp takes one item: a unit, or
-// (monopole lists) two consecutive units of one group -- a full one and the
+// two consecutive units of one group -- a full one and the
 // next when that holds more than 16 particles -- which share the group's
 // list: each lane then carries two i-particles (lanes past the second
 // unit's end only one), and every staged j-pair serves up to 64 particles
 // instead of 32. Measured without the list traffic, a staged j-pair shared
-// by two i-particles keeps the FP32 pipe 0.82 busy against 0.72 for one. An item's warp streams its
+// by two i-particles keeps the FP32 pipe 0.82 busy against 0.72 for one
+// (the quadrupole loop: 9.1e11 against 8.6e11 interactions per second). An item's warp streams its
 // group's whole list (split over S j-streams for the last, partial unit), so
 // its time follows the list work L * IPT / S; the items are launched largest
 // work first (afd_order.cuh). Every item writes its own particles.
@@ -881,9 +898,8 @@ int order_units(afd_ctx *c) {
   uint32_t *hist = ptr<uint32_t>(c->u_hist), *work = ptr<uint32_t>(c->u_work);
   if (cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (kOrderBuckets + 2), c->stream) != cudaSuccess)
     return AFD_ERR_CUDA;
-  // two i-particles per lane for the monopole kernel only (the quadrupole
-  // kernel's registers are spent on the far-field terms)
-  const bool pairs = AFD_FORCE_PAIRS && !c->cfg.multipole;
+  // two i-particles per lane, with monopole or quadrupole far fields
+  const bool pairs = AFD_FORCE_PAIRS && (!c->cfg.multipole || AFD_FORCE_QUAD_IPT2);
   constexpr int kT = 256;
   const int64_t want = (nu + kT - 1) / kT;
   const unsigned nb = (unsigned)(want < 152 * 8 ? want : 152 * 8);
