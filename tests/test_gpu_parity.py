@@ -151,19 +151,21 @@ def test_clustered_and_coincident(env):
     g.close()
 
 
+@pytest.mark.parametrize("quad", [False, True])
 @pytest.mark.parametrize("sizes,n_grp", [
     ([33, 63, 64, 65, 95, 96, 97, 128], 128),
     ([129, 159, 160, 161, 191, 192, 193, 256], 256),
     ([48, 49, 80, 81, 112, 113, 176, 177], 256),
 ])
-def test_group_sizes_around_the_unit_pairing(env, sizes, n_grp):
+def test_group_sizes_around_the_unit_pairing(env, sizes, n_grp, quad):
     """One clump per octant of the root, so each clump is one group of the
     given size: groups of 48, 49, 63, 64, 65, 95, 96, 97, 128 ... particles
     cover every case of the force kernel's work items (a 32-particle unit
     alone, a full unit and the next one of more than 16 particles taken by
     one warp -- 49, 81, 113, 177 -- or of at most 16 left on its own -- 48,
-    80, 112, 176 --, a partial last unit split into j-streams). Structure
-    bit-exact, forces against the oracle."""
+    80, 112, 176 --, a partial last unit split into j-streams), with
+    monopole and with quadrupole superparticles (both kernels take the same
+    items). Structure bit-exact, forces against the oracle."""
     _, _, orc = env
     rng = np.random.default_rng(31)
     xs, ys, zs = [], [], []
@@ -174,12 +176,16 @@ def test_group_sizes_around_the_unit_pairing(env, sizes, n_grp):
     x, y, z = (np.concatenate(a) for a in (xs, ys, zs))
     n = x.size
     p = ics.Particles(x, y, z, np.zeros(n), np.zeros(n), np.zeros(n), np.full(n, 1.0 / n))
-    kw = dict(n_grp=n_grp, theta=0.5, eps=1.0 / 256)
+    kw = dict(n_grp=n_grp, theta=0.5, eps=1.0 / 256, quad=quad)
     g, acc, _ = run_gpu(env, p, **kw)
     t = orc.Tree(p.x, p.y, p.z, p.m, **kw)
-    check_structure(g, t)
+    check_structure(g, t, quad=quad)
     assert sorted(t.groups()["count"].tolist()) == sorted(sizes)
-    assert rms_rel_acc(acc, t.force()) <= FORCE_RMS_TOL
+    ref = t.force()
+    assert rms_rel_acc(acc, ref) <= FORCE_RMS_TOL
+    assert rms_rel_pot(acc, ref) <= POT_RMS_TOL
+    if quad:  # the far field holds quadrupole terms: other clumps' cells
+        assert g.stats()["n_spj"] > 0
     g.close()
 
 
