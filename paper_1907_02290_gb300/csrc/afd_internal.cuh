@@ -38,6 +38,7 @@ enum : int {
   kStOverflow = 8,
   kStBadRadius = 16,
   kStSpin = 32,  // a bounded wait on another block of the same launch gave up
+  kStClimb = 64,  // a bottom-up climb went above the deepest level (a malformed tree)
 };
 int status_to_error(int bits);
 

@@ -70,6 +70,7 @@ struct TboxArgs {
   float4 *blk;  // 16 per cell: its 8 children's boxes by octant (empty: lo > hi)
   uint32_t *arrive;
   uint64_t n_part;  // read only by the self-checking build
+  int *status;      // kStClimb if the climb outruns the tree's depth
 };
 
 __global__ void __launch_bounds__(kThreads) k_nbr_tbox(TboxArgs a) {
@@ -94,9 +95,14 @@ __global__ void __launch_bounds__(kThreads) k_nbr_tbox(TboxArgs a) {
     a.tb[(size_t)c * 2 + 1] = make_float4(__double2float_ru(hi[0]), __double2float_ru(hi[1]),
                                           __double2float_ru(hi[2]), 0.0f);
   }
-  for (;;) {
+  // a leaf of level l reaches the root in l climbs (at most kLevels)
+  for (int round = 0;; round++) {
     const uint32_t p = a.parent[c];
     if (p == kNone) break;
+    if (round > kLevels) {
+      atomicOr(a.status, kStClimb);
+      break;
+    }
     if (!AFD_IN(p, a.n_cells, "tbox parent")) break;
     __threadfence();
     const unsigned old = atomicAdd(&a.arrive[p], 1u);
@@ -508,6 +514,7 @@ int nbr_boxes(afd_ctx *c, const double *h, double skin) {
   a.blk = ptr<float4>(c->nbr_blk);
   a.arrive = ptr<uint32_t>(c->nbr_arrive);
   a.n_part = (uint64_t)c->n;
+  a.status = ptr<int>(c->status);
   k_nbr_tbox<<<blocks_for(nc), kThreads, 0, c->stream>>>(a);
   c->launches++;
   if (ng > 0) {

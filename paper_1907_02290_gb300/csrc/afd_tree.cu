@@ -704,6 +704,7 @@ struct MomArgs {
   const uint32_t *n_leaves;  // their number (device)
   int quad_on;
   int64_t n_part;  // particles (read only by the self-checking build)
+  int *status;     // kStClimb if a climb outruns the tree's depth
 };
 
 __device__ __forceinline__ int n_children(const uint32_t *child, uint32_t c) {
@@ -895,7 +896,13 @@ __global__ void __launch_bounds__(kThreads) k_moments_sums(MomArgs a) {
   // parents this warp completes are summed four lanes each (M, S_x, S_y,
   // S_z: one ordered chain over the octants per lane), eight at a time.
   uint32_t pc = climbing ? a.parent[c] : kNone;  // parent of the climbing cell
-  while (__any_sync(0xffffffffu, climbing)) {
+  // a cell of level l reaches the root in l climbs: at most kLevels + 1
+  // rounds for any tree the link builds (bounded by construction)
+  for (int round = 0; __any_sync(0xffffffffu, climbing); round++) {
+    if (round > kLevels + 1) {
+      if (climbing) atomicOr(a.status, kStClimb);
+      break;
+    }
     bool won = false;
     if (climbing) {
       const uint32_t p = pc;
@@ -966,7 +973,13 @@ __global__ void __launch_bounds__(kThreads) k_moments_quad(MomArgs a) {
     else leaf_quad(a, c);
   }
   uint32_t pc = climbing ? a.parent[c] : kNone;
-  while (__any_sync(0xffffffffu, climbing)) {
+  // a cell of level l reaches the root in l climbs: at most kLevels + 1
+  // rounds for any tree the link builds (bounded by construction)
+  for (int round = 0; __any_sync(0xffffffffu, climbing); round++) {
+    if (round > kLevels + 1) {
+      if (climbing) atomicOr(a.status, kStClimb);
+      break;
+    }
     bool won = false;
     if (climbing) {
       const uint32_t p = pc;
@@ -1502,6 +1515,7 @@ int launch_moments(afd_ctx *c, bool child_blocks, bool need_q) {
   a.n_leaves = leaf_order ? ptr<uint32_t>(c->leaf_aux) + 2 * (size_t)kLeafBuckets * nbl : nullptr;
   a.quad_on = quad_on;
   a.n_part = c->n;
+  a.status = ptr<int>(c->status);
   k_moments_sums<<<blocks_for(nc), kThreads, 0, c->stream>>>(a);
   k_moments_finish<<<blocks_for(nc), kThreads, 0, c->stream>>>(a);
   c->launches += 2;

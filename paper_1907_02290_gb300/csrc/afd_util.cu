@@ -32,7 +32,7 @@ void release(DevBuf &b) {
 int status_to_error(int bits) {
   if (bits & kStNonFinite) return AFD_ERR_NONFINITE;
   if (bits & kStWalkStack) return AFD_ERR_WALK_STACK;
-  if (bits & (kStWalkIter | kStSpin)) return AFD_ERR_TIMEOUT;
+  if (bits & (kStWalkIter | kStSpin | kStClimb)) return AFD_ERR_TIMEOUT;
   if (bits & kStOverflow) return AFD_ERR_LIST_OVERFLOW;
   if (bits & kStBadRadius) return AFD_ERR_BAD_RADIUS;
   return AFD_OK;
