@@ -419,6 +419,100 @@ def test_full_size_plummer_1m(env):
     g.close()
 
 
+def test_full_size_galaxy_8m(env):
+    """The 2^23 galaxy workload (Hernquist halo and exponential disk,
+    quadrupole superparticles, theta 0.4, n_grp 512) with the force launch
+    shape autotuned on its lists, as the bench runs it: keys, topology,
+    moments, groups and lists bit-exact (quadrupoles to 1e-12); forces of
+    every 97th group against the oracle's FP64 sum on the same lists."""
+    torch, afd, orc = env
+    wl = ics.WORKLOADS["galaxy_8m"]
+    p = ics.make(wl["model"], wl["n"], wl["seed"])
+    kw = dict(n_grp=wl["n_grp"], theta=wl["theta"], eps=wl["eps"], quad=True)
+    g, _, (_, _, _, _, acc) = run_gpu(env, p, **kw)
+    afd.afd_autotune_launch(g.ctx, acc, reps=1)
+    afd.afd_calc_force(g.ctx, acc)
+    torch.cuda.synchronize()
+    a = acc.cpu().numpy().astype(np.float64)
+    t = orc.Tree(p.x, p.y, p.z, p.m, **kw)
+    check_structure(g, t, quad=True)
+    ng = t.sizes()["n_groups"]
+    ref = t.force_groups(np.arange(0, ng, 97))
+    mask = np.isfinite(ref[0])
+    assert mask.sum() > 50000
+    assert rms_rel_acc(a[mask], [r[mask] for r in ref]) <= FORCE_RMS_TOL
+    assert rms_rel_pot(a[mask], [r[mask] for r in ref]) <= POT_RMS_TOL
+    g.close()
+
+
+def test_full_size_batch32(env):
+    """The 32-system batched workload (N log-uniform in [2^12, 2^20], 7.1M
+    particles in all) with n_grp autotuned per system and one launch per
+    kernel over all systems, as the bench runs it: for four systems (the
+    largest, the smallest and two others) root, keys, permutation, topology,
+    groups and lists equal those of an oracle run on the system alone with
+    the system's tuned n_grp (ids shifted by the system's offsets), and the
+    system's forces match the oracle's."""
+    torch, afd, orc = env
+    wl = ics.WORKLOADS["batch32"]
+    p, off, _ = ics.make_batch(wl["n_systems"], wl["seed"])
+    dev = torch.device("cuda:0")
+    x, y, z, m = (torch.tensor(a, dtype=torch.float64, device=dev) for a in (p.x, p.y, p.z, p.m))
+    acc = torch.zeros(p.n, 4, dtype=torch.float32, device=dev)
+    kw = dict(theta=wl["theta"], eps=wl["eps"])
+    g = afd.Gravity(afd.Config(n_grp=wl["n_grp"], **kw), 0, torch.cuda.current_stream())
+    afd.afd_set_systems(g.ctx, off)
+    tuned = afd.afd_autotune_n_grp(g.ctx, x, y, z, m, acc, [32, 64, 128, 256, 512], 4,
+                                   n_sys=wl["n_systems"])
+    g.force_all(x, y, z, m, acc, afd.AFD_MAKE_LIST_FOR_REUSE)
+    torch.cuda.synchronize()
+    a = acc.cpu().numpy().astype(np.float64)
+    roots = g.export("root").reshape(-1, 4)
+    keys, perm = g.export("keys"), g.export("perm")
+    lv, fi, ct = g.export("cell_level"), g.export("cell_first"), g.export("cell_count")
+    pa, sk = g.export("cell_parent"), g.export("cell_skip")
+    gf, gc = g.export("group_first"), g.export("group_count")
+    eo, e, so, s = (g.export(k) for k in ("epj_off", "epj_idx", "spj_off", "spj_idx"))
+    sizes = np.diff(off)
+    # each system's cells and groups are contiguous, found by their first particle
+    csys = np.searchsorted(off, fi.astype(np.int64), side="right") - 1
+    gsys = np.searchsorted(off, gf.astype(np.int64), side="right") - 1
+    picks = sorted({int(np.argmax(sizes)), int(np.argmin(sizes)), 7, 20})
+    for k in picks:
+        sl = slice(off[k], off[k + 1])
+        q = [v[sl] for v in (p.x, p.y, p.z, p.m)]
+        t = orc.Tree(*q, n_grp=int(tuned[k]), **kw)
+        assert np.array_equal(roots[k], t.root())
+        tk, tp = t.order()
+        assert np.array_equal(keys[sl], tk)
+        assert np.array_equal(perm[sl].astype(np.int64), tp + off[k])
+        cidx = np.nonzero(csys == k)[0]
+        c0, nc = int(cidx[0]), len(cidx)
+        assert np.array_equal(cidx, np.arange(c0, c0 + nc))
+        c = t.cells()
+        cs = slice(c0, c0 + nc)
+        assert nc == len(c.level)
+        assert np.array_equal(lv[cs], c.level) and np.array_equal(ct[cs], c.count)
+        assert np.array_equal(fi[cs].astype(np.int64), c.first + off[k])
+        assert np.array_equal(sk[cs].astype(np.int64), c.skip + c0)
+        assert np.array_equal(np.where(pa[cs] == NONE, -1, pa[cs].astype(np.int64) - c0), c.parent)
+        gidx = np.nonzero(gsys == k)[0]
+        g0, ng = int(gidx[0]), len(gidx)
+        gr = t.groups()
+        assert ng == len(gr["first"])
+        assert np.array_equal(gf[g0:g0 + ng].astype(np.int64), gr["first"] + off[k])
+        assert np.array_equal(gc[g0:g0 + ng], gr["count"].astype(np.uint32))
+        teo, te, tso, ts = t.lists()
+        assert np.array_equal(np.diff(eo[g0:g0 + ng + 1]).astype(np.int64), np.diff(teo))
+        assert np.array_equal(np.diff(so[g0:g0 + ng + 1]).astype(np.int64), np.diff(tso))
+        assert np.array_equal(e[eo[g0]:eo[g0 + ng]].astype(np.int64), te + off[k])
+        assert np.array_equal(s[so[g0]:so[g0 + ng]].astype(np.int64), ts + c0)
+        ref = t.force()
+        assert rms_rel_acc(a[sl], ref) <= FORCE_RMS_TOL
+        assert rms_rel_pot(a[sl], ref) <= POT_RMS_TOL
+    g.close()
+
+
 @pytest.mark.parametrize("learned", [False, True])
 def test_batched_systems_match_per_system_oracle(env, learned):
     """Several independent systems in one context (one set of launches): each
