@@ -182,18 +182,6 @@ __device__ __forceinline__ uint32_t h2_from_f2(f2 v) {
   return r;
 }
 template <int FAR>
-__device__ __forceinline__ f2 f2_from_h2(uint32_t v) {
-  float a, b;
-  if (FAR == 1) {
-    a = __uint_as_float(v << 16);
-    b = __uint_as_float(v & 0xffff0000u);
-  } else {
-    asm("{.reg .f16 lo, hi; mov.b32 {lo, hi}, %2; cvt.f32.f16 %0, lo; cvt.f32.f16 %1, hi;}"
-        : "=f"(a), "=f"(b) : "r"(v));
-  }
-  return pk(a, b);
-}
-template <int FAR>
 __device__ __forceinline__ uint32_t hfma2(uint32_t a, uint32_t b, uint32_t c) {
   uint32_t d;
   if (FAR == 1) asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
@@ -211,19 +199,30 @@ template <int FAR>
 __device__ __forceinline__ uint32_t hconst2(float v) {
   return h2_from_f2<FAR>(pk(v, v));
 }
-// c + a b for the two halves of FP16 pairs a, b into the FP32 pair c: the
-// product of two FP16 values is exact in FP32, so each half is one rounding
-// to FP32 (mixed-precision FMA), with no FP16 product or conversion between.
+// c + a b for the two halves of half-precision pairs a, b (BF16 or FP16)
+// into the FP32 pair c: the product of two such values is exact in FP32,
+// so each half is one rounding to FP32 (mixed-precision FMA), with no
+// half-precision product or conversion between.
+template <int FAR>
 __device__ __forceinline__ f2 fma_h2_f32(uint32_t a, uint32_t b, f2 c) {
   float c0, c1;
   upk(c, c0, c1);
-  asm("{.reg .f16 a0, a1, b0, b1;\n\t"
-      "mov.b32 {a0, a1}, %2;\n\t"
-      "mov.b32 {b0, b1}, %3;\n\t"
-      "fma.rn.f32.f16 %0, a0, b0, %0;\n\t"
-      "fma.rn.f32.f16 %1, a1, b1, %1;}"
-      : "+f"(c0), "+f"(c1)
-      : "r"(a), "r"(b));
+  if (FAR == 1)
+    asm("{.reg .b16 a0, a1, b0, b1;\n\t"
+        "mov.b32 {a0, a1}, %2;\n\t"
+        "mov.b32 {b0, b1}, %3;\n\t"
+        "fma.rn.f32.bf16 %0, a0, b0, %0;\n\t"
+        "fma.rn.f32.bf16 %1, a1, b1, %1;}"
+        : "+f"(c0), "+f"(c1)
+        : "r"(a), "r"(b));
+  else
+    asm("{.reg .b16 a0, a1, b0, b1;\n\t"
+        "mov.b32 {a0, a1}, %2;\n\t"
+        "mov.b32 {b0, b1}, %3;\n\t"
+        "fma.rn.f32.f16 %0, a0, b0, %0;\n\t"
+        "fma.rn.f32.f16 %1, a1, b1, %1;}"
+        : "+f"(c0), "+f"(c1)
+        : "r"(a), "r"(b));
   return pk(c0, c1);
 }
 
@@ -277,21 +276,13 @@ __device__ __forceinline__ void interact_far_half(float4 a, float4 b, uint4 qa, 
   const uint32_t BX = hfma2<FAR>(SG, hfma2<FAR>(C, UX, PX), UX);
   const uint32_t BY = hfma2<FAR>(SG, hfma2<FAR>(C, UY, PY), UY);
   const uint32_t BZ = hfma2<FAR>(SG, hfma2<FAR>(C, UZ, PZ), UZ);
-  if (FAR == 2) {  // FP16: the product accumulated straight into FP32
-    AX = fma_h2_f32(MU, BX, AX);
-    AY = fma_h2_f32(MU, BY, AY);
-    AZ = fma_h2_f32(MU, BZ, AZ);
-  } else {
-    AX = add2(AX, f2_from_h2<FAR>(hmul2<FAR>(MU, BX)));
-    AY = add2(AY, f2_from_h2<FAR>(hmul2<FAR>(MU, BY)));
-    AZ = add2(AZ, f2_from_h2<FAR>(hmul2<FAR>(MU, BZ)));
-  }
+  // the products accumulated straight into the FP32 sums
+  AX = fma_h2_f32<FAR>(MU, BX, AX);
+  AY = fma_h2_f32<FAR>(MU, BY, AY);
+  AZ = fma_h2_f32<FAR>(MU, BZ, AZ);
   const uint32_t PQ = hmul2<FAR>(hmul2<FAR>(hconst2<FAR>(-0.5f), SG), T);
-  if (FAR == 2) {  // the quadrupole correction (M' / rs) PQ with M' / rs rounded to FP16
-    PP = fma_h2_f32(h2_from_f2<FAR>(MR), PQ, add2(PP, MR));
-  } else {
-    PP = fma2(MR, f2_from_h2<FAR>(PQ), add2(PP, MR));
-  }
+  // the quadrupole correction (M' / rs) PQ, M' / rs rounded to half precision
+  PP = fma_h2_f32<FAR>(h2_from_f2<FAR>(MR), PQ, add2(PP, MR));
 }
 
 // Shared-memory staging of one warp: raw j data of two chunks in flight
