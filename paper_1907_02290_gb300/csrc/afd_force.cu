@@ -57,7 +57,7 @@ namespace {
 #define AFD_FORCE_QUAD_IPT2 1  // the quadrupole kernel also two i-particles per lane
 #endif
 #ifndef AFD_FORCE_QUAD_REGS
-#define AFD_FORCE_QUAD_REGS 128  // register budget of the quadrupole kernel
+#define AFD_FORCE_QUAD_REGS 112  // register budget of the quadrupole kernel
 #endif
 #ifndef AFD_FORCE_PERSISTENT
 #define AFD_FORCE_PERSISTENT 0  // warps take units from an atomic queue
@@ -712,8 +712,8 @@ __device__ __forceinline__ bool launch_item(const ForceArgs &a, int64_t k, int64
 
 // Block shape is a launch choice (2, 4 or 8 warps): each warp's staging area
 // lives in dynamic shared memory. The register budget is the same for every
-// shape: 96 per thread with FP32 monopoles, 128 with quadrupoles (two
-// i-particles per lane in both).
+// shape: 96 per thread with FP32 monopoles, 112 with quadrupoles (two
+// i-particles per lane in both; 104 and 128 measured slower).
 constexpr int kForceMaxThreads = 256;
 
 template <bool GUARD, bool QUAD, int FAR, int CH>
