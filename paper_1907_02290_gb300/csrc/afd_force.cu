@@ -784,54 +784,6 @@ __global__ void __launch_bounds__(256) k_far_half(int64_t nc, const double *__re
                       h2_from_f2<FAR>(pk(q[4], q[5])), __float_as_uint(s2));
 }
 
-// Half-precision far field, per group: the scale 2^-k_g, 2^k_g the smallest
-// power of two >= the largest M / d^2 over the group's SPJ cells (d the
-// distance from the cell's centre of mass to the group's box, which bounds
-// M / rs^2 for every particle of the group). One warp per group.
-__global__ void __launch_bounds__(256) k_far_scale(int64_t ng, const uint64_t *__restrict__ off_s,
-                                                   const uint32_t *__restrict__ spj,
-                                                   const float4 *__restrict__ s_hi,
-                                                   const float *__restrict__ boxf,
-                                                   uint64_t n_cells, float *__restrict__ gscale) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ng; g += warps) {
-    float bmin[3], bmax[3];
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-      bmin[k] = boxf[g * 6 + k];
-      bmax[k] = boxf[g * 6 + 3 + k];
-    }
-    float mu = 0.0f;
-    for (uint64_t k = off_s[g] + lane; k < off_s[g + 1]; k += 32) {
-      uint32_t j = spj[k];
-      if (!AFD_IN(j, n_cells, "far scale cell")) j = 0u;
-      const float4 h = s_hi[j];
-      const float c[3] = {h.x, h.y, h.z};
-      float d2 = 0.0f;
-#pragma unroll
-      for (int a = 0; a < 3; a++) {
-        const float d = c[a] < bmin[a] ? bmin[a] - c[a] : (c[a] > bmax[a] ? c[a] - bmax[a] : 0.0f);
-        d2 = fmaf(d, d, d2);
-      }
-      if (d2 > 0.0f) mu = fmaxf(mu, h.w / d2);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mu = fmaxf(mu, __shfl_xor_sync(0xffffffffu, mu, o));
-    if (lane == 0) {
-      // 2^-k with 2^k >= mu, k clamped to [-100, 100]; 1 without far-field mass
-      int k = 0;
-      if (mu > 0.0f && mu <= 3.4e38f) {
-        const uint32_t b = __float_as_uint(mu);
-        k = (int)((b >> 23) & 0xffu) - 127 + ((b & 0x7fffffu) != 0u ? 1 : 0);
-        k = k < -100 ? -100 : (k > 100 ? 100 : k);
-      } else if (mu > 0.0f) {
-        k = 100;
-      }
-      gscale[g] = __uint_as_float((uint32_t)(127 - k) << 23);
-    }
-  }
-}
 
 // Non-indirect ablation: copy every list entry's j-data into list order.
 __global__ void k_materialize(uint64_t n, const uint32_t *__restrict__ idx,
@@ -901,7 +853,6 @@ __global__ void k_unit_work(int64_t u0, int64_t nu, const uint2 *__restrict__ u_
 
 int order_units(afd_ctx *c) {
   c->u_order_ok = false;
-  c->fscale_ok = false;  // new lists: the far-field scales follow them
   const int64_t u0 = c->share_parts > 1 ? c->share_u0 : 0;
   const int64_t u1 = c->share_parts > 1 ? c->share_u1 : c->n_units;
   const int64_t nu = u1 - u0;
@@ -986,11 +937,10 @@ int launch_force_impl(afd_ctx *c, float *acc4, bool materialized) {
   a.sq1 = ptr<float4>(c->s_q1);
   const int far_p = c->cfg.multipole ? c->cfg.far_precision : 0;
   if (far_p) {
-    // the cells' half records from the current moments, and the groups'
-    // scales from the current lists
-    if (reserve(c->s_h, sizeof(uint4) * (size_t)c->n_cells) != AFD_OK ||
-        reserve(c->g_fscale, sizeof(float) * (size_t)c->n_groups) != AFD_OK)
-      return AFD_ERR_OOM;
+    // the cells' half records from the current moments (the groups' scales
+    // came with the lists: the walk writes them)
+    if (!c->fscale_ok) return AFD_ERR_NO_SAVED_LIST;
+    if (reserve(c->s_h, sizeof(uint4) * (size_t)c->n_cells) != AFD_OK) return AFD_ERR_OOM;
     const unsigned nb_c = (unsigned)((c->n_cells + 255) / 256);
     if (far_p == 1)
       k_far_half<1><<<nb_c, 256, 0, c->stream>>>(c->n_cells, ptr<double>(c->c_quad),
@@ -1001,16 +951,6 @@ int launch_force_impl(afd_ctx *c, float *acc4, bool materialized) {
                                                   ptr<double>(c->c_mass), ptr<float4>(c->node_f),
                                                   ptr<uint4>(c->s_h));
     c->launches++;
-    if (!c->fscale_ok) {
-      const int64_t want = (c->n_groups + 7) / 8;
-      const unsigned nb_g = (unsigned)(want < 152 * 16 ? (want > 0 ? want : 1) : 152 * 16);
-      k_far_scale<<<nb_g, 256, 0, c->stream>>>(c->n_groups, ptr<uint64_t>(c->spj_off),
-                                               ptr<uint32_t>(c->spj), ptr<float4>(c->s_hi),
-                                               ptr<float>(c->g_boxf), (uint64_t)c->n_cells,
-                                               ptr<float>(c->g_fscale));
-      c->launches++;
-      c->fscale_ok = true;
-    }
   }
   a.sh = ptr<uint4>(c->s_h);
   a.gscale = ptr<float>(c->g_fscale);

@@ -42,6 +42,23 @@ enum : int {
 };
 int status_to_error(int bits);
 
+// Half-precision far field: the per-group scale 2^-k, 2^k the smallest power
+// of two >= mu (the largest M / d^2 over the group's far-field cells, d the
+// distance from the cell's centre of mass to the group's box, a bound on
+// every far-field term's magnitude M / rs^2), k clamped to [-100, 100]; 1
+// without far-field mass.
+__device__ __forceinline__ float far_group_scale(float mu) {
+  int k = 0;
+  if (mu > 0.0f && mu <= 3.4e38f) {
+    const uint32_t b = __float_as_uint(mu);
+    k = (int)((b >> 23) & 0xffu) - 127 + ((b & 0x7fffffu) != 0u ? 1 : 0);
+    k = k < -100 ? -100 : (k > 100 ? 100 : k);
+  } else if (mu > 0.0f) {
+    k = 100;
+  }
+  return __uint_as_float((uint32_t)(127 - k) << 23);
+}
+
 // Side of the root cell for a scaled largest extent `target` (1.000001 x the
 // extent, Section 4.3 root rule): the smallest power of two >= target; 1 when
 // target is not positive (a zero extent) or NaN; +inf when no finite power of

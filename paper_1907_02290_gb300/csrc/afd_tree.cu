@@ -1074,7 +1074,7 @@ __global__ void __launch_bounds__(kThreads) k_moments_blocks(MomArgs a) {
   const uint32_t p = (uint32_t)t;
   if (n_children(a.child, p) == 0) return;
   // the walk's view of p's children: (COM_f32, s^2) and (first, count |
-  // leaf, id, 0) per octant slot, id = kNone when empty
+  // leaf, id, mass_f32) per octant slot, id = kNone when empty
   for (int o = 0; o < 8; o++) {
     const uint32_t cc = __ldg(&a.child[(size_t)p * 8 + o]);
     uint4 nf = make_uint4(0u, 0u, 0u, 0u), meta = make_uint4(0u, 0u, kNone, 0u);
@@ -1083,7 +1083,7 @@ __global__ void __launch_bounds__(kThreads) k_moments_blocks(MomArgs a) {
       const uint2 ni = a.node_i[cc];
       nf = make_uint4(__float_as_uint(f.x), __float_as_uint(f.y), __float_as_uint(f.z),
                       __float_as_uint(f.w));
-      meta = make_uint4(ni.x, ni.y, cc, 0u);
+      meta = make_uint4(ni.x, ni.y, cc, __float_as_uint(a.s_hi[cc].w));  // w: mass (FP32)
     }
     a.block[((size_t)p * 8 + o) * 2] = nf;
     a.block[((size_t)p * 8 + o) * 2 + 1] = meta;

@@ -92,6 +92,9 @@ struct WalkArgs {
   // neighbour walk: n_groups counts work items (group, seed cell); their
   // group and the cell the walk starts from
   const uint32_t *it_group, *it_root;
+  // half-precision far field: per group the power-of-two scale of its
+  // far-field terms (null: not wanted)
+  float *gscale;
 };
 
 enum : int { kModeTheta = 0, kModeLearned = 1, kModeNeighbour = 2 };
@@ -105,13 +108,14 @@ __device__ __forceinline__ float sep_axis(float c, float lo, float hi) {
 
 __device__ __forceinline__ uint32_t decide(const float *bmin, const float *bmax, float cx,
                                            float cy, float cz, float s2, bool leaf,
-                                           float theta2) {
+                                           float theta2, float &d2o) {
   const float dx = sep_axis(cx, bmin[0], bmax[0]);
   const float dy = sep_axis(cy, bmin[1], bmax[1]);
   const float dz = sep_axis(cz, bmin[2], bmax[2]);
   float d2 = __fmul_rn(dx, dx);
   d2 = __fadd_rn(d2, __fmul_rn(dy, dy));
   d2 = __fadd_rn(d2, __fmul_rn(dz, dz));
+  d2o = d2;
   const float rhs = __fmul_rn(theta2, d2);
   if (s2 < rhs) return kAccept;
   return leaf ? kLeaf : kOpen;
@@ -140,7 +144,7 @@ __device__ __forceinline__ uint32_t learned_pre(const WalkArgs &a, const float *
                                                 const float *bmax, float cx, float cy, float cz,
                                                 float s2, bool leaf, uint32_t id, uint32_t first,
                                                 uint32_t count, uint32_t gfirst,
-                                                const MacGroup &G, float *f) {
+                                                const MacGroup &G, float *f, float &d2o) {
   const uint32_t closed = leaf ? kLeaf : kOpen;
   if (gfirst >= first && gfirst - first < count) return closed;  // holds the group
   const float dx = sep_axis(cx, bmin[0], bmax[0]);
@@ -149,6 +153,7 @@ __device__ __forceinline__ uint32_t learned_pre(const WalkArgs &a, const float *
   float d2 = __fmul_rn(dx, dx);
   d2 = __fadd_rn(d2, __fmul_rn(dy, dy));
   d2 = __fadd_rn(d2, __fmul_rn(dz, dz));
+  d2o = d2;
   if (s2 < __fmul_rn(a.lo2, d2)) return kAccept;
   if (!(s2 < __fmul_rn(a.hi2, d2))) return closed;
   const float4 sh = a.s_hi[id], q0 = a.s_q0[id], q1 = a.s_q1[id];
@@ -229,7 +234,10 @@ __device__ __forceinline__ int64_t take_group(const WalkArgs &a, int lane) {
 // registers (3.035 against 3.16 ms on the 2^20 Plummer lists). The other
 // modes keep the compiler's own choice (34 and 38 registers; a one-block
 // minimum gives them 55 and made the plain construction step 1.6% slower).
-template <int MODE>
+// SCALE: the group's far-field scale for the half-precision far field is
+// tracked (a separate instantiation, so that the other walks keep their
+// registers).
+template <int MODE, bool SCALE>
 __global__ void __launch_bounds__(kWalkThreads, MODE == kModeLearned ? 8 : 0) k_walk(WalkArgs a) {
   constexpr bool LEARNED = MODE == kModeLearned, NBR = MODE == kModeNeighbour;
   __shared__ uint2 stk_all[kWalkWarps][kStack];
@@ -258,9 +266,11 @@ __global__ void __launch_bounds__(kWalkThreads, MODE == kModeLearned ? 8 : 0) k_
     if (LEARNED) mg = mac_group(bmin, bmax, a.g_amin[g], a.eps2);
     uint64_t ne = 0, ns = 0;
     uint32_t nl = 0;  // leaf records
+    float mu = 0.0f;  // largest M / d^2 of this lane's accepted cells (half far field)
     RecStream rs{kNone, kChunk}, rl{kNone, kChunk};
     uint32_t self_pos = 0;  // 1 + EPJ-list position of the group's first particle
     uint32_t root_drop = 0;
+    float root_d2 = 0.0f;  // (a root holds its groups: never accepted, no far-field term)
     if (lane == 0) {
       uint32_t root = NBR ? a.it_root[g] : a.g_root[g];
       if (!AFD_IN(root, a.n_cells, "walk root")) root = 0u;
@@ -272,7 +282,7 @@ __global__ void __launch_bounds__(kWalkThreads, MODE == kModeLearned ? 8 : 0) k_
       const uint32_t d =
           NBR ? decide_nbr(bmin, bmax, a.tbox[(size_t)root * 2], a.tbox[(size_t)root * 2 + 1], leaf)
           : LEARNED ? (leaf ? kLeaf : kOpen)
-                    : decide(bmin, bmax, nf.x, nf.y, nf.z, nf.w, leaf, a.theta2);
+                    : decide(bmin, bmax, nf.x, nf.y, nf.z, nf.w, leaf, a.theta2, root_d2);
       stk[0] = make_entry(d, root, ni.x, cnt);
       root_drop = (NBR && d == kAccept) ? 1u : 0u;
     }
@@ -356,6 +366,7 @@ __global__ void __launch_bounds__(kWalkThreads, MODE == kModeLearned ? 8 : 0) k_
       bool valid = false, leaf_me = false;
       uint2 child_entry = make_uint2(0u, 0u);
       uint32_t d = 0, c_id = 0, c_first = 0, c_cnt = 0;
+      float m_me = 0.0f, d2_me = 0.0f;  // the child's mass and squared distance to the box
       float feat[kMacNF];
 #pragma unroll
       for (int k = 0; k < kMacNF; k++) feat[k] = 0.0f;
@@ -375,6 +386,7 @@ __global__ void __launch_bounds__(kWalkThreads, MODE == kModeLearned ? 8 : 0) k_
           c_id = meta.z;
           c_first = meta.x;
           c_cnt = meta.y & 0x7fffffffu;
+          m_me = __uint_as_float(meta.w);
           const float cx = __uint_as_float(nf.x), cy = __uint_as_float(nf.y),
                       cz = __uint_as_float(nf.z), s2 = __uint_as_float(nf.w);
           if (NBR) {
@@ -382,8 +394,8 @@ __global__ void __launch_bounds__(kWalkThreads, MODE == kModeLearned ? 8 : 0) k_
             valid = d != kAccept;  // a dropped cell takes no stack entry
           } else {
             d = LEARNED ? learned_pre(a, bmin, bmax, cx, cy, cz, s2, leaf_me, c_id, c_first,
-                                      c_cnt, gfirst, mg, feat)
-                        : decide(bmin, bmax, cx, cy, cz, s2, leaf_me, a.theta2);
+                                      c_cnt, gfirst, mg, feat, d2_me)
+                        : decide(bmin, bmax, cx, cy, cz, s2, leaf_me, a.theta2, d2_me);
           }
         }
       }
@@ -415,6 +427,9 @@ __global__ void __launch_bounds__(kWalkThreads, MODE == kModeLearned ? 8 : 0) k_
           }
         }
       }
+      // an accepted cell's far-field magnitude bound M / d^2 (d^2 > 0: the
+      // criterion accepts only cells away from the box)
+      if (SCALE && !NBR && valid && d == kAccept) mu = fmaxf(mu, __fdiv_rn(m_me, d2_me));
       if (valid) child_entry = make_entry(d, c_id, c_first, c_cnt);
       const unsigned vm = __ballot_sync(0xffffffffu, valid);
       // The rewritten positions [f, last] in output order: a position kept
@@ -460,6 +475,11 @@ __global__ void __launch_bounds__(kWalkThreads, MODE == kModeLearned ? 8 : 0) k_
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) self_pos = max(self_pos, __shfl_xor_sync(0xffffffffu, self_pos, o));
+    if (SCALE && !NBR) {  // the group's far-field scale from its accepted cells
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mu = fmaxf(mu, __shfl_xor_sync(0xffffffffu, mu, o));
+      if (lane == 0) a.gscale[g] = far_group_scale(mu);
+    }
     if (lane == 0) {
       a.cnt_e[g] = (uint32_t)ne;
       a.cnt_s[g] = (uint32_t)ns;
@@ -664,14 +684,14 @@ struct WalkOut {
   uint64_t n_e = 0, n_s = 0, inter = 0;
 };
 
-// Blocks of k_walk<MODE> resident at once on the device (at most one per
-// four groups): the grid of the dynamically scheduled walk.
-template <int MODE>
+// Blocks of k_walk<MODE, SCALE> resident at once on the device (at most one
+// per four groups): the grid of the dynamically scheduled walk.
+template <int MODE, bool SCALE>
 int64_t walk_blocks(int64_t ng) {
   static int per_sm = 0;
   if (per_sm == 0) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_walk<MODE>, kWalkThreads, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_walk<MODE, SCALE>, kWalkThreads, 0) !=
             cudaSuccess ||
         b < 1)
       b = 1;
@@ -709,9 +729,12 @@ int run_walk(afd_ctx *c, WalkArgs &a, int mode, WalkOut &o, int64_t ng) {
   a.stack_cap = c->walk_stack_cap > 0 ? c->walk_stack_cap : kStack;
   a.n_cells = (uint32_t)c->n_cells;
   a.n_groups = ng;
-  const int64_t nb = mode == kModeLearned ? walk_blocks<kModeLearned>(ng)
-                     : nbr                ? walk_blocks<kModeNeighbour>(ng)
-                                          : walk_blocks<kModeTheta>(ng);
+  const bool scale = a.gscale != nullptr;
+  const int64_t nb = mode == kModeLearned ? (scale ? walk_blocks<kModeLearned, true>(ng)
+                                                   : walk_blocks<kModeLearned, false>(ng))
+                     : nbr ? walk_blocks<kModeNeighbour, false>(ng)
+                           : (scale ? walk_blocks<kModeTheta, true>(ng)
+                                    : walk_blocks<kModeTheta, false>(ng));
   a.queue = ptr<unsigned long long>(c->u64acc) + 4;
   unsigned long long *inter = ptr<unsigned long long>(c->u64acc) + 1;
   uint64_t *pin = static_cast<uint64_t *>(c->pinned);
@@ -733,9 +756,16 @@ int run_walk(afd_ctx *c, WalkArgs &a, int mode, WalkOut &o, int64_t ng) {
     if (mode == kModeLearned && cudaMemsetAsync(c->mac_cnt.p, 0, 3 * sizeof(unsigned long long),
                                                 c->stream) != cudaSuccess)
       return AFD_ERR_CUDA;
-    if (mode == kModeLearned) k_walk<kModeLearned><<<(unsigned)nb, kWalkThreads, 0, c->stream>>>(a);
-    else if (nbr) k_walk<kModeNeighbour><<<(unsigned)nb, kWalkThreads, 0, c->stream>>>(a);
-    else k_walk<kModeTheta><<<(unsigned)nb, kWalkThreads, 0, c->stream>>>(a);
+    if (mode == kModeLearned && scale)
+      k_walk<kModeLearned, true><<<(unsigned)nb, kWalkThreads, 0, c->stream>>>(a);
+    else if (mode == kModeLearned)
+      k_walk<kModeLearned, false><<<(unsigned)nb, kWalkThreads, 0, c->stream>>>(a);
+    else if (nbr)
+      k_walk<kModeNeighbour, false><<<(unsigned)nb, kWalkThreads, 0, c->stream>>>(a);
+    else if (scale)
+      k_walk<kModeTheta, true><<<(unsigned)nb, kWalkThreads, 0, c->stream>>>(a);
+    else
+      k_walk<kModeTheta, false><<<(unsigned)nb, kWalkThreads, 0, c->stream>>>(a);
     c->launches++;
     if (cudaGetLastError() != cudaSuccess) return AFD_ERR_CUDA;
     if ((st = scan_u32_to_u64(c, a.cnt_e, ptr<uint64_t>(*o.off_e), ng))) return st;
@@ -872,7 +902,15 @@ int launch_walk(afd_ctx *c) {
   o.off_s = &c->spj_off;
   o.epj = &c->epj;
   o.spj = &c->spj;
+  // the half-precision far field's per-group scales come with the lists
+  c->fscale_ok = false;
+  const bool half_far = c->cfg.multipole && c->cfg.far_precision != 0;
+  if (half_far) {
+    if ((st = reserve(c->g_fscale, sizeof(float) * (size_t)ng))) return st;
+    a.gscale = ptr<float>(c->g_fscale);
+  }
   if ((st = run_walk(c, a, learned ? kModeLearned : kModeTheta, o, ng))) return st;
+  c->fscale_ok = half_far;
   c->n_epj = o.n_e;
   c->n_spj = o.n_s;
   c->interactions = o.inter;
