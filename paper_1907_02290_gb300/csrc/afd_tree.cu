@@ -636,46 +636,70 @@ __device__ __forceinline__ int64_t gallop_down(const uint64_t *K, int64_t lo, in
   return lower_bound_key(K, q + 1, top, v);
 }
 
-__global__ void __launch_bounds__(kThreads) k_link_emit(
-    const uint64_t *__restrict__ K, const uint8_t *__restrict__ dI, const uint8_t *__restrict__ eI,
-    const uint32_t *__restrict__ off, int64_t n, const uint32_t *__restrict__ sys_s,
-    const int64_t *__restrict__ sys_off, uint32_t *__restrict__ level,
-    uint32_t *__restrict__ first, uint32_t *__restrict__ count, uint32_t *__restrict__ skip,
-    uint32_t *__restrict__ parent, uint32_t *__restrict__ child) {
+// Each particle writes the level and first particle of the cells it starts
+// (a few stores, no searches); k_link_cells then completes every cell on a
+// thread of its own, so that the long searches of the large cells near the
+// root (one particle starts all of them) run side by side.
+__global__ void __launch_bounds__(kThreads) k_link_emit(const uint8_t *__restrict__ dI,
+                                                        const uint8_t *__restrict__ eI,
+                                                        const uint32_t *__restrict__ off,
+                                                        int64_t n, uint32_t *__restrict__ level,
+                                                        uint32_t *__restrict__ first) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const int d = dI[i] == 255 ? -1 : (int)dI[i];
+  const int E = eI[i];
+  for (int l = d + 1; l <= E; l++) {
+    const uint32_t id = off[i] + (uint32_t)(l - d - 1);
+    level[id] = (uint32_t)l;
+    first[id] = (uint32_t)i;
+  }
+}
+
+// Cell id of level l started by particle i: its particle count and skip
+// (the end of its key prefix, by a galloping search), its parent (the
+// previous cell of the same particle, or the cell of level l - 1 that holds
+// i, found by a search back to that prefix's first particle) and its slot
+// among the parent's children.
+__global__ void __launch_bounds__(kThreads) k_link_cells(
+    const uint64_t *__restrict__ K, const uint8_t *__restrict__ dI,
+    const uint32_t *__restrict__ off, int64_t n, int64_t n_cells,
+    const uint32_t *__restrict__ sys_s, const int64_t *__restrict__ sys_off,
+    const uint32_t *__restrict__ level, const uint32_t *__restrict__ first,
+    uint32_t *__restrict__ count, uint32_t *__restrict__ skip, uint32_t *__restrict__ parent,
+    uint32_t *__restrict__ child) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_cells) return;
+  const uint32_t id = (uint32_t)t;
+  const int64_t i = first[id];
+  if (!AFD_IN(i, n, "link cell first")) return;
+  const int l = (int)level[id];
   int64_t sstart, send;
   sys_range(sys_s, sys_off, n, i, sstart, send);
   const int d = dI[i] == 255 ? -1 : (int)dI[i];
-  const int E = eI[i];
   const uint64_t ki = K[i];
-  for (int l = d + 1; l <= E; l++) {
-    const uint32_t id = off[i] + (uint32_t)(l - d - 1);
-    int64_t end = send;
-    if (l > 0) {
-      const int shift = 3 * (kLevels - l);
-      const uint64_t P = ki >> shift;
-      end = gallop_up(K, i + 1, send, (P + 1) << shift);
-    }
-    level[id] = (uint32_t)l;
-    first[id] = (uint32_t)i;
-    count[id] = (uint32_t)(end - i);
-    skip[id] = off[end];
-    uint32_t par = kNone;
-    if (l > 0) {
-      if (l - 1 >= d + 1) {
-        par = id - 1;
-      } else {
-        const int pshift = 3 * (kLevels - l + 1);
-        const uint64_t PP = ki >> pshift;
-        const int64_t s = gallop_down(K, sstart, i, PP << pshift);
-        const int ds = dI[s] == 255 ? -1 : (int)dI[s];
-        par = off[s] + (uint32_t)((l - 1) - ds - 1);
-      }
-      child[(size_t)par * 8 + ((ki >> (3 * (kLevels - l))) & 7u)] = id;
-    }
-    parent[id] = par;
+  int64_t end = send;
+  if (l > 0) {
+    const int shift = 3 * (kLevels - l);
+    const uint64_t P = ki >> shift;
+    end = gallop_up(K, i + 1, send, (P + 1) << shift);
   }
+  count[id] = (uint32_t)(end - i);
+  skip[id] = off[end];
+  uint32_t par = kNone;
+  if (l > 0) {
+    if (l - 1 >= d + 1) {
+      par = id - 1;
+    } else {
+      const int pshift = 3 * (kLevels - l + 1);
+      const uint64_t PP = ki >> pshift;
+      const int64_t s = gallop_down(K, sstart, i, PP << pshift);
+      const int ds = dI[s] == 255 ? -1 : (int)dI[s];
+      par = off[s] + (uint32_t)((l - 1) - ds - 1);
+    }
+    child[(size_t)par * 8 + ((ki >> (3 * (kLevels - l))) & 7u)] = id;
+  }
+  parent[id] = par;
 }
 
 // ---------------------------------------------------------------------------
@@ -1430,12 +1454,13 @@ int launch_link(afd_ctx *c, int64_t n) {
   AFD_TRY(reserve(c->c_child, u * 8));
   if (cudaMemsetAsync(c->c_child.p, 0xff, u * 8, c->stream) != cudaSuccess) return AFD_ERR_CUDA;
   k_link_emit<<<blocks_for(n), kThreads, 0, c->stream>>>(
-      ptr<uint64_t>(c->keys), ptr<uint8_t>(c->lk_d), ptr<uint8_t>(c->lk_e),
-      ptr<uint32_t>(c->lk_off), n, sys_s, sys_off, ptr<uint32_t>(c->c_level),
-      ptr<uint32_t>(c->c_first),
-      ptr<uint32_t>(c->c_count), ptr<uint32_t>(c->c_skip), ptr<uint32_t>(c->c_parent),
-      ptr<uint32_t>(c->c_child));
-  c->launches++;
+      ptr<uint8_t>(c->lk_d), ptr<uint8_t>(c->lk_e), ptr<uint32_t>(c->lk_off), n,
+      ptr<uint32_t>(c->c_level), ptr<uint32_t>(c->c_first));
+  k_link_cells<<<blocks_for(nc), kThreads, 0, c->stream>>>(
+      ptr<uint64_t>(c->keys), ptr<uint8_t>(c->lk_d), ptr<uint32_t>(c->lk_off), n, nc, sys_s,
+      sys_off, ptr<uint32_t>(c->c_level), ptr<uint32_t>(c->c_first), ptr<uint32_t>(c->c_count),
+      ptr<uint32_t>(c->c_skip), ptr<uint32_t>(c->c_parent), ptr<uint32_t>(c->c_child));
+  c->launches += 2;
   c->leaf_ord_ok = false;  // a new topology: the leaf order is made when first needed
   return ck();
 }
