@@ -111,6 +111,10 @@ CASES = {
                                  dict(n_leaf=4, n_grp=16, theta=0.3, eps=1.0 / 128)),
     "galaxy_40k_quad": (lambda: ics.galaxy(40000, 3),
                         dict(n_grp=512, theta=0.4, eps=1.0 / 2048, quad=True)),
+    # leaves of up to 80 particles: the link's windows are read from global
+    # memory (the kernel stages windows of up to 64 in shared memory)
+    "plummer_30k_leaf80": (lambda: ics.plummer(30000 + 11, 12),
+                           dict(n_leaf=80, n_grp=160, theta=0.5, eps=1.0 / 512)),
 }
 
 
