@@ -236,9 +236,11 @@ __device__ __forceinline__ f2 fma_h2_f32(uint32_t a, uint32_t b, f2 c) {
 //   a = (M / rs^2) [u + sigma (P - 2.5 T u)],
 //   phi_sum = (M / rs) (1 - 0.5 sigma T)           (phi = -phi_sum).
 // The geometry (d, rs, u, sigma) is FP32; u, sigma, the shape and the
-// magnitude M' / rs^2 are rounded to half precision and the bracket and its
-// product with the magnitude are half-precision arithmetic; the results are
-// converted to FP32 and accumulated in FP32. M' = M 2^-k_g carries the
+// magnitude M' / rs^2 are rounded to half precision and the bracket is
+// half-precision arithmetic; its product with the magnitude goes straight
+// into the FP32 sums by a mixed-precision FMA (fma_h2_f32; likewise the
+// potential's quadrupole correction with M' / rs rounded to half). The
+// group's scale (computed by the list walk): M' = M 2^-k_g carries the
 // group's power-of-two scale (2^k_g >= the largest M / d^2 over the group's
 // far-field cells), so every magnitude is at most about 1 and the FP16
 // range (2^16 above that, 2^-24 below) holds the group's terms; the
