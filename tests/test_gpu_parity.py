@@ -111,8 +111,8 @@ CASES = {
                                  dict(n_leaf=4, n_grp=16, theta=0.3, eps=1.0 / 128)),
     "galaxy_40k_quad": (lambda: ics.galaxy(40000, 3),
                         dict(n_grp=512, theta=0.4, eps=1.0 / 2048, quad=True)),
-    # leaves of up to 80 particles: the link's windows are read from global
-    # memory (the kernel stages windows of up to 64 in shared memory)
+    # leaves of up to 80 particles: long link windows (n_leaf + 1 keys) and
+    # groups of up to 160
     "plummer_30k_leaf80": (lambda: ics.plummer(30000 + 11, 12),
                            dict(n_leaf=80, n_grp=160, theta=0.5, eps=1.0 / 512)),
 }
@@ -245,8 +245,10 @@ def test_signed_zero_coordinates(env):
     g.close()
 
 
-def test_zero_softening(env):
-    """eps = 0 takes the guarded kernel: coincident pairs contribute nothing."""
+@pytest.mark.parametrize("quad", [False, True])
+def test_zero_softening(env, quad):
+    """eps = 0 takes the guarded kernel: coincident pairs contribute nothing
+    (monopole and quadrupole superparticles)."""
     _, _, orc = env
     p = ics.plummer(6000, 21)
     x = p.x.copy()
@@ -255,10 +257,10 @@ def test_zero_softening(env):
     y[:10] = y[10]
     z[:10] = z[10]
     q = ics.Particles(x, y, z, p.vx, p.vy, p.vz, p.m)
-    kw = dict(n_grp=64, theta=0.5, eps=0.0)
+    kw = dict(n_grp=64, theta=0.5, eps=0.0, quad=quad)
     g, acc, _ = run_gpu(env, q, **kw)
     t = orc.Tree(x, y, z, p.m, **kw)
-    check_structure(g, t)
+    check_structure(g, t, quad=quad)
     ref = t.force()
     assert np.all(np.isfinite(acc))
     assert rms_rel_acc(acc[20:], [r[20:] for r in ref]) <= 2e-6
